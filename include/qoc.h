@@ -1,0 +1,198 @@
+/*
+ * qoc.h -- C ABI of the GB300 (sm_103a) library for the exact gradient and
+ * Hessian of the discrete quantum-optimal-control cost by the first- and
+ * second-order adjoint method (H. S. Bhat, "Second-Order Adjoint Method for
+ * Quantum Optimal Control", arXiv 2505.00529).
+ *
+ * The problem (Sec. II, Eqs. Zdef, discTDSE, discretecost, with weights):
+ *
+ *   f   = B theta                       (linear control model, f_j = f(j dt))
+ *   H_j = H0 + f_j M,   U_j = exp(-i dt H_j),   a_{j+1} = U_j a_j,  a_0 = alpha
+ *   J(theta) = w_ctrl * sum_j f_j^2 + w_term * |a_J - beta|^2
+ *
+ * The paper's cost is w_ctrl = 1/2, w_term = rho/2.  The library computes
+ * J, dJ/dtheta (first-order adjoint, Eqs. lambdasys, dLdf; Alg. 1) and the
+ * full K x K Hessian (second-order adjoint, Eqs. musys, gradatheta, d2Ldf2;
+ * Alg. 2), and runs an exact-Hessian trust-region iteration on top of them
+ * (Sec. IV-B).  Every step of an evaluation runs in CUDA kernels on the
+ * device; the host only validates arguments, moves theta in and the results
+ * out, and sequences launches.
+ *
+ * Conventions for every entry point:
+ *   - All floating point arguments are IEEE binary64 (double).
+ *   - Matrices are row-major.  Complex vectors are interleaved (re, im):
+ *     a complex vector of length N is 2N doubles.
+ *   - Host pointers are read during the call only; the caller keeps
+ *     ownership.  Output buffers are caller-allocated.
+ *   - Entry points with the suffix _dev take DEVICE pointers, enqueue work on
+ *     the problem's stream and return without synchronising.
+ *   - Errors are returned as qoc_status, never thrown; the library never
+ *     exits the process and never traps on the device.  After QOC_ECUDA the
+ *     CUDA context may be unusable.
+ *   - A problem object is not thread-safe: calls on one problem must not
+ *     overlap.  Distinct problems may be used from distinct threads.
+ */
+#ifndef QOC_H
+#define QOC_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct qoc_problem qoc_problem; /* opaque; owns all of its device memory */
+
+typedef enum {
+  QOC_OK = 0,
+  QOC_EINVAL = 1,       /* bad argument: null pointer, size out of range, non-symmetric H0/M, ... */
+  QOC_ENOMEM = 2,       /* device or host allocation failed */
+  QOC_ECUDA = 3,        /* a CUDA runtime call or kernel launch failed */
+  QOC_ENUMERIC = 4,     /* non-finite input/output or an eigensolver that did not converge */
+  QOC_ENOTCONV = 5,     /* trust region hit max_iter (best iterate still returned) */
+  QOC_ETIMEOUT = 6,     /* a bounded device wait gave up (kernel returned early) */
+  QOC_EUNSUPPORTED = 7  /* valid request this build does not implement (e.g. N too large) */
+} qoc_status;
+
+/* Arithmetic of the per-step propagator products (the time-stepped sweeps).
+ *   QOC_FP64       : every operation in binary64 ("plain FP64").
+ *   QOC_MIXED_FP32 : propagator-times-panel products in binary32 on the
+ *                    increment D_j = exp(-i dt (H_j - m)) - I with the state
+ *                    carried as an unevaluated float pair; eigendecomposition,
+ *                    divided differences, contractions and the gradient /
+ *                    Hessian accumulation stay binary64. */
+typedef enum { QOC_FP64 = 0, QOC_MIXED_FP32 = 1 } qoc_precision;
+
+/* Which exact form of the Hessian to assemble (both are Eq. d2Ldf2):
+ *   QOC_HESS_SECOND_ORDER_ADJOINT : Alg. 2 -- forward tangent panel S_j and
+ *       backward second-order adjoint panel mu_j,
+ *       Hess = B^T diag(2w+c) B + B^T V + B^T U.
+ *   QOC_HESS_TANGENT : the mu recursion unrolled (no backward panel),
+ *       Hess = B^T diag(2w+c) B + 2 w_term Re(S_J^H S_J) + B^T U + U^T B. */
+typedef enum { QOC_HESS_SECOND_ORDER_ADJOINT = 0, QOC_HESS_TANGENT = 1 } qoc_hess_method;
+
+/* Eigensolver for the per-step H_j (Alg. 2 first loop).
+ *   QOC_EIG_REFINED      : binary32 cyclic Jacobi followed by binary64
+ *                          Ogita-Aishima refinement sweeps (default).
+ *   QOC_EIG_JACOBI_FP64  : binary64 cyclic Jacobi throughout. */
+typedef enum { QOC_EIG_REFINED = 0, QOC_EIG_JACOBI_FP64 = 1 } qoc_eig_method;
+
+/* Create a problem.  Sec. II / Eq. discretecost.
+ *   N          basis size, 1 <= N <= qoc_max_basis_size().
+ *   H0, M      N*N real symmetric (checked to 1e-12 relative), row-major.
+ *   a0, a_target  N complex, interleaved (2N doubles): alpha and beta.
+ *   K          number of control coefficients (>= 1).
+ *   basis      steps*K row-major: basis[j*K + l] = d f_j / d theta_l.
+ *   dt         time step (> 0); steps = J >= 1 (T = J dt).
+ *   w_ctrl, w_term  cost weights (>= 0).
+ *   precision  a qoc_precision value.
+ *   cuda_stream  cudaStream_t to run on, or NULL for a library-owned stream.
+ *   out        receives the new problem.
+ * Device memory for every intermediate (O(J N^2)) is allocated here; no later
+ * call allocates. */
+qoc_status qoc_create_problem(int N, const double* H0, const double* M,
+                              const double* a0, const double* a_target,
+                              int K, const double* basis, double dt, int steps,
+                              double w_ctrl, double w_term, int precision,
+                              void* cuda_stream, qoc_problem** out);
+
+/* Select the Hessian form (qoc_hess_method) / eigensolver (qoc_eig_method). */
+qoc_status qoc_set_hess_method(qoc_problem* p, int method);
+qoc_status qoc_set_eig_method(qoc_problem* p, int method);
+
+/* J(theta), Eq. discretecost.  theta: K host doubles.  J: one host double. */
+qoc_status qoc_eval_J(qoc_problem* p, const double* theta, double* J);
+
+/* J and dJ/dtheta (K host doubles), Eqs. lambdasys and dLdf (Alg. 1). */
+qoc_status qoc_eval_grad(qoc_problem* p, const double* theta, double* J, double* grad);
+
+/* J, gradient and the symmetrised K*K row-major Hessian (Alg. 2, Eq. d2Ldf2). */
+qoc_status qoc_eval_grad_hess(qoc_problem* p, const double* theta, double* J,
+                              double* grad, double* hess);
+
+/* Device-pointer form of qoc_eval_grad_hess: theta_dev (K doubles) is read
+ * and out_dev (1 + K + K*K doubles: J, grad, Hess row-major) written on the
+ * problem's stream; returns after enqueueing.  Device-side failures
+ * (eigensolver non-convergence, bounded-wait timeouts) are reported by the
+ * next qoc_sync_status call. */
+qoc_status qoc_eval_grad_hess_dev(qoc_problem* p, const double* theta_dev, double* out_dev);
+
+/* Wait for the problem's stream and report any device-side status raised
+ * since the last call (clears it). */
+qoc_status qoc_sync_status(qoc_problem* p);
+
+/* Exact-Hessian trust-region iteration (Sec. IV-B; textbook basic trust
+ * region with the exact subproblem; stop rule of Alg. 1/2: |grad| < gtol or
+ * trust radius < xtol).  theta0, theta_out: K host doubles (may alias). */
+typedef struct {
+  double gtol;        /* stop when |grad J| < gtol */
+  double xtol;        /* stop when the trust radius (bound on |step|) < xtol */
+  double radius0;     /* initial radius (> 0) */
+  double radius_max;  /* radius cap (>= radius0) */
+  double eta;         /* accept a step when actual/predicted decrease > eta (0 <= eta < 1/4) */
+  int max_iter;       /* iteration cap (>= 1) */
+} qoc_tr_options;
+
+typedef struct {
+  int iters;          /* iterations performed */
+  int n_eval_J;       /* trial-point cost evaluations */
+  int n_eval_gh;      /* gradient+Hessian evaluations */
+  double J;           /* final cost */
+  double grad_norm;   /* final |grad| */
+  double radius;      /* final trust radius */
+  int stop_reason;    /* 0 gtol, 1 xtol, 2 max_iter (status QOC_ENOTCONV), 3 no predicted decrease */
+} qoc_tr_report;
+
+qoc_status qoc_trust_region_solve(qoc_problem* p, const double* theta0,
+                                  const qoc_tr_options* opt, double* theta_out,
+                                  qoc_tr_report* report);
+
+/* Diagnostics of the last evaluation (host doubles):
+ *   out[0] = max_j | |a_j| - 1 |   (norm drift of the propagated state)
+ *   out[1] = |Hess - Hess^T|_F / |Hess|_F before symmetrisation
+ *   out[2..7] = milliseconds of the phases eig, prep, chains, pointwise,
+ *               panels, assembly (only when timing was enabled, else 0). */
+qoc_status qoc_get_diagnostics(const qoc_problem* p, double* out /* [8] */);
+qoc_status qoc_enable_timing(qoc_problem* p, int on);
+
+/* Copy an intermediate of the last evaluation to the host, for parity
+ * tests against an independent implementation.  `which` and the layout of
+ * the `count` doubles it writes:
+ *   QOC_BUF_F       J doubles: f_j
+ *   QOC_BUF_EIGVAL  J*N: eigenvalues of H_j, ascending
+ *   QOC_BUF_EIGVEC  J*N*N: W_j row-major, column q = eigenvector q
+ *   QOC_BUF_STATE   (J+1)*2N: a_0..a_J (interleaved complex)
+ *   QOC_BUF_COSTATE (J+1)*2N: lambda_1..lambda_J in rows 1..J (row 0 = lambda_0)
+ *   QOC_BUF_G       J: g_j = Re(lambda_{j+1}^H G_j a_j)
+ *   QOC_BUF_C       J: c_j = Re(lambda_{j+1}^H G2_j a_j)
+ *   QOC_BUF_V       J*K: Re(mu_{j+1,l}^H G_j a_j)   (second-order-adjoint form only)
+ *   QOC_BUF_U       J*K: Re(lambda_{j+1}^H G_j S_{j,l})
+ *   QOC_BUF_SJ      N*K*2: S_J = da_J/dtheta (interleaved complex, row-major N x K)
+ *   QOC_BUF_HESS_RAW K*K: Hessian before symmetrisation
+ * Returns QOC_EINVAL if count is smaller than the buffer. */
+enum {
+  QOC_BUF_F = 0, QOC_BUF_EIGVAL = 1, QOC_BUF_EIGVEC = 2, QOC_BUF_STATE = 3,
+  QOC_BUF_COSTATE = 4, QOC_BUF_G = 5, QOC_BUF_C = 6, QOC_BUF_V = 7, QOC_BUF_U = 8,
+  QOC_BUF_SJ = 9, QOC_BUF_HESS_RAW = 10
+};
+qoc_status qoc_read_buffer(const qoc_problem* p, int which, double* host_out, size_t count);
+
+/* Bytes of device memory the problem holds. */
+size_t qoc_device_bytes(const qoc_problem* p);
+
+/* Largest N this build supports. */
+int qoc_max_basis_size(void);
+
+/* Release everything the problem owns (NULL is a no-op). */
+void qoc_destroy_problem(qoc_problem* p);
+
+/* Static, human-readable name of a status. */
+const char* qoc_status_string(qoc_status s);
+
+/* Library ABI version (major*10000 + minor*100 + patch). */
+int qoc_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* QOC_H */
