@@ -1,0 +1,347 @@
+#!/usr/bin/env python
+"""Gradient+Hessian evaluations per second of the discrete quantum-optimal-
+control cost on GB300 (second-order adjoint method, Alg. 2), on the N=32,
+K=64 (sine/cosine), J=4000 workload: CI-shaped synthetic H0 (diagonal
+energies U[-10,0], band-8 couplings N(0,0.1^2)), dense M N(0,0.3^2), T=20.
+
+One step = one full evaluation (J, grad, K x K Hessian) at a fixed seeded
+theta, inputs resident in device memory.  Prints one JSON line (rank 0).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--precision mixed|fp64]
+  python bench.py --impl reference ...   (the FP64 CPU oracle, timed on the host)
+
+A single problem is a dependent chain of J steps and does not shard: with
+N > 1 processes (torchrun) every rank runs an independent replica and the
+value is the total over ranks (weak scaling).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "grad+Hessian evals/s and TR solves/s vs plain FP64 on GB300 at rel err ≤1e-6"
+UNIT = "evals/s"
+WORKLOAD = {"workload": "synthetic CI-shaped single problem, N=32 basis, K=64 sine/cosine "
+                        "coefficients, J=4000 steps, T=20 (dt=0.005)",
+            "N": 32, "K": 64, "J": 4000}
+# library kernel launches per evaluation: control, eig (Jacobi + refine), prep, state chain,
+# terminal, costate chain, pointwise, tangent panel, mu panel, grad, hess partial, hess final
+LAUNCHES_PER_EVAL = 13
+FP64_PEAK_TFLOPS = 1.26    # 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (measured 1.20 at 1.99 GHz)
+FP32_PEAK_TFLOPS = 80.5    # 152 SMs x 128 FMA/clk x 2 flop x 2.07 GHz (measured 70 at 1.99 GHz)
+
+
+def env_int(k, d):
+    try:
+        return int(os.environ.get(k, d))
+    except ValueError:
+        return d
+
+
+# --------------------------------------------------------------------------
+# CPU oracle timing (a deliberately slow reference: spawned process, 1 thread)
+# --------------------------------------------------------------------------
+ORACLE_SNIPPET = r"""
+import sys, time, json
+sys.path.insert(0, %r)
+import numpy as np
+from paper_2505_00529_gb300 import inputs
+from oracle import qoc_oracle as orc
+p = inputs.config_problem(2)
+js = %d
+p.B = p.B[:js]          # first js steps of the same problem (same dt)
+th = inputs.eval_theta(p.K, 0)
+t0 = time.perf_counter()
+r = orc.evaluate(p, th, order=2)
+dt = time.perf_counter() - t0
+print(json.dumps({"seconds": dt, "steps": js}))
+"""
+
+
+def time_oracle(sample_steps: int) -> dict:
+    env = dict(os.environ, OPENBLAS_NUM_THREADS="1", OMP_NUM_THREADS="1", MKL_NUM_THREADS="1",
+               CUDA_VISIBLE_DEVICES="")
+    r = subprocess.run([sys.executable, "-c", ORACLE_SNIPPET % (ROOT, sample_steps)],
+                       capture_output=True, text=True, env=env, timeout=900)
+    if r.returncode != 0:
+        raise RuntimeError(r.stderr[-2000:])
+    d = json.loads(r.stdout.strip().splitlines()[-1])
+    J = WORKLOAD["J"]
+    # the oracle's cost is linear in the number of steps: scale the sample to one full evaluation
+    per_eval = d["seconds"] * J / d["steps"]
+    return {"value": 1.0 / per_eval, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"one oracle evaluation over the first {sample_steps} of the {J} steps "
+                      f"({d['seconds']:.2f} s), scaled by {J}/{sample_steps}"}
+
+
+def run_reference(args):
+    rank = env_int("RANK", 0)
+    if rank != 0:
+        return 0
+    per = []
+    sample = args.ref_sample_steps
+    for _ in range(args.warmup):
+        time_oracle(max(8, sample // 8))
+    for _ in range(args.steps):
+        per.append(1.0 / time_oracle(sample)["value"])
+    ms = 1000.0 * statistics.mean(per)
+    value = 1000.0 / ms
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": dict(WORKLOAD, precision="fp64 (CPU oracle)"),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"each step: one oracle evaluation over the first {sample} "
+                                       f"of {WORKLOAD['J']} steps, scaled to the full problem"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# --------------------------------------------------------------------------
+# clocks during the timed region
+# --------------------------------------------------------------------------
+class ClockSampler:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index, path):
+        self.path = path
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+        try:
+            self.fh.close()
+        except Exception:
+            pass
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        try:
+            for line in open(self.path):
+                f = [x.strip() for x in line.split(",")]
+                if len(f) < 9:
+                    continue
+                try:
+                    sm.append(float(f[1]))
+                    mx = float(f[2])
+                except ValueError:
+                    continue
+                for n, v in zip(names, f[5:9]):
+                    if v.lower() == "active":
+                        reasons.add(n)
+        except FileNotFoundError:
+            pass
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# --------------------------------------------------------------------------
+# our arm
+# --------------------------------------------------------------------------
+def algorithmic_work(N, K, J, precision):
+    """Per-evaluation algorithmic work of each phase (flops), from the
+    method's counts: eig 9N^3, M~ 4N^3, second divided differences 4N^3
+    (one complex-by-real product), propagator-times-vector 8N^2 per vector
+    per step, panels 8N^2 K per step each."""
+    return {
+        "eig": ("alu64", 9.0 * N ** 3 * J),
+        "prep": ("alu64", 8.0 * N ** 3 * J),
+        "chains": ("alu32" if precision == "mixed" else "alu64", 2 * 8.0 * N * N * J),
+        "pointwise": ("alu64", 40.0 * N * N * J),
+        "panels": ("alu32" if precision == "mixed" else "alu64", 2 * 8.0 * N * N * K * J),
+        "assembly": ("alu64", 4.0 * K * K * J),
+    }
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    rank, world, local = env_int("RANK", 0), env_int("WORLD_SIZE", 1), env_int("LOCAL_RANK", 0)
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    import paper_2505_00529_gb300 as q
+    from paper_2505_00529_gb300 import build, inputs
+    build.build()
+
+    prob = inputs.config_problem(2)
+    N, K, J = prob.N, prob.K, prob.J
+    theta = inputs.eval_theta(K, 0)
+    prec = q.QOC_MIXED_FP32 if args.precision == "mixed" else q.QOC_FP64
+    stream = torch.cuda.current_stream()
+    dev = torch.device("cuda", local)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # > L2 (129 MB)
+
+    def measure(precision, steps, warmup, timing=True):
+        P = q.Problem(prob, precision=precision, cuda_stream=stream.cuda_stream)
+        if timing:
+            q.qoc_enable_timing(P.handle, True)
+        th = torch.tensor(theta, dtype=torch.float64, device=dev)
+        out = torch.zeros(1 + K + K * K, dtype=torch.float64, device=dev)
+        for _ in range(warmup):
+            q.qoc_eval_grad_hess_dev(P.handle, th.data_ptr(), out.data_ptr())
+        q.qoc_sync_status(P.handle)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(steps)]
+        phases = []
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        for k in range(steps):
+            flush.fill_(float(k))                         # evict L2 between timed steps
+            ev[k][0].record(stream)
+            q.qoc_eval_grad_hess_dev(P.handle, th.data_ptr(), out.data_ptr())
+            ev[k][1].record(stream)
+            if timing:
+                stream.synchronize()
+                phases.append(q.qoc_get_diagnostics(P.handle)["phase_ms"])
+        torch.cuda.synchronize()
+        q.qoc_sync_status(P.handle)
+        ms = statistics.mean(a.elapsed_time(b) for a, b in ev)
+        if dist:
+            t = torch.tensor([ms], dtype=torch.float64, device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = float(t.item())
+        res = out.cpu().numpy().copy()
+        return P, ms, phases, res
+
+    # ---- headline: device-resident evaluations ----
+    clk = ClockSampler(local, os.path.join(ROOT, "gpurun_out" if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else ".", f"clocks_rank{rank}.csv"))
+    with clk:
+        P, ms, phases, res = measure(prec, args.steps, args.warmup, timing=True)
+    clocks = clk.summary()
+    value = world * 1000.0 / ms
+
+    # ---- end to end through the host API (theta from host, results back to host) ----
+    e2e_times = []
+    for k in range(args.warmup + args.steps):
+        flush.fill_(float(k))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        P.eval_grad_hess(theta)
+        t1 = time.perf_counter()
+        if k >= args.warmup:
+            e2e_times.append(t1 - t0)
+    e2e_ms = 1000.0 * statistics.mean(e2e_times)
+    if dist:
+        t = torch.tensor([e2e_ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+    P.close()
+
+    # ---- plain FP64 GPU method on the same workload ----
+    fp64 = None
+    if prec != q.QOC_FP64 and not args.no_fp64:
+        P64, ms64, _, res64 = measure(q.QOC_FP64, max(2, args.steps // 4), 1, timing=False)
+        P64.close()
+        hess_rel = float(np.linalg.norm(res[1 + K:] - res64[1 + K:]) / np.linalg.norm(res64[1 + K:]))
+        grad_rel = float(np.linalg.norm(res[1:1 + K] - res64[1:1 + K]) / np.linalg.norm(res64[1:1 + K]))
+        fp64 = {"value": world * 1000.0 / ms64, "unit": UNIT, "ms_per_step": ms64,
+                "speedup_mixed_over_fp64": ms64 / ms,
+                "mixed_vs_fp64_rel_err": {"J": abs(res[0] - res64[0]) / abs(res64[0]),
+                                          "grad": grad_rel, "hess": hess_rel}}
+
+    # ---- trust-region solves (from theta = 0, same problem) ----
+    tr = None
+    if not args.no_tr:
+        with q.Problem(prob, precision=prec, cuda_stream=stream.cuda_stream) as PT:
+            t0 = time.perf_counter()
+            th_star, info = PT.trust_region_solve(np.zeros(K), gtol=1e-6, xtol=1e-10, max_iter=500)
+            t1 = time.perf_counter()
+        tr = {"value": world / (t1 - t0), "unit": "TR solves/s", "iters": info["iters"],
+              "n_eval_gh": info["n_eval_gh"], "n_eval_J": info["n_eval_J"], "J": info["J"],
+              "grad_norm": info["grad_norm"], "stop": info["stop"], "gtol": 1e-6}
+
+    # ---- roofline of the dominant phase ----
+    ph_mean = {k: statistics.mean(p[k] for p in phases) for k in phases[0]} if phases else {}
+    work = algorithmic_work(N, K, J, args.precision)
+    roof = None
+    if ph_mean:
+        dom = max(ph_mean, key=lambda k: ph_mean[k])
+        unit_kind, flops = work[dom]
+        peak = FP64_PEAK_TFLOPS if unit_kind == "alu64" else FP32_PEAK_TFLOPS
+        ach = flops / (ph_mean[dom] * 1e-3) / 1e12
+        roof = {"bound": "alu", "kernel": dom, "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+                "frac": ach / peak, "traffic": None,
+                "peak_source": ("binary64 FMA rate" if unit_kind == "alu64" else "binary32 FMA rate")
+                + " from unit counts x max SM clock (see DESIGN.md); not in MEASURED_PEAKS.json",
+                "phase_ms": ph_mean}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        try:
+            cpu = time_oracle(args.ref_sample_steps)
+        except Exception as e:  # reported, never silently dropped
+            cpu = {"error": str(e)[-300:]}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None,
+                "dtype": "f32 panels + f64" if prec == q.QOC_MIXED_FP32 else "f64",
+                "data": "synthetic",
+                "config": dict(WORKLOAD, precision=args.precision, l2="flushed between timed steps",
+                               parallelism=f"replicas x{world}" if world > 1 else "single problem"),
+                "e2e": {"value": world * 1000.0 / e2e_ms, "unit": UNIT, "ms_per_step": e2e_ms,
+                        "h2d_bytes_per_step": 8 * K, "d2h_bytes_per_step": 8 * (1 + K + K * K)},
+                "gpu_launches": LAUNCHES_PER_EVAL * args.steps,
+                "clocks": clocks, "roofline": roof, "cpu_baseline": cpu,
+                "fp64_plain": fp64, "tr_solve": tr}
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--ref-sample-steps", type=int, default=400)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-tr", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,286 @@
+"""Thin ctypes binding of ``libqoc.so`` (declared in ``include/qoc.h``).
+
+Argument marshalling only: every step of an evaluation runs in the CUDA
+library.  There is no CPU fallback; loading fails loudly when the library
+has not been built (``paper_2505_00529_gb300.build.build()``).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+QOC_OK, QOC_EINVAL, QOC_ENOMEM, QOC_ECUDA, QOC_ENUMERIC, QOC_ENOTCONV, QOC_ETIMEOUT, QOC_EUNSUPPORTED = range(8)
+QOC_FP64, QOC_MIXED_FP32 = 0, 1
+QOC_HESS_SECOND_ORDER_ADJOINT, QOC_HESS_TANGENT = 0, 1
+QOC_EIG_REFINED, QOC_EIG_JACOBI_FP64 = 0, 1
+(QOC_BUF_F, QOC_BUF_EIGVAL, QOC_BUF_EIGVEC, QOC_BUF_STATE, QOC_BUF_COSTATE, QOC_BUF_G, QOC_BUF_C,
+ QOC_BUF_V, QOC_BUF_U, QOC_BUF_SJ, QOC_BUF_HESS_RAW) = range(11)
+
+# every entry point declared in include/qoc.h
+EXPORTS = [
+    "qoc_create_problem", "qoc_set_hess_method", "qoc_set_eig_method", "qoc_eval_J",
+    "qoc_eval_grad", "qoc_eval_grad_hess", "qoc_eval_grad_hess_dev", "qoc_sync_status",
+    "qoc_trust_region_solve", "qoc_get_diagnostics", "qoc_enable_timing", "qoc_read_buffer",
+    "qoc_device_bytes", "qoc_max_basis_size", "qoc_destroy_problem", "qoc_status_string",
+    "qoc_version",
+]
+
+
+class TrOptions(C.Structure):
+    _fields_ = [("gtol", C.c_double), ("xtol", C.c_double), ("radius0", C.c_double),
+                ("radius_max", C.c_double), ("eta", C.c_double), ("max_iter", C.c_int)]
+
+
+class TrReport(C.Structure):
+    _fields_ = [("iters", C.c_int), ("n_eval_J", C.c_int), ("n_eval_gh", C.c_int),
+                ("J", C.c_double), ("grad_norm", C.c_double), ("radius", C.c_double),
+                ("stop_reason", C.c_int)]
+
+
+class QocError(RuntimeError):
+    def __init__(self, status, where):
+        self.status = status
+        super().__init__(f"{where}: {status_string(status)} (status {status})")
+
+
+_LIB = None
+_dp = C.POINTER(C.c_double)
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def lib() -> C.CDLL:
+    """Load libqoc.so (raises if it is missing)."""
+    global _LIB
+    if _LIB is None:
+        path = lib_path()
+        if not os.path.exists(path):
+            raise RuntimeError(f"{path} is missing: build it with paper_2505_00529_gb300.build.build()")
+        L = C.CDLL(path)
+        L.qoc_create_problem.argtypes = [C.c_int, _dp, _dp, _dp, _dp, C.c_int, _dp, C.c_double,
+                                         C.c_int, C.c_double, C.c_double, C.c_int, C.c_void_p,
+                                         C.POINTER(C.c_void_p)]
+        L.qoc_set_hess_method.argtypes = [C.c_void_p, C.c_int]
+        L.qoc_set_eig_method.argtypes = [C.c_void_p, C.c_int]
+        L.qoc_eval_J.argtypes = [C.c_void_p, _dp, _dp]
+        L.qoc_eval_grad.argtypes = [C.c_void_p, _dp, _dp, _dp]
+        L.qoc_eval_grad_hess.argtypes = [C.c_void_p, _dp, _dp, _dp, _dp]
+        L.qoc_eval_grad_hess_dev.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p]
+        L.qoc_sync_status.argtypes = [C.c_void_p]
+        L.qoc_trust_region_solve.argtypes = [C.c_void_p, _dp, C.POINTER(TrOptions), _dp,
+                                             C.POINTER(TrReport)]
+        L.qoc_get_diagnostics.argtypes = [C.c_void_p, _dp]
+        L.qoc_enable_timing.argtypes = [C.c_void_p, C.c_int]
+        L.qoc_read_buffer.argtypes = [C.c_void_p, C.c_int, _dp, C.c_size_t]
+        L.qoc_device_bytes.argtypes = [C.c_void_p]
+        L.qoc_device_bytes.restype = C.c_size_t
+        L.qoc_max_basis_size.argtypes = []
+        L.qoc_destroy_problem.argtypes = [C.c_void_p]
+        L.qoc_destroy_problem.restype = None
+        L.qoc_status_string.argtypes = [C.c_int]
+        L.qoc_status_string.restype = C.c_char_p
+        L.qoc_version.argtypes = []
+        _LIB = L
+    return _LIB
+
+
+def status_string(s: int) -> str:
+    return lib().qoc_status_string(int(s)).decode()
+
+
+def _check(status, where):
+    if status != QOC_OK:
+        raise QocError(status, where)
+
+
+def _ptr(a: np.ndarray):
+    return a.ctypes.data_as(_dp)
+
+
+def _f64(a) -> np.ndarray:
+    return np.ascontiguousarray(np.asarray(a, dtype=np.float64))
+
+
+def _cplx(a) -> np.ndarray:
+    a = np.ascontiguousarray(np.asarray(a, dtype=np.complex128))
+    return a.view(np.float64)
+
+
+# ---------------------------------------------------------------------------
+# same names as the C ABI
+# ---------------------------------------------------------------------------
+
+def qoc_create_problem(N, H0, M, a0, a_target, K, basis, dt, steps, w_ctrl, w_term, precision,
+                       cuda_stream=None):
+    """Returns an opaque handle (int).  Arrays: H0, M (N,N) float; a0, a_target (N,) complex;
+    basis (steps, K) float."""
+    H0 = _f64(H0); M = _f64(M); B = _f64(basis)
+    a0v = _cplx(a0); btv = _cplx(a_target)
+    h = C.c_void_p()
+    st = C.c_void_p(int(cuda_stream)) if cuda_stream else None
+    _check(lib().qoc_create_problem(int(N), _ptr(H0), _ptr(M), _ptr(a0v), _ptr(btv), int(K), _ptr(B),
+                                    float(dt), int(steps), float(w_ctrl), float(w_term),
+                                    int(precision), st, C.byref(h)), "qoc_create_problem")
+    return h.value
+
+
+def qoc_destroy_problem(h):
+    lib().qoc_destroy_problem(C.c_void_p(h))
+
+
+def qoc_set_hess_method(h, method):
+    _check(lib().qoc_set_hess_method(C.c_void_p(h), int(method)), "qoc_set_hess_method")
+
+
+def qoc_set_eig_method(h, method):
+    _check(lib().qoc_set_eig_method(C.c_void_p(h), int(method)), "qoc_set_eig_method")
+
+
+def qoc_enable_timing(h, on=True):
+    _check(lib().qoc_enable_timing(C.c_void_p(h), int(bool(on))), "qoc_enable_timing")
+
+
+def qoc_eval_J(h, theta):
+    th = _f64(theta)
+    J = np.zeros(1)
+    _check(lib().qoc_eval_J(C.c_void_p(h), _ptr(th), _ptr(J)), "qoc_eval_J")
+    return float(J[0])
+
+
+def qoc_eval_grad(h, theta):
+    th = _f64(theta)
+    J = np.zeros(1)
+    g = np.zeros(th.size)
+    _check(lib().qoc_eval_grad(C.c_void_p(h), _ptr(th), _ptr(J), _ptr(g)), "qoc_eval_grad")
+    return float(J[0]), g
+
+
+def qoc_eval_grad_hess(h, theta):
+    th = _f64(theta)
+    K = th.size
+    J = np.zeros(1)
+    g = np.zeros(K)
+    H = np.zeros((K, K))
+    _check(lib().qoc_eval_grad_hess(C.c_void_p(h), _ptr(th), _ptr(J), _ptr(g), _ptr(H)),
+           "qoc_eval_grad_hess")
+    return float(J[0]), g, H
+
+
+def qoc_eval_grad_hess_dev(h, theta_dev_ptr: int, out_dev_ptr: int):
+    """Device pointers (e.g. torch tensor .data_ptr()); enqueues and returns."""
+    _check(lib().qoc_eval_grad_hess_dev(C.c_void_p(h), C.c_void_p(int(theta_dev_ptr)),
+                                        C.c_void_p(int(out_dev_ptr))), "qoc_eval_grad_hess_dev")
+
+
+def qoc_sync_status(h):
+    _check(lib().qoc_sync_status(C.c_void_p(h)), "qoc_sync_status")
+
+
+def qoc_trust_region_solve(h, theta0, gtol=1e-10, xtol=1e-10, radius0=1.0, radius_max=1e3,
+                           eta=0.1, max_iter=10000):
+    th = _f64(theta0)
+    out = np.zeros_like(th)
+    opt = TrOptions(gtol, xtol, radius0, radius_max, eta, int(max_iter))
+    rep = TrReport()
+    s = lib().qoc_trust_region_solve(C.c_void_p(h), _ptr(th), C.byref(opt), _ptr(out), C.byref(rep))
+    if s not in (QOC_OK, QOC_ENOTCONV):
+        raise QocError(s, "qoc_trust_region_solve")
+    info = {k: getattr(rep, k) for k, _ in TrReport._fields_}
+    info["stop"] = {0: "gtol", 1: "xtol", 2: "max_iter", 3: "no_decrease"}[rep.stop_reason]
+    info["status"] = s
+    return out, info
+
+
+def qoc_get_diagnostics(h):
+    out = np.zeros(8)
+    _check(lib().qoc_get_diagnostics(C.c_void_p(h), _ptr(out)), "qoc_get_diagnostics")
+    return {"norm_drift": out[0], "hess_asym": out[1],
+            "phase_ms": dict(zip(["eig", "prep", "chains", "pointwise", "panels", "assembly"], out[2:]))}
+
+
+def qoc_read_buffer(h, which, shape, complex_=False):
+    n = int(np.prod(shape)) * (2 if complex_ else 1)
+    out = np.zeros(n)
+    _check(lib().qoc_read_buffer(C.c_void_p(h), int(which), _ptr(out), n), "qoc_read_buffer")
+    if complex_:
+        return out.view(np.complex128).reshape(shape)
+    return out.reshape(shape)
+
+
+def qoc_device_bytes(h) -> int:
+    return int(lib().qoc_device_bytes(C.c_void_p(h)))
+
+
+def qoc_max_basis_size() -> int:
+    return int(lib().qoc_max_basis_size())
+
+
+def qoc_version() -> int:
+    return int(lib().qoc_version())
+
+
+# ---------------------------------------------------------------------------
+# convenience wrapper
+# ---------------------------------------------------------------------------
+
+class Problem:
+    """Owns one qoc_problem built from a problem description with fields
+    H0, M, alpha, beta, B, dt, w_f, w_t (e.g. ``inputs.Problem``)."""
+
+    def __init__(self, prob, precision=QOC_FP64, cuda_stream=None, hess_method=None, eig_method=None):
+        self.N, self.K, self.J = prob.H0.shape[0], prob.B.shape[1], prob.B.shape[0]
+        self.handle = qoc_create_problem(self.N, prob.H0, prob.M, prob.alpha, prob.beta, self.K,
+                                         prob.B, prob.dt, self.J, prob.w_f, prob.w_t, precision,
+                                         cuda_stream)
+        if hess_method is not None:
+            qoc_set_hess_method(self.handle, hess_method)
+        if eig_method is not None:
+            qoc_set_eig_method(self.handle, eig_method)
+
+    def eval_J(self, theta):
+        return qoc_eval_J(self.handle, theta)
+
+    def eval_grad(self, theta):
+        return qoc_eval_grad(self.handle, theta)
+
+    def eval_grad_hess(self, theta):
+        return qoc_eval_grad_hess(self.handle, theta)
+
+    def trust_region_solve(self, theta0, **kw):
+        return qoc_trust_region_solve(self.handle, theta0, **kw)
+
+    def buffer(self, which):
+        N, K, J = self.N, self.K, self.J
+        spec = {
+            QOC_BUF_F: ((J,), False), QOC_BUF_EIGVAL: ((J, N), False), QOC_BUF_EIGVEC: ((J, N, N), False),
+            QOC_BUF_STATE: ((J + 1, N), True), QOC_BUF_COSTATE: ((J + 1, N), True),
+            QOC_BUF_G: ((J,), False), QOC_BUF_C: ((J,), False), QOC_BUF_V: ((J, K), False),
+            QOC_BUF_U: ((J, K), False), QOC_BUF_SJ: ((N, K), True), QOC_BUF_HESS_RAW: ((K, K), False),
+        }[which]
+        return qoc_read_buffer(self.handle, which, *spec)
+
+    def diagnostics(self):
+        return qoc_get_diagnostics(self.handle)
+
+    def close(self):
+        if self.handle:
+            qoc_destroy_problem(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

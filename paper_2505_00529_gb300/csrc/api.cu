@@ -1,0 +1,584 @@
+// C ABI of the library (see include/qoc.h): problem objects, device memory,
+// the evaluation pipeline of Alg. 2 and the trust-region driver.
+//
+// One evaluation at theta enqueues, on the problem's stream:
+//   control       f = B theta
+//   eig           H_j = W_j diag(lambda_j) W_j^T for all j          (parallel over j)
+//   prep          D_j, P~_j = Gamma1 o M~_j, X'_j                    (parallel over j)
+//   state chain   a_0 .. a_J                                         (sequential)
+//   terminal      J, lambda_J = 2 w_t (a_J - beta)
+//   costate chain lambda_J .. lambda_0                               (sequential)
+//   pointwise     p_j, y_j, g_j, c_j                                 (parallel over j)
+//   tangent panel S_0 .. S_J with u_j = Re(y_j^H S_j)                (sequential, K-parallel)
+//   mu panel      mu_J .. mu_0 with v_j = Re(mu_{j+1}^H p_j)         (sequential, K-parallel)
+//   assembly      grad, Hess
+// The host synchronises only when results go back to host memory.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "kernels.hpp"
+#include "qoc.h"
+
+using namespace qoc;
+
+namespace {
+constexpr int kMaxN = 64;       // largest basis the shared-memory kernels take in this build
+constexpr int kMaxK = 4096;
+constexpr int kMaxKTR = 64;     // trust region: Hessian eigensolver in shared memory
+}  // namespace
+
+struct qoc_problem {
+  int N = 0, K = 0, J = 0, Kp = 0;
+  double dt = 0, w_f = 0, w_t = 0, mshift = 0;
+  int precision = 0, hess_method = QOC_HESS_SECOND_ORDER_ADJOINT, eig_method = QOC_EIG_REFINED;
+  int refine_sweeps = 2;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  int timing = 0;
+  cudaEvent_t ev[8] = {};
+  double phase_ms[6] = {0, 0, 0, 0, 0, 0};
+  double diag[2] = {0, 0};
+  int last_order = -1;
+  size_t dstride = 0, vstride = 0, dev_bytes = 0;
+  std::vector<void*> allocs;
+  // device buffers
+  double *H0 = nullptr, *M = nullptr, *B = nullptr, *theta = nullptr, *theta_trial = nullptr;
+  float* Bf = nullptr;
+  double *f = nullptr, *W = nullptr, *eig = nullptr, *g = nullptr, *c = nullptr;
+  double *V = nullptr, *U = nullptr, *work = nullptr, *out = nullptr, *out_trial = nullptr;
+  double *hess_raw = nullptr, *scal = nullptr;
+  double2 *alpha = nullptr, *beta = nullptr, *Ptil = nullptr, *Xp = nullptr, *SJ = nullptr,
+          *lamJ = nullptr;
+  void *D = nullptr, *a_hat = nullptr, *l_hat = nullptr, *p_hat = nullptr, *y_hat = nullptr;
+  int* status = nullptr;
+  double *trwork = nullptr, *trstep = nullptr, *trinfo = nullptr, *trzero = nullptr;
+  // pinned host staging
+  double* hbuf = nullptr;
+  size_t hbuf_len = 0;
+  int* hstatus = nullptr;
+};
+
+namespace {
+
+qoc_status from_cuda(cudaError_t e) {
+  if (e == cudaSuccess) return QOC_OK;
+  if (e == cudaErrorMemoryAllocation) return QOC_ENOMEM;
+  if (e == cudaErrorInvalidConfiguration) return QOC_EUNSUPPORTED;
+  return QOC_ECUDA;
+}
+
+#define QOC_TRY(expr)                         \
+  do {                                        \
+    cudaError_t e_ = (expr);                  \
+    if (e_ != cudaSuccess) return from_cuda(e_); \
+  } while (0)
+
+template <typename T>
+cudaError_t dalloc(qoc_problem* p, T** ptr, size_t bytes) {
+  void* v = nullptr;
+  bytes = (bytes + 255) & ~size_t(255);
+  cudaError_t e = cudaMalloc(&v, bytes);
+  if (e != cudaSuccess) return e;
+  p->allocs.push_back(v);
+  p->dev_bytes += bytes;
+  *ptr = reinterpret_cast<T*>(v);
+  return cudaSuccess;
+}
+
+bool finite_all(const double* x, size_t n) {
+  for (size_t i = 0; i < n; ++i)
+    if (!std::isfinite(x[i])) return false;
+  return true;
+}
+
+bool symmetric(const double* A, int N) {
+  double nrm = 0;
+  for (int i = 0; i < N * N; ++i) nrm = std::fmax(nrm, std::fabs(A[i]));
+  for (int i = 0; i < N; ++i)
+    for (int k = i + 1; k < N; ++k)
+      if (std::fabs(A[i * N + k] - A[k * N + i]) > 1e-12 * std::fmax(nrm, 1e-300)) return false;
+  return true;
+}
+
+double2 cexpi_h(double x) { return make_double2(std::cos(x), std::sin(x)); }
+
+int sweep_kc(const qoc_problem* p) {
+  if (p->precision == QOC_FP64) return 1;
+  if (p->N <= 32) return 4;
+  return 2;
+}
+
+qoc_status device_status(qoc_problem* p) {
+  int s = *p->hstatus;
+  *p->hstatus = 0;
+  if (s == 0) return QOC_OK;
+  if (s & DEV_TIMEOUT) return QOC_ETIMEOUT;
+  if (s & DEV_BADSHAPE) return QOC_EUNSUPPORTED;
+  return QOC_ENUMERIC;
+}
+
+// Enqueue one evaluation.  order 0: J; 1: J + grad; 2: J + grad + Hess.
+// theta_dev: K doubles on the device.  out_dev: 1 + K (+ K*K) doubles.
+qoc_status enqueue_eval(qoc_problem* p, const double* theta_dev, int order, double* out_dev) {
+  cudaStream_t st = p->stream;
+  const int N = p->N, K = p->K, J = p->J;
+  const int mixed = p->precision == QOC_MIXED_FP32 ? 1 : 0;
+  const int d_fp64 = mixed ? 0 : 1;
+  if (p->timing) cudaEventRecord(p->ev[0], st);
+  QOC_TRY(launch_control(p->B, p->Kp, theta_dev, J, K, p->f, st));
+  QOC_TRY(launch_eig(p->H0, p->M, p->f, N, J, p->W, p->eig, p->status,
+                     p->eig_method == QOC_EIG_JACOBI_FP64 ? EIG_JACOBI_FP64 : EIG_REFINED,
+                     p->refine_sweeps, st));
+  if (p->timing) cudaEventRecord(p->ev[1], st);
+  QOC_TRY(launch_prep(p->W, p->eig, p->M, N, J, p->dt, p->mshift, p->D, p->dstride, d_fp64,
+                      order >= 1, p->Ptil, p->Xp, p->status, st));
+  if (p->timing) cudaEventRecord(p->ev[2], st);
+
+  SweepArgs a{};
+  a.N = N; a.K = 1; a.Kp = p->Kp; a.J = J; a.kc = 1; a.backward = 0;
+  a.D = reinterpret_cast<const unsigned char*>(p->D); a.dstride = p->dstride;
+  a.init = p->alpha; a.init_scale = 1.0; a.states = p->a_hat; a.status = p->status;
+  QOC_TRY(launch_sweep(a, d_fp64, st));
+  const double thetaJ = (double)J * p->dt * p->mshift;
+  QOC_TRY(launch_terminal(p->f, J, p->a_hat, mixed, p->beta, N, cexpi_h(thetaJ), p->w_f, p->w_t,
+                          p->lamJ, p->scal + 0, p->scal + 1, st));
+  QOC_TRY(cudaMemcpyAsync(out_dev, p->scal, sizeof(double), cudaMemcpyDeviceToDevice, st));
+  if (order == 0) {
+    if (p->timing) for (int k = 3; k < 7; ++k) cudaEventRecord(p->ev[k], st);
+    return QOC_OK;
+  }
+  SweepArgs l = a;
+  l.backward = 1; l.init = p->lamJ; l.states = p->l_hat;
+  QOC_TRY(launch_sweep(l, d_fp64, st));
+  if (p->timing) cudaEventRecord(p->ev[3], st);
+  const double2 kappa = cexpi_h(p->dt * p->mshift);
+  QOC_TRY(launch_pointwise(p->W, p->Ptil, p->Xp, p->a_hat, p->l_hat, mixed, N, J, kappa, p->p_hat,
+                           p->y_hat, p->g, p->c, order >= 2, st));
+  if (p->timing) cudaEventRecord(p->ev[4], st);
+  if (order >= 2) {
+    SweepArgs s{};
+    s.N = N; s.K = K; s.Kp = p->Kp; s.J = J; s.kc = sweep_kc(p); s.backward = 0;
+    s.D = reinterpret_cast<const unsigned char*>(p->D); s.dstride = p->dstride;
+    s.src = p->p_hat; s.ctr = p->y_hat;
+    s.Brow = mixed ? static_cast<const void*>(p->Bf) : static_cast<const void*>(p->B);
+    s.init = nullptr; s.final_out = p->SJ; s.contr = p->U; s.status = p->status;
+    QOC_TRY(launch_sweep(s, d_fp64, st));
+    if (p->hess_method == QOC_HESS_SECOND_ORDER_ADJOINT) {
+      SweepArgs m = s;
+      m.backward = 1; m.src = p->y_hat; m.ctr = p->p_hat;
+      m.init = p->SJ; m.init_scale = 2.0 * p->w_t; m.final_out = nullptr; m.contr = p->V;
+      QOC_TRY(launch_sweep(m, d_fp64, st));
+    }
+  }
+  if (p->timing) cudaEventRecord(p->ev[5], st);
+  QOC_TRY(launch_assemble(p->B, p->Kp, p->f, p->g, p->c, p->V, p->U, p->SJ, N, J, K, p->w_f,
+                          p->w_t, p->hess_method == QOC_HESS_SECOND_ORDER_ADJOINT ? 0 : 1,
+                          order >= 2, p->work, out_dev, p->hess_raw, p->scal + 2, st));
+  if (p->timing) cudaEventRecord(p->ev[6], st);
+  return QOC_OK;
+}
+
+void collect_timing(qoc_problem* p) {
+  if (!p->timing) return;
+  for (int k = 0; k < 6; ++k) {
+    float ms = 0;
+    if (cudaEventElapsedTime(&ms, p->ev[k], p->ev[k + 1]) == cudaSuccess) p->phase_ms[k] = ms;
+  }
+}
+
+// host-pointer evaluation: theta in, [J, grad, Hess] out
+qoc_status eval_host(qoc_problem* p, const double* theta, int order, double* J, double* grad,
+                     double* hess) {
+  if (!p || !theta || !J) return QOC_EINVAL;
+  if ((order >= 1 && !grad) || (order >= 2 && !hess)) return QOC_EINVAL;
+  if (!finite_all(theta, p->K)) return QOC_EINVAL;
+  const int K = p->K;
+  const size_t nout = 1 + (order >= 1 ? K : 0) + (order >= 2 ? (size_t)K * K : 0);
+  std::memcpy(p->hbuf, theta, sizeof(double) * K);
+  QOC_TRY(cudaMemcpyAsync(p->theta, p->hbuf, sizeof(double) * K, cudaMemcpyHostToDevice, p->stream));
+  qoc_status s = enqueue_eval(p, p->theta, order, p->out);
+  if (s != QOC_OK) return s;
+  QOC_TRY(cudaMemcpyAsync(p->hbuf + K, p->out, sizeof(double) * nout, cudaMemcpyDeviceToHost,
+                          p->stream));
+  QOC_TRY(cudaMemcpyAsync(p->hbuf + K + nout, p->scal, 3 * sizeof(double), cudaMemcpyDeviceToHost,
+                          p->stream));
+  QOC_TRY(cudaMemcpyAsync(p->hstatus, p->status, sizeof(int), cudaMemcpyDeviceToHost, p->stream));
+  QOC_TRY(cudaMemsetAsync(p->status, 0, sizeof(int), p->stream));
+  QOC_TRY(cudaStreamSynchronize(p->stream));
+  collect_timing(p);
+  p->last_order = order;
+  p->diag[0] = p->hbuf[K + nout + 1];
+  p->diag[1] = order >= 2 ? p->hbuf[K + nout + 2] : 0.0;
+  s = device_status(p);
+  const double* o = p->hbuf + K;
+  *J = o[0];
+  if (order >= 1) std::memcpy(grad, o + 1, sizeof(double) * K);
+  if (order >= 2) std::memcpy(hess, o + 1 + K, sizeof(double) * K * K);
+  if (s != QOC_OK) return s;
+  if (!finite_all(o, nout)) return QOC_ENUMERIC;
+  return QOC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int qoc_version(void) { return 100; }
+int qoc_max_basis_size(void) { return kMaxN; }
+
+const char* qoc_status_string(qoc_status s) {
+  switch (s) {
+    case QOC_OK: return "ok";
+    case QOC_EINVAL: return "invalid argument";
+    case QOC_ENOMEM: return "out of memory";
+    case QOC_ECUDA: return "CUDA error";
+    case QOC_ENUMERIC: return "numerical failure (non-finite value or eigensolver not converged)";
+    case QOC_ENOTCONV: return "trust region did not converge within max_iter";
+    case QOC_ETIMEOUT: return "bounded device wait timed out";
+    case QOC_EUNSUPPORTED: return "unsupported size or option in this build";
+  }
+  return "unknown status";
+}
+
+void qoc_destroy_problem(qoc_problem* p) {
+  if (!p) return;
+  if (p->stream) cudaStreamSynchronize(p->stream);
+  for (void* v : p->allocs) cudaFree(v);
+  if (p->hbuf) cudaFreeHost(p->hbuf);
+  if (p->hstatus) cudaFreeHost(p->hstatus);
+  for (auto& e : p->ev)
+    if (e) cudaEventDestroy(e);
+  if (p->own_stream && p->stream) cudaStreamDestroy(p->stream);
+  delete p;
+}
+
+qoc_status qoc_create_problem(int N, const double* H0, const double* M, const double* a0,
+                              const double* a_target, int K, const double* basis, double dt,
+                              int steps, double w_ctrl, double w_term, int precision,
+                              void* cuda_stream, qoc_problem** out) {
+  if (!out) return QOC_EINVAL;
+  *out = nullptr;
+  if (!H0 || !M || !a0 || !a_target || !basis) return QOC_EINVAL;
+  if (N < 1 || K < 1 || steps < 1) return QOC_EINVAL;
+  if (N > kMaxN || K > kMaxK) return QOC_EUNSUPPORTED;
+  if (!(dt > 0) || !std::isfinite(dt) || !(w_ctrl >= 0) || !(w_term >= 0) ||
+      !std::isfinite(w_ctrl) || !std::isfinite(w_term))
+    return QOC_EINVAL;
+  if (precision != QOC_FP64 && precision != QOC_MIXED_FP32) return QOC_EINVAL;
+  const size_t NN = (size_t)N * N;
+  if (!finite_all(H0, NN) || !finite_all(M, NN) || !finite_all(a0, 2 * (size_t)N) ||
+      !finite_all(a_target, 2 * (size_t)N) || !finite_all(basis, (size_t)steps * K))
+    return QOC_EINVAL;
+  if (!symmetric(H0, N) || !symmetric(M, N)) return QOC_EINVAL;
+
+  qoc_problem* p = new (std::nothrow) qoc_problem();
+  if (!p) return QOC_ENOMEM;
+  p->N = N; p->K = K; p->J = steps; p->Kp = (K + 3) / 4 * 4;
+  p->dt = dt; p->w_f = w_ctrl; p->w_t = w_term; p->precision = precision;
+  p->refine_sweeps = precision == QOC_FP64 ? 2 : 1;
+  double tr = 0;
+  for (int i = 0; i < N; ++i) tr += H0[i * N + i];
+  p->mshift = tr / N;
+  const int J = steps;
+  const int mixed = precision == QOC_MIXED_FP32;
+  p->dstride = ((mixed ? 8 : 16) * NN + 15) / 16 * 16;
+  p->vstride = ((mixed ? 8 : 16) * (size_t)N + 15) / 16 * 16;
+
+  cudaError_t e = cudaSuccess;
+  auto fail = [&](cudaError_t err) {
+    qoc_destroy_problem(p);
+    return from_cuda(err);
+  };
+  if (cuda_stream) {
+    p->stream = static_cast<cudaStream_t>(cuda_stream);
+  } else {
+    if ((e = cudaStreamCreateWithFlags(&p->stream, cudaStreamNonBlocking)) != cudaSuccess) return fail(e);
+    p->own_stream = true;
+  }
+  for (auto& ev : p->ev)
+    if ((e = cudaEventCreate(&ev)) != cudaSuccess) return fail(e);
+#define ALLOC(ptr, bytes) \
+  if ((e = dalloc(p, &(ptr), (bytes))) != cudaSuccess) return fail(e)
+  ALLOC(p->H0, 8 * NN);
+  ALLOC(p->M, 8 * NN);
+  ALLOC(p->B, 8 * (size_t)J * p->Kp);
+  ALLOC(p->Bf, 4 * (size_t)J * p->Kp);
+  ALLOC(p->theta, 8 * (size_t)K);
+  ALLOC(p->theta_trial, 8 * (size_t)K);
+  ALLOC(p->f, 8 * (size_t)J);
+  ALLOC(p->W, 8 * (size_t)J * NN);
+  ALLOC(p->eig, 8 * (size_t)J * N);
+  ALLOC(p->g, 8 * (size_t)J);
+  ALLOC(p->c, 8 * (size_t)J);
+  ALLOC(p->V, 8 * (size_t)J * K);
+  ALLOC(p->U, 8 * (size_t)J * K);
+  ALLOC(p->work, 8 * assemble_work_doubles(J, K));
+  ALLOC(p->out, 8 * (1 + (size_t)K + (size_t)K * K));
+  ALLOC(p->out_trial, 8 * (1 + (size_t)K + (size_t)K * K));
+  ALLOC(p->hess_raw, 8 * (size_t)K * K);
+  ALLOC(p->scal, 8 * 8);
+  ALLOC(p->alpha, 16 * (size_t)N);
+  ALLOC(p->beta, 16 * (size_t)N);
+  ALLOC(p->lamJ, 16 * (size_t)N);
+  ALLOC(p->Ptil, 16 * (size_t)J * NN);
+  ALLOC(p->Xp, 16 * (size_t)J * NN);
+  ALLOC(p->SJ, 16 * (size_t)K * N);
+  ALLOC(p->D, (size_t)J * p->dstride);
+  ALLOC(p->a_hat, 16 * (size_t)(J + 1) * N);
+  ALLOC(p->l_hat, 16 * (size_t)(J + 1) * N);
+  ALLOC(p->p_hat, (size_t)J * p->vstride);
+  ALLOC(p->y_hat, (size_t)J * p->vstride);
+  ALLOC(p->status, sizeof(int));
+  if (K <= kMaxKTR) {
+    ALLOC(p->trwork, 8 * tr_work_doubles(K));
+    ALLOC(p->trstep, 8 * (size_t)K);
+    ALLOC(p->trinfo, 8 * 8);
+    ALLOC(p->trzero, 8 * ((size_t)K * K + 1));
+  }
+#undef ALLOC
+  p->hbuf_len = 2 * (1 + (size_t)K + (size_t)K * K) + 2 * (size_t)K + 64;
+  if ((e = cudaMallocHost(&p->hbuf, 8 * p->hbuf_len)) != cudaSuccess) return fail(e);
+  if ((e = cudaMallocHost(&p->hstatus, sizeof(int))) != cudaSuccess) return fail(e);
+  *p->hstatus = 0;
+
+  // upload inputs (the basis is padded to Kp columns, plus a binary32 copy)
+  std::vector<double> Bp((size_t)J * p->Kp, 0.0);
+  std::vector<float> Bfp((size_t)J * p->Kp, 0.0f);
+  for (int j = 0; j < J; ++j)
+    for (int l = 0; l < K; ++l) {
+      Bp[(size_t)j * p->Kp + l] = basis[(size_t)j * K + l];
+      Bfp[(size_t)j * p->Kp + l] = (float)basis[(size_t)j * K + l];
+    }
+  if ((e = cudaMemcpy(p->H0, H0, 8 * NN, cudaMemcpyHostToDevice)) != cudaSuccess) return fail(e);
+  if ((e = cudaMemcpy(p->M, M, 8 * NN, cudaMemcpyHostToDevice)) != cudaSuccess) return fail(e);
+  if ((e = cudaMemcpy(p->B, Bp.data(), 8 * Bp.size(), cudaMemcpyHostToDevice)) != cudaSuccess) return fail(e);
+  if ((e = cudaMemcpy(p->Bf, Bfp.data(), 4 * Bfp.size(), cudaMemcpyHostToDevice)) != cudaSuccess) return fail(e);
+  if ((e = cudaMemcpy(p->alpha, a0, 16 * (size_t)N, cudaMemcpyHostToDevice)) != cudaSuccess) return fail(e);
+  if ((e = cudaMemcpy(p->beta, a_target, 16 * (size_t)N, cudaMemcpyHostToDevice)) != cudaSuccess) return fail(e);
+  if ((e = cudaMemset(p->status, 0, sizeof(int))) != cudaSuccess) return fail(e);
+  if ((e = cudaMemset(p->V, 0, 8 * (size_t)J * K)) != cudaSuccess) return fail(e);
+  if (p->trzero && (e = cudaMemset(p->trzero, 0, 8 * ((size_t)K * K + 1))) != cudaSuccess) return fail(e);
+  *out = p;
+  return QOC_OK;
+}
+
+qoc_status qoc_set_hess_method(qoc_problem* p, int method) {
+  if (!p || (method != QOC_HESS_SECOND_ORDER_ADJOINT && method != QOC_HESS_TANGENT)) return QOC_EINVAL;
+  p->hess_method = method;
+  return QOC_OK;
+}
+
+qoc_status qoc_set_eig_method(qoc_problem* p, int method) {
+  if (!p || (method != QOC_EIG_REFINED && method != QOC_EIG_JACOBI_FP64)) return QOC_EINVAL;
+  p->eig_method = method;
+  return QOC_OK;
+}
+
+qoc_status qoc_enable_timing(qoc_problem* p, int on) {
+  if (!p) return QOC_EINVAL;
+  p->timing = on ? 1 : 0;
+  return QOC_OK;
+}
+
+qoc_status qoc_eval_J(qoc_problem* p, const double* theta, double* J) {
+  return eval_host(p, theta, 0, J, nullptr, nullptr);
+}
+
+qoc_status qoc_eval_grad(qoc_problem* p, const double* theta, double* J, double* grad) {
+  return eval_host(p, theta, 1, J, grad, nullptr);
+}
+
+qoc_status qoc_eval_grad_hess(qoc_problem* p, const double* theta, double* J, double* grad,
+                              double* hess) {
+  return eval_host(p, theta, 2, J, grad, hess);
+}
+
+qoc_status qoc_eval_grad_hess_dev(qoc_problem* p, const double* theta_dev, double* out_dev) {
+  if (!p || !theta_dev || !out_dev) return QOC_EINVAL;
+  p->last_order = 2;
+  return enqueue_eval(p, theta_dev, 2, out_dev);
+}
+
+qoc_status qoc_sync_status(qoc_problem* p) {
+  if (!p) return QOC_EINVAL;
+  QOC_TRY(cudaMemcpyAsync(p->hstatus, p->status, sizeof(int), cudaMemcpyDeviceToHost, p->stream));
+  QOC_TRY(cudaMemsetAsync(p->status, 0, sizeof(int), p->stream));
+  QOC_TRY(cudaStreamSynchronize(p->stream));
+  return device_status(p);
+}
+
+qoc_status qoc_get_diagnostics(const qoc_problem* p, double* out) {
+  if (!p || !out) return QOC_EINVAL;
+  out[0] = p->diag[0];
+  out[1] = p->diag[1];
+  for (int k = 0; k < 6; ++k) out[2 + k] = p->timing ? p->phase_ms[k] : 0.0;
+  return QOC_OK;
+}
+
+size_t qoc_device_bytes(const qoc_problem* p) { return p ? p->dev_bytes : 0; }
+
+qoc_status qoc_read_buffer(const qoc_problem* p, int which, double* host_out, size_t count) {
+  if (!p || !host_out || p->last_order < 0) return QOC_EINVAL;
+  const int N = p->N, K = p->K, J = p->J;
+  const bool mixed = p->precision == QOC_MIXED_FP32;
+  const double m = p->mshift, dt = p->dt;
+  auto need = [&](size_t n) { return count >= n; };
+  cudaError_t e = cudaStreamSynchronize(p->stream);
+  if (e != cudaSuccess) return from_cuda(e);
+  // states are stored in the frame rotating with the shift m: x_j = e^{-i j dt m} x^_j
+  auto unframe_rows = [&](const void* dev, int rows) -> qoc_status {
+    const size_t n = (size_t)rows * N;
+    std::vector<double> raw(4 * n);
+    cudaError_t err = cudaMemcpy(raw.data(), dev, 16 * n, cudaMemcpyDeviceToHost);
+    if (err != cudaSuccess) return from_cuda(err);
+    for (int j = 0; j < rows; ++j) {
+      const double2 ph = cexpi_h(-(double)j * dt * m);
+      for (int i = 0; i < N; ++i) {
+        double xr, xi;
+        const size_t k = (size_t)j * N + i;
+        if (mixed) {
+          const float* fr = reinterpret_cast<const float*>(raw.data());
+          xr = (double)fr[4 * k] + (double)fr[4 * k + 2];
+          xi = (double)fr[4 * k + 1] + (double)fr[4 * k + 3];
+        } else {
+          xr = raw[2 * k];
+          xi = raw[2 * k + 1];
+        }
+        host_out[2 * k] = ph.x * xr - ph.y * xi;
+        host_out[2 * k + 1] = ph.x * xi + ph.y * xr;
+      }
+    }
+    return QOC_OK;
+  };
+  switch (which) {
+    case QOC_BUF_F:
+      if (!need(J)) return QOC_EINVAL;
+      return from_cuda(cudaMemcpy(host_out, p->f, 8 * (size_t)J, cudaMemcpyDeviceToHost));
+    case QOC_BUF_EIGVAL:
+      if (!need((size_t)J * N)) return QOC_EINVAL;
+      return from_cuda(cudaMemcpy(host_out, p->eig, 8 * (size_t)J * N, cudaMemcpyDeviceToHost));
+    case QOC_BUF_EIGVEC:
+      if (!need((size_t)J * N * N)) return QOC_EINVAL;
+      return from_cuda(cudaMemcpy(host_out, p->W, 8 * (size_t)J * N * N, cudaMemcpyDeviceToHost));
+    case QOC_BUF_STATE:
+      if (!need(2 * (size_t)(J + 1) * N)) return QOC_EINVAL;
+      return unframe_rows(p->a_hat, J + 1);
+    case QOC_BUF_COSTATE:
+      if (p->last_order < 1 || !need(2 * (size_t)(J + 1) * N)) return QOC_EINVAL;
+      return unframe_rows(p->l_hat, J + 1);
+    case QOC_BUF_G:
+      if (p->last_order < 1 || !need(J)) return QOC_EINVAL;
+      return from_cuda(cudaMemcpy(host_out, p->g, 8 * (size_t)J, cudaMemcpyDeviceToHost));
+    case QOC_BUF_C:
+      if (p->last_order < 2 || !need(J)) return QOC_EINVAL;
+      return from_cuda(cudaMemcpy(host_out, p->c, 8 * (size_t)J, cudaMemcpyDeviceToHost));
+    case QOC_BUF_V:
+      if (p->last_order < 2 || !need((size_t)J * K)) return QOC_EINVAL;
+      return from_cuda(cudaMemcpy(host_out, p->V, 8 * (size_t)J * K, cudaMemcpyDeviceToHost));
+    case QOC_BUF_U:
+      if (p->last_order < 2 || !need((size_t)J * K)) return QOC_EINVAL;
+      return from_cuda(cudaMemcpy(host_out, p->U, 8 * (size_t)J * K, cudaMemcpyDeviceToHost));
+    case QOC_BUF_SJ: {
+      if (p->last_order < 2 || !need(2 * (size_t)N * K)) return QOC_EINVAL;
+      std::vector<double> raw(2 * (size_t)N * K);
+      e = cudaMemcpy(raw.data(), p->SJ, 16 * (size_t)N * K, cudaMemcpyDeviceToHost);
+      if (e != cudaSuccess) return from_cuda(e);
+      const double2 ph = cexpi_h(-(double)J * dt * m);
+      for (int l = 0; l < K; ++l)
+        for (int i = 0; i < N; ++i) {
+          double xr = raw[2 * ((size_t)l * N + i)], xi = raw[2 * ((size_t)l * N + i) + 1];
+          host_out[2 * ((size_t)i * K + l)] = ph.x * xr - ph.y * xi;
+          host_out[2 * ((size_t)i * K + l) + 1] = ph.x * xi + ph.y * xr;
+        }
+      return QOC_OK;
+    }
+    case QOC_BUF_HESS_RAW:
+      if (p->last_order < 2 || !need((size_t)K * K)) return QOC_EINVAL;
+      return from_cuda(cudaMemcpy(host_out, p->hess_raw, 8 * (size_t)K * K, cudaMemcpyDeviceToHost));
+    default:
+      return QOC_EINVAL;
+  }
+}
+
+qoc_status qoc_trust_region_solve(qoc_problem* p, const double* theta0, const qoc_tr_options* opt,
+                                  double* theta_out, qoc_tr_report* report) {
+  if (!p || !theta0 || !opt || !theta_out || !report) return QOC_EINVAL;
+  if (!p->trwork) return QOC_EUNSUPPORTED;
+  if (!(opt->radius0 > 0) || !(opt->radius_max >= opt->radius0) || opt->max_iter < 1 ||
+      !(opt->eta >= 0 && opt->eta < 0.25) || !(opt->gtol >= 0) || !(opt->xtol >= 0))
+    return QOC_EINVAL;
+  if (!finite_all(theta0, p->K)) return QOC_EINVAL;
+  const int K = p->K;
+  cudaStream_t st = p->stream;
+  std::memset(report, 0, sizeof(*report));
+  double radius = opt->radius0;
+  std::memcpy(p->hbuf, theta0, 8 * (size_t)K);
+  QOC_TRY(cudaMemcpyAsync(p->theta, p->hbuf, 8 * (size_t)K, cudaMemcpyHostToDevice, st));
+  double* hs = p->hbuf + K;   // [J, |g|] and [pred, |s|, sigma, |g|, J_trial]
+  // evaluate grad/Hess at theta and factor the Hessian
+  auto eval_gh = [&]() -> qoc_status {
+    qoc_status s = enqueue_eval(p, p->theta, 2, p->out);
+    if (s != QOC_OK) return s;
+    QOC_TRY(launch_eig(p->out + 1 + K, p->trzero, p->trzero, K, 1, p->trwork + 3 * K,
+                       p->trwork + 2 * K, p->status, EIG_JACOBI_FP64, 0, st));
+    return QOC_OK;
+  };
+  qoc_status s = eval_gh();
+  if (s != QOC_OK) return s;
+  report->n_eval_gh = 1;
+  double Jc = 0;
+  int it = 0;
+  int stop = 2;
+  for (it = 1; it <= opt->max_iter; ++it) {
+    QOC_TRY(launch_tr_subproblem(p->out, K, radius, p->trwork, p->trstep, p->trinfo, p->status, st));
+    QOC_TRY(launch_axpy(p->theta, p->trstep, K, p->theta_trial, st));
+    s = enqueue_eval(p, p->theta_trial, 0, p->out_trial);
+    if (s != QOC_OK) return s;
+    QOC_TRY(cudaMemcpyAsync(hs, p->trinfo, 4 * sizeof(double), cudaMemcpyDeviceToHost, st));
+    QOC_TRY(cudaMemcpyAsync(hs + 4, p->out_trial, sizeof(double), cudaMemcpyDeviceToHost, st));
+    QOC_TRY(cudaMemcpyAsync(hs + 5, p->out, sizeof(double), cudaMemcpyDeviceToHost, st));
+    QOC_TRY(cudaMemcpyAsync(p->hstatus, p->status, sizeof(int), cudaMemcpyDeviceToHost, st));
+    QOC_TRY(cudaStreamSynchronize(st));
+    s = device_status(p);
+    if (s != QOC_OK) return s;
+    const double pred = hs[0], snorm = hs[1], gnorm = hs[3], Jt = hs[4];
+    Jc = hs[5];
+    report->n_eval_J++;
+    report->grad_norm = gnorm;
+    if (gnorm < opt->gtol) { stop = 0; --it; report->n_eval_J--; break; }
+    if (!(pred > 0) || !std::isfinite(pred)) { stop = 3; break; }
+    const double rho = (Jc - Jt) / pred;
+    if (rho < 0.25) radius *= 0.25;
+    else if (rho > 0.75 && std::fabs(snorm - radius) <= 1e-8 * radius)
+      radius = std::fmin(2.0 * radius, opt->radius_max);
+    if (rho > opt->eta) {
+      QOC_TRY(cudaMemcpyAsync(p->theta, p->theta_trial, 8 * (size_t)K, cudaMemcpyDeviceToDevice, st));
+      s = eval_gh();
+      if (s != QOC_OK) return s;
+      report->n_eval_gh++;
+    }
+    if (radius < opt->xtol) { stop = 1; break; }
+  }
+  if (it > opt->max_iter) it = opt->max_iter;
+  // final state: theta, J, |grad|
+  QOC_TRY(cudaMemcpyAsync(p->hbuf, p->theta, 8 * (size_t)K, cudaMemcpyDeviceToHost, st));
+  QOC_TRY(cudaMemcpyAsync(hs, p->out, 8 * (1 + (size_t)K), cudaMemcpyDeviceToHost, st));
+  QOC_TRY(cudaStreamSynchronize(st));
+  std::memcpy(theta_out, p->hbuf, 8 * (size_t)K);
+  double gn = 0;
+  for (int l = 0; l < K; ++l) gn += hs[1 + l] * hs[1 + l];
+  report->iters = it;
+  report->J = hs[0];
+  report->grad_norm = std::sqrt(gn);
+  report->radius = radius;
+  report->stop_reason = stop;
+  p->last_order = 2;
+  return stop == 2 ? QOC_ENOTCONV : QOC_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,214 @@
+// Control synthesis, terminal conditions and the final contraction into
+// J, grad J and the K x K Hessian (all binary64).
+//
+//   f = B theta                                   (Sec. II, linear model)
+//   J = w_f sum f_j^2 + w_t |a_J - beta|^2          (Eq. discretecost, weighted)
+//   lambda_J = 2 w_t (a_J - beta)                  (Eq. lambdafc with the weight)
+//   grad = B^T (2 w_f f + g)                       (Eq. dLdf)
+//   Hess = B^T diag(2 w_f + c) B + B^T V + B^T U   (Eq. d2Ldf2, second-order adjoint)
+//   Hess = B^T diag(2 w_f + c) B + 2 w_t Re(S_J^H S_J) + B^T U + U^T B   (tangent form)
+// The reported Hessian is (H + H^T)/2; |H - H^T|_F / |H|_F is kept.
+#include "common.cuh"
+#include "kernels.hpp"
+
+namespace qoc {
+
+// one warp per step: f_j = sum_l B[j][l] theta_l
+__global__ void k_control(const double* __restrict__ B, int Kp, const double* __restrict__ theta,
+                          int J, int K, double* __restrict__ f) {
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (warp >= J) return;
+  double acc = 0;
+  for (int l = lane; l < K; l += 32) acc = fma(B[(size_t)warp * Kp + l], theta[l], acc);
+  acc = warp_sum(acc);
+  if (lane == 0) f[warp] = acc;
+}
+
+cudaError_t launch_control(const double* B, int Kp, const double* theta, int J, int K, double* f,
+                           cudaStream_t st) {
+  const int threads = 256;
+  const int blocks = (J * 32 + threads - 1) / threads;
+  k_control<<<blocks, threads, 0, st>>>(B, Kp, theta, J, K, f);
+  return cudaGetLastError();
+}
+
+__device__ __forceinline__ double2 load_state2(const void* base, int mixed, size_t idx) {
+  if (mixed) {
+    float4 v = reinterpret_cast<const float4*>(base)[idx];
+    return make_double2((double)v.x + (double)v.z, (double)v.y + (double)v.w);
+  }
+  return reinterpret_cast<const double2*>(base)[idx];
+}
+
+// One CTA: cost, lambda^_J, max_j | |a_j| - 1 |.
+__global__ void k_terminal(const double* __restrict__ f, int J, const void* a_hat, int mixed,
+                           const double2* __restrict__ beta, int N, double2 phaseJ, double w_f,
+                           double w_t, double2* __restrict__ lamJ, double* cost_out,
+                           double* drift_out) {
+  __shared__ double red[3][32];
+  const int tid = threadIdx.x, nt = blockDim.x;
+  double fs = 0, rs = 0, drift = 0;
+  for (int j = tid; j < J; j += nt) fs = fma(f[j], f[j], fs);
+  for (int p = tid; p < N; p += nt) {
+    double2 aj = load_state2(a_hat, mixed, (size_t)J * N + p);
+    double2 d = csub(aj, cmul(phaseJ, beta[p]));
+    rs += d.x * d.x + d.y * d.y;
+    if (lamJ) lamJ[p] = cscale(d, 2.0 * w_t);
+  }
+  for (int j = tid; j <= J; j += nt) {
+    double n2 = 0;
+    for (int p = 0; p < N; ++p) {
+      double2 v = load_state2(a_hat, mixed, (size_t)j * N + p);
+      n2 += v.x * v.x + v.y * v.y;
+    }
+    drift = fmax(drift, fabs(sqrt(n2) - 1.0));
+  }
+  fs = warp_sum(fs);
+  rs = warp_sum(rs);
+  for (int o = 16; o > 0; o >>= 1) drift = fmax(drift, __shfl_xor_sync(0xffffffffu, drift, o));
+  if ((tid & 31) == 0) { red[0][tid >> 5] = fs; red[1][tid >> 5] = rs; red[2][tid >> 5] = drift; }
+  __syncthreads();
+  if (tid == 0) {
+    double a = 0, b = 0, d = 0;
+    for (int w = 0; w < (nt + 31) / 32; ++w) { a += red[0][w]; b += red[1][w]; d = fmax(d, red[2][w]); }
+    *cost_out = w_f * a + w_t * b;
+    if (drift_out) *drift_out = d;
+  }
+}
+
+cudaError_t launch_terminal(const double* f, int J, const void* a_hat, int mixed,
+                            const double2* beta, int N, double2 phaseJ, double w_f, double w_t,
+                            double2* lamJ, double* cost_out, double* drift_out, cudaStream_t st) {
+  k_terminal<<<1, 256, 0, st>>>(f, J, a_hat, mixed, beta, N, phaseJ, w_f, w_t, lamJ, cost_out,
+                                drift_out);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Hessian: partial sums over chunks of steps.  Tile of 16 x 16 (l, m) per
+// CTA, one output per thread; blockIdx.z = chunk of JC steps.
+//   acc1[l][m] = sum_j b_jl ( (2 w_f + c_j) b_jm + U_jm + (SOA ? V_jm : 0) )
+//   acc2[l][m] = sum_j U_jl b_jm                      (tangent form only)
+// The extra chunk z == nchunk adds 2 w_t Re(S_J^H S_J) (tangent form).
+// ---------------------------------------------------------------------------
+constexpr int HT = 16;
+constexpr int JC = 64;
+
+__global__ void k_hess_partial(const double* __restrict__ B, int Kp, const double* __restrict__ c,
+                               const double* __restrict__ V, const double* __restrict__ U,
+                               const double2* __restrict__ SJ, int N, int J, int K, double w_f,
+                               double w_t, int method, int nchunk, double* __restrict__ work) {
+  __shared__ double bl[JC][HT + 1], bm[JC][HT + 1], zm[JC][HT + 1], ul[JC][HT + 1];
+  const int l0 = blockIdx.x * HT, m0 = blockIdx.y * HT, z = blockIdx.z;
+  const int tl = threadIdx.x / HT, tm = threadIdx.x % HT;
+  const int l = l0 + tl, m = m0 + tm;
+  double acc1 = 0, acc2 = 0;
+  if (z < nchunk) {
+    const int j0 = z * JC, j1 = min(J, j0 + JC);
+    for (int e = threadIdx.x; e < JC * HT; e += blockDim.x) {
+      int jj = e / HT, t = e % HT;
+      int j = j0 + jj;
+      bool ok = j < j1;
+      int ll = l0 + t, mm = m0 + t;
+      double cj = ok ? 2.0 * w_f + c[j] : 0.0;
+      bl[jj][t] = (ok && ll < K) ? B[(size_t)j * Kp + ll] : 0.0;
+      double bmv = (ok && mm < K) ? B[(size_t)j * Kp + mm] : 0.0;
+      bm[jj][t] = bmv;
+      double zv = cj * bmv;
+      if (ok && mm < K) {
+        zv += U[(size_t)j * K + mm];
+        if (method == 0) zv += V[(size_t)j * K + mm];
+      }
+      zm[jj][t] = zv;
+      ul[jj][t] = (ok && ll < K && method == 1) ? U[(size_t)j * K + ll] : 0.0;
+    }
+    __syncthreads();
+    for (int jj = 0; jj < j1 - j0; ++jj) {
+      acc1 = fma(bl[jj][tl], zm[jj][tm], acc1);
+      if (method == 1) acc2 = fma(ul[jj][tl], bm[jj][tm], acc2);
+    }
+  } else if (method == 1 && l < K && m < K) {
+    double s = 0;
+    for (int i = 0; i < N; ++i) {
+      double2 a = SJ[(size_t)l * N + i], b = SJ[(size_t)m * N + i];
+      s = fma(a.x, b.x, fma(a.y, b.y, s));
+    }
+    acc1 = 2.0 * w_t * s;
+  }
+  if (l < K && m < K) work[((size_t)z * K + l) * K + m] = acc1 + acc2;
+}
+
+// grad_l = sum_j b_jl (2 w_f f_j + g_j): one CTA per l
+__global__ void k_grad(const double* __restrict__ B, int Kp, const double* __restrict__ f,
+                       const double* __restrict__ g, int J, int K, double w_f, double* out) {
+  __shared__ double red[32];
+  const int l = blockIdx.x;
+  double acc = 0;
+  for (int j = threadIdx.x; j < J; j += blockDim.x)
+    acc = fma(B[(size_t)j * Kp + l], 2.0 * w_f * f[j] + g[j], acc);
+  acc = warp_sum(acc);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = 0;
+    for (int w = 0; w < (blockDim.x + 31) / 32; ++w) s += red[w];
+    out[1 + l] = s;
+  }
+}
+
+// sum the chunks, symmetrise, asymmetry
+__global__ void k_hess_final(const double* __restrict__ work, int nz, int K, double* out,
+                             double* hess_raw, double* asym) {
+  __shared__ double red[2][32];
+  const int tid = threadIdx.x, nt = blockDim.x;
+  for (int e = tid; e < K * K; e += nt) {
+    double s = 0;
+    for (int z = 0; z < nz; ++z) s += work[(size_t)z * K * K + e];
+    hess_raw[e] = s;
+  }
+  __syncthreads();
+  double num = 0, den = 0;
+  for (int e = tid; e < K * K; e += nt) {
+    int l = e / K, m = e % K;
+    double a = hess_raw[e], b = hess_raw[(size_t)m * K + l];
+    out[1 + K + e] = 0.5 * (a + b);
+    num += (a - b) * (a - b);
+    den += a * a;
+  }
+  num = warp_sum(num);
+  den = warp_sum(den);
+  if ((tid & 31) == 0) { red[0][tid >> 5] = num; red[1][tid >> 5] = den; }
+  __syncthreads();
+  if (tid == 0) {
+    double a = 0, b = 0;
+    for (int w = 0; w < (nt + 31) / 32; ++w) { a += red[0][w]; b += red[1][w]; }
+    *asym = b > 0 ? sqrt(a / b) : 0.0;
+  }
+}
+
+size_t assemble_work_doubles(int J, int K) {
+  const int nchunk = (J + JC - 1) / JC;
+  return (size_t)(nchunk + 1) * K * K;
+}
+
+cudaError_t launch_assemble(const double* B, int Kp, const double* f, const double* g,
+                            const double* c, const double* V, const double* U, const double2* SJ,
+                            int N, int J, int K, double w_f, double w_t, int method, int want_hess,
+                            double* work, double* out, double* hess_raw, double* asym,
+                            cudaStream_t st) {
+  k_grad<<<K, 256, 0, st>>>(B, Kp, f, g, J, K, w_f, out);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess || !want_hess) return e;
+  const int nchunk = (J + JC - 1) / JC;
+  const int nz = nchunk + (method == 1 ? 1 : 0);
+  dim3 grid((K + HT - 1) / HT, (K + HT - 1) / HT, nz);
+  k_hess_partial<<<grid, HT * HT, 0, st>>>(B, Kp, c, V, U, SJ, N, J, K, w_f, w_t, method, nchunk,
+                                           work);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  k_hess_final<<<1, 1024, 0, st>>>(work, nz, K, out, hess_raw, asym);
+  return cudaGetLastError();
+}
+
+}  // namespace qoc

@@ -1,0 +1,86 @@
+// Internal launch interface between the C ABI (api.cu) and the kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+
+namespace qoc {
+
+// Device status bits, OR-ed into a word the host reads after each evaluation.
+enum : int {
+  DEV_OK = 0,
+  DEV_EIG_NOCONV = 1,   // Jacobi sweep cap reached
+  DEV_TIMEOUT = 2,      // a bounded wait gave up
+  DEV_NONFINITE = 4,    // a non-finite value was produced
+  DEV_BADSHAPE = 8      // a kernel was launched with a shape it does not support
+};
+
+enum { EIG_REFINED = 0, EIG_JACOBI_FP64 = 1 };
+enum { PREC_FP64 = 0, PREC_MIXED = 1 };
+
+// second divided difference: dt*|hi - lo| at or below which the series is used
+constexpr double TAU_DD2 = 1e-3;
+
+size_t eig_smem_bytes(int N, int method);
+cudaError_t launch_eig(const double* H0, const double* M, const double* f, int N, int J,
+                       double* W, double* eig, int* status, int method, int refine_sweeps,
+                       cudaStream_t st);
+
+size_t prep_smem_bytes(int N);
+// D_j = W diag(exp(-i dt (lambda - m)) - 1) W^T (binary64 when d_fp64, else
+// binary32) at byte stride dstride; with derivs also P~_j = Gamma1 o M~_j and
+// X'_j = 2 sum_r M~_pr M~_rq phi[l_p, l_r, l_q].
+cudaError_t launch_prep(const double* W, const double* eig, const double* M, int N, int J,
+                        double dt, double mshift, void* D, size_t dstride, int d_fp64,
+                        int derivs, double2* Ptil, double2* Xp, int* status, cudaStream_t st);
+
+struct SweepArgs {
+  int N, K, Kp, J;       // Kp: row stride of the basis copy (multiple of 4)
+  int kc;                // columns per CTA
+  int backward;          // 0: X <- X + D X + src b^T ; 1: X <- X + conj(D) X + src b^T, j descending
+  const unsigned char* D;
+  size_t dstride;        // bytes per step of D (multiple of 16)
+  // element types: binary64 sweeps use double2 vectors / double basis rows;
+  // mixed sweeps use float2 / float.
+  const void* src;       // J x N source vectors (null: none)
+  const void* ctr;       // J x N contraction vectors (null: none)
+  const void* Brow;      // J x Kp basis rows (null: b = 1 for the single column)
+  const double2* init;   // [K][N] initial state, or null for zero
+  double init_scale;
+  double2* final_out;    // [K][N] final state (may be null)
+  void* states;          // (J+1) x N states of column 0 (double2, or float4 hi/lo pairs), or null
+  double* contr;         // J x K contraction output (u or v), or null
+  int* status;
+};
+cudaError_t launch_sweep(const SweepArgs& a, int d_fp64, cudaStream_t st);
+
+// p^_j, y^_j, g_j, c_j for all steps from the stored states/costates
+// states / costates as written by the vector chains (double2, or float4 pairs
+// when mixed); p^, y^ written as double2 (binary64 sweeps) or float2 (mixed)
+cudaError_t launch_pointwise(const double* W, const double2* Ptil, const double2* Xp,
+                             const void* a_hat, const void* l_hat, int mixed, int N, int J,
+                             double2 kappa, void* p_hat, void* y_hat, double* g, double* c,
+                             int want_c, cudaStream_t st);
+
+cudaError_t launch_control(const double* B, int Kp, const double* theta, int J, int K, double* f,
+                           cudaStream_t st);
+// lambda^_J = 2 w_t (a^_J - e^{i theta_J} beta); J value; norm drift; returns into out
+cudaError_t launch_terminal(const double* f, int J, const void* a_hat, int mixed,
+                            const double2* beta, int N, double2 phaseJ, double w_f, double w_t,
+                            double2* lamJ, double* cost_out, double* drift_out, cudaStream_t st);
+// grad = B^T (2 w_f f + g); Hess (see qoc.h) into out = [J, grad, Hess], raw Hessian, asymmetry
+cudaError_t launch_assemble(const double* B, int Kp, const double* f, const double* g,
+                            const double* c, const double* V, const double* U, const double2* SJ,
+                            int N, int J, int K, double w_f, double w_t, int method, int want_hess,
+                            double* work, double* out, double* hess_raw, double* asym,
+                            cudaStream_t st);
+size_t assemble_work_doubles(int J, int K);
+
+// trust-region subproblem on the device (K x K, binary64); work holds
+// [gt (K) | st (K) | eigenvalues d (K) | eigenvectors Q (K*K)]
+size_t tr_work_doubles(int K);
+cudaError_t launch_axpy(const double* x, const double* s, int K, double* y, cudaStream_t st);
+cudaError_t launch_tr_subproblem(const double* out_gh, int K, double radius, double* work,
+                                 double* step, double* info, int* status, cudaStream_t st);
+
+}  // namespace qoc

@@ -1,0 +1,129 @@
+// Per-step contractions that need only the state a_j and costate
+// lambda_{j+1} (parallel over j, after the two vector chains):
+//
+//   a~ = W^T a_j,  l~ = W^T lambda_{j+1}           (eigen-coordinates)
+//   p_j = G_j a_j       = W (P~ a~)                (source of the tangent panel, Eq. gradatheta)
+//   y_j = G_j^H l_{j+1} = W (conj(P~) l~)          (source of the mu panel, Eq. musys)
+//   g_j = Re(l_{j+1}^H G_j a_j)   = Re(l~^H P~ a~)   (gradient, Eq. dLdf)
+//   c_j = Re(l_{j+1}^H G2_j a_j)  = Re(l~^H X' a~)   (Hessian diagonal term, Eq. d2Ldf2)
+//
+// with P~ = Gamma1 o M~ and X' from the spectral preparation.  The stored
+// states are in the frame rotating with the spectral shift m (a^_j =
+// e^{i j dt m} a_j, likewise lambda^), so with kappa = e^{i dt m}:
+//   p^_j = kappa W (P~ a~^),  y^_j = conj(kappa) W (conj(P~) l~^),
+//   g_j = Re(kappa l~^H P~ a~),  c_j = Re(kappa l~^H X' a~).
+// Everything here is binary64; one CTA per step.
+#include "common.cuh"
+#include "kernels.hpp"
+
+namespace qoc {
+
+__device__ __forceinline__ double2 load_state(const void* base, int mixed, size_t idx) {
+  if (mixed) {
+    float4 v = reinterpret_cast<const float4*>(base)[idx];
+    return make_double2((double)v.x + (double)v.z, (double)v.y + (double)v.w);
+  }
+  return reinterpret_cast<const double2*>(base)[idx];
+}
+
+__global__ void k_pointwise(const double* __restrict__ Wg, const double2* __restrict__ Ptil,
+                            const double2* __restrict__ Xp, const void* a_hat, const void* l_hat,
+                            int mixed, int N, int J, double2 kappa, void* p_hat, void* y_hat,
+                            size_t vstride, double* __restrict__ g, double* __restrict__ c,
+                            int want_c) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int j = blockIdx.x;
+  if (j >= J) return;
+  const int ld = N + 1;
+  double* W = reinterpret_cast<double*>(smem_raw);                     // [N][ld]
+  // N (N + 1) is even, so the double2 arrays after W stay 16-byte aligned
+  double2* av = reinterpret_cast<double2*>(W + N * ld);                // a~ then P~ a~
+  double2* lv = av + N;                                                // l~ then conj(P~) l~
+  double2* at = lv + N;                                                // a^ raw
+  double2* lt = at + N;                                                // lambda^ raw
+  double* red = reinterpret_cast<double*>(lt + N);                     // [2][32]
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const double* Wj = Wg + (size_t)j * N * N;
+  for (int e = tid; e < N * N; e += nt) W[(e / N) * ld + (e % N)] = Wj[e];
+  for (int p = tid; p < N; p += nt) {
+    at[p] = load_state(a_hat, mixed, (size_t)j * N + p);
+    lt[p] = load_state(l_hat, mixed, (size_t)(j + 1) * N + p);
+  }
+  __syncthreads();
+  // eigen-coordinates
+  for (int p = tid; p < N; p += nt) {
+    double2 sa = make_double2(0, 0), sl = make_double2(0, 0);
+    for (int r = 0; r < N; ++r) {
+      double w = W[r * ld + p];
+      sa.x = fma(w, at[r].x, sa.x); sa.y = fma(w, at[r].y, sa.y);
+      sl.x = fma(w, lt[r].x, sl.x); sl.y = fma(w, lt[r].y, sl.y);
+    }
+    av[p] = sa;
+    lv[p] = sl;
+  }
+  __syncthreads();
+  const double2* Pj = Ptil + (size_t)j * N * N;
+  const double2* Xj = Xp + (size_t)j * N * N;
+  double gpart = 0, cpart = 0;
+  for (int p = tid; p < N; p += nt) {
+    double2 r = make_double2(0, 0), s = make_double2(0, 0), x = make_double2(0, 0);
+    for (int q = 0; q < N; ++q) {
+      double2 P = Pj[(size_t)q * N + p];          // symmetric: P[p][q] = P[q][p]
+      cfma(r, P, av[q]);
+      cfma_conj(s, P, lv[q]);
+      if (want_c) cfma(x, Xj[(size_t)q * N + p], av[q]);
+    }
+    // Re(kappa conj(l~_p) r_p), Re(kappa conj(l~_p) x_p)
+    double2 kr = cmul(kappa, cconjmul(lv[p], r));
+    gpart += kr.x;
+    if (want_c) cpart += cmul(kappa, cconjmul(lv[p], x)).x;
+    at[p] = r;   // a^ no longer needed
+    lt[p] = s;
+  }
+  gpart = warp_sum(gpart);
+  cpart = warp_sum(cpart);
+  if ((tid & 31) == 0) { red[tid >> 5] = gpart; red[32 + (tid >> 5)] = cpart; }
+  __syncthreads();
+  if (tid == 0) {
+    double gs = 0, cs = 0;
+    for (int w = 0; w < (nt + 31) / 32; ++w) { gs += red[w]; cs += red[32 + w]; }
+    g[j] = gs;
+    if (want_c) c[j] = cs;
+  }
+  // p^ = kappa W r, y^ = conj(kappa) W s
+  const double2 ck = cconj(kappa);
+  for (int p = tid; p < N; p += nt) {
+    double2 pv = make_double2(0, 0), yv = make_double2(0, 0);
+    for (int q = 0; q < N; ++q) {
+      double w = W[p * ld + q];
+      pv.x = fma(w, at[q].x, pv.x); pv.y = fma(w, at[q].y, pv.y);
+      yv.x = fma(w, lt[q].x, yv.x); yv.y = fma(w, lt[q].y, yv.y);
+    }
+    pv = cmul(kappa, pv);
+    yv = cmul(ck, yv);
+    unsigned char* pb = reinterpret_cast<unsigned char*>(p_hat) + (size_t)j * vstride;
+    unsigned char* yb = reinterpret_cast<unsigned char*>(y_hat) + (size_t)j * vstride;
+    if (mixed) {
+      reinterpret_cast<float2*>(pb)[p] = make_float2((float)pv.x, (float)pv.y);
+      reinterpret_cast<float2*>(yb)[p] = make_float2((float)yv.x, (float)yv.y);
+    } else {
+      reinterpret_cast<double2*>(pb)[p] = pv;
+      reinterpret_cast<double2*>(yb)[p] = yv;
+    }
+  }
+}
+
+cudaError_t launch_pointwise(const double* W, const double2* Ptil, const double2* Xp,
+                             const void* a_hat, const void* l_hat, int mixed, int N, int J,
+                             double2 kappa, void* p_hat, void* y_hat, double* g, double* c,
+                             int want_c, cudaStream_t st) {
+  const int threads = N <= 32 ? 32 : (N <= 64 ? 64 : (N <= 128 ? 128 : 256));
+  const size_t smem = (size_t)N * (N + 1) * 8 + 4 * (size_t)N * 16 + 64 * 8;
+  const size_t vstride = ((mixed ? 8 : 16) * (size_t)N + 15) / 16 * 16;
+  cudaFuncSetAttribute(k_pointwise, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  k_pointwise<<<J, threads, smem, st>>>(W, Ptil, Xp, a_hat, l_hat, mixed, N, J, kappa, p_hat,
+                                        y_hat, vstride, g, c, want_c);
+  return cudaGetLastError();
+}
+
+}  // namespace qoc

@@ -1,0 +1,269 @@
+// Time-stepped sweeps (Alg. 2, the sequential loops over j).
+//
+// Every recursion of the method has the same shape: a state panel X (N x kc
+// complex columns) is pushed through one step propagator and receives a
+// rank-one source,
+//   forward  (Eq. discTDSE, Eq. gradatheta):  X <- U_j X + s_j b_j^T
+//   backward (Eq. lambdaevolve, Eq. musys):   X <- U_j^H X + s_j b_j^T
+// In a frame rotating with the fixed spectral shift m, U_j = e^{-i dt m}(I + D_j)
+// and (U_j is complex symmetric, W_j being real) U_j^H = e^{i dt m}(I + conj D_j);
+// the phase factors are folded into the stored sources, so the sweep applies
+//   X <- X + D_j X + s^_j b_j^T   or   X <- X + conj(D_j) X + s^_j b_j^T.
+// Before each update a per-column contraction Re(c_j^H X) is taken (the
+// u_j of the tangent panel, the v_j of the second-order adjoint panel).
+//
+// The columns are independent (the paper vectorises over them with vmap),
+// so a CTA owns kc columns and runs all J steps alone: no grid-wide
+// synchronisation.  One thread (or RS lanes) owns one (row, column) entry.
+// D_j, s^_j, c_j and row j of B are staged by one elected thread with bulk
+// async copies into an NS-deep shared-memory ring (mbarrier completion,
+// bounded waits), so the step loop never waits on global memory.
+//
+// Precision: with TD = double2 everything is binary64.  With TD = float2
+// the product D_j X is binary32 and the state is an unevaluated float pair
+// (hi + lo) updated with TwoSum; since |D_j| ~ dt |lambda - m| << 1 the
+// binary32 rounding enters only through the small increment.
+#include "common.cuh"
+#include "kernels.hpp"
+
+namespace qoc {
+
+template <bool MIX> struct SweepT;
+template <> struct SweepT<false> {
+  using D = double2; using V = double2; using B = double; using R = double;
+};
+template <> struct SweepT<true> {
+  using D = float2; using V = float2; using B = float; using R = float;
+};
+
+template <bool MIX, int RS, bool BWD>
+__global__ void __launch_bounds__(1024) k_sweep(const SweepArgs a, const int nstage) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  using TD = typename SweepT<MIX>::D;
+  using TV = typename SweepT<MIX>::V;
+  using TB = typename SweepT<MIX>::B;
+  using R = typename SweepT<MIX>::R;
+  const int N = a.N, kc = a.kc, J = a.J;
+  constexpr int RPW = 32 / RS;
+  const int WPC = (N + RPW - 1) / RPW;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int l = warp / WPC, rb = warp % WPC;
+  const int rsub = lane % RS;
+  const int i = rb * RPW + lane / RS;
+  const int col0 = blockIdx.x * kc;
+  const int ncols = min(kc, a.K - col0);
+  const bool active = (l < ncols) && (i < N);
+  const bool owner = active && rsub == 0;
+
+  // ---- shared memory layout ----
+  const uint32_t dbytes = (uint32_t)a.dstride;
+  const uint32_t sbytes = a.src ? (uint32_t)(sizeof(TV) * N + 15) / 16 * 16 : 0u;
+  const uint32_t cbytes = a.ctr ? (uint32_t)(sizeof(TV) * N + 15) / 16 * 16 : 0u;
+  const uint32_t bbytes = a.Brow ? (uint32_t)(sizeof(TB) * a.Kp) : 0u;
+  const uint32_t stage = dbytes + sbytes + cbytes + bbytes;
+  unsigned char* ring = smem;
+  TD* X = reinterpret_cast<TD*>(ring + (size_t)nstage * stage);      // [2][kc][N] (hi part)
+  double* red = reinterpret_cast<double*>(X + 2 * kc * N);            // [2][kc][WPC]
+  uint64_t* bar = reinterpret_cast<uint64_t*>(red + 2 * kc * WPC + 1);
+  bar = reinterpret_cast<uint64_t*>((reinterpret_cast<uintptr_t>(bar) + 7) & ~uintptr_t(7));
+  __shared__ int abort_flag;
+
+  const unsigned char* gsrc = reinterpret_cast<const unsigned char*>(a.src);
+  const unsigned char* gctr = reinterpret_cast<const unsigned char*>(a.ctr);
+  const unsigned char* gb = reinterpret_cast<const unsigned char*>(a.Brow);
+  auto issue = [&](int it) {
+    const int jj = BWD ? J - 1 - it : it;
+    const int s = it % nstage;
+    unsigned char* dst = ring + (size_t)s * stage;
+    mbar_arrive_expect_tx(&bar[s], stage);
+    bulk_g2s(dst, a.D + (size_t)jj * a.dstride, dbytes, &bar[s]);
+    dst += dbytes;
+    if (sbytes) { bulk_g2s(dst, gsrc + (size_t)jj * sbytes, sbytes, &bar[s]); dst += sbytes; }
+    if (cbytes) { bulk_g2s(dst, gctr + (size_t)jj * cbytes, cbytes, &bar[s]); dst += cbytes; }
+    if (bbytes) { bulk_g2s(dst, gb + (size_t)jj * bbytes, bbytes, &bar[s]); }
+  };
+
+  if (threadIdx.x == 0) {
+    abort_flag = 0;
+    for (int s = 0; s < nstage; ++s) mbar_init(&bar[s], 1);
+    mbar_fence_init();
+  }
+  // initial state
+  double2 x0 = make_double2(0.0, 0.0);
+  if (active && a.init) {
+    x0 = a.init[(size_t)(col0 + l) * N + i];
+    x0.x *= a.init_scale;
+    x0.y *= a.init_scale;
+  }
+  R hx = (R)x0.x, hy = (R)x0.y;   // state (binary64) or its hi part
+  float lx = 0.f, ly = 0.f;        // lo part (mixed only)
+  if (MIX) {
+    lx = (float)(x0.x - (double)hx);
+    ly = (float)(x0.y - (double)hy);
+  }
+  if (owner) {
+    TD v;
+    v.x = hx; v.y = hy;
+    X[(0 * kc + l) * N + i] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const int pre = min(nstage - 1, J);
+    for (int it = 0; it < pre; ++it) issue(it);
+  }
+
+  int cur = 0;
+  int it = 0;
+  for (; it < J; ++it) {
+    const int jj = BWD ? J - 1 - it : it;
+    const int s = it % nstage;
+    if (threadIdx.x == 0 && it + nstage - 1 < J) {
+      fence_proxy_async_smem();
+      issue(it + nstage - 1);
+    }
+    if (a.states && owner && l == 0) {
+      // vector chains store the state entering step j (a_j forward, lambda_{j+1} backward)
+      const size_t row = (size_t)(BWD ? jj + 1 : jj) * N + i;
+      if (MIX) reinterpret_cast<float4*>(a.states)[row] = make_float4((float)hx, (float)hy, lx, ly);
+      else reinterpret_cast<double2*>(a.states)[row] = make_double2((double)hx, (double)hy);
+    }
+    if (!mbar_wait_bounded(&bar[s], (uint32_t)((it / nstage) & 1))) {
+      atomicExch(&abort_flag, 1);
+    }
+    __syncthreads();
+    if (abort_flag) break;
+    const unsigned char* sp = ring + (size_t)s * stage;
+    const TD* Ds = reinterpret_cast<const TD*>(sp);
+    const TV* srcs = reinterpret_cast<const TV*>(sp + dbytes);
+    const TV* ctrs = reinterpret_cast<const TV*>(sp + dbytes + sbytes);
+    const TB* brow = reinterpret_cast<const TB*>(sp + dbytes + sbytes + cbytes);
+    const TD* Xc = X + (size_t)cur * kc * N + (size_t)l * N;
+
+    // contraction on the entering state: Re(c^H x), summed over rows
+    if (a.ctr) {
+      R v = 0;
+      if (owner) {
+        TV c = ctrs[i];
+        v = c.x * hx + c.y * hy;
+      }
+      v = warp_sum(v);
+      if (WPC == 1) {
+        if (lane == 0 && l < ncols) a.contr[(size_t)jj * a.K + col0 + l] = (double)v;
+      } else if (lane == 0 && l < ncols) {
+        red[((it & 1) * kc + l) * WPC + rb] = (double)v;
+      }
+    }
+    // matvec: acc_i = sum_q D[q][i] X[q]   (D symmetric)
+    R ax0 = 0, ay0 = 0, ax1 = 0, ay1 = 0;
+    if (active) {
+      int q = rsub;
+      for (; q + RS < N; q += 2 * RS) {
+        TD d0 = Ds[(size_t)q * N + i], d1 = Ds[(size_t)(q + RS) * N + i];
+        TD x0v = Xc[q], x1v = Xc[q + RS];
+        if (BWD) { d0.y = -d0.y; d1.y = -d1.y; }
+        ax0 = fma(d0.x, x0v.x, ax0); ax0 = fma(-d0.y, x0v.y, ax0);
+        ay0 = fma(d0.x, x0v.y, ay0); ay0 = fma(d0.y, x0v.x, ay0);
+        ax1 = fma(d1.x, x1v.x, ax1); ax1 = fma(-d1.y, x1v.y, ax1);
+        ay1 = fma(d1.x, x1v.y, ay1); ay1 = fma(d1.y, x1v.x, ay1);
+      }
+      if (q < N) {
+        TD d0 = Ds[(size_t)q * N + i];
+        TD x0v = Xc[q];
+        if (BWD) d0.y = -d0.y;
+        ax0 = fma(d0.x, x0v.x, ax0); ax0 = fma(-d0.y, x0v.y, ax0);
+        ay0 = fma(d0.x, x0v.y, ay0); ay0 = fma(d0.y, x0v.x, ay0);
+      }
+    }
+    R ax = ax0 + ax1, ay = ay0 + ay1;
+#pragma unroll
+    for (int o = 1; o < RS; o <<= 1) {
+      ax += __shfl_xor_sync(0xffffffffu, ax, o);
+      ay += __shfl_xor_sync(0xffffffffu, ay, o);
+    }
+    if (owner) {
+      if (a.src) {
+        const TV sv = srcs[i];
+        const R b = a.Brow ? (R)brow[col0 + l] : (R)1;
+        ax = fma(sv.x, b, ax);
+        ay = fma(sv.y, b, ay);
+      }
+      if (MIX) {
+        float fx = (float)hx, fy = (float)hy;
+        pair_add(fx, lx, (float)ax);
+        pair_add(fy, ly, (float)ay);
+        hx = (R)fx;
+        hy = (R)fy;
+      } else {
+        hx += ax;
+        hy += ay;
+      }
+      TD v;
+      v.x = hx; v.y = hy;
+      X[(size_t)(cur ^ 1) * kc * N + (size_t)l * N + i] = v;
+    }
+    __syncthreads();
+    if (a.ctr && WPC > 1 && rb == 0 && lane == 0 && l < ncols) {
+      double v = 0.0;
+      for (int w = 0; w < WPC; ++w) v += red[((it & 1) * kc + l) * WPC + w];
+      a.contr[(size_t)jj * a.K + col0 + l] = v;
+    }
+    cur ^= 1;
+  }
+  if (abort_flag) {
+    if (threadIdx.x == 0) {
+      raise_status(a.status, DEV_TIMEOUT);
+      // drain copies still in flight (bounded) before the CTA retires
+      for (int k = it; k < min(J, it + nstage - 1); ++k)
+        mbar_wait_bounded(&bar[k % nstage], (uint32_t)((k / nstage) & 1), 100000000ull);
+    }
+    return;
+  }
+  const double fx = (double)hx + (double)lx, fy = (double)hy + (double)ly;
+  if (owner) {
+    if (a.final_out) a.final_out[(size_t)(col0 + l) * N + i] = make_double2(fx, fy);
+    if (a.states && l == 0) {
+      const size_t row = (size_t)(BWD ? 0 : J) * N + i;
+      if (MIX) reinterpret_cast<float4*>(a.states)[row] = make_float4((float)hx, (float)hy, lx, ly);
+      else reinterpret_cast<double2*>(a.states)[row] = make_double2(fx, fy);
+    }
+    if (!(isfinite(fx) && isfinite(fy))) raise_status(a.status, DEV_NONFINITE);
+  }
+}
+
+template <bool MIX, int RS, bool BWD>
+static cudaError_t launch_one(const SweepArgs& a, cudaStream_t st) {
+  using TD = typename SweepT<MIX>::D;
+  using TV = typename SweepT<MIX>::V;
+  using TB = typename SweepT<MIX>::B;
+  const int RPW = 32 / RS;
+  const int WPC = (a.N + RPW - 1) / RPW;
+  const int threads = 32 * WPC * a.kc;
+  if (threads > 1024) return cudaErrorInvalidConfiguration;
+  const uint32_t vb = (uint32_t)(sizeof(TV) * a.N + 15) / 16 * 16;
+  const uint32_t stage = (uint32_t)a.dstride + (a.src ? vb : 0u) + (a.ctr ? vb : 0u) +
+                         (a.Brow ? (uint32_t)(sizeof(TB) * a.Kp) : 0u);
+  const size_t fixed = 2 * (size_t)a.kc * a.N * sizeof(TD) + (2 * (size_t)a.kc * WPC + 1) * 8 + 8;
+  const size_t budget = 200 * 1024;
+  int ns = 8;
+  while (ns > 2 && (size_t)ns * stage + fixed + 8 * ns > budget) --ns;
+  const size_t smem = (size_t)ns * stage + fixed + 8 * ns + 16;
+  if (smem > 227 * 1024) return cudaErrorInvalidConfiguration;
+  cudaFuncSetAttribute(k_sweep<MIX, RS, BWD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  const int grid = (a.K + a.kc - 1) / a.kc;
+  k_sweep<MIX, RS, BWD><<<grid, threads, smem, st>>>(a, ns);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sweep(const SweepArgs& a, int d_fp64, cudaStream_t st) {
+  if (d_fp64) {
+    // binary64 is issue-limited (one warp instruction per 64 cycles per
+    // sub-partition): split each dot product over 4 lanes so a column
+    // spreads over all four sub-partitions.
+    if (a.backward) return launch_one<false, 4, true>(a, st);
+    return launch_one<false, 4, false>(a, st);
+  }
+  if (a.backward) return launch_one<true, 1, true>(a, st);
+  return launch_one<true, 1, false>(a, st);
+}
+
+}  // namespace qoc

@@ -1,0 +1,193 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle on the
+same seeded inputs.  Tolerances: 1e-10 relative for the binary64 path,
+1e-6 for mixed precision (the stated targets), per result.
+
+Intermediates are compared only through basis-invariant quantities
+(eigenvalues, the propagators rebuilt from (W, lambda), states, costates,
+per-step contractions), never eigenvectors themselves."""
+import numpy as np
+import pytest
+
+import paper_2505_00529_gb300 as q
+from paper_2505_00529_gb300 import _lib, build, inputs
+from oracle import qoc_oracle as orc
+
+pytestmark = pytest.mark.gpu
+
+TOL = {q.QOC_FP64: 1e-10, q.QOC_MIXED_FP32: 1e-6}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    build.build()
+    _lib.lib()
+
+
+def rel(a, b):
+    a = np.asarray(a)
+    b = np.asarray(b)
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def check_eval(prob, theta, precision, method=q.QOC_HESS_SECOND_ORDER_ADJOINT, eig=None,
+               ref=None, intermediates=True):
+    tol = TOL[precision]
+    ref = ref if ref is not None else orc.evaluate(prob, theta, order=2, keep=intermediates)
+    with q.Problem(prob, precision=precision, hess_method=method, eig_method=eig) as P:
+        J, g, H = P.eval_grad_hess(theta)
+        assert abs(J - ref["J"]) <= tol * abs(ref["J"]), (J, ref["J"])
+        assert rel(g, ref["grad"]) <= tol, rel(g, ref["grad"])
+        assert rel(H, ref["hess"]) <= tol, rel(H, ref["hess"])
+        np.testing.assert_array_equal(H, H.T)
+        if not intermediates:
+            return P.diagnostics()
+        # (a1) control
+        assert rel(P.buffer(_lib.QOC_BUF_F), ref["f"]) <= 1e-14
+        # (a2) eigenvalues, and the propagators rebuilt from (W, lambda)
+        lam = P.buffer(_lib.QOC_BUF_EIGVAL)
+        W = P.buffer(_lib.QOC_BUF_EIGVEC)
+        scale = np.abs(ref["eig"]).max()
+        assert np.abs(lam - ref["eig"]).max() <= 1e-13 * max(scale, 1.0) * prob.N
+        Ug = np.einsum("jpr,jr,jqr->jpq", W, np.exp(-1j * prob.dt * lam), W)
+        assert rel(Ug, ref["U_prop"]) <= 1e-13
+        # (a4) states, (a7) costates
+        a = P.buffer(_lib.QOC_BUF_STATE)
+        assert rel(a, ref["a"]) <= tol
+        lm = P.buffer(_lib.QOC_BUF_COSTATE)
+        assert rel(lm[1:], ref["lam"][1:]) <= tol
+        # (a7/a9) per-step contractions
+        assert rel(P.buffer(_lib.QOC_BUF_G), ref["g"]) <= tol
+        assert rel(P.buffer(_lib.QOC_BUF_C), ref["c"]) <= tol
+        assert rel(P.buffer(_lib.QOC_BUF_U), ref["U"]) <= tol
+        if method == q.QOC_HESS_SECOND_ORDER_ADJOINT:
+            assert rel(P.buffer(_lib.QOC_BUF_V), ref["V"]) <= tol
+            assert rel(P.buffer(_lib.QOC_BUF_HESS_RAW), ref["hess_raw"]) <= tol
+        # (a5) final tangent panel
+        assert rel(P.buffer(_lib.QOC_BUF_SJ), ref["SJ"]) <= tol
+        return P.diagnostics()
+
+
+SHAPES = [  # (N, K, J): tiny, odd N, ragged tails, single step, N = 1, max N
+    (4, 3, 50), (5, 8, 37), (2, 1, 1), (1, 2, 10), (7, 5, 33), (16, 12, 200), (32, 64, 300),
+    (33, 6, 41), (64, 5, 60),
+]
+
+
+@pytest.mark.parametrize("shape", SHAPES, ids=lambda s: "N%d_K%d_J%d" % s)
+@pytest.mark.parametrize("precision", [q.QOC_FP64, q.QOC_MIXED_FP32], ids=["fp64", "mixed"])
+def test_small_parity(shape, precision):
+    N, K, J = shape
+    prob = inputs.small_problem(N=N, K=K, J=J, seed=100 + N + K + J, dt=0.05, basis="random")
+    theta = inputs.eval_theta(K, 7)
+    check_eval(prob, theta, precision)
+
+
+@pytest.mark.parametrize("precision", [q.QOC_FP64, q.QOC_MIXED_FP32], ids=["fp64", "mixed"])
+def test_tangent_form_and_jacobi_eig(precision):
+    prob = inputs.small_problem(N=12, K=10, J=120, seed=5, dt=0.04, basis="sine_cosine")
+    theta = inputs.eval_theta(10, 8)
+    ref = orc.evaluate(prob, theta, order=2, keep=True)
+    check_eval(prob, theta, precision, method=q.QOC_HESS_TANGENT, ref=ref)
+    check_eval(prob, theta, precision, eig=q.QOC_EIG_JACOBI_FP64, ref=ref)
+
+
+def test_maximal_model():
+    """Maximal model f_j = theta_j (Eq. maximal), K = J."""
+    J = 64
+    prob = inputs.small_problem(N=4, K=J, J=J, seed=9, dt=0.1, basis="maximal")
+    theta = inputs.eval_theta(J, 10)
+    check_eval(prob, theta, q.QOC_FP64)
+    check_eval(prob, theta, q.QOC_MIXED_FP32)
+
+
+def test_zero_control_and_degenerate_spectrum():
+    """f = 0 (theta = 0) and an exactly degenerate H0 (repeated energies)."""
+    N, K, J, dt = 6, 4, 80, 0.05
+    prob = inputs.small_problem(N=N, K=K, J=J, seed=12, dt=dt)
+    prob.H0 = np.diag([-1.0, -1.0, -0.5, -0.5, 0.0, 0.0])
+    for theta in (np.zeros(K), inputs.eval_theta(K, 13)):
+        check_eval(prob, theta, q.QOC_FP64)
+        check_eval(prob, theta, q.QOC_MIXED_FP32)
+
+
+@pytest.mark.parametrize("precision", [q.QOC_FP64, q.QOC_MIXED_FP32], ids=["fp64", "mixed"])
+def test_config1_full_size(precision):
+    prob = inputs.config_problem(1)
+    for seed in (0, 1):
+        theta = inputs.eval_theta(prob.K, seed)
+        d = check_eval(prob, theta, precision)
+        assert d["norm_drift"] < (1e-12 if precision == q.QOC_FP64 else 1e-6)
+        assert d["hess_asym"] < 1e-10
+
+
+@pytest.fixture(scope="module")
+def config2_ref():
+    prob = inputs.config_problem(2)
+    theta = inputs.eval_theta(prob.K, 0)
+    return prob, theta, orc.evaluate(prob, theta, order=2)
+
+
+@pytest.mark.parametrize("precision", [q.QOC_FP64, q.QOC_MIXED_FP32], ids=["fp64", "mixed"])
+def test_config2_full_size(config2_ref, precision):
+    prob, theta, ref = config2_ref
+    check_eval(prob, theta, precision, ref=ref, intermediates=False)
+
+
+def test_deterministic():
+    prob = inputs.small_problem(N=16, K=8, J=100, seed=3, dt=0.05)
+    theta = inputs.eval_theta(8, 4)
+    for prec in (q.QOC_FP64, q.QOC_MIXED_FP32):
+        with q.Problem(prob, precision=prec) as P:
+            r1 = P.eval_grad_hess(theta)
+            r2 = P.eval_grad_hess(theta)
+        assert r1[0] == r2[0]
+        np.testing.assert_array_equal(r1[1], r2[1])
+        np.testing.assert_array_equal(r1[2], r2[2])
+
+
+def test_eval_J_and_grad_entry_points():
+    prob = inputs.small_problem(N=8, K=6, J=90, seed=14, dt=0.05)
+    theta = inputs.eval_theta(6, 15)
+    ref = orc.evaluate(prob, theta, order=1)
+    with q.Problem(prob) as P:
+        assert abs(P.eval_J(theta) - ref["J"]) <= 1e-10 * abs(ref["J"])
+        J, g = P.eval_grad(theta)
+        assert rel(g, ref["grad"]) <= 1e-10
+        with pytest.raises(q.QocError) as e:
+            P.eval_J(np.full(6, np.nan))
+        assert e.value.status == _lib.QOC_EINVAL
+
+
+def test_device_pointer_entry_point():
+    torch = pytest.importorskip("torch")
+    prob = inputs.small_problem(N=8, K=6, J=90, seed=16, dt=0.05)
+    theta = inputs.eval_theta(6, 17)
+    stream = torch.cuda.current_stream()
+    with q.Problem(prob, cuda_stream=stream.cuda_stream) as P:
+        J, g, H = P.eval_grad_hess(theta)
+        th = torch.tensor(theta, dtype=torch.float64, device="cuda")
+        out = torch.zeros(1 + 6 + 36, dtype=torch.float64, device="cuda")
+        q.qoc_eval_grad_hess_dev(P.handle, th.data_ptr(), out.data_ptr())
+        q.qoc_sync_status(P.handle)
+        o = out.cpu().numpy()
+    assert o[0] == J
+    np.testing.assert_array_equal(o[1:7], g)
+    np.testing.assert_array_equal(o[7:].reshape(6, 6), H)
+
+
+@pytest.mark.parametrize("precision", [q.QOC_FP64, q.QOC_MIXED_FP32], ids=["fp64", "mixed"])
+def test_trust_region_config1(precision):
+    """Exact-Hessian trust region from theta = 0 (Sec. IV-B): both converge to
+    the same J, |grad| below tolerance, Hessian positive definite."""
+    prob = inputs.config_problem(1)
+    th_o, info_o = orc.trust_region_solve(prob, np.zeros(prob.K), gtol=1e-8, xtol=1e-12)
+    with q.Problem(prob, precision=precision) as P:
+        th, info = P.trust_region_solve(np.zeros(prob.K), gtol=1e-8 if precision == 0 else 1e-5,
+                                        xtol=1e-12)
+        J, g, H = P.eval_grad_hess(th)
+    assert info["stop"] == "gtol", info
+    assert abs(info["J"] - info_o["J"]) <= 1e-8 * abs(info_o["J"])
+    assert np.linalg.eigvalsh(H).min() > 0
+    if precision == q.QOC_FP64:
+        assert info["iters"] == info_o["iters"]
+        assert rel(th, th_o) < 1e-6
