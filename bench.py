@@ -200,8 +200,9 @@ def run_ours(args):
     N, K, J = prob.N, prob.K, prob.J
     theta = inputs.eval_theta(K, 0)
     prec = q.QOC_MIXED_FP32 if args.precision == "mixed" else q.QOC_FP64
-    stream = torch.cuda.current_stream()
     dev = torch.device("cuda", local)
+    stream = torch.cuda.Stream(device=dev)     # a real (non-default) stream the library runs on
+    torch.cuda.set_stream(stream)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # > L2 (129 MB)
 
     def measure(precision, steps, warmup, timing=True):
@@ -225,7 +226,7 @@ def run_ours(args):
             q.qoc_eval_grad_hess_dev(P.handle, th.data_ptr(), out.data_ptr())
             ev[k][1].record(stream)
             if timing:
-                stream.synchronize()
+                q.qoc_sync_status(P.handle)
                 phases.append(q.qoc_get_diagnostics(P.handle)["phase_ms"])
         torch.cuda.synchronize()
         q.qoc_sync_status(P.handle)

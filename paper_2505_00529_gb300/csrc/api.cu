@@ -37,6 +37,7 @@ struct qoc_problem {
   double dt = 0, w_f = 0, w_t = 0, mshift = 0;
   int precision = 0, hess_method = QOC_HESS_SECOND_ORDER_ADJOINT, eig_method = QOC_EIG_REFINED;
   int refine_sweeps = 2;
+  double angle_tol = 1e-13;
   cudaStream_t stream = nullptr;
   bool own_stream = false;
   int timing = 0;
@@ -107,10 +108,12 @@ bool symmetric(const double* A, int N) {
 
 double2 cexpi_h(double x) { return make_double2(std::cos(x), std::sin(x)); }
 
+// panel columns per CTA: binary64 is throughput-limited per SM (one column
+// per CTA spreads the panel over K SMs); binary32 keeps two columns per CTA
+// up to N = 32 (8 warps) and one beyond
 int sweep_kc(const qoc_problem* p) {
   if (p->precision == QOC_FP64) return 1;
-  if (p->N <= 32) return 4;
-  return 2;
+  return p->N <= 32 ? 2 : 1;
 }
 
 qoc_status device_status(qoc_problem* p) {
@@ -133,7 +136,7 @@ qoc_status enqueue_eval(qoc_problem* p, const double* theta_dev, int order, doub
   QOC_TRY(launch_control(p->B, p->Kp, theta_dev, J, K, p->f, st));
   QOC_TRY(launch_eig(p->H0, p->M, p->f, N, J, p->W, p->eig, p->status,
                      p->eig_method == QOC_EIG_JACOBI_FP64 ? EIG_JACOBI_FP64 : EIG_REFINED,
-                     p->refine_sweeps, st));
+                     p->refine_sweeps, p->angle_tol, st));
   if (p->timing) cudaEventRecord(p->ev[1], st);
   QOC_TRY(launch_prep(p->W, p->eig, p->M, N, J, p->dt, p->mshift, p->D, p->dstride, d_fp64,
                       order >= 1, p->Ptil, p->Xp, p->status, st));
@@ -280,7 +283,12 @@ qoc_status qoc_create_problem(int N, const double* H0, const double* M, const do
   if (!p) return QOC_ENOMEM;
   p->N = N; p->K = K; p->J = steps; p->Kp = (K + 3) / 4 * 4;
   p->dt = dt; p->w_f = w_ctrl; p->w_t = w_term; p->precision = precision;
-  p->refine_sweeps = precision == QOC_FP64 ? 2 : 1;
+  // the eigendecomposition is binary64-accurate on both paths: refinement
+  // until W is orthonormal to the binary64 floor (at most 4 updates), then a
+  // clean-up of every rotation angle above 1e-13 (smaller angles move the
+  // propagators by less than 1e-13 dt |lambda_p - lambda_q|)
+  p->refine_sweeps = 4;
+  p->angle_tol = 1e-13;
   double tr = 0;
   for (int i = 0; i < N; ++i) tr += H0[i * N + i];
   p->mshift = tr / N;
@@ -409,6 +417,7 @@ qoc_status qoc_sync_status(qoc_problem* p) {
   QOC_TRY(cudaMemcpyAsync(p->hstatus, p->status, sizeof(int), cudaMemcpyDeviceToHost, p->stream));
   QOC_TRY(cudaMemsetAsync(p->status, 0, sizeof(int), p->stream));
   QOC_TRY(cudaStreamSynchronize(p->stream));
+  collect_timing(p);
   return device_status(p);
 }
 
@@ -525,7 +534,7 @@ qoc_status qoc_trust_region_solve(qoc_problem* p, const double* theta0, const qo
     qoc_status s = enqueue_eval(p, p->theta, 2, p->out);
     if (s != QOC_OK) return s;
     QOC_TRY(launch_eig(p->out + 1 + K, p->trzero, p->trzero, K, 1, p->trwork + 3 * K,
-                       p->trwork + 2 * K, p->status, EIG_JACOBI_FP64, 0, st));
+                       p->trwork + 2 * K, p->status, EIG_JACOBI_FP64, 0, 0.0, st));
     return QOC_OK;
   };
   qoc_status s = eval_gh();

@@ -29,36 +29,27 @@ __device__ __forceinline__ int rr_elem(int pos, int r, int NP) {
   return pos == 0 ? 0 : ((pos - 1 + r) % (NP - 1)) + 1;
 }
 
+// Parallel cyclic Jacobi sweeps on the symmetric A (N x N, leading dimension
+// ld, shared memory), accumulating the rotations into V (V <- V R).  In each
+// round the N/2 disjoint pairs of the round-robin schedule are rotated at
+// once: A <- R^T A R on 2 x 2 blocks (upper triangle, mirrored), V <- V R.
+// A pair (p, q) is rotated when |a_pq| exceeds both the classical threshold
+// (0.01 eps sqrt|a_pp a_qq|) and angle_tol |a_qq - a_pp| (a rotation smaller
+// than angle_tol is not worth applying).  Stops when a sweep rotates nothing
+// or off(A)^2 <= off_tol^2 * |A|_F^2.  Returns 1 when converged.
+// Scratch: cs [NP], pr [NP] ints, red [>= 2*nwarps + 2] doubles (16-aligned).
 template <typename T>
-__global__ void k_eig_jacobi(const double* __restrict__ H0, const double* __restrict__ M,
-                             const double* __restrict__ f, int N, int J,
-                             double* __restrict__ W_out, double* __restrict__ eig_out,
-                             int* status) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int j = blockIdx.x;
-  if (j >= J) return;
-  const int ld = N + 1;
+__device__ int jacobi_sweeps(T* A, T* V, int N, int ld, int max_sweeps, T angle_tol,
+                             double off_tol, T* cs, int* pr, double* red) {
   const int NP = N + (N & 1);
   const int NH = NP / 2;
-  T* A = reinterpret_cast<T*>(smem_raw);
-  T* V = A + N * ld;
-  T* cs = V + N * ld;            // [NH][2] cosine / sine
-  int* pr = reinterpret_cast<int*>(cs + 2 * NH);  // [NH][2] pair indices
-  double* red = reinterpret_cast<double*>(pr + 2 * NH + 2);
-  red = reinterpret_cast<double*>((reinterpret_cast<uintptr_t>(red) + 15) & ~uintptr_t(15));
-
   const int tid = threadIdx.x, nt = blockDim.x;
-  const double fj = f[j];
-  for (int e = tid; e < N * N; e += nt) {
-    int p = e / N, q = e % N;
-    A[p * ld + q] = (T)(H0[e] + fj * M[e]);
-    V[p * ld + q] = (T)(p == q ? 1.0 : 0.0);
-  }
-  __syncthreads();
-
   const T eps = (T)JacobiEps<T>::eps;
-  bool converged = false;
-  for (int sweep = 0; sweep < JacobiEps<T>::max_sweeps && !converged; ++sweep) {
+  __shared__ int nrot;
+  int converged = 0;
+  for (int sweep = 0; sweep < max_sweeps && !converged; ++sweep) {
+    if (tid == 0) nrot = 0;
+    __syncthreads();
     for (int r = 0; r < NP - 1; ++r) {
       if (tid < NH) {
         int p = rr_elem(tid, r, NP), q = rr_elem(NP - 1 - tid, r, NP);
@@ -67,11 +58,13 @@ __global__ void k_eig_jacobi(const double* __restrict__ H0, const double* __rest
         if (q < N) {
           T apq = A[p * ld + q], app = A[p * ld + p], aqq = A[q * ld + q];
           T thr = eps * (T)0.01 * sqrt(fabs(app) * fabs(aqq));
-          if (fabs(apq) > thr && apq != (T)0) {
+          T athr = angle_tol * fabs(aqq - app);
+          if (fabs(apq) > thr && fabs(apq) > athr && apq != (T)0) {
             T th = (aqq - app) / (2 * apq);
             T t = (th >= 0 ? (T)1 : (T)-1) / (fabs(th) + sqrt(th * th + 1));
             c = 1 / sqrt(t * t + 1);
             s = t * c;
+            atomicAdd(&nrot, 1);
           }
         }
         pr[2 * tid] = p;
@@ -80,18 +73,18 @@ __global__ void k_eig_jacobi(const double* __restrict__ H0, const double* __rest
         cs[2 * tid + 1] = s;
       }
       __syncthreads();
-      // A <- R^T A R on 2x2 blocks (k <= l, mirrored), V <- V R
       const int nblk = NH * (NH + 1) / 2;
       for (int b = tid; b < nblk + N * NH; b += nt) {
         if (b < nblk) {
-          // decode upper-triangular block index b -> (k, l), k <= l
           int k = 0, rem = b;
           while (rem >= NH - k) { rem -= NH - k; ++k; }
-          int l = k + rem;
-          int p0 = pr[2 * k], p1 = pr[2 * k + 1], q0 = pr[2 * l], q1 = pr[2 * l + 1];
+          const int l = k + rem;
+          const T sk = cs[2 * k + 1], sl = cs[2 * l + 1];
+          if (sk == (T)0 && sl == (T)0) continue;   // both identity: block unchanged
+          const T ck = cs[2 * k], cl = cs[2 * l];
+          const int p0 = pr[2 * k], p1 = pr[2 * k + 1], q0 = pr[2 * l], q1 = pr[2 * l + 1];
           if (p1 >= N || q1 >= N) {
-            // blocks touching the dummy index of odd N: only the real rows/cols move
-            T ck = cs[2 * k], sk = cs[2 * k + 1], cl = cs[2 * l], sl = cs[2 * l + 1];
+            // blocks touching the dummy index of odd N: only real rows/cols move
             if (p1 < N && q1 >= N) {  // rows p0,p1 x column q0 (q0 unpaired)
               T x0 = A[p0 * ld + q0], x1 = A[p1 * ld + q0];
               T y0 = ck * x0 - sk * x1, y1 = sk * x0 + ck * x1;
@@ -103,32 +96,29 @@ __global__ void k_eig_jacobi(const double* __restrict__ H0, const double* __rest
               A[p0 * ld + q0] = y0; A[p0 * ld + q1] = y1;
               A[q0 * ld + p0] = y0; A[q1 * ld + p0] = y1;
             }
-            // both unpaired: only possible for k == l (the dummy pair); A[p0][p0] unchanged
             continue;
           }
-          T ck = cs[2 * k], sk = cs[2 * k + 1], cl = cs[2 * l], sl = cs[2 * l + 1];
           T a00 = A[p0 * ld + q0], a01 = A[p0 * ld + q1], a10 = A[p1 * ld + q0], a11 = A[p1 * ld + q1];
-          // left: R_k^T [[a00 a01][a10 a11]] with R = [[c s][-s c]] -> R^T = [[c -s][s c]]
+          // left: R_k^T X, R = [[c s][-s c]];  right: (...) R_l
           T b00 = ck * a00 - sk * a10, b01 = ck * a01 - sk * a11;
           T b10 = sk * a00 + ck * a10, b11 = sk * a01 + ck * a11;
-          // right: [...] R_l
           T c00 = cl * b00 - sl * b01, c01 = sl * b00 + cl * b01;
           T c10 = cl * b10 - sl * b11, c11 = sl * b10 + cl * b11;
-          if (k == l) {
-            c01 = (T)0.5 * (c01 + c10);  // exact zero in exact arithmetic after the rotation
-            if (sk != (T)0) c01 = (T)0;
-            c10 = c01;
+          if (k == l) {  // the rotated pair: its off-diagonal is zero by construction
+            c01 = (T)0;
+            c10 = (T)0;
           }
           A[p0 * ld + q0] = c00; A[p0 * ld + q1] = c01; A[p1 * ld + q0] = c10; A[p1 * ld + q1] = c11;
           if (k != l) {
             A[q0 * ld + p0] = c00; A[q1 * ld + p0] = c01; A[q0 * ld + p1] = c10; A[q1 * ld + p1] = c11;
           }
         } else {
-          int e = b - nblk;
-          int i = e / NH, l = e % NH;
-          int q0 = pr[2 * l], q1 = pr[2 * l + 1];
-          if (q1 >= N) continue;
-          T cl = cs[2 * l], sl = cs[2 * l + 1];
+          const int e = b - nblk;
+          const int i = e / NH, l = e % NH;
+          const T sl = cs[2 * l + 1];
+          const int q0 = pr[2 * l], q1 = pr[2 * l + 1];
+          if (q1 >= N || sl == (T)0) continue;
+          const T cl = cs[2 * l];
           T v0 = V[i * ld + q0], v1 = V[i * ld + q1];
           V[i * ld + q0] = cl * v0 - sl * v1;
           V[i * ld + q1] = sl * v0 + cl * v1;
@@ -136,11 +126,11 @@ __global__ void k_eig_jacobi(const double* __restrict__ H0, const double* __rest
       }
       __syncthreads();
     }
-    // convergence: off-diagonal Frobenius^2 vs total
+    // convergence: no rotation in the sweep, or off-diagonal small
     double off = 0, tot = 0;
     for (int e = tid; e < N * N; e += nt) {
-      int p = e / N, q = e % N;
-      double v = (double)A[p * ld + q];
+      const int p = e / N, q = e % N;
+      const double v = (double)A[p * ld + q];
       tot += v * v;
       if (p != q) off += v * v;
     }
@@ -151,22 +141,34 @@ __global__ void k_eig_jacobi(const double* __restrict__ H0, const double* __rest
     if (tid == 0) {
       double o = 0, t = 0;
       for (int w = 0; w < (nt + 31) / 32; ++w) { o += red[2 * w]; t += red[2 * w + 1]; }
-      red[64] = (o <= (double)eps * (double)eps * t || o == 0.0) ? 1.0 : 0.0;
+      red[63] = (nrot == 0 || o <= off_tol * off_tol * t || o == 0.0) ? 1.0 : 0.0;
     }
     __syncthreads();
-    converged = red[64] != 0.0;
+    converged = red[63] != 0.0;
     __syncthreads();
   }
-  if (!converged && tid == 0) raise_status(status, DEV_EIG_NOCONV);
+  return converged;
+}
 
-  // sort ascending (rank sort, ties by index) and write W (columns), lambda
-  double* Wj = W_out + (size_t)j * N * N;
-  double* ej = eig_out + (size_t)j * N;
-  for (int i = tid; i < N; i += nt) {
-    T di = A[i * ld + i];
+// row-major upper-triangle index t -> (i, k), k >= i
+__device__ __forceinline__ void tri_index_e(int t, int N, int& i, int& k) {
+  const float b = 2.0f * N + 1.0f;
+  int r = (int)floorf(0.5f * (b - sqrtf(fmaxf(b * b - 8.0f * t, 0.0f))));
+  r = max(0, min(r, N - 1));
+  while (r > 0 && r * N - r * (r - 1) / 2 > t) --r;
+  while (r + 1 < N && (r + 1) * N - (r + 1) * r / 2 <= t) ++r;
+  i = r;
+  k = t - (r * N - r * (r - 1) / 2) + r;
+}
+
+// rank-sort the diagonal of A ascending (ties by index) and write W = V(:, order), lambda
+template <typename T>
+__device__ void sort_write(const T* A, const T* V, int N, int ld, double* Wj, double* ej) {
+  for (int i = threadIdx.x; i < N; i += blockDim.x) {
+    const T di = A[i * ld + i];
     int rank = 0;
     for (int k = 0; k < N; ++k) {
-      T dk = A[k * ld + k];
+      const T dk = A[k * ld + k];
       rank += (dk < di) || (dk == di && k < i);
     }
     ej[rank] = (double)di;
@@ -174,28 +176,65 @@ __global__ void k_eig_jacobi(const double* __restrict__ H0, const double* __rest
   }
 }
 
-// Ogita-Aishima refinement sweeps in binary64 (see the file header).
-__global__ void k_eig_refine(const double* __restrict__ H0, const double* __restrict__ M,
-                             const double* __restrict__ f, int N, int J, int sweeps,
-                             double* __restrict__ W_io, double* __restrict__ eig_out, int* status) {
+template <typename T>
+__global__ void k_eig_jacobi(const double* __restrict__ H0, const double* __restrict__ M,
+                             const double* __restrict__ f, int N, int J,
+                             double* __restrict__ W_out, double* __restrict__ eig_out,
+                             int* status) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int j = blockIdx.x;
   if (j >= J) return;
   const int ld = N + 1;
+  const int NP = N + (N & 1);
+  T* A = reinterpret_cast<T*>(smem_raw);
+  T* V = A + N * ld;
+  T* cs = V + N * ld;
+  int* pr = reinterpret_cast<int*>(cs + NP);
+  double* red = reinterpret_cast<double*>(pr + NP + 2);
+  red = reinterpret_cast<double*>((reinterpret_cast<uintptr_t>(red) + 15) & ~uintptr_t(15));
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const double fj = f[j];
+  for (int e = tid; e < N * N; e += nt) {
+    const int p = e / N, q = e % N;
+    A[p * ld + q] = (T)(H0[e] + fj * M[e]);
+    V[p * ld + q] = (T)(p == q ? 1.0 : 0.0);
+  }
+  __syncthreads();
+  const int ok = jacobi_sweeps<T>(A, V, N, ld, JacobiEps<T>::max_sweeps, (T)0,
+                                  4.0 * JacobiEps<T>::eps, cs, pr, red);
+  if (!ok && tid == 0) raise_status(status, DEV_EIG_NOCONV);
+  sort_write<T>(A, V, N, ld, W_out + (size_t)j * N * N, eig_out + (size_t)j * N);
+}
+
+// Ogita-Aishima refinement sweeps in binary64 (at most `sweeps` updates,
+// stopping once |I - W^T W|_F reaches the binary64 floor), then a binary64
+// Jacobi clean-up of S = W^T H W that resolves what the refinement leaves
+// alone (pairs closer than its cluster threshold), then W <- W V.
+__global__ void k_eig_refine(const double* __restrict__ H0, const double* __restrict__ M,
+                             const double* __restrict__ f, int N, int J, int sweeps,
+                             double angle_tol, double* __restrict__ W_io,
+                             double* __restrict__ eig_out, int* status) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int j = blockIdx.x;
+  if (j >= J) return;
+  const int ld = N + 1;
+  const int NP = N + (N & 1);
   double* H = reinterpret_cast<double*>(smem_raw);
   double* W = H + N * ld;
   double* T = W + N * ld;
   double* S = T + N * ld;
   double* R = S + N * ld;
-  double* lam = R + N * ld;
-  double* red = lam + N + 1;   // [64]
+  double* lam = R + N * ld;          // [N + 1]
+  double* red = lam + N + 1;         // [64]
+  double* cs = red + 64;             // [NP]
+  int* pr = reinterpret_cast<int*>(cs + NP);  // [NP + 2]
   const int tid = threadIdx.x, nt = blockDim.x;
   const double fj = f[j];
   double* Wg = W_io + (size_t)j * N * N;
   double hn = 0;
   for (int e = tid; e < N * N; e += nt) {
-    int p = e / N, q = e % N;
-    double h = H0[e] + fj * M[e];
+    const int p = e / N, q = e % N;
+    const double h = H0[e] + fj * M[e];
     H[p * ld + q] = h;
     W[p * ld + q] = Wg[e];
     hn += h * h;
@@ -211,37 +250,45 @@ __global__ void k_eig_refine(const double* __restrict__ H0, const double* __rest
   __syncthreads();
   const double Hnorm = red[40];
 
-  for (int it = 0; it < sweeps; ++it) {
+  // Refinement sweeps until W is orthonormal to the binary64 floor: each sweep
+  // computes S = W^T H W and R = I - W^T W; when |R|_F <= orth_tol, S is the
+  // matrix the clean-up diagonalises, otherwise W <- W (I + E).
+  // rounding floor of |I - W^T W|_F for an orthonormal W: ~ eps N^1.5
+  const double orth_tol = 8.0 * 1.12e-16 * (double)N * sqrt((double)N);
+  for (int it = 0;; ++it) {
     // T = H W
     for (int e = tid; e < N * N; e += nt) {
-      int i = e / N, k = e % N;
+      const int i = e / N, k = e % N;
       double acc = 0;
       for (int r = 0; r < N; ++r) acc = fma(H[i * ld + r], W[r * ld + k], acc);
       T[i * ld + k] = acc;
     }
     __syncthreads();
-    // S = W^T T, R = I - W^T W
-    double sn = 0, rn = 0;
-    for (int e = tid; e < N * N; e += nt) {
-      int i = e / N, k = e % N;
-      double s = 0, w = 0;
+    // S = W^T T, R = I - W^T W (both symmetric: upper triangle, mirrored)
+    double rn = 0;
+    for (int t = tid; t < N * (N + 1) / 2; t += nt) {
+      int i, k;
+      tri_index_e(t, N, i, k);
+      double sa = 0, w = 0;
       for (int r = 0; r < N; ++r) {
-        double wri = W[r * ld + i];
-        s = fma(wri, T[r * ld + k], s);
+        const double wri = W[r * ld + i];
+        sa = fma(wri, T[r * ld + k], sa);
         w = fma(wri, W[r * ld + k], w);
       }
-      S[i * ld + k] = s;
-      double rr = (i == k ? 1.0 : 0.0) - w;
+      S[i * ld + k] = sa;
+      S[k * ld + i] = sa;
+      const double rr = (i == k ? 1.0 : 0.0) - w;
       R[i * ld + k] = rr;
-      rn += rr * rr;
+      R[k * ld + i] = rr;
+      rn += (i == k ? 1.0 : 2.0) * rr * rr;
     }
     __syncthreads();
     for (int i = tid; i < N; i += nt) lam[i] = S[i * ld + i] / (1.0 - R[i * ld + i]);
-    __syncthreads();
+    double sn = 0;
     for (int e = tid; e < N * N; e += nt) {
-      int i = e / N, k = e % N;
+      const int i = e / N, k = e % N;
       if (i != k) sn += S[i * ld + k] * S[i * ld + k];
-      else { double d = S[i * ld + i] - lam[i]; sn += d * d; }
+      else { const double d = S[i * ld + i] - S[i * ld + i] / (1.0 - R[i * ld + i]); sn += d * d; }
     }
     sn = warp_sum(sn);
     rn = warp_sum(rn);
@@ -251,68 +298,83 @@ __global__ void k_eig_refine(const double* __restrict__ H0, const double* __rest
       double a = 0, b = 0;
       for (int w = 0; w < (nt + 31) / 32; ++w) { a += red[2 * w]; b += red[2 * w + 1]; }
       red[41] = 2.0 * (sqrt(a) + Hnorm * sqrt(b));  // cluster threshold delta
+      red[42] = sqrt(b);                             // |I - W^T W|_F
     }
     __syncthreads();
     const double delta = red[41];
-    // E overwrites S
+    if (red[42] <= orth_tol) break;
+    if (it >= sweeps) {   // sweep budget spent: flag only a real failure
+      if (tid == 0 && !(red[42] <= 1e-10)) raise_status(status, DEV_EIG_NOCONV);
+      break;
+    }
+    // E overwrites T
     for (int e = tid; e < N * N; e += nt) {
-      int i = e / N, k = e % N;
-      double rik = R[i * ld + k];
+      const int i = e / N, k = e % N;
+      const double rik = R[i * ld + k];
       double eik;
       if (i == k) eik = 0.5 * rik;
       else {
-        double gap = lam[k] - lam[i];
+        const double gap = lam[k] - lam[i];
         eik = fabs(gap) > delta ? (S[i * ld + k] + lam[k] * rik) / gap : 0.5 * rik;
       }
       T[i * ld + k] = eik;
     }
     __syncthreads();
-    // W <- W + W E   (R reused as scratch for W E)
+    // W <- W + W E   (R as scratch for W E)
     for (int e = tid; e < N * N; e += nt) {
-      int i = e / N, k = e % N;
+      const int i = e / N, k = e % N;
       double acc = 0;
       for (int r = 0; r < N; ++r) acc = fma(W[i * ld + r], T[r * ld + k], acc);
       R[i * ld + k] = acc;
     }
     __syncthreads();
     for (int e = tid; e < N * N; e += nt) {
-      int i = e / N, k = e % N;
+      const int i = e / N, k = e % N;
       W[i * ld + k] += R[i * ld + k];
     }
     __syncthreads();
   }
-  // eigenvalues: Rayleigh quotients of the refined vectors (sorted order kept)
+  // clean-up: Jacobi on S = W^T H W with V = I (in R)
+  for (int e = tid; e < N * N; e += nt) R[(e / N) * ld + (e % N)] = (e / N == e % N) ? 1.0 : 0.0;
+  __syncthreads();
+  __shared__ int any_rot;
+  if (tid == 0) any_rot = 0;
+  __syncthreads();
+  const int ok = jacobi_sweeps<double>(S, R, N, ld, 12, angle_tol, 0.0, cs, pr, red);
+  if (!ok && tid == 0) raise_status(status, DEV_EIG_NOCONV);
+  // did anything rotate?  (V != I)
   for (int e = tid; e < N * N; e += nt) {
-    int i = e / N, k = e % N;
-    double acc = 0;
-    for (int r = 0; r < N; ++r) acc = fma(H[i * ld + r], W[r * ld + k], acc);
-    T[i * ld + k] = acc;
+    const int i = e / N, k = e % N;
+    if (R[i * ld + k] != ((i == k) ? 1.0 : 0.0)) any_rot = 1;
   }
   __syncthreads();
-  double* ej = eig_out + (size_t)j * N;
-  for (int k = tid; k < N; k += nt) {
-    double num = 0, den = 0;
-    for (int r = 0; r < N; ++r) {
-      num = fma(W[r * ld + k], T[r * ld + k], num);
-      den = fma(W[r * ld + k], W[r * ld + k], den);
+  if (any_rot) {   // W <- W V (T as scratch)
+    for (int e = tid; e < N * N; e += nt) {
+      const int i = e / N, k = e % N;
+      double acc = 0;
+      for (int r = 0; r < N; ++r) acc = fma(W[i * ld + r], R[r * ld + k], acc);
+      T[i * ld + k] = acc;
     }
-    double l = num / den;
-    if (!isfinite(l)) raise_status(status, DEV_NONFINITE);
-    ej[k] = l;
+    __syncthreads();
+    for (int e = tid; e < N * N; e += nt) W[(e / N) * ld + (e % N)] = T[(e / N) * ld + (e % N)];
+    __syncthreads();
   }
-  for (int e = tid; e < N * N; e += nt) {
-    int p = e / N, q = e % N;
-    Wg[e] = W[p * ld + q];
-  }
+  bool bad = false;
+  for (int i = tid; i < N; i += nt) bad |= !isfinite(S[i * ld + i]);
+  if (bad) raise_status(status, DEV_NONFINITE);
+  sort_write<double>(S, W, N, ld, Wg, eig_out + (size_t)j * N);
 }
 
 static size_t jacobi_smem(int N, size_t tsize) {
-  int NP = N + (N & 1);
+  const int NP = N + (N & 1);
   size_t s = 2 * (size_t)N * (N + 1) * tsize + (size_t)NP * tsize + (size_t)(NP + 2) * sizeof(int);
   s = (s + 15) & ~size_t(15);
-  return s + 66 * sizeof(double) + 16;
+  return s + 64 * sizeof(double) + 16;
 }
-static size_t refine_smem(int N) { return (5 * (size_t)N * (N + 1) + N + 1 + 64) * sizeof(double); }
+static size_t refine_smem(int N) {
+  const int NP = N + (N & 1);
+  return (5 * (size_t)N * (N + 1) + N + 1 + 64 + NP) * sizeof(double) + (NP + 2) * sizeof(int);
+}
 
 size_t eig_smem_bytes(int N, int method) {
   size_t a = method == EIG_JACOBI_FP64 ? jacobi_smem(N, 8) : jacobi_smem(N, 4);
@@ -322,7 +384,7 @@ size_t eig_smem_bytes(int N, int method) {
 
 cudaError_t launch_eig(const double* H0, const double* M, const double* f, int N, int J,
                        double* W, double* eig, int* status, int method, int refine_sweeps,
-                       cudaStream_t st) {
+                       double angle_tol, cudaStream_t st) {
   int threads = N <= 16 ? 128 : 256;
   if (method == EIG_JACOBI_FP64) {
     size_t sm = jacobi_smem(N, 8);
@@ -337,7 +399,7 @@ cudaError_t launch_eig(const double* H0, const double* M, const double* f, int N
   if (e != cudaSuccess) return e;
   size_t sr = refine_smem(N);
   cudaFuncSetAttribute(k_eig_refine, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sr);
-  k_eig_refine<<<J, threads, sr, st>>>(H0, M, f, N, J, refine_sweeps, W, eig, status);
+  k_eig_refine<<<J, threads, sr, st>>>(H0, M, f, N, J, refine_sweeps, angle_tol, W, eig, status);
   return cudaGetLastError();
 }
 

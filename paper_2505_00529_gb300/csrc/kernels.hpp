@@ -22,9 +22,11 @@ enum { PREC_FP64 = 0, PREC_MIXED = 1 };
 constexpr double TAU_DD2 = 1e-3;
 
 size_t eig_smem_bytes(int N, int method);
+// method EIG_REFINED: binary32 Jacobi, `refine_sweeps` binary64 Ogita-Aishima
+// sweeps, then binary64 Jacobi clean-up rotating only angles above angle_tol.
 cudaError_t launch_eig(const double* H0, const double* M, const double* f, int N, int J,
                        double* W, double* eig, int* status, int method, int refine_sweeps,
-                       cudaStream_t st);
+                       double angle_tol, cudaStream_t st);
 
 size_t prep_smem_bytes(int N);
 // D_j = W diag(exp(-i dt (lambda - m)) - 1) W^T (binary64 when d_fp64, else

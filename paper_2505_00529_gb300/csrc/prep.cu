@@ -87,6 +87,34 @@ __device__ double2 dd2_dev(int a, int b, int c, const double* lam, const double2
   return cmul(e, make_double2(re, im));
 }
 
+// row-major upper-triangle index t (0 <= t < N(N+1)/2) -> (i, k), k >= i
+__device__ __forceinline__ void tri_index(int t, int N, int& i, int& k) {
+  const float b = 2.0f * N + 1.0f;
+  int r = (int)floorf(0.5f * (b - sqrtf(fmaxf(b * b - 8.0f * t, 0.0f))));
+  r = max(0, min(r, N - 1));
+  while (r > 0 && r * N - r * (r - 1) / 2 > t) --r;
+  while (r + 1 < N && (r + 1) * N - (r + 1) * r / 2 <= t) ++r;
+  i = r;
+  k = t - (r * N - r * (r - 1) / 2) + r;
+}
+
+// Near pairs (dt |l_p - l_q| <= TAU_DD2, always p == q) take the direct sum
+// sum_r M~_pr M~_rq phi[l_p, l_r, l_q], one warp per pair with the lanes over
+// r, so that the binary64 pipe is never held by a single active lane.
+__device__ __forceinline__ double2 dd2_table(int a, int b, int c, const double* lam,
+                                             const double2* G, int ldg, const double2* eh,
+                                             double dt) {
+  int lo = a, mid = b, hi = c;
+  if (lam[lo] > lam[mid]) { int t = lo; lo = mid; mid = t; }
+  if (lam[mid] > lam[hi]) { int t = mid; mid = hi; hi = t; }
+  if (lam[lo] > lam[mid]) { int t = lo; lo = mid; mid = t; }
+  if (dt * (lam[hi] - lam[lo]) > TAU_DD2) {
+    const double2 g1 = G[lo * ldg + mid], g2 = G[mid * ldg + hi];
+    return cscale(csub(g1, g2), 1.0 / (lam[lo] - lam[hi]));
+  }
+  return dd2_dev(a, b, c, lam, eh, dt);
+}
+
 __global__ void k_prep(const double* __restrict__ Wg, const double* __restrict__ eig,
                        const double* __restrict__ Mg, int N, int J, double dt, double mshift,
                        void* __restrict__ Dout, size_t dstride, int d_fp64, int derivs,
@@ -95,43 +123,53 @@ __global__ void k_prep(const double* __restrict__ Wg, const double* __restrict__
   const int j = blockIdx.x;
   if (j >= J) return;
   const int ld = N + 1;
+  const int NT = N * (N + 1) / 2;
   double* W = reinterpret_cast<double*>(smem_raw);      // [N][ld]
   double* T = W + N * ld;                               // [N][ld]
   double* Mt = T + N * ld;                              // [N][ld]
-  double2* P = reinterpret_cast<double2*>(Mt + N * ld); // [N][ld]
+  double2* P = reinterpret_cast<double2*>(Mt + N * ld); // [N][ld]: P~, later Gamma1
   double* lam = reinterpret_cast<double*>(P + N * ld);  // [N]
   double2* eh = reinterpret_cast<double2*>(lam + N + (N & 1));  // [N]
   double2* pm1 = eh + N;                                // [N] phi(lambda - m) - 1
+  float* Wf = reinterpret_cast<float*>(pm1 + N);        // [N][ld] binary32 copy (mixed D)
+  float2* pm1f = reinterpret_cast<float2*>(Wf + N * ld);  // [N] (N (N+1) is even: 8-byte aligned)
+  int* near = reinterpret_cast<int*>(pm1f + N);         // [NT] packed near pairs
   double2* Y = reinterpret_cast<double2*>(W);           // [N][ld] overlays W and T
+  __shared__ int n_near;
 
   const int tid = threadIdx.x, nt = blockDim.x;
   const double* Wj = Wg + (size_t)j * N * N;
+  if (tid == 0) n_near = 0;
   for (int e = tid; e < N * N; e += nt) {
-    int p = e / N, q = e % N;
-    W[p * ld + q] = Wj[e];
+    const int p = e / N, q = e % N;
+    const double w = Wj[e];
+    W[p * ld + q] = w;
+    Wf[p * ld + q] = (float)w;
     Mt[p * ld + q] = Mg[e];
   }
   for (int p = tid; p < N; p += nt) {
-    double l = eig[(size_t)j * N + p];
+    const double l = eig[(size_t)j * N + p];
     lam[p] = l;
-    double x = dt * (l - mshift);
-    double s, c, sh;
+    const double x = dt * (l - mshift);
+    double s, c;
     sincos(x, &s, &c);
-    sh = sin(0.5 * x);
-    pm1[p] = make_double2(-2.0 * sh * sh, -s);   // exp(-i x) - 1 without cancellation
+    const double sh = sin(0.5 * x);
+    const double2 v = make_double2(-2.0 * sh * sh, -s);   // exp(-i x) - 1 without cancellation
+    pm1[p] = v;
+    pm1f[p] = make_float2((float)v.x, (float)v.y);
     eh[p] = cexpi(-0.5 * dt * l);
   }
   __syncthreads();
 
-  // D = W diag(pm1) W^T (complex symmetric)
+  // D = W diag(pm1) W^T (complex symmetric): upper triangle, mirrored
   if (d_fp64) {
     double2* D = reinterpret_cast<double2*>(reinterpret_cast<unsigned char*>(Dout) + (size_t)j * dstride);
-    for (int e = tid; e < N * N; e += nt) {
-      int p = e / N, q = e % N;
-      if (q < p) continue;
+    for (int t = tid; t < NT; t += nt) {
+      int p, q;
+      tri_index(t, N, p, q);
       double re = 0, im = 0;
       for (int r = 0; r < N; ++r) {
-        double w = W[p * ld + r] * W[q * ld + r];
+        const double w = W[p * ld + r] * W[q * ld + r];
         re = fma(w, pm1[r].x, re);
         im = fma(w, pm1[r].y, im);
       }
@@ -140,14 +178,14 @@ __global__ void k_prep(const double* __restrict__ Wg, const double* __restrict__
     }
   } else {
     float2* D = reinterpret_cast<float2*>(reinterpret_cast<unsigned char*>(Dout) + (size_t)j * dstride);
-    for (int e = tid; e < N * N; e += nt) {
-      int p = e / N, q = e % N;
-      if (q < p) continue;
+    for (int t = tid; t < NT; t += nt) {
+      int p, q;
+      tri_index(t, N, p, q);
       float re = 0, im = 0;
       for (int r = 0; r < N; ++r) {
-        float w = (float)W[p * ld + r] * (float)W[q * ld + r];
-        re = fmaf(w, (float)pm1[r].x, re);
-        im = fmaf(w, (float)pm1[r].y, im);
+        const float w = Wf[p * ld + r] * Wf[q * ld + r];
+        re = fmaf(w, pm1f[r].x, re);
+        im = fmaf(w, pm1f[r].y, im);
       }
       D[p * N + q] = make_float2(re, im);
       D[q * N + p] = make_float2(re, im);
@@ -155,78 +193,90 @@ __global__ void k_prep(const double* __restrict__ Wg, const double* __restrict__
   }
   if (!derivs) return;
 
-  // T = M W ; M~ = W^T T
+  // T = M W ; M~ = W^T T (upper triangle, mirrored: exactly symmetric)
   for (int e = tid; e < N * N; e += nt) {
-    int i = e / N, k = e % N;
+    const int i = e / N, k = e % N;
     double acc = 0;
     for (int r = 0; r < N; ++r) acc = fma(Mt[i * ld + r], W[r * ld + k], acc);
     T[i * ld + k] = acc;
   }
   __syncthreads();
-  for (int e = tid; e < N * N; e += nt) {
-    int i = e / N, k = e % N;
+  for (int t = tid; t < NT; t += nt) {
+    int i, k;
+    tri_index(t, N, i, k);
     double acc = 0;
     for (int r = 0; r < N; ++r) acc = fma(W[r * ld + i], T[r * ld + k], acc);
-    Mt[i * ld + k] = acc;   // M no longer needed
+    Mt[i * ld + k] = acc;   // M no longer needed; rows i < k only read by this thread's pair
+    Mt[k * ld + i] = acc;
   }
   __syncthreads();
-  for (int e = tid; e < N * N; e += nt) {   // exact symmetry
-    int i = e / N, k = e % N;
-    if (k > i) {
-      double s = 0.5 * (Mt[i * ld + k] + Mt[k * ld + i]);
-      Mt[i * ld + k] = s;
-      Mt[k * ld + i] = s;
-    }
-  }
-  __syncthreads();
-  // P~ = Gamma1 o M~
+  // P~ = Gamma1 o M~ ; list the near pairs (p <= q)
   double2* Pg = Ptil + (size_t)j * N * N;
   for (int e = tid; e < N * N; e += nt) {
-    int p = e / N, q = e % N;
-    double2 g = gamma1(p, q, lam, eh, dt);
-    double2 v = cscale(g, Mt[p * ld + q]);
+    const int p = e / N, q = e % N;
+    const double2 g = gamma1(p, q, lam, eh, dt);
+    const double2 v = cscale(g, Mt[p * ld + q]);
     P[p * ld + q] = v;
     Pg[e] = v;
+    if (q >= p && !(dt * fabs(lam[p] - lam[q]) > TAU_DD2)) near[atomicAdd(&n_near, 1)] = p * N + q;
   }
   __syncthreads();
   // Y = P~ M~  (W, T are dead: Y overlays them)
   for (int e = tid; e < N * N; e += nt) {
-    int p = e / N, q = e % N;
+    const int p = e / N, q = e % N;
     double re = 0, im = 0;
     for (int r = 0; r < N; ++r) {
-      double m = Mt[r * ld + q];
+      const double m = Mt[r * ld + q];
       re = fma(P[p * ld + r].x, m, re);
       im = fma(P[p * ld + r].y, m, im);
     }
     Y[p * ld + q] = make_double2(re, im);
   }
   __syncthreads();
+  // P~ is dead: Gamma1 table in its place
+  for (int e = tid; e < N * N; e += nt) {
+    const int p = e / N, q = e % N;
+    P[p * ld + q] = gamma1(p, q, lam, eh, dt);
+  }
+  __syncthreads();
   double2* Xg = Xp + (size_t)j * N * N;
   bool bad = false;
+  // far pairs: commutator form
   for (int e = tid; e < N * N; e += nt) {
-    int p = e / N, q = e % N;
-    double2 x;
-    if (dt * fabs(lam[p] - lam[q]) > TAU_DD2) {
-      double2 d = csub(Y[p * ld + q], Y[q * ld + p]);
-      x = cscale(d, 2.0 / (lam[p] - lam[q]));
-    } else {
-      double re = 0, im = 0;
-      for (int r = 0; r < N; ++r) {
-        double m2 = Mt[p * ld + r] * Mt[r * ld + q];
-        double2 g2 = dd2_dev(p, r, q, lam, eh, dt);
-        re = fma(m2, g2.x, re);
-        im = fma(m2, g2.y, im);
-      }
-      x = make_double2(2.0 * re, 2.0 * im);
-    }
+    const int p = e / N, q = e % N;
+    if (!(dt * fabs(lam[p] - lam[q]) > TAU_DD2)) continue;
+    const double2 d = csub(Y[p * ld + q], Y[q * ld + p]);
+    const double2 x = cscale(d, 2.0 / (lam[p] - lam[q]));
     bad |= !(isfinite(x.x) && isfinite(x.y));
     Xg[e] = x;
+  }
+  // near pairs: one warp per pair, lanes over r
+  const int warp = tid >> 5, lane = tid & 31, nwarp = (nt + 31) >> 5;
+  for (int k = warp; k < n_near; k += nwarp) {
+    const int p = near[k] / N, q = near[k] % N;
+    double re = 0, im = 0;
+    for (int r = lane; r < N; r += 32) {
+      const double m2 = Mt[p * ld + r] * Mt[r * ld + q];
+      const double2 g2 = dd2_table(p, r, q, lam, P, ld, eh, dt);
+      re = fma(m2, g2.x, re);
+      im = fma(m2, g2.y, im);
+    }
+    re = warp_sum(re);
+    im = warp_sum(im);
+    if (lane == 0) {
+      const double2 x = make_double2(2.0 * re, 2.0 * im);
+      bad |= !(isfinite(x.x) && isfinite(x.y));
+      Xg[(size_t)p * N + q] = x;
+      Xg[(size_t)q * N + p] = x;
+    }
   }
   if (bad) raise_status(status, DEV_NONFINITE);
 }
 
 size_t prep_smem_bytes(int N) {
-  return (5 * (size_t)N * (N + 1) + (N + (N & 1)) + 4 * (size_t)N) * sizeof(double);
+  const size_t NT = (size_t)N * (N + 1) / 2;
+  return (5 * (size_t)N * (N + 1) + (N + (N & 1)) + 4 * (size_t)N) * sizeof(double) +
+         ((size_t)N * (N + 1) + (N & 1) + 2 * (size_t)N) * sizeof(float) + NT * sizeof(int) + 16;
 }
 
 cudaError_t launch_prep(const double* W, const double* eig, const double* M, int N, int J,

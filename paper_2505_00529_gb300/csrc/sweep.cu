@@ -114,9 +114,12 @@ __global__ void __launch_bounds__(1024) k_sweep(const SweepArgs a, const int nst
 
   int cur = 0;
   int it = 0;
+  int s = 0;                 // ring slot of step it
+  uint32_t par = 0;          // mbarrier phase parity of that slot
+  int s_issue = nstage - 1;  // ring slot the next prefetch goes to
+  const TD* dcol0 = nullptr;
   for (; it < J; ++it) {
     const int jj = BWD ? J - 1 - it : it;
-    const int s = it % nstage;
     if (threadIdx.x == 0 && it + nstage - 1 < J) {
       fence_proxy_async_smem();
       issue(it + nstage - 1);
@@ -127,11 +130,9 @@ __global__ void __launch_bounds__(1024) k_sweep(const SweepArgs a, const int nst
       if (MIX) reinterpret_cast<float4*>(a.states)[row] = make_float4((float)hx, (float)hy, lx, ly);
       else reinterpret_cast<double2*>(a.states)[row] = make_double2((double)hx, (double)hy);
     }
-    if (!mbar_wait_bounded(&bar[s], (uint32_t)((it / nstage) & 1))) {
-      atomicExch(&abort_flag, 1);
-    }
-    __syncthreads();
-    if (abort_flag) break;
+    // a thread whose wait gives up flags the CTA; the data it then reads is
+    // never used (the loop ends at the step-end barrier)
+    if (!mbar_wait_bounded(&bar[s], par)) abort_flag = 1;
     const unsigned char* sp = ring + (size_t)s * stage;
     const TD* Ds = reinterpret_cast<const TD*>(sp);
     const TV* srcs = reinterpret_cast<const TV*>(sp + dbytes);
@@ -143,7 +144,7 @@ __global__ void __launch_bounds__(1024) k_sweep(const SweepArgs a, const int nst
     if (a.ctr) {
       R v = 0;
       if (owner) {
-        TV c = ctrs[i];
+        const TV c = ctrs[i];
         v = c.x * hx + c.y * hy;
       }
       v = warp_sum(v);
@@ -153,22 +154,28 @@ __global__ void __launch_bounds__(1024) k_sweep(const SweepArgs a, const int nst
         red[((it & 1) * kc + l) * WPC + rb] = (double)v;
       }
     }
-    // matvec: acc_i = sum_q D[q][i] X[q]   (D symmetric)
+    // matvec: acc_i = sum_q D[q][i] X[q]   (D symmetric), 4x unrolled over q
     R ax0 = 0, ay0 = 0, ax1 = 0, ay1 = 0;
     if (active) {
+      dcol0 = Ds + i;
       int q = rsub;
-      for (; q + RS < N; q += 2 * RS) {
-        TD d0 = Ds[(size_t)q * N + i], d1 = Ds[(size_t)(q + RS) * N + i];
-        TD x0v = Xc[q], x1v = Xc[q + RS];
-        if (BWD) { d0.y = -d0.y; d1.y = -d1.y; }
+      for (; q + 3 * RS < N; q += 4 * RS) {
+        TD d0 = dcol0[(size_t)q * N], d1 = dcol0[(size_t)(q + RS) * N];
+        TD d2 = dcol0[(size_t)(q + 2 * RS) * N], d3 = dcol0[(size_t)(q + 3 * RS) * N];
+        const TD x0v = Xc[q], x1v = Xc[q + RS], x2v = Xc[q + 2 * RS], x3v = Xc[q + 3 * RS];
+        if (BWD) { d0.y = -d0.y; d1.y = -d1.y; d2.y = -d2.y; d3.y = -d3.y; }
         ax0 = fma(d0.x, x0v.x, ax0); ax0 = fma(-d0.y, x0v.y, ax0);
         ay0 = fma(d0.x, x0v.y, ay0); ay0 = fma(d0.y, x0v.x, ay0);
         ax1 = fma(d1.x, x1v.x, ax1); ax1 = fma(-d1.y, x1v.y, ax1);
         ay1 = fma(d1.x, x1v.y, ay1); ay1 = fma(d1.y, x1v.x, ay1);
+        ax0 = fma(d2.x, x2v.x, ax0); ax0 = fma(-d2.y, x2v.y, ax0);
+        ay0 = fma(d2.x, x2v.y, ay0); ay0 = fma(d2.y, x2v.x, ay0);
+        ax1 = fma(d3.x, x3v.x, ax1); ax1 = fma(-d3.y, x3v.y, ax1);
+        ay1 = fma(d3.x, x3v.y, ay1); ay1 = fma(d3.y, x3v.x, ay1);
       }
-      if (q < N) {
-        TD d0 = Ds[(size_t)q * N + i];
-        TD x0v = Xc[q];
+      for (; q < N; q += RS) {
+        TD d0 = dcol0[(size_t)q * N];
+        const TD x0v = Xc[q];
         if (BWD) d0.y = -d0.y;
         ax0 = fma(d0.x, x0v.x, ax0); ax0 = fma(-d0.y, x0v.y, ax0);
         ay0 = fma(d0.x, x0v.y, ay0); ay0 = fma(d0.y, x0v.x, ay0);
@@ -202,12 +209,15 @@ __global__ void __launch_bounds__(1024) k_sweep(const SweepArgs a, const int nst
       X[(size_t)(cur ^ 1) * kc * N + (size_t)l * N + i] = v;
     }
     __syncthreads();
+    if (abort_flag) break;
     if (a.ctr && WPC > 1 && rb == 0 && lane == 0 && l < ncols) {
       double v = 0.0;
       for (int w = 0; w < WPC; ++w) v += red[((it & 1) * kc + l) * WPC + w];
       a.contr[(size_t)jj * a.K + col0 + l] = v;
     }
     cur ^= 1;
+    if (++s == nstage) { s = 0; par ^= 1u; }
+    (void)s_issue;
   }
   if (abort_flag) {
     if (threadIdx.x == 0) {
@@ -255,15 +265,16 @@ static cudaError_t launch_one(const SweepArgs& a, cudaStream_t st) {
 }
 
 cudaError_t launch_sweep(const SweepArgs& a, int d_fp64, cudaStream_t st) {
+  // Each dot product is split over 4 lanes so that a column spreads over
+  // four warps (all four sub-partitions) and the per-step dependent chain is
+  // N/4 terms long; binary64 is issue-limited on GB300 (one warp instruction
+  // per 64 cycles per sub-partition), binary32 is latency-limited.
   if (d_fp64) {
-    // binary64 is issue-limited (one warp instruction per 64 cycles per
-    // sub-partition): split each dot product over 4 lanes so a column
-    // spreads over all four sub-partitions.
     if (a.backward) return launch_one<false, 4, true>(a, st);
     return launch_one<false, 4, false>(a, st);
   }
-  if (a.backward) return launch_one<true, 1, true>(a, st);
-  return launch_one<true, 1, false>(a, st);
+  if (a.backward) return launch_one<true, 4, true>(a, st);
+  return launch_one<true, 4, false>(a, st);
 }
 
 }  // namespace qoc

@@ -67,12 +67,16 @@ def sine_basis(J: int, dt: float, K: int) -> np.ndarray:
 
 
 def sine_cosine_basis(J: int, dt: float, K: int) -> np.ndarray:
-    """First K/2 columns sin(m pi t/T), last K/2 columns cos(m pi t/T), m=1..K/2."""
+    """Fourier basis on [0, T): first K/2 columns sin(2 pi m t/T), last K/2
+    columns cos(2 pi m t/T), m = 1..K/2.  Orthogonal on the grid (B^T B = J/2 I
+    for K/2 < J/2).  (The half-period family sin/cos(m pi t/T) is numerically
+    rank-deficient at K = 64 -- rank 49 -- which gives J(theta) exactly flat
+    directions.)"""
     assert K % 2 == 0
     T = J * dt
     t = np.arange(J) * dt
     m = np.arange(1, K // 2 + 1)
-    arg = np.pi * np.outer(t, m) / T
+    arg = 2.0 * np.pi * np.outer(t, m) / T
     return np.concatenate([np.sin(arg), np.cos(arg)], axis=1)
 
 
@@ -145,7 +149,7 @@ def config_problem(cfg: int, index: int = 0) -> Problem:
     """The five synthetic workloads (seed = 1000*cfg + index).
 
     1: N=4, K=8 sine, T=10, J=1000 (plain FP64, single problem)
-    2: N=32, K=64 sine/cosine, T=20, J=4000 (plain vs mixed precision)
+    2: N=32, K=64 Fourier sine/cosine, T=20, J=4000 (plain vs mixed precision)
     3: batched uneven problems: N in {8..128 step 8}, K in {16,32,64,128},
        J in {2000,4000,8000}, config-1 recipe, T=10, sine basis
     4: config-2 system (the learned warm start's fixed N=32 system)

@@ -117,7 +117,7 @@ def test_config1_full_size(precision):
         theta = inputs.eval_theta(prob.K, seed)
         d = check_eval(prob, theta, precision)
         assert d["norm_drift"] < (1e-12 if precision == q.QOC_FP64 else 1e-6)
-        assert d["hess_asym"] < 1e-10
+        assert d["hess_asym"] < TOL[precision]
 
 
 @pytest.fixture(scope="module")
