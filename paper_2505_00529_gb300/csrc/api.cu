@@ -179,8 +179,8 @@ qoc_status enqueue_eval(qoc_problem* p, const double* theta_dev, int order, doub
     }
   }
   if (p->timing) cudaEventRecord(p->ev[5], st);
-  QOC_TRY(launch_assemble(p->B, p->Kp, p->f, p->g, p->c, p->V, p->U, p->SJ, N, J, K, p->w_f,
-                          p->w_t, p->hess_method == QOC_HESS_SECOND_ORDER_ADJOINT ? 0 : 1,
+  QOC_TRY(launch_assemble(p->B, p->Kp, p->f, p->g, p->c, p->V, p->U, mixed, p->SJ, N, J, K,
+                          p->w_f, p->w_t, p->hess_method == QOC_HESS_SECOND_ORDER_ADJOINT ? 0 : 1,
                           order >= 2, p->work, out_dev, p->hess_raw, p->scal + 2, st));
   if (p->timing) cudaEventRecord(p->ev[6], st);
   return QOC_OK;
@@ -487,11 +487,17 @@ qoc_status qoc_read_buffer(const qoc_problem* p, int which, double* host_out, si
       if (p->last_order < 2 || !need(J)) return QOC_EINVAL;
       return from_cuda(cudaMemcpy(host_out, p->c, 8 * (size_t)J, cudaMemcpyDeviceToHost));
     case QOC_BUF_V:
+    case QOC_BUF_U: {
       if (p->last_order < 2 || !need((size_t)J * K)) return QOC_EINVAL;
-      return from_cuda(cudaMemcpy(host_out, p->V, 8 * (size_t)J * K, cudaMemcpyDeviceToHost));
-    case QOC_BUF_U:
-      if (p->last_order < 2 || !need((size_t)J * K)) return QOC_EINVAL;
-      return from_cuda(cudaMemcpy(host_out, p->U, 8 * (size_t)J * K, cudaMemcpyDeviceToHost));
+      const void* src = which == QOC_BUF_V ? static_cast<const void*>(p->V) : static_cast<const void*>(p->U);
+      if (!mixed)
+        return from_cuda(cudaMemcpy(host_out, src, 8 * (size_t)J * K, cudaMemcpyDeviceToHost));
+      std::vector<float> tmp((size_t)J * K);
+      e = cudaMemcpy(tmp.data(), src, 4 * (size_t)J * K, cudaMemcpyDeviceToHost);
+      if (e != cudaSuccess) return from_cuda(e);
+      for (size_t k = 0; k < tmp.size(); ++k) host_out[k] = (double)tmp[k];
+      return QOC_OK;
+    }
     case QOC_BUF_SJ: {
       if (p->last_order < 2 || !need(2 * (size_t)N * K)) return QOC_EINVAL;
       std::vector<double> raw(2 * (size_t)N * K);

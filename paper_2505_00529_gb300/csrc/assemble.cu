@@ -95,8 +95,9 @@ cudaError_t launch_terminal(const double* f, int J, const void* a_hat, int mixed
 constexpr int HT = 16;
 constexpr int JC = 64;
 
+template <typename TU>
 __global__ void k_hess_partial(const double* __restrict__ B, int Kp, const double* __restrict__ c,
-                               const double* __restrict__ V, const double* __restrict__ U,
+                               const TU* __restrict__ V, const TU* __restrict__ U,
                                const double2* __restrict__ SJ, int N, int J, int K, double w_f,
                                double w_t, int method, int nchunk, double* __restrict__ work) {
   __shared__ double bl[JC][HT + 1], bm[JC][HT + 1], zm[JC][HT + 1], ul[JC][HT + 1];
@@ -117,11 +118,11 @@ __global__ void k_hess_partial(const double* __restrict__ B, int Kp, const doubl
       bm[jj][t] = bmv;
       double zv = cj * bmv;
       if (ok && mm < K) {
-        zv += U[(size_t)j * K + mm];
-        if (method == 0) zv += V[(size_t)j * K + mm];
+        zv += (double)U[(size_t)j * K + mm];
+        if (method == 0) zv += (double)V[(size_t)j * K + mm];
       }
       zm[jj][t] = zv;
-      ul[jj][t] = (ok && ll < K && method == 1) ? U[(size_t)j * K + ll] : 0.0;
+      ul[jj][t] = (ok && ll < K && method == 1) ? (double)U[(size_t)j * K + ll] : 0.0;
     }
     __syncthreads();
     for (int jj = 0; jj < j1 - j0; ++jj) {
@@ -193,18 +194,24 @@ size_t assemble_work_doubles(int J, int K) {
 }
 
 cudaError_t launch_assemble(const double* B, int Kp, const double* f, const double* g,
-                            const double* c, const double* V, const double* U, const double2* SJ,
-                            int N, int J, int K, double w_f, double w_t, int method, int want_hess,
-                            double* work, double* out, double* hess_raw, double* asym,
-                            cudaStream_t st) {
+                            const double* c, const void* V, const void* U, int uv_f32,
+                            const double2* SJ, int N, int J, int K, double w_f, double w_t,
+                            int method, int want_hess, double* work, double* out,
+                            double* hess_raw, double* asym, cudaStream_t st) {
   k_grad<<<K, 256, 0, st>>>(B, Kp, f, g, J, K, w_f, out);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess || !want_hess) return e;
   const int nchunk = (J + JC - 1) / JC;
   const int nz = nchunk + (method == 1 ? 1 : 0);
   dim3 grid((K + HT - 1) / HT, (K + HT - 1) / HT, nz);
-  k_hess_partial<<<grid, HT * HT, 0, st>>>(B, Kp, c, V, U, SJ, N, J, K, w_f, w_t, method, nchunk,
-                                           work);
+  if (uv_f32)
+    k_hess_partial<float><<<grid, HT * HT, 0, st>>>(B, Kp, c, static_cast<const float*>(V),
+                                                    static_cast<const float*>(U), SJ, N, J, K, w_f,
+                                                    w_t, method, nchunk, work);
+  else
+    k_hess_partial<double><<<grid, HT * HT, 0, st>>>(B, Kp, c, static_cast<const double*>(V),
+                                                     static_cast<const double*>(U), SJ, N, J, K, w_f,
+                                                     w_t, method, nchunk, work);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   k_hess_final<<<1, 1024, 0, st>>>(work, nz, K, out, hess_raw, asym);

@@ -51,7 +51,7 @@ struct SweepArgs {
   double init_scale;
   double2* final_out;    // [K][N] final state (may be null)
   void* states;          // (J+1) x N states of column 0 (double2, or float4 hi/lo pairs), or null
-  double* contr;         // J x K contraction output (u or v), or null
+  void* contr;           // J x K contraction output (u or v): double, or float when mixed; or null
   int* status;
 };
 cudaError_t launch_sweep(const SweepArgs& a, int d_fp64, cudaStream_t st);
@@ -71,11 +71,12 @@ cudaError_t launch_terminal(const double* f, int J, const void* a_hat, int mixed
                             const double2* beta, int N, double2 phaseJ, double w_f, double w_t,
                             double2* lamJ, double* cost_out, double* drift_out, cudaStream_t st);
 // grad = B^T (2 w_f f + g); Hess (see qoc.h) into out = [J, grad, Hess], raw Hessian, asymmetry
+// V, U: J x K contractions, double (uv_f32 = 0) or float (uv_f32 = 1)
 cudaError_t launch_assemble(const double* B, int Kp, const double* f, const double* g,
-                            const double* c, const double* V, const double* U, const double2* SJ,
-                            int N, int J, int K, double w_f, double w_t, int method, int want_hess,
-                            double* work, double* out, double* hess_raw, double* asym,
-                            cudaStream_t st);
+                            const double* c, const void* V, const void* U, int uv_f32,
+                            const double2* SJ, int N, int J, int K, double w_f, double w_t,
+                            int method, int want_hess, double* work, double* out,
+                            double* hess_raw, double* asym, cudaStream_t st);
 size_t assemble_work_doubles(int J, int K);
 
 // trust-region subproblem on the device (K x K, binary64); work holds

@@ -63,8 +63,8 @@ __global__ void __launch_bounds__(1024) k_sweep(const SweepArgs a, const int nst
   const uint32_t stage = dbytes + sbytes + cbytes + bbytes;
   unsigned char* ring = smem;
   TD* X = reinterpret_cast<TD*>(ring + (size_t)nstage * stage);      // [2][kc][N] (hi part)
-  double* red = reinterpret_cast<double*>(X + 2 * kc * N);            // [2][kc][WPC]
-  uint64_t* bar = reinterpret_cast<uint64_t*>(red + 2 * kc * WPC + 1);
+  R* red = reinterpret_cast<R*>(X + 2 * kc * N);                      // [2][kc][WPC]
+  uint64_t* bar = reinterpret_cast<uint64_t*>(red + 2 * kc * WPC + 2);
   bar = reinterpret_cast<uint64_t*>((reinterpret_cast<uintptr_t>(bar) + 7) & ~uintptr_t(7));
   __shared__ int abort_flag;
 
@@ -149,9 +149,9 @@ __global__ void __launch_bounds__(1024) k_sweep(const SweepArgs a, const int nst
       }
       v = warp_sum(v);
       if (WPC == 1) {
-        if (lane == 0 && l < ncols) a.contr[(size_t)jj * a.K + col0 + l] = (double)v;
+        if (lane == 0 && l < ncols) reinterpret_cast<R*>(a.contr)[(size_t)jj * a.K + col0 + l] = v;
       } else if (lane == 0 && l < ncols) {
-        red[((it & 1) * kc + l) * WPC + rb] = (double)v;
+        red[((it & 1) * kc + l) * WPC + rb] = v;
       }
     }
     // matvec: acc_i = sum_q D[q][i] X[q]   (D symmetric), 4x unrolled over q
@@ -211,9 +211,9 @@ __global__ void __launch_bounds__(1024) k_sweep(const SweepArgs a, const int nst
     __syncthreads();
     if (abort_flag) break;
     if (a.ctr && WPC > 1 && rb == 0 && lane == 0 && l < ncols) {
-      double v = 0.0;
+      R v = 0;
       for (int w = 0; w < WPC; ++w) v += red[((it & 1) * kc + l) * WPC + w];
-      a.contr[(size_t)jj * a.K + col0 + l] = v;
+      reinterpret_cast<R*>(a.contr)[(size_t)jj * a.K + col0 + l] = v;
     }
     cur ^= 1;
     if (++s == nstage) { s = 0; par ^= 1u; }
@@ -252,7 +252,7 @@ static cudaError_t launch_one(const SweepArgs& a, cudaStream_t st) {
   const uint32_t vb = (uint32_t)(sizeof(TV) * a.N + 15) / 16 * 16;
   const uint32_t stage = (uint32_t)a.dstride + (a.src ? vb : 0u) + (a.ctr ? vb : 0u) +
                          (a.Brow ? (uint32_t)(sizeof(TB) * a.Kp) : 0u);
-  const size_t fixed = 2 * (size_t)a.kc * a.N * sizeof(TD) + (2 * (size_t)a.kc * WPC + 1) * 8 + 8;
+  const size_t fixed = 2 * (size_t)a.kc * a.N * sizeof(TD) + (2 * (size_t)a.kc * WPC + 2) * 8 + 8;
   const size_t budget = 200 * 1024;
   int ns = 8;
   while (ns > 2 && (size_t)ns * stage + fixed + 8 * ns > budget) --ns;
