@@ -100,6 +100,15 @@ qoc_status qoc_create_problem(int N, const double* H0, const double* M,
 qoc_status qoc_set_hess_method(qoc_problem* p, int method);
 qoc_status qoc_set_eig_method(qoc_problem* p, int method);
 
+/* Time blocking of the sequential sweeps (no counterpart in the paper; an
+ * exact regrouping of Alg. 2's loops): `steps` consecutive time steps are
+ * folded into one dependent step X <- (I + Delta) X + Q B_blk, with the
+ * block propagators, propagated sources and the contractions at the
+ * intermediate steps computed in parallel over blocks.  1 <= steps <= 8;
+ * 1 selects one dependent step per time step.  Default 8 when J >= 16, else 1.
+ * QOC_EINVAL otherwise. */
+qoc_status qoc_set_block_steps(qoc_problem* p, int steps);
+
 /* J(theta), Eq. discretecost.  theta: K host doubles.  J: one host double. */
 qoc_status qoc_eval_J(qoc_problem* p, const double* theta, double* J);
 

@@ -22,7 +22,8 @@ QOC_EIG_REFINED, QOC_EIG_JACOBI_FP64 = 0, 1
 
 # every entry point declared in include/qoc.h
 EXPORTS = [
-    "qoc_create_problem", "qoc_set_hess_method", "qoc_set_eig_method", "qoc_eval_J",
+    "qoc_create_problem", "qoc_set_hess_method", "qoc_set_eig_method", "qoc_set_block_steps",
+    "qoc_eval_J",
     "qoc_eval_grad", "qoc_eval_grad_hess", "qoc_eval_grad_hess_dev", "qoc_sync_status",
     "qoc_trust_region_solve", "qoc_get_diagnostics", "qoc_enable_timing", "qoc_read_buffer",
     "qoc_device_bytes", "qoc_max_basis_size", "qoc_destroy_problem", "qoc_status_string",
@@ -68,6 +69,7 @@ def lib() -> C.CDLL:
                                          C.POINTER(C.c_void_p)]
         L.qoc_set_hess_method.argtypes = [C.c_void_p, C.c_int]
         L.qoc_set_eig_method.argtypes = [C.c_void_p, C.c_int]
+        L.qoc_set_block_steps.argtypes = [C.c_void_p, C.c_int]
         L.qoc_eval_J.argtypes = [C.c_void_p, _dp, _dp]
         L.qoc_eval_grad.argtypes = [C.c_void_p, _dp, _dp, _dp]
         L.qoc_eval_grad_hess.argtypes = [C.c_void_p, _dp, _dp, _dp, _dp]
@@ -140,6 +142,10 @@ def qoc_set_hess_method(h, method):
 
 def qoc_set_eig_method(h, method):
     _check(lib().qoc_set_eig_method(C.c_void_p(h), int(method)), "qoc_set_eig_method")
+
+
+def qoc_set_block_steps(h, steps):
+    _check(lib().qoc_set_block_steps(C.c_void_p(h), int(steps)), "qoc_set_block_steps")
 
 
 def qoc_enable_timing(h, on=True):
@@ -233,7 +239,8 @@ class Problem:
     """Owns one qoc_problem built from a problem description with fields
     H0, M, alpha, beta, B, dt, w_f, w_t (e.g. ``inputs.Problem``)."""
 
-    def __init__(self, prob, precision=QOC_FP64, cuda_stream=None, hess_method=None, eig_method=None):
+    def __init__(self, prob, precision=QOC_FP64, cuda_stream=None, hess_method=None, eig_method=None,
+                 block_steps=None):
         self.N, self.K, self.J = prob.H0.shape[0], prob.B.shape[1], prob.B.shape[0]
         self.handle = qoc_create_problem(self.N, prob.H0, prob.M, prob.alpha, prob.beta, self.K,
                                          prob.B, prob.dt, self.J, prob.w_f, prob.w_t, precision,
@@ -242,6 +249,8 @@ class Problem:
             qoc_set_hess_method(self.handle, hess_method)
         if eig_method is not None:
             qoc_set_eig_method(self.handle, eig_method)
+        if block_steps is not None:
+            qoc_set_block_steps(self.handle, block_steps)
 
     def eval_J(self, theta):
         return qoc_eval_J(self.handle, theta)

@@ -40,6 +40,9 @@ struct qoc_problem {
   double angle_tol = 1e-13;
   cudaStream_t stream = nullptr;
   bool own_stream = false;
+  cudaStream_t side = nullptr;          // high-priority stream: the latency-bound chains run here
+                                        // while the binary64 derivative preparation fills the GPU
+  cudaEvent_t fork = nullptr, join = nullptr;
   int timing = 0;
   cudaEvent_t ev[8] = {};
   double phase_ms[6] = {0, 0, 0, 0, 0, 0};
@@ -58,6 +61,11 @@ struct qoc_problem {
   void *D = nullptr, *a_hat = nullptr, *l_hat = nullptr, *p_hat = nullptr, *y_hat = nullptr;
   int* status = nullptr;
   double *trwork = nullptr, *trstep = nullptr, *trinfo = nullptr, *trzero = nullptr;
+  // time blocking (bs steps per block; bs == 1: per-step sweeps)
+  int bs = 8, nblk = 0;
+  size_t mstride = 0, qstride = 0, gstride = 0;
+  void *Mf = nullptr, *Mb = nullptr, *Qf = nullptr, *Wf = nullptr, *Gf = nullptr, *Qb = nullptr,
+       *Wb = nullptr, *Gb = nullptr, *Xa = nullptr, *Xl = nullptr, *XS = nullptr, *Xmu = nullptr;
   // pinned host staging
   double* hbuf = nullptr;
   size_t hbuf_len = 0;
@@ -125,6 +133,85 @@ qoc_status device_status(qoc_problem* p) {
   return QOC_ENUMERIC;
 }
 
+// The time-blocked evaluation (see block.cu): everything after the spectral
+// preparation, with the sequential sweeps taking J / bs dependent steps.
+qoc_status enqueue_blocked(qoc_problem* p, int order, double* out_dev) {
+  cudaStream_t st = p->stream;
+  const int N = p->N, K = p->K, J = p->J, bs = p->bs;
+  const int mixed = p->precision == QOC_MIXED_FP32 ? 1 : 0;
+  // The chains (latency-bound, one CTA each) run on a high-priority stream
+  // while the binary64 derivative preparation (M~, Gamma1 o M~, X'; needed
+  // only from the pointwise step on) fills the GPU on the main stream.
+  cudaStream_t cs = st;
+  if (order >= 1) {
+    cs = p->side;
+    QOC_TRY(cudaEventRecord(p->fork, st));
+    QOC_TRY(cudaStreamWaitEvent(cs, p->fork, 0));
+  }
+  QOC_TRY(launch_block_delta(p->D, p->dstride, N, J, bs, 0, mixed, p->Mf, p->mstride, cs));
+  if (order >= 1)
+    QOC_TRY(launch_block_delta(p->D, p->dstride, N, J, bs, 1, mixed, p->Mb, p->mstride, cs));
+  BSweepArgs a{};
+  a.N = N; a.K = 1; a.Kp = p->Kp; a.J = J; a.bs = bs; a.kc = 1; a.backward = 0;
+  a.M = reinterpret_cast<const unsigned char*>(p->Mf); a.mstride = p->mstride;
+  a.init = p->alpha; a.init_scale = 1.0; a.Xblk = p->Xa; a.xblk_pairs = mixed;
+  a.states = p->a_hat; a.status = p->status;
+  QOC_TRY(launch_bsweep(a, mixed, cs));
+  QOC_TRY(launch_block_fill(p->D, p->dstride, N, J, bs, 0, mixed, p->Xa, p->a_hat, cs));
+  const double thetaJ = (double)J * p->dt * p->mshift;
+  QOC_TRY(launch_terminal(p->f, J, p->a_hat, mixed, p->beta, N, cexpi_h(thetaJ), p->w_f, p->w_t,
+                          p->lamJ, p->scal + 0, p->scal + 1, cs));
+  QOC_TRY(cudaMemcpyAsync(out_dev, p->scal, sizeof(double), cudaMemcpyDeviceToDevice, cs));
+  if (order == 0) {
+    if (p->timing) for (int k = 3; k < 7; ++k) cudaEventRecord(p->ev[k], st);
+    return QOC_OK;
+  }
+  BSweepArgs l = a;
+  l.backward = 1; l.M = reinterpret_cast<const unsigned char*>(p->Mb);
+  l.init = p->lamJ; l.Xblk = p->Xl; l.states = p->l_hat;
+  QOC_TRY(launch_bsweep(l, mixed, cs));
+  QOC_TRY(launch_block_fill(p->D, p->dstride, N, J, bs, 1, mixed, p->Xl, p->l_hat, cs));
+  QOC_TRY(cudaEventRecord(p->join, cs));
+  QOC_TRY(launch_prep(p->W, p->eig, p->M, N, J, p->dt, p->mshift, p->D, p->dstride, mixed ? 0 : 1,
+                      2, p->Ptil, p->Xp, p->status, st));
+  QOC_TRY(cudaStreamWaitEvent(st, p->join, 0));
+  if (p->timing) cudaEventRecord(p->ev[3], st);
+  const double2 kappa = cexpi_h(p->dt * p->mshift);
+  QOC_TRY(launch_pointwise(p->W, p->Ptil, p->Xp, p->a_hat, p->l_hat, mixed, N, J, kappa, p->p_hat,
+                           p->y_hat, p->g, p->c, order >= 2, st));
+  if (p->timing) cudaEventRecord(p->ev[4], st);
+  if (order >= 2) {
+    const void* Bsrc = mixed ? static_cast<const void*>(p->Bf) : static_cast<const void*>(p->B);
+    QOC_TRY(launch_block_src(p->D, p->dstride, N, J, bs, 0, mixed, p->p_hat, p->y_hat, p->vstride,
+                             p->Qf, p->Wf, p->Gf, p->qstride, p->gstride, st));
+    BSweepArgs s{};
+    s.N = N; s.K = K; s.Kp = p->Kp; s.J = J; s.bs = bs; s.kc = sweep_kc(p); s.backward = 0;
+    s.M = reinterpret_cast<const unsigned char*>(p->Mf); s.mstride = p->mstride;
+    s.Q = reinterpret_cast<const unsigned char*>(p->Qf); s.qstride = p->qstride; s.Brow = Bsrc;
+    s.final_out = p->SJ; s.Xblk = p->XS; s.xblk_pairs = 0; s.status = p->status;
+    QOC_TRY(launch_bsweep(s, mixed, st));
+    QOC_TRY(launch_block_contract(p->XS, p->Wf, p->Gf, p->qstride, p->gstride, Bsrc, p->Kp, N, K, J,
+                                  bs, 0, mixed, p->U, st));
+    if (p->hess_method == QOC_HESS_SECOND_ORDER_ADJOINT) {
+      QOC_TRY(launch_block_src(p->D, p->dstride, N, J, bs, 1, mixed, p->y_hat, p->p_hat, p->vstride,
+                               p->Qb, p->Wb, p->Gb, p->qstride, p->gstride, st));
+      BSweepArgs m = s;
+      m.backward = 1; m.M = reinterpret_cast<const unsigned char*>(p->Mb);
+      m.Q = reinterpret_cast<const unsigned char*>(p->Qb);
+      m.init = p->SJ; m.init_scale = 2.0 * p->w_t; m.final_out = nullptr; m.Xblk = p->Xmu;
+      QOC_TRY(launch_bsweep(m, mixed, st));
+      QOC_TRY(launch_block_contract(p->Xmu, p->Wb, p->Gb, p->qstride, p->gstride, Bsrc, p->Kp, N, K,
+                                    J, bs, 1, mixed, p->V, st));
+    }
+  }
+  if (p->timing) cudaEventRecord(p->ev[5], st);
+  QOC_TRY(launch_assemble(p->B, p->Kp, p->f, p->g, p->c, p->V, p->U, mixed, p->SJ, N, J, K,
+                          p->w_f, p->w_t, p->hess_method == QOC_HESS_SECOND_ORDER_ADJOINT ? 0 : 1,
+                          order >= 2, p->work, out_dev, p->hess_raw, p->scal + 2, st));
+  if (p->timing) cudaEventRecord(p->ev[6], st);
+  return QOC_OK;
+}
+
 // Enqueue one evaluation.  order 0: J; 1: J + grad; 2: J + grad + Hess.
 // theta_dev: K doubles on the device.  out_dev: 1 + K (+ K*K) doubles.
 qoc_status enqueue_eval(qoc_problem* p, const double* theta_dev, int order, double* out_dev) {
@@ -138,10 +225,14 @@ qoc_status enqueue_eval(qoc_problem* p, const double* theta_dev, int order, doub
                      p->eig_method == QOC_EIG_JACOBI_FP64 ? EIG_JACOBI_FP64 : EIG_REFINED,
                      p->refine_sweeps, p->angle_tol, st));
   if (p->timing) cudaEventRecord(p->ev[1], st);
-  QOC_TRY(launch_prep(p->W, p->eig, p->M, N, J, p->dt, p->mshift, p->D, p->dstride, d_fp64,
-                      order >= 1, p->Ptil, p->Xp, p->status, st));
+  QOC_TRY(launch_prep(p->W, p->eig, p->M, N, J, p->dt, p->mshift, p->D, p->dstride, d_fp64, 1,
+                      p->Ptil, p->Xp, p->status, st));
   if (p->timing) cudaEventRecord(p->ev[2], st);
+  if (p->bs > 1) return enqueue_blocked(p, order, out_dev);
 
+  if (order >= 1)
+    QOC_TRY(launch_prep(p->W, p->eig, p->M, N, J, p->dt, p->mshift, p->D, p->dstride, d_fp64, 2,
+                        p->Ptil, p->Xp, p->status, st));
   SweepArgs a{};
   a.N = N; a.K = 1; a.Kp = p->Kp; a.J = J; a.kc = 1; a.backward = 0;
   a.D = reinterpret_cast<const unsigned char*>(p->D); a.dstride = p->dstride;
@@ -256,6 +347,12 @@ void qoc_destroy_problem(qoc_problem* p) {
   if (p->hstatus) cudaFreeHost(p->hstatus);
   for (auto& e : p->ev)
     if (e) cudaEventDestroy(e);
+  if (p->side) {
+    cudaStreamSynchronize(p->side);
+    cudaStreamDestroy(p->side);
+  }
+  if (p->fork) cudaEventDestroy(p->fork);
+  if (p->join) cudaEventDestroy(p->join);
   if (p->own_stream && p->stream) cudaStreamDestroy(p->stream);
   delete p;
 }
@@ -310,6 +407,13 @@ qoc_status qoc_create_problem(int N, const double* H0, const double* M, const do
   }
   for (auto& ev : p->ev)
     if ((e = cudaEventCreate(&ev)) != cudaSuccess) return fail(e);
+  {
+    int lo = 0, hi = 0;
+    cudaDeviceGetStreamPriorityRange(&lo, &hi);
+    if ((e = cudaStreamCreateWithPriority(&p->side, cudaStreamNonBlocking, hi)) != cudaSuccess) return fail(e);
+  }
+  if ((e = cudaEventCreateWithFlags(&p->fork, cudaEventDisableTiming)) != cudaSuccess) return fail(e);
+  if ((e = cudaEventCreateWithFlags(&p->join, cudaEventDisableTiming)) != cudaSuccess) return fail(e);
 #define ALLOC(ptr, bytes) \
   if ((e = dalloc(p, &(ptr), (bytes))) != cudaSuccess) return fail(e)
   ALLOC(p->H0, 8 * NN);
@@ -342,6 +446,31 @@ qoc_status qoc_create_problem(int N, const double* H0, const double* M, const do
   ALLOC(p->p_hat, (size_t)J * p->vstride);
   ALLOC(p->y_hat, (size_t)J * p->vstride);
   ALLOC(p->status, sizeof(int));
+  // block size: binary32 rounding of the block increment grows ~ sqrt(bs), so
+  // the mixed path keeps 4 (Hessian error ~5e-7 on the N=32 workload, 8e-7 at 8)
+  p->bs = J >= 16 ? (mixed ? 4 : 8) : 1;
+  p->nblk = (J + p->bs - 1) / p->bs;
+  {
+    const size_t cs = mixed ? 8 : 16;
+    // per-block buffers sized for the smallest blocked size (2 steps) and
+    // the largest (8 sources per block)
+    p->mstride = (cs * NN + 15) / 16 * 16;
+    p->qstride = (cs * 8 * (size_t)N + 15) / 16 * 16;
+    p->gstride = (cs * 64 + 15) / 16 * 16;
+    const size_t nbp = ((size_t)J + 1) / 2 + 1;
+    ALLOC(p->Mf, nbp * p->mstride);
+    ALLOC(p->Mb, nbp * p->mstride);
+    ALLOC(p->Qf, nbp * p->qstride);
+    ALLOC(p->Wf, nbp * p->qstride);
+    ALLOC(p->Gf, nbp * p->gstride);
+    ALLOC(p->Qb, nbp * p->qstride);
+    ALLOC(p->Wb, nbp * p->qstride);
+    ALLOC(p->Gb, nbp * p->gstride);
+    ALLOC(p->Xa, 16 * nbp * N);
+    ALLOC(p->Xl, 16 * nbp * N);
+    ALLOC(p->XS, cs * nbp * (size_t)K * N);
+    ALLOC(p->Xmu, cs * nbp * (size_t)K * N);
+  }
   if (K <= kMaxKTR) {
     ALLOC(p->trwork, 8 * tr_work_doubles(K));
     ALLOC(p->trstep, 8 * (size_t)K);
@@ -384,6 +513,13 @@ qoc_status qoc_set_hess_method(qoc_problem* p, int method) {
 qoc_status qoc_set_eig_method(qoc_problem* p, int method) {
   if (!p || (method != QOC_EIG_REFINED && method != QOC_EIG_JACOBI_FP64)) return QOC_EINVAL;
   p->eig_method = method;
+  return QOC_OK;
+}
+
+qoc_status qoc_set_block_steps(qoc_problem* p, int steps) {
+  if (!p || steps < 1 || steps > 8 || (steps > 1 && p->J < steps)) return QOC_EINVAL;
+  p->bs = steps;
+  p->nblk = (p->J + steps - 1) / steps;
   return QOC_OK;
 }
 

@@ -385,16 +385,18 @@ size_t eig_smem_bytes(int N, int method) {
 cudaError_t launch_eig(const double* H0, const double* M, const double* f, int N, int J,
                        double* W, double* eig, int* status, int method, int refine_sweeps,
                        double angle_tol, cudaStream_t st) {
-  int threads = N <= 16 ? 128 : 256;
+  // Jacobi rounds are barrier-bound: few warps per (small) matrix, many CTAs per SM
+  const int jthreads = N <= 32 ? 64 : (N <= 64 ? 128 : 256);
+  const int threads = N <= 16 ? 128 : 256;   // refinement: binary64-throughput bound
   if (method == EIG_JACOBI_FP64) {
     size_t sm = jacobi_smem(N, 8);
     cudaFuncSetAttribute(k_eig_jacobi<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    k_eig_jacobi<double><<<J, threads, sm, st>>>(H0, M, f, N, J, W, eig, status);
+    k_eig_jacobi<double><<<J, jthreads, sm, st>>>(H0, M, f, N, J, W, eig, status);
     return cudaGetLastError();
   }
   size_t sm = jacobi_smem(N, 4);
   cudaFuncSetAttribute(k_eig_jacobi<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-  k_eig_jacobi<float><<<J, threads, sm, st>>>(H0, M, f, N, J, W, eig, status);
+  k_eig_jacobi<float><<<J, jthreads, sm, st>>>(H0, M, f, N, J, W, eig, status);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   size_t sr = refine_smem(N);

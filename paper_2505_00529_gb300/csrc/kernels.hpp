@@ -29,12 +29,12 @@ cudaError_t launch_eig(const double* H0, const double* M, const double* f, int N
                        double angle_tol, cudaStream_t st);
 
 size_t prep_smem_bytes(int N);
-// D_j = W diag(exp(-i dt (lambda - m)) - 1) W^T (binary64 when d_fp64, else
-// binary32) at byte stride dstride; with derivs also P~_j = Gamma1 o M~_j and
-// X'_j = 2 sum_r M~_pr M~_rq phi[l_p, l_r, l_q].
+// parts (bit mask): 1 -> D_j = W diag(exp(-i dt (lambda - m)) - 1) W^T
+// (binary64 when d_fp64, else binary32) at byte stride dstride;
+// 2 -> P~_j = Gamma1 o M~_j and X'_j = 2 sum_r M~_pr M~_rq phi[l_p, l_r, l_q].
 cudaError_t launch_prep(const double* W, const double* eig, const double* M, int N, int J,
                         double dt, double mshift, void* D, size_t dstride, int d_fp64,
-                        int derivs, double2* Ptil, double2* Xp, int* status, cudaStream_t st);
+                        int parts, double2* Ptil, double2* Xp, int* status, cudaStream_t st);
 
 struct SweepArgs {
   int N, K, Kp, J;       // Kp: row stride of the basis copy (multiple of 4)
@@ -55,6 +55,37 @@ struct SweepArgs {
   int* status;
 };
 cudaError_t launch_sweep(const SweepArgs& a, int d_fp64, cudaStream_t st);
+
+// ---- time blocking (block.cu, blocked sweep in sweep.cu) ----
+struct BSweepArgs {
+  int N, K, Kp, J;
+  int bs;                // time steps per block
+  int kc;                // columns per CTA
+  int backward;          // sweep order: j descending (B rows of a block reversed)
+  const unsigned char* M;   // per block [N][N] (M[q][i] = Delta[i][q]), stride mstride bytes
+  size_t mstride;
+  const unsigned char* Q;   // per block [bs][N] propagated sources, stride qstride bytes (or null)
+  size_t qstride;
+  const void* Brow;      // J x Kp basis rows (double, or float when mixed), or null
+  const double2* init;   // [K][N] initial state or null
+  double init_scale;
+  double2* final_out;    // [K][N] final state or null
+  void* Xblk;            // [nblk][K][N] block-start states (C, or float4 pairs when xblk_pairs)
+  int xblk_pairs;
+  void* states;          // vector chains: final state row (J forward, 0 backward), or null
+  int* status;
+};
+cudaError_t launch_bsweep(const BSweepArgs& a, int mixed, cudaStream_t st);
+cudaError_t launch_block_delta(const void* D, size_t dstride, int N, int J, int bsteps, int bwd,
+                               int mixed, void* M, size_t mstride, cudaStream_t st);
+cudaError_t launch_block_src(const void* D, size_t dstride, int N, int J, int bsteps, int bwd,
+                             int mixed, const void* src, const void* ctr, size_t vstride, void* Q,
+                             void* W, void* G, size_t qstride, size_t gstride, cudaStream_t st);
+cudaError_t launch_block_contract(const void* Xblk, const void* W, const void* G, size_t qstride,
+                                  size_t gstride, const void* Brow, int Kp, int N, int K, int J,
+                                  int bsteps, int bwd, int mixed, void* contr, cudaStream_t st);
+cudaError_t launch_block_fill(const void* D, size_t dstride, int N, int J, int bsteps, int bwd,
+                              int mixed, const void* Xblk, void* states, cudaStream_t st);
 
 // p^_j, y^_j, g_j, c_j for all steps from the stored states/costates
 // states / costates as written by the vector chains (double2, or float4 pairs

@@ -162,7 +162,9 @@ __global__ void k_prep(const double* __restrict__ Wg, const double* __restrict__
   __syncthreads();
 
   // D = W diag(pm1) W^T (complex symmetric): upper triangle, mirrored
-  if (d_fp64) {
+  if (!(derivs & 1)) {
+    // derivative-only launch: D is produced by a concurrent launch
+  } else if (d_fp64) {
     double2* D = reinterpret_cast<double2*>(reinterpret_cast<unsigned char*>(Dout) + (size_t)j * dstride);
     for (int t = tid; t < NT; t += nt) {
       int p, q;
@@ -191,7 +193,7 @@ __global__ void k_prep(const double* __restrict__ Wg, const double* __restrict__
       D[q * N + p] = make_float2(re, im);
     }
   }
-  if (!derivs) return;
+  if (!(derivs & 2)) return;
 
   // T = M W ; M~ = W^T T (upper triangle, mirrored: exactly symmetric)
   for (int e = tid; e < N * N; e += nt) {
@@ -281,11 +283,11 @@ size_t prep_smem_bytes(int N) {
 
 cudaError_t launch_prep(const double* W, const double* eig, const double* M, int N, int J,
                         double dt, double mshift, void* D, size_t dstride, int d_fp64,
-                        int derivs, double2* Ptil, double2* Xp, int* status, cudaStream_t st) {
+                        int parts, double2* Ptil, double2* Xp, int* status, cudaStream_t st) {
   size_t sm = prep_smem_bytes(N);
   cudaFuncSetAttribute(k_prep, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   int threads = N <= 8 ? 64 : (N <= 16 ? 128 : 256);
-  k_prep<<<J, threads, sm, st>>>(W, eig, M, N, J, dt, mshift, D, dstride, d_fp64, derivs, Ptil,
+  k_prep<<<J, threads, sm, st>>>(W, eig, M, N, J, dt, mshift, D, dstride, d_fp64, parts, Ptil,
                                  Xp, status);
   return cudaGetLastError();
 }

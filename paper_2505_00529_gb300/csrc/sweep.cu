@@ -278,3 +278,213 @@ cudaError_t launch_sweep(const SweepArgs& a, int d_fp64, cudaStream_t st) {
 }
 
 }  // namespace qoc
+
+namespace qoc {
+
+// ---------------------------------------------------------------------------
+// Blocked sweep: one dependent step per block of bs time steps (see block.cu):
+//   X <- X + Delta X + Q B_blk,   Delta applied as y_i = sum_q M[q][i] x_q,
+// block-start states stored for the contractions (panels) or the
+// intermediate-state fill (vector chains).  Per block, M (N x N), Q (bs
+// columns) and the bs rows of B are staged by bulk copies into the ring.
+// ---------------------------------------------------------------------------
+template <bool MIX, int RS>
+__global__ void __launch_bounds__(1024) k_bsweep(const BSweepArgs a, const int nstage) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  using TD = typename SweepT<MIX>::D;
+  using TB = typename SweepT<MIX>::B;
+  using R = typename SweepT<MIX>::R;
+  const int N = a.N, kc = a.kc, J = a.J, bs = a.bs;
+  const int nblk = (J + bs - 1) / bs;
+  constexpr int RPW = 32 / RS;
+  const int WPC = (N + RPW - 1) / RPW;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int l = warp / WPC, rb = warp % WPC;
+  const int rsub = lane % RS;
+  const int i = rb * RPW + lane / RS;
+  const int col0 = blockIdx.x * kc;
+  const int ncols = min(kc, a.K - col0);
+  const bool active = (l < ncols) && (i < N);
+  const bool owner = active && rsub == 0;
+
+  const uint32_t mbytes = (uint32_t)a.mstride;
+  const uint32_t qbytes = a.Q ? (uint32_t)a.qstride : 0u;
+  const uint32_t browb = (uint32_t)(sizeof(TB) * a.Kp);
+  const uint32_t bmax = a.Brow ? browb * bs : 0u;
+  const uint32_t stage = mbytes + qbytes + bmax;
+  unsigned char* ring = smem;
+  TD* X = reinterpret_cast<TD*>(ring + (size_t)nstage * stage);      // [2][kc][N]
+  uint64_t* bar = reinterpret_cast<uint64_t*>(X + 2 * kc * N);
+  __shared__ int abort_flag;
+
+  const unsigned char* gB = reinterpret_cast<const unsigned char*>(a.Brow);
+  auto issue = [&](int it) {
+    const int s = it % nstage;
+    const int t0 = it * bs, bl = min(bs, J - t0);
+    const int row0 = a.backward ? J - t0 - bl : t0;     // rows of this block, ascending in memory
+    const uint32_t bb = a.Brow ? browb * bl : 0u;
+    unsigned char* dst = ring + (size_t)s * stage;
+    mbar_arrive_expect_tx(&bar[s], mbytes + qbytes + bb);
+    bulk_g2s(dst, a.M + (size_t)it * a.mstride, mbytes, &bar[s]);
+    if (qbytes) bulk_g2s(dst + mbytes, a.Q + (size_t)it * a.qstride, qbytes, &bar[s]);
+    if (bb) bulk_g2s(dst + mbytes + qbytes, gB + (size_t)row0 * browb, bb, &bar[s]);
+  };
+
+  if (threadIdx.x == 0) {
+    abort_flag = 0;
+    for (int s = 0; s < nstage; ++s) mbar_init(&bar[s], 1);
+    mbar_fence_init();
+  }
+  double2 x0 = make_double2(0.0, 0.0);
+  if (active && a.init) {
+    x0 = a.init[(size_t)(col0 + l) * N + i];
+    x0.x *= a.init_scale;
+    x0.y *= a.init_scale;
+  }
+  R hx = (R)x0.x, hy = (R)x0.y;
+  float lx = 0.f, ly = 0.f;
+  if (MIX) {
+    lx = (float)(x0.x - (double)hx);
+    ly = (float)(x0.y - (double)hy);
+  }
+  if (owner) {
+    TD v;
+    v.x = hx; v.y = hy;
+    X[(size_t)l * N + i] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const int pre = min(nstage - 1, nblk);
+    for (int it = 0; it < pre; ++it) issue(it);
+  }
+  int cur = 0, it = 0, s = 0;
+  uint32_t par = 0;
+  for (; it < nblk; ++it) {
+    const int t0 = it * bs, bl = min(bs, J - t0);
+    if (threadIdx.x == 0 && it + nstage - 1 < nblk) {
+      fence_proxy_async_smem();
+      issue(it + nstage - 1);
+    }
+    if (owner) {   // block-start state
+      if (a.xblk_pairs) {
+        reinterpret_cast<float4*>(a.Xblk)[((size_t)it * a.K + col0 + l) * N + i] =
+            make_float4((float)hx, (float)hy, lx, ly);
+      } else {
+        TD v;
+        v.x = hx; v.y = hy;
+        reinterpret_cast<TD*>(a.Xblk)[((size_t)it * a.K + col0 + l) * N + i] = v;
+      }
+    }
+    if (!mbar_wait_bounded(&bar[s], par)) abort_flag = 1;
+    const unsigned char* sp = ring + (size_t)s * stage;
+    const TD* Ms = reinterpret_cast<const TD*>(sp);
+    const TD* Qs = reinterpret_cast<const TD*>(sp + mbytes);
+    const TB* Bs = reinterpret_cast<const TB*>(sp + mbytes + qbytes);
+    const TD* Xc = X + (size_t)cur * kc * N + (size_t)l * N;
+    R ax0 = 0, ay0 = 0, ax1 = 0, ay1 = 0;
+    if (active) {
+      const TD* mcol = Ms + i;
+      int q = rsub;
+      for (; q + 3 * RS < N; q += 4 * RS) {
+        const TD d0 = mcol[(size_t)q * N], d1 = mcol[(size_t)(q + RS) * N];
+        const TD d2 = mcol[(size_t)(q + 2 * RS) * N], d3 = mcol[(size_t)(q + 3 * RS) * N];
+        const TD x0v = Xc[q], x1v = Xc[q + RS], x2v = Xc[q + 2 * RS], x3v = Xc[q + 3 * RS];
+        ax0 = fma(d0.x, x0v.x, ax0); ax0 = fma(-d0.y, x0v.y, ax0);
+        ay0 = fma(d0.x, x0v.y, ay0); ay0 = fma(d0.y, x0v.x, ay0);
+        ax1 = fma(d1.x, x1v.x, ax1); ax1 = fma(-d1.y, x1v.y, ax1);
+        ay1 = fma(d1.x, x1v.y, ay1); ay1 = fma(d1.y, x1v.x, ay1);
+        ax0 = fma(d2.x, x2v.x, ax0); ax0 = fma(-d2.y, x2v.y, ax0);
+        ay0 = fma(d2.x, x2v.y, ay0); ay0 = fma(d2.y, x2v.x, ay0);
+        ax1 = fma(d3.x, x3v.x, ax1); ax1 = fma(-d3.y, x3v.y, ax1);
+        ay1 = fma(d3.x, x3v.y, ay1); ay1 = fma(d3.y, x3v.x, ay1);
+      }
+      for (; q < N; q += RS) {
+        const TD d0 = mcol[(size_t)q * N];
+        const TD x0v = Xc[q];
+        ax0 = fma(d0.x, x0v.x, ax0); ax0 = fma(-d0.y, x0v.y, ax0);
+        ay0 = fma(d0.x, x0v.y, ay0); ay0 = fma(d0.y, x0v.x, ay0);
+      }
+      // rank-bl source update (spread over the RS lanes of the row)
+      if (a.Q) {
+        for (int m = rsub; m < bl; m += RS) {
+          const TD qv = Qs[(size_t)m * N + i];
+          const int lr = a.backward ? bl - 1 - m : m;
+          const R b = (R)Bs[(size_t)lr * a.Kp + col0 + l];
+          ax1 = fma(qv.x, b, ax1);
+          ay1 = fma(qv.y, b, ay1);
+        }
+      }
+    }
+    R ax = ax0 + ax1, ay = ay0 + ay1;
+#pragma unroll
+    for (int o = 1; o < RS; o <<= 1) {
+      ax += __shfl_xor_sync(0xffffffffu, ax, o);
+      ay += __shfl_xor_sync(0xffffffffu, ay, o);
+    }
+    if (owner) {
+      if (MIX) {
+        float fx = (float)hx, fy = (float)hy;
+        pair_add(fx, lx, (float)ax);
+        pair_add(fy, ly, (float)ay);
+        hx = (R)fx;
+        hy = (R)fy;
+      } else {
+        hx += ax;
+        hy += ay;
+      }
+      TD v;
+      v.x = hx; v.y = hy;
+      X[(size_t)(cur ^ 1) * kc * N + (size_t)l * N + i] = v;
+    }
+    __syncthreads();
+    if (abort_flag) break;
+    cur ^= 1;
+    if (++s == nstage) { s = 0; par ^= 1u; }
+  }
+  if (abort_flag) {
+    if (threadIdx.x == 0) {
+      raise_status(a.status, DEV_TIMEOUT);
+      for (int k = it; k < min(nblk, it + nstage - 1); ++k)
+        mbar_wait_bounded(&bar[k % nstage], (uint32_t)((k / nstage) & 1), 100000000ull);
+    }
+    return;
+  }
+  const double fx = (double)hx + (double)lx, fy = (double)hy + (double)ly;
+  if (owner) {
+    if (a.final_out) a.final_out[(size_t)(col0 + l) * N + i] = make_double2(fx, fy);
+    if (a.states) {   // final state of a vector chain: a_J forward, lambda_0 backward
+      const size_t row = (size_t)(a.backward ? 0 : J) * N + i;
+      if (MIX) reinterpret_cast<float4*>(a.states)[row] = make_float4((float)hx, (float)hy, lx, ly);
+      else reinterpret_cast<double2*>(a.states)[row] = make_double2(fx, fy);
+    }
+    if (!(isfinite(fx) && isfinite(fy))) raise_status(a.status, DEV_NONFINITE);
+  }
+}
+
+template <bool MIX, int RS>
+static cudaError_t launch_b(const BSweepArgs& a, cudaStream_t st) {
+  using TD = typename SweepT<MIX>::D;
+  using TB = typename SweepT<MIX>::B;
+  const int RPW = 32 / RS;
+  const int WPC = (a.N + RPW - 1) / RPW;
+  const int threads = 32 * WPC * a.kc;
+  if (threads > 1024) return cudaErrorInvalidConfiguration;
+  const size_t stage = a.mstride + (a.Q ? a.qstride : 0) + (a.Brow ? sizeof(TB) * a.Kp * a.bs : 0);
+  const size_t fixed = 2 * (size_t)a.kc * a.N * sizeof(TD) + 16;
+  const size_t budget = 200 * 1024;
+  int ns = 6;
+  while (ns > 2 && (size_t)ns * stage + fixed + 8 * ns > budget) --ns;
+  const size_t smem = (size_t)ns * stage + fixed + 8 * ns + 16;
+  if (smem > 227 * 1024) return cudaErrorInvalidConfiguration;
+  cudaFuncSetAttribute(k_bsweep<MIX, RS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  const int grid = (a.K + a.kc - 1) / a.kc;
+  k_bsweep<MIX, RS><<<grid, threads, smem, st>>>(a, ns);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_bsweep(const BSweepArgs& a, int mixed, cudaStream_t st) {
+  if (mixed) return launch_b<true, 4>(a, st);
+  return launch_b<false, 4>(a, st);
+}
+
+}  // namespace qoc
