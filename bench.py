@@ -327,6 +327,41 @@ def run_ours(args):
     return 0
 
 
+def run_warm_start(args):
+    """Learned warm start on the N=32 system (H0, M of the bench workload),
+    horizon shortened to T=5 (J=1000, dt=0.005) with a K=64 Fourier basis:
+    theta* from the library's trust region on random unit targets, MLP
+    2N -> 256^3 -> K trained by the library's kernels, then held-out targets
+    solved from theta=0 and from the MLP's theta0 to the same tolerance."""
+    import numpy as np
+    import torch
+    import paper_2505_00529_gb300 as q
+    from paper_2505_00529_gb300 import build, inputs, warmstart
+    torch.cuda.set_device(env_int("LOCAL_RANK", 0))
+    build.build()
+    base = inputs.config_problem(4)
+    J = 1000
+    prob = inputs.Problem(base.H0, base.M, base.alpha, base.beta,
+                          inputs.sine_cosine_basis(J, base.dt, 64), base.dt, base.dt, 1.0, "warm-start")
+    train = inputs.random_targets(4000, prob.N, args.ws_train)
+    test = inputs.random_targets(4001, prob.N, args.ws_test)
+    prec = q.QOC_MIXED_FP32 if args.precision == "mixed" else q.QOC_FP64
+    t0 = time.perf_counter()
+    r = warmstart.compare(prob, train, test, precision=prec, workers=args.ws_workers, epochs=args.ws_epochs,
+                          batch=128, lr=1e-3, seed=0, gtol=args.ws_gtol, xtol=1e-12, max_iter=500)
+    r["total_seconds"] = time.perf_counter() - t0
+    line = {"metric": "trust-region iterations and wall time on held-out targets: learned warm start vs theta=0",
+            "value": r["iters_ratio_mean"], "unit": "mean per-target iteration ratio (theta=0 / MLP)",
+            "higher_is_better": True, "n_gpus": 1, "dtype": "f32 panels + f64" if prec else "f64",
+            "data": "synthetic",
+            "config": {"workload": f"N=32 system, K=64 Fourier basis, T=5, J={J}; {args.ws_train} training / "
+                                   f"{args.ws_test} held-out random unit targets; MLP 64-256-256-256-64 GELU, "
+                                   f"{args.ws_epochs} epochs Adam, bfloat16 inference", "gtol": args.ws_gtol},
+            "warm_start": r}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -338,7 +373,15 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-tr", action="store_true")
+    ap.add_argument("--warm-start", action="store_true", help="run the learned warm-start experiment")
+    ap.add_argument("--ws-train", type=int, default=2000)
+    ap.add_argument("--ws-test", type=int, default=200)
+    ap.add_argument("--ws-epochs", type=int, default=300)
+    ap.add_argument("--ws-workers", type=int, default=8)
+    ap.add_argument("--ws-gtol", type=float, default=1e-5)
     args = ap.parse_args()
+    if args.warm_start:
+        return run_warm_start(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)

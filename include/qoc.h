@@ -109,6 +109,9 @@ qoc_status qoc_set_eig_method(qoc_problem* p, int method);
  * QOC_EINVAL otherwise. */
 qoc_status qoc_set_block_steps(qoc_problem* p, int steps);
 
+/* Replace the target state beta (N complex, interleaved host doubles). */
+qoc_status qoc_set_target(qoc_problem* p, const double* a_target);
+
 /* J(theta), Eq. discretecost.  theta: K host doubles.  J: one host double. */
 qoc_status qoc_eval_J(qoc_problem* p, const double* theta, double* J);
 
@@ -186,6 +189,49 @@ enum {
 };
 qoc_status qoc_read_buffer(const qoc_problem* p, int which, double* host_out, size_t count);
 
+/* ---------------------------------------------------------------------------
+ * Learned warm start (no counterpart in the paper, whose trust region starts
+ * from random theta, Sec. IV-B): a multilayer perceptron
+ *   theta0 = W_L gelu(... gelu(W_1 x + b_1) ...) + b_L,  gelu(x) = x (1 + erf(x/sqrt 2))/2,
+ * mapping features x of a target (e.g. [Re beta, Im beta]) to initial
+ * control coefficients.  binary32 training (own forward/backward/Adam
+ * kernels), bfloat16-weight inference.  Parameters are one flat binary32
+ * vector: for each layer k, W_k (d_k x d_{k+1}, row-major, y = x W_k) then b_k.
+ * ------------------------------------------------------------------------- */
+typedef struct qoc_mlp qoc_mlp;
+
+/* Number of parameters of the layout above (0 on invalid sizes). */
+size_t qoc_mlp_param_count(int n_in, int hidden, int n_hidden_layers, int n_out);
+
+/* Create with initial parameters params_init (host, qoc_mlp_param_count
+ * floats, copied) and buffers for minibatches of up to max_batch rows. */
+qoc_status qoc_mlp_create(int n_in, int hidden, int n_hidden_layers, int n_out,
+                          const float* params_init, int max_batch, void* cuda_stream,
+                          qoc_mlp** out);
+
+/* Upload the training set: X (n x n_in), T (n x n_out), row-major host floats. */
+qoc_status qoc_mlp_set_dataset(qoc_mlp* m, const float* X, const float* T, int n);
+
+/* Train: for each of `epochs` epochs, minibatches of `batch` rows taken in
+ * the order perm[ep*n .. ep*n+n-1] (host ints, a permutation of 0..n-1);
+ * loss 1/(2B) sum |y - t|^2; Adam(lr, 0.9, 0.999, 1e-8).  losses[ep] receives
+ * the mean minibatch loss of the epoch. */
+qoc_status qoc_mlp_train(qoc_mlp* m, const int* perm, int epochs, int batch, float lr,
+                         float* losses);
+
+/* Loss and its gradient with respect to the flat parameter vector for one
+ * minibatch (X batch x n_in, T batch x n_out; host floats). */
+qoc_status qoc_mlp_gradient(qoc_mlp* m, const float* X, const float* T, int batch, float* loss,
+                            float* grad);
+
+/* Inference on n rows of X into Y (n x n_out); bf16 != 0 uses bfloat16 weights. */
+qoc_status qoc_mlp_predict(qoc_mlp* m, const float* X, int n, float* Y, int bf16);
+
+/* Copy the current parameters to the host. */
+qoc_status qoc_mlp_get_params(const qoc_mlp* m, float* params);
+
+void qoc_mlp_destroy(qoc_mlp* m);
+
 /* Bytes of device memory the problem holds. */
 size_t qoc_device_bytes(const qoc_problem* p);
 
@@ -194,6 +240,10 @@ int qoc_max_basis_size(void);
 
 /* Release everything the problem owns (NULL is a no-op). */
 void qoc_destroy_problem(qoc_problem* p);
+
+/* Text of the last CUDA error this thread saw inside the library (empty if
+ * none); valid until the thread's next failing call. */
+const char* qoc_last_error(void);
 
 /* Static, human-readable name of a status. */
 const char* qoc_status_string(qoc_status s);

@@ -27,7 +27,9 @@ EXPORTS = [
     "qoc_eval_grad", "qoc_eval_grad_hess", "qoc_eval_grad_hess_dev", "qoc_sync_status",
     "qoc_trust_region_solve", "qoc_get_diagnostics", "qoc_enable_timing", "qoc_read_buffer",
     "qoc_device_bytes", "qoc_max_basis_size", "qoc_destroy_problem", "qoc_status_string",
-    "qoc_version",
+    "qoc_version", "qoc_set_target", "qoc_mlp_param_count", "qoc_mlp_create", "qoc_mlp_set_dataset",
+    "qoc_mlp_train", "qoc_mlp_gradient", "qoc_mlp_predict", "qoc_mlp_get_params", "qoc_mlp_destroy",
+    "qoc_last_error",
 ]
 
 
@@ -45,7 +47,10 @@ class TrReport(C.Structure):
 class QocError(RuntimeError):
     def __init__(self, status, where):
         self.status = status
-        super().__init__(f"{where}: {status_string(status)} (status {status})")
+        detail = ""
+        if status == QOC_ECUDA:
+            detail = " [" + lib().qoc_last_error().decode() + "]"
+        super().__init__(f"{where}: {status_string(status)} (status {status}){detail}")
 
 
 _LIB = None
@@ -88,6 +93,22 @@ def lib() -> C.CDLL:
         L.qoc_status_string.argtypes = [C.c_int]
         L.qoc_status_string.restype = C.c_char_p
         L.qoc_version.argtypes = []
+        L.qoc_set_target.argtypes = [C.c_void_p, _dp]
+        L.qoc_last_error.argtypes = []
+        L.qoc_last_error.restype = C.c_char_p
+        _fp = C.POINTER(C.c_float)
+        _ip = C.POINTER(C.c_int)
+        L.qoc_mlp_param_count.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int]
+        L.qoc_mlp_param_count.restype = C.c_size_t
+        L.qoc_mlp_create.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int, _fp, C.c_int, C.c_void_p,
+                                     C.POINTER(C.c_void_p)]
+        L.qoc_mlp_set_dataset.argtypes = [C.c_void_p, _fp, _fp, C.c_int]
+        L.qoc_mlp_train.argtypes = [C.c_void_p, _ip, C.c_int, C.c_int, C.c_float, _fp]
+        L.qoc_mlp_gradient.argtypes = [C.c_void_p, _fp, _fp, C.c_int, _fp, _fp]
+        L.qoc_mlp_predict.argtypes = [C.c_void_p, _fp, C.c_int, _fp, C.c_int]
+        L.qoc_mlp_get_params.argtypes = [C.c_void_p, _fp]
+        L.qoc_mlp_destroy.argtypes = [C.c_void_p]
+        L.qoc_mlp_destroy.restype = None
         _LIB = L
     return _LIB
 
@@ -219,6 +240,83 @@ def qoc_read_buffer(h, which, shape, complex_=False):
     return out.reshape(shape)
 
 
+def qoc_set_target(h, a_target):
+    bt = _cplx(a_target)
+    _check(lib().qoc_set_target(C.c_void_p(h), _ptr(bt)), "qoc_set_target")
+
+
+def _f32(a) -> np.ndarray:
+    return np.ascontiguousarray(np.asarray(a, dtype=np.float32))
+
+
+def _fptr(a):
+    return a.ctypes.data_as(C.POINTER(C.c_float))
+
+
+def qoc_mlp_param_count(n_in, hidden, n_hidden_layers, n_out) -> int:
+    return int(lib().qoc_mlp_param_count(n_in, hidden, n_hidden_layers, n_out))
+
+
+class MLP:
+    """The library's warm-start network (binary32 training, bfloat16 inference)."""
+
+    def __init__(self, n_in, hidden, n_hidden_layers, n_out, params, max_batch=256, cuda_stream=None):
+        self.shape = (n_in, hidden, n_hidden_layers, n_out)
+        self.np = qoc_mlp_param_count(*self.shape)
+        p = _f32(params)
+        if p.size != self.np:
+            raise ValueError(f"expected {self.np} parameters, got {p.size}")
+        h = C.c_void_p()
+        st = C.c_void_p(int(cuda_stream)) if cuda_stream else None
+        _check(lib().qoc_mlp_create(n_in, hidden, n_hidden_layers, n_out, _fptr(p), int(max_batch), st,
+                                    C.byref(h)), "qoc_mlp_create")
+        self.handle = h.value
+
+    def set_dataset(self, X, T):
+        X = _f32(X); T = _f32(T)
+        _check(lib().qoc_mlp_set_dataset(C.c_void_p(self.handle), _fptr(X), _fptr(T), X.shape[0]),
+               "qoc_mlp_set_dataset")
+
+    def train(self, perms, batch, lr):
+        perms = np.ascontiguousarray(np.asarray(perms, dtype=np.int32))
+        epochs = perms.shape[0]
+        losses = np.zeros(epochs, dtype=np.float32)
+        _check(lib().qoc_mlp_train(C.c_void_p(self.handle), perms.ctypes.data_as(C.POINTER(C.c_int)),
+                                   epochs, int(batch), float(lr), _fptr(losses)), "qoc_mlp_train")
+        return losses
+
+    def gradient(self, X, T):
+        X = _f32(X); T = _f32(T)
+        loss = np.zeros(1, dtype=np.float32)
+        g = np.zeros(self.np, dtype=np.float32)
+        _check(lib().qoc_mlp_gradient(C.c_void_p(self.handle), _fptr(X), _fptr(T), X.shape[0], _fptr(loss),
+                                      _fptr(g)), "qoc_mlp_gradient")
+        return float(loss[0]), g
+
+    def predict(self, X, bf16=True):
+        X = _f32(X)
+        Y = np.zeros((X.shape[0], self.shape[3]), dtype=np.float32)
+        _check(lib().qoc_mlp_predict(C.c_void_p(self.handle), _fptr(X), X.shape[0], _fptr(Y), int(bool(bf16))),
+               "qoc_mlp_predict")
+        return Y
+
+    def params(self):
+        out = np.zeros(self.np, dtype=np.float32)
+        _check(lib().qoc_mlp_get_params(C.c_void_p(self.handle), _fptr(out)), "qoc_mlp_get_params")
+        return out
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().qoc_mlp_destroy(C.c_void_p(self.handle))
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 def qoc_device_bytes(h) -> int:
     return int(lib().qoc_device_bytes(C.c_void_p(h)))
 
@@ -263,6 +361,9 @@ class Problem:
 
     def trust_region_solve(self, theta0, **kw):
         return qoc_trust_region_solve(self.handle, theta0, **kw)
+
+    def set_target(self, beta):
+        qoc_set_target(self.handle, beta)
 
     def buffer(self, which):
         N, K, J = self.N, self.K, self.J

@@ -74,8 +74,12 @@ struct qoc_problem {
 
 namespace {
 
-qoc_status from_cuda(cudaError_t e) {
+thread_local char g_last_error[256] = "";
+
+qoc_status from_cuda(cudaError_t e, int line = 0) {
   if (e == cudaSuccess) return QOC_OK;
+  std::snprintf(g_last_error, sizeof(g_last_error), "%s: %s (api.cu:%d)", cudaGetErrorName(e),
+                cudaGetErrorString(e), line);
   if (e == cudaErrorMemoryAllocation) return QOC_ENOMEM;
   if (e == cudaErrorInvalidConfiguration) return QOC_EUNSUPPORTED;
   return QOC_ECUDA;
@@ -84,7 +88,7 @@ qoc_status from_cuda(cudaError_t e) {
 #define QOC_TRY(expr)                         \
   do {                                        \
     cudaError_t e_ = (expr);                  \
-    if (e_ != cudaSuccess) return from_cuda(e_); \
+    if (e_ != cudaSuccess) return from_cuda(e_, __LINE__); \
   } while (0)
 
 template <typename T>
@@ -323,6 +327,8 @@ qoc_status eval_host(qoc_problem* p, const double* theta, int order, double* J, 
 extern "C" {
 
 int qoc_version(void) { return 100; }
+
+const char* qoc_last_error(void) { return g_last_error; }
 int qoc_max_basis_size(void) { return kMaxN; }
 
 const char* qoc_status_string(qoc_status s) {
@@ -478,7 +484,7 @@ qoc_status qoc_create_problem(int N, const double* H0, const double* M, const do
     ALLOC(p->trzero, 8 * ((size_t)K * K + 1));
   }
 #undef ALLOC
-  p->hbuf_len = 2 * (1 + (size_t)K + (size_t)K * K) + 2 * (size_t)K + 64;
+  p->hbuf_len = 2 * (1 + (size_t)K + (size_t)K * K) + 2 * (size_t)K + 2 * (size_t)N + 64;
   if ((e = cudaMallocHost(&p->hbuf, 8 * p->hbuf_len)) != cudaSuccess) return fail(e);
   if ((e = cudaMallocHost(&p->hstatus, sizeof(int))) != cudaSuccess) return fail(e);
   *p->hstatus = 0;
@@ -502,6 +508,13 @@ qoc_status qoc_create_problem(int N, const double* H0, const double* M, const do
   if (p->trzero && (e = cudaMemset(p->trzero, 0, 8 * ((size_t)K * K + 1))) != cudaSuccess) return fail(e);
   *out = p;
   return QOC_OK;
+}
+
+qoc_status qoc_set_target(qoc_problem* p, const double* a_target) {
+  if (!p || !a_target || !finite_all(a_target, 2 * (size_t)p->N)) return QOC_EINVAL;
+  std::memcpy(p->hbuf, a_target, 16 * (size_t)p->N);
+  QOC_TRY(cudaMemcpyAsync(p->beta, p->hbuf, 16 * (size_t)p->N, cudaMemcpyHostToDevice, p->stream));
+  return from_cuda(cudaStreamSynchronize(p->stream));
 }
 
 qoc_status qoc_set_hess_method(qoc_problem* p, int method) {

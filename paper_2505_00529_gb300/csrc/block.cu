@@ -328,11 +328,11 @@ cudaError_t launch_block_delta(const void* D, size_t dstride, int N, int J, int 
   const size_t smem = 3 * (size_t)N * (N + 1) * cs;
   const int threads = N <= 16 ? 128 : 256;
   if (mixed) {
-    cudaFuncSetAttribute(k_block_delta<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    set_max_smem((const void*)k_block_delta<true>);
     k_block_delta<true><<<nblk, threads, smem, st>>>((const unsigned char*)D, dstride, N, J, bsteps,
                                                      bwd, (unsigned char*)M, mstride);
   } else {
-    cudaFuncSetAttribute(k_block_delta<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    set_max_smem((const void*)k_block_delta<false>);
     k_block_delta<false><<<nblk, threads, smem, st>>>((const unsigned char*)D, dstride, N, J, bsteps,
                                                       bwd, (unsigned char*)M, mstride);
   }
@@ -347,13 +347,13 @@ cudaError_t launch_block_src(const void* D, size_t dstride, int N, int J, int bs
   const size_t smem = ((size_t)N * (N + 1) + 2 * (size_t)bsteps * N + (size_t)bsteps * bsteps) * cs;
   const int threads = 256;
   if (mixed) {
-    cudaFuncSetAttribute(k_block_src<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    set_max_smem((const void*)k_block_src<true>);
     k_block_src<true><<<nblk, threads, smem, st>>>((const unsigned char*)D, dstride, N, J, bsteps, bwd,
                                                    (const unsigned char*)src, (const unsigned char*)ctr,
                                                    vstride, (unsigned char*)Q, (unsigned char*)W,
                                                    (unsigned char*)G, qstride, gstride);
   } else {
-    cudaFuncSetAttribute(k_block_src<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    set_max_smem((const void*)k_block_src<false>);
     k_block_src<false><<<nblk, threads, smem, st>>>((const unsigned char*)D, dstride, N, J, bsteps, bwd,
                                                     (const unsigned char*)src, (const unsigned char*)ctr,
                                                     vstride, (unsigned char*)Q, (unsigned char*)W,

@@ -390,17 +390,17 @@ cudaError_t launch_eig(const double* H0, const double* M, const double* f, int N
   const int threads = N <= 16 ? 128 : 256;   // refinement: binary64-throughput bound
   if (method == EIG_JACOBI_FP64) {
     size_t sm = jacobi_smem(N, 8);
-    cudaFuncSetAttribute(k_eig_jacobi<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    set_max_smem((const void*)k_eig_jacobi<double>);
     k_eig_jacobi<double><<<J, jthreads, sm, st>>>(H0, M, f, N, J, W, eig, status);
     return cudaGetLastError();
   }
   size_t sm = jacobi_smem(N, 4);
-  cudaFuncSetAttribute(k_eig_jacobi<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  set_max_smem((const void*)k_eig_jacobi<float>);
   k_eig_jacobi<float><<<J, jthreads, sm, st>>>(H0, M, f, N, J, W, eig, status);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   size_t sr = refine_smem(N);
-  cudaFuncSetAttribute(k_eig_refine, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sr);
+  set_max_smem((const void*)k_eig_refine);
   k_eig_refine<<<J, threads, sr, st>>>(H0, M, f, N, J, refine_sweeps, angle_tol, W, eig, status);
   return cudaGetLastError();
 }

@@ -4,7 +4,32 @@
 #include <cuda_runtime.h>
 #include <stddef.h>
 
+#include <mutex>
+#include <set>
+#include <utility>
+
 namespace qoc {
+
+// Raise a kernel's dynamic shared-memory limit to the device maximum, once per
+// (kernel, device).  Setting it per launch to the launch's own size would let
+// a concurrent host thread lower it between another thread's set and launch.
+inline cudaError_t set_max_smem(const void* fn) {
+  static std::mutex mu;
+  static std::set<std::pair<const void*, int>> done;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  std::lock_guard<std::mutex> lock(mu);
+  if (!done.insert({fn, dev}).second) return cudaSuccess;
+  int mx = 0;
+  cudaError_t e = cudaDeviceGetAttribute(&mx, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  if (e != cudaSuccess) return e;
+  cudaFuncAttributes fa;
+  e = cudaFuncGetAttributes(&fa, fn);
+  if (e != cudaSuccess) return e;
+  // the dynamic limit excludes the kernel's static shared memory
+  return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              mx - (int)fa.sharedSizeBytes);
+}
 
 // Device status bits, OR-ed into a word the host reads after each evaluation.
 enum : int {

@@ -120,7 +120,7 @@ cudaError_t launch_pointwise(const double* W, const double2* Ptil, const double2
   const int threads = N <= 32 ? 32 : (N <= 64 ? 64 : (N <= 128 ? 128 : 256));
   const size_t smem = (size_t)N * (N + 1) * 8 + 4 * (size_t)N * 16 + 64 * 8;
   const size_t vstride = ((mixed ? 8 : 16) * (size_t)N + 15) / 16 * 16;
-  cudaFuncSetAttribute(k_pointwise, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  set_max_smem((const void*)k_pointwise);
   k_pointwise<<<J, threads, smem, st>>>(W, Ptil, Xp, a_hat, l_hat, mixed, N, J, kappa, p_hat,
                                         y_hat, vstride, g, c, want_c);
   return cudaGetLastError();

@@ -285,7 +285,7 @@ cudaError_t launch_prep(const double* W, const double* eig, const double* M, int
                         double dt, double mshift, void* D, size_t dstride, int d_fp64,
                         int parts, double2* Ptil, double2* Xp, int* status, cudaStream_t st) {
   size_t sm = prep_smem_bytes(N);
-  cudaFuncSetAttribute(k_prep, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  set_max_smem((const void*)k_prep);
   int threads = N <= 8 ? 64 : (N <= 16 ? 128 : 256);
   k_prep<<<J, threads, sm, st>>>(W, eig, M, N, J, dt, mshift, D, dstride, d_fp64, parts, Ptil,
                                  Xp, status);

@@ -258,7 +258,7 @@ static cudaError_t launch_one(const SweepArgs& a, cudaStream_t st) {
   while (ns > 2 && (size_t)ns * stage + fixed + 8 * ns > budget) --ns;
   const size_t smem = (size_t)ns * stage + fixed + 8 * ns + 16;
   if (smem > 227 * 1024) return cudaErrorInvalidConfiguration;
-  cudaFuncSetAttribute(k_sweep<MIX, RS, BWD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  set_max_smem((const void*)k_sweep<MIX, RS, BWD>);
   const int grid = (a.K + a.kc - 1) / a.kc;
   k_sweep<MIX, RS, BWD><<<grid, threads, smem, st>>>(a, ns);
   return cudaGetLastError();
@@ -476,7 +476,7 @@ static cudaError_t launch_b(const BSweepArgs& a, cudaStream_t st) {
   while (ns > 2 && (size_t)ns * stage + fixed + 8 * ns > budget) --ns;
   const size_t smem = (size_t)ns * stage + fixed + 8 * ns + 16;
   if (smem > 227 * 1024) return cudaErrorInvalidConfiguration;
-  cudaFuncSetAttribute(k_bsweep<MIX, RS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  set_max_smem((const void*)k_bsweep<MIX, RS>);
   const int grid = (a.K + a.kc - 1) / a.kc;
   k_bsweep<MIX, RS><<<grid, threads, smem, st>>>(a, ns);
   return cudaGetLastError();

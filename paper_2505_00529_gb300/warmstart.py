@@ -1,0 +1,128 @@
+"""Learned warm start for the trust-region solve.
+
+A multilayer perceptron (the library's own CUDA kernels, see ``MLP``) maps
+a target state beta to initial control coefficients theta0.  It is trained
+on optimal controls theta* that the library's trust-region solver produces
+from theta = 0, and judged by the same solver: iterations and wall time from
+theta0 = MLP(beta) versus theta0 = 0 on held-out targets, to the same
+gradient tolerance.  theta = 0 stays the fallback.  (The paper starts its
+trust region from random theta, Sec. IV-B; it has no learned component.)
+
+Every numerical step runs in the CUDA library; this module sequences calls.
+"""
+from __future__ import annotations
+
+import concurrent.futures as cf
+import time
+
+import numpy as np
+
+from . import _lib
+
+
+def features(betas: np.ndarray) -> np.ndarray:
+    """[Re beta, Im beta] rows (binary32)."""
+    betas = np.atleast_2d(betas)
+    return np.concatenate([betas.real, betas.imag], axis=1).astype(np.float32)
+
+
+def init_params(n_in, hidden, n_hidden, n_out, seed) -> np.ndarray:
+    """Glorot-normal weights, zero biases, in the library's flat layout."""
+    rng = np.random.default_rng(seed)
+    d = [n_in] + [hidden] * n_hidden + [n_out]
+    out = []
+    for k in range(len(d) - 1):
+        out.append(rng.normal(0.0, np.sqrt(2.0 / (d[k] + d[k + 1])), size=d[k] * d[k + 1]))
+        out.append(np.zeros(d[k + 1]))
+    return np.concatenate(out).astype(np.float32)
+
+
+def solve_many(prob, betas, theta0s, precision=_lib.QOC_MIXED_FP32, workers=4, **tr):
+    """Trust-region solves for each target (one problem object per worker,
+    each on its own stream).  Returns (thetas, infos, seconds)."""
+    n = len(betas)
+    thetas = np.zeros((n, prob.B.shape[1]))
+    infos = [None] * n
+    problems = [_lib.Problem(prob, precision=precision) for _ in range(workers)]
+
+    def run(w):
+        P = problems[w]
+        for i in range(w, n, workers):
+            P.set_target(betas[i])
+            t0 = time.perf_counter()
+            th, info = P.trust_region_solve(theta0s[i], **tr)
+            info["seconds"] = time.perf_counter() - t0
+            thetas[i] = th
+            infos[i] = info
+
+    t0 = time.perf_counter()
+    with cf.ThreadPoolExecutor(workers) as ex:
+        list(ex.map(run, range(workers)))
+    secs = time.perf_counter() - t0
+    for P in problems:
+        P.close()
+    return thetas, infos, secs
+
+
+class WarmStart:
+    """theta0 = scale * MLP([Re beta, Im beta]) + shift (outputs standardised
+    on the training set)."""
+
+    def __init__(self, N, K, hidden=256, n_hidden=3, seed=0, max_batch=256):
+        self.N, self.K = N, K
+        self.mlp = _lib.MLP(2 * N, hidden, n_hidden, K, init_params(2 * N, hidden, n_hidden, K, seed),
+                            max_batch=max_batch)
+        self.shift = np.zeros(K, dtype=np.float32)
+        self.scale = np.ones(K, dtype=np.float32)
+
+    def fit(self, betas, thetas, epochs=200, batch=128, lr=1e-3, seed=0):
+        thetas = np.asarray(thetas, dtype=np.float64)
+        self.shift = thetas.mean(axis=0).astype(np.float32)
+        self.scale = (thetas.std(axis=0) + 1e-6).astype(np.float32)
+        T = ((thetas - self.shift) / self.scale).astype(np.float32)
+        X = features(betas)
+        self.mlp.set_dataset(X, T)
+        rng = np.random.default_rng(seed)
+        perms = np.stack([rng.permutation(len(X)) for _ in range(epochs)])
+        return self.mlp.train(perms, batch, lr)
+
+    def predict(self, betas, bf16=True):
+        Y = self.mlp.predict(features(betas), bf16=bf16)
+        return (Y * self.scale + self.shift).astype(np.float64)
+
+    def close(self):
+        self.mlp.close()
+
+
+def compare(prob, train_betas, test_betas, precision=_lib.QOC_MIXED_FP32, workers=4, epochs=200,
+            batch=128, lr=1e-3, seed=0, **tr):
+    """Full warm-start experiment: theta* for the training targets (from 0),
+    train, then solve the held-out targets from 0 and from the MLP."""
+    K = prob.B.shape[1]
+    N = prob.H0.shape[0]
+    th_train, info_train, t_data = solve_many(prob, train_betas, np.zeros((len(train_betas), K)),
+                                              precision, workers, **tr)
+    ok = np.array([i["stop"] in ("gtol", "xtol") for i in info_train])
+    ws = WarmStart(N, K, seed=seed)
+    t0 = time.perf_counter()
+    losses = ws.fit(train_betas[ok], th_train[ok], epochs=epochs, batch=batch, lr=lr, seed=seed)
+    t_train = time.perf_counter() - t0
+    theta0 = ws.predict(test_betas)
+    _, info_zero, t_zero = solve_many(prob, test_betas, np.zeros((len(test_betas), K)), precision, workers, **tr)
+    _, info_mlp, t_mlp = solve_many(prob, test_betas, theta0, precision, workers, **tr)
+    ws.close()
+    it0 = np.array([i["iters"] for i in info_zero])
+    it1 = np.array([i["iters"] for i in info_mlp])
+    J0 = np.array([i["J"] for i in info_zero])
+    J1 = np.array([i["J"] for i in info_mlp])
+    return {
+        "n_train": int(ok.sum()), "n_test": len(test_betas), "dataset_seconds": t_data,
+        "train_seconds": t_train, "final_train_loss": float(losses[-1]),
+        "iters_zero_mean": float(it0.mean()), "iters_mlp_mean": float(it1.mean()),
+        "iters_ratio_mean": float(np.mean(it0 / np.maximum(it1, 1))),
+        "wall_zero_s": t_zero, "wall_mlp_s": t_mlp,
+        "J_zero_mean": float(J0.mean()), "J_mlp_mean": float(J1.mean()),
+        "frac_mlp_not_worse_J": float(np.mean(J1 <= J0 * (1 + 1e-6))),
+        "converged_zero": float(np.mean([i["stop"] in ("gtol", "xtol") for i in info_zero])),
+        "converged_mlp": float(np.mean([i["stop"] in ("gtol", "xtol") for i in info_mlp])),
+    }

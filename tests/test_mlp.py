@@ -1,0 +1,96 @@
+"""Warm-start network: the FP64 oracle MLP pinned by finite differences (CPU);
+the CUDA forward/backward checked against it, training and bfloat16
+inference, and the warm start's gain over theta = 0 on held-out targets (GPU)."""
+import numpy as np
+import pytest
+
+from oracle import mlp_oracle as mo
+
+
+def _params(d, seed):
+    rng = np.random.default_rng(seed)
+    out = []
+    for k in range(len(d) - 1):
+        out.append(rng.normal(0, np.sqrt(2.0 / (d[k] + d[k + 1])), size=d[k] * d[k + 1]))
+        out.append(rng.normal(0, 0.1, size=d[k + 1]))
+    return np.concatenate(out)
+
+
+def test_oracle_mlp_gradient_by_finite_differences():
+    d = mo.widths(5, 7, 3, 4)
+    p = _params(d, 0)
+    rng = np.random.default_rng(1)
+    X = rng.normal(size=(6, 5))
+    T = rng.normal(size=(6, 4))
+    loss, g = mo.loss_and_grad(p, d, X, T)
+    h = 1e-6
+    idx = rng.choice(p.size, 40, replace=False)
+    for i in idx:
+        e = np.zeros(p.size)
+        e[i] = h
+        fd = (mo.loss_and_grad(p + e, d, X, T)[0] - mo.loss_and_grad(p - e, d, X, T)[0]) / (2 * h)
+        assert abs(fd - g[i]) <= 1e-7 * max(1.0, abs(g[i]))
+
+
+def test_oracle_gelu_closed_values():
+    # x Phi(x): Phi(0) = 1/2, Phi(1) = 0.841344746068543, gelu'(0) = 1/2
+    assert mo.gelu(np.array([0.0]))[0] == 0.0
+    assert abs(mo.gelu(np.array([1.0]))[0] - 0.841344746068543) < 1e-15
+    assert abs(mo.gelu_grad(np.array([0.0]))[0] - 0.5) < 1e-15
+
+
+@pytest.mark.gpu
+def test_gpu_mlp_gradient_matches_oracle():
+    import paper_2505_00529_gb300 as q
+    from paper_2505_00529_gb300 import build
+    build.build()
+    n_in, hid, nh, n_out = 64, 256, 3, 64
+    d = mo.widths(n_in, hid, nh, n_out)
+    p = _params(d, 2).astype(np.float32)
+    rng = np.random.default_rng(3)
+    X = rng.normal(size=(37, n_in)).astype(np.float32)      # ragged batch
+    T = rng.normal(size=(37, n_out)).astype(np.float32)
+    m = q.MLP(n_in, hid, nh, n_out, p, max_batch=64)
+    loss, g = m.gradient(X, T)
+    loss_o, g_o = mo.loss_and_grad(p.astype(float), d, X.astype(float), T.astype(float))
+    assert abs(loss - loss_o) <= 1e-5 * loss_o
+    assert np.linalg.norm(g - g_o) <= 1e-5 * np.linalg.norm(g_o)
+    y32 = m.predict(X, bf16=False)
+    y_o, _ = mo.forward(p.astype(float), d, X.astype(float))
+    assert np.linalg.norm(y32 - y_o) <= 1e-5 * np.linalg.norm(y_o)
+    y16 = m.predict(X, bf16=True)                           # bfloat16 weights: ~3 significant digits
+    assert np.linalg.norm(y16 - y_o) <= 2e-2 * np.linalg.norm(y_o)
+    m.close()
+
+
+@pytest.mark.gpu
+def test_gpu_mlp_training_fits_a_smooth_map():
+    import paper_2505_00529_gb300 as q
+    from paper_2505_00529_gb300 import build, warmstart
+    build.build()
+    rng = np.random.default_rng(4)
+    X = rng.normal(size=(512, 8)).astype(np.float32)
+    A = rng.normal(size=(8, 4))
+    T = np.tanh(X @ A).astype(np.float32)
+    m = q.MLP(8, 64, 2, 4, warmstart.init_params(8, 64, 2, 4, 5), max_batch=128)
+    m.set_dataset(X, T)
+    perms = np.stack([rng.permutation(512) for _ in range(150)])
+    losses = m.train(perms, 64, 3e-3)
+    assert losses[-1] < 0.05 * losses[0]
+    m.close()
+
+
+@pytest.mark.gpu
+def test_gpu_warm_start_reduces_trust_region_iterations():
+    """Trained on theta* from the library's own trust region, the network's
+    theta0 needs fewer iterations than theta = 0 on held-out targets."""
+    from paper_2505_00529_gb300 import build, inputs, warmstart
+    import paper_2505_00529_gb300 as q
+    build.build()
+    prob = inputs.small_problem(N=6, K=8, J=200, seed=31, dt=0.05, basis="sine_cosine")
+    train = inputs.random_targets(101, 6, 192)
+    test = inputs.random_targets(202, 6, 24)
+    r = warmstart.compare(prob, train, test, precision=q.QOC_FP64, workers=4, epochs=300, batch=64,
+                          lr=2e-3, gtol=1e-7, xtol=1e-12, max_iter=200)
+    assert r["converged_mlp"] >= r["converged_zero"] - 1e-9
+    assert r["iters_mlp_mean"] < r["iters_zero_mean"], r
