@@ -684,13 +684,16 @@ qoc_status qoc_trust_region_solve(qoc_problem* p, const double* theta0, const qo
   std::memcpy(p->hbuf, theta0, 8 * (size_t)K);
   QOC_TRY(cudaMemcpyAsync(p->theta, p->hbuf, 8 * (size_t)K, cudaMemcpyHostToDevice, st));
   double* hs = p->hbuf + K;   // [J, |g|] and [pred, |s|, sigma, |g|, J_trial]
-  // evaluate grad/Hess at theta and factor the Hessian
+  // evaluate grad/Hess at theta and factor the Hessian; device status checked here
   auto eval_gh = [&]() -> qoc_status {
     qoc_status s = enqueue_eval(p, p->theta, 2, p->out);
     if (s != QOC_OK) return s;
     QOC_TRY(launch_eig(p->out + 1 + K, p->trzero, p->trzero, K, 1, p->trwork + 3 * K,
                        p->trwork + 2 * K, p->status, EIG_JACOBI_FP64, 0, 0.0, st));
-    return QOC_OK;
+    QOC_TRY(cudaMemcpyAsync(p->hstatus, p->status, sizeof(int), cudaMemcpyDeviceToHost, st));
+    QOC_TRY(cudaMemsetAsync(p->status, 0, sizeof(int), st));
+    QOC_TRY(cudaStreamSynchronize(st));
+    return device_status(p);
   };
   qoc_status s = eval_gh();
   if (s != QOC_OK) return s;
@@ -707,16 +710,19 @@ qoc_status qoc_trust_region_solve(qoc_problem* p, const double* theta0, const qo
     QOC_TRY(cudaMemcpyAsync(hs + 4, p->out_trial, sizeof(double), cudaMemcpyDeviceToHost, st));
     QOC_TRY(cudaMemcpyAsync(hs + 5, p->out, sizeof(double), cudaMemcpyDeviceToHost, st));
     QOC_TRY(cudaMemcpyAsync(p->hstatus, p->status, sizeof(int), cudaMemcpyDeviceToHost, st));
+    QOC_TRY(cudaMemsetAsync(p->status, 0, sizeof(int), st));
     QOC_TRY(cudaStreamSynchronize(st));
     s = device_status(p);
-    if (s != QOC_OK) return s;
+    if (s == QOC_ETIMEOUT || s == QOC_EUNSUPPORTED) return s;
     const double pred = hs[0], snorm = hs[1], gnorm = hs[3], Jt = hs[4];
+    // a trial point whose evaluation failed numerically is a rejected step
+    const bool trial_ok = s == QOC_OK && std::isfinite(Jt);
     Jc = hs[5];
     report->n_eval_J++;
     report->grad_norm = gnorm;
     if (gnorm < opt->gtol) { stop = 0; --it; report->n_eval_J--; break; }
     if (!(pred > 0) || !std::isfinite(pred)) { stop = 3; break; }
-    const double rho = (Jc - Jt) / pred;
+    const double rho = trial_ok ? (Jc - Jt) / pred : -1.0;
     if (rho < 0.25) radius *= 0.25;
     else if (rho > 0.75 && std::fabs(snorm - radius) <= 1e-8 * radius)
       radius = std::fmin(2.0 * radius, opt->radius_max);

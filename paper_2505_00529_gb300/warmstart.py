@@ -50,7 +50,11 @@ def solve_many(prob, betas, theta0s, precision=_lib.QOC_MIXED_FP32, workers=4, *
         for i in range(w, n, workers):
             P.set_target(betas[i])
             t0 = time.perf_counter()
-            th, info = P.trust_region_solve(theta0s[i], **tr)
+            try:
+                th, info = P.trust_region_solve(theta0s[i], **tr)
+            except _lib.QocError as e:   # recorded, not fatal: the solve counts as failed
+                th, info = np.full(prob.B.shape[1], np.nan), {"iters": tr.get("max_iter", 0),
+                                                               "J": np.nan, "stop": f"error {e.status}"}
             info["seconds"] = time.perf_counter() - t0
             thetas[i] = th
             infos[i] = info
@@ -102,7 +106,8 @@ def compare(prob, train_betas, test_betas, precision=_lib.QOC_MIXED_FP32, worker
     N = prob.H0.shape[0]
     th_train, info_train, t_data = solve_many(prob, train_betas, np.zeros((len(train_betas), K)),
                                               precision, workers, **tr)
-    ok = np.array([i["stop"] in ("gtol", "xtol") for i in info_train])
+    ok = np.array([i["stop"] in ("gtol", "xtol") and np.all(np.isfinite(t))
+                   for i, t in zip(info_train, th_train)])
     ws = WarmStart(N, K, seed=seed)
     t0 = time.perf_counter()
     losses = ws.fit(train_betas[ok], th_train[ok], epochs=epochs, batch=batch, lr=lr, seed=seed)
@@ -111,12 +116,15 @@ def compare(prob, train_betas, test_betas, precision=_lib.QOC_MIXED_FP32, worker
     _, info_zero, t_zero = solve_many(prob, test_betas, np.zeros((len(test_betas), K)), precision, workers, **tr)
     _, info_mlp, t_mlp = solve_many(prob, test_betas, theta0, precision, workers, **tr)
     ws.close()
-    it0 = np.array([i["iters"] for i in info_zero])
-    it1 = np.array([i["iters"] for i in info_mlp])
-    J0 = np.array([i["J"] for i in info_zero])
-    J1 = np.array([i["J"] for i in info_mlp])
+    good = np.array([a["stop"] in ("gtol", "xtol") and b["stop"] in ("gtol", "xtol")
+                     for a, b in zip(info_zero, info_mlp)])
+    it0 = np.array([i["iters"] for i in info_zero])[good]
+    it1 = np.array([i["iters"] for i in info_mlp])[good]
+    J0 = np.array([i["J"] for i in info_zero])[good]
+    J1 = np.array([i["J"] for i in info_mlp])[good]
     return {
-        "n_train": int(ok.sum()), "n_test": len(test_betas), "dataset_seconds": t_data,
+        "n_train": int(ok.sum()), "n_train_failed": int((~ok).sum()), "n_test": len(test_betas),
+        "n_test_compared": int(good.sum()), "dataset_seconds": t_data,
         "train_seconds": t_train, "final_train_loss": float(losses[-1]),
         "iters_zero_mean": float(it0.mean()), "iters_mlp_mean": float(it1.mean()),
         "iters_ratio_mean": float(np.mean(it0 / np.maximum(it1, 1))),
