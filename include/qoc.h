@@ -232,6 +232,25 @@ qoc_status qoc_mlp_get_params(const qoc_mlp* m, float* params);
 
 void qoc_mlp_destroy(qoc_mlp* m);
 
+/* ---------------------------------------------------------------------------
+ * Batches of uneven problems (different N, K, J; one precision; time
+ * blocking on).  One batched evaluation = the gradient and Hessian of every
+ * problem at its own theta: the parallel phases of each problem run on that
+ * problem's stream, the four sequential sweeps run as one launch each over
+ * all problems, and the whole evaluation is captured once into a CUDA graph
+ * (qoc_batch_set_graph(b, 0) disables the graph).  The batch references the
+ * problems (caller keeps them alive and must not use them concurrently).
+ *   thetas: concatenation of the problems' theta (sum K_i doubles)
+ *   outs:   concatenation of [J, grad (K_i), Hess (K_i^2)] per problem
+ * ------------------------------------------------------------------------- */
+typedef struct qoc_batch qoc_batch;
+qoc_status qoc_batch_create(qoc_problem* const* problems, int n, void* cuda_stream, qoc_batch** out);
+qoc_status qoc_batch_set_graph(qoc_batch* b, int on);
+qoc_status qoc_batch_eval_grad_hess(qoc_batch* b, const double* thetas, double* outs);
+/* device-pointer form: enqueues on the batch stream and returns */
+qoc_status qoc_batch_eval_grad_hess_dev(qoc_batch* b, const double* thetas_dev, double* outs_dev);
+void qoc_batch_destroy(qoc_batch* b);
+
 /* Bytes of device memory the problem holds. */
 size_t qoc_device_bytes(const qoc_problem* p);
 

@@ -29,7 +29,8 @@ EXPORTS = [
     "qoc_device_bytes", "qoc_max_basis_size", "qoc_destroy_problem", "qoc_status_string",
     "qoc_version", "qoc_set_target", "qoc_mlp_param_count", "qoc_mlp_create", "qoc_mlp_set_dataset",
     "qoc_mlp_train", "qoc_mlp_gradient", "qoc_mlp_predict", "qoc_mlp_get_params", "qoc_mlp_destroy",
-    "qoc_last_error",
+    "qoc_last_error", "qoc_batch_create", "qoc_batch_set_graph", "qoc_batch_eval_grad_hess",
+    "qoc_batch_eval_grad_hess_dev", "qoc_batch_destroy",
 ]
 
 
@@ -96,6 +97,12 @@ def lib() -> C.CDLL:
         L.qoc_set_target.argtypes = [C.c_void_p, _dp]
         L.qoc_last_error.argtypes = []
         L.qoc_last_error.restype = C.c_char_p
+        L.qoc_batch_create.argtypes = [C.POINTER(C.c_void_p), C.c_int, C.c_void_p, C.POINTER(C.c_void_p)]
+        L.qoc_batch_set_graph.argtypes = [C.c_void_p, C.c_int]
+        L.qoc_batch_eval_grad_hess.argtypes = [C.c_void_p, _dp, _dp]
+        L.qoc_batch_eval_grad_hess_dev.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p]
+        L.qoc_batch_destroy.argtypes = [C.c_void_p]
+        L.qoc_batch_destroy.restype = None
         _fp = C.POINTER(C.c_float)
         _ip = C.POINTER(C.c_int)
         L.qoc_mlp_param_count.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int]
@@ -317,6 +324,37 @@ class MLP:
             pass
 
 
+def qoc_batch_create(handles, cuda_stream=None):
+    """Batch over existing problem handles (same precision, time blocking on)."""
+    arr = (C.c_void_p * len(handles))(*[C.c_void_p(h) for h in handles])
+    b = C.c_void_p()
+    st = C.c_void_p(int(cuda_stream)) if cuda_stream else None
+    _check(lib().qoc_batch_create(arr, len(handles), st, C.byref(b)), "qoc_batch_create")
+    return b.value
+
+
+def qoc_batch_set_graph(b, on):
+    _check(lib().qoc_batch_set_graph(C.c_void_p(b), int(bool(on))), "qoc_batch_set_graph")
+
+
+def qoc_batch_eval_grad_hess(b, thetas, outs_len):
+    """thetas: concatenated theta of all problems; returns the concatenated
+    [J, grad, Hess] blocks (outs_len doubles)."""
+    th = _f64(thetas)
+    out = np.zeros(int(outs_len))
+    _check(lib().qoc_batch_eval_grad_hess(C.c_void_p(b), _ptr(th), _ptr(out)), "qoc_batch_eval_grad_hess")
+    return out
+
+
+def qoc_batch_eval_grad_hess_dev(b, thetas_dev_ptr: int, outs_dev_ptr: int):
+    _check(lib().qoc_batch_eval_grad_hess_dev(C.c_void_p(b), C.c_void_p(int(thetas_dev_ptr)),
+                                              C.c_void_p(int(outs_dev_ptr))), "qoc_batch_eval_grad_hess_dev")
+
+
+def qoc_batch_destroy(b):
+    lib().qoc_batch_destroy(C.c_void_p(b))
+
+
 def qoc_device_bytes(h) -> int:
     return int(lib().qoc_device_bytes(C.c_void_p(h)))
 
@@ -381,6 +419,52 @@ class Problem:
     def close(self):
         if self.handle:
             qoc_destroy_problem(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Batch:
+    """Batched gradient + Hessian evaluation over several ``Problem`` objects
+    (which must stay alive while the batch is used)."""
+
+    def __init__(self, problems, cuda_stream=None, graph=True):
+        self.problems = list(problems)
+        self.Ks = [p.K for p in self.problems]
+        self.handle = qoc_batch_create([p.handle for p in self.problems], cuda_stream)
+        if not graph:
+            qoc_batch_set_graph(self.handle, 0)
+        self.n_theta = sum(self.Ks)
+        self.n_out = sum(1 + K + K * K for K in self.Ks)
+
+    def split(self, flat):
+        res, o = [], 0
+        for K in self.Ks:
+            res.append((float(flat[o]), flat[o + 1:o + 1 + K].copy(),
+                        flat[o + 1 + K:o + 1 + K + K * K].reshape(K, K).copy()))
+            o += 1 + K + K * K
+        return res
+
+    def eval_grad_hess(self, thetas):
+        """thetas: list of per-problem theta; returns a list of (J, grad, Hess)."""
+        flat = np.concatenate([_f64(t).ravel() for t in thetas])
+        if flat.size != self.n_theta:
+            raise ValueError(f"expected {self.n_theta} coefficients in total, got {flat.size}")
+        return self.split(qoc_batch_eval_grad_hess(self.handle, flat, self.n_out))
+
+    def close(self):
+        if getattr(self, "handle", None):
+            qoc_batch_destroy(self.handle)
             self.handle = None
 
     def __enter__(self):

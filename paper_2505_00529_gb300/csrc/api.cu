@@ -752,3 +752,280 @@ qoc_status qoc_trust_region_solve(qoc_problem* p, const double* theta0, const qo
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Batches of uneven problems (different N, K, J; same precision).  Each
+// problem's parallel phases run on its own stream; the four latency-bound
+// sweeps (states, costates, tangent panels, second-order adjoint panels) run
+// as one launch each over all problems.  The fork/join graph of one batched
+// evaluation is captured once into a CUDA graph and replayed.
+// ---------------------------------------------------------------------------
+struct qoc_batch {
+  int n = 0, mixed = 0;
+  std::vector<qoc_problem*> P;
+  cudaStream_t st = nullptr;
+  bool own_stream = false;
+  std::vector<cudaEvent_t> ev;         // per problem: 5 phase events; then 5 batch events
+  std::vector<BSweepArgs> hargs[4];
+  std::vector<int> hoff[4];
+  BSweepArgs* dargs[4] = {nullptr, nullptr, nullptr, nullptr};
+  int* doff[4] = {nullptr, nullptr, nullptr, nullptr};
+  int nargs[4] = {0, 0, 0, 0}, total[4] = {0, 0, 0, 0};
+  std::vector<size_t> toff, ooff;
+  size_t ntheta = 0, nout = 0;
+  double *theta = nullptr, *out = nullptr, *hbuf = nullptr;
+  int* hstat = nullptr;
+  int use_graph = 1;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+};
+
+namespace {
+
+BSweepArgs chain_args(qoc_problem* p, int bwd) {
+  BSweepArgs a{};
+  const int mixed = p->precision == QOC_MIXED_FP32;
+  a.N = p->N; a.K = 1; a.Kp = p->Kp; a.J = p->J; a.bs = p->bs; a.kc = 1; a.backward = bwd;
+  a.M = reinterpret_cast<const unsigned char*>(bwd ? p->Mb : p->Mf); a.mstride = p->mstride;
+  a.init = bwd ? p->lamJ : p->alpha; a.init_scale = 1.0;
+  a.Xblk = bwd ? p->Xl : p->Xa; a.xblk_pairs = mixed;
+  a.states = bwd ? p->l_hat : p->a_hat; a.status = p->status;
+  return a;
+}
+
+BSweepArgs panel_args(qoc_problem* p, int bwd) {
+  BSweepArgs s{};
+  const int mixed = p->precision == QOC_MIXED_FP32;
+  s.N = p->N; s.K = p->K; s.Kp = p->Kp; s.J = p->J; s.bs = p->bs; s.kc = sweep_kc(p); s.backward = bwd;
+  s.M = reinterpret_cast<const unsigned char*>(bwd ? p->Mb : p->Mf); s.mstride = p->mstride;
+  s.Q = reinterpret_cast<const unsigned char*>(bwd ? p->Qb : p->Qf); s.qstride = p->qstride;
+  s.Brow = mixed ? static_cast<const void*>(p->Bf) : static_cast<const void*>(p->B);
+  s.status = p->status;
+  if (bwd) {
+    s.init = p->SJ; s.init_scale = 2.0 * p->w_t; s.Xblk = p->Xmu;
+  } else {
+    s.final_out = p->SJ; s.Xblk = p->XS;
+  }
+  return s;
+}
+
+// one phase of problem i of the batch on stream s (see the header comment)
+qoc_status batch_phase(qoc_batch* b, int i, int phase, cudaStream_t s) {
+  qoc_problem* p = b->P[i];
+  const int N = p->N, K = p->K, J = p->J, bs = p->bs, mixed = b->mixed;
+  double* out = b->out + b->ooff[i];
+  const void* Bsrc = mixed ? static_cast<const void*>(p->Bf) : static_cast<const void*>(p->B);
+  switch (phase) {
+    case 0:
+      QOC_TRY(cudaMemcpyAsync(p->theta, b->theta + b->toff[i], 8 * (size_t)K, cudaMemcpyDeviceToDevice, s));
+      QOC_TRY(launch_control(p->B, p->Kp, p->theta, J, K, p->f, s));
+      QOC_TRY(launch_eig(p->H0, p->M, p->f, N, J, p->W, p->eig, p->status,
+                         p->eig_method == QOC_EIG_JACOBI_FP64 ? EIG_JACOBI_FP64 : EIG_REFINED,
+                         p->refine_sweeps, p->angle_tol, s));
+      QOC_TRY(launch_prep(p->W, p->eig, p->M, N, J, p->dt, p->mshift, p->D, p->dstride, mixed ? 0 : 1,
+                          3, p->Ptil, p->Xp, p->status, s));
+      QOC_TRY(launch_block_delta(p->D, p->dstride, N, J, bs, 0, mixed, p->Mf, p->mstride, s));
+      QOC_TRY(launch_block_delta(p->D, p->dstride, N, J, bs, 1, mixed, p->Mb, p->mstride, s));
+      return QOC_OK;
+    case 1: {
+      QOC_TRY(launch_block_fill(p->D, p->dstride, N, J, bs, 0, mixed, p->Xa, p->a_hat, s));
+      const double thetaJ = (double)J * p->dt * p->mshift;
+      QOC_TRY(launch_terminal(p->f, J, p->a_hat, mixed, p->beta, N, cexpi_h(thetaJ), p->w_f, p->w_t,
+                              p->lamJ, p->scal + 0, p->scal + 1, s));
+      QOC_TRY(cudaMemcpyAsync(out, p->scal, sizeof(double), cudaMemcpyDeviceToDevice, s));
+      return QOC_OK;
+    }
+    case 2:
+      QOC_TRY(launch_block_fill(p->D, p->dstride, N, J, bs, 1, mixed, p->Xl, p->l_hat, s));
+      QOC_TRY(launch_pointwise(p->W, p->Ptil, p->Xp, p->a_hat, p->l_hat, mixed, N, J,
+                               cexpi_h(p->dt * p->mshift), p->p_hat, p->y_hat, p->g, p->c, 1, s));
+      QOC_TRY(launch_block_src(p->D, p->dstride, N, J, bs, 0, mixed, p->p_hat, p->y_hat, p->vstride,
+                               p->Qf, p->Wf, p->Gf, p->qstride, p->gstride, s));
+      return QOC_OK;
+    case 3:
+      QOC_TRY(launch_block_contract(p->XS, p->Wf, p->Gf, p->qstride, p->gstride, Bsrc, p->Kp, N, K, J,
+                                    bs, 0, mixed, p->U, s));
+      if (p->hess_method == QOC_HESS_SECOND_ORDER_ADJOINT)
+        QOC_TRY(launch_block_src(p->D, p->dstride, N, J, bs, 1, mixed, p->y_hat, p->p_hat, p->vstride,
+                                 p->Qb, p->Wb, p->Gb, p->qstride, p->gstride, s));
+      return QOC_OK;
+    default:
+      if (p->hess_method == QOC_HESS_SECOND_ORDER_ADJOINT)
+        QOC_TRY(launch_block_contract(p->Xmu, p->Wb, p->Gb, p->qstride, p->gstride, Bsrc, p->Kp, N, K,
+                                      J, bs, 1, mixed, p->V, s));
+      QOC_TRY(launch_assemble(p->B, p->Kp, p->f, p->g, p->c, p->V, p->U, mixed, p->SJ, N, J, K,
+                              p->w_f, p->w_t, p->hess_method == QOC_HESS_SECOND_ORDER_ADJOINT ? 0 : 1,
+                              1, p->work, out, p->hess_raw, p->scal + 2, s));
+      return QOC_OK;
+  }
+}
+
+// the whole batched evaluation, enqueued on b->st with forks to the problems' streams
+qoc_status enqueue_batch(qoc_batch* b) {
+  const int n = b->n;
+  cudaEvent_t* bev = b->ev.data() + 5 * (size_t)n;
+  QOC_TRY(cudaEventRecord(bev[0], b->st));
+  for (int phase = 0; phase < 5; ++phase) {
+    // fork: every problem stream waits for the batch stream, runs its phase
+    for (int i = 0; i < n; ++i) {
+      cudaStream_t s = b->P[i]->stream;
+      QOC_TRY(cudaStreamWaitEvent(s, bev[phase], 0));
+      qoc_status r = batch_phase(b, i, phase, s);
+      if (r != QOC_OK) return r;
+      QOC_TRY(cudaEventRecord(b->ev[5 * (size_t)i + phase], s));
+    }
+    // join, then the batched sweep of this stage
+    for (int i = 0; i < n; ++i) QOC_TRY(cudaStreamWaitEvent(b->st, b->ev[5 * (size_t)i + phase], 0));
+    if (phase < 4) {
+      if (b->nargs[phase] > 0)
+        QOC_TRY(launch_bsweep_batch(b->hargs[phase].data(), b->dargs[phase], b->doff[phase],
+                                    b->nargs[phase], b->total[phase], b->mixed, b->st));
+      QOC_TRY(cudaEventRecord(bev[phase + 1], b->st));
+    }
+  }
+  return QOC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void qoc_batch_destroy(qoc_batch* b) {
+  if (!b) return;
+  if (b->st) cudaStreamSynchronize(b->st);
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  for (auto e : b->ev)
+    if (e) cudaEventDestroy(e);
+  for (int k = 0; k < 4; ++k) {
+    cudaFree(b->dargs[k]);
+    cudaFree(b->doff[k]);
+  }
+  cudaFree(b->theta);
+  cudaFree(b->out);
+  if (b->hbuf) cudaFreeHost(b->hbuf);
+  if (b->hstat) cudaFreeHost(b->hstat);
+  if (b->own_stream && b->st) cudaStreamDestroy(b->st);
+  delete b;
+}
+
+qoc_status qoc_batch_create(qoc_problem* const* problems, int n, void* cuda_stream, qoc_batch** out) {
+  if (!out || !problems || n < 1) return QOC_EINVAL;
+  *out = nullptr;
+  for (int i = 0; i < n; ++i) {
+    if (!problems[i]) return QOC_EINVAL;
+    if (problems[i]->precision != problems[0]->precision) return QOC_EINVAL;
+    if (problems[i]->bs < 2) return QOC_EUNSUPPORTED;
+    for (int k = 0; k < i; ++k)
+      if (problems[k] == problems[i]) return QOC_EINVAL;
+  }
+  qoc_batch* b = new (std::nothrow) qoc_batch();
+  if (!b) return QOC_ENOMEM;
+  b->n = n;
+  b->mixed = problems[0]->precision == QOC_MIXED_FP32;
+  b->P.assign(problems, problems + n);
+  cudaError_t e;
+  auto fail = [&](cudaError_t err) { qoc_batch_destroy(b); return from_cuda(err, __LINE__); };
+  if (cuda_stream) b->st = (cudaStream_t)cuda_stream;
+  else {
+    if ((e = cudaStreamCreateWithFlags(&b->st, cudaStreamNonBlocking)) != cudaSuccess) return fail(e);
+    b->own_stream = true;
+  }
+  b->ev.assign(5 * (size_t)n + 5, nullptr);
+  for (auto& ev : b->ev)
+    if ((e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming)) != cudaSuccess) return fail(e);
+  for (int i = 0; i < n; ++i) {
+    qoc_problem* p = problems[i];
+    b->toff.push_back(b->ntheta);
+    b->ooff.push_back(b->nout);
+    b->ntheta += p->K;
+    b->nout += 1 + (size_t)p->K + (size_t)p->K * p->K;
+    // descriptor lists of the four batched sweeps
+    BSweepArgs args[4] = {chain_args(p, 0), chain_args(p, 1), panel_args(p, 0), panel_args(p, 1)};
+    for (int k = 0; k < 4; ++k) {
+      if (k == 3 && p->hess_method != QOC_HESS_SECOND_ORDER_ADJOINT) continue;
+      b->hoff[k].push_back(b->total[k]);
+      b->hargs[k].push_back(args[k]);
+      b->total[k] += (args[k].K + args[k].kc - 1) / args[k].kc;
+    }
+  }
+  for (int k = 0; k < 4; ++k) {
+    b->nargs[k] = (int)b->hargs[k].size();
+    b->hoff[k].push_back(b->total[k]);
+    if (!b->nargs[k]) continue;
+    if ((e = cudaMalloc(&b->dargs[k], sizeof(BSweepArgs) * b->nargs[k])) != cudaSuccess) return fail(e);
+    if ((e = cudaMalloc(&b->doff[k], sizeof(int) * (b->nargs[k] + 1))) != cudaSuccess) return fail(e);
+    if ((e = cudaMemcpy(b->dargs[k], b->hargs[k].data(), sizeof(BSweepArgs) * b->nargs[k],
+                        cudaMemcpyHostToDevice)) != cudaSuccess) return fail(e);
+    if ((e = cudaMemcpy(b->doff[k], b->hoff[k].data(), sizeof(int) * (b->nargs[k] + 1),
+                        cudaMemcpyHostToDevice)) != cudaSuccess) return fail(e);
+  }
+  if ((e = cudaMalloc(&b->theta, 8 * b->ntheta)) != cudaSuccess) return fail(e);
+  if ((e = cudaMalloc(&b->out, 8 * b->nout)) != cudaSuccess) return fail(e);
+  if ((e = cudaMallocHost(&b->hbuf, 8 * (b->ntheta + b->nout))) != cudaSuccess) return fail(e);
+  if ((e = cudaMallocHost(&b->hstat, sizeof(int) * n)) != cudaSuccess) return fail(e);
+  *out = b;
+  return QOC_OK;
+}
+
+qoc_status qoc_batch_set_graph(qoc_batch* b, int on) {
+  if (!b) return QOC_EINVAL;
+  b->use_graph = on ? 1 : 0;
+  return QOC_OK;
+}
+
+qoc_status qoc_batch_eval_grad_hess_dev(qoc_batch* b, const double* thetas_dev, double* outs_dev) {
+  if (!b || !thetas_dev || !outs_dev) return QOC_EINVAL;
+  if (thetas_dev != b->theta)
+    QOC_TRY(cudaMemcpyAsync(b->theta, thetas_dev, 8 * b->ntheta, cudaMemcpyDeviceToDevice, b->st));
+  if (b->use_graph && b->exec) {
+    QOC_TRY(cudaGraphLaunch(b->exec, b->st));
+  } else {
+    // the first call runs eagerly (one-time kernel attribute set-up happens
+    // outside any capture), then records the same work as a graph for replay
+    qoc_status r = enqueue_batch(b);
+    if (r != QOC_OK) return r;
+    if (b->use_graph) {
+      QOC_TRY(cudaStreamBeginCapture(b->st, cudaStreamCaptureModeThreadLocal));
+      r = enqueue_batch(b);
+      cudaGraph_t g = nullptr;
+      cudaError_t ec = cudaStreamEndCapture(b->st, &g);
+      if (r != QOC_OK) {
+        if (g) cudaGraphDestroy(g);
+        return r;
+      }
+      QOC_TRY(ec);
+      b->graph = g;
+      QOC_TRY(cudaGraphInstantiate(&b->exec, b->graph, 0));
+    }
+  }
+  if (outs_dev != b->out)
+    QOC_TRY(cudaMemcpyAsync(outs_dev, b->out, 8 * b->nout, cudaMemcpyDeviceToDevice, b->st));
+  for (qoc_problem* p : b->P) p->last_order = 2;
+  return QOC_OK;
+}
+
+qoc_status qoc_batch_eval_grad_hess(qoc_batch* b, const double* thetas, double* outs) {
+  if (!b || !thetas || !outs) return QOC_EINVAL;
+  if (!finite_all(thetas, b->ntheta)) return QOC_EINVAL;
+  std::memcpy(b->hbuf, thetas, 8 * b->ntheta);
+  QOC_TRY(cudaMemcpyAsync(b->theta, b->hbuf, 8 * b->ntheta, cudaMemcpyHostToDevice, b->st));
+  qoc_status r = qoc_batch_eval_grad_hess_dev(b, b->theta, b->out);
+  if (r != QOC_OK) return r;
+  QOC_TRY(cudaMemcpyAsync(b->hbuf + b->ntheta, b->out, 8 * b->nout, cudaMemcpyDeviceToHost, b->st));
+  for (int i = 0; i < b->n; ++i) {
+    QOC_TRY(cudaMemcpyAsync(b->hstat + i, b->P[i]->status, sizeof(int), cudaMemcpyDeviceToHost, b->st));
+    QOC_TRY(cudaMemsetAsync(b->P[i]->status, 0, sizeof(int), b->st));
+  }
+  QOC_TRY(cudaStreamSynchronize(b->st));
+  std::memcpy(outs, b->hbuf + b->ntheta, 8 * b->nout);
+  for (int i = 0; i < b->n; ++i) {
+    if (b->hstat[i] == 0) continue;
+    *b->P[i]->hstatus = b->hstat[i];
+    return device_status(b->P[i]);
+  }
+  if (!finite_all(outs, b->nout)) return QOC_ENUMERIC;
+  return QOC_OK;
+}
+
+}  // extern "C"

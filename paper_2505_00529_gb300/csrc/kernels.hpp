@@ -101,6 +101,10 @@ struct BSweepArgs {
   int* status;
 };
 cudaError_t launch_bsweep(const BSweepArgs& a, int mixed, cudaStream_t st);
+// one launch for many problems: CTAs cta_off[p] .. cta_off[p+1]-1 run problem p
+cudaError_t launch_bsweep_batch(const BSweepArgs* host_args, const BSweepArgs* dev_args,
+                                const int* dev_cta_off, int nprob, int total_ctas, int mixed,
+                                cudaStream_t st);
 cudaError_t launch_block_delta(const void* D, size_t dstride, int N, int J, int bsteps, int bwd,
                                int mixed, void* M, size_t mstride, cudaStream_t st);
 cudaError_t launch_block_src(const void* D, size_t dstride, int N, int J, int bsteps, int bwd,

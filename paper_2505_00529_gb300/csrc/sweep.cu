@@ -289,8 +289,8 @@ namespace qoc {
 // columns) and the bs rows of B are staged by bulk copies into the ring.
 // ---------------------------------------------------------------------------
 template <bool MIX, int RS>
-__global__ void __launch_bounds__(1024) k_bsweep(const BSweepArgs a, const int nstage) {
-  extern __shared__ __align__(128) unsigned char smem[];
+__device__ __forceinline__ void bsweep_body(const BSweepArgs& a, const int cta, const int nstage,
+                                            unsigned char* smem) {
   using TD = typename SweepT<MIX>::D;
   using TB = typename SweepT<MIX>::B;
   using R = typename SweepT<MIX>::R;
@@ -302,7 +302,7 @@ __global__ void __launch_bounds__(1024) k_bsweep(const BSweepArgs a, const int n
   const int l = warp / WPC, rb = warp % WPC;
   const int rsub = lane % RS;
   const int i = rb * RPW + lane / RS;
-  const int col0 = blockIdx.x * kc;
+  const int col0 = cta * kc;
   const int ncols = min(kc, a.K - col0);
   const bool active = (l < ncols) && (i < N);
   const bool owner = active && rsub == 0;
@@ -459,6 +459,70 @@ __global__ void __launch_bounds__(1024) k_bsweep(const BSweepArgs a, const int n
     }
     if (!(isfinite(fx) && isfinite(fy))) raise_status(a.status, DEV_NONFINITE);
   }
+}
+
+template <bool MIX, int RS>
+__global__ void __launch_bounds__(1024) k_bsweep(const BSweepArgs a, const int nstage) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  bsweep_body<MIX, RS>(a, blockIdx.x, nstage, smem);
+}
+
+// Many problems in one launch: CTA b belongs to the problem p with
+// cta_off[p] <= b < cta_off[p + 1]; every CTA runs its own dependent chain.
+template <bool MIX, int RS>
+__global__ void __launch_bounds__(1024) k_bsweep_batch(const BSweepArgs* __restrict__ args,
+                                                       const int* __restrict__ cta_off, int nprob,
+                                                       const int nstage) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  int lo = 0, hi = nprob;   // largest p with cta_off[p] <= blockIdx.x
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (cta_off[mid] <= (int)blockIdx.x) lo = mid; else hi = mid;
+  }
+  const BSweepArgs a = args[lo];
+  bsweep_body<MIX, RS>(a, (int)blockIdx.x - cta_off[lo], nstage, smem);
+}
+
+// launch geometry of one problem's blocked sweep: threads, ring stages, smem
+template <bool MIX, int RS>
+static void bsweep_geometry(const BSweepArgs& a, int& threads, size_t& stage, size_t& fixed) {
+  using TD = typename SweepT<MIX>::D;
+  using TB = typename SweepT<MIX>::B;
+  const int RPW = 32 / RS;
+  const int WPC = (a.N + RPW - 1) / RPW;
+  threads = 32 * WPC * a.kc;
+  stage = a.mstride + (a.Q ? a.qstride : 0) + (a.Brow ? sizeof(TB) * a.Kp * a.bs : 0);
+  fixed = 2 * (size_t)a.kc * a.N * sizeof(TD) + 16;
+}
+
+template <bool MIX, int RS>
+static cudaError_t launch_bb(const BSweepArgs* host_args, const BSweepArgs* dev_args,
+                             const int* dev_cta_off, int nprob, int total_ctas, cudaStream_t st) {
+  int threads = 32;
+  size_t stage = 16, fixed = 16;
+  for (int p = 0; p < nprob; ++p) {
+    int t;
+    size_t s, f;
+    bsweep_geometry<MIX, RS>(host_args[p], t, s, f);
+    threads = t > threads ? t : threads;
+    stage = s > stage ? s : stage;
+    fixed = f > fixed ? f : fixed;
+  }
+  if (threads > 1024) return cudaErrorInvalidConfiguration;
+  int ns = 6;
+  while (ns > 2 && (size_t)ns * stage + fixed + 8 * ns > 200 * 1024) --ns;
+  const size_t smem = (size_t)ns * stage + fixed + 8 * ns + 16;
+  if (smem > 227 * 1024) return cudaErrorInvalidConfiguration;
+  set_max_smem((const void*)k_bsweep_batch<MIX, RS>);
+  k_bsweep_batch<MIX, RS><<<total_ctas, threads, smem, st>>>(dev_args, dev_cta_off, nprob, ns);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_bsweep_batch(const BSweepArgs* host_args, const BSweepArgs* dev_args,
+                                const int* dev_cta_off, int nprob, int total_ctas, int mixed,
+                                cudaStream_t st) {
+  if (mixed) return launch_bb<true, 4>(host_args, dev_args, dev_cta_off, nprob, total_ctas, st);
+  return launch_bb<false, 4>(host_args, dev_args, dev_cta_off, nprob, total_ctas, st);
 }
 
 template <bool MIX, int RS>
