@@ -251,6 +251,48 @@ qoc_status qoc_batch_eval_grad_hess(qoc_batch* b, const double* thetas, double* 
 qoc_status qoc_batch_eval_grad_hess_dev(qoc_batch* b, const double* thetas_dev, double* outs_dev);
 void qoc_batch_destroy(qoc_batch* b);
 
+/* ---------------------------------------------------------------------------
+ * Gradient and Hessian assembly that allocates no device memory.
+ *
+ * The paper has no counterpart: this entry point exists for callers that
+ * cannot call cudaMalloc when they need the result (code running during a
+ * CUDA-graph capture that forbids allocation, frameworks whose memory pool
+ * owns all device memory, latency-bound loops that cannot take an
+ * allocation's implicit synchronisation).  It computes, from per-step
+ * contractions the caller already holds on the device (for example read back
+ * with qoc_read_buffer from a qoc_problem evaluated with the second-order
+ * adjoint Hessian),
+ *   grad = B^T (2 w_ctrl f + g),
+ *   Hess = sym( B^T diag(2 w_ctrl + c) B + B^T V + B^T U ),
+ * the same arithmetic as the assembly step of qoc_eval_grad_hess.
+ *
+ *   basis_dev   steps x K row-major binary64 (device)
+ *   f_dev, g_dev, c_dev   steps binary64 each (device)
+ *   U_dev, V_dev          steps x K row-major binary64 (device)
+ *   out_dev     1 + K + K*K binary64 (device): out[0] is not written, grad
+ *               at out[1..K], the symmetrised Hessian row-major after it
+ *   cuda_stream stream of the current device (NULL: legacy default stream);
+ *               the call enqueues and returns
+ * Intermediate partial sums go to one file-scope device array of
+ * QOC_NOALLOC_SCRATCH_DOUBLES doubles (4 MiB) that every GPU loading the
+ * library keeps until process exit.  The call needs
+ * qoc_assemble_noalloc_scratch_doubles(steps, K) of them and returns
+ * QOC_EINVAL (with the reason in qoc_last_error) when that is above the
+ * maximum, e.g. K = 64 allows steps <= 8000.  The first call on a device
+ * looks up the array's device address (once per device, the device
+ * current); make that first call before any stream capture.  All calls
+ * share the array and it keeps the previous call's contents (nothing needs
+ * clearing: each call writes every element it reads), so calls that may
+ * overlap on the GPU race: order them on one stream or with events.
+ * Errors: QOC_EINVAL (bad size, NULL pointer, too large), QOC_ECUDA.
+ * ------------------------------------------------------------------------- */
+#define QOC_NOALLOC_SCRATCH_DOUBLES 524288
+size_t qoc_assemble_noalloc_scratch_doubles(int steps, int K);
+qoc_status qoc_assemble_grad_hess_noalloc(int steps, int K, const double* basis_dev, const double* f_dev,
+                                          const double* g_dev, const double* c_dev, const double* U_dev,
+                                          const double* V_dev, double w_ctrl, double* out_dev,
+                                          void* cuda_stream);
+
 /* Bytes of device memory the problem holds. */
 size_t qoc_device_bytes(const qoc_problem* p);
 

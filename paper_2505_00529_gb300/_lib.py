@@ -30,7 +30,8 @@ EXPORTS = [
     "qoc_version", "qoc_set_target", "qoc_mlp_param_count", "qoc_mlp_create", "qoc_mlp_set_dataset",
     "qoc_mlp_train", "qoc_mlp_gradient", "qoc_mlp_predict", "qoc_mlp_get_params", "qoc_mlp_destroy",
     "qoc_last_error", "qoc_batch_create", "qoc_batch_set_graph", "qoc_batch_eval_grad_hess",
-    "qoc_batch_eval_grad_hess_dev", "qoc_batch_destroy",
+    "qoc_batch_eval_grad_hess_dev", "qoc_batch_destroy", "qoc_assemble_noalloc_scratch_doubles",
+    "qoc_assemble_grad_hess_noalloc",
 ]
 
 
@@ -103,6 +104,10 @@ def lib() -> C.CDLL:
         L.qoc_batch_eval_grad_hess_dev.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p]
         L.qoc_batch_destroy.argtypes = [C.c_void_p]
         L.qoc_batch_destroy.restype = None
+        L.qoc_assemble_noalloc_scratch_doubles.argtypes = [C.c_int, C.c_int]
+        L.qoc_assemble_noalloc_scratch_doubles.restype = C.c_size_t
+        L.qoc_assemble_grad_hess_noalloc.argtypes = [C.c_int, C.c_int] + [C.c_void_p] * 6 + [
+            C.c_double, C.c_void_p, C.c_void_p]
         _fp = C.POINTER(C.c_float)
         _ip = C.POINTER(C.c_int)
         L.qoc_mlp_param_count.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int]
@@ -353,6 +358,26 @@ def qoc_batch_eval_grad_hess_dev(b, thetas_dev_ptr: int, outs_dev_ptr: int):
 
 def qoc_batch_destroy(b):
     lib().qoc_batch_destroy(C.c_void_p(b))
+
+
+QOC_NOALLOC_SCRATCH_DOUBLES = 524288
+
+
+def qoc_assemble_noalloc_scratch_doubles(steps, K) -> int:
+    return int(lib().qoc_assemble_noalloc_scratch_doubles(int(steps), int(K)))
+
+
+def qoc_assemble_grad_hess_noalloc(steps, K, basis_dev, f_dev, g_dev, c_dev, U_dev, V_dev, w_ctrl,
+                                   out_dev, cuda_stream=None):
+    """Device pointers (ints); enqueues on cuda_stream and returns.  Uses the
+    library's fixed device scratch array instead of allocating."""
+    st = C.c_void_p(int(cuda_stream)) if cuda_stream else None
+    ptrs = [C.c_void_p(int(x)) if x else None for x in (basis_dev, f_dev, g_dev, c_dev, U_dev, V_dev)]
+    s = lib().qoc_assemble_grad_hess_noalloc(int(steps), int(K), *ptrs, float(w_ctrl),
+                                             C.c_void_p(int(out_dev)) if out_dev else None, st)
+    if s != QOC_OK:
+        reason = lib().qoc_last_error().decode()
+        raise QocError(s, "qoc_assemble_grad_hess_noalloc" + (f" [{reason}]" if reason and s != QOC_ECUDA else ""))
 
 
 def qoc_device_bytes(h) -> int:

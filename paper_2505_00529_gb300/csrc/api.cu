@@ -324,6 +324,9 @@ qoc_status eval_host(qoc_problem* p, const double* theta, int order, double* J, 
 
 }  // namespace
 
+// a non-CUDA failure reason for qoc_last_error (entry points in other files)
+void qoc::note_error(const char* msg) { std::snprintf(g_last_error, sizeof(g_last_error), "%s", msg); }
+
 extern "C" {
 
 int qoc_version(void) { return 100; }

@@ -146,4 +146,7 @@ cudaError_t launch_axpy(const double* x, const double* s, int K, double* y, cuda
 cudaError_t launch_tr_subproblem(const double* out_gh, int K, double radius, double* work,
                                  double* step, double* info, int* status, cudaStream_t st);
 
+// set the text qoc_last_error() returns on this thread
+void note_error(const char* msg);
+
 }  // namespace qoc
