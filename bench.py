@@ -32,9 +32,11 @@ UNIT = "evals/s"
 WORKLOAD = {"workload": "synthetic CI-shaped single problem, N=32 basis, K=64 sine/cosine "
                         "coefficients, J=4000 steps, T=20 (dt=0.005)",
             "N": 32, "K": 64, "J": 4000}
-# library kernel launches per evaluation: control, eig (Jacobi + refine), prep, state chain,
-# terminal, costate chain, pointwise, tangent panel, mu panel, grad, hess partial, hess final
-LAUNCHES_PER_EVAL = 13
+# library kernel launches per evaluation on the time-blocked path (block steps >= 2):
+# control, binary32 Jacobi, binary64 refinement, propagator increments, 2 block products,
+# state chain, state fill, terminal, costate chain, costate fill, derivative preparation,
+# pointwise, 2 x (block sources, panel chain, panel contraction), grad, hess partial, hess final
+LAUNCHES_PER_EVAL = 22
 FP64_PEAK_TFLOPS = 1.26    # 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (measured 1.20 at 1.99 GHz)
 FP32_PEAK_TFLOPS = 80.5    # 152 SMs x 128 FMA/clk x 2 flop x 2.07 GHz (measured 70 at 1.99 GHz)
 
@@ -167,19 +169,13 @@ class ClockSampler:
 # --------------------------------------------------------------------------
 # our arm
 # --------------------------------------------------------------------------
-def algorithmic_work(N, K, J, precision):
-    """Per-evaluation algorithmic work of each phase (flops), from the
-    method's counts: eig 9N^3, M~ 4N^3, second divided differences 4N^3
-    (one complex-by-real product), propagator-times-vector 8N^2 per vector
-    per step, panels 8N^2 K per step each."""
-    return {
-        "eig": ("alu64", 9.0 * N ** 3 * J),
-        "prep": ("alu64", 8.0 * N ** 3 * J),
-        "chains": ("alu32" if precision == "mixed" else "alu64", 2 * 8.0 * N * N * J),
-        "pointwise": ("alu64", 40.0 * N * N * J),
-        "panels": ("alu32" if precision == "mixed" else "alu64", 2 * 8.0 * N * N * K * J),
-        "assembly": ("alu64", 4.0 * K * K * J),
-    }
+def refine_flops(N, J, updates_per_step, rotated_fraction):
+    """Binary64 flops of one k_eig_refine launch: per step, u Ogita-Aishima
+    updates (H W: N^3 FMA, the W^T H W and W^T W triangles: N^3 FMA, W E: N^3
+    FMA), the final residual pass (2 N^3 FMA), and W V (N^3 FMA) when the
+    clean-up rotated; 2 flops per FMA."""
+    fma = (3.0 * updates_per_step + 2.0 + rotated_fraction) * N ** 3
+    return 2.0 * fma * J
 
 
 def run_ours(args):
@@ -227,7 +223,10 @@ def run_ours(args):
             ev[k][1].record(stream)
             if timing:
                 q.qoc_sync_status(P.handle)
-                phases.append(q.qoc_get_diagnostics(P.handle)["phase_ms"])
+                ph = q.qoc_get_diagnostics(P.handle)["phase_ms"]
+                ph.update({"k_" + k: v for k, v in q.qoc_get_phase_times(P.handle).items()})
+                ph.update(q.qoc_get_eig_stats(P.handle))
+                phases.append(ph)
         torch.cuda.synchronize()
         q.qoc_sync_status(P.handle)
         ms = statistics.mean(a.elapsed_time(b) for a, b in ev)
@@ -285,20 +284,24 @@ def run_ours(args):
               "n_eval_gh": info["n_eval_gh"], "n_eval_J": info["n_eval_J"], "J": info["J"],
               "grad_norm": info["grad_norm"], "stop": info["stop"], "gtol": 1e-6}
 
-    # ---- roofline of the dominant phase ----
+    # ---- roofline of the dominant kernel (k_eig_refine: timed by events around its launch) ----
     ph_mean = {k: statistics.mean(p[k] for p in phases) for k in phases[0]} if phases else {}
-    work = algorithmic_work(N, K, J, args.precision)
     roof = None
     if ph_mean:
-        dom = max(ph_mean, key=lambda k: ph_mean[k])
-        unit_kind, flops = work[dom]
-        peak = FP64_PEAK_TFLOPS if unit_kind == "alu64" else FP32_PEAK_TFLOPS
-        ach = flops / (ph_mean[dom] * 1e-3) / 1e12
-        roof = {"bound": "alu", "kernel": dom, "achieved": ach, "peak": peak, "unit": "TFLOP/s",
-                "frac": ach / peak, "traffic": None,
-                "peak_source": ("binary64 FMA rate" if unit_kind == "alu64" else "binary32 FMA rate")
-                + " from unit counts x max SM clock (see DESIGN.md); not in MEASURED_PEAKS.json",
-                "phase_ms": ph_mean}
+        u, rot = ph_mean["refine_updates_per_step"], ph_mean["cleanup_rotated_fraction"]
+        t_ref = ph_mean["k_eig_refine"]
+        flops = refine_flops(N, J, u, rot)
+        ach = flops / (t_ref * 1e-3) / 1e12
+        roof = {"bound": "alu", "kernel": "k_eig_refine", "achieved": ach, "peak": FP64_PEAK_TFLOPS,
+                "unit": "TFLOP/s", "frac": ach / FP64_PEAK_TFLOPS, "traffic": None,
+                "peak_source": "binary64 FMA rate from unit counts x max SM clock (152 SMs x 2 DFMA/clk "
+                               "x 2 x 2.07 GHz); MEASURED_PEAKS.json has no binary64 figure",
+                "algorithmic": f"(3u + 2 + r) N^3 FMA per step, u = {u:.3f} updates/step, "
+                               f"r = {rot:.3f} clean-up rotated fraction, N={N}, J={J}",
+                "kernel_ms": t_ref,
+                "phase_ms": {k: v for k, v in ph_mean.items() if not k.startswith("k_") and k in
+                             ("eig", "prep", "chains", "pointwise", "panels", "assembly")},
+                "kernel_phase_ms": {k[2:]: v for k, v in ph_mean.items() if k.startswith("k_")}}
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -362,6 +365,117 @@ def run_warm_start(args):
     return 0
 
 
+def run_batch(args):
+    """Batching pattern: uneven problems drawn from the batched-workload
+    recipe (N from {8,...,128} step 8, K from {16,32,64,128}, J from
+    {2000,4000,8000}, per-problem seeds), keeping the draws with N <= the
+    library's maximum basis size; one batched evaluation (graph replay) vs
+    the same problems evaluated one after another on one stream."""
+    import numpy as np
+    import torch
+    import paper_2505_00529_gb300 as q
+    from paper_2505_00529_gb300 import build, inputs
+    local = env_int("LOCAL_RANK", 0)
+    torch.cuda.set_device(local)
+    build.build()
+    dev = torch.device("cuda", local)
+    nmax = q.qoc_max_basis_size()
+    probs, i = [], 0
+    while len(probs) < args.batch_size:
+        pr = inputs.config_problem(3, i)
+        i += 1
+        if pr.N <= nmax:
+            probs.append(pr)
+    prec = q.QOC_MIXED_FP32 if args.precision == "mixed" else q.QOC_FP64
+    stream = torch.cuda.Stream(device=dev)
+    torch.cuda.set_stream(stream)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    Ps = [q.Problem(pr, precision=prec) for pr in probs]
+    thetas = [inputs.eval_theta(pr.K, 7 + k) for k, pr in enumerate(probs)]
+    b = q.Batch(Ps, cuda_stream=stream.cuda_stream)
+    th = torch.tensor(np.concatenate(thetas), dtype=torch.float64, device=dev)
+    out = torch.zeros(b.n_out, dtype=torch.float64, device=dev)
+
+    def timed(fn, steps, warmup):
+        for _ in range(warmup):
+            fn()
+        torch.cuda.synchronize()
+        ts = []
+        for k in range(steps):
+            flush.fill_(float(k))
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            ts.append((e0, e1))
+        torch.cuda.synchronize()
+        return statistics.mean(a.elapsed_time(c) for a, c in ts)
+
+    def batched():
+        q.qoc_batch_eval_grad_hess_dev(b.handle, th.data_ptr(), out.data_ptr())
+
+    # sequential: each problem on its own library stream, serialised by the host
+    th_i = [torch.tensor(t, dtype=torch.float64, device=dev) for t in thetas]
+    out_i = [torch.zeros(1 + pr.K + pr.K ** 2, dtype=torch.float64, device=dev) for pr in probs]
+
+    def sequential():        # one problem after another
+        for P, t, o in zip(Ps, th_i, out_i):
+            q.qoc_eval_grad_hess_dev(P.handle, t.data_ptr(), o.data_ptr())
+            q.qoc_sync_status(P.handle)
+
+    def streams():           # every problem enqueued on its own stream, no batched sweeps
+        for P, t, o in zip(Ps, th_i, out_i):
+            q.qoc_eval_grad_hess_dev(P.handle, t.data_ptr(), o.data_ptr())
+        for P in Ps:
+            q.qoc_sync_status(P.handle)
+
+    def wall(fn, steps):
+        fn()
+        torch.cuda.synchronize()
+        ts = []
+        for k in range(steps):
+            flush.fill_(float(k))
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            fn()
+            torch.cuda.synchronize()
+            ts.append(1000.0 * (time.perf_counter() - t0))
+        return statistics.mean(ts)
+
+    clk = ClockSampler(local, os.path.join(ROOT, "gpurun_out" if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else ".", "clocks_batch.csv"))
+    with clk:
+        ms_b = timed(batched, args.steps, args.warmup)
+    for P in Ps:
+        q.qoc_sync_status(P.handle)
+    ms_s = wall(sequential, max(1, args.steps // 4))
+    ms_c = wall(streams, max(1, args.steps // 4))
+    # the batched results equal each problem's own evaluation
+    res = b.split(out.cpu().numpy())
+    worst = 0.0
+    for k in range(0, len(Ps), max(1, len(Ps) // 8)):
+        Jk, gk, Hk = Ps[k].eval_grad_hess(thetas[k])
+        worst = max(worst, float(np.linalg.norm(res[k][2] - Hk) / np.linalg.norm(Hk)))
+    b.close()
+    shapes = [(pr.N, pr.K, pr.J) for pr in probs]
+    line = {"metric": "batched grad+Hessian evaluations/s over uneven problems", "value": len(Ps) * 1000.0 / ms_b,
+            "unit": "problem evals/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms_b, "higher_is_better": True,
+            "dtype": "f32 panels + f64" if prec == q.QOC_MIXED_FP32 else "f64", "data": "synthetic",
+            "config": {"workload": f"{len(Ps)} uneven problems from the batched-workload recipe with N <= {nmax}",
+                       "N_range": [min(x[0] for x in shapes), max(x[0] for x in shapes)],
+                       "K_values": sorted({x[1] for x in shapes}), "J_values": sorted({x[2] for x in shapes}),
+                       "total_steps": sum(x[2] for x in shapes), "l2": "flushed between timed steps",
+                       "graph": True},
+            "sequential_ms": ms_s, "speedup_over_sequential": ms_s / ms_b,
+            "separate_streams_ms": ms_c, "speedup_over_separate_streams": ms_c / ms_b,
+            "batched_vs_individual_hess_rel_max": worst, "clocks": clk.summary(),
+            "device_bytes": sum(q.qoc_device_bytes(P.handle) for P in Ps)}
+    for P in Ps:
+        P.close()
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -374,6 +488,8 @@ def main():
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-tr", action="store_true")
     ap.add_argument("--warm-start", action="store_true", help="run the learned warm-start experiment")
+    ap.add_argument("--batch", action="store_true", help="run the batched uneven-problem measurement")
+    ap.add_argument("--batch-size", type=int, default=256)
     ap.add_argument("--ws-train", type=int, default=2000)
     ap.add_argument("--ws-test", type=int, default=200)
     ap.add_argument("--ws-epochs", type=int, default=300)
@@ -382,6 +498,8 @@ def main():
     args = ap.parse_args()
     if args.warm_start:
         return run_warm_start(args)
+    if args.batch:
+        return run_batch(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)

@@ -165,6 +165,26 @@ qoc_status qoc_trust_region_solve(qoc_problem* p, const double* theta0,
  *   out[2..7] = milliseconds of the phases eig, prep, chains, pointwise,
  *               panels, assembly (only when timing was enabled, else 0). */
 qoc_status qoc_get_diagnostics(const qoc_problem* p, double* out /* [8] */);
+
+/* Per-kernel timing of the last evaluation (timing enabled), milliseconds
+ * between events on the problem's stream, in this order:
+ *   0 control (f = B theta)         1 binary32 Jacobi (k_eig_jacobi)
+ *   2 binary64 refinement or the binary64 Jacobi (k_eig_refine / k_eig_jacobi)
+ *   3 propagator increments D_j     4 derivative preparation (M~, Gamma1, X'),
+ *                                     concurrent with the chains
+ *   5 wait for the state/costate chains after 4
+ *   6 pointwise contractions        7 tangent and second-order adjoint panels
+ *   8 gradient/Hessian assembly
+ * Writes min(n, QOC_N_PHASES) values. */
+#define QOC_N_PHASES 9
+qoc_status qoc_get_phase_times(const qoc_problem* p, double* out, int n);
+
+/* Work counters of the last evaluation's refined eigensolver (timing
+ * enabled; 0 otherwise), after the evaluation has completed:
+ *   out[0] = mean binary64 Ogita-Aishima updates per step
+ *   out[1] = fraction of steps whose binary64 Jacobi clean-up rotated
+ * Synchronises the problem's stream. */
+qoc_status qoc_get_eig_stats(qoc_problem* p, double* out /* [2] */);
 qoc_status qoc_enable_timing(qoc_problem* p, int on);
 
 /* Copy an intermediate of the last evaluation to the host, for parity

@@ -31,7 +31,7 @@ EXPORTS = [
     "qoc_mlp_train", "qoc_mlp_gradient", "qoc_mlp_predict", "qoc_mlp_get_params", "qoc_mlp_destroy",
     "qoc_last_error", "qoc_batch_create", "qoc_batch_set_graph", "qoc_batch_eval_grad_hess",
     "qoc_batch_eval_grad_hess_dev", "qoc_batch_destroy", "qoc_assemble_noalloc_scratch_doubles",
-    "qoc_assemble_grad_hess_noalloc",
+    "qoc_assemble_grad_hess_noalloc", "qoc_get_phase_times", "qoc_get_eig_stats",
 ]
 
 
@@ -85,6 +85,8 @@ def lib() -> C.CDLL:
         L.qoc_trust_region_solve.argtypes = [C.c_void_p, _dp, C.POINTER(TrOptions), _dp,
                                              C.POINTER(TrReport)]
         L.qoc_get_diagnostics.argtypes = [C.c_void_p, _dp]
+        L.qoc_get_phase_times.argtypes = [C.c_void_p, _dp, C.c_int]
+        L.qoc_get_eig_stats.argtypes = [C.c_void_p, _dp]
         L.qoc_enable_timing.argtypes = [C.c_void_p, C.c_int]
         L.qoc_read_buffer.argtypes = [C.c_void_p, C.c_int, _dp, C.c_size_t]
         L.qoc_device_bytes.argtypes = [C.c_void_p]
@@ -241,6 +243,22 @@ def qoc_get_diagnostics(h):
     _check(lib().qoc_get_diagnostics(C.c_void_p(h), _ptr(out)), "qoc_get_diagnostics")
     return {"norm_drift": out[0], "hess_asym": out[1],
             "phase_ms": dict(zip(["eig", "prep", "chains", "pointwise", "panels", "assembly"], out[2:]))}
+
+
+PHASES = ["control", "eig_jacobi", "eig_refine", "prep_D", "deriv_prep", "chains_wait", "pointwise",
+          "panels", "assembly"]
+
+
+def qoc_get_phase_times(h):
+    out = np.zeros(len(PHASES))
+    _check(lib().qoc_get_phase_times(C.c_void_p(h), _ptr(out), len(PHASES)), "qoc_get_phase_times")
+    return dict(zip(PHASES, out))
+
+
+def qoc_get_eig_stats(h):
+    out = np.zeros(2)
+    _check(lib().qoc_get_eig_stats(C.c_void_p(h), _ptr(out)), "qoc_get_eig_stats")
+    return {"refine_updates_per_step": out[0], "cleanup_rotated_fraction": out[1]}
 
 
 def qoc_read_buffer(h, which, shape, complex_=False):

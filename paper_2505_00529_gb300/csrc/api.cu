@@ -44,8 +44,9 @@ struct qoc_problem {
                                         // while the binary64 derivative preparation fills the GPU
   cudaEvent_t fork = nullptr, join = nullptr;
   int timing = 0;
-  cudaEvent_t ev[8] = {};
+  cudaEvent_t ev[10] = {};
   double phase_ms[6] = {0, 0, 0, 0, 0, 0};
+  double kphase_ms[QOC_N_PHASES] = {};
   double diag[2] = {0, 0};
   int last_order = -1;
   size_t dstride = 0, vstride = 0, dev_bytes = 0;
@@ -56,6 +57,7 @@ struct qoc_problem {
   double *f = nullptr, *W = nullptr, *eig = nullptr, *g = nullptr, *c = nullptr;
   double *V = nullptr, *U = nullptr, *work = nullptr, *out = nullptr, *out_trial = nullptr;
   double *hess_raw = nullptr, *scal = nullptr;
+  unsigned int* eigstats = nullptr;     // refinement counters (timing mode)
   double2 *alpha = nullptr, *beta = nullptr, *Ptil = nullptr, *Xp = nullptr, *SJ = nullptr,
           *lamJ = nullptr;
   void *D = nullptr, *a_hat = nullptr, *l_hat = nullptr, *p_hat = nullptr, *y_hat = nullptr;
@@ -167,7 +169,10 @@ qoc_status enqueue_blocked(qoc_problem* p, int order, double* out_dev) {
                           p->lamJ, p->scal + 0, p->scal + 1, cs));
   QOC_TRY(cudaMemcpyAsync(out_dev, p->scal, sizeof(double), cudaMemcpyDeviceToDevice, cs));
   if (order == 0) {
-    if (p->timing) for (int k = 3; k < 7; ++k) cudaEventRecord(p->ev[k], st);
+    if (p->timing) {
+      cudaEventRecord(p->ev[9], st);
+      for (int k = 3; k < 7; ++k) cudaEventRecord(p->ev[k], st);
+    }
     return QOC_OK;
   }
   BSweepArgs l = a;
@@ -178,6 +183,7 @@ qoc_status enqueue_blocked(qoc_problem* p, int order, double* out_dev) {
   QOC_TRY(cudaEventRecord(p->join, cs));
   QOC_TRY(launch_prep(p->W, p->eig, p->M, N, J, p->dt, p->mshift, p->D, p->dstride, mixed ? 0 : 1,
                       2, p->Ptil, p->Xp, p->status, st));
+  if (p->timing) cudaEventRecord(p->ev[9], st);
   QOC_TRY(cudaStreamWaitEvent(st, p->join, 0));
   if (p->timing) cudaEventRecord(p->ev[3], st);
   const double2 kappa = cexpi_h(p->dt * p->mshift);
@@ -225,9 +231,14 @@ qoc_status enqueue_eval(qoc_problem* p, const double* theta_dev, int order, doub
   const int d_fp64 = mixed ? 0 : 1;
   if (p->timing) cudaEventRecord(p->ev[0], st);
   QOC_TRY(launch_control(p->B, p->Kp, theta_dev, J, K, p->f, st));
+  if (p->timing) {
+    cudaEventRecord(p->ev[7], st);
+    QOC_TRY(cudaMemsetAsync(p->eigstats, 0, 2 * sizeof(unsigned int), st));
+  }
   QOC_TRY(launch_eig(p->H0, p->M, p->f, N, J, p->W, p->eig, p->status,
                      p->eig_method == QOC_EIG_JACOBI_FP64 ? EIG_JACOBI_FP64 : EIG_REFINED,
-                     p->refine_sweeps, p->angle_tol, st));
+                     p->refine_sweeps, p->angle_tol, st, p->timing ? p->ev[8] : nullptr,
+                     p->timing ? p->eigstats : nullptr));
   if (p->timing) cudaEventRecord(p->ev[1], st);
   QOC_TRY(launch_prep(p->W, p->eig, p->M, N, J, p->dt, p->mshift, p->D, p->dstride, d_fp64, 1,
                       p->Ptil, p->Xp, p->status, st));
@@ -237,6 +248,7 @@ qoc_status enqueue_eval(qoc_problem* p, const double* theta_dev, int order, doub
   if (order >= 1)
     QOC_TRY(launch_prep(p->W, p->eig, p->M, N, J, p->dt, p->mshift, p->D, p->dstride, d_fp64, 2,
                         p->Ptil, p->Xp, p->status, st));
+  if (p->timing) cudaEventRecord(p->ev[9], st);
   SweepArgs a{};
   a.N = N; a.K = 1; a.Kp = p->Kp; a.J = J; a.kc = 1; a.backward = 0;
   a.D = reinterpret_cast<const unsigned char*>(p->D); a.dstride = p->dstride;
@@ -286,6 +298,14 @@ void collect_timing(qoc_problem* p) {
   for (int k = 0; k < 6; ++k) {
     float ms = 0;
     if (cudaEventElapsedTime(&ms, p->ev[k], p->ev[k + 1]) == cudaSuccess) p->phase_ms[k] = ms;
+  }
+  // event order on the main stream: 0 start, 7 control, 8 binary32 Jacobi, 1 refinement,
+  // 2 propagator increments, 9 derivative preparation, 3 chains joined, 4, 5, 6
+  static const int from[QOC_N_PHASES] = {0, 7, 8, 1, 2, 9, 3, 4, 5};
+  static const int to[QOC_N_PHASES] = {7, 8, 1, 2, 9, 3, 4, 5, 6};
+  for (int k = 0; k < QOC_N_PHASES; ++k) {
+    float ms = 0;
+    if (cudaEventElapsedTime(&ms, p->ev[from[k]], p->ev[to[k]]) == cudaSuccess) p->kphase_ms[k] = ms;
   }
 }
 
@@ -443,6 +463,7 @@ qoc_status qoc_create_problem(int N, const double* H0, const double* M, const do
   ALLOC(p->out_trial, 8 * (1 + (size_t)K + (size_t)K * K));
   ALLOC(p->hess_raw, 8 * (size_t)K * K);
   ALLOC(p->scal, 8 * 8);
+  ALLOC(p->eigstats, 2 * sizeof(unsigned int));
   ALLOC(p->alpha, 16 * (size_t)N);
   ALLOC(p->beta, 16 * (size_t)N);
   ALLOC(p->lamJ, 16 * (size_t)N);
@@ -578,6 +599,22 @@ qoc_status qoc_get_diagnostics(const qoc_problem* p, double* out) {
   out[0] = p->diag[0];
   out[1] = p->diag[1];
   for (int k = 0; k < 6; ++k) out[2 + k] = p->timing ? p->phase_ms[k] : 0.0;
+  return QOC_OK;
+}
+
+qoc_status qoc_get_eig_stats(qoc_problem* p, double* out) {
+  if (!p || !out) return QOC_EINVAL;
+  unsigned int h[2] = {0, 0};
+  QOC_TRY(cudaMemcpyAsync(h, p->eigstats, sizeof(h), cudaMemcpyDeviceToHost, p->stream));
+  QOC_TRY(cudaStreamSynchronize(p->stream));
+  out[0] = p->timing ? (double)h[0] / p->J : 0.0;
+  out[1] = p->timing ? (double)h[1] / p->J : 0.0;
+  return QOC_OK;
+}
+
+qoc_status qoc_get_phase_times(const qoc_problem* p, double* out, int n) {
+  if (!p || !out || n < 0) return QOC_EINVAL;
+  for (int k = 0; k < n && k < QOC_N_PHASES; ++k) out[k] = p->timing ? p->kphase_ms[k] : 0.0;
   return QOC_OK;
 }
 

@@ -213,7 +213,7 @@ __global__ void k_eig_jacobi(const double* __restrict__ H0, const double* __rest
 __global__ void k_eig_refine(const double* __restrict__ H0, const double* __restrict__ M,
                              const double* __restrict__ f, int N, int J, int sweeps,
                              double angle_tol, double* __restrict__ W_io,
-                             double* __restrict__ eig_out, int* status) {
+                             double* __restrict__ eig_out, int* status, unsigned int* stats) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int j = blockIdx.x;
   if (j >= J) return;
@@ -302,12 +302,19 @@ __global__ void k_eig_refine(const double* __restrict__ H0, const double* __rest
     }
     __syncthreads();
     const double delta = red[41];
-    if (red[42] <= orth_tol) break;
-    if (it >= sweeps) {   // sweep budget spent: flag only a real failure
-      if (tid == 0 && !(red[42] <= 1e-10)) raise_status(status, DEV_EIG_NOCONV);
+    if (red[42] <= orth_tol || it >= sweeps) {
+      // sweep budget spent: flag only a real failure
+      if (red[42] > orth_tol && tid == 0 && !(red[42] <= 1e-10)) raise_status(status, DEV_EIG_NOCONV);
+      if (stats && tid == 0) atomicAdd(&stats[0], (unsigned int)it);
       break;
     }
-    // E overwrites T
+    // E overwrites T.  A pair counts as separated only if it is outside the
+    // cluster threshold AND its first-order correction is small (|S_ik| <=
+    // kLinear |gap|): a binary32 start can mix two close eigenvectors by a
+    // large angle (near an avoided crossing), where the linearised update
+    // would destroy orthogonality.  Such pairs only get the orthogonality
+    // part R/2 here; the binary64 Jacobi clean-up rotates them exactly.
+    constexpr double kLinear = 1e-3;
     for (int e = tid; e < N * N; e += nt) {
       const int i = e / N, k = e % N;
       const double rik = R[i * ld + k];
@@ -315,7 +322,9 @@ __global__ void k_eig_refine(const double* __restrict__ H0, const double* __rest
       if (i == k) eik = 0.5 * rik;
       else {
         const double gap = lam[k] - lam[i];
-        eik = fabs(gap) > delta ? (S[i * ld + k] + lam[k] * rik) / gap : 0.5 * rik;
+        const double sik = S[i * ld + k];
+        eik = (fabs(gap) > delta && fabs(sik) <= kLinear * fabs(gap)) ? (sik + lam[k] * rik) / gap
+                                                                       : 0.5 * rik;
       }
       T[i * ld + k] = eik;
     }
@@ -348,6 +357,7 @@ __global__ void k_eig_refine(const double* __restrict__ H0, const double* __rest
     if (R[i * ld + k] != ((i == k) ? 1.0 : 0.0)) any_rot = 1;
   }
   __syncthreads();
+  if (stats && tid == 0 && any_rot) atomicAdd(&stats[1], 1u);
   if (any_rot) {   // W <- W V (T as scratch)
     for (int e = tid; e < N * N; e += nt) {
       const int i = e / N, k = e % N;
@@ -384,7 +394,7 @@ size_t eig_smem_bytes(int N, int method) {
 
 cudaError_t launch_eig(const double* H0, const double* M, const double* f, int N, int J,
                        double* W, double* eig, int* status, int method, int refine_sweeps,
-                       double angle_tol, cudaStream_t st) {
+                       double angle_tol, cudaStream_t st, cudaEvent_t mid, unsigned int* stats) {
   // Jacobi rounds are barrier-bound: few warps per (small) matrix, many CTAs per SM
   const int jthreads = N <= 32 ? 64 : (N <= 64 ? 128 : 256);
   const int threads = N <= 16 ? 128 : 256;   // refinement: binary64-throughput bound
@@ -392,6 +402,7 @@ cudaError_t launch_eig(const double* H0, const double* M, const double* f, int N
     size_t sm = jacobi_smem(N, 8);
     set_max_smem((const void*)k_eig_jacobi<double>);
     k_eig_jacobi<double><<<J, jthreads, sm, st>>>(H0, M, f, N, J, W, eig, status);
+    if (mid) cudaEventRecord(mid, st);
     return cudaGetLastError();
   }
   size_t sm = jacobi_smem(N, 4);
@@ -399,9 +410,11 @@ cudaError_t launch_eig(const double* H0, const double* M, const double* f, int N
   k_eig_jacobi<float><<<J, jthreads, sm, st>>>(H0, M, f, N, J, W, eig, status);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
+  if (mid) cudaEventRecord(mid, st);
   size_t sr = refine_smem(N);
   set_max_smem((const void*)k_eig_refine);
-  k_eig_refine<<<J, threads, sr, st>>>(H0, M, f, N, J, refine_sweeps, angle_tol, W, eig, status);
+  k_eig_refine<<<J, threads, sr, st>>>(H0, M, f, N, J, refine_sweeps, angle_tol, W, eig, status,
+                                       stats);
   return cudaGetLastError();
 }
 

@@ -47,11 +47,13 @@ enum { PREC_FP64 = 0, PREC_MIXED = 1 };
 constexpr double TAU_DD2 = 1e-3;
 
 size_t eig_smem_bytes(int N, int method);
+// stats (optional, device): [0] += refinement updates, [1] += steps whose clean-up rotated
 // method EIG_REFINED: binary32 Jacobi, `refine_sweeps` binary64 Ogita-Aishima
 // sweeps, then binary64 Jacobi clean-up rotating only angles above angle_tol.
 cudaError_t launch_eig(const double* H0, const double* M, const double* f, int N, int J,
                        double* W, double* eig, int* status, int method, int refine_sweeps,
-                       double angle_tol, cudaStream_t st);
+                       double angle_tol, cudaStream_t st, cudaEvent_t mid = nullptr,
+                       unsigned int* stats = nullptr);
 
 size_t prep_smem_bytes(int N);
 // parts (bit mask): 1 -> D_j = W diag(exp(-i dt (lambda - m)) - 1) W^T

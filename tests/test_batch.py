@@ -127,3 +127,21 @@ def test_batch_validation():
     finally:
         for P in (P1, P2, P3):
             P.close()
+
+
+@pytest.mark.parametrize("precision", [q.QOC_FP64, q.QOC_MIXED_FP32], ids=["fp64", "mixed"])
+def test_batched_workload_avoided_crossing(precision):
+    """A problem of the batched-workload recipe (N=48, K=32, J=4000) whose
+    trajectory passes an avoided crossing (eigenvalue gap 3e-5 against
+    |H| ~ 50 at one step): the refined eigensolver must succeed and agree
+    with the binary64 Jacobi eigensolver path."""
+    pr = inputs.config_problem(3, 344)
+    assert (pr.N, pr.K, pr.J) == (48, 32, 4000)
+    th = inputs.eval_theta(pr.K, 167)
+    with q.Problem(pr, precision=q.QOC_FP64, eig_method=q.QOC_EIG_JACOBI_FP64) as P:
+        J0, g0, H0 = P.eval_grad_hess(th)
+    with q.Problem(pr, precision=precision) as P:
+        J1, g1, H1 = P.eval_grad_hess(th)
+    tol = TOL[precision]
+    assert abs(J1 - J0) <= tol * abs(J0)
+    assert rel(g1, g0) <= tol and rel(H1, H0) <= tol, (rel(g1, g0), rel(H1, H0))

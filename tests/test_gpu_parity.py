@@ -116,6 +116,36 @@ def test_zero_control_and_degenerate_spectrum():
 
 
 @pytest.mark.parametrize("precision", [q.QOC_FP64, q.QOC_MIXED_FP32], ids=["fp64", "mixed"])
+def test_avoided_crossing(precision):
+    """A step lands exactly on an avoided crossing (gap 2e-6 against |H| ~ 5):
+    levels 0 and 1 of H0 + f M cross at f = 1 with coupling 1e-6, the whole
+    system rotated by a random orthogonal Q so every entry is dense.  The
+    binary32 eigenvector start mixes the close pair by a large angle there."""
+    rng = np.random.default_rng(77)
+    N, K, J, dt, c = 8, 3, 120, 0.02, 1e-6
+    A = rng.normal(0.0, 0.05, (N - 2, N - 2))
+    H0 = np.zeros((N, N)); M = np.zeros((N, N))
+    H0[:2, :2] = [[0.0, c], [c, 1.0]]
+    M[:2, :2] = [[0.0, 0.0], [0.0, -1.0]]
+    H0[2:, 2:] = np.diag(np.linspace(2.0, 5.0, N - 2)) + (A + A.T) / 2
+    Bm = rng.normal(0.0, 0.3, (N - 2, N - 2))
+    M[2:, 2:] = (Bm + Bm.T) / 2
+    Q, _ = np.linalg.qr(rng.normal(size=(N, N)))
+    H0 = Q @ H0 @ Q.T; H0 = (H0 + H0.T) / 2
+    M = Q @ M @ Q.T; M = (M + M.T) / 2
+    j = np.arange(J)
+    B = np.stack([j / (J // 2), np.sin(np.pi * j / J), np.sin(2 * np.pi * j / J)], axis=1)
+    alpha = np.zeros(N, complex); alpha[0] = 1.0
+    beta = rng.normal(size=N) + 1j * rng.normal(size=N); beta /= np.linalg.norm(beta)
+    prob = inputs.Problem(H0, M, alpha, beta, B, dt, dt, 1.0, name="avoided-crossing")
+    theta = np.array([1.0, 0.0, 0.0])      # f at step J/2 is exactly 1
+    lam = np.linalg.eigvalsh(H0 + M)
+    assert np.diff(lam).min() < 3e-6
+    check_eval(prob, theta, precision)
+    check_eval(prob, np.array([1.0, 0.3, -0.2]), precision)
+
+
+@pytest.mark.parametrize("precision", [q.QOC_FP64, q.QOC_MIXED_FP32], ids=["fp64", "mixed"])
 def test_config1_full_size(precision):
     prob = inputs.config_problem(1)
     for seed in (0, 1):
