@@ -169,12 +169,13 @@ class ClockSampler:
 # --------------------------------------------------------------------------
 # our arm
 # --------------------------------------------------------------------------
-def refine_flops(N, J, updates_per_step, rotated_fraction):
+def refine_flops(N, J, updates_per_step, rotated_fraction, final_fraction):
     """Binary64 flops of one k_eig_refine launch: per step, u Ogita-Aishima
     updates (H W: N^3 FMA, the W^T H W and W^T W triangles: N^3 FMA, W E: N^3
-    FMA), the final residual pass (2 N^3 FMA), and W V (N^3 FMA) when the
-    clean-up rotated; 2 flops per FMA."""
-    fma = (3.0 * updates_per_step + 2.0 + rotated_fraction) * N ** 3
+    FMA), the final residual pass (2 N^3 FMA) on the steps that take it
+    (fraction p; the others finish early), and W V (N^3 FMA) when the clean-up
+    rotated (fraction r); 2 flops per FMA."""
+    fma = (3.0 * updates_per_step + 2.0 * final_fraction + rotated_fraction) * N ** 3
     return 2.0 * fma * J
 
 
@@ -201,8 +202,15 @@ def run_ours(args):
     torch.cuda.set_stream(stream)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # > L2 (129 MB)
 
+    from paper_2505_00529_gb300 import autotune
+    tuned = {}
+
     def measure(precision, steps, warmup, timing=True):
+        if not args.no_autotune and precision not in tuned:
+            tuned[precision] = autotune.tune(prob, precision, evals=3, theta=theta)
         P = q.Problem(prob, precision=precision, cuda_stream=stream.cuda_stream)
+        if precision in tuned:
+            autotune.apply(P, tuned[precision])
         if timing:
             q.qoc_enable_timing(P.handle, True)
         th = torch.tensor(theta, dtype=torch.float64, device=dev)
@@ -289,15 +297,17 @@ def run_ours(args):
     roof = None
     if ph_mean:
         u, rot = ph_mean["refine_updates_per_step"], ph_mean["cleanup_rotated_fraction"]
+        fin = ph_mean["final_pass_fraction"]
         t_ref = ph_mean["k_eig_refine"]
-        flops = refine_flops(N, J, u, rot)
+        flops = refine_flops(N, J, u, rot, fin)
         ach = flops / (t_ref * 1e-3) / 1e12
         roof = {"bound": "alu", "kernel": "k_eig_refine", "achieved": ach, "peak": FP64_PEAK_TFLOPS,
                 "unit": "TFLOP/s", "frac": ach / FP64_PEAK_TFLOPS, "traffic": None,
                 "peak_source": "binary64 FMA rate from unit counts x max SM clock (152 SMs x 2 DFMA/clk "
                                "x 2 x 2.07 GHz); MEASURED_PEAKS.json has no binary64 figure",
-                "algorithmic": f"(3u + 2 + r) N^3 FMA per step, u = {u:.3f} updates/step, "
-                               f"r = {rot:.3f} clean-up rotated fraction, N={N}, J={J}",
+                "algorithmic": f"(3u + 2p + r) N^3 FMA per step, u = {u:.3f} updates/step, "
+                               f"p = {fin:.3f} final-pass fraction, r = {rot:.3f} clean-up rotated "
+                               f"fraction, N={N}, J={J}",
                 "kernel_ms": t_ref,
                 "phase_ms": {k: v for k, v in ph_mean.items() if not k.startswith("k_") and k in
                              ("eig", "prep", "chains", "pointwise", "panels", "assembly")},
@@ -317,7 +327,11 @@ def run_ours(args):
                 "dtype": "f32 panels + f64" if prec == q.QOC_MIXED_FP32 else "f64",
                 "data": "synthetic",
                 "config": dict(WORKLOAD, precision=args.precision, l2="flushed between timed steps",
-                               parallelism=f"replicas x{world}" if world > 1 else "single problem"),
+                               parallelism=f"replicas x{world}" if world > 1 else "single problem",
+                               launch=({"block_steps": tuned[prec]["block_steps"],
+                                        "panel_columns": tuned[prec]["panel_columns"],
+                                        "autotune_table_ms": tuned[prec]["table"]}
+                                       if prec in tuned else "library defaults")),
                 "e2e": {"value": world * 1000.0 / e2e_ms, "unit": UNIT, "ms_per_step": e2e_ms,
                         "h2d_bytes_per_step": 8 * K, "d2h_bytes_per_step": 8 * (1 + K + K * K)},
                 "gpu_launches": LAUNCHES_PER_EVAL * args.steps,
@@ -392,6 +406,14 @@ def run_batch(args):
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     Ps = [q.Problem(pr, precision=prec) for pr in probs]
     thetas = [inputs.eval_theta(pr.K, 7 + k) for k, pr in enumerate(probs)]
+    tune_s = None
+    if not args.no_autotune:
+        from paper_2505_00529_gb300 import autotune
+        t0 = time.perf_counter()
+        cfgs = autotune.tune_batch(probs, prec, evals=2)
+        tune_s = time.perf_counter() - t0
+        for P, cfg in zip(Ps, cfgs):
+            autotune.apply(P, cfg)
     b = q.Batch(Ps, cuda_stream=stream.cuda_stream)
     th = torch.tensor(np.concatenate(thetas), dtype=torch.float64, device=dev)
     out = torch.zeros(b.n_out, dtype=torch.float64, device=dev)
@@ -465,7 +487,7 @@ def run_batch(args):
                        "N_range": [min(x[0] for x in shapes), max(x[0] for x in shapes)],
                        "K_values": sorted({x[1] for x in shapes}), "J_values": sorted({x[2] for x in shapes}),
                        "total_steps": sum(x[2] for x in shapes), "l2": "flushed between timed steps",
-                       "graph": True},
+                       "graph": True, "autotuned": tune_s is not None, "autotune_seconds": tune_s},
             "sequential_ms": ms_s, "speedup_over_sequential": ms_s / ms_b,
             "separate_streams_ms": ms_c, "speedup_over_separate_streams": ms_c / ms_b,
             "batched_vs_individual_hess_rel_max": worst, "clocks": clk.summary(),
@@ -487,6 +509,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-tr", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true", help="library default launch shapes")
     ap.add_argument("--warm-start", action="store_true", help="run the learned warm-start experiment")
     ap.add_argument("--batch", action="store_true", help="run the batched uneven-problem measurement")
     ap.add_argument("--batch-size", type=int, default=256)

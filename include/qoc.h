@@ -105,9 +105,18 @@ qoc_status qoc_set_eig_method(qoc_problem* p, int method);
  * folded into one dependent step X <- (I + Delta) X + Q B_blk, with the
  * block propagators, propagated sources and the contractions at the
  * intermediate steps computed in parallel over blocks.  1 <= steps <= 8;
- * 1 selects one dependent step per time step.  Default 8 when J >= 16, else 1.
- * QOC_EINVAL otherwise. */
+ * 1 selects one dependent step per time step.  Default when J >= 16: 8 for
+ * QOC_FP64, 4 for QOC_MIXED_FP32 (the binary32 rounding of the block
+ * propagator grows like sqrt(steps); 4 keeps the mixed results within 1e-6
+ * of binary64); 1 when J < 16.  QOC_EINVAL otherwise. */
 qoc_status qoc_set_block_steps(qoc_problem* p, int steps);
+
+/* Panel columns per CTA of the tangent and second-order adjoint sweeps
+ * (1, 2 or 4; 0 restores the built-in choice: 2 for binary32 panels with
+ * N <= 32, else 1).  A launch-shape knob with no effect on the results'
+ * arithmetic; the autotuner in the Python package picks it together with
+ * the block steps.  QOC_EUNSUPPORTED when 32 ceil(N/8) kc > 1024 threads. */
+qoc_status qoc_set_panel_columns(qoc_problem* p, int kc);
 
 /* Replace the target state beta (N complex, interleaved host doubles). */
 qoc_status qoc_set_target(qoc_problem* p, const double* a_target);
@@ -167,24 +176,28 @@ qoc_status qoc_trust_region_solve(qoc_problem* p, const double* theta0,
 qoc_status qoc_get_diagnostics(const qoc_problem* p, double* out /* [8] */);
 
 /* Per-kernel timing of the last evaluation (timing enabled), milliseconds
- * between events on the problem's stream, in this order:
- *   0 control (f = B theta)         1 binary32 Jacobi (k_eig_jacobi)
+ * between events, in this order:
+ *   0 control (f = B theta)         1 binary32 Jacobi (k_eig_jacobi32)
  *   2 binary64 refinement or the binary64 Jacobi (k_eig_refine / k_eig_jacobi)
- *   3 propagator increments D_j     4 derivative preparation (M~, Gamma1, X'),
- *                                     concurrent with the chains
- *   5 wait for the state/costate chains after 4
- *   6 pointwise contractions        7 tangent and second-order adjoint panels
- *   8 gradient/Hessian assembly
+ *   3 propagator increments D_j     4 derivative preparation (M~, P~, X')
+ *   5 state and costate chains      6 pointwise contractions
+ *   7 tangent and second-order adjoint panels    8 gradient/Hessian assembly
+ *   9 the whole evaluation (first to last event on the problem's stream)
+ * With time blocking and a gradient or Hessian request the chains, the
+ * panels and the derivative preparation run concurrently on three streams
+ * (5 and 7 are then measured on their own streams and overlap 4 and 6).
  * Writes min(n, QOC_N_PHASES) values. */
-#define QOC_N_PHASES 9
+#define QOC_N_PHASES 10
 qoc_status qoc_get_phase_times(const qoc_problem* p, double* out, int n);
 
 /* Work counters of the last evaluation's refined eigensolver (timing
  * enabled; 0 otherwise), after the evaluation has completed:
  *   out[0] = mean binary64 Ogita-Aishima updates per step
  *   out[1] = fraction of steps whose binary64 Jacobi clean-up rotated
+ *   out[2] = fraction of steps that took the final residual pass and the
+ *            clean-up (the others finish early after their last update)
  * Synchronises the problem's stream. */
-qoc_status qoc_get_eig_stats(qoc_problem* p, double* out /* [2] */);
+qoc_status qoc_get_eig_stats(qoc_problem* p, double* out /* [3] */);
 qoc_status qoc_enable_timing(qoc_problem* p, int on);
 
 /* Copy an intermediate of the last evaluation to the host, for parity

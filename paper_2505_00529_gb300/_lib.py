@@ -32,6 +32,7 @@ EXPORTS = [
     "qoc_last_error", "qoc_batch_create", "qoc_batch_set_graph", "qoc_batch_eval_grad_hess",
     "qoc_batch_eval_grad_hess_dev", "qoc_batch_destroy", "qoc_assemble_noalloc_scratch_doubles",
     "qoc_assemble_grad_hess_noalloc", "qoc_get_phase_times", "qoc_get_eig_stats",
+    "qoc_set_panel_columns",
 ]
 
 
@@ -77,6 +78,7 @@ def lib() -> C.CDLL:
         L.qoc_set_hess_method.argtypes = [C.c_void_p, C.c_int]
         L.qoc_set_eig_method.argtypes = [C.c_void_p, C.c_int]
         L.qoc_set_block_steps.argtypes = [C.c_void_p, C.c_int]
+        L.qoc_set_panel_columns.argtypes = [C.c_void_p, C.c_int]
         L.qoc_eval_J.argtypes = [C.c_void_p, _dp, _dp]
         L.qoc_eval_grad.argtypes = [C.c_void_p, _dp, _dp, _dp]
         L.qoc_eval_grad_hess.argtypes = [C.c_void_p, _dp, _dp, _dp, _dp]
@@ -183,6 +185,10 @@ def qoc_set_block_steps(h, steps):
     _check(lib().qoc_set_block_steps(C.c_void_p(h), int(steps)), "qoc_set_block_steps")
 
 
+def qoc_set_panel_columns(h, kc):
+    _check(lib().qoc_set_panel_columns(C.c_void_p(h), int(kc)), "qoc_set_panel_columns")
+
+
 def qoc_enable_timing(h, on=True):
     _check(lib().qoc_enable_timing(C.c_void_p(h), int(bool(on))), "qoc_enable_timing")
 
@@ -245,8 +251,8 @@ def qoc_get_diagnostics(h):
             "phase_ms": dict(zip(["eig", "prep", "chains", "pointwise", "panels", "assembly"], out[2:]))}
 
 
-PHASES = ["control", "eig_jacobi", "eig_refine", "prep_D", "deriv_prep", "chains_wait", "pointwise",
-          "panels", "assembly"]
+PHASES = ["control", "eig_jacobi", "eig_refine", "prep_D", "deriv_prep", "chains", "pointwise",
+          "panels", "assembly", "total"]
 
 
 def qoc_get_phase_times(h):
@@ -256,9 +262,10 @@ def qoc_get_phase_times(h):
 
 
 def qoc_get_eig_stats(h):
-    out = np.zeros(2)
+    out = np.zeros(3)
     _check(lib().qoc_get_eig_stats(C.c_void_p(h), _ptr(out)), "qoc_get_eig_stats")
-    return {"refine_updates_per_step": out[0], "cleanup_rotated_fraction": out[1]}
+    return {"refine_updates_per_step": out[0], "cleanup_rotated_fraction": out[1],
+            "final_pass_fraction": out[2]}
 
 
 def qoc_read_buffer(h, which, shape, complex_=False):
@@ -419,7 +426,7 @@ class Problem:
     H0, M, alpha, beta, B, dt, w_f, w_t (e.g. ``inputs.Problem``)."""
 
     def __init__(self, prob, precision=QOC_FP64, cuda_stream=None, hess_method=None, eig_method=None,
-                 block_steps=None):
+                 block_steps=None, panel_columns=None):
         self.N, self.K, self.J = prob.H0.shape[0], prob.B.shape[1], prob.B.shape[0]
         self.handle = qoc_create_problem(self.N, prob.H0, prob.M, prob.alpha, prob.beta, self.K,
                                          prob.B, prob.dt, self.J, prob.w_f, prob.w_t, precision,
@@ -430,6 +437,8 @@ class Problem:
             qoc_set_eig_method(self.handle, eig_method)
         if block_steps is not None:
             qoc_set_block_steps(self.handle, block_steps)
+        if panel_columns is not None:
+            qoc_set_panel_columns(self.handle, panel_columns)
 
     def eval_J(self, theta):
         return qoc_eval_J(self.handle, theta)

@@ -42,9 +42,12 @@ struct qoc_problem {
   bool own_stream = false;
   cudaStream_t side = nullptr;          // high-priority stream: the latency-bound chains run here
                                         // while the binary64 derivative preparation fills the GPU
+  cudaStream_t pstream = nullptr;       // high-priority stream of the panel sweeps
   cudaEvent_t fork = nullptr, join = nullptr;
+  cudaEvent_t ev_state = nullptr, ev_ptil = nullptr, ev_panels = nullptr;
   int timing = 0;
-  cudaEvent_t ev[10] = {};
+  int sched = 0;                        // 0 sequential, 1 three-stream (time-blocked, order >= 1)
+  cudaEvent_t ev[14] = {};
   double phase_ms[6] = {0, 0, 0, 0, 0, 0};
   double kphase_ms[QOC_N_PHASES] = {};
   double diag[2] = {0, 0};
@@ -60,11 +63,13 @@ struct qoc_problem {
   unsigned int* eigstats = nullptr;     // refinement counters (timing mode)
   double2 *alpha = nullptr, *beta = nullptr, *Ptil = nullptr, *Xp = nullptr, *SJ = nullptr,
           *lamJ = nullptr;
+  double* Mtil = nullptr;               // M~_j = W_j^T M W_j (three-stream schedule)
   void *D = nullptr, *a_hat = nullptr, *l_hat = nullptr, *p_hat = nullptr, *y_hat = nullptr;
   int* status = nullptr;
   double *trwork = nullptr, *trstep = nullptr, *trinfo = nullptr, *trzero = nullptr;
   // time blocking (bs steps per block; bs == 1: per-step sweeps)
   int bs = 8, nblk = 0;
+  int kc = 0;                           // panel columns per CTA (0: built-in choice)
   size_t mstride = 0, qstride = 0, gstride = 0;
   void *Mf = nullptr, *Mb = nullptr, *Qf = nullptr, *Wf = nullptr, *Gf = nullptr, *Qb = nullptr,
        *Wb = nullptr, *Gb = nullptr, *Xa = nullptr, *Xl = nullptr, *XS = nullptr, *Xmu = nullptr;
@@ -126,6 +131,7 @@ double2 cexpi_h(double x) { return make_double2(std::cos(x), std::sin(x)); }
 // per CTA spreads the panel over K SMs); binary32 keeps two columns per CTA
 // up to N = 32 (8 warps) and one beyond
 int sweep_kc(const qoc_problem* p) {
+  if (p->kc > 0) return p->kc;
   if (p->precision == QOC_FP64) return 1;
   return p->N <= 32 ? 2 : 1;
 }
@@ -141,83 +147,139 @@ qoc_status device_status(qoc_problem* p) {
 
 // The time-blocked evaluation (see block.cu): everything after the spectral
 // preparation, with the sequential sweeps taking J / bs dependent steps.
+BSweepArgs chain_sweep_args(qoc_problem* p, int bwd) {
+  BSweepArgs a{};
+  const int mixed = p->precision == QOC_MIXED_FP32;
+  a.N = p->N; a.K = 1; a.Kp = p->Kp; a.J = p->J; a.bs = p->bs; a.kc = 1; a.backward = bwd;
+  a.M = reinterpret_cast<const unsigned char*>(bwd ? p->Mb : p->Mf); a.mstride = p->mstride;
+  a.init = bwd ? p->lamJ : p->alpha; a.init_scale = 1.0;
+  a.Xblk = bwd ? p->Xl : p->Xa; a.xblk_pairs = mixed;
+  a.states = bwd ? p->l_hat : p->a_hat; a.status = p->status;
+  return a;
+}
+
+BSweepArgs panel_sweep_args(qoc_problem* p, int bwd) {
+  BSweepArgs s{};
+  const int mixed = p->precision == QOC_MIXED_FP32;
+  s.N = p->N; s.K = p->K; s.Kp = p->Kp; s.J = p->J; s.bs = p->bs; s.kc = sweep_kc(p); s.backward = bwd;
+  s.M = reinterpret_cast<const unsigned char*>(bwd ? p->Mb : p->Mf); s.mstride = p->mstride;
+  s.Q = reinterpret_cast<const unsigned char*>(bwd ? p->Qb : p->Qf); s.qstride = p->qstride;
+  s.Brow = mixed ? static_cast<const void*>(p->Bf) : static_cast<const void*>(p->B);
+  s.status = p->status;
+  if (bwd) {
+    s.init = p->SJ; s.init_scale = 2.0 * p->w_t; s.Xblk = p->Xmu;
+  } else {
+    s.final_out = p->SJ; s.Xblk = p->XS;
+  }
+  return s;
+}
+
+
+// Time-blocked evaluation on three streams (order >= 1):
+//   chains (high priority): block products, state chain + fill, terminal,
+//       costate chain + fill
+//   main: derivative preparation P~ (then X' for the Hessian), pointwise c_j,
+//       assembly
+//   panels (high priority), order 2: as soon as the state and P~ exist:
+//       p^ -> propagated sources -> tangent panel sweep; after the costate:
+//       y^, g -> contraction U -> second-order adjoint sources and sweep ->
+//       contraction V
+// so that the two latency-bound panel sweeps overlap the costate chain and
+// the binary64 X' preparation instead of following them.
 qoc_status enqueue_blocked(qoc_problem* p, int order, double* out_dev) {
   cudaStream_t st = p->stream;
   const int N = p->N, K = p->K, J = p->J, bs = p->bs;
   const int mixed = p->precision == QOC_MIXED_FP32 ? 1 : 0;
-  // The chains (latency-bound, one CTA each) run on a high-priority stream
-  // while the binary64 derivative preparation (M~, Gamma1 o M~, X'; needed
-  // only from the pointwise step on) fills the GPU on the main stream.
-  cudaStream_t cs = st;
-  if (order >= 1) {
-    cs = p->side;
-    QOC_TRY(cudaEventRecord(p->fork, st));
-    QOC_TRY(cudaStreamWaitEvent(cs, p->fork, 0));
-  }
-  QOC_TRY(launch_block_delta(p->D, p->dstride, N, J, bs, 0, mixed, p->Mf, p->mstride, cs));
-  if (order >= 1)
-    QOC_TRY(launch_block_delta(p->D, p->dstride, N, J, bs, 1, mixed, p->Mb, p->mstride, cs));
-  BSweepArgs a{};
-  a.N = N; a.K = 1; a.Kp = p->Kp; a.J = J; a.bs = bs; a.kc = 1; a.backward = 0;
-  a.M = reinterpret_cast<const unsigned char*>(p->Mf); a.mstride = p->mstride;
-  a.init = p->alpha; a.init_scale = 1.0; a.Xblk = p->Xa; a.xblk_pairs = mixed;
-  a.states = p->a_hat; a.status = p->status;
-  QOC_TRY(launch_bsweep(a, mixed, cs));
-  QOC_TRY(launch_block_fill(p->D, p->dstride, N, J, bs, 0, mixed, p->Xa, p->a_hat, cs));
   const double thetaJ = (double)J * p->dt * p->mshift;
-  QOC_TRY(launch_terminal(p->f, J, p->a_hat, mixed, p->beta, N, cexpi_h(thetaJ), p->w_f, p->w_t,
-                          p->lamJ, p->scal + 0, p->scal + 1, cs));
-  QOC_TRY(cudaMemcpyAsync(out_dev, p->scal, sizeof(double), cudaMemcpyDeviceToDevice, cs));
+  const double2 kappa = cexpi_h(p->dt * p->mshift);
+  const bool soa = p->hess_method == QOC_HESS_SECOND_ORDER_ADJOINT;
+  const void* Bsrc = mixed ? static_cast<const void*>(p->Bf) : static_cast<const void*>(p->B);
   if (order == 0) {
-    if (p->timing) {
-      cudaEventRecord(p->ev[9], st);
-      for (int k = 3; k < 7; ++k) cudaEventRecord(p->ev[k], st);
-    }
+    p->sched = 0;
+    QOC_TRY(launch_block_delta(p->D, p->dstride, N, J, bs, 0, mixed, p->Mf, p->mstride, st));
+    QOC_TRY(launch_bsweep(chain_sweep_args(p, 0), mixed, st));
+    QOC_TRY(launch_block_fill(p->D, p->dstride, N, J, bs, 0, mixed, p->Xa, p->a_hat, st));
+    QOC_TRY(launch_terminal(p->f, J, p->a_hat, mixed, p->beta, N, cexpi_h(thetaJ), p->w_f, p->w_t,
+                            p->lamJ, p->scal + 0, nullptr, st));
+    QOC_TRY(launch_drift(p->a_hat, mixed, N, J, p->scal + 1, st));
+    QOC_TRY(cudaMemcpyAsync(out_dev, p->scal, sizeof(double), cudaMemcpyDeviceToDevice, st));
+    if (p->timing) for (int k : {9, 3, 4, 5, 6}) cudaEventRecord(p->ev[k], st);
     return QOC_OK;
   }
-  BSweepArgs l = a;
-  l.backward = 1; l.M = reinterpret_cast<const unsigned char*>(p->Mb);
-  l.init = p->lamJ; l.Xblk = p->Xl; l.states = p->l_hat;
-  QOC_TRY(launch_bsweep(l, mixed, cs));
+  p->sched = 1;
+  cudaStream_t cs = p->side, ps = p->pstream;
+  QOC_TRY(cudaEventRecord(p->fork, st));
+  // ---- chains ----
+  QOC_TRY(cudaStreamWaitEvent(cs, p->fork, 0));
+  if (p->timing) cudaEventRecord(p->ev[10], cs);
+  QOC_TRY(launch_block_delta(p->D, p->dstride, N, J, bs, 0, mixed, p->Mf, p->mstride, cs));
+  QOC_TRY(launch_block_delta(p->D, p->dstride, N, J, bs, 1, mixed, p->Mb, p->mstride, cs));
+  QOC_TRY(launch_bsweep(chain_sweep_args(p, 0), mixed, cs));
+  QOC_TRY(launch_block_fill(p->D, p->dstride, N, J, bs, 0, mixed, p->Xa, p->a_hat, cs));
+  QOC_TRY(launch_terminal(p->f, J, p->a_hat, mixed, p->beta, N, cexpi_h(thetaJ), p->w_f, p->w_t,
+                          p->lamJ, p->scal + 0, nullptr, cs));
+  QOC_TRY(cudaMemcpyAsync(out_dev, p->scal, sizeof(double), cudaMemcpyDeviceToDevice, cs));
+  QOC_TRY(cudaEventRecord(p->ev_state, cs));
+  QOC_TRY(launch_bsweep(chain_sweep_args(p, 1), mixed, cs));
   QOC_TRY(launch_block_fill(p->D, p->dstride, N, J, bs, 1, mixed, p->Xl, p->l_hat, cs));
+  if (p->timing) cudaEventRecord(p->ev[11], cs);
   QOC_TRY(cudaEventRecord(p->join, cs));
+  // ---- main: P~ ----
   QOC_TRY(launch_prep(p->W, p->eig, p->M, N, J, p->dt, p->mshift, p->D, p->dstride, mixed ? 0 : 1,
-                      2, p->Ptil, p->Xp, p->status, st));
-  if (p->timing) cudaEventRecord(p->ev[9], st);
-  QOC_TRY(cudaStreamWaitEvent(st, p->join, 0));
-  if (p->timing) cudaEventRecord(p->ev[3], st);
-  const double2 kappa = cexpi_h(p->dt * p->mshift);
-  QOC_TRY(launch_pointwise(p->W, p->Ptil, p->Xp, p->a_hat, p->l_hat, mixed, N, J, kappa, p->p_hat,
-                           p->y_hat, p->g, p->c, order >= 2, st));
-  if (p->timing) cudaEventRecord(p->ev[4], st);
+                      PREP_P, p->Ptil, p->Xp, p->Mtil, p->status, st));
+  QOC_TRY(cudaEventRecord(p->ev_ptil, st));
   if (order >= 2) {
-    const void* Bsrc = mixed ? static_cast<const void*>(p->Bf) : static_cast<const void*>(p->B);
+    // ---- panels ----
+    QOC_TRY(cudaStreamWaitEvent(ps, p->ev_ptil, 0));
+    QOC_TRY(cudaStreamWaitEvent(ps, p->ev_state, 0));
+    if (p->timing) cudaEventRecord(p->ev[12], ps);
+    QOC_TRY(launch_drift(p->a_hat, mixed, N, J, p->scal + 1, ps));
+    QOC_TRY(launch_pointwise(p->W, p->Ptil, p->Xp, p->a_hat, p->l_hat, mixed, N, J, kappa, p->p_hat,
+                             p->y_hat, p->g, p->c, PW_P, ps));
     QOC_TRY(launch_block_src(p->D, p->dstride, N, J, bs, 0, mixed, p->p_hat, p->y_hat, p->vstride,
-                             p->Qf, p->Wf, p->Gf, p->qstride, p->gstride, st));
-    BSweepArgs s{};
-    s.N = N; s.K = K; s.Kp = p->Kp; s.J = J; s.bs = bs; s.kc = sweep_kc(p); s.backward = 0;
-    s.M = reinterpret_cast<const unsigned char*>(p->Mf); s.mstride = p->mstride;
-    s.Q = reinterpret_cast<const unsigned char*>(p->Qf); s.qstride = p->qstride; s.Brow = Bsrc;
-    s.final_out = p->SJ; s.Xblk = p->XS; s.xblk_pairs = 0; s.status = p->status;
-    QOC_TRY(launch_bsweep(s, mixed, st));
+                             p->Qf, p->Wf, p->Gf, p->qstride, p->gstride, BS_Q, ps));
+    QOC_TRY(launch_bsweep(panel_sweep_args(p, 0), mixed, ps));
+    QOC_TRY(cudaStreamWaitEvent(ps, p->join, 0));
+    QOC_TRY(launch_pointwise(p->W, p->Ptil, p->Xp, p->a_hat, p->l_hat, mixed, N, J, kappa, p->p_hat,
+                             p->y_hat, p->g, p->c, PW_Y, ps));
+    QOC_TRY(launch_block_src(p->D, p->dstride, N, J, bs, 0, mixed, p->p_hat, p->y_hat, p->vstride,
+                             p->Qf, p->Wf, p->Gf, p->qstride, p->gstride, BS_WG, ps));
     QOC_TRY(launch_block_contract(p->XS, p->Wf, p->Gf, p->qstride, p->gstride, Bsrc, p->Kp, N, K, J,
-                                  bs, 0, mixed, p->U, st));
-    if (p->hess_method == QOC_HESS_SECOND_ORDER_ADJOINT) {
+                                  bs, 0, mixed, p->U, ps));
+    if (soa) {
       QOC_TRY(launch_block_src(p->D, p->dstride, N, J, bs, 1, mixed, p->y_hat, p->p_hat, p->vstride,
-                               p->Qb, p->Wb, p->Gb, p->qstride, p->gstride, st));
-      BSweepArgs m = s;
-      m.backward = 1; m.M = reinterpret_cast<const unsigned char*>(p->Mb);
-      m.Q = reinterpret_cast<const unsigned char*>(p->Qb);
-      m.init = p->SJ; m.init_scale = 2.0 * p->w_t; m.final_out = nullptr; m.Xblk = p->Xmu;
-      QOC_TRY(launch_bsweep(m, mixed, st));
+                               p->Qb, p->Wb, p->Gb, p->qstride, p->gstride, BS_Q | BS_WG, ps));
+      QOC_TRY(launch_bsweep(panel_sweep_args(p, 1), mixed, ps));
       QOC_TRY(launch_block_contract(p->Xmu, p->Wb, p->Gb, p->qstride, p->gstride, Bsrc, p->Kp, N, K,
-                                    J, bs, 1, mixed, p->V, st));
+                                    J, bs, 1, mixed, p->V, ps));
     }
+    if (p->timing) cudaEventRecord(p->ev[13], ps);
+    QOC_TRY(cudaEventRecord(p->ev_panels, ps));
+    // ---- main: X', c_j ----
+    QOC_TRY(launch_prep(p->W, p->eig, p->M, N, J, p->dt, p->mshift, p->D, p->dstride, mixed ? 0 : 1,
+                        PREP_X, p->Ptil, p->Xp, p->Mtil, p->status, st));
+    if (p->timing) cudaEventRecord(p->ev[3], st);
+    QOC_TRY(cudaStreamWaitEvent(st, p->join, 0));
+    QOC_TRY(launch_pointwise(p->W, p->Ptil, p->Xp, p->a_hat, p->l_hat, mixed, N, J, kappa, p->p_hat,
+                             p->y_hat, p->g, p->c, PW_C, st));
+    if (p->timing) cudaEventRecord(p->ev[4], st);
+    QOC_TRY(cudaStreamWaitEvent(st, p->ev_panels, 0));
+  } else {
+    if (p->timing) {
+      cudaEventRecord(p->ev[3], st);
+      cudaEventRecord(p->ev[12], st);
+      cudaEventRecord(p->ev[13], st);
+    }
+    QOC_TRY(cudaStreamWaitEvent(st, p->join, 0));
+    QOC_TRY(launch_drift(p->a_hat, mixed, N, J, p->scal + 1, st));
+    QOC_TRY(launch_pointwise(p->W, p->Ptil, p->Xp, p->a_hat, p->l_hat, mixed, N, J, kappa, p->p_hat,
+                             p->y_hat, p->g, p->c, PW_Y, st));
+    if (p->timing) cudaEventRecord(p->ev[4], st);
   }
   if (p->timing) cudaEventRecord(p->ev[5], st);
   QOC_TRY(launch_assemble(p->B, p->Kp, p->f, p->g, p->c, p->V, p->U, mixed, p->SJ, N, J, K,
-                          p->w_f, p->w_t, p->hess_method == QOC_HESS_SECOND_ORDER_ADJOINT ? 0 : 1,
-                          order >= 2, p->work, out_dev, p->hess_raw, p->scal + 2, st));
+                          p->w_f, p->w_t, soa ? 0 : 1, order >= 2, p->work, out_dev, p->hess_raw,
+                          p->scal + 2, st));
   if (p->timing) cudaEventRecord(p->ev[6], st);
   return QOC_OK;
 }
@@ -233,21 +295,21 @@ qoc_status enqueue_eval(qoc_problem* p, const double* theta_dev, int order, doub
   QOC_TRY(launch_control(p->B, p->Kp, theta_dev, J, K, p->f, st));
   if (p->timing) {
     cudaEventRecord(p->ev[7], st);
-    QOC_TRY(cudaMemsetAsync(p->eigstats, 0, 2 * sizeof(unsigned int), st));
+    QOC_TRY(cudaMemsetAsync(p->eigstats, 0, 4 * sizeof(unsigned int), st));
   }
   QOC_TRY(launch_eig(p->H0, p->M, p->f, N, J, p->W, p->eig, p->status,
                      p->eig_method == QOC_EIG_JACOBI_FP64 ? EIG_JACOBI_FP64 : EIG_REFINED,
                      p->refine_sweeps, p->angle_tol, st, p->timing ? p->ev[8] : nullptr,
                      p->timing ? p->eigstats : nullptr));
   if (p->timing) cudaEventRecord(p->ev[1], st);
-  QOC_TRY(launch_prep(p->W, p->eig, p->M, N, J, p->dt, p->mshift, p->D, p->dstride, d_fp64, 1,
-                      p->Ptil, p->Xp, p->status, st));
+  QOC_TRY(launch_prep(p->W, p->eig, p->M, N, J, p->dt, p->mshift, p->D, p->dstride, d_fp64, PREP_D,
+                      p->Ptil, p->Xp, nullptr, p->status, st));
   if (p->timing) cudaEventRecord(p->ev[2], st);
   if (p->bs > 1) return enqueue_blocked(p, order, out_dev);
-
+  p->sched = 0;
   if (order >= 1)
-    QOC_TRY(launch_prep(p->W, p->eig, p->M, N, J, p->dt, p->mshift, p->D, p->dstride, d_fp64, 2,
-                        p->Ptil, p->Xp, p->status, st));
+    QOC_TRY(launch_prep(p->W, p->eig, p->M, N, J, p->dt, p->mshift, p->D, p->dstride, d_fp64,
+                        PREP_P | PREP_X, p->Ptil, p->Xp, nullptr, p->status, st));
   if (p->timing) cudaEventRecord(p->ev[9], st);
   SweepArgs a{};
   a.N = N; a.K = 1; a.Kp = p->Kp; a.J = J; a.kc = 1; a.backward = 0;
@@ -268,7 +330,7 @@ qoc_status enqueue_eval(qoc_problem* p, const double* theta_dev, int order, doub
   if (p->timing) cudaEventRecord(p->ev[3], st);
   const double2 kappa = cexpi_h(p->dt * p->mshift);
   QOC_TRY(launch_pointwise(p->W, p->Ptil, p->Xp, p->a_hat, p->l_hat, mixed, N, J, kappa, p->p_hat,
-                           p->y_hat, p->g, p->c, order >= 2, st));
+                           p->y_hat, p->g, p->c, PW_P | PW_Y | (order >= 2 ? PW_C : 0), st));
   if (p->timing) cudaEventRecord(p->ev[4], st);
   if (order >= 2) {
     SweepArgs s{};
@@ -295,17 +357,24 @@ qoc_status enqueue_eval(qoc_problem* p, const double* theta_dev, int order, doub
 
 void collect_timing(qoc_problem* p) {
   if (!p->timing) return;
-  for (int k = 0; k < 6; ++k) {
+  auto el = [&](int a, int b) {
     float ms = 0;
-    if (cudaEventElapsedTime(&ms, p->ev[k], p->ev[k + 1]) == cudaSuccess) p->phase_ms[k] = ms;
-  }
-  // event order on the main stream: 0 start, 7 control, 8 binary32 Jacobi, 1 refinement,
-  // 2 propagator increments, 9 derivative preparation, 3 chains joined, 4, 5, 6
-  static const int from[QOC_N_PHASES] = {0, 7, 8, 1, 2, 9, 3, 4, 5};
-  static const int to[QOC_N_PHASES] = {7, 8, 1, 2, 9, 3, 4, 5, 6};
-  for (int k = 0; k < QOC_N_PHASES; ++k) {
-    float ms = 0;
-    if (cudaEventElapsedTime(&ms, p->ev[from[k]], p->ev[to[k]]) == cudaSuccess) p->kphase_ms[k] = ms;
+    return cudaEventElapsedTime(&ms, p->ev[a], p->ev[b]) == cudaSuccess ? (double)ms : 0.0;
+  };
+  // events: 0 start, 7 control, 8 binary32 Jacobi, 1 refinement, 2 increments D_j,
+  // sequential schedule: 9 derivative preparation, 3 chains, 4 pointwise, 5 panels, 6 assembly;
+  // three-stream schedule: 3 P~ and X' (main), 4 c_j (main), 5 panels joined, 6 assembly,
+  // 10/11 chains (chain stream), 12/13 panels (panel stream)
+  double* k = p->kphase_ms;
+  k[9] = el(0, 6);
+  k[0] = el(0, 7); k[1] = el(7, 8); k[2] = el(8, 1); k[3] = el(1, 2); k[8] = el(5, 6);
+  if (p->sched == 1) {
+    k[4] = el(2, 3); k[5] = el(10, 11); k[6] = el(3, 4); k[7] = el(12, 13);
+    const double ph[6] = {el(0, 1), el(1, 3), el(10, 11), el(3, 4), el(12, 13), el(5, 6)};
+    for (int i = 0; i < 6; ++i) p->phase_ms[i] = ph[i];
+  } else {
+    k[4] = el(2, 9); k[5] = el(9, 3); k[6] = el(3, 4); k[7] = el(4, 5);
+    for (int i = 0; i < 6; ++i) p->phase_ms[i] = el(i, i + 1);
   }
 }
 
@@ -376,12 +445,13 @@ void qoc_destroy_problem(qoc_problem* p) {
   if (p->hstatus) cudaFreeHost(p->hstatus);
   for (auto& e : p->ev)
     if (e) cudaEventDestroy(e);
-  if (p->side) {
-    cudaStreamSynchronize(p->side);
-    cudaStreamDestroy(p->side);
-  }
-  if (p->fork) cudaEventDestroy(p->fork);
-  if (p->join) cudaEventDestroy(p->join);
+  for (cudaStream_t* sp : {&p->side, &p->pstream})
+    if (*sp) {
+      cudaStreamSynchronize(*sp);
+      cudaStreamDestroy(*sp);
+    }
+  for (cudaEvent_t e : {p->fork, p->join, p->ev_state, p->ev_ptil, p->ev_panels})
+    if (e) cudaEventDestroy(e);
   if (p->own_stream && p->stream) cudaStreamDestroy(p->stream);
   delete p;
 }
@@ -440,9 +510,11 @@ qoc_status qoc_create_problem(int N, const double* H0, const double* M, const do
     int lo = 0, hi = 0;
     cudaDeviceGetStreamPriorityRange(&lo, &hi);
     if ((e = cudaStreamCreateWithPriority(&p->side, cudaStreamNonBlocking, hi)) != cudaSuccess) return fail(e);
+    if ((e = cudaStreamCreateWithPriority(&p->pstream, cudaStreamNonBlocking, hi)) != cudaSuccess)
+      return fail(e);
   }
-  if ((e = cudaEventCreateWithFlags(&p->fork, cudaEventDisableTiming)) != cudaSuccess) return fail(e);
-  if ((e = cudaEventCreateWithFlags(&p->join, cudaEventDisableTiming)) != cudaSuccess) return fail(e);
+  for (cudaEvent_t* ep : {&p->fork, &p->join, &p->ev_state, &p->ev_ptil, &p->ev_panels})
+    if ((e = cudaEventCreateWithFlags(ep, cudaEventDisableTiming)) != cudaSuccess) return fail(e);
 #define ALLOC(ptr, bytes) \
   if ((e = dalloc(p, &(ptr), (bytes))) != cudaSuccess) return fail(e)
   ALLOC(p->H0, 8 * NN);
@@ -463,11 +535,12 @@ qoc_status qoc_create_problem(int N, const double* H0, const double* M, const do
   ALLOC(p->out_trial, 8 * (1 + (size_t)K + (size_t)K * K));
   ALLOC(p->hess_raw, 8 * (size_t)K * K);
   ALLOC(p->scal, 8 * 8);
-  ALLOC(p->eigstats, 2 * sizeof(unsigned int));
+  ALLOC(p->eigstats, 4 * sizeof(unsigned int));
   ALLOC(p->alpha, 16 * (size_t)N);
   ALLOC(p->beta, 16 * (size_t)N);
   ALLOC(p->lamJ, 16 * (size_t)N);
   ALLOC(p->Ptil, 16 * (size_t)J * NN);
+  ALLOC(p->Mtil, 8 * (size_t)J * NN);
   ALLOC(p->Xp, 16 * (size_t)J * NN);
   ALLOC(p->SJ, 16 * (size_t)K * N);
   ALLOC(p->D, (size_t)J * p->dstride);
@@ -560,6 +633,13 @@ qoc_status qoc_set_block_steps(qoc_problem* p, int steps) {
   return QOC_OK;
 }
 
+qoc_status qoc_set_panel_columns(qoc_problem* p, int kc) {
+  if (!p || kc < 0 || kc > 4) return QOC_EINVAL;
+  if (kc > 0 && 32 * ((p->N + 7) / 8) * kc > 1024) return QOC_EUNSUPPORTED;
+  p->kc = kc;
+  return QOC_OK;
+}
+
 qoc_status qoc_enable_timing(qoc_problem* p, int on) {
   if (!p) return QOC_EINVAL;
   p->timing = on ? 1 : 0;
@@ -604,11 +684,10 @@ qoc_status qoc_get_diagnostics(const qoc_problem* p, double* out) {
 
 qoc_status qoc_get_eig_stats(qoc_problem* p, double* out) {
   if (!p || !out) return QOC_EINVAL;
-  unsigned int h[2] = {0, 0};
+  unsigned int h[3] = {0, 0, 0};
   QOC_TRY(cudaMemcpyAsync(h, p->eigstats, sizeof(h), cudaMemcpyDeviceToHost, p->stream));
   QOC_TRY(cudaStreamSynchronize(p->stream));
-  out[0] = p->timing ? (double)h[0] / p->J : 0.0;
-  out[1] = p->timing ? (double)h[1] / p->J : 0.0;
+  for (int i = 0; i < 3; ++i) out[i] = p->timing ? (double)h[i] / p->J : 0.0;
   return QOC_OK;
 }
 
@@ -822,33 +901,6 @@ struct qoc_batch {
 
 namespace {
 
-BSweepArgs chain_args(qoc_problem* p, int bwd) {
-  BSweepArgs a{};
-  const int mixed = p->precision == QOC_MIXED_FP32;
-  a.N = p->N; a.K = 1; a.Kp = p->Kp; a.J = p->J; a.bs = p->bs; a.kc = 1; a.backward = bwd;
-  a.M = reinterpret_cast<const unsigned char*>(bwd ? p->Mb : p->Mf); a.mstride = p->mstride;
-  a.init = bwd ? p->lamJ : p->alpha; a.init_scale = 1.0;
-  a.Xblk = bwd ? p->Xl : p->Xa; a.xblk_pairs = mixed;
-  a.states = bwd ? p->l_hat : p->a_hat; a.status = p->status;
-  return a;
-}
-
-BSweepArgs panel_args(qoc_problem* p, int bwd) {
-  BSweepArgs s{};
-  const int mixed = p->precision == QOC_MIXED_FP32;
-  s.N = p->N; s.K = p->K; s.Kp = p->Kp; s.J = p->J; s.bs = p->bs; s.kc = sweep_kc(p); s.backward = bwd;
-  s.M = reinterpret_cast<const unsigned char*>(bwd ? p->Mb : p->Mf); s.mstride = p->mstride;
-  s.Q = reinterpret_cast<const unsigned char*>(bwd ? p->Qb : p->Qf); s.qstride = p->qstride;
-  s.Brow = mixed ? static_cast<const void*>(p->Bf) : static_cast<const void*>(p->B);
-  s.status = p->status;
-  if (bwd) {
-    s.init = p->SJ; s.init_scale = 2.0 * p->w_t; s.Xblk = p->Xmu;
-  } else {
-    s.final_out = p->SJ; s.Xblk = p->XS;
-  }
-  return s;
-}
-
 // one phase of problem i of the batch on stream s (see the header comment)
 qoc_status batch_phase(qoc_batch* b, int i, int phase, cudaStream_t s) {
   qoc_problem* p = b->P[i];
@@ -863,7 +915,7 @@ qoc_status batch_phase(qoc_batch* b, int i, int phase, cudaStream_t s) {
                          p->eig_method == QOC_EIG_JACOBI_FP64 ? EIG_JACOBI_FP64 : EIG_REFINED,
                          p->refine_sweeps, p->angle_tol, s));
       QOC_TRY(launch_prep(p->W, p->eig, p->M, N, J, p->dt, p->mshift, p->D, p->dstride, mixed ? 0 : 1,
-                          3, p->Ptil, p->Xp, p->status, s));
+                          PREP_D | PREP_P | PREP_X, p->Ptil, p->Xp, nullptr, p->status, s));
       QOC_TRY(launch_block_delta(p->D, p->dstride, N, J, bs, 0, mixed, p->Mf, p->mstride, s));
       QOC_TRY(launch_block_delta(p->D, p->dstride, N, J, bs, 1, mixed, p->Mb, p->mstride, s));
       return QOC_OK;
@@ -878,16 +930,16 @@ qoc_status batch_phase(qoc_batch* b, int i, int phase, cudaStream_t s) {
     case 2:
       QOC_TRY(launch_block_fill(p->D, p->dstride, N, J, bs, 1, mixed, p->Xl, p->l_hat, s));
       QOC_TRY(launch_pointwise(p->W, p->Ptil, p->Xp, p->a_hat, p->l_hat, mixed, N, J,
-                               cexpi_h(p->dt * p->mshift), p->p_hat, p->y_hat, p->g, p->c, 1, s));
+                               cexpi_h(p->dt * p->mshift), p->p_hat, p->y_hat, p->g, p->c, PW_P | PW_Y | PW_C, s));
       QOC_TRY(launch_block_src(p->D, p->dstride, N, J, bs, 0, mixed, p->p_hat, p->y_hat, p->vstride,
-                               p->Qf, p->Wf, p->Gf, p->qstride, p->gstride, s));
+                               p->Qf, p->Wf, p->Gf, p->qstride, p->gstride, BS_Q | BS_WG, s));
       return QOC_OK;
     case 3:
       QOC_TRY(launch_block_contract(p->XS, p->Wf, p->Gf, p->qstride, p->gstride, Bsrc, p->Kp, N, K, J,
                                     bs, 0, mixed, p->U, s));
       if (p->hess_method == QOC_HESS_SECOND_ORDER_ADJOINT)
         QOC_TRY(launch_block_src(p->D, p->dstride, N, J, bs, 1, mixed, p->y_hat, p->p_hat, p->vstride,
-                                 p->Qb, p->Wb, p->Gb, p->qstride, p->gstride, s));
+                                 p->Qb, p->Wb, p->Gb, p->qstride, p->gstride, BS_Q | BS_WG, s));
       return QOC_OK;
     default:
       if (p->hess_method == QOC_HESS_SECOND_ORDER_ADJOINT)
@@ -981,7 +1033,8 @@ qoc_status qoc_batch_create(qoc_problem* const* problems, int n, void* cuda_stre
     b->ntheta += p->K;
     b->nout += 1 + (size_t)p->K + (size_t)p->K * p->K;
     // descriptor lists of the four batched sweeps
-    BSweepArgs args[4] = {chain_args(p, 0), chain_args(p, 1), panel_args(p, 0), panel_args(p, 1)};
+    BSweepArgs args[4] = {chain_sweep_args(p, 0), chain_sweep_args(p, 1), panel_sweep_args(p, 0),
+                           panel_sweep_args(p, 1)};
     for (int k = 0; k < 4; ++k) {
       if (k == 3 && p->hess_method != QOC_HESS_SECOND_ORDER_ADJOINT) continue;
       b->hoff[k].push_back(b->total[k]);

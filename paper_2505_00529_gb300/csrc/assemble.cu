@@ -56,7 +56,7 @@ __global__ void k_terminal(const double* __restrict__ f, int J, const void* a_ha
     rs += d.x * d.x + d.y * d.y;
     if (lamJ) lamJ[p] = cscale(d, 2.0 * w_t);
   }
-  for (int j = tid; j <= J; j += nt) {
+  for (int j = tid; drift_out && j <= J; j += nt) {   // (the three-stream schedule uses k_drift)
     double n2 = 0;
     for (int p = 0; p < N; ++p) {
       double2 v = load_state2(a_hat, mixed, (size_t)j * N + p);

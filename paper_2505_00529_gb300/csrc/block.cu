@@ -108,8 +108,10 @@ __global__ void k_block_src(const unsigned char* __restrict__ D, size_t dstride,
                             int bsteps, int bwd, const unsigned char* __restrict__ src,
                             const unsigned char* __restrict__ ctr, size_t vstride,
                             unsigned char* __restrict__ Qo, unsigned char* __restrict__ Wo,
-                            unsigned char* __restrict__ Go, size_t qstride, size_t gstride) {
+                            unsigned char* __restrict__ Go, size_t qstride, size_t gstride,
+                            int what) {
   using C = typename BlkT<MIX>::C;
+  const bool wq = what & BS_Q, wg = what & BS_WG;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int blk = blockIdx.x;
   const int t0 = blk * bsteps;
@@ -135,7 +137,7 @@ __global__ void k_block_src(const unsigned char* __restrict__ D, size_t dstride,
     __syncthreads();
     // Gamma_{k,m} = z_k^H Q[:, m] for m < k  (one warp per m)
     const int warp = tid >> 5, lane = tid & 31, nwarp = (nt + 31) >> 5;
-    for (int m = warp; m < k; m += nwarp) {
+    for (int m = warp; wg && m < k; m += nwarp) {
       typename BlkT<MIX>::R gx = 0, gy = 0;
       for (int i = lane; i < N; i += 32) {
         const C z = vec(ctr, j, i), q = Pn[m * N + i];
@@ -167,8 +169,11 @@ __global__ void k_block_src(const unsigned char* __restrict__ D, size_t dstride,
     }
     __syncthreads();
   }
-  C* qo = reinterpret_cast<C*>(Qo + (size_t)blk * qstride);
-  for (int e = tid; e < bsteps * N; e += nt) qo[e] = (e / N) < bl ? Pn[e] : cz<C>();
+  if (wq) {
+    C* qo = reinterpret_cast<C*>(Qo + (size_t)blk * qstride);
+    for (int e = tid; e < bsteps * N; e += nt) qo[e] = (e / N) < bl ? Pn[e] : cz<C>();
+  }
+  if (!wg) return;
   C* go = reinterpret_cast<C*>(Go + (size_t)blk * gstride);
   for (int e = tid; e < bsteps * bsteps; e += nt) go[e] = Gm[e];
   __syncthreads();
@@ -341,7 +346,8 @@ cudaError_t launch_block_delta(const void* D, size_t dstride, int N, int J, int 
 
 cudaError_t launch_block_src(const void* D, size_t dstride, int N, int J, int bsteps, int bwd,
                              int mixed, const void* src, const void* ctr, size_t vstride, void* Q,
-                             void* W, void* G, size_t qstride, size_t gstride, cudaStream_t st) {
+                             void* W, void* G, size_t qstride, size_t gstride, int what,
+                             cudaStream_t st) {
   const int nblk = (J + bsteps - 1) / bsteps;
   const size_t cs = mixed ? 8 : 16;
   const size_t smem = ((size_t)N * (N + 1) + 2 * (size_t)bsteps * N + (size_t)bsteps * bsteps) * cs;
@@ -351,13 +357,13 @@ cudaError_t launch_block_src(const void* D, size_t dstride, int N, int J, int bs
     k_block_src<true><<<nblk, threads, smem, st>>>((const unsigned char*)D, dstride, N, J, bsteps, bwd,
                                                    (const unsigned char*)src, (const unsigned char*)ctr,
                                                    vstride, (unsigned char*)Q, (unsigned char*)W,
-                                                   (unsigned char*)G, qstride, gstride);
+                                                   (unsigned char*)G, qstride, gstride, what);
   } else {
     set_max_smem((const void*)k_block_src<false>);
     k_block_src<false><<<nblk, threads, smem, st>>>((const unsigned char*)D, dstride, N, J, bsteps, bwd,
                                                     (const unsigned char*)src, (const unsigned char*)ctr,
                                                     vstride, (unsigned char*)Q, (unsigned char*)W,
-                                                    (unsigned char*)G, qstride, gstride);
+                                                    (unsigned char*)G, qstride, gstride, what);
   }
   return cudaGetLastError();
 }

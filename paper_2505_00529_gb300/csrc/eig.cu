@@ -255,6 +255,15 @@ __global__ void k_eig_refine(const double* __restrict__ H0, const double* __rest
   // matrix the clean-up diagonalises, otherwise W <- W (I + E).
   // rounding floor of |I - W^T W|_F for an orthonormal W: ~ eps N^1.5
   const double orth_tol = 8.0 * 1.12e-16 * (double)N * sqrt((double)N);
+  // Early finish: when an update has no cluster pairs and both |R|_F and the
+  // largest |E_ik| are below kDone = sqrt(orth_tol) / 10, the updated W is
+  // orthonormal and accurate to the binary64 floor (the next residual is
+  // O(|E|^2 + |R| |E|) <= orth_tol / 50), and the Rayleigh quotients lambda of
+  // this pass are exact to O(|E|^2 |H|): the final residual pass and the
+  // clean-up are skipped.
+  const double kDone = 0.1 * sqrt(orth_tol);
+  __shared__ int not_done;
+  bool finished = false;
   for (int it = 0;; ++it) {
     // T = H W
     for (int e = tid; e < N * N; e += nt) {
@@ -315,6 +324,8 @@ __global__ void k_eig_refine(const double* __restrict__ H0, const double* __rest
     // would destroy orthogonality.  Such pairs only get the orthogonality
     // part R/2 here; the binary64 Jacobi clean-up rotates them exactly.
     constexpr double kLinear = 1e-3;
+    if (tid == 0) not_done = red[42] > kDone ? 1 : 0;
+    __syncthreads();
     for (int e = tid; e < N * N; e += nt) {
       const int i = e / N, k = e % N;
       const double rik = R[i * ld + k];
@@ -323,8 +334,9 @@ __global__ void k_eig_refine(const double* __restrict__ H0, const double* __rest
       else {
         const double gap = lam[k] - lam[i];
         const double sik = S[i * ld + k];
-        eik = (fabs(gap) > delta && fabs(sik) <= kLinear * fabs(gap)) ? (sik + lam[k] * rik) / gap
-                                                                       : 0.5 * rik;
+        const bool sep = fabs(gap) > delta && fabs(sik) <= kLinear * fabs(gap);
+        eik = sep ? (sik + lam[k] * rik) / gap : 0.5 * rik;
+        if (!sep || fabs(eik) > kDone) not_done = 1;
       }
       T[i * ld + k] = eik;
     }
@@ -341,8 +353,17 @@ __global__ void k_eig_refine(const double* __restrict__ H0, const double* __rest
       const int i = e / N, k = e % N;
       W[i * ld + k] += R[i * ld + k];
     }
+    if (!not_done) {   // uniform across the CTA (read after the barrier above)
+      for (int i = tid; i < N; i += nt) S[i * ld + i] = lam[i];
+      if (stats && tid == 0) atomicAdd(&stats[0], (unsigned int)(it + 1));
+      finished = true;
+      __syncthreads();
+      break;
+    }
     __syncthreads();
   }
+  if (!finished) {
+  if (stats && tid == 0) atomicAdd(&stats[2], 1u);
   // clean-up: Jacobi on S = W^T H W with V = I (in R)
   for (int e = tid; e < N * N; e += nt) R[(e / N) * ld + (e % N)] = (e / N == e % N) ? 1.0 : 0.0;
   __syncthreads();
@@ -369,11 +390,162 @@ __global__ void k_eig_refine(const double* __restrict__ H0, const double* __rest
     for (int e = tid; e < N * N; e += nt) W[(e / N) * ld + (e % N)] = T[(e / N) * ld + (e % N)];
     __syncthreads();
   }
+  }
   bool bad = false;
   for (int i = tid; i < N; i += nt) bad |= !isfinite(S[i * ld + i]);
   if (bad) raise_status(status, DEV_NONFINITE);
   sort_write<double>(S, W, N, ld, Wg, eig_out + (size_t)j * N);
 }
+
+// ---------------------------------------------------------------------------
+// Binary32 Jacobi with one warp per matrix (several matrices per CTA): the
+// round-robin parallel cyclic scheme of jacobi_sweeps, synchronised by
+// __syncwarp only.  In a round every lane updates whole 2 x 2 blocks
+// R_k^T A R_l of the full matrix (each element belongs to exactly one block,
+// so nothing is mirrored) and rows of V R; the (k, l) and (i, l)
+// enumerations advance by a fixed stride with a carry instead of divisions.
+// Convergence: no rotation in a sweep, or off(A)^2 <= (4 eps)^2 |A|_F^2.
+// ---------------------------------------------------------------------------
+__host__ __device__ inline int jacobi32_slot_floats(int N) {
+  const int NP = N + (N & 1);
+  const int n = 2 * N * (N + 1) + 2 * NP;
+  return (n + 3) & ~3;
+}
+
+__device__ __forceinline__ float warp_sum_f(float v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+__global__ void __launch_bounds__(128) k_eig_jacobi32(const double* __restrict__ H0,
+                                                      const double* __restrict__ M,
+                                                      const double* __restrict__ f, int N, int J,
+                                                      int mpb, double* __restrict__ W_out,
+                                                      double* __restrict__ eig_out, int* status) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int j = blockIdx.x * mpb + wid;
+  if (wid >= mpb || j >= J) return;   // whole warps leave; only __syncwarp below
+  const int ld = N + 1, NP = N + (N & 1), NH = NP / 2;
+  float* A = reinterpret_cast<float*>(smem_raw) + (size_t)wid * jacobi32_slot_floats(N);
+  float* V = A + N * ld;
+  float* cs = V + N * ld;                        // [NP]: c_k, s_k
+  int* pr = reinterpret_cast<int*>(cs + NP);     // [NP]: p_k, q_k
+  const double fj = f[j];
+  for (int p = 0; p < N; ++p)
+    for (int q = lane; q < N; q += 32) {
+      A[p * ld + q] = (float)(H0[p * N + q] + fj * M[p * N + q]);
+      V[p * ld + q] = p == q ? 1.f : 0.f;
+    }
+  __syncwarp();
+  const float eps = 5.96e-8f;
+  const float off_tol2 = 16.f * eps * eps;
+  const int kstep = 32 % NH, lstep = 32 / NH;    // stride 32 in a (row, col) enumeration over NH
+  bool converged = false;
+  for (int sweep = 0; sweep < 24 && !converged; ++sweep) {
+    bool rot = false;
+    for (int r = 0; r < NP - 1; ++r) {
+      if (lane < NH) {
+        int p = rr_elem(lane, r, NP), q = rr_elem(NP - 1 - lane, r, NP);
+        if (p > q) { const int t = p; p = q; q = t; }
+        float c = 1.f, s = 0.f;
+        if (q < N) {
+          const float apq = A[p * ld + q], app = A[p * ld + p], aqq = A[q * ld + q];
+          const float thr = eps * 0.01f * sqrtf(fabsf(app) * fabsf(aqq));
+          if (fabsf(apq) > thr && apq != 0.f) {
+            const float th = (aqq - app) / (2.f * apq);
+            const float t = (th >= 0.f ? 1.f : -1.f) / (fabsf(th) + sqrtf(th * th + 1.f));
+            c = 1.f / sqrtf(t * t + 1.f);
+            s = t * c;
+            rot = true;
+          }
+        }
+        pr[2 * lane] = p;
+        pr[2 * lane + 1] = q;
+        cs[2 * lane] = c;
+        cs[2 * lane + 1] = s;
+      }
+      __syncwarp();
+      // A <- R^T A R, block (k, l): rows of pair k, columns of pair l
+      for (int k = lane % NH, l = lane / NH; l < NH;) {
+        const float sk = cs[2 * k + 1], sl = cs[2 * l + 1];
+        if (sk != 0.f || sl != 0.f) {
+          const float ck = cs[2 * k], cl = cs[2 * l];
+          const int p0 = pr[2 * k], p1 = pr[2 * k + 1], q0 = pr[2 * l], q1 = pr[2 * l + 1];
+          if (p1 >= N) {          // pair k holds the dummy index of odd N: row p0 only
+            if (q1 < N) {
+              const float x0 = A[p0 * ld + q0], x1 = A[p0 * ld + q1];
+              A[p0 * ld + q0] = cl * x0 - sl * x1;
+              A[p0 * ld + q1] = sl * x0 + cl * x1;
+            }
+          } else if (q1 >= N) {   // pair l holds the dummy: column q0 only
+            const float x0 = A[p0 * ld + q0], x1 = A[p1 * ld + q0];
+            A[p0 * ld + q0] = ck * x0 - sk * x1;
+            A[p1 * ld + q0] = sk * x0 + ck * x1;
+          } else {
+            const float a00 = A[p0 * ld + q0], a01 = A[p0 * ld + q1];
+            const float a10 = A[p1 * ld + q0], a11 = A[p1 * ld + q1];
+            const float b00 = ck * a00 - sk * a10, b01 = ck * a01 - sk * a11;
+            const float b10 = sk * a00 + ck * a10, b11 = sk * a01 + ck * a11;
+            A[p0 * ld + q0] = cl * b00 - sl * b01;
+            A[p1 * ld + q1] = sl * b10 + cl * b11;
+            if (k == l) {         // the rotated pair: its off-diagonal is zero by construction
+              A[p0 * ld + q1] = 0.f;
+              A[p1 * ld + q0] = 0.f;
+            } else {
+              A[p0 * ld + q1] = sl * b00 + cl * b01;
+              A[p1 * ld + q0] = cl * b10 - sl * b11;
+            }
+          }
+        }
+        k += kstep;
+        l += lstep;
+        if (k >= NH) { k -= NH; ++l; }
+      }
+      // V <- V R, row i, pair l
+      for (int l = lane % NH, i = lane / NH; i < N;) {
+        const float sl = cs[2 * l + 1];
+        const int q1 = pr[2 * l + 1];
+        if (sl != 0.f && q1 < N) {
+          const float cl = cs[2 * l];
+          const int q0 = pr[2 * l];
+          const float v0 = V[i * ld + q0], v1 = V[i * ld + q1];
+          V[i * ld + q0] = cl * v0 - sl * v1;
+          V[i * ld + q1] = sl * v0 + cl * v1;
+        }
+        l += kstep;
+        i += lstep;
+        if (l >= NH) { l -= NH; ++i; }
+      }
+      __syncwarp();
+    }
+    float off = 0.f, tot = 0.f;
+    for (int p = 0; p < N; ++p)
+      for (int q = lane; q < N; q += 32) {
+        const float v = A[p * ld + q];
+        tot = fmaf(v, v, tot);
+        if (p != q) off = fmaf(v, v, off);
+      }
+    off = warp_sum_f(off);
+    tot = warp_sum_f(tot);
+    converged = !__any_sync(0xffffffffu, rot) || off <= off_tol2 * tot || off == 0.f;
+  }
+  if (!converged && lane == 0) raise_status(status, DEV_EIG_NOCONV);
+  // rank-sort the diagonal (ties by index) and write W = V(:, order), lambda
+  double* Wj = W_out + (size_t)j * N * N;
+  for (int i = lane; i < N; i += 32) {
+    const float di = A[i * ld + i];
+    int rank = 0;
+    for (int k = 0; k < N; ++k) {
+      const float dk = A[k * ld + k];
+      rank += (dk < di) || (dk == di && k < i);
+    }
+    eig_out[(size_t)j * N + rank] = (double)di;
+    for (int row = 0; row < N; ++row) Wj[row * N + rank] = (double)V[row * ld + i];
+  }
+}
+
+static int jacobi32_mpb(int N) { return N <= 16 ? 4 : (N <= 40 ? 2 : 1); }
 
 static size_t jacobi_smem(int N, size_t tsize) {
   const int NP = N + (N & 1);
@@ -387,7 +559,8 @@ static size_t refine_smem(int N) {
 }
 
 size_t eig_smem_bytes(int N, int method) {
-  size_t a = method == EIG_JACOBI_FP64 ? jacobi_smem(N, 8) : jacobi_smem(N, 4);
+  size_t a = method == EIG_JACOBI_FP64 ? jacobi_smem(N, 8)
+                                       : (size_t)jacobi32_mpb(N) * jacobi32_slot_floats(N) * sizeof(float);
   size_t b = method == EIG_JACOBI_FP64 ? 0 : refine_smem(N);
   return a > b ? a : b;
 }
@@ -405,9 +578,10 @@ cudaError_t launch_eig(const double* H0, const double* M, const double* f, int N
     if (mid) cudaEventRecord(mid, st);
     return cudaGetLastError();
   }
-  size_t sm = jacobi_smem(N, 4);
-  set_max_smem((const void*)k_eig_jacobi<float>);
-  k_eig_jacobi<float><<<J, jthreads, sm, st>>>(H0, M, f, N, J, W, eig, status);
+  const int mpb = jacobi32_mpb(N);
+  const size_t sm = (size_t)mpb * jacobi32_slot_floats(N) * sizeof(float);
+  set_max_smem((const void*)k_eig_jacobi32);
+  k_eig_jacobi32<<<(J + mpb - 1) / mpb, 32 * mpb, sm, st>>>(H0, M, f, N, J, mpb, W, eig, status);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   if (mid) cudaEventRecord(mid, st);

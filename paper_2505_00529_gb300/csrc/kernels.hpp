@@ -47,7 +47,8 @@ enum { PREC_FP64 = 0, PREC_MIXED = 1 };
 constexpr double TAU_DD2 = 1e-3;
 
 size_t eig_smem_bytes(int N, int method);
-// stats (optional, device): [0] += refinement updates, [1] += steps whose clean-up rotated
+// stats (optional, device): [0] += refinement updates, [1] += steps whose clean-up rotated,
+// [2] += steps that took the final residual pass (no early finish)
 // method EIG_REFINED: binary32 Jacobi, `refine_sweeps` binary64 Ogita-Aishima
 // sweeps, then binary64 Jacobi clean-up rotating only angles above angle_tol.
 cudaError_t launch_eig(const double* H0, const double* M, const double* f, int N, int J,
@@ -59,9 +60,13 @@ size_t prep_smem_bytes(int N);
 // parts (bit mask): 1 -> D_j = W diag(exp(-i dt (lambda - m)) - 1) W^T
 // (binary64 when d_fp64, else binary32) at byte stride dstride;
 // 2 -> P~_j = Gamma1 o M~_j and X'_j = 2 sum_r M~_pr M~_rq phi[l_p, l_r, l_q].
+// parts: PREP_D (increments D_j), PREP_P (M~, P~ = Gamma1 o M~; M~ stored in Mtil when
+// non-null), PREP_X (X'; alone it reads M~ and P~ back from Mtil and Ptil)
+enum { PREP_D = 1, PREP_P = 2, PREP_X = 4 };
 cudaError_t launch_prep(const double* W, const double* eig, const double* M, int N, int J,
                         double dt, double mshift, void* D, size_t dstride, int d_fp64,
-                        int parts, double2* Ptil, double2* Xp, int* status, cudaStream_t st);
+                        int parts, double2* Ptil, double2* Xp, double* Mtil, int* status,
+                        cudaStream_t st);
 
 struct SweepArgs {
   int N, K, Kp, J;       // Kp: row stride of the basis copy (multiple of 4)
@@ -109,9 +114,12 @@ cudaError_t launch_bsweep_batch(const BSweepArgs* host_args, const BSweepArgs* d
                                 cudaStream_t st);
 cudaError_t launch_block_delta(const void* D, size_t dstride, int N, int J, int bsteps, int bwd,
                                int mixed, void* M, size_t mstride, cudaStream_t st);
+// what: BS_Q (propagated sources Q, from src only), BS_WG (W and Gamma, needs ctr)
+enum { BS_Q = 1, BS_WG = 2 };
 cudaError_t launch_block_src(const void* D, size_t dstride, int N, int J, int bsteps, int bwd,
                              int mixed, const void* src, const void* ctr, size_t vstride, void* Q,
-                             void* W, void* G, size_t qstride, size_t gstride, cudaStream_t st);
+                             void* W, void* G, size_t qstride, size_t gstride, int what,
+                             cudaStream_t st);
 cudaError_t launch_block_contract(const void* Xblk, const void* W, const void* G, size_t qstride,
                                   size_t gstride, const void* Brow, int Kp, int N, int K, int J,
                                   int bsteps, int bwd, int mixed, void* contr, cudaStream_t st);
@@ -121,10 +129,14 @@ cudaError_t launch_block_fill(const void* D, size_t dstride, int N, int J, int b
 // p^_j, y^_j, g_j, c_j for all steps from the stored states/costates
 // states / costates as written by the vector chains (double2, or float4 pairs
 // when mixed); p^, y^ written as double2 (binary64 sweeps) or float2 (mixed)
+// what: PW_P (p^ from a^), PW_Y (y^ and g from lambda^ and a^), PW_C (c from X', a^, lambda^)
+enum { PW_P = 1, PW_Y = 2, PW_C = 4 };
 cudaError_t launch_pointwise(const double* W, const double2* Ptil, const double2* Xp,
                              const void* a_hat, const void* l_hat, int mixed, int N, int J,
                              double2 kappa, void* p_hat, void* y_hat, double* g, double* c,
-                             int want_c, cudaStream_t st);
+                             int what, cudaStream_t st);
+// max_j | |a_j| - 1 | over the stored states j = 0..J into *drift (zeroed here)
+cudaError_t launch_drift(const void* a_hat, int mixed, int N, int J, double* drift, cudaStream_t st);
 
 cudaError_t launch_control(const double* B, int Kp, const double* theta, int J, int K, double* f,
                            cudaStream_t st);

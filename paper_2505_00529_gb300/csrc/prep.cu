@@ -118,7 +118,8 @@ __device__ __forceinline__ double2 dd2_table(int a, int b, int c, const double* 
 __global__ void k_prep(const double* __restrict__ Wg, const double* __restrict__ eig,
                        const double* __restrict__ Mg, int N, int J, double dt, double mshift,
                        void* __restrict__ Dout, size_t dstride, int d_fp64, int derivs,
-                       double2* __restrict__ Ptil, double2* __restrict__ Xp, int* status) {
+                       double2* __restrict__ Ptil, double2* __restrict__ Xp,
+                       double* __restrict__ Mtil, int* status) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int j = blockIdx.x;
   if (j >= J) return;
@@ -139,13 +140,23 @@ __global__ void k_prep(const double* __restrict__ Wg, const double* __restrict__
 
   const int tid = threadIdx.x, nt = blockDim.x;
   const double* Wj = Wg + (size_t)j * N * N;
+  // parts: PREP_D (D_j), PREP_P (M~ and P~; M~ also stored when Mtil is given),
+  // PREP_X (X'; from this launch's M~, P~ or, alone, from the stored ones)
+  const bool doD = derivs & PREP_D, doP = derivs & PREP_P, doX = derivs & PREP_X;
+  const bool loadMP = doX && !doP;
   if (tid == 0) n_near = 0;
   for (int e = tid; e < N * N; e += nt) {
     const int p = e / N, q = e % N;
-    const double w = Wj[e];
-    W[p * ld + q] = w;
-    Wf[p * ld + q] = (float)w;
-    Mt[p * ld + q] = Mg[e];
+    if (doD || doP) {
+      const double w = Wj[e];
+      W[p * ld + q] = w;
+      Wf[p * ld + q] = (float)w;
+    }
+    if (doP) Mt[p * ld + q] = Mg[e];
+    if (loadMP) {
+      Mt[p * ld + q] = Mtil[(size_t)j * N * N + e];
+      P[p * ld + q] = Ptil[(size_t)j * N * N + e];
+    }
   }
   for (int p = tid; p < N; p += nt) {
     const double l = eig[(size_t)j * N + p];
@@ -162,7 +173,7 @@ __global__ void k_prep(const double* __restrict__ Wg, const double* __restrict__
   __syncthreads();
 
   // D = W diag(pm1) W^T (complex symmetric): upper triangle, mirrored
-  if (!(derivs & 1)) {
+  if (!doD) {
     // derivative-only launch: D is produced by a concurrent launch
   } else if (d_fp64) {
     double2* D = reinterpret_cast<double2*>(reinterpret_cast<unsigned char*>(Dout) + (size_t)j * dstride);
@@ -193,8 +204,9 @@ __global__ void k_prep(const double* __restrict__ Wg, const double* __restrict__
       D[q * N + p] = make_float2(re, im);
     }
   }
-  if (!(derivs & 2)) return;
-
+  if (!doP && !doX) return;
+  double2* Pg = Ptil + (size_t)j * N * N;
+  if (doP) {
   // T = M W ; M~ = W^T T (upper triangle, mirrored: exactly symmetric)
   for (int e = tid; e < N * N; e += nt) {
     const int i = e / N, k = e % N;
@@ -212,14 +224,20 @@ __global__ void k_prep(const double* __restrict__ Wg, const double* __restrict__
     Mt[k * ld + i] = acc;
   }
   __syncthreads();
-  // P~ = Gamma1 o M~ ; list the near pairs (p <= q)
-  double2* Pg = Ptil + (size_t)j * N * N;
+  // P~ = Gamma1 o M~
   for (int e = tid; e < N * N; e += nt) {
     const int p = e / N, q = e % N;
     const double2 g = gamma1(p, q, lam, eh, dt);
     const double2 v = cscale(g, Mt[p * ld + q]);
     P[p * ld + q] = v;
     Pg[e] = v;
+    if (Mtil) Mtil[(size_t)j * N * N + e] = Mt[p * ld + q];
+  }
+  }
+  if (!doX) return;
+  // list the near pairs (p <= q)
+  for (int e = tid; e < N * N; e += nt) {
+    const int p = e / N, q = e % N;
     if (q >= p && !(dt * fabs(lam[p] - lam[q]) > TAU_DD2)) near[atomicAdd(&n_near, 1)] = p * N + q;
   }
   __syncthreads();
@@ -283,12 +301,13 @@ size_t prep_smem_bytes(int N) {
 
 cudaError_t launch_prep(const double* W, const double* eig, const double* M, int N, int J,
                         double dt, double mshift, void* D, size_t dstride, int d_fp64,
-                        int parts, double2* Ptil, double2* Xp, int* status, cudaStream_t st) {
+                        int parts, double2* Ptil, double2* Xp, double* Mtil, int* status,
+                        cudaStream_t st) {
   size_t sm = prep_smem_bytes(N);
   set_max_smem((const void*)k_prep);
   int threads = N <= 8 ? 64 : (N <= 16 ? 128 : 256);
   k_prep<<<J, threads, sm, st>>>(W, eig, M, N, J, dt, mshift, D, dstride, d_fp64, parts, Ptil,
-                                 Xp, status);
+                                 Xp, Mtil, status);
   return cudaGetLastError();
 }
 

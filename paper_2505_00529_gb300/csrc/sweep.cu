@@ -495,6 +495,30 @@ static void bsweep_geometry(const BSweepArgs& a, int& threads, size_t& stage, si
   fixed = 2 * (size_t)a.kc * a.N * sizeof(TD) + 16;
 }
 
+// Ring depth of a blocked-sweep launch: as deep as 16 stages when the grid
+// fits one CTA per SM (bulk-copy latency is what the chain waits on), else
+// shallow enough that ceil(grid / SMs) CTAs share an SM's shared memory.
+static int ring_stages(size_t stage, size_t fixed, int threads, int total_ctas) {
+  static int nsm = 0;
+  if (!nsm) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || nsm < 1)
+      nsm = 1;
+  }
+  int cps = (total_ctas + nsm - 1) / nsm;
+  const int by_threads = 2048 / (threads > 0 ? threads : 32);
+  if (cps > by_threads) cps = by_threads;
+  if (cps > 32) cps = 32;
+  if (cps < 1) cps = 1;
+  size_t budget = (size_t)(228 * 1024) / cps;
+  budget = budget > 1024 + 16 ? budget - 1024 - 16 : 0;
+  if (budget > 200 * 1024) budget = 200 * 1024;
+  int ns = 16;
+  while (ns > 2 && (size_t)ns * stage + fixed + 8 * ns > budget) --ns;
+  return ns;
+}
+
 template <bool MIX, int RS>
 static cudaError_t launch_bb(const BSweepArgs* host_args, const BSweepArgs* dev_args,
                              const int* dev_cta_off, int nprob, int total_ctas, cudaStream_t st) {
@@ -509,8 +533,7 @@ static cudaError_t launch_bb(const BSweepArgs* host_args, const BSweepArgs* dev_
     fixed = f > fixed ? f : fixed;
   }
   if (threads > 1024) return cudaErrorInvalidConfiguration;
-  int ns = 6;
-  while (ns > 2 && (size_t)ns * stage + fixed + 8 * ns > 200 * 1024) --ns;
+  const int ns = ring_stages(stage, fixed, threads, total_ctas);
   const size_t smem = (size_t)ns * stage + fixed + 8 * ns + 16;
   if (smem > 227 * 1024) return cudaErrorInvalidConfiguration;
   set_max_smem((const void*)k_bsweep_batch<MIX, RS>);
@@ -535,13 +558,11 @@ static cudaError_t launch_b(const BSweepArgs& a, cudaStream_t st) {
   if (threads > 1024) return cudaErrorInvalidConfiguration;
   const size_t stage = a.mstride + (a.Q ? a.qstride : 0) + (a.Brow ? sizeof(TB) * a.Kp * a.bs : 0);
   const size_t fixed = 2 * (size_t)a.kc * a.N * sizeof(TD) + 16;
-  const size_t budget = 200 * 1024;
-  int ns = 6;
-  while (ns > 2 && (size_t)ns * stage + fixed + 8 * ns > budget) --ns;
+  const int grid = (a.K + a.kc - 1) / a.kc;
+  const int ns = ring_stages(stage, fixed, threads, grid);
   const size_t smem = (size_t)ns * stage + fixed + 8 * ns + 16;
   if (smem > 227 * 1024) return cudaErrorInvalidConfiguration;
   set_max_smem((const void*)k_bsweep<MIX, RS>);
-  const int grid = (a.K + a.kc - 1) / a.kc;
   k_bsweep<MIX, RS><<<grid, threads, smem, st>>>(a, ns);
   return cudaGetLastError();
 }
