@@ -32,11 +32,13 @@ UNIT = "evals/s"
 WORKLOAD = {"workload": "synthetic CI-shaped single problem, N=32 basis, K=64 sine/cosine "
                         "coefficients, J=4000 steps, T=20 (dt=0.005)",
             "N": 32, "K": 64, "J": 4000}
-# library kernel launches per evaluation on the time-blocked path (block steps >= 2):
-# control, binary32 Jacobi, binary64 refinement, propagator increments, 2 block products,
-# state chain, state fill, terminal, costate chain, costate fill, derivative preparation,
-# pointwise, 2 x (block sources, panel chain, panel contraction), grad, hess partial, hess final
-LAUNCHES_PER_EVAL = 22
+# library kernel launches per gradient + Hessian evaluation on the time-blocked path:
+# control, binary32 Jacobi, binary64 refinement, 3 preparation parts (D, P~, X'),
+# 2 block products, state chain + fill, terminal, costate chain + fill, drift,
+# 3 pointwise parts (p^, y^/g, c), 3 block-source launches (Q, W/Gamma, backward),
+# tangent and second-order adjoint panels, 2 panel contractions, grad, hess partial,
+# hess final
+LAUNCHES_PER_EVAL = 27
 FP64_PEAK_TFLOPS = 1.26    # 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (measured 1.20 at 1.99 GHz)
 FP32_PEAK_TFLOPS = 80.5    # 152 SMs x 128 FMA/clk x 2 flop x 2.07 GHz (measured 70 at 1.99 GHz)
 

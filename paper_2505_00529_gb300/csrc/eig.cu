@@ -441,21 +441,25 @@ __global__ void __launch_bounds__(128) k_eig_jacobi32(const double* __restrict__
   const float eps = 5.96e-8f;
   const float off_tol2 = 16.f * eps * eps;
   const int kstep = 32 % NH, lstep = 32 / NH;    // stride 32 in a (row, col) enumeration over NH
+  const int NR = NP - 1;                         // rounds per sweep
   bool converged = false;
   for (int sweep = 0; sweep < 24 && !converged; ++sweep) {
     bool rot = false;
-    for (int r = 0; r < NP - 1; ++r) {
+    // round-robin positions of this lane's pair, advanced by one per round
+    int pa = (lane + NR - 1) % NR, qa = (NR - 1 - lane + NR) % NR;
+    for (int r = 0; r < NR; ++r) {
       if (lane < NH) {
-        int p = rr_elem(lane, r, NP), q = rr_elem(NP - 1 - lane, r, NP);
+        int p = lane == 0 ? 0 : pa + 1, q = qa + 1;
         if (p > q) { const int t = p; p = q; q = t; }
         float c = 1.f, s = 0.f;
         if (q < N) {
           const float apq = A[p * ld + q], app = A[p * ld + p], aqq = A[q * ld + q];
           const float thr = eps * 0.01f * sqrtf(fabsf(app) * fabsf(aqq));
           if (fabsf(apq) > thr && apq != 0.f) {
-            const float th = (aqq - app) / (2.f * apq);
-            const float t = (th >= 0.f ? 1.f : -1.f) / (fabsf(th) + sqrtf(th * th + 1.f));
-            c = 1.f / sqrtf(t * t + 1.f);
+            // binary32 start only (refined in binary64): fast reciprocals suffice
+            const float th = __fdividef(aqq - app, 2.f * apq);
+            const float t = copysignf(__fdividef(1.f, fabsf(th) + sqrtf(fmaf(th, th, 1.f))), th);
+            c = rsqrtf(fmaf(t, t, 1.f));
             s = t * c;
             rot = true;
           }
@@ -465,7 +469,56 @@ __global__ void __launch_bounds__(128) k_eig_jacobi32(const double* __restrict__
         cs[2 * lane] = c;
         cs[2 * lane + 1] = s;
       }
+      if (++pa == NR) pa = 0;
+      if (++qa == NR) qa = 0;
       __syncwarp();
+      if (kstep == 0) {
+        // NH divides 32: every lane keeps one row pair k (blocks) and one column pair l (V)
+        const int k = lane % NH;
+        const float ck = cs[2 * k], sk = cs[2 * k + 1];
+        const int p0 = pr[2 * k], p1 = pr[2 * k + 1];
+        for (int l = lane / NH; l < NH; l += lstep) {
+          const float sl = cs[2 * l + 1];
+          if (sk == 0.f && sl == 0.f) continue;
+          const float cl = cs[2 * l];
+          const int q0 = pr[2 * l], q1 = pr[2 * l + 1];
+          if (p1 >= N) {
+            if (q1 < N) {
+              const float x0 = A[p0 * ld + q0], x1 = A[p0 * ld + q1];
+              A[p0 * ld + q0] = cl * x0 - sl * x1;
+              A[p0 * ld + q1] = sl * x0 + cl * x1;
+            }
+          } else if (q1 >= N) {
+            const float x0 = A[p0 * ld + q0], x1 = A[p1 * ld + q0];
+            A[p0 * ld + q0] = ck * x0 - sk * x1;
+            A[p1 * ld + q0] = sk * x0 + ck * x1;
+          } else {
+            const float a00 = A[p0 * ld + q0], a01 = A[p0 * ld + q1];
+            const float a10 = A[p1 * ld + q0], a11 = A[p1 * ld + q1];
+            const float b00 = ck * a00 - sk * a10, b01 = ck * a01 - sk * a11;
+            const float b10 = sk * a00 + ck * a10, b11 = sk * a01 + ck * a11;
+            A[p0 * ld + q0] = cl * b00 - sl * b01;
+            A[p1 * ld + q1] = sl * b10 + cl * b11;
+            if (k == l) {
+              A[p0 * ld + q1] = 0.f;
+              A[p1 * ld + q0] = 0.f;
+            } else {
+              A[p0 * ld + q1] = sl * b00 + cl * b01;
+              A[p1 * ld + q0] = cl * b10 - sl * b11;
+            }
+          }
+        }
+        // V <- V R: this lane's column pair is k, rows i = lane / NH + lstep t
+        if (sk != 0.f && p1 < N) {
+          for (int i = lane / NH; i < N; i += lstep) {
+            const float v0 = V[i * ld + p0], v1 = V[i * ld + p1];
+            V[i * ld + p0] = ck * v0 - sk * v1;
+            V[i * ld + p1] = sk * v0 + ck * v1;
+          }
+        }
+        __syncwarp();
+        continue;
+      }
       // A <- R^T A R, block (k, l): rows of pair k, columns of pair l
       for (int k = lane % NH, l = lane / NH; l < NH;) {
         const float sk = cs[2 * k + 1], sl = cs[2 * l + 1];
