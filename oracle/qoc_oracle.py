@@ -140,7 +140,7 @@ def propagators(W, lam, dt):
 
 def rotated_dipoles(W, M):
     """M~_j = W_j^T M W_j, the dipole matrix in the eigenbasis of H_j."""
-    return np.einsum("jrp,rs,jsq->jpq", W, M, W)
+    return np.einsum("jrp,rs,jsq->jpq", W, M, W, optimize=True)
 
 
 def frechet1(W, lam, M, dt):
@@ -148,7 +148,7 @@ def frechet1(W, lam, M, dt):
     Gamma1_pq = phi[lambda_p, lambda_q] (Daleckii-Krein)."""
     Mt = rotated_dipoles(W, M)
     G1 = dd1(lam[:, :, None], lam[:, None, :], dt)
-    return np.einsum("jpr,jrs,jqs->jpq", W, G1 * Mt, W)
+    return np.einsum("jpr,jrs,jqs->jpq", W, G1 * Mt, W, optimize=True)
 
 
 def frechet2(W, lam, M, dt, chunk=64):
@@ -162,7 +162,7 @@ def frechet2(W, lam, M, dt, chunk=64):
         L = lam[j0:j1]
         G2 = dd2(L[:, :, None, None], L[:, None, :, None], L[:, None, None, :], dt)  # [j, p, r, q]
         X = 2.0 * np.einsum("jpr,jrq,jprq->jpq", Mt[j0:j1], Mt[j0:j1], G2)
-        out[j0:j1] = np.einsum("jpr,jrs,jqs->jpq", W[j0:j1], X, W[j0:j1])
+        out[j0:j1] = np.einsum("jpr,jrs,jqs->jpq", W[j0:j1], X, W[j0:j1], optimize=True)
     return out
 
 
