@@ -335,8 +335,9 @@ int qoc_max_basis_size(void);
 /* Release everything the problem owns (NULL is a no-op). */
 void qoc_destroy_problem(qoc_problem* p);
 
-/* Text of the last CUDA error this thread saw inside the library (empty if
- * none); valid until the thread's next failing call. */
+/* Text of the last failure this thread saw inside the library: the CUDA
+ * error, or the device status bits behind QOC_ENUMERIC / QOC_ETIMEOUT, or a
+ * size limit (empty if none); valid until the thread's next failing call. */
 const char* qoc_last_error(void);
 
 /* Static, human-readable name of a status. */

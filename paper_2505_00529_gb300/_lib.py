@@ -51,8 +51,9 @@ class QocError(RuntimeError):
     def __init__(self, status, where):
         self.status = status
         detail = ""
-        if status == QOC_ECUDA:
-            detail = " [" + lib().qoc_last_error().decode() + "]"
+        if status in (QOC_ECUDA, QOC_ENUMERIC, QOC_ETIMEOUT, QOC_EUNSUPPORTED):
+            msg = lib().qoc_last_error().decode()
+            detail = f" [{msg}]" if msg else ""
         super().__init__(f"{where}: {status_string(status)} (status {status}){detail}")
 
 

@@ -27,9 +27,9 @@
 using namespace qoc;
 
 namespace {
-constexpr int kMaxN = 64;       // largest basis the shared-memory kernels take in this build
+constexpr int kMaxN = 256;      // largest basis (above 64 the per-step kernels use a global workspace)
 constexpr int kMaxK = 4096;
-constexpr int kMaxKTR = 64;     // trust region: Hessian eigensolver in shared memory
+constexpr int kMaxKTR = 256;    // trust region: K x K Hessian eigensolver
 }  // namespace
 
 struct qoc_problem {
@@ -64,6 +64,8 @@ struct qoc_problem {
   double2 *alpha = nullptr, *beta = nullptr, *Ptil = nullptr, *Xp = nullptr, *SJ = nullptr,
           *lamJ = nullptr;
   double* Mtil = nullptr;               // M~_j = W_j^T M W_j (three-stream schedule)
+  StepSpace ws[3];                      // per-step storage beyond shared memory, one region per
+                                        // stream (main, chains, panels); empty for N <= 64
   void *D = nullptr, *a_hat = nullptr, *l_hat = nullptr, *p_hat = nullptr, *y_hat = nullptr;
   int* status = nullptr;
   double *trwork = nullptr, *trstep = nullptr, *trinfo = nullptr, *trzero = nullptr;
@@ -140,6 +142,9 @@ qoc_status device_status(qoc_problem* p) {
   int s = *p->hstatus;
   *p->hstatus = 0;
   if (s == 0) return QOC_OK;
+  std::snprintf(g_last_error, sizeof(g_last_error),
+                "device status 0x%x (1: eigensolver not converged, 2: bounded wait gave up, "
+                "4: non-finite value, 8: unsupported shape)", s);
   if (s & DEV_TIMEOUT) return QOC_ETIMEOUT;
   if (s & DEV_BADSHAPE) return QOC_EUNSUPPORTED;
   return QOC_ENUMERIC;
@@ -196,7 +201,7 @@ qoc_status enqueue_blocked(qoc_problem* p, int order, double* out_dev) {
   const void* Bsrc = mixed ? static_cast<const void*>(p->Bf) : static_cast<const void*>(p->B);
   if (order == 0) {
     p->sched = 0;
-    QOC_TRY(launch_block_delta(p->D, p->dstride, N, J, bs, 0, mixed, p->Mf, p->mstride, st));
+    QOC_TRY(launch_block_delta(p->D, p->dstride, N, J, bs, 0, mixed, p->Mf, p->mstride, st, p->ws[0]));
     QOC_TRY(launch_bsweep(chain_sweep_args(p, 0), mixed, st));
     QOC_TRY(launch_block_fill(p->D, p->dstride, N, J, bs, 0, mixed, p->Xa, p->a_hat, st));
     QOC_TRY(launch_terminal(p->f, J, p->a_hat, mixed, p->beta, N, cexpi_h(thetaJ), p->w_f, p->w_t,
@@ -212,8 +217,8 @@ qoc_status enqueue_blocked(qoc_problem* p, int order, double* out_dev) {
   // ---- chains ----
   QOC_TRY(cudaStreamWaitEvent(cs, p->fork, 0));
   if (p->timing) cudaEventRecord(p->ev[10], cs);
-  QOC_TRY(launch_block_delta(p->D, p->dstride, N, J, bs, 0, mixed, p->Mf, p->mstride, cs));
-  QOC_TRY(launch_block_delta(p->D, p->dstride, N, J, bs, 1, mixed, p->Mb, p->mstride, cs));
+  QOC_TRY(launch_block_delta(p->D, p->dstride, N, J, bs, 0, mixed, p->Mf, p->mstride, cs, p->ws[1]));
+  QOC_TRY(launch_block_delta(p->D, p->dstride, N, J, bs, 1, mixed, p->Mb, p->mstride, cs, p->ws[1]));
   QOC_TRY(launch_bsweep(chain_sweep_args(p, 0), mixed, cs));
   QOC_TRY(launch_block_fill(p->D, p->dstride, N, J, bs, 0, mixed, p->Xa, p->a_hat, cs));
   QOC_TRY(launch_terminal(p->f, J, p->a_hat, mixed, p->beta, N, cexpi_h(thetaJ), p->w_f, p->w_t,
@@ -226,7 +231,7 @@ qoc_status enqueue_blocked(qoc_problem* p, int order, double* out_dev) {
   QOC_TRY(cudaEventRecord(p->join, cs));
   // ---- main: P~ ----
   QOC_TRY(launch_prep(p->W, p->eig, p->M, N, J, p->dt, p->mshift, p->D, p->dstride, mixed ? 0 : 1,
-                      PREP_P, p->Ptil, p->Xp, p->Mtil, p->status, st));
+                      PREP_P, p->Ptil, p->Xp, p->Mtil, p->status, st, p->ws[0]));
   QOC_TRY(cudaEventRecord(p->ev_ptil, st));
   if (order >= 2) {
     // ---- panels ----
@@ -235,20 +240,20 @@ qoc_status enqueue_blocked(qoc_problem* p, int order, double* out_dev) {
     if (p->timing) cudaEventRecord(p->ev[12], ps);
     QOC_TRY(launch_drift(p->a_hat, mixed, N, J, p->scal + 1, ps));
     QOC_TRY(launch_pointwise(p->W, p->Ptil, p->Xp, p->a_hat, p->l_hat, mixed, N, J, kappa, p->p_hat,
-                             p->y_hat, p->g, p->c, PW_P, ps));
+                             p->y_hat, p->g, p->c, PW_P, ps, p->ws[2]));
     QOC_TRY(launch_block_src(p->D, p->dstride, N, J, bs, 0, mixed, p->p_hat, p->y_hat, p->vstride,
-                             p->Qf, p->Wf, p->Gf, p->qstride, p->gstride, BS_Q, ps));
+                             p->Qf, p->Wf, p->Gf, p->qstride, p->gstride, BS_Q, ps, p->ws[2]));
     QOC_TRY(launch_bsweep(panel_sweep_args(p, 0), mixed, ps));
     QOC_TRY(cudaStreamWaitEvent(ps, p->join, 0));
     QOC_TRY(launch_pointwise(p->W, p->Ptil, p->Xp, p->a_hat, p->l_hat, mixed, N, J, kappa, p->p_hat,
-                             p->y_hat, p->g, p->c, PW_Y, ps));
+                             p->y_hat, p->g, p->c, PW_Y, ps, p->ws[2]));
     QOC_TRY(launch_block_src(p->D, p->dstride, N, J, bs, 0, mixed, p->p_hat, p->y_hat, p->vstride,
-                             p->Qf, p->Wf, p->Gf, p->qstride, p->gstride, BS_WG, ps));
+                             p->Qf, p->Wf, p->Gf, p->qstride, p->gstride, BS_WG, ps, p->ws[2]));
     QOC_TRY(launch_block_contract(p->XS, p->Wf, p->Gf, p->qstride, p->gstride, Bsrc, p->Kp, N, K, J,
                                   bs, 0, mixed, p->U, ps));
     if (soa) {
       QOC_TRY(launch_block_src(p->D, p->dstride, N, J, bs, 1, mixed, p->y_hat, p->p_hat, p->vstride,
-                               p->Qb, p->Wb, p->Gb, p->qstride, p->gstride, BS_Q | BS_WG, ps));
+                               p->Qb, p->Wb, p->Gb, p->qstride, p->gstride, BS_Q | BS_WG, ps, p->ws[2]));
       QOC_TRY(launch_bsweep(panel_sweep_args(p, 1), mixed, ps));
       QOC_TRY(launch_block_contract(p->Xmu, p->Wb, p->Gb, p->qstride, p->gstride, Bsrc, p->Kp, N, K,
                                     J, bs, 1, mixed, p->V, ps));
@@ -257,11 +262,11 @@ qoc_status enqueue_blocked(qoc_problem* p, int order, double* out_dev) {
     QOC_TRY(cudaEventRecord(p->ev_panels, ps));
     // ---- main: X', c_j ----
     QOC_TRY(launch_prep(p->W, p->eig, p->M, N, J, p->dt, p->mshift, p->D, p->dstride, mixed ? 0 : 1,
-                        PREP_X, p->Ptil, p->Xp, p->Mtil, p->status, st));
+                        PREP_X, p->Ptil, p->Xp, p->Mtil, p->status, st, p->ws[0]));
     if (p->timing) cudaEventRecord(p->ev[3], st);
     QOC_TRY(cudaStreamWaitEvent(st, p->join, 0));
     QOC_TRY(launch_pointwise(p->W, p->Ptil, p->Xp, p->a_hat, p->l_hat, mixed, N, J, kappa, p->p_hat,
-                             p->y_hat, p->g, p->c, PW_C, st));
+                             p->y_hat, p->g, p->c, PW_C, st, p->ws[0]));
     if (p->timing) cudaEventRecord(p->ev[4], st);
     QOC_TRY(cudaStreamWaitEvent(st, p->ev_panels, 0));
   } else {
@@ -273,7 +278,7 @@ qoc_status enqueue_blocked(qoc_problem* p, int order, double* out_dev) {
     QOC_TRY(cudaStreamWaitEvent(st, p->join, 0));
     QOC_TRY(launch_drift(p->a_hat, mixed, N, J, p->scal + 1, st));
     QOC_TRY(launch_pointwise(p->W, p->Ptil, p->Xp, p->a_hat, p->l_hat, mixed, N, J, kappa, p->p_hat,
-                             p->y_hat, p->g, p->c, PW_Y, st));
+                             p->y_hat, p->g, p->c, PW_Y, st, p->ws[0]));
     if (p->timing) cudaEventRecord(p->ev[4], st);
   }
   if (p->timing) cudaEventRecord(p->ev[5], st);
@@ -299,17 +304,17 @@ qoc_status enqueue_eval(qoc_problem* p, const double* theta_dev, int order, doub
   }
   QOC_TRY(launch_eig(p->H0, p->M, p->f, N, J, p->W, p->eig, p->status,
                      p->eig_method == QOC_EIG_JACOBI_FP64 ? EIG_JACOBI_FP64 : EIG_REFINED,
-                     p->refine_sweeps, p->angle_tol, st, p->timing ? p->ev[8] : nullptr,
+                     p->refine_sweeps, p->angle_tol, st, p->ws[0], p->timing ? p->ev[8] : nullptr,
                      p->timing ? p->eigstats : nullptr));
   if (p->timing) cudaEventRecord(p->ev[1], st);
   QOC_TRY(launch_prep(p->W, p->eig, p->M, N, J, p->dt, p->mshift, p->D, p->dstride, d_fp64, PREP_D,
-                      p->Ptil, p->Xp, nullptr, p->status, st));
+                      p->Ptil, p->Xp, nullptr, p->status, st, p->ws[0]));
   if (p->timing) cudaEventRecord(p->ev[2], st);
   if (p->bs > 1) return enqueue_blocked(p, order, out_dev);
   p->sched = 0;
   if (order >= 1)
     QOC_TRY(launch_prep(p->W, p->eig, p->M, N, J, p->dt, p->mshift, p->D, p->dstride, d_fp64,
-                        PREP_P | PREP_X, p->Ptil, p->Xp, nullptr, p->status, st));
+                        PREP_P | PREP_X, p->Ptil, p->Xp, nullptr, p->status, st, p->ws[0]));
   if (p->timing) cudaEventRecord(p->ev[9], st);
   SweepArgs a{};
   a.N = N; a.K = 1; a.Kp = p->Kp; a.J = J; a.kc = 1; a.backward = 0;
@@ -330,7 +335,7 @@ qoc_status enqueue_eval(qoc_problem* p, const double* theta_dev, int order, doub
   if (p->timing) cudaEventRecord(p->ev[3], st);
   const double2 kappa = cexpi_h(p->dt * p->mshift);
   QOC_TRY(launch_pointwise(p->W, p->Ptil, p->Xp, p->a_hat, p->l_hat, mixed, N, J, kappa, p->p_hat,
-                           p->y_hat, p->g, p->c, PW_P | PW_Y | (order >= 2 ? PW_C : 0), st));
+                           p->y_hat, p->g, p->c, PW_P | PW_Y | (order >= 2 ? PW_C : 0), st, p->ws[0]));
   if (p->timing) cudaEventRecord(p->ev[4], st);
   if (order >= 2) {
     SweepArgs s{};
@@ -483,7 +488,9 @@ qoc_status qoc_create_problem(int N, const double* H0, const double* M, const do
   // until W is orthonormal to the binary64 floor (at most 4 updates), then a
   // clean-up of every rotation angle above 1e-13 (smaller angles move the
   // propagators by less than 1e-13 dt |lambda_p - lambda_q|)
-  p->refine_sweeps = 4;
+  // binary64 refinement updates allowed per step: the binary32 start is
+  // coarser relative to the eigenvalue gaps at large N
+  p->refine_sweeps = N <= 64 ? 4 : 8;
   p->angle_tol = 1e-13;
   double tr = 0;
   for (int i = 0; i < N; ++i) tr += H0[i * N + i];
@@ -579,6 +586,30 @@ qoc_status qoc_create_problem(int N, const double* H0, const double* M, const do
     ALLOC(p->trstep, 8 * (size_t)K);
     ALLOC(p->trinfo, 8 * 8);
     ALLOC(p->trzero, 8 * ((size_t)K * K + 1));
+  }
+  {
+    // Per-step storage for matrices that do not fit in shared memory (N > 64,
+    // or the trust region's K x K eigensolver for K > 64): one region per
+    // stream, each a slice per CTA of a persistent grid.
+    const int mx = precision == QOC_MIXED_FP32 ? 1 : 0;
+    size_t need = 0;
+    for (size_t v : {eig_step_bytes(N), prep_smem_bytes(N), pointwise_step_bytes(N),
+                     block_delta_bytes(N, mx), block_src_bytes(N, 8, mx)})
+      need = v > need ? v : need;
+    const size_t need_tr = K <= kMaxKTR ? eig_step_bytes(K) : 0;
+    int nsm = 1, dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    const size_t big = 200 * 1024;
+    for (int r = 0; r < 3; ++r) {
+      size_t per = need;
+      if (r == 0 && need_tr > per) per = need_tr;
+      if (per <= big) continue;
+      per = (per + 255) & ~size_t(255);
+      const size_t nct = (r == 0 ? 2 : 1) * (size_t)nsm;
+      ALLOC(p->ws[r].base, per * nct);
+      p->ws[r].bytes = per * nct;
+    }
   }
 #undef ALLOC
   p->hbuf_len = 2 * (1 + (size_t)K + (size_t)K * K) + 2 * (size_t)K + 2 * (size_t)N + 64;
@@ -808,7 +839,7 @@ qoc_status qoc_trust_region_solve(qoc_problem* p, const double* theta0, const qo
     qoc_status s = enqueue_eval(p, p->theta, 2, p->out);
     if (s != QOC_OK) return s;
     QOC_TRY(launch_eig(p->out + 1 + K, p->trzero, p->trzero, K, 1, p->trwork + 3 * K,
-                       p->trwork + 2 * K, p->status, EIG_JACOBI_FP64, 0, 0.0, st));
+                       p->trwork + 2 * K, p->status, EIG_JACOBI_FP64, 0, 0.0, st, p->ws[0]));
     QOC_TRY(cudaMemcpyAsync(p->hstatus, p->status, sizeof(int), cudaMemcpyDeviceToHost, st));
     QOC_TRY(cudaMemsetAsync(p->status, 0, sizeof(int), st));
     QOC_TRY(cudaStreamSynchronize(st));
@@ -913,11 +944,11 @@ qoc_status batch_phase(qoc_batch* b, int i, int phase, cudaStream_t s) {
       QOC_TRY(launch_control(p->B, p->Kp, p->theta, J, K, p->f, s));
       QOC_TRY(launch_eig(p->H0, p->M, p->f, N, J, p->W, p->eig, p->status,
                          p->eig_method == QOC_EIG_JACOBI_FP64 ? EIG_JACOBI_FP64 : EIG_REFINED,
-                         p->refine_sweeps, p->angle_tol, s));
+                         p->refine_sweeps, p->angle_tol, s, p->ws[0]));
       QOC_TRY(launch_prep(p->W, p->eig, p->M, N, J, p->dt, p->mshift, p->D, p->dstride, mixed ? 0 : 1,
-                          PREP_D | PREP_P | PREP_X, p->Ptil, p->Xp, nullptr, p->status, s));
-      QOC_TRY(launch_block_delta(p->D, p->dstride, N, J, bs, 0, mixed, p->Mf, p->mstride, s));
-      QOC_TRY(launch_block_delta(p->D, p->dstride, N, J, bs, 1, mixed, p->Mb, p->mstride, s));
+                          PREP_D | PREP_P | PREP_X, p->Ptil, p->Xp, nullptr, p->status, s, p->ws[0]));
+      QOC_TRY(launch_block_delta(p->D, p->dstride, N, J, bs, 0, mixed, p->Mf, p->mstride, s, p->ws[0]));
+      QOC_TRY(launch_block_delta(p->D, p->dstride, N, J, bs, 1, mixed, p->Mb, p->mstride, s, p->ws[0]));
       return QOC_OK;
     case 1: {
       QOC_TRY(launch_block_fill(p->D, p->dstride, N, J, bs, 0, mixed, p->Xa, p->a_hat, s));
@@ -930,16 +961,16 @@ qoc_status batch_phase(qoc_batch* b, int i, int phase, cudaStream_t s) {
     case 2:
       QOC_TRY(launch_block_fill(p->D, p->dstride, N, J, bs, 1, mixed, p->Xl, p->l_hat, s));
       QOC_TRY(launch_pointwise(p->W, p->Ptil, p->Xp, p->a_hat, p->l_hat, mixed, N, J,
-                               cexpi_h(p->dt * p->mshift), p->p_hat, p->y_hat, p->g, p->c, PW_P | PW_Y | PW_C, s));
+                               cexpi_h(p->dt * p->mshift), p->p_hat, p->y_hat, p->g, p->c, PW_P | PW_Y | PW_C, s, p->ws[0]));
       QOC_TRY(launch_block_src(p->D, p->dstride, N, J, bs, 0, mixed, p->p_hat, p->y_hat, p->vstride,
-                               p->Qf, p->Wf, p->Gf, p->qstride, p->gstride, BS_Q | BS_WG, s));
+                               p->Qf, p->Wf, p->Gf, p->qstride, p->gstride, BS_Q | BS_WG, s, p->ws[0]));
       return QOC_OK;
     case 3:
       QOC_TRY(launch_block_contract(p->XS, p->Wf, p->Gf, p->qstride, p->gstride, Bsrc, p->Kp, N, K, J,
                                     bs, 0, mixed, p->U, s));
       if (p->hess_method == QOC_HESS_SECOND_ORDER_ADJOINT)
         QOC_TRY(launch_block_src(p->D, p->dstride, N, J, bs, 1, mixed, p->y_hat, p->p_hat, p->vstride,
-                                 p->Qb, p->Wb, p->Gb, p->qstride, p->gstride, BS_Q | BS_WG, s));
+                                 p->Qb, p->Wb, p->Gb, p->qstride, p->gstride, BS_Q | BS_WG, s, p->ws[0]));
       return QOC_OK;
     default:
       if (p->hess_method == QOC_HESS_SECOND_ORDER_ADJOINT)

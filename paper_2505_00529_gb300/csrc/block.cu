@@ -49,11 +49,11 @@ __device__ __forceinline__ C load_E(const unsigned char* D, size_t dstride, int 
 // column-wise (y_i = sum_q M[q][i] x_q).
 // ---------------------------------------------------------------------------
 template <bool MIX>
-__global__ void k_block_delta(const unsigned char* __restrict__ D, size_t dstride, int N, int J,
-                              int bsteps, int bwd, unsigned char* __restrict__ Mo, size_t mstride) {
+__device__ __forceinline__ void block_delta_step(const unsigned char* __restrict__ D, size_t dstride,
+                                                 int N, int J, int bsteps, int bwd,
+                                                 unsigned char* __restrict__ Mo, size_t mstride,
+                                                 int blk, unsigned char* smem_raw) {
   using C = typename BlkT<MIX>::C;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int blk = blockIdx.x;
   const int t0 = blk * bsteps;
   if (t0 >= J) return;
   const int bl = min(bsteps, J - t0);
@@ -93,6 +93,19 @@ __global__ void k_block_delta(const unsigned char* __restrict__ D, size_t dstrid
   }
 }
 
+// one block per CTA in shared memory, or a persistent grid over a global workspace
+template <bool MIX>
+__global__ void k_block_delta(const unsigned char* __restrict__ D, size_t dstride, int N, int J,
+                              int bsteps, int bwd, unsigned char* __restrict__ Mo, size_t mstride,
+                              int nblk, unsigned char* gws, size_t per_cta) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  unsigned char* base = gws ? gws + (size_t)blockIdx.x * per_cta : smem_raw;
+  for (int blk = blockIdx.x; blk < nblk; blk += gridDim.x) {
+    block_delta_step<MIX>(D, dstride, N, J, bsteps, bwd, Mo, mstride, blk, base);
+    __syncthreads();
+  }
+}
+
 // ---------------------------------------------------------------------------
 // Q, W, Gamma per block for one direction (one CTA per block).
 //   forward recursion  Qk <- Qk + E_k Qk + s_k e_k^T, Gamma_{k,.} = z_k^H Qk (before)
@@ -104,16 +117,17 @@ __global__ void k_block_delta(const unsigned char* __restrict__ D, size_t dstrid
 // backward.
 // ---------------------------------------------------------------------------
 template <bool MIX>
-__global__ void k_block_src(const unsigned char* __restrict__ D, size_t dstride, int N, int J,
-                            int bsteps, int bwd, const unsigned char* __restrict__ src,
-                            const unsigned char* __restrict__ ctr, size_t vstride,
-                            unsigned char* __restrict__ Qo, unsigned char* __restrict__ Wo,
-                            unsigned char* __restrict__ Go, size_t qstride, size_t gstride,
-                            int what) {
+__device__ __forceinline__ void block_src_step(const unsigned char* __restrict__ D, size_t dstride,
+                                               int N, int J, int bsteps, int bwd,
+                                               const unsigned char* __restrict__ src,
+                                               const unsigned char* __restrict__ ctr, size_t vstride,
+                                               unsigned char* __restrict__ Qo,
+                                               unsigned char* __restrict__ Wo,
+                                               unsigned char* __restrict__ Go, size_t qstride,
+                                               size_t gstride, int what, int blk,
+                                               unsigned char* smem_raw) {
   using C = typename BlkT<MIX>::C;
   const bool wq = what & BS_Q, wg = what & BS_WG;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int blk = blockIdx.x;
   const int t0 = blk * bsteps;
   if (t0 >= J) return;
   const int bl = min(bsteps, J - t0);
@@ -207,6 +221,22 @@ __global__ void k_block_src(const unsigned char* __restrict__ D, size_t dstride,
   }
   C* wo = reinterpret_cast<C*>(Wo + (size_t)blk * qstride);
   for (int e = tid; e < bsteps * N; e += nt) wo[e] = (e / N) < bl ? Pn[e] : cz<C>();
+}
+
+template <bool MIX>
+__global__ void k_block_src(const unsigned char* __restrict__ D, size_t dstride, int N, int J,
+                            int bsteps, int bwd, const unsigned char* __restrict__ src,
+                            const unsigned char* __restrict__ ctr, size_t vstride,
+                            unsigned char* __restrict__ Qo, unsigned char* __restrict__ Wo,
+                            unsigned char* __restrict__ Go, size_t qstride, size_t gstride,
+                            int what, int nblk, unsigned char* gws, size_t per_cta) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  unsigned char* base = gws ? gws + (size_t)blockIdx.x * per_cta : smem_raw;
+  for (int blk = blockIdx.x; blk < nblk; blk += gridDim.x) {
+    block_src_step<MIX>(D, dstride, N, J, bsteps, bwd, src, ctr, vstride, Qo, Wo, Go, qstride,
+                        gstride, what, blk, base);
+    __syncthreads();
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -326,48 +356,58 @@ __global__ void k_block_fill(const unsigned char* __restrict__ D, size_t dstride
 // ---------------------------------------------------------------------------
 // launchers
 // ---------------------------------------------------------------------------
+size_t block_delta_bytes(int N, int mixed) { return 3 * (size_t)N * (N + 1) * (mixed ? 8 : 16); }
+size_t block_src_bytes(int N, int bsteps, int mixed) {
+  return ((size_t)N * (N + 1) + 2 * (size_t)bsteps * N + (size_t)bsteps * bsteps) * (mixed ? 8 : 16);
+}
+
 cudaError_t launch_block_delta(const void* D, size_t dstride, int N, int J, int bsteps, int bwd,
-                               int mixed, void* M, size_t mstride, cudaStream_t st) {
+                               int mixed, void* M, size_t mstride, cudaStream_t st,
+                               const StepSpace& ws) {
   const int nblk = (J + bsteps - 1) / bsteps;
-  const size_t cs = mixed ? 8 : 16;
-  const size_t smem = 3 * (size_t)N * (N + 1) * cs;
-  const int threads = N <= 16 ? 128 : 256;
+  const int threads = N <= 16 ? 128 : (N <= 128 ? 256 : 512);
+  StepGrid g;
   if (mixed) {
-    set_max_smem((const void*)k_block_delta<true>);
-    k_block_delta<true><<<nblk, threads, smem, st>>>((const unsigned char*)D, dstride, N, J, bsteps,
-                                                     bwd, (unsigned char*)M, mstride);
+    if (!step_grid(block_delta_bytes(N, 1), nblk, ws, (const void*)k_block_delta<true>, g))
+      return cudaErrorInvalidConfiguration;
+    k_block_delta<true><<<g.grid, threads, g.smem, st>>>((const unsigned char*)D, dstride, N, J, bsteps,
+                                                         bwd, (unsigned char*)M, mstride, nblk, g.gws,
+                                                         g.per_cta);
   } else {
-    set_max_smem((const void*)k_block_delta<false>);
-    k_block_delta<false><<<nblk, threads, smem, st>>>((const unsigned char*)D, dstride, N, J, bsteps,
-                                                      bwd, (unsigned char*)M, mstride);
+    if (!step_grid(block_delta_bytes(N, 0), nblk, ws, (const void*)k_block_delta<false>, g))
+      return cudaErrorInvalidConfiguration;
+    k_block_delta<false><<<g.grid, threads, g.smem, st>>>((const unsigned char*)D, dstride, N, J, bsteps,
+                                                          bwd, (unsigned char*)M, mstride, nblk, g.gws,
+                                                          g.per_cta);
   }
   return cudaGetLastError();
 }
-
 cudaError_t launch_block_src(const void* D, size_t dstride, int N, int J, int bsteps, int bwd,
                              int mixed, const void* src, const void* ctr, size_t vstride, void* Q,
                              void* W, void* G, size_t qstride, size_t gstride, int what,
-                             cudaStream_t st) {
+                             cudaStream_t st, const StepSpace& ws) {
   const int nblk = (J + bsteps - 1) / bsteps;
-  const size_t cs = mixed ? 8 : 16;
-  const size_t smem = ((size_t)N * (N + 1) + 2 * (size_t)bsteps * N + (size_t)bsteps * bsteps) * cs;
-  const int threads = 256;
+  const int threads = N <= 128 ? 256 : 512;
+  StepGrid g;
   if (mixed) {
-    set_max_smem((const void*)k_block_src<true>);
-    k_block_src<true><<<nblk, threads, smem, st>>>((const unsigned char*)D, dstride, N, J, bsteps, bwd,
-                                                   (const unsigned char*)src, (const unsigned char*)ctr,
-                                                   vstride, (unsigned char*)Q, (unsigned char*)W,
-                                                   (unsigned char*)G, qstride, gstride, what);
+    if (!step_grid(block_src_bytes(N, bsteps, 1), nblk, ws, (const void*)k_block_src<true>, g))
+      return cudaErrorInvalidConfiguration;
+    k_block_src<true><<<g.grid, threads, g.smem, st>>>((const unsigned char*)D, dstride, N, J, bsteps, bwd,
+                                                       (const unsigned char*)src, (const unsigned char*)ctr,
+                                                       vstride, (unsigned char*)Q, (unsigned char*)W,
+                                                       (unsigned char*)G, qstride, gstride, what, nblk,
+                                                       g.gws, g.per_cta);
   } else {
-    set_max_smem((const void*)k_block_src<false>);
-    k_block_src<false><<<nblk, threads, smem, st>>>((const unsigned char*)D, dstride, N, J, bsteps, bwd,
-                                                    (const unsigned char*)src, (const unsigned char*)ctr,
-                                                    vstride, (unsigned char*)Q, (unsigned char*)W,
-                                                    (unsigned char*)G, qstride, gstride, what);
+    if (!step_grid(block_src_bytes(N, bsteps, 0), nblk, ws, (const void*)k_block_src<false>, g))
+      return cudaErrorInvalidConfiguration;
+    k_block_src<false><<<g.grid, threads, g.smem, st>>>((const unsigned char*)D, dstride, N, J, bsteps, bwd,
+                                                        (const unsigned char*)src, (const unsigned char*)ctr,
+                                                        vstride, (unsigned char*)Q, (unsigned char*)W,
+                                                        (unsigned char*)G, qstride, gstride, what, nblk,
+                                                        g.gws, g.per_cta);
   }
   return cudaGetLastError();
 }
-
 cudaError_t launch_block_contract(const void* Xblk, const void* W, const void* G, size_t qstride,
                                   size_t gstride, const void* Brow, int Kp, int N, int K, int J,
                                   int bsteps, int bwd, int mixed, void* contr, cudaStream_t st) {

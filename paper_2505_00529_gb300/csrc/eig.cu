@@ -177,13 +177,12 @@ __device__ void sort_write(const T* A, const T* V, int N, int ld, double* Wj, do
 }
 
 template <typename T>
-__global__ void k_eig_jacobi(const double* __restrict__ H0, const double* __restrict__ M,
-                             const double* __restrict__ f, int N, int J,
-                             double* __restrict__ W_out, double* __restrict__ eig_out,
-                             int* status) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int j = blockIdx.x;
-  if (j >= J) return;
+__device__ __forceinline__ void eig_jacobi_step(const double* __restrict__ H0,
+                                                const double* __restrict__ M,
+                                                const double* __restrict__ f, int N, int j,
+                                                double* __restrict__ W_out,
+                                                double* __restrict__ eig_out, int* status,
+                                                unsigned char* smem_raw) {
   const int ld = N + 1;
   const int NP = N + (N & 1);
   T* A = reinterpret_cast<T*>(smem_raw);
@@ -200,23 +199,42 @@ __global__ void k_eig_jacobi(const double* __restrict__ H0, const double* __rest
     V[p * ld + q] = (T)(p == q ? 1.0 : 0.0);
   }
   __syncthreads();
-  const int ok = jacobi_sweeps<T>(A, V, N, ld, JacobiEps<T>::max_sweeps, (T)0,
-                                  4.0 * JacobiEps<T>::eps, cs, pr, red);
-  if (!ok && tid == 0) raise_status(status, DEV_EIG_NOCONV);
+  // The rounding floor of off(A) grows with N (about sqrt(N) eps |A|_F), so the
+  // stopping tolerance does too: 4 eps for N <= 16, 4 eps sqrt(N / 16) above.
+  // A binary32 result only seeds the binary64 refinement, which checks the
+  // outcome itself; only the binary64 method reports non-convergence here.
+  const double off_tol = 4.0 * JacobiEps<T>::eps * sqrt(fmax(1.0, N / 16.0));
+  const int ok = jacobi_sweeps<T>(A, V, N, ld, JacobiEps<T>::max_sweeps, (T)0, off_tol, cs, pr, red);
+  if (!ok && sizeof(T) == sizeof(double) && tid == 0) raise_status(status, DEV_EIG_NOCONV);
   sort_write<T>(A, V, N, ld, W_out + (size_t)j * N * N, eig_out + (size_t)j * N);
+}
+
+// One matrix per CTA in shared memory, or (gws != nullptr, large N) a
+// persistent grid whose CTAs each own a slice of a global workspace.
+template <typename T>
+__global__ void k_eig_jacobi(const double* __restrict__ H0, const double* __restrict__ M,
+                             const double* __restrict__ f, int N, int J,
+                             double* __restrict__ W_out, double* __restrict__ eig_out,
+                             int* status, unsigned char* gws, size_t per_cta) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  unsigned char* base = gws ? gws + (size_t)blockIdx.x * per_cta : smem_raw;
+  for (int j = blockIdx.x; j < J; j += gridDim.x) {
+    eig_jacobi_step<T>(H0, M, f, N, j, W_out, eig_out, status, base);
+    __syncthreads();
+  }
 }
 
 // Ogita-Aishima refinement sweeps in binary64 (at most `sweeps` updates,
 // stopping once |I - W^T W|_F reaches the binary64 floor), then a binary64
 // Jacobi clean-up of S = W^T H W that resolves what the refinement leaves
 // alone (pairs closer than its cluster threshold), then W <- W V.
-__global__ void k_eig_refine(const double* __restrict__ H0, const double* __restrict__ M,
-                             const double* __restrict__ f, int N, int J, int sweeps,
-                             double angle_tol, double* __restrict__ W_io,
-                             double* __restrict__ eig_out, int* status, unsigned int* stats) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int j = blockIdx.x;
-  if (j >= J) return;
+__device__ __forceinline__ void eig_refine_step(const double* __restrict__ H0,
+                                                const double* __restrict__ M,
+                                                const double* __restrict__ f, int N, int j,
+                                                int sweeps, double angle_tol,
+                                                double* __restrict__ W_io,
+                                                double* __restrict__ eig_out, int* status,
+                                                unsigned int* stats, unsigned char* smem_raw) {
   const int ld = N + 1;
   const int NP = N + (N & 1);
   double* H = reinterpret_cast<double*>(smem_raw);
@@ -370,7 +388,12 @@ __global__ void k_eig_refine(const double* __restrict__ H0, const double* __rest
   __shared__ int any_rot;
   if (tid == 0) any_rot = 0;
   __syncthreads();
-  const int ok = jacobi_sweeps<double>(S, R, N, ld, 12, angle_tol, 0.0, cs, pr, red);
+  // stops at no rotation or once off(S) is at the rounding floor of
+  // S = W^T H W itself (length-N dot products: about N eps |S|_F; 8 N eps used):
+  // a pair still mixed below that is a near-degenerate one whose mixing changes
+  // neither the propagator nor the eigenvalues measurably
+  const int ok = jacobi_sweeps<double>(S, R, N, ld, N <= 64 ? 12 : 30, angle_tol,
+                                       8.0 * 1.12e-16 * (double)N, cs, pr, red);
   if (!ok && tid == 0) raise_status(status, DEV_EIG_NOCONV);
   // did anything rotate?  (V != I)
   for (int e = tid; e < N * N; e += nt) {
@@ -395,6 +418,19 @@ __global__ void k_eig_refine(const double* __restrict__ H0, const double* __rest
   for (int i = tid; i < N; i += nt) bad |= !isfinite(S[i * ld + i]);
   if (bad) raise_status(status, DEV_NONFINITE);
   sort_write<double>(S, W, N, ld, Wg, eig_out + (size_t)j * N);
+}
+
+__global__ void k_eig_refine(const double* __restrict__ H0, const double* __restrict__ M,
+                             const double* __restrict__ f, int N, int J, int sweeps,
+                             double angle_tol, double* __restrict__ W_io,
+                             double* __restrict__ eig_out, int* status, unsigned int* stats,
+                             unsigned char* gws, size_t per_cta) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  unsigned char* base = gws ? gws + (size_t)blockIdx.x * per_cta : smem_raw;
+  for (int j = blockIdx.x; j < J; j += gridDim.x) {
+    eig_refine_step(H0, M, f, N, j, sweeps, angle_tol, W_io, eig_out, status, stats, base);
+    __syncthreads();
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -611,38 +647,46 @@ static size_t refine_smem(int N) {
   return (5 * (size_t)N * (N + 1) + N + 1 + 64 + NP) * sizeof(double) + (NP + 2) * sizeof(int);
 }
 
-size_t eig_smem_bytes(int N, int method) {
-  size_t a = method == EIG_JACOBI_FP64 ? jacobi_smem(N, 8)
-                                       : (size_t)jacobi32_mpb(N) * jacobi32_slot_floats(N) * sizeof(float);
-  size_t b = method == EIG_JACOBI_FP64 ? 0 : refine_smem(N);
-  return a > b ? a : b;
-}
-
 cudaError_t launch_eig(const double* H0, const double* M, const double* f, int N, int J,
                        double* W, double* eig, int* status, int method, int refine_sweeps,
-                       double angle_tol, cudaStream_t st, cudaEvent_t mid, unsigned int* stats) {
+                       double angle_tol, cudaStream_t st, const StepSpace& ws, cudaEvent_t mid,
+                       unsigned int* stats) {
   // Jacobi rounds are barrier-bound: few warps per (small) matrix, many CTAs per SM
-  const int jthreads = N <= 32 ? 64 : (N <= 64 ? 128 : 256);
-  const int threads = N <= 16 ? 128 : 256;   // refinement: binary64-throughput bound
+  const int jthreads = N <= 32 ? 64 : (N <= 64 ? 128 : (N <= 128 ? 256 : 512));
+  const int threads = N <= 16 ? 128 : (N <= 128 ? 256 : 512);   // refinement: binary64-bound
+  StepGrid g;
   if (method == EIG_JACOBI_FP64) {
-    size_t sm = jacobi_smem(N, 8);
-    set_max_smem((const void*)k_eig_jacobi<double>);
-    k_eig_jacobi<double><<<J, jthreads, sm, st>>>(H0, M, f, N, J, W, eig, status);
+    if (!step_grid(jacobi_smem(N, 8), J, ws, (const void*)k_eig_jacobi<double>, g))
+      return cudaErrorInvalidConfiguration;
+    k_eig_jacobi<double><<<g.grid, jthreads, g.smem, st>>>(H0, M, f, N, J, W, eig, status, g.gws,
+                                                           g.per_cta);
     if (mid) cudaEventRecord(mid, st);
     return cudaGetLastError();
   }
-  const int mpb = jacobi32_mpb(N);
-  const size_t sm = (size_t)mpb * jacobi32_slot_floats(N) * sizeof(float);
-  set_max_smem((const void*)k_eig_jacobi32);
-  k_eig_jacobi32<<<(J + mpb - 1) / mpb, 32 * mpb, sm, st>>>(H0, M, f, N, J, mpb, W, eig, status);
+  if (N <= 64) {
+    const int mpb = jacobi32_mpb(N);
+    const size_t sm = (size_t)mpb * jacobi32_slot_floats(N) * sizeof(float);
+    set_max_smem((const void*)k_eig_jacobi32);
+    k_eig_jacobi32<<<(J + mpb - 1) / mpb, 32 * mpb, sm, st>>>(H0, M, f, N, J, mpb, W, eig, status);
+  } else {
+    if (!step_grid(jacobi_smem(N, 4), J, ws, (const void*)k_eig_jacobi<float>, g))
+      return cudaErrorInvalidConfiguration;
+    k_eig_jacobi<float><<<g.grid, jthreads, g.smem, st>>>(H0, M, f, N, J, W, eig, status, g.gws,
+                                                          g.per_cta);
+  }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   if (mid) cudaEventRecord(mid, st);
-  size_t sr = refine_smem(N);
-  set_max_smem((const void*)k_eig_refine);
-  k_eig_refine<<<J, threads, sr, st>>>(H0, M, f, N, J, refine_sweeps, angle_tol, W, eig, status,
-                                       stats);
+  if (!step_grid(refine_smem(N), J, ws, (const void*)k_eig_refine, g))
+    return cudaErrorInvalidConfiguration;
+  k_eig_refine<<<g.grid, threads, g.smem, st>>>(H0, M, f, N, J, refine_sweeps, angle_tol, W, eig,
+                                                status, stats, g.gws, g.per_cta);
   return cudaGetLastError();
+}
+
+size_t eig_step_bytes(int N) {
+  const size_t a = jacobi_smem(N, 8), b = jacobi_smem(N, 4), c = refine_smem(N);
+  return a > b ? (a > c ? a : c) : (b > c ? b : c);
 }
 
 }  // namespace qoc

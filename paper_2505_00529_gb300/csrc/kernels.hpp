@@ -5,31 +5,78 @@
 #include <stddef.h>
 
 #include <mutex>
+#include <map>
 #include <set>
 #include <utility>
 
 namespace qoc {
 
-// Raise a kernel's dynamic shared-memory limit to the device maximum, once per
-// (kernel, device).  Setting it per launch to the launch's own size would let
-// a concurrent host thread lower it between another thread's set and launch.
-inline cudaError_t set_max_smem(const void* fn) {
+// Largest dynamic shared memory of a kernel on the current device (the opt-in
+// limit minus its static shared memory), raised to that as the kernel's
+// attribute once per (kernel, device).  Setting it per launch to the launch's
+// own size would let a concurrent host thread lower it between another
+// thread's set and launch.
+inline size_t max_dyn_smem(const void* fn) {
   static std::mutex mu;
-  static std::set<std::pair<const void*, int>> done;
+  static std::map<std::pair<const void*, int>, size_t> done;
   int dev = 0;
   cudaGetDevice(&dev);
   std::lock_guard<std::mutex> lock(mu);
-  if (!done.insert({fn, dev}).second) return cudaSuccess;
+  auto it = done.find({fn, dev});
+  if (it != done.end()) return it->second;
   int mx = 0;
-  cudaError_t e = cudaDeviceGetAttribute(&mx, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-  if (e != cudaSuccess) return e;
+  if (cudaDeviceGetAttribute(&mx, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) return 0;
   cudaFuncAttributes fa;
-  e = cudaFuncGetAttributes(&fa, fn);
-  if (e != cudaSuccess) return e;
-  // the dynamic limit excludes the kernel's static shared memory
-  return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              mx - (int)fa.sharedSizeBytes);
+  if (cudaFuncGetAttributes(&fa, fn) != cudaSuccess) return 0;
+  const int lim = mx - (int)fa.sharedSizeBytes;
+  if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, lim) != cudaSuccess) return 0;
+  done[{fn, dev}] = (size_t)lim;
+  return (size_t)lim;
 }
+inline cudaError_t set_max_smem(const void* fn) {
+  return max_dyn_smem(fn) ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+// Working storage of a per-step kernel whose matrices do not fit in shared
+// memory (large N): a global workspace.  The launch then uses a persistent
+// grid in which every CTA owns one slice and loops over the steps.
+struct StepSpace {
+  unsigned char* base = nullptr;
+  size_t bytes = 0;
+};
+struct StepGrid {
+  int grid = 0;
+  size_t smem = 0;
+  unsigned char* gws = nullptr;
+  size_t per_cta = 0;
+};
+// `units` work units (steps or blocks), `need` bytes of storage each.
+inline bool step_grid(size_t need, int units, const StepSpace& ws, const void* fn, StepGrid& g) {
+  if (need <= max_dyn_smem(fn)) {
+    g.grid = units; g.smem = need; g.gws = nullptr; g.per_cta = 0;
+    return true;
+  }
+  if (!ws.base) return false;
+  const size_t per = (need + 255) & ~size_t(255);
+  size_t n = ws.bytes / per;
+  if (n < 1) return false;
+  // no more CTAs than keep the slices L2-resident (96 MB), but at least one per SM
+  static int nsm = 0;
+  if (!nsm) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || nsm < 1)
+      nsm = 1;
+  }
+  size_t cap = (size_t)(96u << 20) / per;
+  if (cap < (size_t)nsm) cap = (size_t)nsm;
+  if (n > cap) n = cap;
+  if (n > (size_t)units) n = (size_t)units;
+  g.grid = (int)n; g.smem = 0; g.gws = ws.base; g.per_cta = per;
+  return true;
+}
+// bytes per CTA that the per-step kernels ask of a workspace for this N (0 if all fit)
+size_t step_workspace_per_cta(int N, int K, int bs_max, int mixed);
 
 // Device status bits, OR-ed into a word the host reads after each evaluation.
 enum : int {
@@ -46,15 +93,15 @@ enum { PREC_FP64 = 0, PREC_MIXED = 1 };
 // second divided difference: dt*|hi - lo| at or below which the series is used
 constexpr double TAU_DD2 = 1e-3;
 
-size_t eig_smem_bytes(int N, int method);
 // stats (optional, device): [0] += refinement updates, [1] += steps whose clean-up rotated,
 // [2] += steps that took the final residual pass (no early finish)
 // method EIG_REFINED: binary32 Jacobi, `refine_sweeps` binary64 Ogita-Aishima
 // sweeps, then binary64 Jacobi clean-up rotating only angles above angle_tol.
 cudaError_t launch_eig(const double* H0, const double* M, const double* f, int N, int J,
                        double* W, double* eig, int* status, int method, int refine_sweeps,
-                       double angle_tol, cudaStream_t st, cudaEvent_t mid = nullptr,
-                       unsigned int* stats = nullptr);
+                       double angle_tol, cudaStream_t st, const StepSpace& ws,
+                       cudaEvent_t mid = nullptr, unsigned int* stats = nullptr);
+size_t eig_step_bytes(int N);   // largest per-matrix storage of the eigensolver kernels
 
 size_t prep_smem_bytes(int N);
 // parts (bit mask): 1 -> D_j = W diag(exp(-i dt (lambda - m)) - 1) W^T
@@ -66,7 +113,7 @@ enum { PREP_D = 1, PREP_P = 2, PREP_X = 4 };
 cudaError_t launch_prep(const double* W, const double* eig, const double* M, int N, int J,
                         double dt, double mshift, void* D, size_t dstride, int d_fp64,
                         int parts, double2* Ptil, double2* Xp, double* Mtil, int* status,
-                        cudaStream_t st);
+                        cudaStream_t st, const StepSpace& ws);
 
 struct SweepArgs {
   int N, K, Kp, J;       // Kp: row stride of the basis copy (multiple of 4)
@@ -113,13 +160,16 @@ cudaError_t launch_bsweep_batch(const BSweepArgs* host_args, const BSweepArgs* d
                                 const int* dev_cta_off, int nprob, int total_ctas, int mixed,
                                 cudaStream_t st);
 cudaError_t launch_block_delta(const void* D, size_t dstride, int N, int J, int bsteps, int bwd,
-                               int mixed, void* M, size_t mstride, cudaStream_t st);
+                               int mixed, void* M, size_t mstride, cudaStream_t st,
+                               const StepSpace& ws);
+size_t block_delta_bytes(int N, int mixed);
+size_t block_src_bytes(int N, int bsteps, int mixed);
 // what: BS_Q (propagated sources Q, from src only), BS_WG (W and Gamma, needs ctr)
 enum { BS_Q = 1, BS_WG = 2 };
 cudaError_t launch_block_src(const void* D, size_t dstride, int N, int J, int bsteps, int bwd,
                              int mixed, const void* src, const void* ctr, size_t vstride, void* Q,
                              void* W, void* G, size_t qstride, size_t gstride, int what,
-                             cudaStream_t st);
+                             cudaStream_t st, const StepSpace& ws);
 cudaError_t launch_block_contract(const void* Xblk, const void* W, const void* G, size_t qstride,
                                   size_t gstride, const void* Brow, int Kp, int N, int K, int J,
                                   int bsteps, int bwd, int mixed, void* contr, cudaStream_t st);
@@ -134,7 +184,8 @@ enum { PW_P = 1, PW_Y = 2, PW_C = 4 };
 cudaError_t launch_pointwise(const double* W, const double2* Ptil, const double2* Xp,
                              const void* a_hat, const void* l_hat, int mixed, int N, int J,
                              double2 kappa, void* p_hat, void* y_hat, double* g, double* c,
-                             int what, cudaStream_t st);
+                             int what, cudaStream_t st, const StepSpace& ws);
+size_t pointwise_step_bytes(int N);
 // max_j | |a_j| - 1 | over the stored states j = 0..J into *drift (zeroed here)
 cudaError_t launch_drift(const void* a_hat, int mixed, int N, int J, double* drift, cudaStream_t st);
 

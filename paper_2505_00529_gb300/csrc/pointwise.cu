@@ -26,14 +26,14 @@ __device__ __forceinline__ double2 load_state(const void* base, int mixed, size_
   return reinterpret_cast<const double2*>(base)[idx];
 }
 
-__global__ void k_pointwise(const double* __restrict__ Wg, const double2* __restrict__ Ptil,
-                            const double2* __restrict__ Xp, const void* a_hat, const void* l_hat,
-                            int mixed, int N, int J, double2 kappa, void* p_hat, void* y_hat,
-                            size_t vstride, double* __restrict__ g, double* __restrict__ c,
-                            int what) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int j = blockIdx.x;
-  if (j >= J) return;
+__device__ __forceinline__ void pointwise_step(const double* __restrict__ Wg,
+                                               const double2* __restrict__ Ptil,
+                                               const double2* __restrict__ Xp, const void* a_hat,
+                                               const void* l_hat, int mixed, int N, int j,
+                                               double2 kappa, void* p_hat, void* y_hat,
+                                               size_t vstride, double* __restrict__ g,
+                                               double* __restrict__ c, int what,
+                                               unsigned char* smem_raw) {
   const bool wp = what & PW_P, wy = what & PW_Y, wc = what & PW_C;
   const bool need_l = wy || wc;
   const int ld = N + 1;
@@ -119,6 +119,20 @@ __global__ void k_pointwise(const double* __restrict__ Wg, const double2* __rest
   }
 }
 
+__global__ void k_pointwise(const double* __restrict__ Wg, const double2* __restrict__ Ptil,
+                            const double2* __restrict__ Xp, const void* a_hat, const void* l_hat,
+                            int mixed, int N, int J, double2 kappa, void* p_hat, void* y_hat,
+                            size_t vstride, double* __restrict__ g, double* __restrict__ c,
+                            int what, unsigned char* gws, size_t per_cta) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  unsigned char* base = gws ? gws + (size_t)blockIdx.x * per_cta : smem_raw;
+  for (int j = blockIdx.x; j < J; j += gridDim.x) {
+    pointwise_step(Wg, Ptil, Xp, a_hat, l_hat, mixed, N, j, kappa, p_hat, y_hat, vstride, g, c,
+                   what, base);
+    __syncthreads();
+  }
+}
+
 // max_j | |a_j| - 1 |, j = 0..J, as a non-negative binary64 reduced with an
 // integer atomicMax on its bit pattern (monotone for non-negative values);
 // *drift must hold +0.0 before the launch.
@@ -147,16 +161,19 @@ cudaError_t launch_drift(const void* a_hat, int mixed, int N, int J, double* dri
   return cudaGetLastError();
 }
 
+size_t pointwise_step_bytes(int N) { return (size_t)N * (N + 1) * 8 + 4 * (size_t)N * 16 + 64 * 8; }
+
 cudaError_t launch_pointwise(const double* W, const double2* Ptil, const double2* Xp,
                              const void* a_hat, const void* l_hat, int mixed, int N, int J,
                              double2 kappa, void* p_hat, void* y_hat, double* g, double* c,
-                             int what, cudaStream_t st) {
+                             int what, cudaStream_t st, const StepSpace& ws) {
   const int threads = N <= 32 ? 32 : (N <= 64 ? 64 : (N <= 128 ? 128 : 256));
-  const size_t smem = (size_t)N * (N + 1) * 8 + 4 * (size_t)N * 16 + 64 * 8;
   const size_t vstride = ((mixed ? 8 : 16) * (size_t)N + 15) / 16 * 16;
-  set_max_smem((const void*)k_pointwise);
-  k_pointwise<<<J, threads, smem, st>>>(W, Ptil, Xp, a_hat, l_hat, mixed, N, J, kappa, p_hat,
-                                        y_hat, vstride, g, c, what);
+  StepGrid sg;
+  if (!step_grid(pointwise_step_bytes(N), J, ws, (const void*)k_pointwise, sg))
+    return cudaErrorInvalidConfiguration;
+  k_pointwise<<<sg.grid, threads, sg.smem, st>>>(W, Ptil, Xp, a_hat, l_hat, mixed, N, J, kappa, p_hat,
+                                                 y_hat, vstride, g, c, what, sg.gws, sg.per_cta);
   return cudaGetLastError();
 }
 

@@ -115,14 +115,13 @@ __device__ __forceinline__ double2 dd2_table(int a, int b, int c, const double* 
   return dd2_dev(a, b, c, lam, eh, dt);
 }
 
-__global__ void k_prep(const double* __restrict__ Wg, const double* __restrict__ eig,
-                       const double* __restrict__ Mg, int N, int J, double dt, double mshift,
-                       void* __restrict__ Dout, size_t dstride, int d_fp64, int derivs,
-                       double2* __restrict__ Ptil, double2* __restrict__ Xp,
-                       double* __restrict__ Mtil, int* status) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int j = blockIdx.x;
-  if (j >= J) return;
+__device__ __forceinline__ void prep_step(const double* __restrict__ Wg,
+                                          const double* __restrict__ eig,
+                                          const double* __restrict__ Mg, int N, int j, double dt,
+                                          double mshift, void* __restrict__ Dout, size_t dstride,
+                                          int d_fp64, int derivs, double2* __restrict__ Ptil,
+                                          double2* __restrict__ Xp, double* __restrict__ Mtil,
+                                          int* status, unsigned char* smem_raw) {
   const int ld = N + 1;
   const int NT = N * (N + 1) / 2;
   double* W = reinterpret_cast<double*>(smem_raw);      // [N][ld]
@@ -293,6 +292,23 @@ __global__ void k_prep(const double* __restrict__ Wg, const double* __restrict__
   if (bad) raise_status(status, DEV_NONFINITE);
 }
 
+// One step per CTA in shared memory, or (gws != nullptr, large N) a persistent
+// grid whose CTAs each own a slice of a global workspace.
+__global__ void k_prep(const double* __restrict__ Wg, const double* __restrict__ eig,
+                       const double* __restrict__ Mg, int N, int J, double dt, double mshift,
+                       void* __restrict__ Dout, size_t dstride, int d_fp64, int derivs,
+                       double2* __restrict__ Ptil, double2* __restrict__ Xp,
+                       double* __restrict__ Mtil, int* status, unsigned char* gws,
+                       size_t per_cta) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  unsigned char* base = gws ? gws + (size_t)blockIdx.x * per_cta : smem_raw;
+  for (int j = blockIdx.x; j < J; j += gridDim.x) {
+    prep_step(Wg, eig, Mg, N, j, dt, mshift, Dout, dstride, d_fp64, derivs, Ptil, Xp, Mtil, status,
+              base);
+    __syncthreads();
+  }
+}
+
 size_t prep_smem_bytes(int N) {
   const size_t NT = (size_t)N * (N + 1) / 2;
   return (5 * (size_t)N * (N + 1) + (N + (N & 1)) + 4 * (size_t)N) * sizeof(double) +
@@ -302,12 +318,12 @@ size_t prep_smem_bytes(int N) {
 cudaError_t launch_prep(const double* W, const double* eig, const double* M, int N, int J,
                         double dt, double mshift, void* D, size_t dstride, int d_fp64,
                         int parts, double2* Ptil, double2* Xp, double* Mtil, int* status,
-                        cudaStream_t st) {
-  size_t sm = prep_smem_bytes(N);
-  set_max_smem((const void*)k_prep);
-  int threads = N <= 8 ? 64 : (N <= 16 ? 128 : 256);
-  k_prep<<<J, threads, sm, st>>>(W, eig, M, N, J, dt, mshift, D, dstride, d_fp64, parts, Ptil,
-                                 Xp, Mtil, status);
+                        cudaStream_t st, const StepSpace& ws) {
+  StepGrid g;
+  if (!step_grid(prep_smem_bytes(N), J, ws, (const void*)k_prep, g)) return cudaErrorInvalidConfiguration;
+  int threads = N <= 8 ? 64 : (N <= 16 ? 128 : (N <= 128 ? 256 : 512));
+  k_prep<<<g.grid, threads, g.smem, st>>>(W, eig, M, N, J, dt, mshift, D, dstride, d_fp64, parts,
+                                          Ptil, Xp, Mtil, status, g.gws, g.per_cta);
   return cudaGetLastError();
 }
 

@@ -107,7 +107,9 @@ __global__ void __launch_bounds__(1024) k_sweep(const SweepArgs a, const int nst
     X[(0 * kc + l) * N + i] = v;
   }
   __syncthreads();
-  if (threadIdx.x == 0) {
+  // nstage == 0: direct mode (large N): the step data is read from global memory
+  const bool ring_mode = nstage > 0;
+  if (threadIdx.x == 0 && ring_mode) {
     const int pre = min(nstage - 1, J);
     for (int it = 0; it < pre; ++it) issue(it);
   }
@@ -120,7 +122,7 @@ __global__ void __launch_bounds__(1024) k_sweep(const SweepArgs a, const int nst
   const TD* dcol0 = nullptr;
   for (; it < J; ++it) {
     const int jj = BWD ? J - 1 - it : it;
-    if (threadIdx.x == 0 && it + nstage - 1 < J) {
+    if (threadIdx.x == 0 && ring_mode && it + nstage - 1 < J) {
       fence_proxy_async_smem();
       issue(it + nstage - 1);
     }
@@ -132,12 +134,23 @@ __global__ void __launch_bounds__(1024) k_sweep(const SweepArgs a, const int nst
     }
     // a thread whose wait gives up flags the CTA; the data it then reads is
     // never used (the loop ends at the step-end barrier)
-    if (!mbar_wait_bounded(&bar[s], par)) abort_flag = 1;
-    const unsigned char* sp = ring + (size_t)s * stage;
-    const TD* Ds = reinterpret_cast<const TD*>(sp);
-    const TV* srcs = reinterpret_cast<const TV*>(sp + dbytes);
-    const TV* ctrs = reinterpret_cast<const TV*>(sp + dbytes + sbytes);
-    const TB* brow = reinterpret_cast<const TB*>(sp + dbytes + sbytes + cbytes);
+    const TD* Ds;
+    const TV* srcs;
+    const TV* ctrs;
+    const TB* brow;
+    if (ring_mode) {
+      if (!mbar_wait_bounded(&bar[s], par)) abort_flag = 1;
+      const unsigned char* sp = ring + (size_t)s * stage;
+      Ds = reinterpret_cast<const TD*>(sp);
+      srcs = reinterpret_cast<const TV*>(sp + dbytes);
+      ctrs = reinterpret_cast<const TV*>(sp + dbytes + sbytes);
+      brow = reinterpret_cast<const TB*>(sp + dbytes + sbytes + cbytes);
+    } else {
+      Ds = reinterpret_cast<const TD*>(a.D + (size_t)jj * a.dstride);
+      srcs = reinterpret_cast<const TV*>(gsrc + (size_t)jj * sbytes);
+      ctrs = reinterpret_cast<const TV*>(gctr + (size_t)jj * cbytes);
+      brow = reinterpret_cast<const TB*>(gb + (size_t)jj * bbytes);
+    }
     const TD* Xc = X + (size_t)cur * kc * N + (size_t)l * N;
 
     // contraction on the entering state: Re(c^H x), summed over rows
@@ -256,6 +269,7 @@ static cudaError_t launch_one(const SweepArgs& a, cudaStream_t st) {
   const size_t budget = 200 * 1024;
   int ns = 8;
   while (ns > 2 && (size_t)ns * stage + fixed + 8 * ns > budget) --ns;
+  if (2 * (size_t)stage + fixed + 16 > budget) ns = 0;   // direct mode (large N)
   const size_t smem = (size_t)ns * stage + fixed + 8 * ns + 16;
   if (smem > 227 * 1024) return cudaErrorInvalidConfiguration;
   set_max_smem((const void*)k_sweep<MIX, RS, BWD>);
@@ -330,6 +344,9 @@ __device__ __forceinline__ void bsweep_body(const BSweepArgs& a, const int cta, 
     if (bb) bulk_g2s(dst + mbytes + qbytes, gB + (size_t)row0 * browb, bb, &bar[s]);
   };
 
+  // nstage == 0: direct mode (large N, a block does not fit the ring twice):
+  // the block data is read straight from global memory (L2), no copies
+  const bool ring_mode = nstage > 0;
   if (threadIdx.x == 0) {
     abort_flag = 0;
     for (int s = 0; s < nstage; ++s) mbar_init(&bar[s], 1);
@@ -353,7 +370,7 @@ __device__ __forceinline__ void bsweep_body(const BSweepArgs& a, const int cta, 
     X[(size_t)l * N + i] = v;
   }
   __syncthreads();
-  if (threadIdx.x == 0) {
+  if (threadIdx.x == 0 && ring_mode) {
     const int pre = min(nstage - 1, nblk);
     for (int it = 0; it < pre; ++it) issue(it);
   }
@@ -361,7 +378,7 @@ __device__ __forceinline__ void bsweep_body(const BSweepArgs& a, const int cta, 
   uint32_t par = 0;
   for (; it < nblk; ++it) {
     const int t0 = it * bs, bl = min(bs, J - t0);
-    if (threadIdx.x == 0 && it + nstage - 1 < nblk) {
+    if (threadIdx.x == 0 && ring_mode && it + nstage - 1 < nblk) {
       fence_proxy_async_smem();
       issue(it + nstage - 1);
     }
@@ -375,11 +392,21 @@ __device__ __forceinline__ void bsweep_body(const BSweepArgs& a, const int cta, 
         reinterpret_cast<TD*>(a.Xblk)[((size_t)it * a.K + col0 + l) * N + i] = v;
       }
     }
-    if (!mbar_wait_bounded(&bar[s], par)) abort_flag = 1;
-    const unsigned char* sp = ring + (size_t)s * stage;
-    const TD* Ms = reinterpret_cast<const TD*>(sp);
-    const TD* Qs = reinterpret_cast<const TD*>(sp + mbytes);
-    const TB* Bs = reinterpret_cast<const TB*>(sp + mbytes + qbytes);
+    const TD* Ms;
+    const TD* Qs;
+    const TB* Bs;
+    if (ring_mode) {
+      if (!mbar_wait_bounded(&bar[s], par)) abort_flag = 1;
+      const unsigned char* sp = ring + (size_t)s * stage;
+      Ms = reinterpret_cast<const TD*>(sp);
+      Qs = reinterpret_cast<const TD*>(sp + mbytes);
+      Bs = reinterpret_cast<const TB*>(sp + mbytes + qbytes);
+    } else {
+      const int row0 = a.backward ? J - t0 - bl : t0;
+      Ms = reinterpret_cast<const TD*>(a.M + (size_t)it * a.mstride);
+      Qs = a.Q ? reinterpret_cast<const TD*>(a.Q + (size_t)it * a.qstride) : nullptr;
+      Bs = a.Brow ? reinterpret_cast<const TB*>(gB + (size_t)row0 * browb) : nullptr;
+    }
     const TD* Xc = X + (size_t)cur * kc * N + (size_t)l * N;
     R ax0 = 0, ay0 = 0, ax1 = 0, ay1 = 0;
     if (active) {
@@ -499,6 +526,7 @@ static void bsweep_geometry(const BSweepArgs& a, int& threads, size_t& stage, si
 // fits one CTA per SM (bulk-copy latency is what the chain waits on), else
 // shallow enough that ceil(grid / SMs) CTAs share an SM's shared memory.
 static int ring_stages(size_t stage, size_t fixed, int threads, int total_ctas) {
+  if (2 * stage + fixed + 16 + 16 > 200 * 1024) return 0;   // direct mode (large N)
   static int nsm = 0;
   if (!nsm) {
     int dev = 0;
