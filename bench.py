@@ -382,11 +382,12 @@ def run_warm_start(args):
 
 
 def run_batch(args):
-    """Batching pattern: uneven problems drawn from the batched-workload
-    recipe (N from {8,...,128} step 8, K from {16,32,64,128}, J from
-    {2000,4000,8000}, per-problem seeds), keeping the draws with N <= the
-    library's maximum basis size; one batched evaluation (graph replay) vs
-    the same problems evaluated one after another on one stream."""
+    """Batching pattern: the batched-workload recipe (N from {8,...,128} step
+    8, K from {16,32,64,128}, J from {2000,4000,8000}, per-problem seeds).
+    Problems are created chunk by chunk within a device-memory budget; each
+    chunk is one batch (per-problem phase streams, one launch per sequential
+    sweep over the chunk, CUDA graph replay), timed with CUDA events; the
+    same problems evaluated one after another give the comparison."""
     import numpy as np
     import torch
     import paper_2505_00529_gb300 as q
@@ -406,19 +407,14 @@ def run_batch(args):
     stream = torch.cuda.Stream(device=dev)
     torch.cuda.set_stream(stream)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
-    Ps = [q.Problem(pr, precision=prec) for pr in probs]
     thetas = [inputs.eval_theta(pr.K, 7 + k) for k, pr in enumerate(probs)]
-    tune_s = None
+    cfgs, tune_s = None, None
     if not args.no_autotune:
         from paper_2505_00529_gb300 import autotune
         t0 = time.perf_counter()
         cfgs = autotune.tune_batch(probs, prec, evals=2)
         tune_s = time.perf_counter() - t0
-        for P, cfg in zip(Ps, cfgs):
-            autotune.apply(P, cfg)
-    b = q.Batch(Ps, cuda_stream=stream.cuda_stream)
-    th = torch.tensor(np.concatenate(thetas), dtype=torch.float64, device=dev)
-    out = torch.zeros(b.n_out, dtype=torch.float64, device=dev)
+    budget = args.batch_mem_gb * (1 << 30)
 
     def timed(fn, steps, warmup):
         for _ in range(warmup):
@@ -435,24 +431,6 @@ def run_batch(args):
         torch.cuda.synchronize()
         return statistics.mean(a.elapsed_time(c) for a, c in ts)
 
-    def batched():
-        q.qoc_batch_eval_grad_hess_dev(b.handle, th.data_ptr(), out.data_ptr())
-
-    # sequential: each problem on its own library stream, serialised by the host
-    th_i = [torch.tensor(t, dtype=torch.float64, device=dev) for t in thetas]
-    out_i = [torch.zeros(1 + pr.K + pr.K ** 2, dtype=torch.float64, device=dev) for pr in probs]
-
-    def sequential():        # one problem after another
-        for P, t, o in zip(Ps, th_i, out_i):
-            q.qoc_eval_grad_hess_dev(P.handle, t.data_ptr(), o.data_ptr())
-            q.qoc_sync_status(P.handle)
-
-    def streams():           # every problem enqueued on its own stream, no batched sweeps
-        for P, t, o in zip(Ps, th_i, out_i):
-            q.qoc_eval_grad_hess_dev(P.handle, t.data_ptr(), o.data_ptr())
-        for P in Ps:
-            q.qoc_sync_status(P.handle)
-
     def wall(fn, steps):
         fn()
         torch.cuda.synchronize()
@@ -466,36 +444,64 @@ def run_batch(args):
             ts.append(1000.0 * (time.perf_counter() - t0))
         return statistics.mean(ts)
 
-    clk = ClockSampler(local, os.path.join(ROOT, "gpurun_out" if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else ".", "clocks_batch.csv"))
-    with clk:
-        ms_b = timed(batched, args.steps, args.warmup)
-    for P in Ps:
-        q.qoc_sync_status(P.handle)
-    ms_s = wall(sequential, max(1, args.steps // 4))
-    ms_c = wall(streams, max(1, args.steps // 4))
-    # the batched results equal each problem's own evaluation
-    res = b.split(out.cpu().numpy())
-    worst = 0.0
-    for k in range(0, len(Ps), max(1, len(Ps) // 8)):
-        Jk, gk, Hk = Ps[k].eval_grad_hess(thetas[k])
-        worst = max(worst, float(np.linalg.norm(res[k][2] - Hk) / np.linalg.norm(Hk)))
-    b.close()
+    total_b = total_s = 0.0
+    chunks, worst, peak_bytes, k0 = [], 0.0, 0, 0
+    while k0 < len(probs):
+        Ps, used = [], 0
+        while k0 + len(Ps) < len(probs):
+            P = q.Problem(probs[k0 + len(Ps)], precision=prec)
+            nb = q.qoc_device_bytes(P.handle)
+            if Ps and used + nb > budget:
+                P.close()
+                break
+            if cfgs is not None:
+                from paper_2505_00529_gb300 import autotune
+                autotune.apply(P, cfgs[k0 + len(Ps)])
+            Ps.append(P)
+            used += nb
+        idx = list(range(k0, k0 + len(Ps)))
+        b = q.Batch(Ps, cuda_stream=stream.cuda_stream)
+        th = torch.tensor(np.concatenate([thetas[k] for k in idx]), dtype=torch.float64, device=dev)
+        out = torch.zeros(b.n_out, dtype=torch.float64, device=dev)
+        ms_b = timed(lambda: q.qoc_batch_eval_grad_hess_dev(b.handle, th.data_ptr(), out.data_ptr()),
+                     args.steps, args.warmup)
+        for P in Ps:
+            q.qoc_sync_status(P.handle)
+        th_i = [torch.tensor(thetas[k], dtype=torch.float64, device=dev) for k in idx]
+        out_i = [torch.zeros(1 + probs[k].K ** 2 + probs[k].K, dtype=torch.float64, device=dev) for k in idx]
+
+        def sequential():
+            for P, t, o in zip(Ps, th_i, out_i):
+                q.qoc_eval_grad_hess_dev(P.handle, t.data_ptr(), o.data_ptr())
+                q.qoc_sync_status(P.handle)
+        ms_s = wall(sequential, 1)
+        res = b.split(out.cpu().numpy())
+        for j in range(0, len(Ps), max(1, len(Ps) // 4)):   # batched results = per-problem ones
+            Jk, gk, Hk = Ps[j].eval_grad_hess(thetas[idx[j]])
+            worst = max(worst, float(np.linalg.norm(res[j][2] - Hk) / np.linalg.norm(Hk)))
+        chunks.append({"problems": len(Ps), "device_gb": round(used / 2 ** 30, 1), "batched_ms": ms_b,
+                       "sequential_ms": ms_s})
+        total_b += ms_b
+        total_s += ms_s
+        peak_bytes = max(peak_bytes, used)
+        b.close()
+        for P in Ps:
+            P.close()
+        del out, th
+        k0 += len(Ps)
     shapes = [(pr.N, pr.K, pr.J) for pr in probs]
-    line = {"metric": "batched grad+Hessian evaluations/s over uneven problems", "value": len(Ps) * 1000.0 / ms_b,
-            "unit": "problem evals/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": ms_b, "higher_is_better": True,
+    line = {"metric": "batched grad+Hessian evaluations/s over uneven problems",
+            "value": len(probs) * 1000.0 / total_b, "unit": "problem evals/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_b, "higher_is_better": True,
             "dtype": "f32 panels + f64" if prec == q.QOC_MIXED_FP32 else "f64", "data": "synthetic",
-            "config": {"workload": f"{len(Ps)} uneven problems from the batched-workload recipe with N <= {nmax}",
+            "config": {"workload": f"{len(probs)} uneven problems from the batched-workload recipe",
                        "N_range": [min(x[0] for x in shapes), max(x[0] for x in shapes)],
                        "K_values": sorted({x[1] for x in shapes}), "J_values": sorted({x[2] for x in shapes}),
                        "total_steps": sum(x[2] for x in shapes), "l2": "flushed between timed steps",
-                       "graph": True, "autotuned": tune_s is not None, "autotune_seconds": tune_s},
-            "sequential_ms": ms_s, "speedup_over_sequential": ms_s / ms_b,
-            "separate_streams_ms": ms_c, "speedup_over_separate_streams": ms_c / ms_b,
-            "batched_vs_individual_hess_rel_max": worst, "clocks": clk.summary(),
-            "device_bytes": sum(q.qoc_device_bytes(P.handle) for P in Ps)}
-    for P in Ps:
-        P.close()
+                       "graph": True, "autotuned": tune_s is not None, "autotune_seconds": tune_s,
+                       "memory_budget_gb": args.batch_mem_gb},
+            "chunks": chunks, "sequential_ms": total_s, "speedup_over_sequential": total_s / total_b,
+            "batched_vs_individual_hess_rel_max": worst, "peak_chunk_device_gb": round(peak_bytes / 2 ** 30, 1)}
     print(json.dumps(line), flush=True)
     return 0
 
@@ -515,6 +521,8 @@ def main():
     ap.add_argument("--warm-start", action="store_true", help="run the learned warm-start experiment")
     ap.add_argument("--batch", action="store_true", help="run the batched uneven-problem measurement")
     ap.add_argument("--batch-size", type=int, default=256)
+    ap.add_argument("--batch-mem-gb", type=float, default=160.0,
+                    help="device memory per batch chunk (problems are created chunk by chunk)")
     ap.add_argument("--ws-train", type=int, default=2000)
     ap.add_argument("--ws-test", type=int, default=200)
     ap.add_argument("--ws-epochs", type=int, default=300)
