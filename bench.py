@@ -173,11 +173,14 @@ class ClockSampler:
 # --------------------------------------------------------------------------
 def refine_flops(N, J, updates_per_step, rotated_fraction, final_fraction):
     """Binary64 flops of one k_eig_refine launch: per step, u Ogita-Aishima
-    updates (H W: N^3 FMA, the W^T H W and W^T W triangles: N^3 FMA, W E: N^3
-    FMA), the final residual pass (2 N^3 FMA) on the steps that take it
-    (fraction p; the others finish early), and W V (N^3 FMA) when the clean-up
-    rotated (fraction r); 2 flops per FMA."""
-    fma = (3.0 * updates_per_step + 2.0 * final_fraction + rotated_fraction) * N ** 3
+    updates with two binary64 N^3 products each (H W, and the W^T H W and W^T W
+    triangles); the third product, W E, is binary64 only in an update that
+    ends the refinement early (the others form it in binary32, not counted);
+    the final residual pass (2 N^3 FMA) on the steps that take it (fraction p;
+    the others finish early), and W V (N^3 FMA) when the clean-up rotated
+    (fraction r); 2 flops per FMA."""
+    fma = (2.0 * updates_per_step + (1.0 - final_fraction) + 2.0 * final_fraction
+           + rotated_fraction) * N ** 3
     return 2.0 * fma * J
 
 
@@ -307,7 +310,7 @@ def run_ours(args):
                 "unit": "TFLOP/s", "frac": ach / FP64_PEAK_TFLOPS, "traffic": None,
                 "peak_source": "binary64 FMA rate from unit counts x max SM clock (152 SMs x 2 DFMA/clk "
                                "x 2 x 2.07 GHz); MEASURED_PEAKS.json has no binary64 figure",
-                "algorithmic": f"(3u + 2p + r) N^3 FMA per step, u = {u:.3f} updates/step, "
+                "algorithmic": f"(2u + 1 + p + r) N^3 binary64 FMA per step, u = {u:.3f} updates/step, "
                                f"p = {fin:.3f} final-pass fraction, r = {rot:.3f} clean-up rotated "
                                f"fraction, N={N}, J={J}",
                 "kernel_ms": t_ref,

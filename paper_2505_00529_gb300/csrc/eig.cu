@@ -246,6 +246,9 @@ __device__ __forceinline__ void eig_refine_step(const double* __restrict__ H0,
   double* red = lam + N + 1;         // [64]
   double* cs = red + 64;             // [NP]
   int* pr = reinterpret_cast<int*>(cs + NP);  // [NP + 2]
+  float* Wf = reinterpret_cast<float*>(
+      (reinterpret_cast<uintptr_t>(pr + NP + 2) + 15) & ~uintptr_t(15));   // [N][ld] binary32 W
+  float* Ef = Wf + N * ld;                                                  // [N][ld] binary32 E
   const int tid = threadIdx.x, nt = blockDim.x;
   const double fj = f[j];
   double* Wg = W_io + (size_t)j * N * N;
@@ -359,12 +362,31 @@ __device__ __forceinline__ void eig_refine_step(const double* __restrict__ H0,
       T[i * ld + k] = eik;
     }
     __syncthreads();
-    // W <- W + W E   (R as scratch for W E)
-    for (int e = tid; e < N * N; e += nt) {
-      const int i = e / N, k = e % N;
-      double acc = 0;
-      for (int r = 0; r < N; ++r) acc = fma(W[i * ld + r], T[r * ld + k], acc);
-      R[i * ld + k] = acc;
+    // W <- W + W E (R as scratch for W E).  An update that cannot end the
+    // refinement (some |E_ik| or |R|_F above kDone) forms the product in
+    // binary32: E is then a correction the next update refines, and the
+    // binary32 product is off by about N eps32 |W| |E|, far below the error
+    // that update removes.  A finishing update forms it in binary64.
+    if (not_done) {
+      for (int e = tid; e < N * N; e += nt) {
+        const int i = e / N, k = e % N;
+        Wf[i * ld + k] = (float)W[i * ld + k];
+        Ef[i * ld + k] = (float)T[i * ld + k];
+      }
+      __syncthreads();
+      for (int e = tid; e < N * N; e += nt) {
+        const int i = e / N, k = e % N;
+        float acc = 0.f;
+        for (int r = 0; r < N; ++r) acc = fmaf(Wf[i * ld + r], Ef[r * ld + k], acc);
+        R[i * ld + k] = (double)acc;
+      }
+    } else {
+      for (int e = tid; e < N * N; e += nt) {
+        const int i = e / N, k = e % N;
+        double acc = 0;
+        for (int r = 0; r < N; ++r) acc = fma(W[i * ld + r], T[r * ld + k], acc);
+        R[i * ld + k] = acc;
+      }
     }
     __syncthreads();
     for (int e = tid; e < N * N; e += nt) {
@@ -644,7 +666,8 @@ static size_t jacobi_smem(int N, size_t tsize) {
 }
 static size_t refine_smem(int N) {
   const int NP = N + (N & 1);
-  return (5 * (size_t)N * (N + 1) + N + 1 + 64 + NP) * sizeof(double) + (NP + 2) * sizeof(int);
+  return (5 * (size_t)N * (N + 1) + N + 1 + 64 + NP) * sizeof(double) + (NP + 2) * sizeof(int) + 16 +
+         2 * (size_t)N * (N + 1) * sizeof(float);
 }
 
 cudaError_t launch_eig(const double* H0, const double* M, const double* f, int N, int J,
