@@ -94,12 +94,12 @@ __device__ __forceinline__ void block_delta_step(const unsigned char* __restrict
 }
 
 // one block per CTA in shared memory, or a persistent grid over a global workspace
-template <bool MIX>
+template <bool MIX, bool GWS>   // GWS: storage in the global workspace (compile-time)
 __global__ void k_block_delta(const unsigned char* __restrict__ D, size_t dstride, int N, int J,
                               int bsteps, int bwd, unsigned char* __restrict__ Mo, size_t mstride,
                               int nblk, unsigned char* gws, size_t per_cta) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  unsigned char* base = gws ? gws + (size_t)blockIdx.x * per_cta : smem_raw;
+  unsigned char* base = GWS ? gws + (size_t)blockIdx.x * per_cta : smem_raw;
   for (int blk = blockIdx.x; blk < nblk; blk += gridDim.x) {
     block_delta_step<MIX>(D, dstride, N, J, bsteps, bwd, Mo, mstride, blk, base);
     __syncthreads();
@@ -223,7 +223,7 @@ __device__ __forceinline__ void block_src_step(const unsigned char* __restrict__
   for (int e = tid; e < bsteps * N; e += nt) wo[e] = (e / N) < bl ? Pn[e] : cz<C>();
 }
 
-template <bool MIX>
+template <bool MIX, bool GWS>   // GWS: storage in the global workspace (compile-time)
 __global__ void k_block_src(const unsigned char* __restrict__ D, size_t dstride, int N, int J,
                             int bsteps, int bwd, const unsigned char* __restrict__ src,
                             const unsigned char* __restrict__ ctr, size_t vstride,
@@ -231,7 +231,7 @@ __global__ void k_block_src(const unsigned char* __restrict__ D, size_t dstride,
                             unsigned char* __restrict__ Go, size_t qstride, size_t gstride,
                             int what, int nblk, unsigned char* gws, size_t per_cta) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  unsigned char* base = gws ? gws + (size_t)blockIdx.x * per_cta : smem_raw;
+  unsigned char* base = GWS ? gws + (size_t)blockIdx.x * per_cta : smem_raw;
   for (int blk = blockIdx.x; blk < nblk; blk += gridDim.x) {
     block_src_step<MIX>(D, dstride, N, J, bsteps, bwd, src, ctr, vstride, Qo, Wo, Go, qstride,
                         gstride, what, blk, base);
@@ -368,17 +368,27 @@ cudaError_t launch_block_delta(const void* D, size_t dstride, int N, int J, int 
   const int threads = N <= 16 ? 128 : (N <= 128 ? 256 : 512);
   StepGrid g;
   if (mixed) {
-    if (!step_grid(block_delta_bytes(N, 1), nblk, ws, (const void*)k_block_delta<true>, g))
+    if (!step_grid(block_delta_bytes(N, 1), nblk, ws, (const void*)k_block_delta<true, false>, g))
       return cudaErrorInvalidConfiguration;
-    k_block_delta<true><<<g.grid, threads, g.smem, st>>>((const unsigned char*)D, dstride, N, J, bsteps,
-                                                         bwd, (unsigned char*)M, mstride, nblk, g.gws,
-                                                         g.per_cta);
+    if (g.gws)
+      k_block_delta<true, true><<<g.grid, threads, g.smem, st>>>((const unsigned char*)D, dstride, N, J, bsteps,
+                                                           bwd, (unsigned char*)M, mstride, nblk, g.gws,
+                                                           g.per_cta);
+    else
+      k_block_delta<true, false><<<g.grid, threads, g.smem, st>>>((const unsigned char*)D, dstride, N, J, bsteps,
+                                                           bwd, (unsigned char*)M, mstride, nblk, g.gws,
+                                                           g.per_cta);
   } else {
-    if (!step_grid(block_delta_bytes(N, 0), nblk, ws, (const void*)k_block_delta<false>, g))
+    if (!step_grid(block_delta_bytes(N, 0), nblk, ws, (const void*)k_block_delta<false, false>, g))
       return cudaErrorInvalidConfiguration;
-    k_block_delta<false><<<g.grid, threads, g.smem, st>>>((const unsigned char*)D, dstride, N, J, bsteps,
-                                                          bwd, (unsigned char*)M, mstride, nblk, g.gws,
-                                                          g.per_cta);
+    if (g.gws)
+      k_block_delta<false, true><<<g.grid, threads, g.smem, st>>>((const unsigned char*)D, dstride, N, J, bsteps,
+                                                            bwd, (unsigned char*)M, mstride, nblk, g.gws,
+                                                            g.per_cta);
+    else
+      k_block_delta<false, false><<<g.grid, threads, g.smem, st>>>((const unsigned char*)D, dstride, N, J, bsteps,
+                                                            bwd, (unsigned char*)M, mstride, nblk, g.gws,
+                                                            g.per_cta);
   }
   return cudaGetLastError();
 }
@@ -390,21 +400,35 @@ cudaError_t launch_block_src(const void* D, size_t dstride, int N, int J, int bs
   const int threads = N <= 128 ? 256 : 512;
   StepGrid g;
   if (mixed) {
-    if (!step_grid(block_src_bytes(N, bsteps, 1), nblk, ws, (const void*)k_block_src<true>, g))
+    if (!step_grid(block_src_bytes(N, bsteps, 1), nblk, ws, (const void*)k_block_src<true, false>, g))
       return cudaErrorInvalidConfiguration;
-    k_block_src<true><<<g.grid, threads, g.smem, st>>>((const unsigned char*)D, dstride, N, J, bsteps, bwd,
-                                                       (const unsigned char*)src, (const unsigned char*)ctr,
-                                                       vstride, (unsigned char*)Q, (unsigned char*)W,
-                                                       (unsigned char*)G, qstride, gstride, what, nblk,
-                                                       g.gws, g.per_cta);
+    if (g.gws)
+      k_block_src<true, true><<<g.grid, threads, g.smem, st>>>((const unsigned char*)D, dstride, N, J, bsteps, bwd,
+                                                         (const unsigned char*)src, (const unsigned char*)ctr,
+                                                         vstride, (unsigned char*)Q, (unsigned char*)W,
+                                                         (unsigned char*)G, qstride, gstride, what, nblk,
+                                                         g.gws, g.per_cta);
+    else
+      k_block_src<true, false><<<g.grid, threads, g.smem, st>>>((const unsigned char*)D, dstride, N, J, bsteps, bwd,
+                                                         (const unsigned char*)src, (const unsigned char*)ctr,
+                                                         vstride, (unsigned char*)Q, (unsigned char*)W,
+                                                         (unsigned char*)G, qstride, gstride, what, nblk,
+                                                         g.gws, g.per_cta);
   } else {
-    if (!step_grid(block_src_bytes(N, bsteps, 0), nblk, ws, (const void*)k_block_src<false>, g))
+    if (!step_grid(block_src_bytes(N, bsteps, 0), nblk, ws, (const void*)k_block_src<false, false>, g))
       return cudaErrorInvalidConfiguration;
-    k_block_src<false><<<g.grid, threads, g.smem, st>>>((const unsigned char*)D, dstride, N, J, bsteps, bwd,
-                                                        (const unsigned char*)src, (const unsigned char*)ctr,
-                                                        vstride, (unsigned char*)Q, (unsigned char*)W,
-                                                        (unsigned char*)G, qstride, gstride, what, nblk,
-                                                        g.gws, g.per_cta);
+    if (g.gws)
+      k_block_src<false, true><<<g.grid, threads, g.smem, st>>>((const unsigned char*)D, dstride, N, J, bsteps, bwd,
+                                                          (const unsigned char*)src, (const unsigned char*)ctr,
+                                                          vstride, (unsigned char*)Q, (unsigned char*)W,
+                                                          (unsigned char*)G, qstride, gstride, what, nblk,
+                                                          g.gws, g.per_cta);
+    else
+      k_block_src<false, false><<<g.grid, threads, g.smem, st>>>((const unsigned char*)D, dstride, N, J, bsteps, bwd,
+                                                          (const unsigned char*)src, (const unsigned char*)ctr,
+                                                          vstride, (unsigned char*)Q, (unsigned char*)W,
+                                                          (unsigned char*)G, qstride, gstride, what, nblk,
+                                                          g.gws, g.per_cta);
   }
   return cudaGetLastError();
 }

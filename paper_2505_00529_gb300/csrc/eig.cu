@@ -211,13 +211,14 @@ __device__ __forceinline__ void eig_jacobi_step(const double* __restrict__ H0,
 
 // One matrix per CTA in shared memory, or (gws != nullptr, large N) a
 // persistent grid whose CTAs each own a slice of a global workspace.
-template <typename T>
+// GWS: storage in the global workspace (compile-time, see k_eig_refine)
+template <typename T, bool GWS>
 __global__ void k_eig_jacobi(const double* __restrict__ H0, const double* __restrict__ M,
                              const double* __restrict__ f, int N, int J,
                              double* __restrict__ W_out, double* __restrict__ eig_out,
                              int* status, unsigned char* gws, size_t per_cta) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  unsigned char* base = gws ? gws + (size_t)blockIdx.x * per_cta : smem_raw;
+  unsigned char* base = GWS ? gws + (size_t)blockIdx.x * per_cta : smem_raw;
   for (int j = blockIdx.x; j < J; j += gridDim.x) {
     eig_jacobi_step<T>(H0, M, f, N, j, W_out, eig_out, status, base);
     __syncthreads();
@@ -442,13 +443,19 @@ __device__ __forceinline__ void eig_refine_step(const double* __restrict__ H0,
   sort_write<double>(S, W, N, ld, Wg, eig_out + (size_t)j * N);
 }
 
-__global__ void k_eig_refine(const double* __restrict__ H0, const double* __restrict__ M,
+// MAXT: the launch's thread count bound; 256 keeps at least 4 CTAs of
+// registers per SM (the binary64 pipe wants every resident warp), 512 is the
+// large-N launch.  GWS: storage in the global workspace (a compile-time
+// choice, so that the shared-memory instantiation keeps shared-memory loads).
+template <int MAXT, bool GWS>
+__global__ void __launch_bounds__(MAXT, MAXT <= 256 ? 4 : 1)
+k_eig_refine(const double* __restrict__ H0, const double* __restrict__ M,
                              const double* __restrict__ f, int N, int J, int sweeps,
                              double angle_tol, double* __restrict__ W_io,
                              double* __restrict__ eig_out, int* status, unsigned int* stats,
                              unsigned char* gws, size_t per_cta) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  unsigned char* base = gws ? gws + (size_t)blockIdx.x * per_cta : smem_raw;
+  unsigned char* base = GWS ? gws + (size_t)blockIdx.x * per_cta : smem_raw;
   for (int j = blockIdx.x; j < J; j += gridDim.x) {
     eig_refine_step(H0, M, f, N, j, sweeps, angle_tol, W_io, eig_out, status, stats, base);
     __syncthreads();
@@ -679,10 +686,14 @@ cudaError_t launch_eig(const double* H0, const double* M, const double* f, int N
   const int threads = N <= 16 ? 128 : (N <= 128 ? 256 : 512);   // refinement: binary64-bound
   StepGrid g;
   if (method == EIG_JACOBI_FP64) {
-    if (!step_grid(jacobi_smem(N, 8), J, ws, (const void*)k_eig_jacobi<double>, g))
+    if (!step_grid(jacobi_smem(N, 8), J, ws, (const void*)k_eig_jacobi<double, false>, g))
       return cudaErrorInvalidConfiguration;
-    k_eig_jacobi<double><<<g.grid, jthreads, g.smem, st>>>(H0, M, f, N, J, W, eig, status, g.gws,
-                                                           g.per_cta);
+    if (g.gws)
+      k_eig_jacobi<double, true><<<g.grid, jthreads, g.smem, st>>>(H0, M, f, N, J, W, eig, status,
+                                                                   g.gws, g.per_cta);
+    else
+      k_eig_jacobi<double, false><<<g.grid, jthreads, g.smem, st>>>(H0, M, f, N, J, W, eig, status,
+                                                                    g.gws, g.per_cta);
     if (mid) cudaEventRecord(mid, st);
     return cudaGetLastError();
   }
@@ -692,18 +703,37 @@ cudaError_t launch_eig(const double* H0, const double* M, const double* f, int N
     set_max_smem((const void*)k_eig_jacobi32);
     k_eig_jacobi32<<<(J + mpb - 1) / mpb, 32 * mpb, sm, st>>>(H0, M, f, N, J, mpb, W, eig, status);
   } else {
-    if (!step_grid(jacobi_smem(N, 4), J, ws, (const void*)k_eig_jacobi<float>, g))
+    if (!step_grid(jacobi_smem(N, 4), J, ws, (const void*)k_eig_jacobi<float, false>, g))
       return cudaErrorInvalidConfiguration;
-    k_eig_jacobi<float><<<g.grid, jthreads, g.smem, st>>>(H0, M, f, N, J, W, eig, status, g.gws,
-                                                          g.per_cta);
+    if (g.gws)
+      k_eig_jacobi<float, true><<<g.grid, jthreads, g.smem, st>>>(H0, M, f, N, J, W, eig, status,
+                                                                  g.gws, g.per_cta);
+    else
+      k_eig_jacobi<float, false><<<g.grid, jthreads, g.smem, st>>>(H0, M, f, N, J, W, eig, status,
+                                                                   g.gws, g.per_cta);
   }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   if (mid) cudaEventRecord(mid, st);
-  if (!step_grid(refine_smem(N), J, ws, (const void*)k_eig_refine, g))
-    return cudaErrorInvalidConfiguration;
-  k_eig_refine<<<g.grid, threads, g.smem, st>>>(H0, M, f, N, J, refine_sweeps, angle_tol, W, eig,
-                                                status, stats, g.gws, g.per_cta);
+  if (threads <= 256) {
+    if (!step_grid(refine_smem(N), J, ws, (const void*)k_eig_refine<256, false>, g))
+      return cudaErrorInvalidConfiguration;
+    if (g.gws)
+      k_eig_refine<256, true><<<g.grid, threads, g.smem, st>>>(H0, M, f, N, J, refine_sweeps, angle_tol,
+                                                               W, eig, status, stats, g.gws, g.per_cta);
+    else
+      k_eig_refine<256, false><<<g.grid, threads, g.smem, st>>>(H0, M, f, N, J, refine_sweeps, angle_tol,
+                                                                W, eig, status, stats, g.gws, g.per_cta);
+  } else {
+    if (!step_grid(refine_smem(N), J, ws, (const void*)k_eig_refine<512, false>, g))
+      return cudaErrorInvalidConfiguration;
+    if (g.gws)
+      k_eig_refine<512, true><<<g.grid, threads, g.smem, st>>>(H0, M, f, N, J, refine_sweeps, angle_tol,
+                                                               W, eig, status, stats, g.gws, g.per_cta);
+    else
+      k_eig_refine<512, false><<<g.grid, threads, g.smem, st>>>(H0, M, f, N, J, refine_sweeps, angle_tol,
+                                                                W, eig, status, stats, g.gws, g.per_cta);
+  }
   return cudaGetLastError();
 }
 

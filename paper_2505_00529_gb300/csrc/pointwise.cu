@@ -119,13 +119,16 @@ __device__ __forceinline__ void pointwise_step(const double* __restrict__ Wg,
   }
 }
 
+// GWS: storage in the global workspace (compile-time, so that the
+// shared-memory instantiation keeps shared-memory loads)
+template <bool GWS>
 __global__ void k_pointwise(const double* __restrict__ Wg, const double2* __restrict__ Ptil,
                             const double2* __restrict__ Xp, const void* a_hat, const void* l_hat,
                             int mixed, int N, int J, double2 kappa, void* p_hat, void* y_hat,
                             size_t vstride, double* __restrict__ g, double* __restrict__ c,
                             int what, unsigned char* gws, size_t per_cta) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  unsigned char* base = gws ? gws + (size_t)blockIdx.x * per_cta : smem_raw;
+  unsigned char* base = GWS ? gws + (size_t)blockIdx.x * per_cta : smem_raw;
   for (int j = blockIdx.x; j < J; j += gridDim.x) {
     pointwise_step(Wg, Ptil, Xp, a_hat, l_hat, mixed, N, j, kappa, p_hat, y_hat, vstride, g, c,
                    what, base);
@@ -170,10 +173,16 @@ cudaError_t launch_pointwise(const double* W, const double2* Ptil, const double2
   const int threads = N <= 32 ? 32 : (N <= 64 ? 64 : (N <= 128 ? 128 : 256));
   const size_t vstride = ((mixed ? 8 : 16) * (size_t)N + 15) / 16 * 16;
   StepGrid sg;
-  if (!step_grid(pointwise_step_bytes(N), J, ws, (const void*)k_pointwise, sg))
+  if (!step_grid(pointwise_step_bytes(N), J, ws, (const void*)k_pointwise<false>, sg))
     return cudaErrorInvalidConfiguration;
-  k_pointwise<<<sg.grid, threads, sg.smem, st>>>(W, Ptil, Xp, a_hat, l_hat, mixed, N, J, kappa, p_hat,
-                                                 y_hat, vstride, g, c, what, sg.gws, sg.per_cta);
+  if (sg.gws)
+    k_pointwise<true><<<sg.grid, threads, sg.smem, st>>>(W, Ptil, Xp, a_hat, l_hat, mixed, N, J, kappa,
+                                                         p_hat, y_hat, vstride, g, c, what, sg.gws,
+                                                         sg.per_cta);
+  else
+    k_pointwise<false><<<sg.grid, threads, sg.smem, st>>>(W, Ptil, Xp, a_hat, l_hat, mixed, N, J, kappa,
+                                                          p_hat, y_hat, vstride, g, c, what, sg.gws,
+                                                          sg.per_cta);
   return cudaGetLastError();
 }
 

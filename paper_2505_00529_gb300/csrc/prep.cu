@@ -294,14 +294,20 @@ __device__ __forceinline__ void prep_step(const double* __restrict__ Wg,
 
 // One step per CTA in shared memory, or (gws != nullptr, large N) a persistent
 // grid whose CTAs each own a slice of a global workspace.
-__global__ void k_prep(const double* __restrict__ Wg, const double* __restrict__ eig,
+// MAXT: the launch's thread count bound (256: at least 3 CTAs of registers
+// per SM; 512: the large-N launch).  GWS: storage in the global workspace (a
+// compile-time choice, so that the shared-memory instantiation keeps
+// shared-memory loads).
+template <int MAXT, bool GWS>
+__global__ void __launch_bounds__(MAXT, MAXT <= 256 ? 3 : 1)
+k_prep(const double* __restrict__ Wg, const double* __restrict__ eig,
                        const double* __restrict__ Mg, int N, int J, double dt, double mshift,
                        void* __restrict__ Dout, size_t dstride, int d_fp64, int derivs,
                        double2* __restrict__ Ptil, double2* __restrict__ Xp,
                        double* __restrict__ Mtil, int* status, unsigned char* gws,
                        size_t per_cta) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  unsigned char* base = gws ? gws + (size_t)blockIdx.x * per_cta : smem_raw;
+  unsigned char* base = GWS ? gws + (size_t)blockIdx.x * per_cta : smem_raw;
   for (int j = blockIdx.x; j < J; j += gridDim.x) {
     prep_step(Wg, eig, Mg, N, j, dt, mshift, Dout, dstride, d_fp64, derivs, Ptil, Xp, Mtil, status,
               base);
@@ -320,10 +326,26 @@ cudaError_t launch_prep(const double* W, const double* eig, const double* M, int
                         int parts, double2* Ptil, double2* Xp, double* Mtil, int* status,
                         cudaStream_t st, const StepSpace& ws) {
   StepGrid g;
-  if (!step_grid(prep_smem_bytes(N), J, ws, (const void*)k_prep, g)) return cudaErrorInvalidConfiguration;
-  int threads = N <= 8 ? 64 : (N <= 16 ? 128 : (N <= 128 ? 256 : 512));
-  k_prep<<<g.grid, threads, g.smem, st>>>(W, eig, M, N, J, dt, mshift, D, dstride, d_fp64, parts,
-                                          Ptil, Xp, Mtil, status, g.gws, g.per_cta);
+  const int threads = N <= 8 ? 64 : (N <= 16 ? 128 : (N <= 128 ? 256 : 512));
+  if (threads <= 256) {
+    if (!step_grid(prep_smem_bytes(N), J, ws, (const void*)k_prep<256, false>, g))
+      return cudaErrorInvalidConfiguration;
+    if (g.gws)
+      k_prep<256, true><<<g.grid, threads, g.smem, st>>>(W, eig, M, N, J, dt, mshift, D, dstride, d_fp64,
+                                                         parts, Ptil, Xp, Mtil, status, g.gws, g.per_cta);
+    else
+      k_prep<256, false><<<g.grid, threads, g.smem, st>>>(W, eig, M, N, J, dt, mshift, D, dstride, d_fp64,
+                                                          parts, Ptil, Xp, Mtil, status, g.gws, g.per_cta);
+  } else {
+    if (!step_grid(prep_smem_bytes(N), J, ws, (const void*)k_prep<512, false>, g))
+      return cudaErrorInvalidConfiguration;
+    if (g.gws)
+      k_prep<512, true><<<g.grid, threads, g.smem, st>>>(W, eig, M, N, J, dt, mshift, D, dstride, d_fp64,
+                                                         parts, Ptil, Xp, Mtil, status, g.gws, g.per_cta);
+    else
+      k_prep<512, false><<<g.grid, threads, g.smem, st>>>(W, eig, M, N, J, dt, mshift, D, dstride, d_fp64,
+                                                          parts, Ptil, Xp, Mtil, status, g.gws, g.per_cta);
+  }
   return cudaGetLastError();
 }
 

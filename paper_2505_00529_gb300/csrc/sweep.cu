@@ -36,7 +36,10 @@ template <> struct SweepT<true> {
   using D = float2; using V = float2; using B = float; using R = float;
 };
 
-template <bool MIX, int RS, bool BWD>
+// DIRECT: step data read straight from global memory (large N) instead of the
+// shared-memory ring; a template flag so that the ring instantiation keeps
+// shared-memory (not generic) loads.
+template <bool MIX, int RS, bool BWD, bool DIRECT>
 __global__ void __launch_bounds__(1024) k_sweep(const SweepArgs a, const int nstage) {
   extern __shared__ __align__(128) unsigned char smem[];
   using TD = typename SweepT<MIX>::D;
@@ -107,8 +110,8 @@ __global__ void __launch_bounds__(1024) k_sweep(const SweepArgs a, const int nst
     X[(0 * kc + l) * N + i] = v;
   }
   __syncthreads();
-  // nstage == 0: direct mode (large N): the step data is read from global memory
-  const bool ring_mode = nstage > 0;
+  // direct mode (large N): the step data is read from global memory
+  constexpr bool ring_mode = !DIRECT;
   if (threadIdx.x == 0 && ring_mode) {
     const int pre = min(nstage - 1, J);
     for (int it = 0; it < pre; ++it) issue(it);
@@ -272,9 +275,14 @@ static cudaError_t launch_one(const SweepArgs& a, cudaStream_t st) {
   if (2 * (size_t)stage + fixed + 16 > budget) ns = 0;   // direct mode (large N)
   const size_t smem = (size_t)ns * stage + fixed + 8 * ns + 16;
   if (smem > 227 * 1024) return cudaErrorInvalidConfiguration;
-  set_max_smem((const void*)k_sweep<MIX, RS, BWD>);
   const int grid = (a.K + a.kc - 1) / a.kc;
-  k_sweep<MIX, RS, BWD><<<grid, threads, smem, st>>>(a, ns);
+  if (ns == 0) {
+    set_max_smem((const void*)k_sweep<MIX, RS, BWD, true>);
+    k_sweep<MIX, RS, BWD, true><<<grid, threads, smem, st>>>(a, ns);
+  } else {
+    set_max_smem((const void*)k_sweep<MIX, RS, BWD, false>);
+    k_sweep<MIX, RS, BWD, false><<<grid, threads, smem, st>>>(a, ns);
+  }
   return cudaGetLastError();
 }
 
@@ -302,7 +310,7 @@ namespace qoc {
 // intermediate-state fill (vector chains).  Per block, M (N x N), Q (bs
 // columns) and the bs rows of B are staged by bulk copies into the ring.
 // ---------------------------------------------------------------------------
-template <bool MIX, int RS>
+template <bool MIX, int RS, bool DIRECT>
 __device__ __forceinline__ void bsweep_body(const BSweepArgs& a, const int cta, const int nstage,
                                             unsigned char* smem) {
   using TD = typename SweepT<MIX>::D;
@@ -344,9 +352,9 @@ __device__ __forceinline__ void bsweep_body(const BSweepArgs& a, const int cta, 
     if (bb) bulk_g2s(dst + mbytes + qbytes, gB + (size_t)row0 * browb, bb, &bar[s]);
   };
 
-  // nstage == 0: direct mode (large N, a block does not fit the ring twice):
-  // the block data is read straight from global memory (L2), no copies
-  const bool ring_mode = nstage > 0;
+  // direct mode (large N, a block does not fit the ring twice): the block
+  // data is read straight from global memory (L2), no copies
+  constexpr bool ring_mode = !DIRECT;
   if (threadIdx.x == 0) {
     abort_flag = 0;
     for (int s = 0; s < nstage; ++s) mbar_init(&bar[s], 1);
@@ -488,15 +496,15 @@ __device__ __forceinline__ void bsweep_body(const BSweepArgs& a, const int cta, 
   }
 }
 
-template <bool MIX, int RS>
+template <bool MIX, int RS, bool DIRECT>
 __global__ void __launch_bounds__(1024) k_bsweep(const BSweepArgs a, const int nstage) {
   extern __shared__ __align__(128) unsigned char smem[];
-  bsweep_body<MIX, RS>(a, blockIdx.x, nstage, smem);
+  bsweep_body<MIX, RS, DIRECT>(a, blockIdx.x, nstage, smem);
 }
 
 // Many problems in one launch: CTA b belongs to the problem p with
 // cta_off[p] <= b < cta_off[p + 1]; every CTA runs its own dependent chain.
-template <bool MIX, int RS>
+template <bool MIX, int RS, bool DIRECT>
 __global__ void __launch_bounds__(1024) k_bsweep_batch(const BSweepArgs* __restrict__ args,
                                                        const int* __restrict__ cta_off, int nprob,
                                                        const int nstage) {
@@ -507,7 +515,7 @@ __global__ void __launch_bounds__(1024) k_bsweep_batch(const BSweepArgs* __restr
     if (cta_off[mid] <= (int)blockIdx.x) lo = mid; else hi = mid;
   }
   const BSweepArgs a = args[lo];
-  bsweep_body<MIX, RS>(a, (int)blockIdx.x - cta_off[lo], nstage, smem);
+  bsweep_body<MIX, RS, DIRECT>(a, (int)blockIdx.x - cta_off[lo], nstage, smem);
 }
 
 // launch geometry of one problem's blocked sweep: threads, ring stages, smem
@@ -564,8 +572,13 @@ static cudaError_t launch_bb(const BSweepArgs* host_args, const BSweepArgs* dev_
   const int ns = ring_stages(stage, fixed, threads, total_ctas);
   const size_t smem = (size_t)ns * stage + fixed + 8 * ns + 16;
   if (smem > 227 * 1024) return cudaErrorInvalidConfiguration;
-  set_max_smem((const void*)k_bsweep_batch<MIX, RS>);
-  k_bsweep_batch<MIX, RS><<<total_ctas, threads, smem, st>>>(dev_args, dev_cta_off, nprob, ns);
+  if (ns == 0) {
+    set_max_smem((const void*)k_bsweep_batch<MIX, RS, true>);
+    k_bsweep_batch<MIX, RS, true><<<total_ctas, threads, smem, st>>>(dev_args, dev_cta_off, nprob, ns);
+  } else {
+    set_max_smem((const void*)k_bsweep_batch<MIX, RS, false>);
+    k_bsweep_batch<MIX, RS, false><<<total_ctas, threads, smem, st>>>(dev_args, dev_cta_off, nprob, ns);
+  }
   return cudaGetLastError();
 }
 
@@ -590,8 +603,13 @@ static cudaError_t launch_b(const BSweepArgs& a, cudaStream_t st) {
   const int ns = ring_stages(stage, fixed, threads, grid);
   const size_t smem = (size_t)ns * stage + fixed + 8 * ns + 16;
   if (smem > 227 * 1024) return cudaErrorInvalidConfiguration;
-  set_max_smem((const void*)k_bsweep<MIX, RS>);
-  k_bsweep<MIX, RS><<<grid, threads, smem, st>>>(a, ns);
+  if (ns == 0) {
+    set_max_smem((const void*)k_bsweep<MIX, RS, true>);
+    k_bsweep<MIX, RS, true><<<grid, threads, smem, st>>>(a, ns);
+  } else {
+    set_max_smem((const void*)k_bsweep<MIX, RS, false>);
+    k_bsweep<MIX, RS, false><<<grid, threads, smem, st>>>(a, ns);
+  }
   return cudaGetLastError();
 }
 
