@@ -18,6 +18,8 @@
 // r), which costs one complex-by-real N^3 product, and from the direct
 // N-term sum with a stable second divided difference for the pairs with
 // dt |l_p - l_q| <= TAU_DD2 (always including p == q).
+#include <type_traits>
+
 #include "common.cuh"
 #include "kernels.hpp"
 
@@ -130,28 +132,24 @@ __device__ __forceinline__ void prep_step(const double* __restrict__ Wg,
   double2* P = reinterpret_cast<double2*>(Mt + N * ld); // [N][ld]: P~, later Gamma1
   double* lam = reinterpret_cast<double*>(P + N * ld);  // [N]
   double2* eh = reinterpret_cast<double2*>(lam + N + (N & 1));  // [N]
-  double2* pm1 = eh + N;                                // [N] phi(lambda - m) - 1
-  float* Wf = reinterpret_cast<float*>(pm1 + N);        // [N][ld] binary32 copy (mixed D)
-  float2* pm1f = reinterpret_cast<float2*>(Wf + N * ld);  // [N] (N (N+1) is even: 8-byte aligned)
-  int* near = reinterpret_cast<int*>(pm1f + N);         // [NT] packed near pairs
+  int* near = reinterpret_cast<int*>(eh + N);           // [NT] packed near pairs
   double2* Y = reinterpret_cast<double2*>(W);           // [N][ld] overlays W and T
   __shared__ int n_near;
 
   const int tid = threadIdx.x, nt = blockDim.x;
   const double* Wj = Wg + (size_t)j * N * N;
-  // parts: PREP_D (D_j), PREP_P (M~ and P~; M~ also stored when Mtil is given),
-  // PREP_X (X'; from this launch's M~, P~ or, alone, from the stored ones)
-  const bool doD = derivs & PREP_D, doP = derivs & PREP_P, doX = derivs & PREP_X;
+  // parts: PREP_P (M~ and P~; M~ also stored when Mtil is given), PREP_X (X';
+  // from this launch's M~, P~ or, alone, from the stored ones).  The
+  // increments D_j (PREP_D) are k_increments' work.
+  const bool doP = derivs & PREP_P, doX = derivs & PREP_X;
   const bool loadMP = doX && !doP;
   if (tid == 0) n_near = 0;
   for (int e = tid; e < N * N; e += nt) {
     const int p = e / N, q = e % N;
-    if (doD || doP) {
-      const double w = Wj[e];
-      W[p * ld + q] = w;
-      Wf[p * ld + q] = (float)w;
+    if (doP) {
+      W[p * ld + q] = Wj[e];
+      Mt[p * ld + q] = Mg[e];
     }
-    if (doP) Mt[p * ld + q] = Mg[e];
     if (loadMP) {
       Mt[p * ld + q] = Mtil[(size_t)j * N * N + e];
       P[p * ld + q] = Ptil[(size_t)j * N * N + e];
@@ -160,49 +158,10 @@ __device__ __forceinline__ void prep_step(const double* __restrict__ Wg,
   for (int p = tid; p < N; p += nt) {
     const double l = eig[(size_t)j * N + p];
     lam[p] = l;
-    const double x = dt * (l - mshift);
-    double s, c;
-    sincos(x, &s, &c);
-    const double sh = sin(0.5 * x);
-    const double2 v = make_double2(-2.0 * sh * sh, -s);   // exp(-i x) - 1 without cancellation
-    pm1[p] = v;
-    pm1f[p] = make_float2((float)v.x, (float)v.y);
     eh[p] = cexpi(-0.5 * dt * l);
   }
   __syncthreads();
 
-  // D = W diag(pm1) W^T (complex symmetric): upper triangle, mirrored
-  if (!doD) {
-    // derivative-only launch: D is produced by a concurrent launch
-  } else if (d_fp64) {
-    double2* D = reinterpret_cast<double2*>(reinterpret_cast<unsigned char*>(Dout) + (size_t)j * dstride);
-    for (int t = tid; t < NT; t += nt) {
-      int p, q;
-      tri_index(t, N, p, q);
-      double re = 0, im = 0;
-      for (int r = 0; r < N; ++r) {
-        const double w = W[p * ld + r] * W[q * ld + r];
-        re = fma(w, pm1[r].x, re);
-        im = fma(w, pm1[r].y, im);
-      }
-      D[p * N + q] = make_double2(re, im);
-      D[q * N + p] = make_double2(re, im);
-    }
-  } else {
-    float2* D = reinterpret_cast<float2*>(reinterpret_cast<unsigned char*>(Dout) + (size_t)j * dstride);
-    for (int t = tid; t < NT; t += nt) {
-      int p, q;
-      tri_index(t, N, p, q);
-      float re = 0, im = 0;
-      for (int r = 0; r < N; ++r) {
-        const float w = Wf[p * ld + r] * Wf[q * ld + r];
-        re = fmaf(w, pm1f[r].x, re);
-        im = fmaf(w, pm1f[r].y, im);
-      }
-      D[p * N + q] = make_float2(re, im);
-      D[q * N + p] = make_float2(re, im);
-    }
-  }
   if (!doP && !doX) return;
   double2* Pg = Ptil + (size_t)j * N * N;
   if (doP) {
@@ -317,14 +276,93 @@ k_prep(const double* __restrict__ Wg, const double* __restrict__ eig,
 
 size_t prep_smem_bytes(int N) {
   const size_t NT = (size_t)N * (N + 1) / 2;
-  return (5 * (size_t)N * (N + 1) + (N + (N & 1)) + 4 * (size_t)N) * sizeof(double) +
-         ((size_t)N * (N + 1) + (N & 1) + 2 * (size_t)N) * sizeof(float) + NT * sizeof(int) + 16;
+  return (5 * (size_t)N * (N + 1) + (N + (N & 1)) + 2 * (size_t)N) * sizeof(double) +
+         NT * sizeof(int) + 16;
+}
+
+// ---------------------------------------------------------------------------
+// Increments D_j = W diag(phi(lambda - m) - 1) W^T (complex symmetric; upper
+// triangle computed, mirrored), one step per CTA: binary64 for the binary64
+// sweeps, binary32 from a binary32 copy of W for the mixed ones.  With
+// phi(x) - 1 = (-2 sin^2(x/2), -sin x) there is no cancellation.
+// ---------------------------------------------------------------------------
+template <typename R, bool GWS>
+__global__ void __launch_bounds__(256) k_increments(const double* __restrict__ Wg,
+                                                    const double* __restrict__ eig, int N, int J,
+                                                    double dt, double mshift,
+                                                    void* __restrict__ Dout, size_t dstride,
+                                                    unsigned char* gws, size_t per_cta) {
+  using C = typename std::conditional<sizeof(R) == 8, double2, float2>::type;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  unsigned char* base = GWS ? gws + (size_t)blockIdx.x * per_cta : smem_raw;
+  const int ld = N + 1, NT = N * (N + 1) / 2;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  C* pm = reinterpret_cast<C*>(base);                 // [N]
+  R* Ws = reinterpret_cast<R*>(pm + N);               // [N][ld]
+  for (int j = blockIdx.x; j < J; j += gridDim.x) {
+    const double* Wj = Wg + (size_t)j * N * N;
+    for (int e = tid; e < N * N; e += nt) Ws[(e / N) * ld + (e % N)] = (R)Wj[e];
+    for (int p = tid; p < N; p += nt) {
+      const double x = dt * (eig[(size_t)j * N + p] - mshift);
+      const double sh = sin(0.5 * x);
+      C v;
+      v.x = (R)(-2.0 * sh * sh);
+      v.y = (R)(-sin(x));
+      pm[p] = v;
+    }
+    __syncthreads();
+    C* D = reinterpret_cast<C*>(reinterpret_cast<unsigned char*>(Dout) + (size_t)j * dstride);
+    for (int t = tid; t < NT; t += nt) {
+      int p, q;
+      tri_index(t, N, p, q);
+      R re = 0, im = 0;
+      for (int r = 0; r < N; ++r) {
+        const R w = Ws[p * ld + r] * Ws[q * ld + r];
+        re = fma(w, pm[r].x, re);
+        im = fma(w, pm[r].y, im);
+      }
+      C v;
+      v.x = re;
+      v.y = im;
+      D[p * N + q] = v;
+      D[q * N + p] = v;
+    }
+    __syncthreads();
+  }
+}
+
+static size_t increments_bytes(int N, int d_fp64) {
+  return (size_t)N * (d_fp64 ? 16 : 8) + (size_t)N * (N + 1) * (d_fp64 ? 8 : 4) + 16;
+}
+
+template <typename R>
+static cudaError_t launch_inc(const double* W, const double* eig, int N, int J, double dt,
+                              double mshift, void* D, size_t dstride, cudaStream_t st,
+                              const StepSpace& ws) {
+  StepGrid g;
+  if (!step_grid(increments_bytes(N, sizeof(R) == 8), J, ws, (const void*)k_increments<R, false>, g))
+    return cudaErrorInvalidConfiguration;
+  const int threads = N <= 16 ? 128 : 256;
+  if (g.gws)
+    k_increments<R, true><<<g.grid, threads, g.smem, st>>>(W, eig, N, J, dt, mshift, D, dstride, g.gws,
+                                                           g.per_cta);
+  else
+    k_increments<R, false><<<g.grid, threads, g.smem, st>>>(W, eig, N, J, dt, mshift, D, dstride, g.gws,
+                                                            g.per_cta);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_prep(const double* W, const double* eig, const double* M, int N, int J,
                         double dt, double mshift, void* D, size_t dstride, int d_fp64,
                         int parts, double2* Ptil, double2* Xp, double* Mtil, int* status,
                         cudaStream_t st, const StepSpace& ws) {
+  if (parts & PREP_D) {
+    cudaError_t e = d_fp64 ? launch_inc<double>(W, eig, N, J, dt, mshift, D, dstride, st, ws)
+                           : launch_inc<float>(W, eig, N, J, dt, mshift, D, dstride, st, ws);
+    if (e != cudaSuccess) return e;
+    parts &= ~PREP_D;
+    if (!parts) return cudaSuccess;
+  }
   StepGrid g;
   const int threads = N <= 8 ? 64 : (N <= 16 ? 128 : (N <= 128 ? 256 : 512));
   if (threads <= 256) {
