@@ -39,6 +39,9 @@ WORKLOAD = {"workload": "synthetic CI-shaped single problem, N=32 basis, K=64 si
 # tangent and second-order adjoint panels, 2 panel contractions, grad, hess partial,
 # hess final
 LAUNCHES_PER_EVAL = 27
+# DRAM bytes of one k_eig_refine launch on this workload (ncu capture of the
+# current kernel: 32.93 MB read, 0 written; algorithmic: W read once, 32.8 MB)
+REFINE_TRAFFIC_BYTES = 32.93e6
 FP64_PEAK_TFLOPS = 1.26    # 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (measured 1.20 at 1.99 GHz)
 FP32_PEAK_TFLOPS = 80.5    # 152 SMs x 128 FMA/clk x 2 flop x 2.07 GHz (measured 70 at 1.99 GHz)
 
@@ -307,7 +310,10 @@ def run_ours(args):
         flops = refine_flops(N, J, u, rot, fin)
         ach = flops / (t_ref * 1e-3) / 1e12
         roof = {"bound": "alu", "kernel": "k_eig_refine", "achieved": ach, "peak": FP64_PEAK_TFLOPS,
-                "unit": "TFLOP/s", "frac": ach / FP64_PEAK_TFLOPS, "traffic": None,
+                "unit": "TFLOP/s", "frac": ach / FP64_PEAK_TFLOPS,
+                "traffic": REFINE_TRAFFIC_BYTES if (N, J) == (32, 4000) else None,
+                "traffic_source": "dram__bytes_read.sum + dram__bytes_write.sum of one k_eig_refine "
+                                  "launch (ncu; profiles/kernels_grad_hess_N32_K64_J4000_mixed.md)",
                 "peak_source": "binary64 FMA rate from unit counts x max SM clock (152 SMs x 2 DFMA/clk "
                                "x 2 x 2.07 GHz); MEASURED_PEAKS.json has no binary64 figure",
                 "algorithmic": f"(2u + 1 + p + r) N^3 binary64 FMA per step, u = {u:.3f} updates/step, "
