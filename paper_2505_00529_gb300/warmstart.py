@@ -68,6 +68,44 @@ def solve_many(prob, betas, theta0s, precision=_lib.QOC_MIXED_FP32, workers=4, *
     return thetas, infos, secs
 
 
+GUARD_STEPS = (0.0, 0.25, 0.5, 0.75, 1.0)
+
+
+def guarded_starts(prob, betas, theta_mlp, precision=_lib.QOC_MIXED_FP32, workers=4,
+                   steps=GUARD_STEPS):
+    """theta0 = t* MLP(beta) with t* the minimiser of J(t MLP(beta)) over
+    `steps` (t = 0 included, so theta = 0 stays the fallback and the start is
+    never worse in J).  Cost-only evaluations by the library; returns
+    (theta0s, t*, seconds)."""
+    n, K = len(betas), prob.B.shape[1]
+    out = np.zeros((n, K))
+    tstar = np.zeros(n)
+    problems = [_lib.Problem(prob, precision=precision) for _ in range(workers)]
+
+    def run(w):
+        P = problems[w]
+        for i in range(w, n, workers):
+            P.set_target(betas[i])
+            best, bt = None, 0.0
+            for t in steps:
+                try:
+                    J = P.eval_J(t * theta_mlp[i])
+                except _lib.QocError:
+                    continue
+                if best is None or J < best:
+                    best, bt = J, t
+            tstar[i] = bt
+            out[i] = bt * theta_mlp[i]
+
+    t0 = time.perf_counter()
+    with cf.ThreadPoolExecutor(workers) as ex:
+        list(ex.map(run, range(workers)))
+    secs = time.perf_counter() - t0
+    for P in problems:
+        P.close()
+    return out, tstar, secs
+
+
 class WarmStart:
     """theta0 = scale * MLP([Re beta, Im beta]) + shift (outputs standardised
     on the training set)."""
@@ -115,22 +153,43 @@ def compare(prob, train_betas, test_betas, precision=_lib.QOC_MIXED_FP32, worker
     theta0 = ws.predict(test_betas)
     _, info_zero, t_zero = solve_many(prob, test_betas, np.zeros((len(test_betas), K)), precision, workers, **tr)
     _, info_mlp, t_mlp = solve_many(prob, test_betas, theta0, precision, workers, **tr)
+    theta_g, tstar, t_guard_eval = guarded_starts(prob, test_betas, theta0, precision, workers)
+    _, info_g, t_g = solve_many(prob, test_betas, theta_g, precision, workers, **tr)
     ws.close()
-    good = np.array([a["stop"] in ("gtol", "xtol") and b["stop"] in ("gtol", "xtol")
-                     for a, b in zip(info_zero, info_mlp)])
+    conv = lambda i: i["stop"] in ("gtol", "xtol")
+    good = np.array([conv(a) and conv(b) and conv(c) for a, b, c in zip(info_zero, info_mlp, info_g)])
+    gh0 = np.array([i.get("n_eval_gh", 0) for i in info_zero])[good]
+    gh1 = np.array([i.get("n_eval_gh", 0) for i in info_mlp])[good]
     it0 = np.array([i["iters"] for i in info_zero])[good]
     it1 = np.array([i["iters"] for i in info_mlp])[good]
+    itg = np.array([i["iters"] for i in info_g])[good]
     J0 = np.array([i["J"] for i in info_zero])[good]
     J1 = np.array([i["J"] for i in info_mlp])[good]
+    Jg = np.array([i["J"] for i in info_g])[good]
     return {
         "n_train": int(ok.sum()), "n_train_failed": int((~ok).sum()), "n_test": len(test_betas),
         "n_test_compared": int(good.sum()), "dataset_seconds": t_data,
         "train_seconds": t_train, "final_train_loss": float(losses[-1]),
         "iters_zero_mean": float(it0.mean()), "iters_mlp_mean": float(it1.mean()),
+        "iters_zero_median": float(np.median(it0)), "iters_mlp_median": float(np.median(it1)),
         "iters_ratio_mean": float(np.mean(it0 / np.maximum(it1, 1))),
+        "frac_mlp_fewer_iters": float(np.mean(it1 < it0)), "frac_mlp_more_iters": float(np.mean(it1 > it0)),
+        "hess_evals_zero_mean": float(gh0.mean()), "hess_evals_mlp_mean": float(gh1.mean()),
+        "wall_ratio_zero_over_mlp": t_zero / t_mlp,
         "wall_zero_s": t_zero, "wall_mlp_s": t_mlp,
         "J_zero_mean": float(J0.mean()), "J_mlp_mean": float(J1.mean()),
         "frac_mlp_not_worse_J": float(np.mean(J1 <= J0 * (1 + 1e-6))),
         "converged_zero": float(np.mean([i["stop"] in ("gtol", "xtol") for i in info_zero])),
         "converged_mlp": float(np.mean([i["stop"] in ("gtol", "xtol") for i in info_mlp])),
+        "guarded": {
+            "rule": "theta0 = t* MLP(beta), t* = argmin J(t MLP(beta)) over t in "
+                    + ", ".join(f"{t:g}" for t in GUARD_STEPS),
+            "t_star_mean": float(tstar.mean()), "t_star_zero_fraction": float(np.mean(tstar == 0.0)),
+            "iters_mean": float(itg.mean()), "iters_median": float(np.median(itg)),
+            "iters_ratio_mean": float(np.mean(it0 / np.maximum(itg, 1))),
+            "frac_fewer_iters": float(np.mean(itg < it0)), "frac_more_iters": float(np.mean(itg > it0)),
+            "wall_s": t_g + t_guard_eval, "guard_eval_s": t_guard_eval,
+            "J_mean": float(Jg.mean()), "frac_not_worse_J": float(np.mean(Jg <= J0 * (1 + 1e-6))),
+            "converged": float(np.mean([conv(i) for i in info_g])),
+        },
     }
