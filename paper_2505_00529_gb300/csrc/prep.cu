@@ -120,8 +120,7 @@ __device__ __forceinline__ double2 dd2_table(int a, int b, int c, const double* 
 __device__ __forceinline__ void prep_step(const double* __restrict__ Wg,
                                           const double* __restrict__ eig,
                                           const double* __restrict__ Mg, int N, int j, double dt,
-                                          double mshift, void* __restrict__ Dout, size_t dstride,
-                                          int d_fp64, int derivs, double2* __restrict__ Ptil,
+                                          int derivs, double2* __restrict__ Ptil,
                                           double2* __restrict__ Xp, double* __restrict__ Mtil,
                                           int* status, unsigned char* smem_raw) {
   const int ld = N + 1;
@@ -260,16 +259,14 @@ __device__ __forceinline__ void prep_step(const double* __restrict__ Wg,
 template <int MAXT, bool GWS>
 __global__ void __launch_bounds__(MAXT, MAXT <= 256 ? 3 : 1)
 k_prep(const double* __restrict__ Wg, const double* __restrict__ eig,
-                       const double* __restrict__ Mg, int N, int J, double dt, double mshift,
-                       void* __restrict__ Dout, size_t dstride, int d_fp64, int derivs,
+                       const double* __restrict__ Mg, int N, int J, double dt, int derivs,
                        double2* __restrict__ Ptil, double2* __restrict__ Xp,
                        double* __restrict__ Mtil, int* status, unsigned char* gws,
                        size_t per_cta) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   unsigned char* base = GWS ? gws + (size_t)blockIdx.x * per_cta : smem_raw;
   for (int j = blockIdx.x; j < J; j += gridDim.x) {
-    prep_step(Wg, eig, Mg, N, j, dt, mshift, Dout, dstride, d_fp64, derivs, Ptil, Xp, Mtil, status,
-              base);
+    prep_step(Wg, eig, Mg, N, j, dt, derivs, Ptil, Xp, Mtil, status, base);
     __syncthreads();
   }
 }
@@ -369,20 +366,20 @@ cudaError_t launch_prep(const double* W, const double* eig, const double* M, int
     if (!step_grid(prep_smem_bytes(N), J, ws, (const void*)k_prep<256, false>, g))
       return cudaErrorInvalidConfiguration;
     if (g.gws)
-      k_prep<256, true><<<g.grid, threads, g.smem, st>>>(W, eig, M, N, J, dt, mshift, D, dstride, d_fp64,
-                                                         parts, Ptil, Xp, Mtil, status, g.gws, g.per_cta);
+      k_prep<256, true><<<g.grid, threads, g.smem, st>>>(W, eig, M, N, J, dt, parts, Ptil, Xp, Mtil,
+                                                         status, g.gws, g.per_cta);
     else
-      k_prep<256, false><<<g.grid, threads, g.smem, st>>>(W, eig, M, N, J, dt, mshift, D, dstride, d_fp64,
-                                                          parts, Ptil, Xp, Mtil, status, g.gws, g.per_cta);
+      k_prep<256, false><<<g.grid, threads, g.smem, st>>>(W, eig, M, N, J, dt, parts, Ptil, Xp, Mtil,
+                                                          status, g.gws, g.per_cta);
   } else {
     if (!step_grid(prep_smem_bytes(N), J, ws, (const void*)k_prep<512, false>, g))
       return cudaErrorInvalidConfiguration;
     if (g.gws)
-      k_prep<512, true><<<g.grid, threads, g.smem, st>>>(W, eig, M, N, J, dt, mshift, D, dstride, d_fp64,
-                                                         parts, Ptil, Xp, Mtil, status, g.gws, g.per_cta);
+      k_prep<512, true><<<g.grid, threads, g.smem, st>>>(W, eig, M, N, J, dt, parts, Ptil, Xp, Mtil,
+                                                         status, g.gws, g.per_cta);
     else
-      k_prep<512, false><<<g.grid, threads, g.smem, st>>>(W, eig, M, N, J, dt, mshift, D, dstride, d_fp64,
-                                                          parts, Ptil, Xp, Mtil, status, g.gws, g.per_cta);
+      k_prep<512, false><<<g.grid, threads, g.smem, st>>>(W, eig, M, N, J, dt, parts, Ptil, Xp, Mtil,
+                                                          status, g.gws, g.per_cta);
   }
   return cudaGetLastError();
 }
