@@ -239,10 +239,16 @@ def test_time_blocking(bs, precision):
     tol = TOL[precision]
     for method in (q.QOC_HESS_SECOND_ORDER_ADJOINT, q.QOC_HESS_TANGENT):
         with q.Problem(prob, precision=precision, hess_method=method, block_steps=bs) as P:
+            # the vector chains take twice the panels' block steps, at most 8
+            assert P.block_steps == (bs, 1 if bs == 1 else min(8, 2 * bs))
             J, g, H = P.eval_grad_hess(theta)
             assert abs(J - ref["J"]) <= tol * abs(ref["J"])
             assert rel(g, ref["grad"]) <= tol
             assert rel(H, ref["hess"]) <= tol
+            J1, g1 = P.eval_grad(theta)
+            assert abs(J1 - ref["J"]) <= tol * abs(ref["J"])
+            assert rel(g1, ref["grad"]) <= tol
+            assert abs(P.eval_J(theta) - ref["J"]) <= tol * abs(ref["J"])
             tin = TOL_INTER[precision]
             assert rel(P.buffer(_lib.QOC_BUF_STATE), ref["a"]) <= tin
             assert rel(P.buffer(_lib.QOC_BUF_COSTATE)[1:], ref["lam"][1:]) <= tin
@@ -257,3 +263,7 @@ def test_block_steps_validation():
         for bad in (0, 9, 6):
             with pytest.raises(q.QocError):
                 q.qoc_set_block_steps(P.handle, bad)
+        # chain blocks never exceed J
+        for bs, expect in ((1, (1, 1)), (2, (2, 4)), (3, (3, 3)), (4, (4, 4)), (5, (5, 5))):
+            q.qoc_set_block_steps(P.handle, bs)
+            assert P.block_steps == expect
