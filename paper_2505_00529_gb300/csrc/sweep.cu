@@ -496,6 +496,264 @@ __device__ __forceinline__ void bsweep_body(const BSweepArgs& a, const int cta, 
   }
 }
 
+// ---------------------------------------------------------------------------
+// Blocked sweep with binary32 increments for N <= 4 NQ, warp-specialised.
+// One producer warp keeps the ring full: an elected lane refills a slot with
+// bulk copies as soon as every consumer warp has released it on the slot's
+// "empty" barrier.  The consumer warps own the state: four lanes per row i,
+// lane r taking the terms q = r, r + 4, ...; each lane holds its M (and Q, B)
+// entries of the NEXT block in registers, loaded while the current block is
+// reduced, so that the dependent part of a block step is: read X (shared,
+// broadcast, padded runs of the permuted layout below), the FMA chain, two
+// shuffle rounds, the TwoSum update, write X, one named barrier.
+// X layout per column: entry q at run (q mod 4), position (q div 4); runs are
+// XS = NQ + 2 float2 apart so the four runs a warp reads sit in different
+// banks.
+// ---------------------------------------------------------------------------
+template <int NQ>
+struct FastRegs {
+  float2 m[NQ];
+  float2 q[2];
+  float b[2];
+};
+
+template <int NQ>
+__device__ __forceinline__ void fast_load(FastRegs<NQ>& r, const BSweepArgs& a, const unsigned char* sp,
+                                          int it, int rsub, int i, int col, int kq, bool active) {
+  const int N = a.N;
+  const float2* Ms = reinterpret_cast<const float2*>(sp);
+  const int off = rsub * N + i;
+#pragma unroll
+  for (int k = 0; k < NQ; ++k)
+    r.m[k] = (active && k < kq) ? Ms[off + 4 * k * N] : make_float2(0.f, 0.f);
+  if (a.Q) {
+    const int t0 = it * a.bs, bl = min(a.bs, a.J - t0);
+    const float2* Qs = reinterpret_cast<const float2*>(sp + a.mstride);
+    const float* Bs = reinterpret_cast<const float*>(sp + a.mstride + a.qstride);
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      const int mm = rsub + 4 * u;
+      if (active && mm < bl) {
+        const int lr = a.backward ? bl - 1 - mm : mm;
+        r.q[u] = Qs[mm * N + i];
+        r.b[u] = Bs[lr * a.Kp + col];
+      } else {
+        r.q[u] = make_float2(0.f, 0.f);
+        r.b[u] = 0.f;
+      }
+    }
+  }
+}
+
+template <int NQ>
+__device__ __forceinline__ void bsweep_fast_body(const BSweepArgs& a, const int cta, const int nstage,
+                                                 unsigned char* smem) {
+  constexpr int RS = 4, RPW = 8, XS = NQ + 2;
+  const int N = a.N, kc = a.kc, J = a.J, bs = a.bs;
+  const int nblk = (J + bs - 1) / bs;
+  const int WPC = (N + RPW - 1) / RPW;
+  const int ncw = WPC * kc;                       // consumer warps
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint32_t mbytes = (uint32_t)a.mstride;
+  const uint32_t qbytes = a.Q ? (uint32_t)a.qstride : 0u;
+  const uint32_t browb = (uint32_t)(sizeof(float) * a.Kp);
+  const uint32_t stage = mbytes + qbytes + (a.Brow ? browb * bs : 0u);
+  unsigned char* ring = smem;
+  float2* Xs = reinterpret_cast<float2*>(ring + (size_t)nstage * stage);   // [2][kc][RS][XS]
+  const int xbuf = kc * RS * XS;
+  uint64_t* full = reinterpret_cast<uint64_t*>(Xs + 2 * xbuf);
+  uint64_t* empty = full + nstage;
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(empty + nstage);
+
+  for (int e = threadIdx.x; e < 2 * xbuf; e += blockDim.x) Xs[e] = make_float2(0.f, 0.f);
+  if (threadIdx.x == 0) {
+    *abort_flag = 0;
+    for (int s = 0; s < nstage; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], ncw);
+    }
+    mbar_fence_init();
+  }
+  __syncthreads();
+  if (warp > ncw) return;
+
+  if (warp == ncw) {   // ---- producer ----
+    if (lane != 0) return;
+    const unsigned char* gB = reinterpret_cast<const unsigned char*>(a.Brow);
+    int s = 0, round = 0, issued = 0;
+    for (int it = 0; it < nblk; ++it) {
+      if (*abort_flag) break;
+      if (it >= nstage && !mbar_wait_or_flag(&empty[s], (uint32_t)((round - 1) & 1), abort_flag)) {
+        *abort_flag = 1;
+        break;
+      }
+      const int t0 = it * bs, bl = min(bs, J - t0);
+      const int row0 = a.backward ? J - t0 - bl : t0;
+      const uint32_t qb = qbytes ? (((uint32_t)(bl * N) * 8u + 15u) & ~15u) : 0u;
+      const uint32_t bb = a.Brow ? browb * (uint32_t)bl : 0u;
+      unsigned char* dst = ring + (size_t)s * stage;
+      fence_proxy_async_smem();
+      mbar_arrive_expect_tx(&full[s], mbytes + qb + bb);
+      bulk_g2s(dst, a.M + (size_t)it * a.mstride, mbytes, &full[s]);
+      if (qb) bulk_g2s(dst + mbytes, a.Q + (size_t)it * a.qstride, qb, &full[s]);
+      if (bb) bulk_g2s(dst + mbytes + qbytes, gB + (size_t)row0 * browb, bb, &full[s]);
+      issued = it + 1;
+      if (++s == nstage) { s = 0; ++round; }
+    }
+    // the copies issued last (each the latest phase of its slot) have landed
+    // before the CTA may exit, also when the consumers stopped early
+    for (int k = max(0, issued - nstage); k < issued; ++k)
+      mbar_wait_bounded(&full[k % nstage], (uint32_t)((k / nstage) & 1), 100000000ull);
+    return;
+  }
+
+  // ---- consumers ----
+  const int l = warp / WPC, rb = warp % WPC;
+  const int rsub = lane & 3;
+  const int i = rb * RPW + (lane >> 2);
+  const int col = cta * kc + l;
+  const bool active = col < a.K && i < N;
+  const bool owner = active && rsub == 0;
+  const int kq = (N - rsub + 3) >> 2;             // terms q = rsub + 4k < N
+  const int nthr = 32 * ncw;
+  const int xw = (i & 3) * XS + (i >> 2);         // this row's entry in the permuted layout
+  float2* Xl = Xs + l * RS * XS;
+  const float4* Xr = reinterpret_cast<const float4*>(Xl + rsub * XS);
+
+  double2 x0 = make_double2(0.0, 0.0);
+  if (active && a.init) {
+    x0 = a.init[(size_t)col * N + i];
+    x0.x *= a.init_scale;
+    x0.y *= a.init_scale;
+  }
+  float hx = (float)x0.x, hy = (float)x0.y;
+  float lx = (float)(x0.x - (double)hx), ly = (float)(x0.y - (double)hy);
+  const size_t xb_stride = (size_t)a.K * N;
+  size_t xb_off = (size_t)col * N + i;
+  auto store_blk = [&]() {
+    if (a.xblk_pairs) reinterpret_cast<float4*>(a.Xblk)[xb_off] = make_float4(hx, hy, lx, ly);
+    else reinterpret_cast<float2*>(a.Xblk)[xb_off] = make_float2(hx, hy);
+  };
+  if (owner) {
+    Xl[xw] = make_float2(hx, hy);
+    store_blk();
+  }
+
+  // Every consumer takes the same exit decision: the OR, over the consumers,
+  // of a failed wait or a raised flag, formed by the step's barrier itself.
+  FastRegs<NQ> ra, rb2;
+  int s = 0;
+  uint32_t par = 0;
+  bool bad = false;
+  if (!mbar_wait_or_flag(&full[0], 0u, abort_flag)) {
+    bad = true;
+    *abort_flag = 1;
+  }
+  fast_load<NQ>(ra, a, ring, 0, rsub, i, col, kq, active);
+  bool ok = !named_barrier_or(1, nthr, bad || *abort_flag != 0);
+
+  int cur = 0;
+  // one block step with `r` holding this block's data; `nx` receives the next block's
+  auto step = [&](int it, const FastRegs<NQ>& r, FastRegs<NQ>& nx) -> bool {
+    // release this block's slot: its entries were loaded before the last barrier
+    if (lane == 0) mbar_arrive(&empty[s]);
+    const float4* xp = Xr + cur * (xbuf / 2);
+    float4 xv[NQ / 2];
+#pragma unroll
+    for (int k = 0; k < NQ / 2; ++k) xv[k] = xp[k];
+    float ax[4] = {0.f, 0.f, 0.f, 0.f}, ay[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+    for (int k = 0; k < NQ; ++k) {
+      const float xr = (k & 1) ? xv[k >> 1].z : xv[k >> 1].x;
+      const float xi = (k & 1) ? xv[k >> 1].w : xv[k >> 1].y;
+      ax[k & 3] = fmaf(r.m[k].x, xr, ax[k & 3]);
+      ay[k & 3] = fmaf(r.m[k].x, xi, ay[k & 3]);
+      ax[k & 3] = fmaf(-r.m[k].y, xi, ax[k & 3]);
+      ay[k & 3] = fmaf(r.m[k].y, xr, ay[k & 3]);
+    }
+    if (a.Q) {
+      ax[0] = fmaf(r.q[0].x, r.b[0], ax[0]);
+      ay[0] = fmaf(r.q[0].y, r.b[0], ay[0]);
+      ax[1] = fmaf(r.q[1].x, r.b[1], ax[1]);
+      ay[1] = fmaf(r.q[1].y, r.b[1], ay[1]);
+    }
+    // next block's data (independent of X)
+    int s1 = s + 1;
+    uint32_t par1 = par;
+    if (s1 == nstage) { s1 = 0; par1 ^= 1u; }
+    if (it + 1 < nblk) {
+      if (!mbar_wait_or_flag(&full[s1], par1, abort_flag)) {
+        bad = true;
+        *abort_flag = 1;
+      }
+      fast_load<NQ>(nx, a, ring + (size_t)s1 * stage, it + 1, rsub, i, col, kq, active);
+    }
+    float sx = (ax[0] + ax[1]) + (ax[2] + ax[3]);
+    float sy = (ay[0] + ay[1]) + (ay[2] + ay[3]);
+    sx += __shfl_xor_sync(0xffffffffu, sx, 1);
+    sy += __shfl_xor_sync(0xffffffffu, sy, 1);
+    sx += __shfl_xor_sync(0xffffffffu, sx, 2);
+    sy += __shfl_xor_sync(0xffffffffu, sy, 2);
+    if (owner) {
+      pair_add(hx, lx, sx);
+      pair_add(hy, ly, sy);
+      Xl[(cur ^ 1) * xbuf + xw] = make_float2(hx, hy);
+      if (it + 1 < nblk) {
+        xb_off += xb_stride;
+        store_blk();
+      }
+    }
+    const bool stop = named_barrier_or(1, nthr, bad || *abort_flag != 0);
+    cur ^= 1;
+    s = s1;
+    par = par1;
+    return !stop;
+  };
+  int it = 0;
+  for (; ok && it + 1 < nblk; it += 2) {
+    ok = step(it, ra, rb2);
+    if (ok) ok = step(it + 1, rb2, ra);
+  }
+  if (ok && it < nblk) ok = step(it, ra, rb2);
+  if (!ok) {
+    if (threadIdx.x == 0) raise_status(a.status, DEV_TIMEOUT);
+    *abort_flag = 1;   // stops the producer
+    return;
+  }
+  const double fx = (double)hx + (double)lx, fy = (double)hy + (double)ly;
+  if (owner) {
+    if (a.final_out) a.final_out[(size_t)col * N + i] = make_double2(fx, fy);
+    if (a.states) {   // final state of a vector chain: a_J forward, lambda_0 backward
+      const size_t row = (size_t)(a.backward ? 0 : J) * N + i;
+      reinterpret_cast<float4*>(a.states)[row] = make_float4(hx, hy, lx, ly);
+    }
+    if (!(isfinite(fx) && isfinite(fy))) raise_status(a.status, DEV_NONFINITE);
+  }
+}
+
+// thread cap of the warp-specialised kernels: room for two blocks of entries in registers
+template <int NQ> struct FastCap { static constexpr int threads = NQ <= 8 ? 512 : 384; };
+
+template <int NQ>
+__global__ void __launch_bounds__(FastCap<NQ>::threads) k_bsweep_fast(const BSweepArgs a, const int nstage) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  bsweep_fast_body<NQ>(a, blockIdx.x, nstage, smem);
+}
+
+template <int NQ>
+__global__ void __launch_bounds__(FastCap<NQ>::threads) k_bsweep_fast_batch(const BSweepArgs* __restrict__ args,
+                                                            const int* __restrict__ cta_off, int nprob,
+                                                            const int nstage) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  int lo = 0, hi = nprob;   // largest p with cta_off[p] <= blockIdx.x
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (cta_off[mid] <= (int)blockIdx.x) lo = mid; else hi = mid;
+  }
+  const BSweepArgs a = args[lo];
+  bsweep_fast_body<NQ>(a, (int)blockIdx.x - cta_off[lo], nstage, smem);
+}
+
 template <bool MIX, int RS, bool DIRECT>
 __global__ void __launch_bounds__(1024) k_bsweep(const BSweepArgs a, const int nstage) {
   extern __shared__ __align__(128) unsigned char smem[];
@@ -582,10 +840,74 @@ static cudaError_t launch_bb(const BSweepArgs* host_args, const BSweepArgs* dev_
   return cudaGetLastError();
 }
 
+// geometry of the warp-specialised binary32 sweep (consumer warps + producer)
+template <int NQ>
+static void fast_geometry(const BSweepArgs& a, int& threads, size_t& stage, size_t& fixed) {
+  threads = 32 * (((a.N + 7) / 8) * a.kc + 1);
+  stage = a.mstride + (a.Q ? a.qstride : 0) + (a.Brow ? sizeof(float) * a.Kp * a.bs : 0);
+  fixed = 2 * (size_t)a.kc * 4 * (NQ + 2) * sizeof(float2) + 16;
+}
+
+// ring depth and shared memory of a warp-specialised launch; 0 if it does not apply
+template <int NQ>
+static int fast_plan(int threads, size_t stage, size_t fixed, int total_ctas, size_t& smem) {
+  if (threads > FastCap<NQ>::threads) return 0;
+  const int ns = ring_stages(stage, fixed + 8 * 16, threads, total_ctas);
+  if (ns < 2) return 0;
+  smem = (size_t)ns * stage + fixed + 16 * (size_t)ns + 16;
+  return smem <= 227 * 1024 ? ns : 0;
+}
+
+template <int NQ>
+static bool launch_fast(const BSweepArgs& a, cudaStream_t st, cudaError_t& err) {
+  int threads;
+  size_t stage, fixed, smem = 0;
+  fast_geometry<NQ>(a, threads, stage, fixed);
+  const int grid = (a.K + a.kc - 1) / a.kc;
+  const int ns = fast_plan<NQ>(threads, stage, fixed, grid, smem);
+  if (!ns) return false;
+  set_max_smem((const void*)k_bsweep_fast<NQ>);
+  k_bsweep_fast<NQ><<<grid, threads, smem, st>>>(a, ns);
+  err = cudaGetLastError();
+  return true;
+}
+
+template <int NQ>
+static bool launch_fast_batch(const BSweepArgs* host_args, const BSweepArgs* dev_args,
+                              const int* dev_cta_off, int nprob, int total_ctas, cudaStream_t st,
+                              cudaError_t& err) {
+  int threads = 32;
+  size_t stage = 16, fixed = 16, smem = 0;
+  for (int p = 0; p < nprob; ++p) {
+    int t;
+    size_t sg, f;
+    fast_geometry<NQ>(host_args[p], t, sg, f);
+    threads = t > threads ? t : threads;
+    stage = sg > stage ? sg : stage;
+    fixed = f > fixed ? f : fixed;
+  }
+  const int ns = fast_plan<NQ>(threads, stage, fixed, total_ctas, smem);
+  if (!ns) return false;
+  set_max_smem((const void*)k_bsweep_fast_batch<NQ>);
+  k_bsweep_fast_batch<NQ><<<total_ctas, threads, smem, st>>>(dev_args, dev_cta_off, nprob, ns);
+  err = cudaGetLastError();
+  return true;
+}
+
 cudaError_t launch_bsweep_batch(const BSweepArgs* host_args, const BSweepArgs* dev_args,
                                 const int* dev_cta_off, int nprob, int total_ctas, int mixed,
                                 cudaStream_t st) {
-  if (mixed) return launch_bb<true, 4>(host_args, dev_args, dev_cta_off, nprob, total_ctas, st);
+  if (mixed) {
+    int nmax = 0;
+    for (int p = 0; p < nprob; ++p) nmax = host_args[p].N > nmax ? host_args[p].N : nmax;
+    cudaError_t e = cudaSuccess;
+    if (nmax <= 32 && launch_fast_batch<8>(host_args, dev_args, dev_cta_off, nprob, total_ctas, st, e))
+      return e;
+    if (nmax > 32 && nmax <= 64 &&
+        launch_fast_batch<16>(host_args, dev_args, dev_cta_off, nprob, total_ctas, st, e))
+      return e;
+    return launch_bb<true, 4>(host_args, dev_args, dev_cta_off, nprob, total_ctas, st);
+  }
   return launch_bb<false, 4>(host_args, dev_args, dev_cta_off, nprob, total_ctas, st);
 }
 
@@ -614,7 +936,12 @@ static cudaError_t launch_b(const BSweepArgs& a, cudaStream_t st) {
 }
 
 cudaError_t launch_bsweep(const BSweepArgs& a, int mixed, cudaStream_t st) {
-  if (mixed) return launch_b<true, 4>(a, st);
+  if (mixed) {
+    cudaError_t e = cudaSuccess;
+    if (a.N <= 32 && launch_fast<8>(a, st, e)) return e;
+    if (a.N > 32 && a.N <= 64 && launch_fast<16>(a, st, e)) return e;
+    return launch_b<true, 4>(a, st);
+  }
   return launch_b<false, 4>(a, st);
 }
 
