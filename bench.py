@@ -37,7 +37,7 @@ WORKLOAD = {"workload": "synthetic CI-shaped single problem, N=32 basis, K=64 si
 # 2 block products, state chain + fill, terminal, costate chain + fill, drift,
 # 3 pointwise parts (p^, y^/g, c), 3 block-source launches (Q, W/Gamma, backward),
 # tangent and second-order adjoint panels, 2 panel contractions, grad, hess partial,
-# hess final; 2 more block products when the chains take longer blocks than the panels
+# hess final
 LAUNCHES_PER_EVAL = 27
 # DRAM bytes of one k_eig_refine launch on this workload (ncu capture of the
 # current kernel: 32.93 MB read, 0 written; algorithmic: W read once, 32.8 MB)
@@ -258,8 +258,6 @@ def run_ours(args):
     with clk:
         P, ms, phases, res = measure(prec, args.steps, args.warmup, timing=True)
     clocks = clk.summary()
-    panel_bs, chain_bs = P.block_steps
-    launches = LAUNCHES_PER_EVAL + (2 if chain_bs != panel_bs else 0)
     value = world * 1000.0 / ms
 
     # ---- end to end through the host API (theta from host, results back to host) ----
@@ -344,11 +342,10 @@ def run_ours(args):
                                launch=({"block_steps": tuned[prec]["block_steps"],
                                         "panel_columns": tuned[prec]["panel_columns"],
                                         "autotune_table_ms": tuned[prec]["table"]}
-                                       if prec in tuned else "library defaults"),
-                               chain_block_steps=chain_bs),
+                                       if prec in tuned else "library defaults")),
                 "e2e": {"value": world * 1000.0 / e2e_ms, "unit": UNIT, "ms_per_step": e2e_ms,
                         "h2d_bytes_per_step": 8 * K, "d2h_bytes_per_step": 8 * (1 + K + K * K)},
-                "gpu_launches": launches * args.steps,
+                "gpu_launches": LAUNCHES_PER_EVAL * args.steps,
                 "clocks": clocks, "roofline": roof, "cpu_baseline": cpu,
                 "fp64_plain": fp64, "tr_solve": tr}
         print(json.dumps(line), flush=True)

@@ -108,17 +108,8 @@ qoc_status qoc_set_eig_method(qoc_problem* p, int method);
  * 1 selects one dependent step per time step.  Default when J >= 16: 8 for
  * QOC_FP64, 4 for QOC_MIXED_FP32 (the binary32 rounding of the block
  * propagator grows like sqrt(steps); 4 keeps the mixed results within 1e-6
- * of binary64); 1 when J < 16.  QOC_EINVAL otherwise.  The two vector
- * chains (state a_j, costate lambda_j) take their own, longer blocks: twice
- * `steps`, at most 8 and at most J (so equal to `steps` for 8 or 1); their
- * sweep step is one matrix-vector product whatever the block length. */
+ * of binary64); 1 when J < 16.  QOC_EINVAL otherwise. */
 qoc_status qoc_set_block_steps(qoc_problem* p, int steps);
-
-/* The block steps in use: *panel_steps for the tangent and second-order
- * adjoint panels (the value qoc_set_block_steps set), *chain_steps for the
- * state and costate chains.  Either pointer may be NULL.  QOC_EINVAL if p is
- * NULL. */
-qoc_status qoc_get_block_steps(const qoc_problem* p, int* panel_steps, int* chain_steps);
 
 /* Panel columns per CTA of the tangent and second-order adjoint sweeps
  * (1, 2 or 4; 0 restores the built-in choice: 2 for binary32 panels with

@@ -32,7 +32,7 @@ EXPORTS = [
     "qoc_last_error", "qoc_batch_create", "qoc_batch_set_graph", "qoc_batch_eval_grad_hess",
     "qoc_batch_eval_grad_hess_dev", "qoc_batch_destroy", "qoc_assemble_noalloc_scratch_doubles",
     "qoc_assemble_grad_hess_noalloc", "qoc_get_phase_times", "qoc_get_eig_stats",
-    "qoc_set_panel_columns", "qoc_get_block_steps",
+    "qoc_set_panel_columns",
 ]
 
 
@@ -80,7 +80,6 @@ def lib() -> C.CDLL:
         L.qoc_set_eig_method.argtypes = [C.c_void_p, C.c_int]
         L.qoc_set_block_steps.argtypes = [C.c_void_p, C.c_int]
         L.qoc_set_panel_columns.argtypes = [C.c_void_p, C.c_int]
-        L.qoc_get_block_steps.argtypes = [C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_int)]
         L.qoc_eval_J.argtypes = [C.c_void_p, _dp, _dp]
         L.qoc_eval_grad.argtypes = [C.c_void_p, _dp, _dp, _dp]
         L.qoc_eval_grad_hess.argtypes = [C.c_void_p, _dp, _dp, _dp, _dp]
@@ -185,13 +184,6 @@ def qoc_set_eig_method(h, method):
 
 def qoc_set_block_steps(h, steps):
     _check(lib().qoc_set_block_steps(C.c_void_p(h), int(steps)), "qoc_set_block_steps")
-
-
-def qoc_get_block_steps(h):
-    """(panel block steps, chain block steps) in use."""
-    bp, bc = C.c_int(0), C.c_int(0)
-    _check(lib().qoc_get_block_steps(C.c_void_p(h), C.byref(bp), C.byref(bc)), "qoc_get_block_steps")
-    return bp.value, bc.value
 
 
 def qoc_set_panel_columns(h, kc):
@@ -448,11 +440,6 @@ class Problem:
             qoc_set_block_steps(self.handle, block_steps)
         if panel_columns is not None:
             qoc_set_panel_columns(self.handle, panel_columns)
-
-    @property
-    def block_steps(self):
-        """(panel block steps, chain block steps) in use."""
-        return qoc_get_block_steps(self.handle)
 
     def eval_J(self, theta):
         return qoc_eval_J(self.handle, theta)

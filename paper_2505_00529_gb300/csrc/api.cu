@@ -75,7 +75,6 @@ struct qoc_problem {
   size_t mstride = 0, qstride = 0, gstride = 0;
   void *Mf = nullptr, *Mb = nullptr, *Qf = nullptr, *Wf = nullptr, *Gf = nullptr, *Qb = nullptr,
        *Wb = nullptr, *Gb = nullptr, *Xa = nullptr, *Xl = nullptr, *XS = nullptr, *Xmu = nullptr;
-  void *Mfc = nullptr, *Mbc = nullptr;  // block products of the vector chains (longer blocks)
   // pinned host staging
   double* hbuf = nullptr;
   size_t hbuf_len = 0;
@@ -151,28 +150,13 @@ qoc_status device_status(qoc_problem* p) {
   return QOC_ENUMERIC;
 }
 
-// Block steps of the two vector chains: twice the panels' block steps, at
-// most 8.  A chain step is one N x N matrix-vector product whatever the
-// block length, so longer blocks halve the chains' dependent steps; their own
-// block products (Mfc, Mbc) then sit beside the panels'.
-int chain_bs(const qoc_problem* p) {
-  if (p->bs < 2 || !p->Mfc) return p->bs;
-  const int c = p->bs >= 4 ? 8 : 2 * p->bs;
-  return c <= p->J ? c : p->bs;
-}
-
-void* chain_M(qoc_problem* p, int bwd) {
-  if (chain_bs(p) == p->bs) return bwd ? p->Mb : p->Mf;
-  return bwd ? p->Mbc : p->Mfc;
-}
-
 // The time-blocked evaluation (see block.cu): everything after the spectral
 // preparation, with the sequential sweeps taking J / bs dependent steps.
 BSweepArgs chain_sweep_args(qoc_problem* p, int bwd) {
   BSweepArgs a{};
   const int mixed = p->precision == QOC_MIXED_FP32;
-  a.N = p->N; a.K = 1; a.Kp = p->Kp; a.J = p->J; a.bs = chain_bs(p); a.kc = 1; a.backward = bwd;
-  a.M = reinterpret_cast<const unsigned char*>(chain_M(p, bwd)); a.mstride = p->mstride;
+  a.N = p->N; a.K = 1; a.Kp = p->Kp; a.J = p->J; a.bs = p->bs; a.kc = 1; a.backward = bwd;
+  a.M = reinterpret_cast<const unsigned char*>(bwd ? p->Mb : p->Mf); a.mstride = p->mstride;
   a.init = bwd ? p->lamJ : p->alpha; a.init_scale = 1.0;
   a.Xblk = bwd ? p->Xl : p->Xa; a.xblk_pairs = mixed;
   a.states = bwd ? p->l_hat : p->a_hat; a.status = p->status;
@@ -197,12 +181,11 @@ BSweepArgs panel_sweep_args(qoc_problem* p, int bwd) {
 
 
 // Time-blocked evaluation on three streams (order >= 1):
-//   chains (high priority): state block products, state chain + fill,
-//       terminal; costate block products, costate chain + fill
+//   chains (high priority): forward block products, state chain + fill,
+//       terminal; backward block products, costate chain + fill
 //   main: derivative preparation P~ (then X' for the Hessian), pointwise c_j,
 //       assembly
-//   panels (high priority), order 2: the panels' own block products when the
-//       chains take longer blocks; as soon as the state and P~ exist:
+//   panels (high priority), order 2: as soon as the state and P~ exist:
 //       p^ -> propagated sources -> tangent panel sweep; after the costate:
 //       y^, g -> contraction U -> second-order adjoint sources and sweep ->
 //       contraction V
@@ -210,8 +193,7 @@ BSweepArgs panel_sweep_args(qoc_problem* p, int bwd) {
 // the binary64 X' preparation instead of following them.
 qoc_status enqueue_blocked(qoc_problem* p, int order, double* out_dev) {
   cudaStream_t st = p->stream;
-  const int N = p->N, K = p->K, J = p->J, bs = p->bs, bsc = chain_bs(p);
-  const bool split = bsc != bs;
+  const int N = p->N, K = p->K, J = p->J, bs = p->bs;
   const int mixed = p->precision == QOC_MIXED_FP32 ? 1 : 0;
   const double thetaJ = (double)J * p->dt * p->mshift;
   const double2 kappa = cexpi_h(p->dt * p->mshift);
@@ -219,10 +201,9 @@ qoc_status enqueue_blocked(qoc_problem* p, int order, double* out_dev) {
   const void* Bsrc = mixed ? static_cast<const void*>(p->Bf) : static_cast<const void*>(p->B);
   if (order == 0) {
     p->sched = 0;
-    QOC_TRY(launch_block_delta(p->D, p->dstride, N, J, bsc, 0, mixed, chain_M(p, 0), p->mstride, st,
-                               p->ws[0]));
+    QOC_TRY(launch_block_delta(p->D, p->dstride, N, J, bs, 0, mixed, p->Mf, p->mstride, st, p->ws[0]));
     QOC_TRY(launch_bsweep(chain_sweep_args(p, 0), mixed, st));
-    QOC_TRY(launch_block_fill(p->D, p->dstride, N, J, bsc, 0, mixed, p->Xa, p->a_hat, st));
+    QOC_TRY(launch_block_fill(p->D, p->dstride, N, J, bs, 0, mixed, p->Xa, p->a_hat, st));
     QOC_TRY(launch_terminal(p->f, J, p->a_hat, mixed, p->beta, N, cexpi_h(thetaJ), p->w_f, p->w_t,
                             p->lamJ, p->scal + 0, nullptr, st));
     QOC_TRY(launch_drift(p->a_hat, mixed, N, J, p->scal + 1, st));
@@ -236,21 +217,17 @@ qoc_status enqueue_blocked(qoc_problem* p, int order, double* out_dev) {
   // ---- chains ----
   QOC_TRY(cudaStreamWaitEvent(cs, p->fork, 0));
   if (p->timing) cudaEventRecord(p->ev[10], cs);
-  QOC_TRY(launch_block_delta(p->D, p->dstride, N, J, bsc, 0, mixed, chain_M(p, 0), p->mstride, cs,
-                             p->ws[1]));
+  QOC_TRY(launch_block_delta(p->D, p->dstride, N, J, bs, 0, mixed, p->Mf, p->mstride, cs, p->ws[1]));
   QOC_TRY(launch_bsweep(chain_sweep_args(p, 0), mixed, cs));
-  QOC_TRY(launch_block_fill(p->D, p->dstride, N, J, bsc, 0, mixed, p->Xa, p->a_hat, cs));
+  QOC_TRY(launch_block_fill(p->D, p->dstride, N, J, bs, 0, mixed, p->Xa, p->a_hat, cs));
   QOC_TRY(launch_terminal(p->f, J, p->a_hat, mixed, p->beta, N, cexpi_h(thetaJ), p->w_f, p->w_t,
                           p->lamJ, p->scal + 0, nullptr, cs));
   QOC_TRY(cudaMemcpyAsync(out_dev, p->scal, sizeof(double), cudaMemcpyDeviceToDevice, cs));
   QOC_TRY(cudaEventRecord(p->ev_state, cs));
-  QOC_TRY(launch_block_delta(p->D, p->dstride, N, J, bsc, 1, mixed, chain_M(p, 1), p->mstride, cs,
-                             p->ws[1]));
+  // backward block products after the state: the panels start on the state
+  QOC_TRY(launch_block_delta(p->D, p->dstride, N, J, bs, 1, mixed, p->Mb, p->mstride, cs, p->ws[1]));
   QOC_TRY(launch_bsweep(chain_sweep_args(p, 1), mixed, cs));
-  QOC_TRY(launch_block_fill(p->D, p->dstride, N, J, bsc, 1, mixed, p->Xl, p->l_hat, cs));
-  // the panels' backward block products, needed only after the costate
-  if (split && order >= 2 && soa)
-    QOC_TRY(launch_block_delta(p->D, p->dstride, N, J, bs, 1, mixed, p->Mb, p->mstride, cs, p->ws[1]));
+  QOC_TRY(launch_block_fill(p->D, p->dstride, N, J, bs, 1, mixed, p->Xl, p->l_hat, cs));
   if (p->timing) cudaEventRecord(p->ev[11], cs);
   QOC_TRY(cudaEventRecord(p->join, cs));
   // ---- main: P~ ----
@@ -259,10 +236,6 @@ qoc_status enqueue_blocked(qoc_problem* p, int order, double* out_dev) {
   QOC_TRY(cudaEventRecord(p->ev_ptil, st));
   if (order >= 2) {
     // ---- panels ----
-    if (split) {
-      QOC_TRY(cudaStreamWaitEvent(ps, p->fork, 0));
-      QOC_TRY(launch_block_delta(p->D, p->dstride, N, J, bs, 0, mixed, p->Mf, p->mstride, ps, p->ws[2]));
-    }
     QOC_TRY(cudaStreamWaitEvent(ps, p->ev_ptil, 0));
     QOC_TRY(cudaStreamWaitEvent(ps, p->ev_state, 0));
     if (p->timing) cudaEventRecord(p->ev[12], ps);
@@ -606,12 +579,6 @@ qoc_status qoc_create_problem(int N, const double* H0, const double* M, const do
     ALLOC(p->Gb, nbp * p->gstride);
     ALLOC(p->Xa, 16 * nbp * N);
     ALLOC(p->Xl, 16 * nbp * N);
-    if (J >= 4) {
-      // the chains' blocks are at least 4 steps long when they differ from the panels'
-      const size_t nbc = ((size_t)J + 3) / 4 + 1;
-      ALLOC(p->Mfc, nbc * p->mstride);
-      ALLOC(p->Mbc, nbc * p->mstride);
-    }
     ALLOC(p->XS, cs * nbp * (size_t)K * N);
     ALLOC(p->Xmu, cs * nbp * (size_t)K * N);
   }
@@ -695,13 +662,6 @@ qoc_status qoc_set_block_steps(qoc_problem* p, int steps) {
   if (!p || steps < 1 || steps > 8 || (steps > 1 && p->J < steps)) return QOC_EINVAL;
   p->bs = steps;
   p->nblk = (p->J + steps - 1) / steps;
-  return QOC_OK;
-}
-
-qoc_status qoc_get_block_steps(const qoc_problem* p, int* panel_steps, int* chain_steps) {
-  if (!p) return QOC_EINVAL;
-  if (panel_steps) *panel_steps = p->bs;
-  if (chain_steps) *chain_steps = chain_bs(p);
   return QOC_OK;
 }
 
@@ -976,7 +936,7 @@ namespace {
 // one phase of problem i of the batch on stream s (see the header comment)
 qoc_status batch_phase(qoc_batch* b, int i, int phase, cudaStream_t s) {
   qoc_problem* p = b->P[i];
-  const int N = p->N, K = p->K, J = p->J, bs = p->bs, bsc = chain_bs(p), mixed = b->mixed;
+  const int N = p->N, K = p->K, J = p->J, bs = p->bs, mixed = b->mixed;
   double* out = b->out + b->ooff[i];
   const void* Bsrc = mixed ? static_cast<const void*>(p->Bf) : static_cast<const void*>(p->B);
   switch (phase) {
@@ -988,17 +948,11 @@ qoc_status batch_phase(qoc_batch* b, int i, int phase, cudaStream_t s) {
                          p->refine_sweeps, p->angle_tol, s, p->ws[0]));
       QOC_TRY(launch_prep(p->W, p->eig, p->M, N, J, p->dt, p->mshift, p->D, p->dstride, mixed ? 0 : 1,
                           PREP_D | PREP_P | PREP_X, p->Ptil, p->Xp, nullptr, p->status, s, p->ws[0]));
-      QOC_TRY(launch_block_delta(p->D, p->dstride, N, J, bsc, 0, mixed, chain_M(p, 0), p->mstride, s,
-                                 p->ws[0]));
-      QOC_TRY(launch_block_delta(p->D, p->dstride, N, J, bsc, 1, mixed, chain_M(p, 1), p->mstride, s,
-                                 p->ws[0]));
-      if (bsc != bs) {
-        QOC_TRY(launch_block_delta(p->D, p->dstride, N, J, bs, 0, mixed, p->Mf, p->mstride, s, p->ws[0]));
-        QOC_TRY(launch_block_delta(p->D, p->dstride, N, J, bs, 1, mixed, p->Mb, p->mstride, s, p->ws[0]));
-      }
+      QOC_TRY(launch_block_delta(p->D, p->dstride, N, J, bs, 0, mixed, p->Mf, p->mstride, s, p->ws[0]));
+      QOC_TRY(launch_block_delta(p->D, p->dstride, N, J, bs, 1, mixed, p->Mb, p->mstride, s, p->ws[0]));
       return QOC_OK;
     case 1: {
-      QOC_TRY(launch_block_fill(p->D, p->dstride, N, J, bsc, 0, mixed, p->Xa, p->a_hat, s));
+      QOC_TRY(launch_block_fill(p->D, p->dstride, N, J, bs, 0, mixed, p->Xa, p->a_hat, s));
       const double thetaJ = (double)J * p->dt * p->mshift;
       QOC_TRY(launch_terminal(p->f, J, p->a_hat, mixed, p->beta, N, cexpi_h(thetaJ), p->w_f, p->w_t,
                               p->lamJ, p->scal + 0, p->scal + 1, s));
@@ -1006,7 +960,7 @@ qoc_status batch_phase(qoc_batch* b, int i, int phase, cudaStream_t s) {
       return QOC_OK;
     }
     case 2:
-      QOC_TRY(launch_block_fill(p->D, p->dstride, N, J, bsc, 1, mixed, p->Xl, p->l_hat, s));
+      QOC_TRY(launch_block_fill(p->D, p->dstride, N, J, bs, 1, mixed, p->Xl, p->l_hat, s));
       QOC_TRY(launch_pointwise(p->W, p->Ptil, p->Xp, p->a_hat, p->l_hat, mixed, N, J,
                                cexpi_h(p->dt * p->mshift), p->p_hat, p->y_hat, p->g, p->c, PW_P | PW_Y | PW_C, s, p->ws[0]));
       QOC_TRY(launch_block_src(p->D, p->dstride, N, J, bs, 0, mixed, p->p_hat, p->y_hat, p->vstride,
