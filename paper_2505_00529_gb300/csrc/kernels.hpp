@@ -155,6 +155,9 @@ struct BSweepArgs {
   int* status;
 };
 cudaError_t launch_bsweep(const BSweepArgs& a, int mixed, cudaStream_t st);
+// whether launch_bsweep takes the warp-specialised binary32 sweep for `a`
+// (binary32, N <= 64, the CTA within the kernel's thread cap)
+bool bsweep_fast_ok(const BSweepArgs& a, int mixed);
 // one launch for many problems: CTAs cta_off[p] .. cta_off[p+1]-1 run problem p
 cudaError_t launch_bsweep_batch(const BSweepArgs* host_args, const BSweepArgs* dev_args,
                                 const int* dev_cta_off, int nprob, int total_ctas, int mixed,

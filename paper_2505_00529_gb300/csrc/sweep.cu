@@ -894,18 +894,39 @@ static bool launch_fast_batch(const BSweepArgs* host_args, const BSweepArgs* dev
   return true;
 }
 
+bool bsweep_fast_ok(const BSweepArgs& a, int mixed) {
+  if (!mixed || a.N > 64) return false;
+  int threads;
+  size_t stage, fixed, smem = 0;
+  if (a.N <= 32) {
+    fast_geometry<8>(a, threads, stage, fixed);
+    return fast_plan<8>(threads, stage, fixed, 1, smem) > 0;
+  }
+  fast_geometry<16>(a, threads, stage, fixed);
+  return fast_plan<16>(threads, stage, fixed, 1, smem) > 0;
+}
+
+// A batch whose problems all pass bsweep_fast_ok runs the warp-specialised
+// kernel (the entries beyond a problem's N are zeros, so the N <= 64 variant
+// gives an N <= 32 problem the same sums); any other batch the general one.
 cudaError_t launch_bsweep_batch(const BSweepArgs* host_args, const BSweepArgs* dev_args,
                                 const int* dev_cta_off, int nprob, int total_ctas, int mixed,
                                 cudaStream_t st) {
   if (mixed) {
     int nmax = 0;
-    for (int p = 0; p < nprob; ++p) nmax = host_args[p].N > nmax ? host_args[p].N : nmax;
+    bool fast = true;
+    for (int p = 0; p < nprob; ++p) {
+      nmax = host_args[p].N > nmax ? host_args[p].N : nmax;
+      fast = fast && bsweep_fast_ok(host_args[p], mixed);
+    }
     cudaError_t e = cudaSuccess;
-    if (nmax <= 32 && launch_fast_batch<8>(host_args, dev_args, dev_cta_off, nprob, total_ctas, st, e))
+    if (fast && nmax <= 32 &&
+        launch_fast_batch<8>(host_args, dev_args, dev_cta_off, nprob, total_ctas, st, e))
       return e;
-    if (nmax > 32 && nmax <= 64 &&
+    if (fast && nmax > 32 &&
         launch_fast_batch<16>(host_args, dev_args, dev_cta_off, nprob, total_ctas, st, e))
       return e;
+    if (fast) return cudaErrorInvalidConfiguration;   // the single-problem path would differ
     return launch_bb<true, 4>(host_args, dev_args, dev_cta_off, nprob, total_ctas, st);
   }
   return launch_bb<false, 4>(host_args, dev_args, dev_cta_off, nprob, total_ctas, st);
@@ -938,8 +959,10 @@ static cudaError_t launch_b(const BSweepArgs& a, cudaStream_t st) {
 cudaError_t launch_bsweep(const BSweepArgs& a, int mixed, cudaStream_t st) {
   if (mixed) {
     cudaError_t e = cudaSuccess;
-    if (a.N <= 32 && launch_fast<8>(a, st, e)) return e;
-    if (a.N > 32 && a.N <= 64 && launch_fast<16>(a, st, e)) return e;
+    if (bsweep_fast_ok(a, mixed)) {
+      if (a.N <= 32 ? launch_fast<8>(a, st, e) : launch_fast<16>(a, st, e)) return e;
+      return cudaErrorInvalidConfiguration;
+    }
     return launch_b<true, 4>(a, st);
   }
   return launch_b<false, 4>(a, st);
