@@ -50,6 +50,17 @@ struct StepGrid {
   unsigned char* gws = nullptr;
   size_t per_cta = 0;
 };
+// streaming multiprocessors of the current device (cached)
+inline int num_sms() {
+  static int nsm = 0;
+  if (!nsm) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || nsm < 1)
+      nsm = 1;
+  }
+  return nsm;
+}
 // `units` work units (steps or blocks), `need` bytes of storage each.
 inline bool step_grid(size_t need, int units, const StepSpace& ws, const void* fn, StepGrid& g) {
   if (need <= max_dyn_smem(fn)) {
@@ -61,13 +72,7 @@ inline bool step_grid(size_t need, int units, const StepSpace& ws, const void* f
   size_t n = ws.bytes / per;
   if (n < 1) return false;
   // no more CTAs than keep the slices L2-resident (96 MB), but at least one per SM
-  static int nsm = 0;
-  if (!nsm) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || nsm < 1)
-      nsm = 1;
-  }
+  const int nsm = num_sms();
   size_t cap = (size_t)(96u << 20) / per;
   if (cap < (size_t)nsm) cap = (size_t)nsm;
   if (n > cap) n = cap;
