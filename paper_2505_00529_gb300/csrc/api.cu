@@ -129,13 +129,11 @@ bool symmetric(const double* A, int N) {
 
 double2 cexpi_h(double x) { return make_double2(std::cos(x), std::sin(x)); }
 
-// panel columns per CTA: binary64 is throughput-limited per SM (one column
-// per CTA spreads the panel over K SMs); binary32 keeps two columns per CTA
-// up to N = 32 (8 warps) and one beyond
+// panel columns per CTA: one by default, which spreads a panel over K SMs
+// (binary64 is throughput-limited per SM; the binary32 sweep is latency-bound
+// per dependent step, which more columns per CTA only lengthen)
 int sweep_kc(const qoc_problem* p) {
-  if (p->kc > 0) return p->kc;
-  if (p->precision == QOC_FP64) return 1;
-  return p->N <= 32 ? 2 : 1;
+  return p->kc > 0 ? p->kc : 1;
 }
 
 qoc_status device_status(qoc_problem* p) {
