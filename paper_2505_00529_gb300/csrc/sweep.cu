@@ -501,14 +501,19 @@ __device__ __forceinline__ void bsweep_body(const BSweepArgs& a, const int cta, 
 // One producer warp keeps the ring full: an elected lane refills a slot with
 // bulk copies as soon as every consumer warp has released it on the slot's
 // "empty" barrier.  The consumer warps own the state: four lanes per row i,
-// lane r taking the terms q = r, r + 4, ...; each lane holds its M (and Q, B)
-// entries of the NEXT block in registers, loaded while the current block is
-// reduced, so that the dependent part of a block step is: read X (shared,
-// broadcast, padded runs of the permuted layout below), the FMA chain, two
-// shuffle rounds, the TwoSum update, write X, one named barrier.
+// lane r taking the terms q = r, r + 4, ...; each lane loads its M (and Q, B)
+// entries of the NEXT block into registers right after the current block's
+// X, so that the dependent part of a block step is: read X (shared,
+// broadcast), the FMA chain, two shuffle rounds, two additions, write X, one
+// named barrier.  NF = N when N is fixed at compile time (32 or 64: constant
+// offsets), else 0.
 // X layout per column: entry q at run (q mod 4), position (q div 4); runs are
 // XS = NQ + 2 float2 apart so the four runs a warp reads sit in different
 // banks.
+// State update: with the state an unevaluated pair (hi, lo), the increment d
+// is first added to lo (t = d + lo, one binary32 rounding of the order of the
+// increment's own) and TwoSum(hi, t) gives the new pair exactly; only hi
+// enters the next product.
 // ---------------------------------------------------------------------------
 template <int NQ>
 struct FastRegs {
@@ -517,26 +522,27 @@ struct FastRegs {
   float b[2];
 };
 
-template <int NQ>
-__device__ __forceinline__ void fast_load(FastRegs<NQ>& r, const BSweepArgs& a, const unsigned char* sp,
-                                          int it, int rsub, int i, int col, int kq, bool active) {
-  const int N = a.N;
-  const float2* Ms = reinterpret_cast<const float2*>(sp);
-  const int off = rsub * N + i;
+// the entries one lane needs of one block (zeros where q >= N or the lane is idle)
+template <int NQ, int NF>
+__device__ __forceinline__ void fast_load(FastRegs<NQ>& r, const unsigned char* sp, int Nrt, int mk,
+                                          uint32_t mbytes, uint32_t qbytes, bool has_q, int bl,
+                                          bool bwd, int Kp, int rsub, int i, int col, int kq,
+                                          bool active) {
+  const int N = NF ? NF : Nrt;
+  const float2* Ms = reinterpret_cast<const float2*>(sp) + rsub * N + i;
 #pragma unroll
   for (int k = 0; k < NQ; ++k)
-    r.m[k] = (active && k < kq) ? Ms[off + 4 * k * N] : make_float2(0.f, 0.f);
-  if (a.Q) {
-    const int t0 = it * a.bs, bl = min(a.bs, a.J - t0);
-    const float2* Qs = reinterpret_cast<const float2*>(sp + a.mstride);
-    const float* Bs = reinterpret_cast<const float*>(sp + a.mstride + a.qstride);
+    r.m[k] = (active && k < kq) ? Ms[NF ? 4 * k * NF : k * mk] : make_float2(0.f, 0.f);
+  if (has_q) {
+    const float2* Qs = reinterpret_cast<const float2*>(sp + mbytes);
+    const float* Bs = reinterpret_cast<const float*>(sp + mbytes + qbytes);
 #pragma unroll
     for (int u = 0; u < 2; ++u) {
       const int mm = rsub + 4 * u;
       if (active && mm < bl) {
-        const int lr = a.backward ? bl - 1 - mm : mm;
+        const int lr = bwd ? bl - 1 - mm : mm;
         r.q[u] = Qs[mm * N + i];
-        r.b[u] = Bs[lr * a.Kp + col];
+        r.b[u] = Bs[lr * Kp + col];
       } else {
         r.q[u] = make_float2(0.f, 0.f);
         r.b[u] = 0.f;
@@ -545,19 +551,22 @@ __device__ __forceinline__ void fast_load(FastRegs<NQ>& r, const BSweepArgs& a, 
   }
 }
 
-template <int NQ>
+template <int NQ, int NF>
 __device__ __forceinline__ void bsweep_fast_body(const BSweepArgs& a, const int cta, const int nstage,
                                                  unsigned char* smem) {
   constexpr int RS = 4, RPW = 8, XS = NQ + 2;
-  const int N = a.N, kc = a.kc, J = a.J, bs = a.bs;
+  const int N = NF ? NF : a.N;
+  const int kc = a.kc, J = a.J, bs = a.bs, K = a.K, Kp = a.Kp;
+  const bool bwd = a.backward != 0, has_q = a.Q != nullptr, has_b = a.Brow != nullptr;
+  const bool pairs = a.xblk_pairs != 0;
   const int nblk = (J + bs - 1) / bs;
   const int WPC = (N + RPW - 1) / RPW;
   const int ncw = WPC * kc;                       // consumer warps
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const uint32_t mbytes = (uint32_t)a.mstride;
-  const uint32_t qbytes = a.Q ? (uint32_t)a.qstride : 0u;
-  const uint32_t browb = (uint32_t)(sizeof(float) * a.Kp);
-  const uint32_t stage = mbytes + qbytes + (a.Brow ? browb * bs : 0u);
+  const uint32_t qbytes = has_q ? (uint32_t)a.qstride : 0u;
+  const uint32_t browb = (uint32_t)(sizeof(float) * Kp);
+  const uint32_t stage = mbytes + qbytes + (has_b ? browb * bs : 0u);
   unsigned char* ring = smem;
   float2* Xs = reinterpret_cast<float2*>(ring + (size_t)nstage * stage);   // [2][kc][RS][XS]
   const int xbuf = kc * RS * XS;
@@ -579,7 +588,10 @@ __device__ __forceinline__ void bsweep_fast_body(const BSweepArgs& a, const int 
 
   if (warp == ncw) {   // ---- producer ----
     if (lane != 0) return;
+    const unsigned char* gM = a.M;
+    const unsigned char* gQ = a.Q;
     const unsigned char* gB = reinterpret_cast<const unsigned char*>(a.Brow);
+    const size_t ms = a.mstride, qs = a.qstride;
     int s = 0, round = 0, issued = 0;
     for (int it = 0; it < nblk; ++it) {
       if (*abort_flag) break;
@@ -588,14 +600,14 @@ __device__ __forceinline__ void bsweep_fast_body(const BSweepArgs& a, const int 
         break;
       }
       const int t0 = it * bs, bl = min(bs, J - t0);
-      const int row0 = a.backward ? J - t0 - bl : t0;
-      const uint32_t qb = qbytes ? (((uint32_t)(bl * N) * 8u + 15u) & ~15u) : 0u;
-      const uint32_t bb = a.Brow ? browb * (uint32_t)bl : 0u;
+      const int row0 = bwd ? J - t0 - bl : t0;
+      const uint32_t qb = has_q ? (((uint32_t)(bl * N) * 8u + 15u) & ~15u) : 0u;
+      const uint32_t bb = has_b ? browb * (uint32_t)bl : 0u;
       unsigned char* dst = ring + (size_t)s * stage;
       fence_proxy_async_smem();
       mbar_arrive_expect_tx(&full[s], mbytes + qb + bb);
-      bulk_g2s(dst, a.M + (size_t)it * a.mstride, mbytes, &full[s]);
-      if (qb) bulk_g2s(dst + mbytes, a.Q + (size_t)it * a.qstride, qb, &full[s]);
+      bulk_g2s(dst, gM + (size_t)it * ms, mbytes, &full[s]);
+      if (qb) bulk_g2s(dst + mbytes, gQ + (size_t)it * qs, qb, &full[s]);
       if (bb) bulk_g2s(dst + mbytes + qbytes, gB + (size_t)row0 * browb, bb, &full[s]);
       issued = it + 1;
       if (++s == nstage) { s = 0; ++round; }
@@ -612,9 +624,10 @@ __device__ __forceinline__ void bsweep_fast_body(const BSweepArgs& a, const int 
   const int rsub = lane & 3;
   const int i = rb * RPW + (lane >> 2);
   const int col = cta * kc + l;
-  const bool active = col < a.K && i < N;
+  const bool active = col < K && i < N;
   const bool owner = active && rsub == 0;
   const int kq = (N - rsub + 3) >> 2;             // terms q = rsub + 4k < N
+  const int mk = 4 * N;                           // float2 stride between a lane's terms
   const int nthr = 32 * ncw;
   const int xw = (i & 3) * XS + (i >> 2);         // this row's entry in the permuted layout
   float2* Xl = Xs + l * RS * XS;
@@ -628,19 +641,17 @@ __device__ __forceinline__ void bsweep_fast_body(const BSweepArgs& a, const int 
   }
   float hx = (float)x0.x, hy = (float)x0.y;
   float lx = (float)(x0.x - (double)hx), ly = (float)(x0.y - (double)hy);
-  const size_t xb_stride = (size_t)a.K * N;
-  size_t xb_off = (size_t)col * N + i;
-  auto store_blk = [&]() {
-    if (a.xblk_pairs) reinterpret_cast<float4*>(a.Xblk)[xb_off] = make_float4(hx, hy, lx, ly);
-    else reinterpret_cast<float2*>(a.Xblk)[xb_off] = make_float2(hx, hy);
-  };
+  const size_t xb_stride = (size_t)K * N;
+  float4* xb4 = reinterpret_cast<float4*>(a.Xblk) + (size_t)col * N + i;
+  float2* xb2 = reinterpret_cast<float2*>(a.Xblk) + (size_t)col * N + i;
   if (owner) {
     Xl[xw] = make_float2(hx, hy);
-    store_blk();
+    if (pairs) *xb4 = make_float4(hx, hy, lx, ly);
+    else *xb2 = make_float2(hx, hy);
   }
 
   // Every consumer takes the same exit decision: the OR, over the consumers,
-  // of a failed wait or a raised flag, formed by the step's barrier itself.
+  // of a failed wait, formed by the step's barrier itself.
   FastRegs<NQ> ra, rb2;
   int s = 0;
   uint32_t par = 0;
@@ -649,18 +660,33 @@ __device__ __forceinline__ void bsweep_fast_body(const BSweepArgs& a, const int 
     bad = true;
     *abort_flag = 1;
   }
-  fast_load<NQ>(ra, a, ring, 0, rsub, i, col, kq, active);
-  bool ok = !named_barrier_or(1, nthr, bad || *abort_flag != 0);
+  fast_load<NQ, NF>(ra, ring, N, mk, mbytes, qbytes, has_q, min(bs, J), bwd, Kp, rsub, i, col, kq,
+                    active);
+  bool ok = !named_barrier_or(1, nthr, bad);
 
   int cur = 0;
   // one block step with `r` holding this block's data; `nx` receives the next block's
   auto step = [&](int it, const FastRegs<NQ>& r, FastRegs<NQ>& nx) -> bool {
-    // release this block's slot: its entries were loaded before the last barrier
+    int s1 = s + 1;
+    uint32_t par1 = par;
+    if (s1 == nstage) { s1 = 0; par1 ^= 1u; }
+    const bool more = it + 1 < nblk;
+    // release this block's slot (its entries were loaded before the last
+    // barrier) and make sure the next block has landed
     if (lane == 0) mbar_arrive(&empty[s]);
+    if (more && !mbar_wait_or_flag(&full[s1], par1, abort_flag)) {
+      bad = true;
+      *abort_flag = 1;
+    }
     const float4* xp = Xr + cur * (xbuf / 2);
     float4 xv[NQ / 2];
 #pragma unroll
     for (int k = 0; k < NQ / 2; ++k) xv[k] = xp[k];
+    if (more) {
+      const int t1 = (it + 1) * bs;
+      fast_load<NQ, NF>(nx, ring + (size_t)s1 * stage, N, mk, mbytes, qbytes, has_q, min(bs, J - t1),
+                        bwd, Kp, rsub, i, col, kq, active);
+    }
     float ax[4] = {0.f, 0.f, 0.f, 0.f}, ay[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
     for (int k = 0; k < NQ; ++k) {
@@ -671,22 +697,11 @@ __device__ __forceinline__ void bsweep_fast_body(const BSweepArgs& a, const int 
       ax[k & 3] = fmaf(-r.m[k].y, xi, ax[k & 3]);
       ay[k & 3] = fmaf(r.m[k].y, xr, ay[k & 3]);
     }
-    if (a.Q) {
+    if (has_q) {
       ax[0] = fmaf(r.q[0].x, r.b[0], ax[0]);
       ay[0] = fmaf(r.q[0].y, r.b[0], ay[0]);
       ax[1] = fmaf(r.q[1].x, r.b[1], ax[1]);
       ay[1] = fmaf(r.q[1].y, r.b[1], ay[1]);
-    }
-    // next block's data (independent of X)
-    int s1 = s + 1;
-    uint32_t par1 = par;
-    if (s1 == nstage) { s1 = 0; par1 ^= 1u; }
-    if (it + 1 < nblk) {
-      if (!mbar_wait_or_flag(&full[s1], par1, abort_flag)) {
-        bad = true;
-        *abort_flag = 1;
-      }
-      fast_load<NQ>(nx, a, ring + (size_t)s1 * stage, it + 1, rsub, i, col, kq, active);
     }
     float sx = (ax[0] + ax[1]) + (ax[2] + ax[3]);
     float sy = (ay[0] + ay[1]) + (ay[2] + ay[3]);
@@ -695,15 +710,17 @@ __device__ __forceinline__ void bsweep_fast_body(const BSweepArgs& a, const int 
     sx += __shfl_xor_sync(0xffffffffu, sx, 2);
     sy += __shfl_xor_sync(0xffffffffu, sy, 2);
     if (owner) {
-      pair_add(hx, lx, sx);
-      pair_add(hy, ly, sy);
+      two_sum(hx, __fadd_rn(sx, lx), hx, lx);
+      two_sum(hy, __fadd_rn(sy, ly), hy, ly);
       Xl[(cur ^ 1) * xbuf + xw] = make_float2(hx, hy);
-      if (it + 1 < nblk) {
-        xb_off += xb_stride;
-        store_blk();
+      if (more) {
+        xb4 += xb_stride;
+        xb2 += xb_stride;
+        if (pairs) *xb4 = make_float4(hx, hy, lx, ly);
+        else *xb2 = make_float2(hx, hy);
       }
     }
-    const bool stop = named_barrier_or(1, nthr, bad || *abort_flag != 0);
+    const bool stop = named_barrier_or(1, nthr, bad);
     cur ^= 1;
     s = s1;
     par = par1;
@@ -724,7 +741,7 @@ __device__ __forceinline__ void bsweep_fast_body(const BSweepArgs& a, const int 
   if (owner) {
     if (a.final_out) a.final_out[(size_t)col * N + i] = make_double2(fx, fy);
     if (a.states) {   // final state of a vector chain: a_J forward, lambda_0 backward
-      const size_t row = (size_t)(a.backward ? 0 : J) * N + i;
+      const size_t row = (size_t)(bwd ? 0 : J) * N + i;
       reinterpret_cast<float4*>(a.states)[row] = make_float4(hx, hy, lx, ly);
     }
     if (!(isfinite(fx) && isfinite(fy))) raise_status(a.status, DEV_NONFINITE);
@@ -734,10 +751,10 @@ __device__ __forceinline__ void bsweep_fast_body(const BSweepArgs& a, const int 
 // thread cap of the warp-specialised kernels: room for two blocks of entries in registers
 template <int NQ> struct FastCap { static constexpr int threads = NQ <= 8 ? 512 : 384; };
 
-template <int NQ>
+template <int NQ, int NF>
 __global__ void __launch_bounds__(FastCap<NQ>::threads) k_bsweep_fast(const BSweepArgs a, const int nstage) {
   extern __shared__ __align__(128) unsigned char smem[];
-  bsweep_fast_body<NQ>(a, blockIdx.x, nstage, smem);
+  bsweep_fast_body<NQ, NF>(a, blockIdx.x, nstage, smem);
 }
 
 template <int NQ>
@@ -751,7 +768,7 @@ __global__ void __launch_bounds__(FastCap<NQ>::threads) k_bsweep_fast_batch(cons
     if (cta_off[mid] <= (int)blockIdx.x) lo = mid; else hi = mid;
   }
   const BSweepArgs a = args[lo];
-  bsweep_fast_body<NQ>(a, (int)blockIdx.x - cta_off[lo], nstage, smem);
+  bsweep_fast_body<NQ, 0>(a, (int)blockIdx.x - cta_off[lo], nstage, smem);
 }
 
 template <bool MIX, int RS, bool DIRECT>
@@ -866,8 +883,13 @@ static bool launch_fast(const BSweepArgs& a, cudaStream_t st, cudaError_t& err) 
   const int grid = (a.K + a.kc - 1) / a.kc;
   const int ns = fast_plan<NQ>(threads, stage, fixed, grid, smem);
   if (!ns) return false;
-  set_max_smem((const void*)k_bsweep_fast<NQ>);
-  k_bsweep_fast<NQ><<<grid, threads, smem, st>>>(a, ns);
+  if (a.N == 4 * NQ) {   // N = 32 or 64: offsets fixed at compile time
+    set_max_smem((const void*)k_bsweep_fast<NQ, 4 * NQ>);
+    k_bsweep_fast<NQ, 4 * NQ><<<grid, threads, smem, st>>>(a, ns);
+  } else {
+    set_max_smem((const void*)k_bsweep_fast<NQ, 0>);
+    k_bsweep_fast<NQ, 0><<<grid, threads, smem, st>>>(a, ns);
+  }
   err = cudaGetLastError();
   return true;
 }
