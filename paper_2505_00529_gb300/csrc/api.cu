@@ -915,16 +915,18 @@ struct qoc_batch {
   cudaStream_t st = nullptr;
   bool own_stream = false;
   std::vector<cudaEvent_t> ev;         // per problem: 5 phase events; then 5 batch events
-  // the four batched sweeps, each split into the problems taking the
-  // warp-specialised binary32 sweep (group 0) and the rest (group 1), the
-  // same choice as a single evaluation makes: index 2 * sweep + group
-  std::vector<BSweepArgs> hargs[8];
-  std::vector<int> hoff[8];
-  BSweepArgs* dargs[8] = {};
-  int* doff[8] = {};
-  int nargs[8] = {}, total[8] = {};
-  cudaStream_t aux = nullptr;          // group 1 runs here, beside group 0
-  cudaEvent_t gev[8] = {};             // per sweep: fork and join of the two groups
+  // the four batched sweeps, each split into groups by the sweep kernel a
+  // single evaluation of the problem takes (bsweep_variant), one launch per
+  // group: index kSweepVariants * sweep + variant
+  static constexpr int NG = 4 * kSweepVariants;
+  std::vector<BSweepArgs> hargs[NG];
+  std::vector<int> hoff[NG];
+  BSweepArgs* dargs[NG] = {};
+  int* doff[NG] = {};
+  int nargs[NG] = {}, total[NG] = {};
+  cudaStream_t aux[kSweepVariants] = {};   // each group's stream (0 is the batch stream)
+  cudaEvent_t fork[4] = {};                // per sweep: fork of the groups
+  cudaEvent_t gjoin[NG] = {};              // per group: its join
   std::vector<size_t> toff, ooff;
   size_t ntheta = 0, nout = 0;
   double *theta = nullptr, *out = nullptr, *hbuf = nullptr;
@@ -1004,22 +1006,27 @@ qoc_status enqueue_batch(qoc_batch* b) {
     // join, then the batched sweep of this stage
     for (int i = 0; i < n; ++i) QOC_TRY(cudaStreamWaitEvent(b->st, b->ev[5 * (size_t)i + phase], 0));
     if (phase < 4) {
-      const int g0 = 2 * phase, g1 = g0 + 1;
-      const bool both = b->nargs[g0] > 0 && b->nargs[g1] > 0;
-      if (both) {
-        QOC_TRY(cudaEventRecord(b->gev[g0], b->st));
-        QOC_TRY(cudaStreamWaitEvent(b->aux, b->gev[g0], 0));
-      }
-      for (int g : {g0, g1}) {
+      // one launch per kernel group, the groups side by side on their streams
+      const int g0 = kSweepVariants * phase;
+      bool forked = false;
+      for (int v = 0; v < kSweepVariants; ++v) {
+        const int g = g0 + v;
         if (!b->nargs[g]) continue;
-        cudaStream_t s = (both && g == g1) ? b->aux : b->st;
+        cudaStream_t s = b->st;
+        if (v > 0) {
+          if (!forked) {
+            QOC_TRY(cudaEventRecord(b->fork[phase], b->st));
+            forked = true;
+          }
+          s = b->aux[v];
+          QOC_TRY(cudaStreamWaitEvent(s, b->fork[phase], 0));
+        }
         QOC_TRY(launch_bsweep_batch(b->hargs[g].data(), b->dargs[g], b->doff[g], b->nargs[g],
                                     b->total[g], b->mixed, s));
+        if (v > 0) QOC_TRY(cudaEventRecord(b->gjoin[g], s));
       }
-      if (both) {
-        QOC_TRY(cudaEventRecord(b->gev[g1], b->aux));
-        QOC_TRY(cudaStreamWaitEvent(b->st, b->gev[g1], 0));
-      }
+      for (int v = 1; v < kSweepVariants; ++v)
+        if (b->nargs[g0 + v]) QOC_TRY(cudaStreamWaitEvent(b->st, b->gjoin[g0 + v], 0));
       QOC_TRY(cudaEventRecord(bev[phase + 1], b->st));
     }
   }
@@ -1035,15 +1042,19 @@ void qoc_batch_destroy(qoc_batch* b) {
   if (b->st) cudaStreamSynchronize(b->st);
   if (b->exec) cudaGraphExecDestroy(b->exec);
   if (b->graph) cudaGraphDestroy(b->graph);
-  if (b->aux) cudaStreamSynchronize(b->aux);
+  for (auto a : b->aux)
+    if (a) cudaStreamSynchronize(a);
   for (auto e : b->ev)
     if (e) cudaEventDestroy(e);
-  for (int k = 0; k < 8; ++k) {
+  for (int k = 0; k < qoc_batch::NG; ++k) {
     cudaFree(b->dargs[k]);
     cudaFree(b->doff[k]);
-    if (b->gev[k]) cudaEventDestroy(b->gev[k]);
+    if (b->gjoin[k]) cudaEventDestroy(b->gjoin[k]);
   }
-  if (b->aux) cudaStreamDestroy(b->aux);
+  for (auto e : b->fork)
+    if (e) cudaEventDestroy(e);
+  for (auto a : b->aux)
+    if (a) cudaStreamDestroy(a);
   cudaFree(b->theta);
   cudaFree(b->out);
   if (b->hbuf) cudaFreeHost(b->hbuf);
@@ -1077,9 +1088,12 @@ qoc_status qoc_batch_create(qoc_problem* const* problems, int n, void* cuda_stre
   b->ev.assign(5 * (size_t)n + 5, nullptr);
   for (auto& ev : b->ev)
     if ((e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming)) != cudaSuccess) return fail(e);
-  for (auto& ev : b->gev)
+  for (auto& ev : b->gjoin)
     if ((e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming)) != cudaSuccess) return fail(e);
-  if ((e = cudaStreamCreateWithFlags(&b->aux, cudaStreamNonBlocking)) != cudaSuccess) return fail(e);
+  for (auto& ev : b->fork)
+    if ((e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming)) != cudaSuccess) return fail(e);
+  for (int v = 1; v < kSweepVariants; ++v)
+    if ((e = cudaStreamCreateWithFlags(&b->aux[v], cudaStreamNonBlocking)) != cudaSuccess) return fail(e);
   for (int i = 0; i < n; ++i) {
     qoc_problem* p = problems[i];
     b->toff.push_back(b->ntheta);
@@ -1091,13 +1105,13 @@ qoc_status qoc_batch_create(qoc_problem* const* problems, int n, void* cuda_stre
                            panel_sweep_args(p, 1)};
     for (int k = 0; k < 4; ++k) {
       if (k == 3 && p->hess_method != QOC_HESS_SECOND_ORDER_ADJOINT) continue;
-      const int g = 2 * k + (bsweep_fast_ok(args[k], b->mixed) ? 0 : 1);
+      const int g = kSweepVariants * k + bsweep_variant(args[k], b->mixed);
       b->hoff[g].push_back(b->total[g]);
       b->hargs[g].push_back(args[k]);
       b->total[g] += (args[k].K + args[k].kc - 1) / args[k].kc;
     }
   }
-  for (int k = 0; k < 8; ++k) {
+  for (int k = 0; k < qoc_batch::NG; ++k) {
     b->nargs[k] = (int)b->hargs[k].size();
     b->hoff[k].push_back(b->total[k]);
     if (!b->nargs[k]) continue;

@@ -160,9 +160,11 @@ struct BSweepArgs {
   int* status;
 };
 cudaError_t launch_bsweep(const BSweepArgs& a, int mixed, cudaStream_t st);
-// whether launch_bsweep takes the warp-specialised binary32 sweep for `a`
-// (binary32, N <= 64, the CTA within the kernel's thread cap)
-bool bsweep_fast_ok(const BSweepArgs& a, int mixed);
+// which sweep kernel launch_bsweep takes for `a`: 0 the general one, 1 or 2
+// a warp-specialised binary32 one (N <= 32 / N <= 64, CTA within its thread
+// cap); kernels differ in the order of their sums
+int bsweep_variant(const BSweepArgs& a, int mixed);
+constexpr int kSweepVariants = 3;
 // one launch for many problems: CTAs cta_off[p] .. cta_off[p+1]-1 run problem p
 cudaError_t launch_bsweep_batch(const BSweepArgs* host_args, const BSweepArgs* dev_args,
                                 const int* dev_cta_off, int nprob, int total_ctas, int mixed,

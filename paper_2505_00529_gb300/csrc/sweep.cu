@@ -497,34 +497,38 @@ __device__ __forceinline__ void bsweep_body(const BSweepArgs& a, const int cta, 
 }
 
 // ---------------------------------------------------------------------------
-// Blocked sweep with binary32 increments for N <= 4 NQ, warp-specialised.
+// Blocked sweep with binary32 increments for N <= RS * NQ, warp-specialised.
 // One producer warp keeps the ring full: an elected lane refills a slot with
 // bulk copies as soon as every consumer warp has released it on the slot's
-// "empty" barrier.  The consumer warps own the state: four lanes per row i,
-// lane r taking the terms q = r, r + 4, ...; each lane loads its M (and Q, B)
+// "empty" barrier.  The consumer warps own the state: RS lanes per row i,
+// lane r taking the terms q = r, r + RS, ...  A warp covers 32 / RS rows with
+// r in the high lane bits, so each half-warp reads 16 (RS = 2) or 8 (RS = 4)
+// consecutive rows of M: its shared-memory loads are free of (RS = 2) or have
+// at most two-way (RS = 4) bank conflicts.  Each lane loads its M (and Q, B)
 // entries of the NEXT block into registers right after the current block's
 // X, so that the dependent part of a block step is: read X (shared,
-// broadcast), the FMA chain, two shuffle rounds, two additions, write X, one
-// named barrier.  NF = N when N is fixed at compile time (32 or 64: constant
-// offsets), else 0.
-// X layout per column: entry q at run (q mod 4), position (q div 4); runs are
-// XS = NQ + 2 float2 apart so the four runs a warp reads sit in different
+// broadcast), the FMA chain, log2(RS) shuffle rounds, two additions, write
+// X, one named barrier.  NF = N when N = RS * NQ is fixed at compile time
+// (constant offsets), else 0.
+// X layout per column: entry q at run (q mod RS), position (q div RS); runs
+// are XS = NQ + 2 float2 apart so the runs a warp reads sit in different
 // banks.
 // State update: with the state an unevaluated pair (hi, lo), the increment d
 // is first added to lo (t = d + lo, one binary32 rounding of the order of the
 // increment's own) and TwoSum(hi, t) gives the new pair exactly; only hi
 // enters the next product.
 // ---------------------------------------------------------------------------
-template <int NQ>
+template <int RS, int NQ>
 struct FastRegs {
+  static constexpr int UQ = (8 + RS - 1) / RS;   // source terms per lane (bs <= 8)
   float2 m[NQ];
-  float2 q[2];
-  float b[2];
+  float2 q[UQ];
+  float b[UQ];
 };
 
 // the entries one lane needs of one block (zeros where q >= N or the lane is idle)
-template <int NQ, int NF>
-__device__ __forceinline__ void fast_load(FastRegs<NQ>& r, const unsigned char* sp, int Nrt, int mk,
+template <int RS, int NQ, int NF>
+__device__ __forceinline__ void fast_load(FastRegs<RS, NQ>& r, const unsigned char* sp, int Nrt,
                                           uint32_t mbytes, uint32_t qbytes, bool has_q, int bl,
                                           bool bwd, int Kp, int rsub, int i, int col, int kq,
                                           bool active) {
@@ -532,13 +536,13 @@ __device__ __forceinline__ void fast_load(FastRegs<NQ>& r, const unsigned char* 
   const float2* Ms = reinterpret_cast<const float2*>(sp) + rsub * N + i;
 #pragma unroll
   for (int k = 0; k < NQ; ++k)
-    r.m[k] = (active && k < kq) ? Ms[NF ? 4 * k * NF : k * mk] : make_float2(0.f, 0.f);
+    r.m[k] = (active && k < kq) ? Ms[RS * k * N] : make_float2(0.f, 0.f);
   if (has_q) {
     const float2* Qs = reinterpret_cast<const float2*>(sp + mbytes);
     const float* Bs = reinterpret_cast<const float*>(sp + mbytes + qbytes);
 #pragma unroll
-    for (int u = 0; u < 2; ++u) {
-      const int mm = rsub + 4 * u;
+    for (int u = 0; u < FastRegs<RS, NQ>::UQ; ++u) {
+      const int mm = rsub + RS * u;
       if (active && mm < bl) {
         const int lr = bwd ? bl - 1 - mm : mm;
         r.q[u] = Qs[mm * N + i];
@@ -551,10 +555,10 @@ __device__ __forceinline__ void fast_load(FastRegs<NQ>& r, const unsigned char* 
   }
 }
 
-template <int NQ, int NF>
+template <int RS, int NQ, int NF>
 __device__ __forceinline__ void bsweep_fast_body(const BSweepArgs& a, const int cta, const int nstage,
                                                  unsigned char* smem) {
-  constexpr int RS = 4, RPW = 8, XS = NQ + 2;
+  constexpr int RPW = 32 / RS, XS = NQ + 2, UQ = FastRegs<RS, NQ>::UQ;
   const int N = NF ? NF : a.N;
   const int kc = a.kc, J = a.J, bs = a.bs, K = a.K, Kp = a.Kp;
   const bool bwd = a.backward != 0, has_q = a.Q != nullptr, has_b = a.Brow != nullptr;
@@ -621,15 +625,14 @@ __device__ __forceinline__ void bsweep_fast_body(const BSweepArgs& a, const int 
 
   // ---- consumers ----
   const int l = warp / WPC, rb = warp % WPC;
-  const int rsub = lane & 3;
-  const int i = rb * RPW + (lane >> 2);
+  const int rsub = lane / RPW;
+  const int i = rb * RPW + (lane % RPW);
   const int col = cta * kc + l;
   const bool active = col < K && i < N;
   const bool owner = active && rsub == 0;
-  const int kq = (N - rsub + 3) >> 2;             // terms q = rsub + 4k < N
-  const int mk = 4 * N;                           // float2 stride between a lane's terms
+  const int kq = (N - rsub + RS - 1) / RS;        // terms q = rsub + RS k < N
   const int nthr = 32 * ncw;
-  const int xw = (i & 3) * XS + (i >> 2);         // this row's entry in the permuted layout
+  const int xw = (i % RS) * XS + i / RS;          // this row's entry in the permuted layout
   float2* Xl = Xs + l * RS * XS;
   const float4* Xr = reinterpret_cast<const float4*>(Xl + rsub * XS);
 
@@ -652,7 +655,7 @@ __device__ __forceinline__ void bsweep_fast_body(const BSweepArgs& a, const int 
 
   // Every consumer takes the same exit decision: the OR, over the consumers,
   // of a failed wait, formed by the step's barrier itself.
-  FastRegs<NQ> ra, rb2;
+  FastRegs<RS, NQ> ra, rb2;
   int s = 0;
   uint32_t par = 0;
   bool bad = false;
@@ -660,32 +663,32 @@ __device__ __forceinline__ void bsweep_fast_body(const BSweepArgs& a, const int 
     bad = true;
     *abort_flag = 1;
   }
-  fast_load<NQ, NF>(ra, ring, N, mk, mbytes, qbytes, has_q, min(bs, J), bwd, Kp, rsub, i, col, kq,
-                    active);
+  fast_load<RS, NQ, NF>(ra, ring, N, mbytes, qbytes, has_q, min(bs, J), bwd, Kp, rsub, i, col, kq,
+                        active);
   bool ok = !named_barrier_or(1, nthr, bad);
 
   int cur = 0;
   // one block step with `r` holding this block's data; `nx` receives the next block's
-  auto step = [&](int it, const FastRegs<NQ>& r, FastRegs<NQ>& nx) -> bool {
+  auto step = [&](int it, const FastRegs<RS, NQ>& r, FastRegs<RS, NQ>& nx) -> bool {
     int s1 = s + 1;
     uint32_t par1 = par;
     if (s1 == nstage) { s1 = 0; par1 ^= 1u; }
     const bool more = it + 1 < nblk;
-    // release this block's slot (its entries were loaded before the last
-    // barrier) and make sure the next block has landed
+    // release this block's slot: its entries were loaded before the last barrier
     if (lane == 0) mbar_arrive(&empty[s]);
-    if (more && !mbar_wait_or_flag(&full[s1], par1, abort_flag)) {
-      bad = true;
-      *abort_flag = 1;
-    }
     const float4* xp = Xr + cur * (xbuf / 2);
     float4 xv[NQ / 2];
 #pragma unroll
     for (int k = 0; k < NQ / 2; ++k) xv[k] = xp[k];
+    // the next block (independent of X): landed, then into registers
     if (more) {
+      if (!mbar_wait_or_flag(&full[s1], par1, abort_flag)) {
+        bad = true;
+        *abort_flag = 1;
+      }
       const int t1 = (it + 1) * bs;
-      fast_load<NQ, NF>(nx, ring + (size_t)s1 * stage, N, mk, mbytes, qbytes, has_q, min(bs, J - t1),
-                        bwd, Kp, rsub, i, col, kq, active);
+      fast_load<RS, NQ, NF>(nx, ring + (size_t)s1 * stage, N, mbytes, qbytes, has_q, min(bs, J - t1),
+                            bwd, Kp, rsub, i, col, kq, active);
     }
     float ax[4] = {0.f, 0.f, 0.f, 0.f}, ay[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
@@ -698,17 +701,19 @@ __device__ __forceinline__ void bsweep_fast_body(const BSweepArgs& a, const int 
       ay[k & 3] = fmaf(r.m[k].y, xr, ay[k & 3]);
     }
     if (has_q) {
-      ax[0] = fmaf(r.q[0].x, r.b[0], ax[0]);
-      ay[0] = fmaf(r.q[0].y, r.b[0], ay[0]);
-      ax[1] = fmaf(r.q[1].x, r.b[1], ax[1]);
-      ay[1] = fmaf(r.q[1].y, r.b[1], ay[1]);
+#pragma unroll
+      for (int u = 0; u < UQ; ++u) {
+        ax[u & 3] = fmaf(r.q[u].x, r.b[u], ax[u & 3]);
+        ay[u & 3] = fmaf(r.q[u].y, r.b[u], ay[u & 3]);
+      }
     }
     float sx = (ax[0] + ax[1]) + (ax[2] + ax[3]);
     float sy = (ay[0] + ay[1]) + (ay[2] + ay[3]);
-    sx += __shfl_xor_sync(0xffffffffu, sx, 1);
-    sy += __shfl_xor_sync(0xffffffffu, sy, 1);
-    sx += __shfl_xor_sync(0xffffffffu, sx, 2);
-    sy += __shfl_xor_sync(0xffffffffu, sy, 2);
+#pragma unroll
+    for (int o = RPW; o < 32; o <<= 1) {
+      sx += __shfl_xor_sync(0xffffffffu, sx, o);
+      sy += __shfl_xor_sync(0xffffffffu, sy, o);
+    }
     if (owner) {
       two_sum(hx, __fadd_rn(sx, lx), hx, lx);
       two_sum(hy, __fadd_rn(sy, ly), hy, ly);
@@ -748,19 +753,22 @@ __device__ __forceinline__ void bsweep_fast_body(const BSweepArgs& a, const int 
   }
 }
 
-// thread cap of the warp-specialised kernels: room for two blocks of entries in registers
-template <int NQ> struct FastCap { static constexpr int threads = NQ <= 8 ? 512 : 384; };
+// The two warp-specialised variants: RS = 2 for N <= 32, RS = 4 for N <= 64
+// (16 terms per lane either way), with their CTA thread cap (two blocks of
+// entries in registers).
+constexpr int kFastThreads = 384;
+enum { SWEEP_GENERAL = 0, SWEEP_FAST_R2 = 1, SWEEP_FAST_R4 = 2 };
 
-template <int NQ, int NF>
-__global__ void __launch_bounds__(FastCap<NQ>::threads) k_bsweep_fast(const BSweepArgs a, const int nstage) {
+template <int RS, int NF>
+__global__ void __launch_bounds__(kFastThreads) k_bsweep_fast(const BSweepArgs a, const int nstage) {
   extern __shared__ __align__(128) unsigned char smem[];
-  bsweep_fast_body<NQ, NF>(a, blockIdx.x, nstage, smem);
+  bsweep_fast_body<RS, 16, NF>(a, blockIdx.x, nstage, smem);
 }
 
-template <int NQ>
-__global__ void __launch_bounds__(FastCap<NQ>::threads) k_bsweep_fast_batch(const BSweepArgs* __restrict__ args,
-                                                            const int* __restrict__ cta_off, int nprob,
-                                                            const int nstage) {
+template <int RS>
+__global__ void __launch_bounds__(kFastThreads) k_bsweep_fast_batch(const BSweepArgs* __restrict__ args,
+                                                                 const int* __restrict__ cta_off,
+                                                                 int nprob, const int nstage) {
   extern __shared__ __align__(128) unsigned char smem[];
   int lo = 0, hi = nprob;   // largest p with cta_off[p] <= blockIdx.x
   while (hi - lo > 1) {
@@ -768,7 +776,7 @@ __global__ void __launch_bounds__(FastCap<NQ>::threads) k_bsweep_fast_batch(cons
     if (cta_off[mid] <= (int)blockIdx.x) lo = mid; else hi = mid;
   }
   const BSweepArgs a = args[lo];
-  bsweep_fast_body<NQ, 0>(a, (int)blockIdx.x - cta_off[lo], nstage, smem);
+  bsweep_fast_body<RS, 16, 0>(a, (int)blockIdx.x - cta_off[lo], nstage, smem);
 }
 
 template <bool MIX, int RS, bool DIRECT>
@@ -858,99 +866,86 @@ static cudaError_t launch_bb(const BSweepArgs* host_args, const BSweepArgs* dev_
 }
 
 // geometry of the warp-specialised binary32 sweep (consumer warps + producer)
-template <int NQ>
+template <int RS>
 static void fast_geometry(const BSweepArgs& a, int& threads, size_t& stage, size_t& fixed) {
-  threads = 32 * (((a.N + 7) / 8) * a.kc + 1);
+  threads = 32 * (((a.N + 32 / RS - 1) / (32 / RS)) * a.kc + 1);
   stage = a.mstride + (a.Q ? a.qstride : 0) + (a.Brow ? sizeof(float) * a.Kp * a.bs : 0);
-  fixed = 2 * (size_t)a.kc * 4 * (NQ + 2) * sizeof(float2) + 16;
+  fixed = 2 * (size_t)a.kc * RS * (16 + 2) * sizeof(float2) + 16;
 }
 
 // ring depth and shared memory of a warp-specialised launch; 0 if it does not apply
-template <int NQ>
 static int fast_plan(int threads, size_t stage, size_t fixed, int total_ctas, size_t& smem) {
-  if (threads > FastCap<NQ>::threads) return 0;
+  if (threads > kFastThreads) return 0;
   const int ns = ring_stages(stage, fixed + 8 * 16, threads, total_ctas);
   if (ns < 2) return 0;
   smem = (size_t)ns * stage + fixed + 16 * (size_t)ns + 16;
   return smem <= 227 * 1024 ? ns : 0;
 }
 
-template <int NQ>
-static bool launch_fast(const BSweepArgs& a, cudaStream_t st, cudaError_t& err) {
+template <int RS>
+static cudaError_t launch_fast(const BSweepArgs& a, cudaStream_t st) {
   int threads;
   size_t stage, fixed, smem = 0;
-  fast_geometry<NQ>(a, threads, stage, fixed);
+  fast_geometry<RS>(a, threads, stage, fixed);
   const int grid = (a.K + a.kc - 1) / a.kc;
-  const int ns = fast_plan<NQ>(threads, stage, fixed, grid, smem);
-  if (!ns) return false;
-  if (a.N == 4 * NQ) {   // N = 32 or 64: offsets fixed at compile time
-    set_max_smem((const void*)k_bsweep_fast<NQ, 4 * NQ>);
-    k_bsweep_fast<NQ, 4 * NQ><<<grid, threads, smem, st>>>(a, ns);
+  const int ns = fast_plan(threads, stage, fixed, grid, smem);
+  if (!ns) return cudaErrorInvalidConfiguration;
+  if (a.N == 16 * RS) {   // N = 32 or 64: offsets fixed at compile time
+    set_max_smem((const void*)k_bsweep_fast<RS, 16 * RS>);
+    k_bsweep_fast<RS, 16 * RS><<<grid, threads, smem, st>>>(a, ns);
   } else {
-    set_max_smem((const void*)k_bsweep_fast<NQ, 0>);
-    k_bsweep_fast<NQ, 0><<<grid, threads, smem, st>>>(a, ns);
+    set_max_smem((const void*)k_bsweep_fast<RS, 0>);
+    k_bsweep_fast<RS, 0><<<grid, threads, smem, st>>>(a, ns);
   }
-  err = cudaGetLastError();
-  return true;
+  return cudaGetLastError();
 }
 
-template <int NQ>
-static bool launch_fast_batch(const BSweepArgs* host_args, const BSweepArgs* dev_args,
-                              const int* dev_cta_off, int nprob, int total_ctas, cudaStream_t st,
-                              cudaError_t& err) {
+template <int RS>
+static cudaError_t launch_fast_batch(const BSweepArgs* host_args, const BSweepArgs* dev_args,
+                                     const int* dev_cta_off, int nprob, int total_ctas,
+                                     cudaStream_t st) {
   int threads = 32;
   size_t stage = 16, fixed = 16, smem = 0;
   for (int p = 0; p < nprob; ++p) {
     int t;
     size_t sg, f;
-    fast_geometry<NQ>(host_args[p], t, sg, f);
+    fast_geometry<RS>(host_args[p], t, sg, f);
     threads = t > threads ? t : threads;
     stage = sg > stage ? sg : stage;
     fixed = f > fixed ? f : fixed;
   }
-  const int ns = fast_plan<NQ>(threads, stage, fixed, total_ctas, smem);
-  if (!ns) return false;
-  set_max_smem((const void*)k_bsweep_fast_batch<NQ>);
-  k_bsweep_fast_batch<NQ><<<total_ctas, threads, smem, st>>>(dev_args, dev_cta_off, nprob, ns);
-  err = cudaGetLastError();
-  return true;
+  const int ns = fast_plan(threads, stage, fixed, total_ctas, smem);
+  if (!ns) return cudaErrorInvalidConfiguration;
+  set_max_smem((const void*)k_bsweep_fast_batch<RS>);
+  k_bsweep_fast_batch<RS><<<total_ctas, threads, smem, st>>>(dev_args, dev_cta_off, nprob, ns);
+  return cudaGetLastError();
 }
 
-bool bsweep_fast_ok(const BSweepArgs& a, int mixed) {
-  if (!mixed || a.N > 64) return false;
+int bsweep_variant(const BSweepArgs& a, int mixed) {
+  if (!mixed || a.N > 64) return SWEEP_GENERAL;
   int threads;
   size_t stage, fixed, smem = 0;
   if (a.N <= 32) {
-    fast_geometry<8>(a, threads, stage, fixed);
-    return fast_plan<8>(threads, stage, fixed, 1, smem) > 0;
+    fast_geometry<2>(a, threads, stage, fixed);
+    return fast_plan(threads, stage, fixed, 1, smem) > 0 ? SWEEP_FAST_R2 : SWEEP_GENERAL;
   }
-  fast_geometry<16>(a, threads, stage, fixed);
-  return fast_plan<16>(threads, stage, fixed, 1, smem) > 0;
+  fast_geometry<4>(a, threads, stage, fixed);
+  return fast_plan(threads, stage, fixed, 1, smem) > 0 ? SWEEP_FAST_R4 : SWEEP_GENERAL;
 }
 
-// A batch whose problems all pass bsweep_fast_ok runs the warp-specialised
-// kernel (the entries beyond a problem's N are zeros, so the N <= 64 variant
-// gives an N <= 32 problem the same sums); any other batch the general one.
+// The problems of one batched launch share the variant (the caller groups
+// them so: a single evaluation of each takes the same one).
 cudaError_t launch_bsweep_batch(const BSweepArgs* host_args, const BSweepArgs* dev_args,
                                 const int* dev_cta_off, int nprob, int total_ctas, int mixed,
                                 cudaStream_t st) {
-  if (mixed) {
-    int nmax = 0;
-    bool fast = true;
-    for (int p = 0; p < nprob; ++p) {
-      nmax = host_args[p].N > nmax ? host_args[p].N : nmax;
-      fast = fast && bsweep_fast_ok(host_args[p], mixed);
-    }
-    cudaError_t e = cudaSuccess;
-    if (fast && nmax <= 32 &&
-        launch_fast_batch<8>(host_args, dev_args, dev_cta_off, nprob, total_ctas, st, e))
-      return e;
-    if (fast && nmax > 32 &&
-        launch_fast_batch<16>(host_args, dev_args, dev_cta_off, nprob, total_ctas, st, e))
-      return e;
-    if (fast) return cudaErrorInvalidConfiguration;   // the single-problem path would differ
-    return launch_bb<true, 4>(host_args, dev_args, dev_cta_off, nprob, total_ctas, st);
-  }
+  const int v = nprob > 0 ? bsweep_variant(host_args[0], mixed) : SWEEP_GENERAL;
+  for (int p = 1; p < nprob; ++p)
+    if (bsweep_variant(host_args[p], mixed) != v) return cudaErrorInvalidValue;
+  if (v == SWEEP_FAST_R2)
+    return launch_fast_batch<2>(host_args, dev_args, dev_cta_off, nprob, total_ctas, st);
+  if (v == SWEEP_FAST_R4)
+    return launch_fast_batch<4>(host_args, dev_args, dev_cta_off, nprob, total_ctas, st);
+  if (mixed) return launch_bb<true, 4>(host_args, dev_args, dev_cta_off, nprob, total_ctas, st);
   return launch_bb<false, 4>(host_args, dev_args, dev_cta_off, nprob, total_ctas, st);
 }
 
@@ -980,11 +975,9 @@ static cudaError_t launch_b(const BSweepArgs& a, cudaStream_t st) {
 
 cudaError_t launch_bsweep(const BSweepArgs& a, int mixed, cudaStream_t st) {
   if (mixed) {
-    cudaError_t e = cudaSuccess;
-    if (bsweep_fast_ok(a, mixed)) {
-      if (a.N <= 32 ? launch_fast<8>(a, st, e) : launch_fast<16>(a, st, e)) return e;
-      return cudaErrorInvalidConfiguration;
-    }
+    const int v = bsweep_variant(a, mixed);
+    if (v == SWEEP_FAST_R2) return launch_fast<2>(a, st);
+    if (v == SWEEP_FAST_R4) return launch_fast<4>(a, st);
     return launch_b<true, 4>(a, st);
   }
   return launch_b<false, 4>(a, st);
