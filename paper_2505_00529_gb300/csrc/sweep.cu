@@ -753,19 +753,22 @@ __device__ __forceinline__ void bsweep_fast_body(const BSweepArgs& a, const int 
   }
 }
 
-// The two warp-specialised variants: RS = 2 for N <= 32, RS = 4 for N <= 64
-// (16 terms per lane either way), with their CTA thread cap (two blocks of
-// entries in registers).
+// The two warp-specialised variants: kSmallRS lanes per row for N <= 32,
+// four for N <= 64, with their CTA thread cap (two blocks of entries in
+// registers).  Two lanes per row measured fastest at N = 32 (four and eight
+// spread a column over more warps but lose more to the kernels that share
+// the SMs during the panel sweeps).
 constexpr int kFastThreads = 384;
-enum { SWEEP_GENERAL = 0, SWEEP_FAST_R2 = 1, SWEEP_FAST_R4 = 2 };
+constexpr int kSmallRS = 2;
+enum { SWEEP_GENERAL = 0, SWEEP_FAST_SMALL = 1, SWEEP_FAST_R4 = 2 };
 
-template <int RS, int NF>
+template <int RS, int NQ, int NF>
 __global__ void __launch_bounds__(kFastThreads) k_bsweep_fast(const BSweepArgs a, const int nstage) {
   extern __shared__ __align__(128) unsigned char smem[];
-  bsweep_fast_body<RS, 16, NF>(a, blockIdx.x, nstage, smem);
+  bsweep_fast_body<RS, NQ, NF>(a, blockIdx.x, nstage, smem);
 }
 
-template <int RS>
+template <int RS, int NQ>
 __global__ void __launch_bounds__(kFastThreads) k_bsweep_fast_batch(const BSweepArgs* __restrict__ args,
                                                                  const int* __restrict__ cta_off,
                                                                  int nprob, const int nstage) {
@@ -776,7 +779,7 @@ __global__ void __launch_bounds__(kFastThreads) k_bsweep_fast_batch(const BSweep
     if (cta_off[mid] <= (int)blockIdx.x) lo = mid; else hi = mid;
   }
   const BSweepArgs a = args[lo];
-  bsweep_fast_body<RS, 16, 0>(a, (int)blockIdx.x - cta_off[lo], nstage, smem);
+  bsweep_fast_body<RS, NQ, 0>(a, (int)blockIdx.x - cta_off[lo], nstage, smem);
 }
 
 template <bool MIX, int RS, bool DIRECT>
@@ -866,11 +869,11 @@ static cudaError_t launch_bb(const BSweepArgs* host_args, const BSweepArgs* dev_
 }
 
 // geometry of the warp-specialised binary32 sweep (consumer warps + producer)
-template <int RS>
+template <int RS, int NQ>
 static void fast_geometry(const BSweepArgs& a, int& threads, size_t& stage, size_t& fixed) {
   threads = 32 * (((a.N + 32 / RS - 1) / (32 / RS)) * a.kc + 1);
   stage = a.mstride + (a.Q ? a.qstride : 0) + (a.Brow ? sizeof(float) * a.Kp * a.bs : 0);
-  fixed = 2 * (size_t)a.kc * RS * (16 + 2) * sizeof(float2) + 16;
+  fixed = 2 * (size_t)a.kc * RS * (NQ + 2) * sizeof(float2) + 16;
 }
 
 // ring depth and shared memory of a warp-specialised launch; 0 if it does not apply
@@ -882,25 +885,25 @@ static int fast_plan(int threads, size_t stage, size_t fixed, int total_ctas, si
   return smem <= 227 * 1024 ? ns : 0;
 }
 
-template <int RS>
+template <int RS, int NQ>
 static cudaError_t launch_fast(const BSweepArgs& a, cudaStream_t st) {
   int threads;
   size_t stage, fixed, smem = 0;
-  fast_geometry<RS>(a, threads, stage, fixed);
+  fast_geometry<RS, NQ>(a, threads, stage, fixed);
   const int grid = (a.K + a.kc - 1) / a.kc;
   const int ns = fast_plan(threads, stage, fixed, grid, smem);
   if (!ns) return cudaErrorInvalidConfiguration;
-  if (a.N == 16 * RS) {   // N = 32 or 64: offsets fixed at compile time
-    set_max_smem((const void*)k_bsweep_fast<RS, 16 * RS>);
-    k_bsweep_fast<RS, 16 * RS><<<grid, threads, smem, st>>>(a, ns);
+  if (a.N == NQ * RS) {   // N = 32 or 64: offsets fixed at compile time
+    set_max_smem((const void*)k_bsweep_fast<RS, NQ, NQ * RS>);
+    k_bsweep_fast<RS, NQ, NQ * RS><<<grid, threads, smem, st>>>(a, ns);
   } else {
-    set_max_smem((const void*)k_bsweep_fast<RS, 0>);
-    k_bsweep_fast<RS, 0><<<grid, threads, smem, st>>>(a, ns);
+    set_max_smem((const void*)k_bsweep_fast<RS, NQ, 0>);
+    k_bsweep_fast<RS, NQ, 0><<<grid, threads, smem, st>>>(a, ns);
   }
   return cudaGetLastError();
 }
 
-template <int RS>
+template <int RS, int NQ>
 static cudaError_t launch_fast_batch(const BSweepArgs* host_args, const BSweepArgs* dev_args,
                                      const int* dev_cta_off, int nprob, int total_ctas,
                                      cudaStream_t st) {
@@ -909,15 +912,15 @@ static cudaError_t launch_fast_batch(const BSweepArgs* host_args, const BSweepAr
   for (int p = 0; p < nprob; ++p) {
     int t;
     size_t sg, f;
-    fast_geometry<RS>(host_args[p], t, sg, f);
+    fast_geometry<RS, NQ>(host_args[p], t, sg, f);
     threads = t > threads ? t : threads;
     stage = sg > stage ? sg : stage;
     fixed = f > fixed ? f : fixed;
   }
   const int ns = fast_plan(threads, stage, fixed, total_ctas, smem);
   if (!ns) return cudaErrorInvalidConfiguration;
-  set_max_smem((const void*)k_bsweep_fast_batch<RS>);
-  k_bsweep_fast_batch<RS><<<total_ctas, threads, smem, st>>>(dev_args, dev_cta_off, nprob, ns);
+  set_max_smem((const void*)k_bsweep_fast_batch<RS, NQ>);
+  k_bsweep_fast_batch<RS, NQ><<<total_ctas, threads, smem, st>>>(dev_args, dev_cta_off, nprob, ns);
   return cudaGetLastError();
 }
 
@@ -926,10 +929,10 @@ int bsweep_variant(const BSweepArgs& a, int mixed) {
   int threads;
   size_t stage, fixed, smem = 0;
   if (a.N <= 32) {
-    fast_geometry<2>(a, threads, stage, fixed);
-    return fast_plan(threads, stage, fixed, 1, smem) > 0 ? SWEEP_FAST_R2 : SWEEP_GENERAL;
+    fast_geometry<kSmallRS, 32 / kSmallRS>(a, threads, stage, fixed);
+    return fast_plan(threads, stage, fixed, 1, smem) > 0 ? SWEEP_FAST_SMALL : SWEEP_GENERAL;
   }
-  fast_geometry<4>(a, threads, stage, fixed);
+  fast_geometry<4, 16>(a, threads, stage, fixed);
   return fast_plan(threads, stage, fixed, 1, smem) > 0 ? SWEEP_FAST_R4 : SWEEP_GENERAL;
 }
 
@@ -941,10 +944,11 @@ cudaError_t launch_bsweep_batch(const BSweepArgs* host_args, const BSweepArgs* d
   const int v = nprob > 0 ? bsweep_variant(host_args[0], mixed) : SWEEP_GENERAL;
   for (int p = 1; p < nprob; ++p)
     if (bsweep_variant(host_args[p], mixed) != v) return cudaErrorInvalidValue;
-  if (v == SWEEP_FAST_R2)
-    return launch_fast_batch<2>(host_args, dev_args, dev_cta_off, nprob, total_ctas, st);
+  if (v == SWEEP_FAST_SMALL)
+    return launch_fast_batch<kSmallRS, 32 / kSmallRS>(host_args, dev_args, dev_cta_off, nprob,
+                                                      total_ctas, st);
   if (v == SWEEP_FAST_R4)
-    return launch_fast_batch<4>(host_args, dev_args, dev_cta_off, nprob, total_ctas, st);
+    return launch_fast_batch<4, 16>(host_args, dev_args, dev_cta_off, nprob, total_ctas, st);
   if (mixed) return launch_bb<true, 4>(host_args, dev_args, dev_cta_off, nprob, total_ctas, st);
   return launch_bb<false, 4>(host_args, dev_args, dev_cta_off, nprob, total_ctas, st);
 }
@@ -976,8 +980,8 @@ static cudaError_t launch_b(const BSweepArgs& a, cudaStream_t st) {
 cudaError_t launch_bsweep(const BSweepArgs& a, int mixed, cudaStream_t st) {
   if (mixed) {
     const int v = bsweep_variant(a, mixed);
-    if (v == SWEEP_FAST_R2) return launch_fast<2>(a, st);
-    if (v == SWEEP_FAST_R4) return launch_fast<4>(a, st);
+    if (v == SWEEP_FAST_SMALL) return launch_fast<kSmallRS, 32 / kSmallRS>(a, st);
+    if (v == SWEEP_FAST_R4) return launch_fast<4, 16>(a, st);
     return launch_b<true, 4>(a, st);
   }
   return launch_b<false, 4>(a, st);
