@@ -508,8 +508,8 @@ __device__ __forceinline__ void bsweep_body(const BSweepArgs& a, const int cta, 
 // entries of the NEXT block into registers right after the current block's
 // X, so that the dependent part of a block step is: read X (shared,
 // broadcast), the FMA chain, log2(RS) shuffle rounds, two additions, write
-// X, one named barrier.  NF = N when N = RS * NQ is fixed at compile time
-// (constant offsets), else 0.
+// X, one named barrier; the test that a block has landed runs a step ahead.
+// NF = N when N = RS * NQ is fixed at compile time (constant offsets), else 0.
 // X layout per column: entry q at run (q mod RS), position (q div RS); runs
 // are XS = NQ + 2 float2 apart so the runs a warp reads sit in different
 // banks.
@@ -655,6 +655,10 @@ __device__ __forceinline__ void bsweep_fast_body(const BSweepArgs& a, const int 
 
   // Every consumer takes the same exit decision: the OR, over the consumers,
   // of a failed wait, formed by the step's barrier itself.
+  // Readiness runs one block ahead of use: step it tests block it + 2 (the
+  // producer can always issue it once block it is released, even with two
+  // slots) and consumes the test only at its end, so the test's latency is
+  // off the dependent path; step it + 1 then loads block it + 2.
   FastRegs<RS, NQ> ra, rb2;
   int s = 0;
   uint32_t par = 0;
@@ -665,6 +669,13 @@ __device__ __forceinline__ void bsweep_fast_body(const BSweepArgs& a, const int 
   }
   fast_load<RS, NQ, NF>(ra, ring, N, mbytes, qbytes, has_q, min(bs, J), bwd, Kp, rsub, i, col, kq,
                         active);
+  if (nblk > 1 &&
+      !mbar_wait_or_flag(&full[1 % nstage], (uint32_t)((1 / nstage) & 1), abort_flag)) {
+    bad = true;
+    *abort_flag = 1;
+  }
+  int s2 = 2 % nstage;                              // slot and parity of block it + 2
+  uint32_t par2 = (uint32_t)((2 / nstage) & 1);
   bool ok = !named_barrier_or(1, nthr, bad);
 
   int cur = 0;
@@ -680,12 +691,10 @@ __device__ __forceinline__ void bsweep_fast_body(const BSweepArgs& a, const int 
     float4 xv[NQ / 2];
 #pragma unroll
     for (int k = 0; k < NQ / 2; ++k) xv[k] = xp[k];
-    // the next block (independent of X): landed, then into registers
+    const bool look = it + 2 < nblk;
+    const uint32_t rdy = look ? mbar_try_wait(&full[s2], par2) : 1u;
+    // the next block (independent of X, landed as tested one step earlier)
     if (more) {
-      if (!mbar_wait_or_flag(&full[s1], par1, abort_flag)) {
-        bad = true;
-        *abort_flag = 1;
-      }
       const int t1 = (it + 1) * bs;
       fast_load<RS, NQ, NF>(nx, ring + (size_t)s1 * stage, N, mbytes, qbytes, has_q, min(bs, J - t1),
                             bwd, Kp, rsub, i, col, kq, active);
@@ -725,10 +734,15 @@ __device__ __forceinline__ void bsweep_fast_body(const BSweepArgs& a, const int 
         else *xb2 = make_float2(hx, hy);
       }
     }
+    if (!rdy && !mbar_wait_or_flag(&full[s2], par2, abort_flag)) {
+      bad = true;
+      *abort_flag = 1;
+    }
     const bool stop = named_barrier_or(1, nthr, bad);
     cur ^= 1;
     s = s1;
     par = par1;
+    if (++s2 == nstage) { s2 = 0; par2 ^= 1u; }
     return !stop;
   };
   int it = 0;
