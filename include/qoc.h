@@ -114,10 +114,10 @@ qoc_status qoc_set_block_steps(qoc_problem* p, int steps);
 /* Panel columns per CTA of the tangent and second-order adjoint sweeps
  * (1, 2 or 4; 0 restores the built-in choice, 1).  A launch-shape knob; the
  * autotuner in the Python package picks it together with the block steps.
- * It leaves the arithmetic unchanged except for binary32 panels whose CTA
- * exceeds the warp-specialised sweep's thread cap (32 (ceil(N/8) kc + 1) >
- * 512 for N <= 32, > 384 for N <= 64): those run the general sweep, whose
- * sums are ordered differently (results agree to rounding).
+ * It leaves the arithmetic unchanged except for binary32 panels with
+ * 32 < N <= 64 whose CTA exceeds the warp-specialised sweep's thread cap
+ * (32 (ceil(N/8) kc + 1) > 384): those run the general sweep, whose sums are
+ * ordered differently (results agree to rounding).
  * QOC_EUNSUPPORTED when 32 ceil(N/8) kc > 1024 threads. */
 qoc_status qoc_set_panel_columns(qoc_problem* p, int kc);
 
