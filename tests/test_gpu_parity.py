@@ -262,3 +262,27 @@ def test_block_steps_validation():
         for bad in (0, 9, 6):
             with pytest.raises(q.QocError):
                 q.qoc_set_block_steps(P.handle, bad)
+
+
+@pytest.mark.parametrize("N,K,J", [(32, 9, 64), (20, 7, 45), (40, 7, 50)], ids=lambda v: str(v))
+def test_panel_columns(N, K, J):
+    """Several panel columns per CTA (ragged last CTA): the oracle's results in
+    both precisions; for binary32 panels with N <= 32 the column count leaves
+    the arithmetic unchanged (the same warp-specialised kernel), so the
+    results equal the one-column ones bit for bit."""
+    prob = inputs.small_problem(N=N, K=K, J=J, seed=500 + N, dt=0.05, basis="random")
+    theta = inputs.eval_theta(K, 501)
+    ref = orc.evaluate(prob, theta, order=2)
+    for precision in (q.QOC_FP64, q.QOC_MIXED_FP32):
+        tol = TOL[precision]
+        res = {}
+        for kc in (1, 2, 4):
+            with q.Problem(prob, precision=precision, panel_columns=kc) as P:
+                res[kc] = P.eval_grad_hess(theta)
+            Jv, g, H = res[kc]
+            assert abs(Jv - ref["J"]) <= tol * abs(ref["J"]), (precision, kc)
+            assert rel(g, ref["grad"]) <= tol and rel(H, ref["hess"]) <= tol, (precision, kc)
+        if precision == q.QOC_MIXED_FP32 and N <= 32:
+            for kc in (2, 4):
+                assert res[kc][0] == res[1][0]
+                assert np.array_equal(res[kc][1], res[1][1]) and np.array_equal(res[kc][2], res[1][2])
