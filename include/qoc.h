@@ -272,10 +272,14 @@ void qoc_mlp_destroy(qoc_mlp* m);
  * Batches of uneven problems (different N, K, J; one precision; time
  * blocking on).  One batched evaluation = the gradient and Hessian of every
  * problem at its own theta: the parallel phases of each problem run on that
- * problem's stream, the four sequential sweeps run as one launch each over
- * all problems, and the whole evaluation is captured once into a CUDA graph
- * (qoc_batch_set_graph(b, 0) disables the graph).  The batch references the
- * problems (caller keeps them alive and must not use them concurrently).
+ * problem's stream, each of the four sequential sweeps runs as one launch
+ * per sweep kernel over all problems that take it (binary32 N <= 32,
+ * binary32 N <= 64, the rest; side by side on their own streams), and the
+ * whole evaluation is captured once into a CUDA graph (qoc_batch_set_graph(b,
+ * 0) disables the graph).  Every problem takes the kernel a single
+ * evaluation of it takes, so batched results equal single ones bit for bit.
+ * The batch references the problems (caller keeps them alive and must not
+ * use them concurrently).
  *   thetas: concatenation of the problems' theta (sum K_i doubles)
  *   outs:   concatenation of [J, grad (K_i), Hess (K_i^2)] per problem
  * ------------------------------------------------------------------------- */
