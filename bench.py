@@ -53,6 +53,24 @@ def env_int(k, d):
         return d
 
 
+def max_over_ranks(x, dist=None, device="cpu"):
+    """The largest x over the ranks of the process group `dist` (x itself
+    without one): every rank times its own replica and the job is as slow as
+    its slowest rank."""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(world, ms):
+    """Evaluations per second of the whole job: each of the `world` ranks
+    finishes one evaluation per step of `ms` milliseconds (the slowest rank's)."""
+    return world * 1000.0 / ms
+
+
 # --------------------------------------------------------------------------
 # CPU oracle timing (a deliberately slow reference: spawned process, 1 thread)
 # --------------------------------------------------------------------------
@@ -245,11 +263,7 @@ def run_ours(args):
                 phases.append(ph)
         torch.cuda.synchronize()
         q.qoc_sync_status(P.handle)
-        ms = statistics.mean(a.elapsed_time(b) for a, b in ev)
-        if dist:
-            t = torch.tensor([ms], dtype=torch.float64, device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms = float(t.item())
+        ms = max_over_ranks(statistics.mean(a.elapsed_time(b) for a, b in ev), dist, dev)
         res = out.cpu().numpy().copy()
         return P, ms, phases, res
 
@@ -258,7 +272,7 @@ def run_ours(args):
     with clk:
         P, ms, phases, res = measure(prec, args.steps, args.warmup, timing=True)
     clocks = clk.summary()
-    value = world * 1000.0 / ms
+    value = whole_job_rate(world, ms)
 
     # ---- end to end through the host API (theta from host, results back to host) ----
     e2e_times = []
@@ -270,11 +284,7 @@ def run_ours(args):
         t1 = time.perf_counter()
         if k >= args.warmup:
             e2e_times.append(t1 - t0)
-    e2e_ms = 1000.0 * statistics.mean(e2e_times)
-    if dist:
-        t = torch.tensor([e2e_ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = float(t.item())
+    e2e_ms = max_over_ranks(1000.0 * statistics.mean(e2e_times), dist, dev)
     P.close()
 
     # ---- plain FP64 GPU method on the same workload ----
@@ -284,7 +294,7 @@ def run_ours(args):
         P64.close()
         hess_rel = float(np.linalg.norm(res[1 + K:] - res64[1 + K:]) / np.linalg.norm(res64[1 + K:]))
         grad_rel = float(np.linalg.norm(res[1:1 + K] - res64[1:1 + K]) / np.linalg.norm(res64[1:1 + K]))
-        fp64 = {"value": world * 1000.0 / ms64, "unit": UNIT, "ms_per_step": ms64,
+        fp64 = {"value": whole_job_rate(world, ms64), "unit": UNIT, "ms_per_step": ms64,
                 "speedup_mixed_over_fp64": ms64 / ms,
                 "mixed_vs_fp64_rel_err": {"J": abs(res[0] - res64[0]) / abs(res64[0]),
                                           "grad": grad_rel, "hess": hess_rel}}
@@ -296,7 +306,8 @@ def run_ours(args):
             t0 = time.perf_counter()
             th_star, info = PT.trust_region_solve(np.zeros(K), gtol=1e-6, xtol=1e-10, max_iter=500)
             t1 = time.perf_counter()
-        tr = {"value": world / (t1 - t0), "unit": "TR solves/s", "iters": info["iters"],
+        tr_s = max_over_ranks(t1 - t0, dist, dev)
+        tr = {"value": world / tr_s, "unit": "TR solves/s", "iters": info["iters"],
               "n_eval_gh": info["n_eval_gh"], "n_eval_J": info["n_eval_J"], "J": info["J"],
               "grad_norm": info["grad_norm"], "stop": info["stop"], "gtol": 1e-6}
 
@@ -343,7 +354,7 @@ def run_ours(args):
                                         "panel_columns": tuned[prec]["panel_columns"],
                                         "autotune_table_ms": tuned[prec]["table"]}
                                        if prec in tuned else "library defaults")),
-                "e2e": {"value": world * 1000.0 / e2e_ms, "unit": UNIT, "ms_per_step": e2e_ms,
+                "e2e": {"value": whole_job_rate(world, e2e_ms), "unit": UNIT, "ms_per_step": e2e_ms,
                         "h2d_bytes_per_step": 8 * K, "d2h_bytes_per_step": 8 * (1 + K + K * K)},
                 "gpu_launches": LAUNCHES_PER_EVAL * args.steps,
                 "clocks": clocks, "roofline": roof, "cpu_baseline": cpu,
