@@ -22,6 +22,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
@@ -268,7 +269,8 @@ def run_ours(args):
         return P, ms, phases, res
 
     # ---- headline: device-resident evaluations ----
-    clk = ClockSampler(local, os.path.join(ROOT, "gpurun_out" if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else ".", f"clocks_rank{rank}.csv"))
+    clk_dir = tempfile.mkdtemp(prefix="qoc_clocks_")
+    clk = ClockSampler(local, os.path.join(clk_dir, f"clocks_rank{rank}.csv"))
     with clk:
         P, ms, phases, res = measure(prec, args.steps, args.warmup, timing=True)
     clocks = clk.summary()
@@ -324,7 +326,7 @@ def run_ours(args):
                 "unit": "TFLOP/s", "frac": ach / FP64_PEAK_TFLOPS,
                 "traffic": REFINE_TRAFFIC_BYTES if (N, J) == (32, 4000) else None,
                 "traffic_source": "dram__bytes_read.sum + dram__bytes_write.sum of one k_eig_refine "
-                                  "launch (ncu; profiles/kernels_grad_hess_N32_K64_J4000_mixed.md)",
+                                  "launch (ncu capture of this workload)",
                 "peak_source": "binary64 FMA rate from unit counts x max SM clock (152 SMs x 2 DFMA/clk "
                                "x 2 x 2.07 GHz); MEASURED_PEAKS.json has no binary64 figure",
                 "algorithmic": f"(2u + 1 + p + r) N^3 binary64 FMA per step, u = {u:.3f} updates/step, "

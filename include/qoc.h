@@ -319,8 +319,10 @@ void qoc_batch_destroy(qoc_batch* b);
  * qoc_assemble_noalloc_scratch_doubles(steps, K) of them and returns
  * QOC_EINVAL (with the reason in qoc_last_error) when that is above the
  * maximum, e.g. K = 64 allows steps <= 8000.  The first call on a device
- * looks up the array's device address (once per device, the device
- * current); make that first call before any stream capture.  All calls
+ * looks up the array's device address with that device current, and every
+ * later call made while cuda_stream is not being captured looks it up again
+ * (the address changes if the device's context is destroyed and recreated);
+ * make that first call before any stream capture.  All calls
  * share the array and it keeps the previous call's contents (nothing needs
  * clearing: each call writes every element it reads), so calls that may
  * overlap on the GPU race: order them on one stream or with events.

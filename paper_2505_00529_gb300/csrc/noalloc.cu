@@ -32,19 +32,30 @@ constexpr int kMaxDevices = 64;
 std::mutex g_mu;
 double* g_scratch[kMaxDevices] = {};
 
-// device address of the array on the current device; taken once per device
-cudaError_t scratch_address(double** out) {
+// Device address of the array on the current device.  Outside a stream
+// capture the address is looked up again on every call and the per-device
+// copy refreshed: the library's device image is reloaded, possibly at another
+// address, when the device's primary context is destroyed and recreated (for
+// example after cudaDeviceReset), so a copy kept from before would be stale.
+// While `st` is being captured the copy from the last uncaptured call is
+// used, because the lookup may load the module, which a capture does not
+// allow; a first call on a device that comes during a capture is refused.
+cudaError_t scratch_address(cudaStream_t st, double** out) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  e = cudaStreamIsCapturing(st, &cap);
+  if (e != cudaSuccess) return e;
   std::lock_guard<std::mutex> lock(g_mu);
-  if (!g_scratch[dev]) {
+  if (cap == cudaStreamCaptureStatusNone) {
     void* ptr = nullptr;
     e = cudaGetSymbolAddress(&ptr, noalloc_scratch);
     if (e != cudaSuccess) return e;
     g_scratch[dev] = static_cast<double*>(ptr);
   }
+  if (!g_scratch[dev]) return cudaErrorStreamCaptureUnsupported;
   *out = g_scratch[dev];
   return cudaSuccess;
 }
@@ -74,7 +85,7 @@ extern "C" qoc_status qoc_assemble_grad_hess_noalloc(int steps, int K, const dou
     return QOC_EINVAL;
   }
   double* scratch = nullptr;
-  cudaError_t e = scratch_address(&scratch);
+  cudaError_t e = scratch_address(static_cast<cudaStream_t>(cuda_stream), &scratch);
   if (e == cudaSuccess) {
     const size_t nwork = qoc::assemble_work_doubles(steps, K);
     double* hess_raw = scratch + nwork;

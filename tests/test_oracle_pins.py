@@ -295,7 +295,7 @@ def _richardson(fun, theta, h):
     return np.array(out)
 
 
-@pytest.mark.parametrize("w", [(None, 1.0), (0.5, 0.5e3)])  # BASELINE weights, paper weights (rho=1e3)
+@pytest.mark.parametrize("w", [(None, 1.0), (0.5, 0.5e3)])  # workload weights (dt, 1), paper weights (rho=1e3)
 def test_gradient_and_hessian_by_finite_differences(w):
     w_f, w_t = w
     prob = inputs.small_problem(N=4, K=3, J=50, seed=31, dt=0.04, basis="random",
