@@ -7,8 +7,19 @@ energies U[-10,0], band-8 couplings N(0,0.1^2)), dense M N(0,0.3^2), T=20.
 One step = one full evaluation (J, grad, K x K Hessian) at a fixed seeded
 theta, inputs resident in device memory.  Prints one JSON line (rank 0).
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--precision mixed|fp64]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--precision mixed|fp64] [--no-extra]
   python bench.py --impl reference ...   (the FP64 CPU oracle, timed on the host)
+  python bench.py --fp64-peak            (binary64 peak: FMA chains and cuBLAS DGEMM)
+  python bench.py --profile ...          (the workload's evaluations only, for ncu)
+  python bench.py --batch / --warm-start (the batched and warm-start measurements)
+  python bench.py --scaling              (wall time vs J on the maximal model, Fig. 1)
+  python bench.py --tr-ratios            (Alg. 1 + BFGS vs Alg. 2 trust regions, Tables I/II)
+
+Besides the headline, the line carries the plain binary64 GPU method on the
+same workload, trust-region solves, the binary64-bound kernels against the
+binary64 FMA rate measured in the same run, the CPU oracle (one whole
+evaluation on one core), and the other workloads (small single, largest
+single, a batch of the uneven recipe) measured the same way.
 
 A single problem is a dependent chain of J steps and does not shard: with
 N > 1 processes (torchrun) every rank runs an independent replica and the
@@ -40,11 +51,10 @@ WORKLOAD = {"workload": "synthetic CI-shaped single problem, N=32 basis, K=64 si
 # tangent and second-order adjoint panels, 2 panel contractions, grad, hess partial,
 # hess final
 LAUNCHES_PER_EVAL = 27
-# DRAM bytes of one k_eig_refine launch on this workload (ncu capture of the
-# current kernel: 32.93 MB read, 0 written; algorithmic: W read once, 32.8 MB)
-REFINE_TRAFFIC_BYTES = 32.93e6
-FP64_PEAK_TFLOPS = 1.26    # 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (measured 1.20 at 1.99 GHz)
-FP32_PEAK_TFLOPS = 80.5    # 152 SMs x 128 FMA/clk x 2 flop x 2.07 GHz (measured 70 at 1.99 GHz)
+# DRAM bytes (read + written) of one launch of a kernel on a workload, from an
+# ncu capture of the current kernel: (kernel, N, J) -> bytes.  k_eig_refine:
+# 32.93 MB read, 0 written (algorithmic: W read once, 32.8 MB).
+TRAFFIC_BYTES = {("k_eig_refine", 32, 4000): 32.93e6}
 
 
 def env_int(k, d):
@@ -83,7 +93,7 @@ from paper_2505_00529_gb300 import inputs
 from oracle import qoc_oracle as orc
 p = inputs.config_problem(2)
 js = %d
-p.B = p.B[:js]          # first js steps of the same problem (same dt)
+p.B = p.B[:js]          # js = J: the whole workload; fewer: its first js steps (warm-up only)
 th = inputs.eval_theta(p.K, 0)
 t0 = time.perf_counter()
 r = orc.evaluate(p, th, order=2)
@@ -92,32 +102,28 @@ print(json.dumps({"seconds": dt, "steps": js}))
 """
 
 
-def time_oracle(sample_steps: int) -> dict:
+def time_oracle(steps: int = WORKLOAD["J"]) -> dict:
+    """One oracle evaluation (J, gradient, Hessian) of the bench workload on
+    one host core, timed whole: `steps` = J is the full workload."""
     env = dict(os.environ, OPENBLAS_NUM_THREADS="1", OMP_NUM_THREADS="1", MKL_NUM_THREADS="1",
                CUDA_VISIBLE_DEVICES="")
-    r = subprocess.run([sys.executable, "-c", ORACLE_SNIPPET % (ROOT, sample_steps)],
+    r = subprocess.run([sys.executable, "-c", ORACLE_SNIPPET % (ROOT, steps)],
                        capture_output=True, text=True, env=env, timeout=900)
     if r.returncode != 0:
         raise RuntimeError(r.stderr[-2000:])
     d = json.loads(r.stdout.strip().splitlines()[-1])
-    J = WORKLOAD["J"]
-    # the oracle's cost is linear in the number of steps: scale the sample to one full evaluation
-    per_eval = d["seconds"] * J / d["steps"]
-    return {"value": 1.0 / per_eval, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"one oracle evaluation over the first {sample_steps} of the {J} steps "
-                      f"({d['seconds']:.2f} s), scaled by {J}/{sample_steps}"}
+    return {"value": 1.0 / d["seconds"], "unit": UNIT, "cores": 1, "kind": "oracle", "seconds": d["seconds"],
+            "sample": f"one whole oracle evaluation of the workload ({d['steps']} steps, "
+                      f"{d['seconds']:.2f} s), nothing extrapolated"}
 
 
 def run_reference(args):
     rank = env_int("RANK", 0)
     if rank != 0:
         return 0
-    per = []
-    sample = args.ref_sample_steps
-    for _ in range(args.warmup):
-        time_oracle(max(8, sample // 8))
-    for _ in range(args.steps):
-        per.append(1.0 / time_oracle(sample)["value"])
+    for _ in range(args.warmup):            # untimed: short samples that load numpy and warm the caches
+        time_oracle(100)
+    per = [time_oracle()["seconds"] for _ in range(args.steps)]
     ms = 1000.0 * statistics.mean(per)
     value = 1000.0 / ms
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
@@ -125,8 +131,9 @@ def run_reference(args):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": dict(WORKLOAD, precision="fp64 (CPU oracle)"),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": f"each step: one oracle evaluation over the first {sample} "
-                                       f"of {WORKLOAD['J']} steps, scaled to the full problem"},
+                             "sample": f"each step: one whole oracle evaluation of the {WORKLOAD['J']}-step "
+                                       f"workload (J, gradient, Hessian), timed whole; warm-up steps "
+                                       f"evaluate its first 100 steps"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -193,19 +200,6 @@ class ClockSampler:
 # --------------------------------------------------------------------------
 # our arm
 # --------------------------------------------------------------------------
-def refine_flops(N, J, updates_per_step, rotated_fraction, final_fraction):
-    """Binary64 flops of one k_eig_refine launch: per step, u Ogita-Aishima
-    updates with two binary64 N^3 products each (H W, and the W^T H W and W^T W
-    triangles); the third product, W E, is binary64 only in an update that
-    ends the refinement early (the others form it in binary32, not counted);
-    the final residual pass (2 N^3 FMA) on the steps that take it (fraction p;
-    the others finish early), and W V (N^3 FMA) when the clean-up rotated
-    (fraction r); 2 flops per FMA."""
-    fma = (2.0 * updates_per_step + (1.0 - final_fraction) + 2.0 * final_fraction
-           + rotated_fraction) * N ** 3
-    return 2.0 * fma * J
-
-
 def run_ours(args):
     import numpy as np
     import torch
@@ -313,34 +307,21 @@ def run_ours(args):
               "n_eval_gh": info["n_eval_gh"], "n_eval_J": info["n_eval_J"], "J": info["J"],
               "grad_norm": info["grad_norm"], "stop": info["stop"], "gtol": 1e-6}
 
-    # ---- roofline of the dominant kernel (k_eig_refine: timed by events around its launch) ----
+    # ---- roofline: the binary64-bound kernels against the measured binary64 rate ----
+    fp64_tf, fp64_ms = q.qoc_measure_fp64_rate(4, 5)
     ph_mean = {k: statistics.mean(p[k] for p in phases) for k in phases[0]} if phases else {}
     roof = None
     if ph_mean:
-        u, rot = ph_mean["refine_updates_per_step"], ph_mean["cleanup_rotated_fraction"]
-        fin = ph_mean["final_pass_fraction"]
-        t_ref = ph_mean["k_eig_refine"]
-        flops = refine_flops(N, J, u, rot, fin)
-        ach = flops / (t_ref * 1e-3) / 1e12
-        roof = {"bound": "alu", "kernel": "k_eig_refine", "achieved": ach, "peak": FP64_PEAK_TFLOPS,
-                "unit": "TFLOP/s", "frac": ach / FP64_PEAK_TFLOPS,
-                "traffic": REFINE_TRAFFIC_BYTES if (N, J) == (32, 4000) else None,
-                "traffic_source": "dram__bytes_read.sum + dram__bytes_write.sum of one k_eig_refine "
-                                  "launch (ncu capture of this workload)",
-                "peak_source": "binary64 FMA rate from unit counts x max SM clock (152 SMs x 2 DFMA/clk "
-                               "x 2 x 2.07 GHz); MEASURED_PEAKS.json has no binary64 figure",
-                "algorithmic": f"(2u + 1 + p + r) N^3 binary64 FMA per step, u = {u:.3f} updates/step, "
-                               f"p = {fin:.3f} final-pass fraction, r = {rot:.3f} clean-up rotated "
-                               f"fraction, N={N}, J={J}",
-                "kernel_ms": t_ref,
-                "phase_ms": {k: v for k, v in ph_mean.items() if not k.startswith("k_") and k in
-                             ("eig", "prep", "chains", "pointwise", "panels", "assembly")},
-                "kernel_phase_ms": {k[2:]: v for k, v in ph_mean.items() if k.startswith("k_")}}
+        roof = roofline(N, J, ph_mean, fp64_tf)
+
+    extra = {}
+    if not args.no_extra:
+        extra = run_extra_workloads(q, inputs, stream, flush, dev, dist)
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         try:
-            cpu = time_oracle(args.ref_sample_steps)
+            cpu = time_oracle()
         except Exception as e:  # reported, never silently dropped
             cpu = {"error": str(e)[-300:]}
 
@@ -360,11 +341,315 @@ def run_ours(args):
                         "h2d_bytes_per_step": 8 * K, "d2h_bytes_per_step": 8 * (1 + K + K * K)},
                 "gpu_launches": LAUNCHES_PER_EVAL * args.steps,
                 "clocks": clocks, "roofline": roof, "cpu_baseline": cpu,
-                "fp64_plain": fp64, "tr_solve": tr}
+                "fp64_plain": fp64, "tr_solve": tr,
+                "fp64_fma_peak": {"tflops": fp64_tf, "ms": fp64_ms, "how": "qoc_measure_fp64_rate: "
+                                  "independent binary64 FMA chains, 4 CTAs x 256 threads per SM, best of 5"},
+                "other_workloads": extra}
         print(json.dumps(line), flush=True)
     if dist:
         dist.barrier()
         dist.destroy_process_group()
+    return 0
+
+
+# algorithmic binary64 flops per time step (the per-step counts of the method:
+# eigendecomposition 9 N^3, the textbook count of the symmetric QR with
+# vectors; M~ = W^T M W 4 N^3 and the second-derivative term X' 8 N^3)
+def eig_flops_per_step(N):
+    return 9.0 * N ** 3
+
+
+def prep_flops_per_step(N):
+    return 12.0 * N ** 3
+
+
+def roofline(N, J, ph, fp64_tf):
+    """Achieved binary64 rate of the binary64-bound kernels: algorithmic flops
+    per launch (per-step count x J steps) / the kernel's duration, measured by
+    CUDA events around its launch on the problem's stream, against the binary64
+    FMA rate measured in this run.  The dominant one (longest) is the line's
+    roofline; the others are listed with it."""
+    rows = {
+        "k_prep": (prep_flops_per_step(N) * J, ph["k_deriv_prep"],
+                   "M~ = W^T M W (4 N^3) and X' (8 N^3) per step"),
+        "k_eig_refine": (eig_flops_per_step(N) * J, ph["k_eig_refine"],
+                         "the whole eigendecomposition's 9 N^3 per step, credited to the refinement kernel"),
+        "eig (k_eig_jacobi32 + k_eig_refine)": (eig_flops_per_step(N) * J, ph["k_eig_jacobi"] + ph["k_eig_refine"],
+                                                "9 N^3 per step over both eigensolver kernels"),
+    }
+    kern = {}
+    for name, (fl, t, how) in rows.items():
+        ach = fl / (t * 1e-3) / 1e12
+        kern[name] = {"achieved": ach, "frac": ach / fp64_tf, "kernel_ms": t, "algorithmic_gflop": fl / 1e9,
+                      "count": how}
+    dom = max(("k_prep", "k_eig_refine"), key=lambda k: kern[k]["kernel_ms"])
+    d = kern[dom]
+    return {"bound": "alu", "kernel": dom, "achieved": d["achieved"], "peak": fp64_tf, "unit": "TFLOP/s",
+            "frac": d["frac"], "traffic": TRAFFIC_BYTES.get((dom, N, J)),
+            "traffic_source": "dram__bytes_read.sum + dram__bytes_write.sum of one launch (ncu capture of "
+                              "this workload, current kernel)" if TRAFFIC_BYTES.get((dom, N, J)) else None,
+            "peak_source": "binary64 FMA rate measured in this run (qoc_measure_fp64_rate); "
+                           "MEASURED_PEAKS.json has no binary64 figure",
+            "algorithmic": f"{d['algorithmic_gflop']:.3f} GFLOP per launch: {d['count']}, N={N}, J={J}",
+            "kernel_ms": d["kernel_ms"], "kernels": kern,
+            "phase_ms": {k: v for k, v in ph.items() if not k.startswith("k_") and k in
+                         ("eig", "prep", "chains", "pointwise", "panels", "assembly")},
+            "kernel_phase_ms": {k[2:]: v for k, v in ph.items() if k.startswith("k_")}}
+
+
+def _timed_evals(q, P, K, th, out, stream, flush, steps, warmup):
+    """Mean device time (ms) of `steps` gradient + Hessian evaluations of P."""
+    import torch
+    for _ in range(warmup):
+        q.qoc_eval_grad_hess_dev(P.handle, th.data_ptr(), out.data_ptr())
+    q.qoc_sync_status(P.handle)
+    ev = []
+    for k in range(steps):
+        flush.fill_(float(k))
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        q.qoc_eval_grad_hess_dev(P.handle, th.data_ptr(), out.data_ptr())
+        e1.record(stream)
+        ev.append((e0, e1))
+    torch.cuda.synchronize()
+    q.qoc_sync_status(P.handle)
+    return statistics.mean(a.elapsed_time(b) for a, b in ev)
+
+
+def run_extra_workloads(q, inputs, stream, flush, dev, dist):
+    """The other single-problem workloads and a batch of the uneven recipe,
+    device-resident, each timed with CUDA events (L2 flushed in between):
+    small single (N=4, K=8, J=1000) in both precisions, largest single
+    (N=256, K=128, J=10^4) one evaluation in mixed precision (the policy's
+    sweep precision reported), and the first 32 problems of the batched
+    recipe as one batch against the same problems one by one."""
+    import numpy as np
+    import torch
+    res = {}
+    p1 = inputs.config_problem(1)
+    th1 = torch.tensor(inputs.eval_theta(p1.K, 0), dtype=torch.float64, device=dev)
+    o1 = torch.zeros(1 + p1.K + p1.K ** 2, dtype=torch.float64, device=dev)
+    r1 = {}
+    for name, prec in (("fp64", q.QOC_FP64), ("mixed", q.QOC_MIXED_FP32)):
+        with q.Problem(p1, precision=prec, cuda_stream=stream.cuda_stream) as P:
+            t = max_over_ranks(_timed_evals(q, P, p1.K, th1, o1, stream, flush, 20, 3), dist, dev)
+            r1[name] = {"evals_per_s": 1000.0 / t, "ms": t, "sweep_precision": P.precision()[0]}
+    res["small single N=4 K=8 J=1000"] = r1
+    p5 = inputs.config_problem(5)
+    th5 = torch.tensor(inputs.eval_theta(p5.K, 5), dtype=torch.float64, device=dev)
+    o5 = torch.zeros(1 + p5.K + p5.K ** 2, dtype=torch.float64, device=dev)
+    with q.Problem(p5, precision=q.QOC_MIXED_FP32, cuda_stream=stream.cuda_stream) as P:
+        eff, est = P.precision()
+        t = max_over_ranks(_timed_evals(q, P, p5.K, th5, o5, stream, flush, 1, 0), dist, dev)
+    res["largest single N=256 K=128 J=10000"] = {
+        "precision": "mixed", "sweep_precision": "fp64" if eff == q.QOC_FP64 else "fp32",
+        "binary32_error_estimate": est, "evals_per_s": 1000.0 / t, "ms": t}
+    probs = [inputs.config_problem(3, i) for i in range(32)]
+    Ps = [q.Problem(p, precision=q.QOC_MIXED_FP32) for p in probs]
+    try:
+        with q.Batch(Ps, cuda_stream=stream.cuda_stream) as b:
+            thetas = [inputs.eval_theta(p.K, 7 + k) for k, p in enumerate(probs)]
+            th = torch.tensor(np.concatenate(thetas), dtype=torch.float64, device=dev)
+            out = torch.zeros(b.n_out, dtype=torch.float64, device=dev)
+            q.qoc_batch_eval_grad_hess_dev(b.handle, th.data_ptr(), out.data_ptr())   # eager + graph capture
+            torch.cuda.synchronize()
+            ev = []
+            for k in range(2):
+                flush.fill_(float(k))
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                q.qoc_batch_eval_grad_hess_dev(b.handle, th.data_ptr(), out.data_ptr())
+                e1.record(stream)
+                ev.append((e0, e1))
+            torch.cuda.synchronize()
+            for P in Ps:
+                q.qoc_sync_status(P.handle)
+            tb = max_over_ranks(statistics.mean(a.elapsed_time(c) for a, c in ev), dist, dev)
+            ths = [torch.tensor(t_, dtype=torch.float64, device=dev) for t_ in thetas]
+            outs = [torch.zeros(1 + p.K + p.K ** 2, dtype=torch.float64, device=dev) for p in probs]
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for P, t_, o_ in zip(Ps, ths, outs):
+                q.qoc_eval_grad_hess_dev(P.handle, t_.data_ptr(), o_.data_ptr())
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ts = max_over_ranks(e0.elapsed_time(e1), dist, dev)
+        res["batched recipe, first 32 problems"] = {
+            "problem_evals_per_s": 32 * 1000.0 / tb, "batched_ms": tb, "one_by_one_ms": ts,
+            "speedup_over_one_by_one": ts / tb, "binary64_sweep_problems":
+                sum(P.precision()[0] == q.QOC_FP64 for P in Ps),
+            "N": [p.N for p in probs], "K": [p.K for p in probs], "J": [p.J for p in probs]}
+    finally:
+        for P in Ps:
+            P.close()
+    return res
+
+
+def run_fp64_peak(args):
+    """Binary64 peak of this GPU: the library's FMA-chain kernel and cuBLAS
+    DGEMM (torch.matmul in float64, 8192^3), with the SM clocks sampled."""
+    import torch
+    import paper_2505_00529_gb300 as q
+    from paper_2505_00529_gb300 import build
+    local = env_int("LOCAL_RANK", 0)
+    torch.cuda.set_device(local)
+    build.build()
+    clk = ClockSampler(local, os.path.join(tempfile.mkdtemp(prefix="qoc_clocks_"), "clocks.csv"))
+    with clk:
+        fma = [q.qoc_measure_fp64_rate(c, 5) for c in (1, 2, 4, 8)]
+        n = 8192
+        a = torch.randn(n, n, dtype=torch.float64, device="cuda")
+        b = torch.randn(n, n, dtype=torch.float64, device="cuda")
+        torch.matmul(a, b)
+        torch.cuda.synchronize()
+        best = None
+        for _ in range(3):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            torch.matmul(a, b)
+            e1.record()
+            torch.cuda.synchronize()
+            t = e0.elapsed_time(e1)
+            best = t if best is None else min(best, t)
+    dgemm = 2.0 * n ** 3 / (best * 1e-3) / 1e12
+    print(json.dumps({"metric": "binary64 peak", "fma_chain_tflops": {str(c): f[0] for c, f in zip((1, 2, 4, 8), fma)},
+                      "cublas_dgemm_tflops": dgemm, "dgemm_ms": best, "n": n, "clocks": clk.summary()}), flush=True)
+    return 0
+
+
+# the paper's OLS slopes of log2 wall time against log2 J (Sec. IV-A), context only
+PAPER_SLOPES = {"alg1": {4: 0.9082, 16: 0.9067, 64: 0.9999, 144: 1.001},
+                "alg2": {4: 0.9871, 16: 0.9938, 64: 0.9975, 144: 1.006}}
+
+
+def run_scaling(args):
+    """Wall-time scaling in J (Sec. IV-A, Fig. 1): the maximal model (K = J),
+    N in {4, 16, 64, 144}, J = 2^2 .. 2^10; per (N, J) `scaling_runs` timed
+    evaluations of Alg. 1 (J and gradient) and Alg. 2 (J, gradient, Hessian)
+    at the same theta ~ N(0, 1), through the host API (theta in, results out,
+    as a caller of the library sees them), mean and standard deviation; then
+    the OLS slope of log2(mean time) against log2(J) per N and algorithm."""
+    import numpy as np
+    import torch
+    import paper_2505_00529_gb300 as q
+    from paper_2505_00529_gb300 import build, inputs
+    torch.cuda.set_device(env_int("LOCAL_RANK", 0))
+    build.build()
+    prec = q.QOC_MIXED_FP32 if args.precision == "mixed" else q.QOC_FP64
+    Ns = [int(x) for x in args.scaling_n.split(",")]
+    kappas = list(range(2, 11))
+    rows, slopes = [], {}
+    for N in Ns:
+        t1, t2 = [], []
+        for kap in kappas:
+            J = 2 ** kap
+            prob = inputs.scaling_problem(N, J, seed=100 * N + kap)
+            theta = inputs.eval_theta(J, 7 * N + kap)
+            with q.Problem(prob, precision=prec) as P:
+                for _ in range(3):
+                    P.eval_grad(theta)
+                    P.eval_grad_hess(theta)
+                a1, a2 = [], []
+                for _ in range(args.scaling_runs):
+                    torch.cuda.synchronize()
+                    t0 = time.perf_counter()
+                    P.eval_grad(theta)
+                    a1.append(1000.0 * (time.perf_counter() - t0))
+                    t0 = time.perf_counter()
+                    P.eval_grad_hess(theta)
+                    a2.append(1000.0 * (time.perf_counter() - t0))
+                sweep = P.precision()[0]
+            rows.append({"N": N, "J": J, "alg1_ms": statistics.mean(a1), "alg1_sd": statistics.pstdev(a1),
+                         "alg2_ms": statistics.mean(a2), "alg2_sd": statistics.pstdev(a2),
+                         "sweep_precision": "fp64" if sweep == q.QOC_FP64 else "fp32"})
+            t1.append(statistics.mean(a1))
+            t2.append(statistics.mean(a2))
+        x = np.log2([2.0 ** k for k in kappas])
+        slopes[N] = {"alg1": float(np.polyfit(x, np.log2(t1), 1)[0]),
+                     "alg2": float(np.polyfit(x, np.log2(t2), 1)[0]),
+                     "alg2_over_alg1_at_J1024": t2[-1] / t1[-1]}
+    print(json.dumps({"metric": "wall time vs J, maximal model (log-log OLS slope)", "unit": "ms",
+                      "precision": args.precision, "runs_per_point": args.scaling_runs,
+                      "config": {"workload": "maximal model K=J, alpha=e_1, beta=e_N, diagonal H0 U[-2,0], "
+                                             "symmetric M N(0,0.5^2), dt=0.1, theta ~ N(0,1), host API"},
+                      "slopes": slopes, "paper_slopes_A100_context": PAPER_SLOPES, "points": rows}),
+          flush=True)
+    return 0
+
+
+def run_tr_ratios(args):
+    """Gradient-only (Alg. 1 + BFGS) against exact-Hessian (Alg. 2) trust
+    regions, the comparison of Sec. IV-B (Tables I and II) on synthetic
+    stand-ins for its molecular systems: N in {4, 16} (the sizes of the
+    STO-3G and 6-31G full-CI problems), the maximal model with J = 200 steps
+    of dt = 0.1 (K = J = 200), rho = 1e6 (w_f = 1/2, w_t = rho/2),
+    alpha = e_1, beta = e_N, tolerances delta = epsilon = 1e-10, at most 10^4
+    iterations.  Each trial draws theta0 ~ N(0, 1) and solves from it with
+    both methods; per-trial ratios Alg1/Alg2 of iterations, wall time, final
+    cost, final |grad| and target violation |a_J - beta| are summarised by
+    their mean and (0.05, 0.95) quantiles as in Table II."""
+    import numpy as np
+    import torch
+    import paper_2505_00529_gb300 as q
+    from paper_2505_00529_gb300 import build, inputs
+    torch.cuda.set_device(env_int("LOCAL_RANK", 0))
+    build.build()
+    prec = q.QOC_MIXED_FP32 if args.precision == "mixed" else q.QOC_FP64
+    J, rho = 200, 1e6
+    out = {}
+    for N in (4, 16):
+        base = inputs.scaling_problem(N, J, seed=7000 + N)
+        prob = inputs.Problem(base.H0, base.M, base.alpha, base.beta, base.B, base.dt, 0.5, rho / 2,
+                              name=f"tables_N{N}")
+        rows = []
+        with q.Problem(prob, precision=prec) as P:
+            for t in range(args.tr_trials):
+                th0 = np.random.default_rng(500 + t).normal(size=J)
+                rec = {}
+                for alg, hess in (("alg1", "bfgs"), ("alg2", "exact")):
+                    torch.cuda.synchronize()
+                    t0 = time.perf_counter()
+                    th, info = P.trust_region_solve(th0, gtol=1e-10, xtol=1e-10, max_iter=10000, hessian=hess)
+                    wall = time.perf_counter() - t0
+                    viol = np.sqrt(max(info["J"] - 0.5 * float(th @ th), 0.0) / (rho / 2))
+                    rec[alg] = {"iters": info["iters"], "wall_s": wall, "cost": info["J"],
+                                "grad": info["grad_norm"], "viol": viol, "stop": info["stop"]}
+                rows.append(rec)
+        summ = {}
+        for key in ("iters", "wall_s", "cost", "grad", "viol"):
+            a1 = np.array([r["alg1"][key] for r in rows], float)
+            a2 = np.array([r["alg2"][key] for r in rows], float)
+            ratio = a1 / np.maximum(a2, 1e-300)
+            summ[key] = {"alg1_mean": float(a1.mean()), "alg2_mean": float(a2.mean()),
+                         "ratio_mean": float(ratio.mean()),
+                         "ratio_q05": float(np.quantile(ratio, 0.05)), "ratio_q95": float(np.quantile(ratio, 0.95))}
+        summ["stops"] = {alg: {s_: sum(r[alg]["stop"] == s_ for r in rows) for s_ in ("gtol", "xtol", "max_iter",
+                                                                                 "no_decrease")}
+                         for alg in ("alg1", "alg2")}
+        out[f"N={N}"] = summ
+    print(json.dumps({"metric": "per-trial ratios Alg1 (BFGS) / Alg2 (exact Hessian) of trust-region solves",
+                      "trials": args.tr_trials, "precision": args.precision,
+                      "config": {"workload": "maximal model J=K=200, dt=0.1, rho=1e6, alpha=e_1, beta=e_N, "
+                                             "diagonal H0 U[-2,0], symmetric M N(0,0.5^2), tol 1e-10"},
+                      "results": out}), flush=True)
+    return 0
+
+
+def run_profile(args):
+    """The bench workload only (for ncu): `warmup` + `steps` evaluations of the
+    N=32, K=64, J=4000 problem at library defaults, no extras, no output line."""
+    import torch
+    import paper_2505_00529_gb300 as q
+    from paper_2505_00529_gb300 import build, inputs
+    torch.cuda.set_device(env_int("LOCAL_RANK", 0))
+    build.build()
+    prob = inputs.config_problem(2)
+    theta = inputs.eval_theta(prob.K, 0)
+    prec = q.QOC_MIXED_FP32 if args.precision == "mixed" else q.QOC_FP64
+    with q.Problem(prob, precision=prec) as P:
+        for _ in range(args.warmup + args.steps):
+            P.eval_grad_hess(theta)
     return 0
 
 
@@ -538,11 +823,18 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
-    ap.add_argument("--ref-sample-steps", type=int, default=400)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-tr", action="store_true")
     ap.add_argument("--no-autotune", action="store_true", help="library default launch shapes")
+    ap.add_argument("--no-extra", action="store_true", help="skip the other workloads")
+    ap.add_argument("--fp64-peak", action="store_true", help="measure the binary64 peak and exit")
+    ap.add_argument("--profile", action="store_true", help="evaluations of the bench workload only (for ncu)")
+    ap.add_argument("--scaling", action="store_true", help="wall time vs J on the maximal model (Fig. 1)")
+    ap.add_argument("--tr-ratios", action="store_true", help="Alg. 1 + BFGS vs Alg. 2 trust regions (Tables I/II)")
+    ap.add_argument("--tr-trials", type=int, default=10)
+    ap.add_argument("--scaling-runs", type=int, default=20)
+    ap.add_argument("--scaling-n", default="4,16,64,144")
     ap.add_argument("--warm-start", action="store_true", help="run the learned warm-start experiment")
     ap.add_argument("--batch", action="store_true", help="run the batched uneven-problem measurement")
     ap.add_argument("--batch-size", type=int, default=256)
@@ -554,6 +846,14 @@ def main():
     ap.add_argument("--ws-workers", type=int, default=8)
     ap.add_argument("--ws-gtol", type=float, default=1e-5)
     args = ap.parse_args()
+    if args.fp64_peak:
+        return run_fp64_peak(args)
+    if args.profile:
+        return run_profile(args)
+    if args.scaling:
+        return run_scaling(args)
+    if args.tr_ratios:
+        return run_tr_ratios(args)
     if args.warm_start:
         return run_warm_start(args)
     if args.batch:

@@ -56,12 +56,31 @@ typedef enum {
 
 /* Arithmetic of the per-step propagator products (the time-stepped sweeps).
  *   QOC_FP64       : every operation in binary64 ("plain FP64").
- *   QOC_MIXED_FP32 : propagator-times-panel products in binary32 on the
- *                    increment D_j = exp(-i dt (H_j - m)) - I with the state
- *                    carried as an unevaluated float pair; eigendecomposition,
+ *   QOC_MIXED_FP32 : mixed precision held to a relative error of 1e-6 in J,
+ *                    the gradient and the Hessian.  The propagator-times-panel
+ *                    products run in binary32 on the increment
+ *                    D_j = exp(-i dt (H_j - m)) - I with the state carried as
+ *                    an unevaluated float pair, while the eigendecomposition,
  *                    divided differences, contractions and the gradient /
- *                    Hessian accumulation stay binary64. */
-typedef enum { QOC_FP64 = 0, QOC_MIXED_FP32 = 1 } qoc_precision;
+ *                    Hessian accumulation stay binary64 -- unless the a priori
+ *                    estimate of the binary32 rounding error (below) exceeds
+ *                    1e-6, in which case the sweeps run in binary64 as with
+ *                    QOC_FP64.  qoc_get_precision reports which was chosen.
+ *   QOC_MIXED_FP32_ALWAYS : binary32 increments whatever the estimate (the
+ *                    error then follows the estimate and may exceed 1e-6).
+ *
+ * The binary32 rounding of the increments accumulates like a random walk
+ * over the J steps and the N-term sums of every product, so the relative
+ * error of the Hessian (the most sensitive result) is estimated as
+ *     err = 0.3 eps32 dt sigma sqrt(J N b),   eps32 = 2^-24,
+ * b the time-block length (qoc_set_block_steps) and sigma the rms spread of
+ * the spectra of H_j - m for theta ~ N(0, I) (the random start of Sec. IV-A):
+ *     sigma^2 = ( |H0 - m I|_F^2 + |M|_F^2 mean_j |b_j|^2 ) / N,
+ * with m = tr(H0)/N and b_j the rows of the basis.  The constant 0.3 is the
+ * measured one (0.24 at N = 32, J = 4000; 0.28 at N = 256, J = 10^4, block
+ * lengths 1 to 8).  The choice is made at qoc_create_problem with the default
+ * block length. */
+typedef enum { QOC_FP64 = 0, QOC_MIXED_FP32 = 1, QOC_MIXED_FP32_ALWAYS = 2 } qoc_precision;
 
 /* Which exact form of the Hessian to assemble (both are Eq. d2Ldf2):
  *   QOC_HESS_SECOND_ORDER_ADJOINT : Alg. 2 -- forward tangent panel S_j and
@@ -106,9 +125,10 @@ qoc_status qoc_set_eig_method(qoc_problem* p, int method);
  * block propagators, propagated sources and the contractions at the
  * intermediate steps computed in parallel over blocks.  1 <= steps <= 8;
  * 1 selects one dependent step per time step.  Default when J >= 16: 8 for
- * QOC_FP64, 4 for QOC_MIXED_FP32 (the binary32 rounding of the block
- * propagator grows like sqrt(steps); 4 keeps the mixed results within 1e-6
- * of binary64); 1 when J < 16.  QOC_EINVAL otherwise. */
+ * binary64 sweeps, 4 for binary32 ones (the binary32 rounding of the block
+ * propagator grows like sqrt(steps)); 1 when J < 16.  QOC_EINVAL otherwise,
+ * and for a QOC_MIXED_FP32 problem on binary32 sweeps when the new length
+ * would raise the error estimate above 1e-6. */
 qoc_status qoc_set_block_steps(qoc_problem* p, int steps);
 
 /* Panel columns per CTA of the tangent and second-order adjoint sweeps
@@ -120,6 +140,12 @@ qoc_status qoc_set_block_steps(qoc_problem* p, int steps);
  * ordered differently (results agree to rounding).
  * QOC_EUNSUPPORTED when 32 ceil(N/8) kc > 1024 threads. */
 qoc_status qoc_set_panel_columns(qoc_problem* p, int kc);
+
+/* The arithmetic a problem's sweeps use (*effective: QOC_FP64 or
+ * QOC_MIXED_FP32) and the estimated relative error of binary32 increments
+ * at the current block length (*estimate, see qoc_precision; computed for
+ * every precision).  Either pointer may be NULL. */
+qoc_status qoc_get_precision(const qoc_problem* p, int* effective, double* estimate);
 
 /* Replace the target state beta (N complex, interleaved host doubles). */
 qoc_status qoc_set_target(qoc_problem* p, const double* a_target);
@@ -170,6 +196,22 @@ typedef struct {
 qoc_status qoc_trust_region_solve(qoc_problem* p, const double* theta0,
                                   const qoc_tr_options* opt, double* theta_out,
                                   qoc_tr_report* report);
+
+/* Gradient-only trust region (Alg. 1 with a quasi-Newton model: the
+ * baseline of Sec. IV-B, where the optimiser builds a Hessian approximation
+ * from gradients by BFGS updates).  The iteration of qoc_trust_region_solve
+ * with the exact Hessian replaced by B: B = I until the first trial with
+ * positive curvature y^T s, which first sets B = (y^T y / y^T s) I; every
+ * evaluated trial (accepted or not) then updates
+ *   B <- B - (B s)(B s)^T / (s^T B s) + y y^T / (y^T s)
+ * with s its step and y its gradient minus the current one, skipped unless
+ * y^T s > 1e-8 |s| |y| (Nocedal & Wright, Eq. 6.19).  Each trial evaluation
+ * is J and the gradient (qoc_eval_grad's work); no Hessian is evaluated.
+ * The report's n_eval_J counts the trial evaluations and n_eval_gh is 0.
+ * Arguments and statuses as qoc_trust_region_solve. */
+qoc_status qoc_trust_region_solve_bfgs(qoc_problem* p, const double* theta0,
+                                       const qoc_tr_options* opt, double* theta_out,
+                                       qoc_tr_report* report);
 
 /* Diagnostics of the last evaluation (host doubles):
  *   out[0] = max_j | |a_j| - 1 |   (norm drift of the propagated state)
@@ -269,12 +311,13 @@ qoc_status qoc_mlp_get_params(const qoc_mlp* m, float* params);
 void qoc_mlp_destroy(qoc_mlp* m);
 
 /* ---------------------------------------------------------------------------
- * Batches of uneven problems (different N, K, J; one precision; time
+ * Batches of uneven problems (different N, K, J and sweep precision; time
  * blocking on).  One batched evaluation = the gradient and Hessian of every
  * problem at its own theta: the parallel phases of each problem run on that
  * problem's stream, each of the four sequential sweeps runs as one launch
- * per sweep kernel over all problems that take it (binary32 N <= 32,
- * binary32 N <= 64, the rest; side by side on their own streams), and the
+ * per sweep precision and kernel over all problems that take it (binary32
+ * N <= 32, binary32 N <= 64, the general binary32 one, binary64; side by
+ * side on their own streams), and the
  * whole evaluation is captured once into a CUDA graph (qoc_batch_set_graph(b,
  * 0) disables the graph).  Every problem takes the kernel a single
  * evaluation of it takes, so batched results equal single ones bit for bit.
@@ -290,6 +333,37 @@ qoc_status qoc_batch_eval_grad_hess(qoc_batch* b, const double* thetas, double* 
 /* device-pointer form: enqueues on the batch stream and returns */
 qoc_status qoc_batch_eval_grad_hess_dev(qoc_batch* b, const double* thetas_dev, double* outs_dev);
 void qoc_batch_destroy(qoc_batch* b);
+
+/* Batched exact-Hessian trust region (Sec. IV-B runs one solve per trial;
+ * the batching pattern runs many at once): every problem takes the basic
+ * trust region of qoc_trust_region_solve from its own theta0 with the same
+ * options, all advancing together.  One iteration is: on the device, per
+ * problem, the gtol test, the exact subproblem and the trial point; one
+ * batched gradient + Hessian evaluation of every trial point (a qoc_batch
+ * with its CUDA graph); the eigendecomposition of each trial Hessian; on the
+ * device, the ratio test, radius update, acceptance (theta, J, gradient,
+ * Hessian and its eigendecomposition taken over from the trial) and the
+ * xtol / iteration-cap tests.  The host reads the problems' states once per
+ * iteration for the whole batch and, when some have stopped, rebuilds the
+ * batch over the others.  Each trial point is evaluated with its gradient
+ * and Hessian, so an accepted step costs no further evaluation; the
+ * iterates are those of qoc_trust_region_solve.
+ *   problems  n distinct problems with time blocking (steps >= 16) and
+ *             K <= 256; the caller keeps them alive, unused meanwhile.
+ *   theta0s   concatenation of the starting points (sum K_i host doubles).
+ *   theta_out concatenation of the final points (may alias theta0s).
+ *   reports   n reports: iters, n_eval_J (trial evaluations), n_eval_gh
+ *             (1 + accepted steps), final J, |grad|, radius, stop_reason
+ *             (0 gtol, 1 xtol, 2 max_iter, 3 no predicted decrease,
+ *             4 device failure of that problem's evaluation).
+ *   cuda_stream  stream to run on, or NULL for a temporary one.
+ * Returns QOC_OK when every problem stopped by 0, 1 or 3; QOC_ENOTCONV if
+ * one hit max_iter; the failing problem's status (QOC_ETIMEOUT, ...) if one
+ * failed (the others' results are still written).  Allocates a small state
+ * array and each problem's trial eigendecomposition for the call. */
+qoc_status qoc_batch_trust_region_solve(qoc_problem* const* problems, int n, const double* theta0s,
+                                        const qoc_tr_options* opt, double* theta_out,
+                                        qoc_tr_report* reports, void* cuda_stream);
 
 /* ---------------------------------------------------------------------------
  * Gradient and Hessian assembly that allocates no device memory.
@@ -334,6 +408,14 @@ qoc_status qoc_assemble_grad_hess_noalloc(int steps, int K, const double* basis_
                                           const double* g_dev, const double* c_dev, const double* U_dev,
                                           const double* V_dev, double w_ctrl, double* out_dev,
                                           void* cuda_stream);
+
+/* Measured binary64 FMA rate of the current device (no counterpart in the
+ * paper; the denominator of the roofline of the binary64-bound kernels):
+ * a kernel of independent FMA chains on ctas_per_sm x 256 threads per SM,
+ * timed `repeats` times with CUDA events after one warm-up launch; the
+ * fastest launch gives *tflops (2 flops per FMA) and *ms (may be NULL).
+ * Allocates and frees a small output buffer; synchronises the device. */
+qoc_status qoc_measure_fp64_rate(int ctas_per_sm, int repeats, double* tflops, double* ms);
 
 /* Bytes of device memory the problem holds. */
 size_t qoc_device_bytes(const qoc_problem* p);

@@ -151,10 +151,15 @@ def frechet1(W, lam, M, dt):
     return np.einsum("jpr,jrs,jqs->jpq", W, G1 * Mt, W, optimize=True)
 
 
-def frechet2(W, lam, M, dt, chunk=64):
+def frechet2(W, lam, M, dt, chunk=None):
     """G2_j = d^2 U_j / df_j^2 = -dt^2 d^2exp_{Z_j}[M, M] = W X W^T with
-    X_pq = 2 sum_r M~_pr M~_rq phi[lambda_p, lambda_r, lambda_q]."""
+    X_pq = 2 sum_r M~_pr M~_rq phi[lambda_p, lambda_r, lambda_q].
+    Steps are taken `chunk` at a time (each step on its own; by default as
+    many as keep the [chunk, N, N, N] divided-difference array near 2^22
+    entries)."""
     J, N = lam.shape
+    if chunk is None:
+        chunk = max(1, min(64, (1 << 22) // N ** 3))
     out = np.empty((J, N, N), dtype=np.complex128)
     Mt = rotated_dipoles(W, M)
     for j0 in range(0, J, chunk):
@@ -428,3 +433,69 @@ def trust_region_solve(prob, theta0, gtol=1e-10, xtol=1e-10, radius0=1.0,
             break
     return theta, {"iters": it, "J": Jc, "grad_norm": float(np.linalg.norm(g)),
                    "stop": stop, "n_eval_J": n_J, "n_eval_gh": n_gh, "hess": H}
+
+
+# ---------------------------------------------------------------------------
+# Alg. 1 with a quasi-Newton trust region (Sec. IV-B: gradients alone, the
+# optimiser building its Hessian approximation by BFGS updates)
+# ---------------------------------------------------------------------------
+
+def bfgs_update(Bk, s, y, min_curvature=1e-8):
+    """BFGS update of a Hessian approximation (Nocedal & Wright, Eq. 6.19):
+    B+ = B - (B s)(B s)^T / (s^T B s) + y y^T / (y^T s).  Skipped (B returned
+    unchanged) when the curvature y^T s is not above min_curvature |s| |y|,
+    the condition under which the update keeps B positive definite."""
+    sy = float(y @ s)
+    if not sy > min_curvature * np.linalg.norm(s) * np.linalg.norm(y):
+        return Bk
+    Bs = Bk @ s
+    return Bk - np.outer(Bs, Bs) / float(s @ Bs) + np.outer(y, y) / sy
+
+
+def trust_region_solve_bfgs(prob, theta0, gtol=1e-10, xtol=1e-10, radius0=1.0,
+                            radius_max=1e3, max_iter=10000, eta=0.1):
+    """The trust region of trust_region_solve with the exact Hessian replaced
+    by a BFGS approximation built from Alg. 1 gradients: B = I until the
+    first update, which starts from (y^T y / y^T s) I; every evaluated trial
+    point updates B with s = its step and y = its gradient minus the current
+    one (accepted or not).  Returns (theta, info)."""
+    theta = np.array(theta0, float)
+    K = theta.size
+    radius = radius0
+    Jc, g = eval_grad(prob, theta)
+    Bk = np.eye(K)
+    scaled = False
+    n_J = 0
+    stop = "max_iter"
+    it = 0
+    for it in range(1, max_iter + 1):
+        if np.linalg.norm(g) < gtol:
+            stop = "gtol"
+            it -= 1
+            break
+        s, _ = tr_subproblem(g, Bk, radius)
+        pred = -(g @ s + 0.5 * s @ Bk @ s)
+        if pred <= 0:
+            stop = "no_decrease"
+            break
+        Jt, gt = eval_grad(prob, theta + s)
+        n_J += 1
+        y = gt - g
+        if not scaled and y @ s > 0:
+            Bk = (y @ y) / (y @ s) * np.eye(K)
+            scaled = True
+        Bk = bfgs_update(Bk, s, y)
+        rho = (Jc - Jt) / pred
+        ns = np.linalg.norm(s)
+        if rho < 0.25:
+            radius = 0.25 * radius
+        elif rho > 0.75 and abs(ns - radius) <= 1e-8 * radius:
+            radius = min(2.0 * radius, radius_max)
+        if rho > eta:
+            theta = theta + s
+            Jc, g = Jt, gt
+        if radius < xtol:
+            stop = "xtol"
+            break
+    return theta, {"iters": it, "J": Jc, "grad_norm": float(np.linalg.norm(g)),
+                   "stop": stop, "n_eval_grad": n_J + 1, "hess_approx": Bk}

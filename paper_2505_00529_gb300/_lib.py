@@ -14,7 +14,7 @@ import numpy as np
 from . import build as _build
 
 QOC_OK, QOC_EINVAL, QOC_ENOMEM, QOC_ECUDA, QOC_ENUMERIC, QOC_ENOTCONV, QOC_ETIMEOUT, QOC_EUNSUPPORTED = range(8)
-QOC_FP64, QOC_MIXED_FP32 = 0, 1
+QOC_FP64, QOC_MIXED_FP32, QOC_MIXED_FP32_ALWAYS = 0, 1, 2
 QOC_HESS_SECOND_ORDER_ADJOINT, QOC_HESS_TANGENT = 0, 1
 QOC_EIG_REFINED, QOC_EIG_JACOBI_FP64 = 0, 1
 (QOC_BUF_F, QOC_BUF_EIGVAL, QOC_BUF_EIGVEC, QOC_BUF_STATE, QOC_BUF_COSTATE, QOC_BUF_G, QOC_BUF_C,
@@ -32,7 +32,8 @@ EXPORTS = [
     "qoc_last_error", "qoc_batch_create", "qoc_batch_set_graph", "qoc_batch_eval_grad_hess",
     "qoc_batch_eval_grad_hess_dev", "qoc_batch_destroy", "qoc_assemble_noalloc_scratch_doubles",
     "qoc_assemble_grad_hess_noalloc", "qoc_get_phase_times", "qoc_get_eig_stats",
-    "qoc_set_panel_columns",
+    "qoc_set_panel_columns", "qoc_get_precision", "qoc_measure_fp64_rate",
+    "qoc_batch_trust_region_solve", "qoc_trust_region_solve_bfgs",
 ]
 
 
@@ -80,6 +81,8 @@ def lib() -> C.CDLL:
         L.qoc_set_eig_method.argtypes = [C.c_void_p, C.c_int]
         L.qoc_set_block_steps.argtypes = [C.c_void_p, C.c_int]
         L.qoc_set_panel_columns.argtypes = [C.c_void_p, C.c_int]
+        L.qoc_get_precision.argtypes = [C.c_void_p, C.POINTER(C.c_int), _dp]
+        L.qoc_measure_fp64_rate.argtypes = [C.c_int, C.c_int, _dp, _dp]
         L.qoc_eval_J.argtypes = [C.c_void_p, _dp, _dp]
         L.qoc_eval_grad.argtypes = [C.c_void_p, _dp, _dp, _dp]
         L.qoc_eval_grad_hess.argtypes = [C.c_void_p, _dp, _dp, _dp, _dp]
@@ -87,6 +90,8 @@ def lib() -> C.CDLL:
         L.qoc_sync_status.argtypes = [C.c_void_p]
         L.qoc_trust_region_solve.argtypes = [C.c_void_p, _dp, C.POINTER(TrOptions), _dp,
                                              C.POINTER(TrReport)]
+        L.qoc_trust_region_solve_bfgs.argtypes = [C.c_void_p, _dp, C.POINTER(TrOptions), _dp,
+                                                  C.POINTER(TrReport)]
         L.qoc_get_diagnostics.argtypes = [C.c_void_p, _dp]
         L.qoc_get_phase_times.argtypes = [C.c_void_p, _dp, C.c_int]
         L.qoc_get_eig_stats.argtypes = [C.c_void_p, _dp]
@@ -108,6 +113,8 @@ def lib() -> C.CDLL:
         L.qoc_batch_eval_grad_hess.argtypes = [C.c_void_p, _dp, _dp]
         L.qoc_batch_eval_grad_hess_dev.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p]
         L.qoc_batch_destroy.argtypes = [C.c_void_p]
+        L.qoc_batch_trust_region_solve.argtypes = [C.POINTER(C.c_void_p), C.c_int, _dp, C.POINTER(TrOptions),
+                                                   _dp, C.POINTER(TrReport), C.c_void_p]
         L.qoc_batch_destroy.restype = None
         L.qoc_assemble_noalloc_scratch_doubles.argtypes = [C.c_int, C.c_int]
         L.qoc_assemble_noalloc_scratch_doubles.restype = C.c_size_t
@@ -190,6 +197,14 @@ def qoc_set_panel_columns(h, kc):
     _check(lib().qoc_set_panel_columns(C.c_void_p(h), int(kc)), "qoc_set_panel_columns")
 
 
+def qoc_get_precision(h):
+    """(effective sweep precision, estimated binary32 error at the current block length)"""
+    eff = C.c_int(0)
+    est = C.c_double(0.0)
+    _check(lib().qoc_get_precision(h, C.byref(eff), C.byref(est)), "qoc_get_precision")
+    return int(eff.value), float(est.value)
+
+
 def qoc_enable_timing(h, on=True):
     _check(lib().qoc_enable_timing(C.c_void_p(h), int(bool(on))), "qoc_enable_timing")
 
@@ -231,18 +246,48 @@ def qoc_sync_status(h):
 
 
 def qoc_trust_region_solve(h, theta0, gtol=1e-10, xtol=1e-10, radius0=1.0, radius_max=1e3,
-                           eta=0.1, max_iter=10000):
+                           eta=0.1, max_iter=10000, hessian="exact"):
+    """hessian="exact" (Alg. 2) or "bfgs" (Alg. 1 gradients, BFGS model)."""
     th = _f64(theta0)
     out = np.zeros_like(th)
     opt = TrOptions(gtol, xtol, radius0, radius_max, eta, int(max_iter))
     rep = TrReport()
-    s = lib().qoc_trust_region_solve(C.c_void_p(h), _ptr(th), C.byref(opt), _ptr(out), C.byref(rep))
+    fn = {"exact": lib().qoc_trust_region_solve, "bfgs": lib().qoc_trust_region_solve_bfgs}[hessian]
+    s = fn(C.c_void_p(h), _ptr(th), C.byref(opt), _ptr(out), C.byref(rep))
     if s not in (QOC_OK, QOC_ENOTCONV):
-        raise QocError(s, "qoc_trust_region_solve")
+        raise QocError(s, "qoc_trust_region_solve" + ("" if hessian == "exact" else "_bfgs"))
     info = {k: getattr(rep, k) for k, _ in TrReport._fields_}
     info["stop"] = {0: "gtol", 1: "xtol", 2: "max_iter", 3: "no_decrease"}[rep.stop_reason]
     info["status"] = s
     return out, info
+
+
+_STOP = {0: "gtol", 1: "xtol", 2: "max_iter", 3: "no_decrease", 4: "failed"}
+
+
+def qoc_batch_trust_region_solve(handles, theta0s, gtol=1e-10, xtol=1e-10, radius0=1.0, radius_max=1e3,
+                                 eta=0.1, max_iter=10000, cuda_stream=None):
+    """Batched trust region over problem handles; theta0s: list of per-problem
+    starting points.  Returns (list of theta*, list of report dicts, status)."""
+    n = len(handles)
+    Ks = [len(t) for t in theta0s]
+    flat = np.concatenate([_f64(t).ravel() for t in theta0s])
+    out = np.zeros_like(flat)
+    arr = (C.c_void_p * n)(*[C.c_void_p(h) for h in handles])
+    reps = (TrReport * n)()
+    opt = TrOptions(gtol, xtol, radius0, radius_max, eta, int(max_iter))
+    s = lib().qoc_batch_trust_region_solve(arr, n, _ptr(flat), C.byref(opt), _ptr(out), reps,
+                                           C.c_void_p(cuda_stream) if cuda_stream else None)
+    if s not in (QOC_OK, QOC_ENOTCONV):
+        raise QocError(s, "qoc_batch_trust_region_solve")
+    thetas, infos, o = [], [], 0
+    for k, K in enumerate(Ks):
+        thetas.append(out[o:o + K].copy())
+        o += K
+        info = {f: getattr(reps[k], f) for f, _ in TrReport._fields_}
+        info["stop"] = _STOP[reps[k].stop_reason]
+        infos.append(info)
+    return thetas, infos, s
 
 
 def qoc_get_diagnostics(h):
@@ -406,6 +451,15 @@ def qoc_assemble_grad_hess_noalloc(steps, K, basis_dev, f_dev, g_dev, c_dev, U_d
         raise QocError(s, "qoc_assemble_grad_hess_noalloc" + (f" [{reason}]" if reason and s != QOC_ECUDA else ""))
 
 
+def qoc_measure_fp64_rate(ctas_per_sm=4, repeats=5):
+    """(TFLOP/s, ms) of the fastest of `repeats` binary64 FMA-chain launches."""
+    tf = C.c_double(0.0)
+    ms = C.c_double(0.0)
+    _check(lib().qoc_measure_fp64_rate(int(ctas_per_sm), int(repeats), C.byref(tf), C.byref(ms)),
+           "qoc_measure_fp64_rate")
+    return float(tf.value), float(ms.value)
+
+
 def qoc_device_bytes(h) -> int:
     return int(lib().qoc_device_bytes(C.c_void_p(h)))
 
@@ -468,6 +522,10 @@ class Problem:
 
     def diagnostics(self):
         return qoc_get_diagnostics(self.handle)
+
+    def precision(self):
+        """(effective sweep precision, estimated binary32 error) -- see qoc_get_precision"""
+        return qoc_get_precision(self.handle)
 
     def close(self):
         if self.handle:

@@ -36,6 +36,8 @@ struct qoc_problem {
   int N = 0, K = 0, J = 0, Kp = 0;
   double dt = 0, w_f = 0, w_t = 0, mshift = 0;
   int precision = 0, hess_method = QOC_HESS_SECOND_ORDER_ADJOINT, eig_method = QOC_EIG_REFINED;
+  int requested_precision = 0;          // as passed to qoc_create_problem
+  double err_sigma = 0;                 // sigma of the binary32 error estimate (see qoc.h)
   int refine_sweeps = 2;
   double angle_tol = 1e-13;
   cudaStream_t stream = nullptr;
@@ -128,6 +130,37 @@ bool symmetric(const double* A, int N) {
 }
 
 double2 cexpi_h(double x) { return make_double2(std::cos(x), std::sin(x)); }
+
+// Rms spread of the spectra of H_j - m for theta ~ N(0, I):
+// sigma^2 = (|H0 - m I|_F^2 + |M|_F^2 mean_j |b_j|^2) / N  (see qoc_precision in qoc.h)
+double spectral_sigma(int N, const double* H0, const double* M, const double* basis, int K, int J,
+                      double m) {
+  double a = 0, c = 0, s2 = 0;
+  for (int i = 0; i < N; ++i)
+    for (int k = 0; k < N; ++k) {
+      const double h = H0[i * N + k] - (i == k ? m : 0.0);
+      a += h * h;
+      c += M[i * N + k] * M[i * N + k];
+    }
+  for (size_t e = 0; e < (size_t)J * K; ++e) s2 += basis[e] * basis[e];
+  s2 /= (double)J;
+  return std::sqrt((a + c * s2) / N);
+}
+
+// estimated relative error of binary32 increments at block length bs
+constexpr double kMixedTarget = 1e-6;
+double mixed_error_estimate(const qoc_problem* p, int bs) {
+  return 0.3 * 5.9604644775390625e-8 * p->dt * p->err_sigma *
+         std::sqrt((double)p->J * (double)p->N * (double)(bs < 1 ? 1 : bs));
+}
+
+// Relaxed finish of the eigenvector refinement for binary32 sweeps: their
+// results need the eigendecomposition's residual only to ~1e-9 |H| (binary32
+// increments round at 6e-8), which the first binary64 Ogita-Aishima update
+// from the binary32 Jacobi start reaches on most steps (orthogonality defect
+// <= 3e-5, whose square is what the update leaves); binary64 sweeps refine
+// to the binary64 floor.
+double eig_finish_tol(const qoc_problem* p) { return p->precision == QOC_MIXED_FP32 ? 3e-5 : 0.0; }
 
 // panel columns per CTA: one by default, which spreads a panel over K SMs
 // (binary64 is throughput-limited per SM; the binary32 sweep is latency-bound
@@ -304,7 +337,7 @@ qoc_status enqueue_eval(qoc_problem* p, const double* theta_dev, int order, doub
   QOC_TRY(launch_eig(p->H0, p->M, p->f, N, J, p->W, p->eig, p->status,
                      p->eig_method == QOC_EIG_JACOBI_FP64 ? EIG_JACOBI_FP64 : EIG_REFINED,
                      p->refine_sweeps, p->angle_tol, st, p->ws[0], p->timing ? p->ev[8] : nullptr,
-                     p->timing ? p->eigstats : nullptr));
+                     p->timing ? p->eigstats : nullptr, eig_finish_tol(p)));
   if (p->timing) cudaEventRecord(p->ev[1], st);
   QOC_TRY(launch_prep(p->W, p->eig, p->M, N, J, p->dt, p->mshift, p->D, p->dstride, d_fp64, PREP_D,
                       p->Ptil, p->Xp, nullptr, p->status, st, p->ws[0]));
@@ -472,7 +505,8 @@ qoc_status qoc_create_problem(int N, const double* H0, const double* M, const do
   if (!(dt > 0) || !std::isfinite(dt) || !(w_ctrl >= 0) || !(w_term >= 0) ||
       !std::isfinite(w_ctrl) || !std::isfinite(w_term))
     return QOC_EINVAL;
-  if (precision != QOC_FP64 && precision != QOC_MIXED_FP32) return QOC_EINVAL;
+  if (precision != QOC_FP64 && precision != QOC_MIXED_FP32 && precision != QOC_MIXED_FP32_ALWAYS)
+    return QOC_EINVAL;
   const size_t NN = (size_t)N * N;
   if (!finite_all(H0, NN) || !finite_all(M, NN) || !finite_all(a0, 2 * (size_t)N) ||
       !finite_all(a_target, 2 * (size_t)N) || !finite_all(basis, (size_t)steps * K))
@@ -482,7 +516,7 @@ qoc_status qoc_create_problem(int N, const double* H0, const double* M, const do
   qoc_problem* p = new (std::nothrow) qoc_problem();
   if (!p) return QOC_ENOMEM;
   p->N = N; p->K = K; p->J = steps; p->Kp = (K + 3) / 4 * 4;
-  p->dt = dt; p->w_f = w_ctrl; p->w_t = w_term; p->precision = precision;
+  p->dt = dt; p->w_f = w_ctrl; p->w_t = w_term; p->requested_precision = precision;
   // the eigendecomposition is binary64-accurate on both paths: refinement
   // until W is orthonormal to the binary64 floor (at most 4 updates), then a
   // clean-up of every rotation angle above 1e-13 (smaller angles move the
@@ -495,6 +529,14 @@ qoc_status qoc_create_problem(int N, const double* H0, const double* M, const do
   for (int i = 0; i < N; ++i) tr += H0[i * N + i];
   p->mshift = tr / N;
   const int J = steps;
+  // precision policy: binary32 increments unless their estimated error at
+  // the default block length exceeds the mixed-precision target
+  p->err_sigma = spectral_sigma(N, H0, M, basis, K, J, p->mshift);
+  if (precision == QOC_MIXED_FP32_ALWAYS) p->precision = QOC_MIXED_FP32;
+  else if (precision == QOC_MIXED_FP32)
+    p->precision = mixed_error_estimate(p, J >= 16 ? 4 : 1) <= kMixedTarget ? QOC_MIXED_FP32 : QOC_FP64;
+  else p->precision = QOC_FP64;
+  precision = p->precision;
   const int mixed = precision == QOC_MIXED_FP32;
   p->dstride = ((mixed ? 8 : 16) * NN + 15) / 16 * 16;
   p->vstride = ((mixed ? 8 : 16) * (size_t)N + 15) / 16 * 16;
@@ -656,8 +698,23 @@ qoc_status qoc_set_eig_method(qoc_problem* p, int method) {
   return QOC_OK;
 }
 
+qoc_status qoc_get_precision(const qoc_problem* p, int* effective, double* estimate) {
+  if (!p) return QOC_EINVAL;
+  if (effective) *effective = p->precision;
+  if (estimate) *estimate = mixed_error_estimate(p, p->bs);
+  return QOC_OK;
+}
+
 qoc_status qoc_set_block_steps(qoc_problem* p, int steps) {
   if (!p || steps < 1 || steps > 8 || (steps > 1 && p->J < steps)) return QOC_EINVAL;
+  if (p->requested_precision == QOC_MIXED_FP32 && p->precision == QOC_MIXED_FP32 &&
+      mixed_error_estimate(p, steps) > kMixedTarget) {
+    std::snprintf(g_last_error, sizeof(g_last_error),
+                  "qoc_set_block_steps: %d steps per block raise the binary32 error estimate to %.2e, "
+                  "above the mixed-precision target %.0e", steps, mixed_error_estimate(p, steps),
+                  kMixedTarget);
+    return QOC_EINVAL;
+  }
   p->bs = steps;
   p->nblk = (p->J + steps - 1) / steps;
   return QOC_OK;
@@ -900,31 +957,107 @@ qoc_status qoc_trust_region_solve(qoc_problem* p, const double* theta0, const qo
   return stop == 2 ? QOC_ENOTCONV : QOC_OK;
 }
 
+qoc_status qoc_trust_region_solve_bfgs(qoc_problem* p, const double* theta0, const qoc_tr_options* opt,
+                                       double* theta_out, qoc_tr_report* report) {
+  if (!p || !theta0 || !opt || !theta_out || !report) return QOC_EINVAL;
+  if (!p->trwork) return QOC_EUNSUPPORTED;
+  if (!(opt->radius0 > 0) || !(opt->radius_max >= opt->radius0) || opt->max_iter < 1 ||
+      !(opt->eta >= 0 && opt->eta < 0.25) || !(opt->gtol >= 0) || !(opt->xtol >= 0))
+    return QOC_EINVAL;
+  if (!finite_all(theta0, p->K)) return QOC_EINVAL;
+  const int K = p->K;
+  cudaStream_t st = p->stream;
+  std::memset(report, 0, sizeof(*report));
+  double radius = opt->radius0;
+  // the model Hessian B sits in the Hessian slot of out (gradient-only
+  // evaluations leave it alone); the trial's Hessian slot is the update's
+  // scratch; trinfo[4] flags the first (scaling) update
+  double* Bm = p->out + 1 + K;
+  std::memcpy(p->hbuf, theta0, 8 * (size_t)K);
+  QOC_TRY(cudaMemcpyAsync(p->theta, p->hbuf, 8 * (size_t)K, cudaMemcpyHostToDevice, st));
+  QOC_TRY(cudaMemsetAsync(p->trinfo + 4, 0, sizeof(double), st));
+  qoc_status s = enqueue_eval(p, p->theta, 1, p->out);
+  if (s != QOC_OK) return s;
+  QOC_TRY(launch_set_identity(Bm, K, st));
+  double* hs = p->hbuf + K;
+  int it = 0, stop = 2;
+  for (it = 1; it <= opt->max_iter; ++it) {
+    QOC_TRY(launch_eig(Bm, p->trzero, p->trzero, K, 1, p->trwork + 3 * K, p->trwork + 2 * K, p->status,
+                       EIG_JACOBI_FP64, 0, 0.0, st, p->ws[0]));
+    QOC_TRY(launch_tr_subproblem(p->out, K, radius, p->trwork, p->trstep, p->trinfo, p->status, st));
+    QOC_TRY(launch_axpy(p->theta, p->trstep, K, p->theta_trial, st));
+    s = enqueue_eval(p, p->theta_trial, 1, p->out_trial);
+    if (s != QOC_OK) return s;
+    QOC_TRY(launch_bfgs_update(Bm, p->trstep, p->out + 1, p->out_trial + 1, K, p->trinfo + 4, 1e-8,
+                               p->out_trial + 1 + K, st));
+    QOC_TRY(cudaMemcpyAsync(hs, p->trinfo, 4 * sizeof(double), cudaMemcpyDeviceToHost, st));
+    QOC_TRY(cudaMemcpyAsync(hs + 4, p->out_trial, sizeof(double), cudaMemcpyDeviceToHost, st));
+    QOC_TRY(cudaMemcpyAsync(hs + 5, p->out, sizeof(double), cudaMemcpyDeviceToHost, st));
+    QOC_TRY(cudaMemcpyAsync(p->hstatus, p->status, sizeof(int), cudaMemcpyDeviceToHost, st));
+    QOC_TRY(cudaMemsetAsync(p->status, 0, sizeof(int), st));
+    QOC_TRY(cudaStreamSynchronize(st));
+    s = device_status(p);
+    if (s == QOC_ETIMEOUT || s == QOC_EUNSUPPORTED) return s;
+    const double pred = hs[0], snorm = hs[1], gnorm = hs[3], Jt = hs[4], Jc = hs[5];
+    const bool trial_ok = s == QOC_OK && std::isfinite(Jt);
+    report->n_eval_J++;
+    report->grad_norm = gnorm;
+    if (gnorm < opt->gtol) { stop = 0; --it; report->n_eval_J--; break; }
+    if (!(pred > 0) || !std::isfinite(pred)) { stop = 3; break; }
+    const double rho = trial_ok ? (Jc - Jt) / pred : -1.0;
+    if (rho < 0.25) radius *= 0.25;
+    else if (rho > 0.75 && std::fabs(snorm - radius) <= 1e-8 * radius)
+      radius = std::fmin(2.0 * radius, opt->radius_max);
+    if (rho > opt->eta) {
+      QOC_TRY(cudaMemcpyAsync(p->theta, p->theta_trial, 8 * (size_t)K, cudaMemcpyDeviceToDevice, st));
+      QOC_TRY(cudaMemcpyAsync(p->out, p->out_trial, 8 * (1 + (size_t)K), cudaMemcpyDeviceToDevice, st));
+    }
+    if (radius < opt->xtol) { stop = 1; break; }
+  }
+  if (it > opt->max_iter) it = opt->max_iter;
+  QOC_TRY(cudaMemcpyAsync(p->hbuf, p->theta, 8 * (size_t)K, cudaMemcpyDeviceToHost, st));
+  QOC_TRY(cudaMemcpyAsync(hs, p->out, 8 * (1 + (size_t)K), cudaMemcpyDeviceToHost, st));
+  QOC_TRY(cudaStreamSynchronize(st));
+  std::memcpy(theta_out, p->hbuf, 8 * (size_t)K);
+  double gn = 0;
+  for (int l = 0; l < K; ++l) gn += hs[1 + l] * hs[1 + l];
+  report->iters = it;
+  report->J = hs[0];
+  report->grad_norm = std::sqrt(gn);
+  report->radius = radius;
+  report->stop_reason = stop;
+  report->n_eval_gh = 0;
+  p->last_order = 1;
+  return stop == 2 ? QOC_ENOTCONV : QOC_OK;
+}
+
 }  // extern "C"
 
 // ---------------------------------------------------------------------------
-// Batches of uneven problems (different N, K, J; same precision).  Each
+// Batches of uneven problems (different N, K, J and sweep precision).  Each
 // problem's parallel phases run on its own stream; the four latency-bound
 // sweeps (states, costates, tangent panels, second-order adjoint panels) run
 // as one launch each over all problems.  The fork/join graph of one batched
 // evaluation is captured once into a CUDA graph and replayed.
 // ---------------------------------------------------------------------------
 struct qoc_batch {
-  int n = 0, mixed = 0;
+  int n = 0;
   std::vector<qoc_problem*> P;
   cudaStream_t st = nullptr;
   bool own_stream = false;
   std::vector<cudaEvent_t> ev;         // per problem: 5 phase events; then 5 batch events
-  // the four batched sweeps, each split into groups by the sweep kernel a
-  // single evaluation of the problem takes (bsweep_variant), one launch per
-  // group: index kSweepVariants * sweep + variant
-  static constexpr int NG = 4 * kSweepVariants;
+  // the four batched sweeps, each split into groups by the sweep precision
+  // and the sweep kernel a single evaluation of the problem takes
+  // (bsweep_variant), one launch per group: index GPS * sweep + gi with
+  // gi = kSweepVariants * mixed + variant
+  static constexpr int GPS = 2 * kSweepVariants;
+  static constexpr int NG = 4 * GPS;
   std::vector<BSweepArgs> hargs[NG];
   std::vector<int> hoff[NG];
   BSweepArgs* dargs[NG] = {};
   int* doff[NG] = {};
   int nargs[NG] = {}, total[NG] = {};
-  cudaStream_t aux[kSweepVariants] = {};   // each group's stream (0 is the batch stream)
+  cudaStream_t aux[GPS] = {};              // each group's stream (0 is the batch stream)
   cudaEvent_t fork[4] = {};                // per sweep: fork of the groups
   cudaEvent_t gjoin[NG] = {};              // per group: its join
   std::vector<size_t> toff, ooff;
@@ -941,7 +1074,7 @@ namespace {
 // one phase of problem i of the batch on stream s (see the header comment)
 qoc_status batch_phase(qoc_batch* b, int i, int phase, cudaStream_t s) {
   qoc_problem* p = b->P[i];
-  const int N = p->N, K = p->K, J = p->J, bs = p->bs, mixed = b->mixed;
+  const int N = p->N, K = p->K, J = p->J, bs = p->bs, mixed = p->precision == QOC_MIXED_FP32 ? 1 : 0;
   double* out = b->out + b->ooff[i];
   const void* Bsrc = mixed ? static_cast<const void*>(p->Bf) : static_cast<const void*>(p->B);
   switch (phase) {
@@ -950,7 +1083,7 @@ qoc_status batch_phase(qoc_batch* b, int i, int phase, cudaStream_t s) {
       QOC_TRY(launch_control(p->B, p->Kp, p->theta, J, K, p->f, s));
       QOC_TRY(launch_eig(p->H0, p->M, p->f, N, J, p->W, p->eig, p->status,
                          p->eig_method == QOC_EIG_JACOBI_FP64 ? EIG_JACOBI_FP64 : EIG_REFINED,
-                         p->refine_sweeps, p->angle_tol, s, p->ws[0]));
+                         p->refine_sweeps, p->angle_tol, s, p->ws[0], nullptr, nullptr, eig_finish_tol(p)));
       QOC_TRY(launch_prep(p->W, p->eig, p->M, N, J, p->dt, p->mshift, p->D, p->dstride, mixed ? 0 : 1,
                           PREP_D | PREP_P | PREP_X, p->Ptil, p->Xp, nullptr, p->status, s, p->ws[0]));
       QOC_TRY(launch_block_delta(p->D, p->dstride, N, J, bs, 0, mixed, p->Mf, p->mstride, s, p->ws[0]));
@@ -1007,9 +1140,9 @@ qoc_status enqueue_batch(qoc_batch* b) {
     for (int i = 0; i < n; ++i) QOC_TRY(cudaStreamWaitEvent(b->st, b->ev[5 * (size_t)i + phase], 0));
     if (phase < 4) {
       // one launch per kernel group, the groups side by side on their streams
-      const int g0 = kSweepVariants * phase;
+      const int g0 = qoc_batch::GPS * phase;
       bool forked = false;
-      for (int v = 0; v < kSweepVariants; ++v) {
+      for (int v = 0; v < qoc_batch::GPS; ++v) {
         const int g = g0 + v;
         if (!b->nargs[g]) continue;
         cudaStream_t s = b->st;
@@ -1022,10 +1155,10 @@ qoc_status enqueue_batch(qoc_batch* b) {
           QOC_TRY(cudaStreamWaitEvent(s, b->fork[phase], 0));
         }
         QOC_TRY(launch_bsweep_batch(b->hargs[g].data(), b->dargs[g], b->doff[g], b->nargs[g],
-                                    b->total[g], b->mixed, s));
+                                    b->total[g], v >= kSweepVariants ? 1 : 0, s));
         if (v > 0) QOC_TRY(cudaEventRecord(b->gjoin[g], s));
       }
-      for (int v = 1; v < kSweepVariants; ++v)
+      for (int v = 1; v < qoc_batch::GPS; ++v)
         if (b->nargs[g0 + v]) QOC_TRY(cudaStreamWaitEvent(b->st, b->gjoin[g0 + v], 0));
       QOC_TRY(cudaEventRecord(bev[phase + 1], b->st));
     }
@@ -1068,7 +1201,6 @@ qoc_status qoc_batch_create(qoc_problem* const* problems, int n, void* cuda_stre
   *out = nullptr;
   for (int i = 0; i < n; ++i) {
     if (!problems[i]) return QOC_EINVAL;
-    if (problems[i]->precision != problems[0]->precision) return QOC_EINVAL;
     if (problems[i]->bs < 2) return QOC_EUNSUPPORTED;
     for (int k = 0; k < i; ++k)
       if (problems[k] == problems[i]) return QOC_EINVAL;
@@ -1076,7 +1208,6 @@ qoc_status qoc_batch_create(qoc_problem* const* problems, int n, void* cuda_stre
   qoc_batch* b = new (std::nothrow) qoc_batch();
   if (!b) return QOC_ENOMEM;
   b->n = n;
-  b->mixed = problems[0]->precision == QOC_MIXED_FP32;
   b->P.assign(problems, problems + n);
   cudaError_t e;
   auto fail = [&](cudaError_t err) { qoc_batch_destroy(b); return from_cuda(err, __LINE__); };
@@ -1092,7 +1223,7 @@ qoc_status qoc_batch_create(qoc_problem* const* problems, int n, void* cuda_stre
     if ((e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming)) != cudaSuccess) return fail(e);
   for (auto& ev : b->fork)
     if ((e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming)) != cudaSuccess) return fail(e);
-  for (int v = 1; v < kSweepVariants; ++v)
+  for (int v = 1; v < qoc_batch::GPS; ++v)
     if ((e = cudaStreamCreateWithFlags(&b->aux[v], cudaStreamNonBlocking)) != cudaSuccess) return fail(e);
   for (int i = 0; i < n; ++i) {
     qoc_problem* p = problems[i];
@@ -1105,7 +1236,8 @@ qoc_status qoc_batch_create(qoc_problem* const* problems, int n, void* cuda_stre
                            panel_sweep_args(p, 1)};
     for (int k = 0; k < 4; ++k) {
       if (k == 3 && p->hess_method != QOC_HESS_SECOND_ORDER_ADJOINT) continue;
-      const int g = kSweepVariants * k + bsweep_variant(args[k], b->mixed);
+      const int mx = p->precision == QOC_MIXED_FP32 ? 1 : 0;
+      const int g = qoc_batch::GPS * k + kSweepVariants * mx + bsweep_variant(args[k], mx);
       b->hoff[g].push_back(b->total[g]);
       b->hargs[g].push_back(args[k]);
       b->total[g] += (args[k].K + args[k].kc - 1) / args[k].kc;
@@ -1191,3 +1323,195 @@ qoc_status qoc_batch_eval_grad_hess(qoc_batch* b, const double* thetas, double* 
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Batched trust region: every problem runs the basic trust region of
+// qoc_trust_region_solve, all of them advancing together.  One iteration is
+// enqueued as: propose (device: gtol test, exact subproblem, trial point) ->
+// one batched gradient + Hessian evaluation of every trial point (the batch's
+// CUDA graph) -> eigendecomposition of each trial Hessian -> update (device:
+// ratio test, radius, acceptance, xtol and iteration cap).  The host then
+// reads the per-problem state once for the whole batch and, when problems
+// have stopped, rebuilds the batch over those still running.
+// ---------------------------------------------------------------------------
+namespace {
+
+struct TrBatchRun {
+  std::vector<qoc_problem*> P;
+  std::vector<TrSlot> slot;              // host copy of every problem's state
+  std::vector<int> act;                  // indices of the problems in the current batch
+  TrSlot* dslots = nullptr;              // device slots of the current batch
+  double* etrial = nullptr;              // per problem [d (K) | Q (K*K)] of its trial Hessian
+  double* thcur = nullptr;               // per problem its current point (K); the batched
+                                         // evaluation copies each trial point into the
+                                         // problem's own theta buffer, so that one cannot hold it
+  std::vector<size_t> eoff, toff;
+  qoc_batch* b = nullptr;
+  cudaStream_t st = nullptr;
+  bool own_stream = false;
+  ~TrBatchRun() {
+    if (st) cudaStreamSynchronize(st);
+    if (b) qoc_batch_destroy(b);
+    cudaFree(dslots);
+    cudaFree(etrial);
+    cudaFree(thcur);
+    if (own_stream && st) cudaStreamDestroy(st);
+  }
+};
+
+// (re)build the batch over run.act and upload its slots
+qoc_status tr_rebuild(TrBatchRun& run) {
+  if (run.b) {
+    QOC_TRY(cudaStreamSynchronize(run.st));
+    qoc_batch_destroy(run.b);
+    run.b = nullptr;
+  }
+  std::vector<qoc_problem*> ps;
+  for (int i : run.act) ps.push_back(run.P[i]);
+  qoc_status s = qoc_batch_create(ps.data(), (int)ps.size(), run.st, &run.b);
+  if (s != QOC_OK) return s;
+  std::vector<TrSlot> dev(run.act.size());
+  for (size_t k = 0; k < run.act.size(); ++k) {
+    TrSlot& t = run.slot[run.act[k]];
+    t.theta_trial = run.b->theta + run.b->toff[k];
+    t.gh_trial = run.b->out + run.b->ooff[k];
+    dev[k] = t;
+  }
+  QOC_TRY(cudaMemcpyAsync(run.dslots, dev.data(), sizeof(TrSlot) * dev.size(), cudaMemcpyHostToDevice,
+                          run.st));
+  return QOC_OK;
+}
+
+// evaluate the current batch at its trial points and factor each trial Hessian
+qoc_status tr_eval_trials(TrBatchRun& run) {
+  qoc_status s = qoc_batch_eval_grad_hess_dev(run.b, run.b->theta, run.b->out);
+  if (s != QOC_OK) return s;
+  for (size_t k = 0; k < run.act.size(); ++k) {
+    qoc_problem* p = run.P[run.act[k]];
+    const int K = p->K;
+    double* e = run.etrial + run.eoff[run.act[k]];
+    QOC_TRY(launch_eig(run.b->out + run.b->ooff[k] + 1 + K, p->trzero, p->trzero, K, 1, e + K, e,
+                       p->status, EIG_JACOBI_FP64, 0, 0.0, run.st, p->ws[0]));
+  }
+  return QOC_OK;
+}
+
+// read the batch's slots back into run.slot (synchronises)
+qoc_status tr_pull(TrBatchRun& run) {
+  std::vector<TrSlot> dev(run.act.size());
+  QOC_TRY(cudaMemcpyAsync(dev.data(), run.dslots, sizeof(TrSlot) * dev.size(), cudaMemcpyDeviceToHost,
+                          run.st));
+  QOC_TRY(cudaStreamSynchronize(run.st));
+  for (size_t k = 0; k < run.act.size(); ++k) run.slot[run.act[k]] = dev[k];
+  return QOC_OK;
+}
+
+}  // namespace
+
+extern "C" qoc_status qoc_batch_trust_region_solve(qoc_problem* const* problems, int n,
+                                                   const double* theta0s, const qoc_tr_options* opt,
+                                                   double* theta_out, qoc_tr_report* reports,
+                                                   void* cuda_stream) {
+  if (!problems || n < 1 || !theta0s || !opt || !theta_out || !reports) return QOC_EINVAL;
+  if (!(opt->radius0 > 0) || !(opt->radius_max >= opt->radius0) || opt->max_iter < 1 ||
+      !(opt->eta >= 0 && opt->eta < 0.25) || !(opt->gtol >= 0) || !(opt->xtol >= 0))
+    return QOC_EINVAL;
+  size_t ntheta = 0;
+  for (int i = 0; i < n; ++i) {
+    qoc_problem* p = problems[i];
+    if (!p) return QOC_EINVAL;
+    for (int k = 0; k < i; ++k)
+      if (problems[k] == p) return QOC_EINVAL;
+    if (!p->trwork || p->bs < 2) return QOC_EUNSUPPORTED;
+    ntheta += p->K;
+  }
+  if (!finite_all(theta0s, ntheta)) return QOC_EINVAL;
+  TrBatchRun run;
+  run.P.assign(problems, problems + n);
+  if (cuda_stream) run.st = static_cast<cudaStream_t>(cuda_stream);
+  else {
+    QOC_TRY(cudaStreamCreateWithFlags(&run.st, cudaStreamNonBlocking));
+    run.own_stream = true;
+  }
+  size_t ne = 0, nt = 0;
+  run.slot.resize(n);
+  for (int i = 0; i < n; ++i) {
+    qoc_problem* p = run.P[i];
+    run.eoff.push_back(ne);
+    run.toff.push_back(nt);
+    ne += (size_t)p->K + (size_t)p->K * p->K;
+    nt += (size_t)p->K;
+    TrSlot& t = run.slot[i];
+    std::memset(&t, 0, sizeof(t));
+    t.K = p->K; t.gh = p->out; t.work = p->trwork; t.step = p->trstep; t.info = p->trinfo;
+    t.status = p->status; t.active = 1;
+    run.act.push_back(i);
+  }
+  QOC_TRY(cudaMalloc(&run.dslots, sizeof(TrSlot) * n));
+  QOC_TRY(cudaMalloc(&run.etrial, 8 * ne));
+  QOC_TRY(cudaMalloc(&run.thcur, 8 * nt));
+  for (int i = 0; i < n; ++i) {
+    run.slot[i].eig_trial = run.etrial + run.eoff[i];
+    run.slot[i].theta = run.thcur + run.toff[i];
+  }
+  const TrBatchOptions o{opt->gtol, opt->xtol, opt->radius0, opt->radius_max, opt->eta, opt->max_iter};
+  qoc_status s = tr_rebuild(run);
+  if (s != QOC_OK) return s;
+  // initial point: theta0 into the trial slots, evaluated and taken as current
+  {
+    std::vector<double> th(run.b->ntheta);
+    std::memcpy(th.data(), theta0s, 8 * ntheta);
+    QOC_TRY(cudaMemcpyAsync(run.b->theta, th.data(), 8 * ntheta, cudaMemcpyHostToDevice, run.st));
+    for (int i = 0; i < n; ++i) QOC_TRY(cudaMemsetAsync(run.P[i]->status, 0, sizeof(int), run.st));
+    if ((s = tr_eval_trials(run)) != QOC_OK) return s;
+    QOC_TRY(launch_tr_batch(0, run.dslots, n, 0, o, run.st));
+    if ((s = tr_pull(run)) != QOC_OK) return s;
+  }
+  for (int it = 1; it <= opt->max_iter; ++it) {
+    std::vector<int> still;
+    for (int i : run.act)
+      if (run.slot[i].active) still.push_back(i);
+    if (still.empty()) break;
+    if (still.size() != run.act.size()) {
+      run.act = still;
+      if ((s = tr_rebuild(run)) != QOC_OK) return s;
+    }
+    const int na = (int)run.act.size();
+    QOC_TRY(launch_tr_batch(1, run.dslots, na, it, o, run.st));
+    if ((s = tr_eval_trials(run)) != QOC_OK) return s;
+    QOC_TRY(launch_tr_batch(2, run.dslots, na, it, o, run.st));
+    if ((s = tr_pull(run)) != QOC_OK) return s;
+  }
+  // results: theta, J and |grad| of the final iterates; status words of
+  // problems evaluated after they stopped are cleared
+  for (int i = 0; i < n; ++i) QOC_TRY(cudaMemsetAsync(run.P[i]->status, 0, sizeof(int), run.st));
+  QOC_TRY(cudaStreamSynchronize(run.st));
+  qoc_status worst = QOC_OK;
+  size_t off = 0;
+  for (int i = 0; i < n; ++i) {
+    qoc_problem* p = run.P[i];
+    const int K = p->K;
+    std::vector<double> gh(1 + (size_t)K);
+    QOC_TRY(cudaMemcpy(theta_out + off, run.thcur + run.toff[i], 8 * (size_t)K, cudaMemcpyDeviceToHost));
+    QOC_TRY(cudaMemcpy(p->theta, run.thcur + run.toff[i], 8 * (size_t)K, cudaMemcpyDeviceToDevice));
+    QOC_TRY(cudaMemcpy(gh.data(), p->out, 8 * (1 + (size_t)K), cudaMemcpyDeviceToHost));
+    off += K;
+    const TrSlot& t = run.slot[i];
+    double gn = 0;
+    for (int l = 0; l < K; ++l) gn += gh[1 + l] * gh[1 + l];
+    qoc_tr_report& r = reports[i];
+    std::memset(&r, 0, sizeof(r));
+    r.iters = t.iters; r.n_eval_J = t.n_eval_J; r.n_eval_gh = t.n_eval_gh;
+    r.J = gh[0]; r.grad_norm = std::sqrt(gn); r.radius = t.radius; r.stop_reason = t.stop;
+    p->last_order = 2;
+    if (t.stop == 4) {
+      *p->hstatus = t.fail;
+      qoc_status e = device_status(p);
+      if (e == QOC_OK) e = QOC_ENUMERIC;
+      if (worst == QOC_OK || worst == QOC_ENOTCONV) worst = e;
+    } else if (t.stop == 2 && worst == QOC_OK) {
+      worst = QOC_ENOTCONV;
+    }
+  }
+  return worst;
+}

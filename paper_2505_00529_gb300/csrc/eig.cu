@@ -235,7 +235,8 @@ __device__ __forceinline__ void eig_refine_step(const double* __restrict__ H0,
                                                 int sweeps, double angle_tol,
                                                 double* __restrict__ W_io,
                                                 double* __restrict__ eig_out, int* status,
-                                                unsigned int* stats, unsigned char* smem_raw) {
+                                                unsigned int* stats, double finish_tol,
+                                                unsigned char* smem_raw) {
   const int ld = N + 1;
   const int NP = N + (N & 1);
   double* H = reinterpret_cast<double*>(smem_raw);
@@ -283,7 +284,18 @@ __device__ __forceinline__ void eig_refine_step(const double* __restrict__ H0,
   // O(|E|^2 + |R| |E|) <= orth_tol / 50), and the Rayleigh quotients lambda of
   // this pass are exact to O(|E|^2 |H|): the final residual pass and the
   // clean-up are skipped.
-  const double kDone = 0.1 * sqrt(orth_tol);
+  // finish_tol > 0 (relaxed finish, for callers whose results need only the
+  // residual H W - W Lambda, relative to |H|, at about 1e-9): an update with
+  // no cluster pairs, |R|_F <= finish_tol and |E|_F |off(S)|_F <= kRes |H|_F
+  // ends the refinement.  The update cancels the residual to first order, so
+  // what it leaves is O(|E| |off(S)| + |R|^2) -- a pair of close eigenvalues
+  // may keep a sizeable rotation between its two eigenvectors, which moves
+  // smooth functions of H (the propagator and its Frechet derivatives) only
+  // through that residual.  Its W E is formed in binary32 like every
+  // non-final update.
+  const bool relaxed = finish_tol > 0;
+  constexpr double kRes = 1e-9;
+  const double kDone = relaxed ? finish_tol : 0.1 * sqrt(orth_tol);
   __shared__ int not_done;
   bool finished = false;
   for (int it = 0;; ++it) {
@@ -330,6 +342,7 @@ __device__ __forceinline__ void eig_refine_step(const double* __restrict__ H0,
       for (int w = 0; w < (nt + 31) / 32; ++w) { a += red[2 * w]; b += red[2 * w + 1]; }
       red[41] = 2.0 * (sqrt(a) + Hnorm * sqrt(b));  // cluster threshold delta
       red[42] = sqrt(b);                             // |I - W^T W|_F
+      red[43] = sqrt(a);                             // |off(S)|_F with the diagonal's correction
     }
     __syncthreads();
     const double delta = red[41];
@@ -348,6 +361,7 @@ __device__ __forceinline__ void eig_refine_step(const double* __restrict__ H0,
     constexpr double kLinear = 1e-3;
     if (tid == 0) not_done = red[42] > kDone ? 1 : 0;
     __syncthreads();
+    double esq = 0;
     for (int e = tid; e < N * N; e += nt) {
       const int i = e / N, k = e % N;
       const double rik = R[i * ld + k];
@@ -358,9 +372,20 @@ __device__ __forceinline__ void eig_refine_step(const double* __restrict__ H0,
         const double sik = S[i * ld + k];
         const bool sep = fabs(gap) > delta && fabs(sik) <= kLinear * fabs(gap);
         eik = sep ? (sik + lam[k] * rik) / gap : 0.5 * rik;
-        if (!sep || fabs(eik) > kDone) not_done = 1;
+        if (!sep || (!relaxed && fabs(eik) > kDone)) not_done = 1;
+        esq = fma(eik, eik, esq);
       }
       T[i * ld + k] = eik;
+    }
+    if (relaxed) {   // |E|_F |off(S)|_F against kRes |H|_F
+      esq = warp_sum(esq);
+      if ((tid & 31) == 0) red[2 * (tid >> 5)] = esq;
+      __syncthreads();
+      if (tid == 0) {
+        double es = 0;
+        for (int w = 0; w < (nt + 31) / 32; ++w) es += red[2 * w];
+        if (sqrt(es) * red[43] > kRes * Hnorm) not_done = 1;
+      }
     }
     __syncthreads();
     // W <- W + W E (R as scratch for W E).  An update that cannot end the
@@ -368,7 +393,7 @@ __device__ __forceinline__ void eig_refine_step(const double* __restrict__ H0,
     // binary32: E is then a correction the next update refines, and the
     // binary32 product is off by about N eps32 |W| |E|, far below the error
     // that update removes.  A finishing update forms it in binary64.
-    if (not_done) {
+    if (not_done || relaxed) {
       for (int e = tid; e < N * N; e += nt) {
         const int i = e / N, k = e % N;
         Wf[i * ld + k] = (float)W[i * ld + k];
@@ -453,11 +478,11 @@ k_eig_refine(const double* __restrict__ H0, const double* __restrict__ M,
                              const double* __restrict__ f, int N, int J, int sweeps,
                              double angle_tol, double* __restrict__ W_io,
                              double* __restrict__ eig_out, int* status, unsigned int* stats,
-                             unsigned char* gws, size_t per_cta) {
+                             double finish_tol, unsigned char* gws, size_t per_cta) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   unsigned char* base = GWS ? gws + (size_t)blockIdx.x * per_cta : smem_raw;
   for (int j = blockIdx.x; j < J; j += gridDim.x) {
-    eig_refine_step(H0, M, f, N, j, sweeps, angle_tol, W_io, eig_out, status, stats, base);
+    eig_refine_step(H0, M, f, N, j, sweeps, angle_tol, W_io, eig_out, status, stats, finish_tol, base);
     __syncthreads();
   }
 }
@@ -680,7 +705,7 @@ static size_t refine_smem(int N) {
 cudaError_t launch_eig(const double* H0, const double* M, const double* f, int N, int J,
                        double* W, double* eig, int* status, int method, int refine_sweeps,
                        double angle_tol, cudaStream_t st, const StepSpace& ws, cudaEvent_t mid,
-                       unsigned int* stats) {
+                       unsigned int* stats, double finish_tol) {
   // Jacobi rounds are barrier-bound: few warps per (small) matrix, many CTAs per SM
   const int jthreads = N <= 32 ? 64 : (N <= 64 ? 128 : (N <= 128 ? 256 : 512));
   const int threads = N <= 16 ? 128 : (N <= 128 ? 256 : 512);   // refinement: binary64-bound
@@ -720,19 +745,19 @@ cudaError_t launch_eig(const double* H0, const double* M, const double* f, int N
       return cudaErrorInvalidConfiguration;
     if (g.gws)
       k_eig_refine<256, true><<<g.grid, threads, g.smem, st>>>(H0, M, f, N, J, refine_sweeps, angle_tol,
-                                                               W, eig, status, stats, g.gws, g.per_cta);
+                                                               W, eig, status, stats, finish_tol, g.gws, g.per_cta);
     else
       k_eig_refine<256, false><<<g.grid, threads, g.smem, st>>>(H0, M, f, N, J, refine_sweeps, angle_tol,
-                                                                W, eig, status, stats, g.gws, g.per_cta);
+                                                                W, eig, status, stats, finish_tol, g.gws, g.per_cta);
   } else {
     if (!step_grid(refine_smem(N), J, ws, (const void*)k_eig_refine<512, false>, g))
       return cudaErrorInvalidConfiguration;
     if (g.gws)
       k_eig_refine<512, true><<<g.grid, threads, g.smem, st>>>(H0, M, f, N, J, refine_sweeps, angle_tol,
-                                                               W, eig, status, stats, g.gws, g.per_cta);
+                                                               W, eig, status, stats, finish_tol, g.gws, g.per_cta);
     else
       k_eig_refine<512, false><<<g.grid, threads, g.smem, st>>>(H0, M, f, N, J, refine_sweeps, angle_tol,
-                                                                W, eig, status, stats, g.gws, g.per_cta);
+                                                                W, eig, status, stats, finish_tol, g.gws, g.per_cta);
   }
   return cudaGetLastError();
 }

@@ -102,10 +102,14 @@ constexpr double TAU_DD2 = 1e-3;
 // [2] += steps that took the final residual pass (no early finish)
 // method EIG_REFINED: binary32 Jacobi, `refine_sweeps` binary64 Ogita-Aishima
 // sweeps, then binary64 Jacobi clean-up rotating only angles above angle_tol.
+// finish_tol > 0: the refinement ends after the first update with no cluster
+// pairs whose |I - W^T W|_F and largest correction are <= finish_tol (W then
+// accurate to about finish_tol^2); 0: refinement to the binary64 floor.
 cudaError_t launch_eig(const double* H0, const double* M, const double* f, int N, int J,
                        double* W, double* eig, int* status, int method, int refine_sweeps,
                        double angle_tol, cudaStream_t st, const StepSpace& ws,
-                       cudaEvent_t mid = nullptr, unsigned int* stats = nullptr);
+                       cudaEvent_t mid = nullptr, unsigned int* stats = nullptr,
+                       double finish_tol = 0.0);
 size_t eig_step_bytes(int N);   // largest per-matrix storage of the eigensolver kernels
 
 size_t prep_smem_bytes(int N);
@@ -220,6 +224,38 @@ size_t tr_work_doubles(int K);
 cudaError_t launch_axpy(const double* x, const double* s, int K, double* y, cudaStream_t st);
 cudaError_t launch_tr_subproblem(const double* out_gh, int K, double radius, double* work,
                                  double* step, double* info, int* status, cudaStream_t st);
+
+// BFGS update of the K x K model Hessian B from the step s and the gradients
+// (state[0]: 0 until the first update with positive curvature scales B, then 1);
+// scratch: K doubles
+cudaError_t launch_bfgs_update(double* B, const double* s, const double* g_old, const double* g_new, int K,
+                               double* state, double min_curv, double* scratch, cudaStream_t st);
+cudaError_t launch_set_identity(double* B, int K, cudaStream_t st);
+
+// one problem of a batched trust-region solve (device array, one CTA each)
+struct TrSlot {
+  int K;
+  double* gh;               // [J, grad, Hess] at theta (1 + K + K*K)
+  double* work;             // tr_work_doubles(K): [gt | st | d | Q] of the current Hessian
+  double* step;             // K
+  double* info;             // [pred, |s|, sigma, |g|]
+  double* theta;            // K: current point
+  double* theta_trial;      // K: trial point (the batched evaluation reads it)
+  const double* gh_trial;   // [J, grad, Hess] at the trial point
+  const double* eig_trial;  // [d (K) | Q (K*K)] of the trial Hessian
+  int* status;              // the problem's device status word (read and cleared)
+  double radius;
+  int active, stop, iters, n_eval_J, n_eval_gh, fail;
+};
+struct TrBatchOptions {
+  double gtol, xtol, radius0, radius_max, eta;
+  int max_iter;
+};
+// phase 0: take the evaluated initial point; 1: propose (gtol test,
+// subproblem, trial point); 2: update (ratio test, radius, acceptance, xtol
+// and iteration cap) -- iteration `it`
+cudaError_t launch_tr_batch(int phase, TrSlot* slots, int n, int it, const TrBatchOptions& o,
+                            cudaStream_t st);
 
 // set the text qoc_last_error() returns on this thread
 void note_error(const char* msg);

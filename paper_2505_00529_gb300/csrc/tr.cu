@@ -30,11 +30,11 @@ __device__ double block_sum(double v, double* red) {
 
 // work layout: [0..K) gt, [K..2K) st
 // info: [0] predicted decrease, [1] |s|, [2] sigma, [3] |g|
-__global__ void k_tr_subproblem(const double* __restrict__ gh, const double* __restrict__ Q,
-                                const double* __restrict__ d, int K, double radius,
-                                double* __restrict__ work, double* __restrict__ step,
-                                double* __restrict__ info, int* status) {
-  __shared__ double red[32];
+// (the body of one CTA; `red` is 32 doubles of shared memory)
+__device__ void tr_subproblem_body(const double* __restrict__ gh, const double* __restrict__ Q,
+                                   const double* __restrict__ d, int K, double radius,
+                                   double* __restrict__ work, double* __restrict__ step,
+                                   double* __restrict__ info, int* status, double* red) {
   double* gt = work;
   double* st = work + K;
   const double* g = gh + 1;
@@ -142,6 +142,209 @@ __global__ void k_tr_subproblem(const double* __restrict__ gh, const double* __r
     info[2] = sigma;
     info[3] = gn;
   }
+  __syncthreads();
+}
+
+__global__ void k_tr_subproblem(const double* __restrict__ gh, const double* __restrict__ Q,
+                                const double* __restrict__ d, int K, double radius,
+                                double* __restrict__ work, double* __restrict__ step,
+                                double* __restrict__ info, int* status) {
+  __shared__ double red[32];
+  tr_subproblem_body(gh, Q, d, K, radius, work, step, info, status, red);
+}
+
+// ---------------------------------------------------------------------------
+// Batched trust region (one CTA per problem, problems in a TrSlot array).
+// The iteration is the same basic trust region as the single-problem solve
+// (gtol test on the current gradient, exact subproblem, ratio test, radius
+// update, acceptance, xtol test), except that the trial point is evaluated
+// with its gradient and Hessian (by the batched evaluation between the two
+// kernels below), so that an accepted step needs no further evaluation.
+// ---------------------------------------------------------------------------
+
+// first half of iteration `it`: gtol test, subproblem, trial point
+__global__ void k_tr_batch_propose(TrSlot* slots, int n, int it, double gtol) {
+  __shared__ double red[32];
+  const int i = blockIdx.x;
+  if (i >= n) return;
+  TrSlot& t = slots[i];
+  if (!t.active) return;
+  const int K = t.K;
+  if (threadIdx.x == 0) {
+    double gn = 0;
+    for (int l = 0; l < K; ++l) gn = fma(t.gh[1 + l], t.gh[1 + l], gn);
+    red[31] = sqrt(gn);
+  }
+  __syncthreads();
+  if (red[31] < gtol) {
+    __syncthreads();
+    if (threadIdx.x == 0) { t.stop = 0; t.iters = it - 1; t.active = 0; }
+    return;
+  }
+  __syncthreads();
+  tr_subproblem_body(t.gh, t.work + 3 * K, t.work + 2 * K, K, t.radius, t.work, t.step, t.info,
+                     t.status, red);
+  const double pred = t.info[0];
+  if (!(pred > 0) || !isfinite(pred)) {
+    if (threadIdx.x == 0) { t.stop = 3; t.iters = it; t.active = 0; }
+    return;
+  }
+  for (int l = threadIdx.x; l < K; l += blockDim.x) t.theta_trial[l] = t.theta[l] + t.step[l];
+}
+
+// second half: ratio test on the evaluated trial, radius update, acceptance
+// (theta, [J, grad, Hess] and the Hessian's eigendecomposition taken from the
+// trial), xtol and iteration-cap tests.  Device status bits of the trial
+// evaluation: a non-finite value or an unconverged eigensolver rejects the
+// step; a timeout or an unsupported shape ends the problem's solve with
+// stop = 4 and the bits kept in `fail`.
+__global__ void k_tr_batch_update(TrSlot* slots, int n, int it, int max_iter, double xtol,
+                                  double radius_max, double eta) {
+  __shared__ int acc;
+  const int i = blockIdx.x;
+  if (i >= n) return;
+  TrSlot& t = slots[i];
+  if (!t.active) return;
+  const int K = t.K;
+  if (threadIdx.x == 0) {
+    const int st = *t.status;
+    *t.status = 0;
+    acc = 0;
+    t.n_eval_J += 1;
+    if (st & (DEV_TIMEOUT | DEV_BADSHAPE)) {
+      t.fail = st;
+      t.stop = 4;
+      t.iters = it;
+      t.active = 0;
+    } else {
+      const double pred = t.info[0], snorm = t.info[1];
+      const double Jc = t.gh[0], Jt = t.gh_trial[0];
+      const bool ok = st == 0 && isfinite(Jt);
+      const double rho = ok ? (Jc - Jt) / pred : -1.0;
+      double r = t.radius;
+      if (rho < 0.25) r *= 0.25;
+      else if (rho > 0.75 && fabs(snorm - r) <= 1e-8 * r) r = fmin(2.0 * r, radius_max);
+      t.radius = r;
+      if (rho > eta) {
+        acc = 1;
+        t.n_eval_gh += 1;
+      }
+    }
+  }
+  __syncthreads();
+  if (!t.active) return;
+  if (acc) {
+    for (int l = threadIdx.x; l < K; l += blockDim.x) t.theta[l] = t.theta_trial[l];
+    const size_t ngh = 1 + (size_t)K + (size_t)K * K;
+    for (size_t e = threadIdx.x; e < ngh; e += blockDim.x) t.gh[e] = t.gh_trial[e];
+    const size_t neig = (size_t)K + (size_t)K * K;   // eigenvalues d, eigenvectors Q
+    for (size_t e = threadIdx.x; e < neig; e += blockDim.x) t.work[2 * K + e] = t.eig_trial[e];
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    if (t.radius < xtol) { t.stop = 1; t.iters = it; t.active = 0; }
+    else if (it >= max_iter) { t.stop = 2; t.iters = max_iter; t.active = 0; }
+  }
+}
+
+// the initial point: [J, grad, Hess] and eigendecomposition taken as current
+__global__ void k_tr_batch_init(TrSlot* slots, int n, double radius0) {
+  const int i = blockIdx.x;
+  if (i >= n) return;
+  TrSlot& t = slots[i];
+  const int K = t.K;
+  const size_t ngh = 1 + (size_t)K + (size_t)K * K;
+  for (size_t e = threadIdx.x; e < ngh; e += blockDim.x) t.gh[e] = t.gh_trial[e];
+  const size_t neig = (size_t)K + (size_t)K * K;
+  for (size_t e = threadIdx.x; e < neig; e += blockDim.x) t.work[2 * K + e] = t.eig_trial[e];
+  for (int l = threadIdx.x; l < K; l += blockDim.x) t.theta[l] = t.theta_trial[l];
+  if (threadIdx.x == 0) {
+    const int st = *t.status;
+    *t.status = 0;
+    t.radius = radius0;
+    t.iters = 0; t.n_eval_J = 0; t.n_eval_gh = 1;
+    t.stop = 2;
+    t.fail = st;
+    t.active = st == 0 && isfinite(t.gh[0]) ? 1 : 0;
+    if (!t.active) t.stop = 4;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// BFGS update of the Hessian approximation of the gradient-only trust region
+// (Alg. 1 with the quasi-Newton model; Nocedal & Wright, Eq. 6.19), one CTA:
+//   y = g_new - g_old, s = the trial step;
+//   first update with y^T s > 0: B <- (y^T y / y^T s) I (state[0] = 1 after);
+//   y^T s > min_curv |s| |y|:   B <- B - (B s)(B s)^T / (s^T B s) + y y^T / (y^T s),
+// otherwise B is kept.  B is K x K row-major, symmetric.
+// ---------------------------------------------------------------------------
+__global__ void k_bfgs_update(double* __restrict__ B, const double* __restrict__ s,
+                              const double* __restrict__ g_old, const double* __restrict__ g_new,
+                              int K, double* __restrict__ state, double min_curv,
+                              double* __restrict__ Bs) {
+  __shared__ double red[32];
+  __shared__ double sc[4];
+  const int tid = threadIdx.x, nt = blockDim.x;
+  if (tid == 0) sc[2] = state[0];
+  double sy = 0, yy = 0, ss = 0;
+  for (int l = tid; l < K; l += nt) {
+    const double y = g_new[l] - g_old[l];
+    sy = fma(y, s[l], sy);
+    yy = fma(y, y, yy);
+    ss = fma(s[l], s[l], ss);
+  }
+  sy = block_sum(sy, red);
+  yy = block_sum(yy, red);
+  ss = block_sum(ss, red);
+  __syncthreads();
+  if (sc[2] == 0.0 && sy > 0) {   // sc[2] read before block_sum's barriers
+    const double scale = yy / sy;
+    for (int e = tid; e < K * K; e += nt) B[e] = (e / K == e % K) ? scale : 0.0;
+    __syncthreads();
+    if (tid == 0) state[0] = 1.0;
+  }
+  if (!(sy > min_curv * sqrt(ss) * sqrt(yy))) return;   // uniform across the CTA
+  double sbs = 0;
+  for (int i = tid; i < K; i += nt) {
+    double acc = 0;
+    for (int k = 0; k < K; ++k) acc = fma(B[(size_t)i * K + k], s[k], acc);
+    Bs[i] = acc;
+    sbs = fma(s[i], acc, sbs);
+  }
+  sbs = block_sum(sbs, red);
+  __syncthreads();
+  if (tid == 0) { sc[0] = sbs; sc[1] = sy; }
+  __syncthreads();
+  for (int e = tid; e < K * K; e += nt) {
+    const int i = e / K, k = e % K;
+    const double yi = g_new[i] - g_old[i], yk = g_new[k] - g_old[k];
+    B[e] = B[e] - (Bs[i] * Bs[k]) / sc[0] + (yi * yk) / sc[1];
+  }
+}
+
+__global__ void k_set_identity(double* __restrict__ B, int K) {
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < K * K; e += gridDim.x * blockDim.x)
+    B[e] = (e / K == e % K) ? 1.0 : 0.0;
+}
+
+cudaError_t launch_bfgs_update(double* B, const double* s, const double* g_old, const double* g_new, int K,
+                               double* state, double min_curv, double* scratch, cudaStream_t st) {
+  k_bfgs_update<<<1, 256, 0, st>>>(B, s, g_old, g_new, K, state, min_curv, scratch);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_set_identity(double* B, int K, cudaStream_t st) {
+  k_set_identity<<<(K * K + 255) / 256, 256, 0, st>>>(B, K);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_tr_batch(int phase, TrSlot* slots, int n, int it, const TrBatchOptions& o,
+                            cudaStream_t st) {
+  if (n < 1) return cudaSuccess;
+  if (phase == 0) k_tr_batch_init<<<n, 128, 0, st>>>(slots, n, o.radius0);
+  else if (phase == 1) k_tr_batch_propose<<<n, 128, 0, st>>>(slots, n, it, o.gtol);
+  else k_tr_batch_update<<<n, 128, 0, st>>>(slots, n, it, o.max_iter, o.xtol, o.radius_max, o.eta);
+  return cudaGetLastError();
 }
 
 __global__ void k_axpy(const double* __restrict__ x, const double* __restrict__ s, int K,

@@ -185,6 +185,33 @@ def config_problem(cfg: int, index: int = 0) -> Problem:
     return Problem(H0, M, alpha, beta, B, dt, dt, 1.0, name=f"config{cfg}_{index}")
 
 
+def scaling_problem(N: int, J: int, seed: int, dt: float = 0.1) -> Problem:
+    """The wall-time scaling experiment's setting (Sec. IV-A, Fig. 1): the
+    maximal model f_j = theta_j (K = J), alpha = e_1, beta = e_N, a random
+    diagonal H0 and a random symmetric M (real symmetric here; the paper's are
+    Hermitian), diagonal energies U[-2, 0] and M entries N(0, 0.5^2) as in
+    the small single workload; paper weights (w_f = 1/2, w_t = rho/2 with
+    rho = 1)."""
+    rng = np.random.default_rng(seed)
+    H0 = np.diag(np.sort(rng.uniform(-2.0, 0.0, N)))
+    M = _sym_upper(rng, N, 0.5)
+    alpha = np.zeros(N, complex)
+    alpha[0] = 1.0
+    beta = np.zeros(N, complex)
+    beta[-1] = 1.0
+    return Problem(H0, M, alpha, beta, maximal_basis(J), dt, 0.5, 0.5, name=f"scaling_N{N}_J{J}")
+
+
+def batched_shape(index: int):
+    """(N, K, J) of problem `index` of the batched workload (config 3), drawn
+    exactly as config_problem(3, index) draws them, without the matrices."""
+    rng = np.random.default_rng(1000 * 3 + index)
+    N = int(rng.choice(np.arange(8, 129, 8)))
+    K = int(rng.choice([16, 32, 64, 128]))
+    J = int(rng.choice([2000, 4000, 8000]))
+    return N, K, J
+
+
 def eval_theta(K: int, seed: int, scale: float = 1.0) -> np.ndarray:
     """Evaluation point theta ~ N(0, scale^2) (Sec. IV-A draws N(0,1))."""
     return scale * np.random.default_rng(seed).normal(size=K)

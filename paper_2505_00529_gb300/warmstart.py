@@ -37,34 +37,36 @@ def init_params(n_in, hidden, n_hidden, n_out, seed) -> np.ndarray:
     return np.concatenate(out).astype(np.float32)
 
 
-def solve_many(prob, betas, theta0s, precision=_lib.QOC_MIXED_FP32, workers=4, **tr):
-    """Trust-region solves for each target (one problem object per worker,
-    each on its own stream).  Returns (thetas, infos, seconds)."""
+def solve_many(prob, betas, theta0s, precision=_lib.QOC_MIXED_FP32, batch=32, **tr):
+    """Trust-region solves for each target, `batch` targets at a time through
+    the library's batched trust region (one problem object per slot of the
+    batch, re-targeted between batches).  Returns (thetas, infos, seconds)."""
     n = len(betas)
-    thetas = np.zeros((n, prob.B.shape[1]))
+    K = prob.B.shape[1]
+    thetas = np.zeros((n, K))
     infos = [None] * n
-    problems = [_lib.Problem(prob, precision=precision) for _ in range(workers)]
-
-    def run(w):
-        P = problems[w]
-        for i in range(w, n, workers):
-            P.set_target(betas[i])
-            t0 = time.perf_counter()
-            try:
-                th, info = P.trust_region_solve(theta0s[i], **tr)
-            except _lib.QocError as e:   # recorded, not fatal: the solve counts as failed
-                th, info = np.full(prob.B.shape[1], np.nan), {"iters": tr.get("max_iter", 0),
-                                                               "J": np.nan, "stop": f"error {e.status}"}
-            info["seconds"] = time.perf_counter() - t0
-            thetas[i] = th
-            infos[i] = info
-
+    problems = [_lib.Problem(prob, precision=precision) for _ in range(min(batch, n))]
     t0 = time.perf_counter()
-    with cf.ThreadPoolExecutor(workers) as ex:
-        list(ex.map(run, range(workers)))
-    secs = time.perf_counter() - t0
-    for P in problems:
-        P.close()
+    try:
+        for s0 in range(0, n, batch):
+            idx = list(range(s0, min(n, s0 + batch)))
+            Ps = problems[:len(idx)]
+            for P, i in zip(Ps, idx):
+                P.set_target(betas[i])
+            try:
+                ths, inf, _ = _lib.qoc_batch_trust_region_solve([P.handle for P in Ps],
+                                                                [theta0s[i] for i in idx], **tr)
+            except _lib.QocError as e:   # recorded, not fatal: the solves of this batch count as failed
+                ths = [np.full(K, np.nan)] * len(idx)
+                inf = [{"iters": tr.get("max_iter", 0), "J": np.nan, "stop": f"error {e.status}"}
+                       for _ in idx]
+            for i, th, info in zip(idx, ths, inf):
+                thetas[i] = th
+                infos[i] = info
+    finally:
+        secs = time.perf_counter() - t0
+        for P in problems:
+            P.close()
     return thetas, infos, secs
 
 
@@ -137,13 +139,13 @@ class WarmStart:
 
 
 def compare(prob, train_betas, test_betas, precision=_lib.QOC_MIXED_FP32, workers=4, epochs=200,
-            batch=128, lr=1e-3, seed=0, **tr):
+            batch=128, lr=1e-3, seed=0, tr_batch=32, **tr):
     """Full warm-start experiment: theta* for the training targets (from 0),
     train, then solve the held-out targets from 0 and from the MLP."""
     K = prob.B.shape[1]
     N = prob.H0.shape[0]
     th_train, info_train, t_data = solve_many(prob, train_betas, np.zeros((len(train_betas), K)),
-                                              precision, workers, **tr)
+                                              precision, tr_batch, **tr)
     ok = np.array([i["stop"] in ("gtol", "xtol") and np.all(np.isfinite(t))
                    for i, t in zip(info_train, th_train)])
     ws = WarmStart(N, K, seed=seed)
@@ -151,10 +153,10 @@ def compare(prob, train_betas, test_betas, precision=_lib.QOC_MIXED_FP32, worker
     losses = ws.fit(train_betas[ok], th_train[ok], epochs=epochs, batch=batch, lr=lr, seed=seed)
     t_train = time.perf_counter() - t0
     theta0 = ws.predict(test_betas)
-    _, info_zero, t_zero = solve_many(prob, test_betas, np.zeros((len(test_betas), K)), precision, workers, **tr)
-    _, info_mlp, t_mlp = solve_many(prob, test_betas, theta0, precision, workers, **tr)
+    _, info_zero, t_zero = solve_many(prob, test_betas, np.zeros((len(test_betas), K)), precision, tr_batch, **tr)
+    _, info_mlp, t_mlp = solve_many(prob, test_betas, theta0, precision, tr_batch, **tr)
     theta_g, tstar, t_guard_eval = guarded_starts(prob, test_betas, theta0, precision, workers)
-    _, info_g, t_g = solve_many(prob, test_betas, theta_g, precision, workers, **tr)
+    _, info_g, t_g = solve_many(prob, test_betas, theta_g, precision, tr_batch, **tr)
     ws.close()
     conv = lambda i: i["stop"] in ("gtol", "xtol")
     good = np.array([conv(a) and conv(b) and conv(c) for a, b, c in zip(info_zero, info_mlp, info_g)])

@@ -110,9 +110,6 @@ def test_batch_validation():
     P3 = q.Problem(c, precision=q.QOC_FP64)
     try:
         with pytest.raises(q.QocError) as e:
-            q.Batch([P1, P2])
-        assert e.value.status == _lib.QOC_EINVAL
-        with pytest.raises(q.QocError) as e:
             q.Batch([P1, P1])
         assert e.value.status == _lib.QOC_EINVAL
         with pytest.raises(q.QocError) as e:
@@ -129,19 +126,51 @@ def test_batch_validation():
             P.close()
 
 
+def test_batch_mixed_sweep_precisions():
+    """One batch holding binary64-sweep and binary32-sweep problems (the
+    sweeps are grouped by precision as well as by kernel): every result
+    equals the problem's own evaluation and the oracle's within its tolerance."""
+    probs = _problems(seed0=21)[:4]
+    precs = [q.QOC_FP64, q.QOC_MIXED_FP32, q.QOC_MIXED_FP32, q.QOC_FP64]
+    Ps = [q.Problem(p, precision=pr) for p, pr in zip(probs, precs)]
+    try:
+        assert [P.precision()[0] for P in Ps] == precs
+        with q.Batch(Ps) as b:
+            thetas = _thetas(probs, 1300)
+            for _ in range(2):
+                res = b.eval_grad_hess(thetas)
+                for P, p, pr, th, (J, g, H) in zip(Ps, probs, precs, thetas, res):
+                    Ji, gi, Hi = P.eval_grad_hess(th)
+                    assert abs(J - Ji) <= 1e-13 * abs(Ji) and rel(g, gi) <= 1e-13 and rel(H, Hi) <= 1e-13
+                    ref = orc.evaluate(p, th, order=2)
+                    assert rel(H, ref["hess"]) <= TOL[pr], (p.N, pr, rel(H, ref["hess"]))
+    finally:
+        for P in Ps:
+            P.close()
+
+
+@pytest.fixture(scope="module")
+def avoided_crossing_ref():
+    pr = inputs.config_problem(3, 344)
+    th = inputs.eval_theta(pr.K, 167)
+    return pr, th, orc.evaluate(pr, th, order=2)
+
+
 @pytest.mark.parametrize("precision", [q.QOC_FP64, q.QOC_MIXED_FP32], ids=["fp64", "mixed"])
-def test_batched_workload_avoided_crossing(precision):
+def test_batched_workload_avoided_crossing(avoided_crossing_ref, precision):
     """A problem of the batched-workload recipe (N=48, K=32, J=4000) whose
     trajectory passes an avoided crossing (eigenvalue gap 3e-5 against
-    |H| ~ 50 at one step): the refined eigensolver must succeed and agree
-    with the binary64 Jacobi eigensolver path."""
-    pr = inputs.config_problem(3, 344)
+    |H| ~ 50 at one step): the refined eigensolver must succeed, and J, the
+    gradient and the Hessian must match the oracle (and, for the binary64
+    sweeps, the binary64 Jacobi eigensolver path)."""
+    pr, th, ref = avoided_crossing_ref
     assert (pr.N, pr.K, pr.J) == (48, 32, 4000)
-    th = inputs.eval_theta(pr.K, 167)
-    with q.Problem(pr, precision=q.QOC_FP64, eig_method=q.QOC_EIG_JACOBI_FP64) as P:
-        J0, g0, H0 = P.eval_grad_hess(th)
+    tol = TOL[precision]
     with q.Problem(pr, precision=precision) as P:
         J1, g1, H1 = P.eval_grad_hess(th)
-    tol = TOL[precision]
-    assert abs(J1 - J0) <= tol * abs(J0)
-    assert rel(g1, g0) <= tol and rel(H1, H0) <= tol, (rel(g1, g0), rel(H1, H0))
+    assert abs(J1 - ref["J"]) <= tol * abs(ref["J"])
+    assert rel(g1, ref["grad"]) <= tol and rel(H1, ref["hess"]) <= tol, (rel(g1, ref["grad"]), rel(H1, ref["hess"]))
+    if precision == q.QOC_FP64:
+        with q.Problem(pr, precision=q.QOC_FP64, eig_method=q.QOC_EIG_JACOBI_FP64) as P:
+            J0, g0, H0 = P.eval_grad_hess(th)
+        assert rel(H1, H0) <= tol and rel(g1, g0) <= tol

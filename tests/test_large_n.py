@@ -2,8 +2,11 @@
 and the largest single problem, N = 256): the per-step kernels then keep their
 matrices in a per-CTA slice of a global workspace and the sweeps read their
 block data straight from global memory.  Parity with the oracle on the same
-seeded inputs (small J), the full-size N=256/K=128/J=10^4 problem through
+seeded inputs (small J), the N=256/K=128 system over 200 steps against a
+stored oracle evaluation, the full-size N=256/K=128/J=10^4 problem through
 properties that hold at any size, and the trust region at K = 128."""
+import os
+
 import numpy as np
 import pytest
 
@@ -37,7 +40,8 @@ def check(prob, theta, precision, block_steps=None, intermediates=True):
         np.testing.assert_array_equal(H, H.T)
         if intermediates:
             lam = P.buffer(_lib.QOC_BUF_EIGVAL)
-            assert np.abs(lam - ref["eig"]).max() <= 1e-13 * max(np.abs(ref["eig"]).max(), 1.0) * prob.N
+            teig = 1e-13 if precision == q.QOC_FP64 else 1e-8   # binary32 sweeps: relaxed refinement
+            assert np.abs(lam - ref["eig"]).max() <= teig * max(np.abs(ref["eig"]).max(), 1.0) * prob.N
             a = P.buffer(_lib.QOC_BUF_STATE)
             assert rel(a, ref["a"]) <= (1e-10 if precision == q.QOC_FP64 else 1e-5)
 
@@ -51,37 +55,83 @@ def test_large_n_parity(shape, precision):
     check(prob, inputs.eval_theta(K, N, 0.5), precision)
 
 
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "largest_N256_K128_J200.npz")
+
+
+def rowwise(a, b, floor=0.1):
+    """Worst per-step relative error (step norms floored at `floor` x rms)."""
+    a = np.asarray(a).reshape(len(b), -1)
+    b = np.asarray(b).reshape(len(b), -1)
+    nb = np.linalg.norm(b, axis=1)
+    den = np.maximum(nb, floor * max(np.sqrt(np.mean(nb ** 2)), 1e-300))
+    return float((np.linalg.norm(a - b, axis=1) / den).max())
+
+
+def _interleaved(z):
+    z = np.asarray(z)
+    out = np.empty(z.shape[:-1] + (2 * z.shape[-1],))
+    out[..., 0::2] = z.real
+    out[..., 1::2] = z.imag
+    return out
+
+
 @pytest.fixture(scope="module")
-def largest_truncated():
-    """The N=256, K=128 system of the largest workload on its first 8 steps
-    (same H0, M, target, basis rows and dt) and its oracle evaluation."""
+def largest_200():
+    """The N=256, K=128 system of the largest workload on its first 200 steps
+    (same H0, M, target, basis rows and dt) and the oracle's evaluation of it,
+    stored by tests/golden/make_largest_N256.py."""
     full = inputs.config_problem(5)
-    prob = inputs.Problem(full.H0, full.M, full.alpha, full.beta, full.B[:8], full.dt, full.w_f,
-                          full.w_t, name="largest-8")
+    prob = inputs.Problem(full.H0, full.M, full.alpha, full.beta, full.B[:200], full.dt, full.w_f,
+                          full.w_t, name="largest-200")
     theta = inputs.eval_theta(full.K, 5)
-    return prob, theta, orc.evaluate(prob, theta, order=2)
+    ref = dict(np.load(GOLDEN))
+    np.testing.assert_array_equal(ref["theta"], theta)
+    return prob, theta, ref
 
 
-@pytest.mark.parametrize("block_steps", [1, 2], ids=["per_step", "blocked"])
+@pytest.mark.parametrize("block_steps", [1, None], ids=["per_step", "blocked"])
 @pytest.mark.parametrize("precision", [q.QOC_FP64, q.QOC_MIXED_FP32], ids=["fp64", "mixed"])
-def test_largest_system_truncated(largest_truncated, precision, block_steps):
-    prob, theta, ref = largest_truncated
+def test_largest_system_200_steps(largest_200, precision, block_steps):
+    """N=256, K=128 over 200 steps against the stored oracle evaluation:
+    J, gradient, Hessian and the raw Hessian; g_j, c_j, u_j, v_j and the
+    sampled states, costates and eigenvalues, whole arrays and step by step.
+    On this horizon the binary32 increments stay within the mixed target (the
+    estimate is below 1e-6), so the mixed path runs binary32 sweeps here."""
+    prob, theta, ref = largest_200
     tol = TOL[precision]
+    tin = {q.QOC_FP64: 1e-10, q.QOC_MIXED_FP32: 1e-5}[precision]
+    trow = {q.QOC_FP64: 1e-9, q.QOC_MIXED_FP32: 1e-4}[precision]
     with q.Problem(prob, precision=precision, block_steps=block_steps) as P:
+        assert P.precision()[0] == precision
         J, g, H = P.eval_grad_hess(theta)
-    assert abs(J - ref["J"]) <= tol * abs(ref["J"]), (J, ref["J"])
-    assert rel(g, ref["grad"]) <= tol, rel(g, ref["grad"])
-    assert rel(H, ref["hess"]) <= tol, rel(H, ref["hess"])
+        assert abs(J - ref["J"]) <= tol * abs(ref["J"]), (J, ref["J"])
+        assert rel(g, ref["grad"]) <= tol, rel(g, ref["grad"])
+        assert rel(H, ref["hess"]) <= tol, rel(H, ref["hess"])
+        assert rel(P.buffer(_lib.QOC_BUF_HESS_RAW), ref["hess_raw"]) <= tol
+        np.testing.assert_array_equal(H, H.T)
+        for which, key in ((_lib.QOC_BUF_G, "g"), (_lib.QOC_BUF_C, "c"), (_lib.QOC_BUF_U, "U"),
+                           (_lib.QOC_BUF_V, "V")):
+            got = P.buffer(which)
+            assert rel(got, ref[key]) <= tin, (key, rel(got, ref[key]))
+            assert rowwise(got, ref[key]) <= trow, (key, rowwise(got, ref[key]))
+        rows = ref["step_sample"]
+        a = _interleaved(P.buffer(_lib.QOC_BUF_STATE)[rows])
+        lm = _interleaved(P.buffer(_lib.QOC_BUF_COSTATE)[rows[1:]])
+        assert rowwise(a, ref["a"]) <= trow, rowwise(a, ref["a"])
+        assert rowwise(lm, ref["lam"][1:]) <= trow, rowwise(lm, ref["lam"][1:])
+        lam = P.buffer(_lib.QOC_BUF_EIGVAL)[ref["eig_steps"]]
+        teig = 1e-13 if precision == q.QOC_FP64 else 1e-8   # binary32 sweeps: relaxed refinement
+        assert np.abs(lam - ref["eig"]).max() <= teig * np.abs(ref["eig"]).max() * prob.N
 
 
 def test_largest_system_full_size():
     """N=256, K=128, J=10^4: the binary64 gradient against a central difference
     of J along a random direction and the Hessian against a central difference
-    of the gradient, Hessian symmetry before symmetrisation, norm drift; mixed
-    vs binary64.  At this size the mixed path meets 1e-6 for J and the gradient
-    but not for the Hessian: the binary32 rounding of increments |D_j| ~ 0.2
-    accumulates over 10^4 steps to about 5e-6 (measured 4.6e-6), so the Hessian
-    is held to 1e-5 here; the binary64 path is the one to use for this size."""
+    of the gradient, Hessian symmetry before symmetrisation, norm drift.  At
+    this size binary32 increments cannot meet the mixed target (estimated
+    6e-6): QOC_MIXED_FP32 must choose binary64 sweeps and agree with binary64
+    to 1e-6, while QOC_MIXED_FP32_ALWAYS keeps binary32 and its measured
+    error must follow the estimate (within a factor of 3)."""
     import time
     prob = inputs.config_problem(5)
     theta = inputs.eval_theta(prob.K, 5)
@@ -101,11 +151,20 @@ def test_largest_system_full_size():
         gm = P.eval_grad(theta - h * v)[1]
         assert rel((gp - gm) / (2 * h), H64 @ v) <= 1e-5
     with q.Problem(prob, precision=q.QOC_MIXED_FP32) as P:
-        t0 = time.perf_counter()
+        eff, est = P.precision()
+        assert eff == q.QOC_FP64 and est > 1e-6, (eff, est)
         J32, g32, H32 = P.eval_grad_hess(theta)
-        print(f"N=256 K=128 J=10^4 mixed evaluation: {time.perf_counter() - t0:.2f} s")
     assert abs(J32 - J64) <= 1e-6 * abs(J64)
-    assert rel(g32, g64) <= 1e-6 and rel(H32, H64) <= 1e-5, (rel(g32, g64), rel(H32, H64))
+    assert rel(g32, g64) <= 1e-6 and rel(H32, H64) <= 1e-6, (rel(g32, g64), rel(H32, H64))
+    with q.Problem(prob, precision=q.QOC_MIXED_FP32_ALWAYS) as P:
+        eff, est = P.precision()
+        assert eff == q.QOC_MIXED_FP32
+        t0 = time.perf_counter()
+        Ja, ga, Ha = P.eval_grad_hess(theta)
+        print(f"N=256 K=128 J=10^4 binary32-increment evaluation: {time.perf_counter() - t0:.2f} s; "
+              f"Hessian error {rel(Ha, H64):.2e} against the estimate {est:.2e}")
+    assert abs(Ja - J64) <= 1e-6 * abs(J64) and rel(ga, g64) <= 1e-6
+    assert est / 3 <= rel(Ha, H64) <= 3 * est, (rel(Ha, H64), est)
 
 
 @pytest.mark.parametrize("precision", [q.QOC_FP64, q.QOC_MIXED_FP32], ids=["fp64", "mixed"])

@@ -417,3 +417,57 @@ def test_tr_converges_in_one_step_on_convex_quadratic():
     assert info["stop"] == "gtol"
     assert info["n_eval_gh"] == 2 and info["n_eval_J"] == 1
     assert np.linalg.norm(theta) < 1e-10
+
+
+# --------------------------------------------------------------------------
+# Alg. 1 with the BFGS trust region (Sec. IV-B's gradient-only baseline)
+# --------------------------------------------------------------------------
+
+def test_bfgs_update_secant_symmetry_and_definiteness():
+    """The BFGS update satisfies the secant equation B+ s = y, keeps B
+    symmetric and positive definite when y^T s > 0, and is skipped when the
+    curvature is not positive (Nocedal & Wright, Sec. 6.1)."""
+    rng = np.random.default_rng(5)
+    K = 7
+    A = rng.normal(size=(K, K))
+    B = A @ A.T + K * np.eye(K)
+    for _ in range(5):
+        s = rng.normal(size=K)
+        y = rng.normal(size=K)
+        if y @ s <= 0:
+            y = -y
+        Bp = orc.bfgs_update(B, s, y)
+        np.testing.assert_allclose(Bp @ s, y, rtol=1e-12, atol=1e-12 * np.linalg.norm(y))
+        np.testing.assert_array_equal(Bp, Bp.T)
+        assert np.linalg.eigvalsh(Bp).min() > 0
+        assert orc.bfgs_update(B, s, -y) is B
+        B = Bp
+
+
+def test_bfgs_trust_region_on_convex_quadratic():
+    """w_t = 0: J = w_f |B theta|^2 is a convex quadratic, every y equals
+    A s with A = 2 w_f B^T B; the BFGS trust region must reach the minimiser
+    theta = 0 and its last approximation must satisfy the secant equation of
+    the quadratic along its last step direction."""
+    prob = inputs.small_problem(N=3, K=4, J=30, seed=61, dt=0.05, w_t=0.0)
+    A = 2 * prob.w_f * prob.B.T @ prob.B
+    theta, info = orc.trust_region_solve_bfgs(prob, np.array([0.2, -0.1, 0.3, 0.1]), gtol=1e-10)
+    assert info["stop"] == "gtol", info
+    assert np.linalg.norm(theta) < 1e-9
+    assert np.linalg.eigvalsh(info["hess_approx"]).min() > 0
+    # B reproduces the exact curvature on the span it has explored
+    Bk = info["hess_approx"]
+    assert np.linalg.norm(Bk - A) < np.linalg.norm(A)
+
+
+def test_bfgs_trust_region_reaches_the_exact_minimiser():
+    """From theta = 0 the BFGS (Alg. 1) and exact-Hessian (Alg. 2) trust
+    regions converge to the same local minimiser; the BFGS one needs at
+    least as many iterations."""
+    prob = inputs.small_problem(N=4, K=3, J=50, seed=62, dt=0.05)
+    th2, info2 = orc.trust_region_solve(prob, np.zeros(3), gtol=1e-8, xtol=1e-14)
+    th1, info1 = orc.trust_region_solve_bfgs(prob, np.zeros(3), gtol=1e-8, xtol=1e-14)
+    assert info1["stop"] == "gtol" and info2["stop"] == "gtol", (info1["stop"], info2["stop"])
+    assert np.linalg.norm(th1 - th2) <= 1e-6 * max(1.0, np.linalg.norm(th2))
+    assert abs(info1["J"] - info2["J"]) <= 1e-12 * abs(info2["J"])
+    assert info1["iters"] >= info2["iters"]
