@@ -37,6 +37,7 @@ struct qoc_problem {
   double dt = 0, w_f = 0, w_t = 0, mshift = 0;
   int precision = 0, hess_method = QOC_HESS_SECOND_ORDER_ADJOINT, eig_method = QOC_EIG_REFINED;
   int requested_precision = 0;          // as passed to qoc_create_problem
+  int identity_basis = 0;               // B = I (the maximal model): assembly without the j-sums
   double err_sigma = 0;                 // sigma of the binary32 error estimate (see qoc.h)
   int refine_sweeps = 2;
   double angle_tol = 1e-13;
@@ -316,7 +317,7 @@ qoc_status enqueue_blocked(qoc_problem* p, int order, double* out_dev) {
   if (p->timing) cudaEventRecord(p->ev[5], st);
   QOC_TRY(launch_assemble(p->B, p->Kp, p->f, p->g, p->c, p->V, p->U, mixed, p->SJ, N, J, K,
                           p->w_f, p->w_t, soa ? 0 : 1, order >= 2, p->work, out_dev, p->hess_raw,
-                          p->scal + 2, st));
+                          p->scal + 2, st, p->identity_basis));
   if (p->timing) cudaEventRecord(p->ev[6], st);
   return QOC_OK;
 }
@@ -387,7 +388,7 @@ qoc_status enqueue_eval(qoc_problem* p, const double* theta_dev, int order, doub
   if (p->timing) cudaEventRecord(p->ev[5], st);
   QOC_TRY(launch_assemble(p->B, p->Kp, p->f, p->g, p->c, p->V, p->U, mixed, p->SJ, N, J, K,
                           p->w_f, p->w_t, p->hess_method == QOC_HESS_SECOND_ORDER_ADJOINT ? 0 : 1,
-                          order >= 2, p->work, out_dev, p->hess_raw, p->scal + 2, st));
+                          order >= 2, p->work, out_dev, p->hess_raw, p->scal + 2, st, p->identity_basis));
   if (p->timing) cudaEventRecord(p->ev[6], st);
   return QOC_OK;
 }
@@ -532,6 +533,13 @@ qoc_status qoc_create_problem(int N, const double* H0, const double* M, const do
   // precision policy: binary32 increments unless their estimated error at
   // the default block length exceeds the mixed-precision target
   p->err_sigma = spectral_sigma(N, H0, M, basis, K, J, p->mshift);
+  if (K == J) {
+    bool id = true;
+    for (int j = 0; j < J && id; ++j)
+      for (int l = 0; l < K; ++l)
+        if (basis[(size_t)j * K + l] != (j == l ? 1.0 : 0.0)) { id = false; break; }
+    p->identity_basis = id ? 1 : 0;
+  }
   if (precision == QOC_MIXED_FP32_ALWAYS) p->precision = QOC_MIXED_FP32;
   else if (precision == QOC_MIXED_FP32)
     p->precision = mixed_error_estimate(p, J >= 16 ? 4 : 1) <= kMixedTarget ? QOC_MIXED_FP32 : QOC_FP64;
@@ -1117,7 +1125,7 @@ qoc_status batch_phase(qoc_batch* b, int i, int phase, cudaStream_t s) {
                                       J, bs, 1, mixed, p->V, s));
       QOC_TRY(launch_assemble(p->B, p->Kp, p->f, p->g, p->c, p->V, p->U, mixed, p->SJ, N, J, K,
                               p->w_f, p->w_t, p->hess_method == QOC_HESS_SECOND_ORDER_ADJOINT ? 0 : 1,
-                              1, p->work, out, p->hess_raw, p->scal + 2, s));
+                              1, p->work, out, p->hess_raw, p->scal + 2, s, p->identity_basis));
       return QOC_OK;
   }
 }

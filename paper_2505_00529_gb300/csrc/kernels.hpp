@@ -211,11 +211,13 @@ cudaError_t launch_terminal(const double* f, int J, const void* a_hat, int mixed
                             double2* lamJ, double* cost_out, double* drift_out, cudaStream_t st);
 // grad = B^T (2 w_f f + g); Hess (see qoc.h) into out = [J, grad, Hess], raw Hessian, asymmetry
 // V, U: J x K contractions, double (uv_f32 = 0) or float (uv_f32 = 1)
+// identity != 0: B = I (K = J), the maximal model -- same results without the
+// contraction over j
 cudaError_t launch_assemble(const double* B, int Kp, const double* f, const double* g,
                             const double* c, const void* V, const void* U, int uv_f32,
                             const double2* SJ, int N, int J, int K, double w_f, double w_t,
                             int method, int want_hess, double* work, double* out,
-                            double* hess_raw, double* asym, cudaStream_t st);
+                            double* hess_raw, double* asym, cudaStream_t st, int identity = 0);
 size_t assemble_work_doubles(int J, int K);
 
 // trust-region subproblem on the device (K x K, binary64); work holds

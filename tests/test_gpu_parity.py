@@ -132,6 +132,27 @@ def test_maximal_model():
     check_eval(prob, theta, q.QOC_MIXED_FP32)
 
 
+@pytest.mark.parametrize("method", [q.QOC_HESS_SECOND_ORDER_ADJOINT, q.QOC_HESS_TANGENT], ids=["soa", "tangent"])
+@pytest.mark.parametrize("precision", [q.QOC_FP64, q.QOC_MIXED_FP32], ids=["fp64", "mixed"])
+def test_maximal_model_identity_assembly(precision, method):
+    """Maximal model at J = K = 300 (several assembly chunks, a ragged last
+    one): the identity-basis assembly (no sums over steps) against the
+    oracle, both Hessian forms."""
+    J = 300
+    prob = inputs.small_problem(N=5, K=J, J=J, seed=19, dt=0.05, basis="maximal")
+    theta = inputs.eval_theta(J, 20)
+    ref = orc.evaluate(prob, theta, order=2)
+    tol = TOL[precision]
+    with q.Problem(prob, precision=precision, hess_method=method) as P:
+        Jv, g, H = P.eval_grad_hess(theta)
+        assert abs(Jv - ref["J"]) <= tol * abs(ref["J"])
+        assert rel(g, ref["grad"]) <= tol and rel(H, ref["hess"]) <= tol, (rel(g, ref["grad"]), rel(H, ref["hess"]))
+        np.testing.assert_array_equal(H, H.T)
+        if method == q.QOC_HESS_SECOND_ORDER_ADJOINT:
+            assert rel(P.buffer(_lib.QOC_BUF_HESS_RAW), ref["hess_raw"]) <= tol
+        assert P.diagnostics()["hess_asym"] < 10 * tol
+
+
 def test_zero_control_and_degenerate_spectrum():
     """f = 0 (theta = 0) and an exactly degenerate H0 (repeated energies)."""
     N, K, J, dt = 6, 4, 80, 0.05
