@@ -307,6 +307,32 @@ def run_ours(args):
               "n_eval_gh": info["n_eval_gh"], "n_eval_J": info["n_eval_J"], "J": info["J"],
               "grad_norm": info["grad_norm"], "stop": info["stop"], "gtol": 1e-6}
 
+    # ---- batched trust-region solves: 32 random targets of the same system, from theta = 0 ----
+    trb = None
+    if not args.no_tr:
+        betas = inputs.random_targets(4100, N, 32)
+        Ps = [q.Problem(prob, precision=prec, cuda_stream=stream.cuda_stream) for _ in betas]
+        try:
+            for P, bt in zip(Ps, betas):
+                P.set_target(bt)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            _, infos, _st = q.qoc_batch_trust_region_solve([P.handle for P in Ps], [np.zeros(K)] * len(Ps),
+                                                           gtol=1e-6, xtol=1e-10, max_iter=500,
+                                                           cuda_stream=stream.cuda_stream)
+            t1 = time.perf_counter()
+        finally:
+            for P in Ps:
+                P.close()
+        trb_s = max_over_ranks(t1 - t0, dist, dev)
+        trb = {"value": world * len(betas) / trb_s, "unit": "TR solves/s", "problems": len(betas),
+               "seconds": trb_s, "iters_mean": float(np.mean([i["iters"] for i in infos])),
+               "iters_max": int(max(i["iters"] for i in infos)),
+               "stops": {s_: sum(i["stop"] == s_ for i in infos) for s_ in ("gtol", "xtol", "max_iter",
+                                                                            "no_decrease", "failed")},
+               "how": "qoc_batch_trust_region_solve over 32 random targets of the workload's system, "
+                      "theta0 = 0, gtol 1e-6; every trial point evaluated with its gradient and Hessian"}
+
     # ---- roofline: the binary64-bound kernels against the measured binary64 rate ----
     fp64_tf, fp64_ms = q.qoc_measure_fp64_rate(4, 5)
     ph_mean = {k: statistics.mean(p[k] for p in phases) for k in phases[0]} if phases else {}
@@ -341,7 +367,7 @@ def run_ours(args):
                         "h2d_bytes_per_step": 8 * K, "d2h_bytes_per_step": 8 * (1 + K + K * K)},
                 "gpu_launches": LAUNCHES_PER_EVAL * args.steps,
                 "clocks": clocks, "roofline": roof, "cpu_baseline": cpu,
-                "fp64_plain": fp64, "tr_solve": tr,
+                "fp64_plain": fp64, "tr_solve": tr, "tr_solve_batched": trb,
                 "fp64_fma_peak": {"tflops": fp64_tf, "ms": fp64_ms, "how": "qoc_measure_fp64_rate: "
                                   "independent binary64 FMA chains, 4 CTAs x 256 threads per SM, best of 5"},
                 "other_workloads": extra}

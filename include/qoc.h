@@ -160,6 +160,21 @@ qoc_status qoc_eval_grad(qoc_problem* p, const double* theta, double* J, double*
 qoc_status qoc_eval_grad_hess(qoc_problem* p, const double* theta, double* J,
                               double* grad, double* hess);
 
+/* Control models that are not linear in theta (f(t; theta), e.g. a neural
+ * network in t, Sec. III-D; Eq. d2Ldf2 with its d^2 f / dtheta^2 terms).
+ * The caller gives, at its current theta, the samples f (steps doubles, f_j =
+ * f(j dt; theta)) and the Jacobian jac (steps x K row-major, jac[j*K + l] =
+ * d f_j / d theta_l).  Returns J, grad = jac^T d, the symmetrised Hessian
+ * WITHOUT the model's second-derivative term,
+ *   hess = jac^T diag(2 w_ctrl + c) jac + jac^T V + jac^T U,
+ * and dJdf (steps doubles): d_j = dJ/df_j = 2 w_ctrl f_j + g_j.  The full
+ * Hessian is hess + sum_j d_j d^2 f_j / dtheta^2, the last term being the
+ * model's own (its second derivatives, which only the caller knows).  The
+ * Jacobian replaces the problem's basis: later theta-evaluations use it as
+ * the linear model.  Synchronises; host pointers. */
+qoc_status qoc_eval_grad_hess_model(qoc_problem* p, const double* f, const double* jac, double* J,
+                                    double* grad, double* hess, double* dJdf);
+
 /* Device-pointer form of qoc_eval_grad_hess: theta_dev (K doubles) is read
  * and out_dev (1 + K + K*K doubles: J, grad, Hess row-major) written on the
  * problem's stream; returns after enqueueing.  Device-side failures
@@ -213,12 +228,30 @@ qoc_status qoc_trust_region_solve_bfgs(qoc_problem* p, const double* theta0,
                                        const qoc_tr_options* opt, double* theta_out,
                                        qoc_tr_report* report);
 
-/* Diagnostics of the last evaluation (host doubles):
- *   out[0] = max_j | |a_j| - 1 |   (norm drift of the propagated state)
- *   out[1] = |Hess - Hess^T|_F / |Hess|_F before symmetrisation
- *   out[2..7] = milliseconds of the phases eig, prep, chains, pointwise,
- *               panels, assembly (only when timing was enabled, else 0). */
-qoc_status qoc_get_diagnostics(const qoc_problem* p, double* out /* [8] */);
+/* One trust-region subproblem (the step both trust regions take, Sec. IV-B;
+ * Nocedal & Wright Sec. 4.3): s minimising g^T s + s^T H s / 2 subject to
+ * |s| <= radius, exactly (secular equation |s(sigma)| = radius with
+ * s(sigma) = -(H + sigma I)^-1 g, sigma >= max(0, -lambda_min(H)), and the
+ * hard case), in binary64 on the device.
+ *   K        size (1 <= K <= 4096); g: K host doubles; H: K*K symmetric host doubles.
+ *   method   0: as the solvers choose it (1 for K < 48, 2 from 48);
+ *            1: through the eigendecomposition of H (binary64 Jacobi);
+ *            2: through the Householder tridiagonal reduction of H, Sturm
+ *               bisection for lambda_min and tridiagonal LDL^T solves.
+ *   s        K host doubles (output).
+ *   info     4 host doubles (output): predicted decrease -(g^T s + s^T H s / 2),
+ *            |s|, sigma, |g|.
+ * Allocates and frees its device memory; synchronises. */
+qoc_status qoc_tr_subproblem(int K, const double* g, const double* H, double radius, int method,
+                             double* s, double* info);
+
+/* Diagnostics of the last evaluation (host doubles; each pointer may be NULL):
+ *   norm_drift   max_j | |a_j| - 1 |   (norm drift of the propagated state)
+ *   hess_asym    |Hess - Hess^T|_F / |Hess|_F before symmetrisation
+ *   phase_ms[6]  milliseconds of the phases eig, prep, chains, pointwise,
+ *                panels, assembly (only when timing was enabled, else 0). */
+qoc_status qoc_get_diagnostics(const qoc_problem* p, double* norm_drift, double* hess_asym,
+                               double* phase_ms /* [6] */);
 
 /* Per-kernel timing of the last evaluation (timing enabled), milliseconds
  * between events, in this order:

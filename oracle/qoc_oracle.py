@@ -266,7 +266,28 @@ def evaluate(prob, theta, order=2, keep=False):
     Returns a dict with J, grad, (hess, hess_raw, asym, c, V, U) and, with
     keep=True, every stored intermediate."""
     theta = np.asarray(theta, float)
-    f = control_signal(prob.B, theta)
+    return evaluate_samples(prob, control_signal(prob.B, theta), prob.B, order, keep)
+
+
+def evaluate_model(prob, f, jac, order=2):
+    """Alg. 2 for a control model f(t; theta) that need not be linear in
+    theta: the samples f_j and the Jacobian rows b_j = df_j/dtheta at the
+    current theta are given.  Eq. d2Ldf2 then carries, besides the linear
+    model's terms, sum_j d_j d^2 f_j/dtheta^2 with d_j = dJ/df_j =
+    2 w_f f_j + g_j (its control-cost part and the dexp.M bracket with the
+    second derivative of f); that term belongs to the model.  Returns the
+    dict of evaluate() for (f, jac) -- grad = jac^T d and hess the Hessian
+    without the model's second-derivative term -- plus "d"."""
+    f = np.asarray(f, float)
+    jac = np.asarray(jac, float)
+    out = evaluate_samples(prob, f, jac, order)
+    if order >= 1:
+        out["d"] = 2 * prob.w_f * f + out["g"]
+    return out
+
+
+def evaluate_samples(prob, f, B, order=2, keep=False):
+    """Alg. 2 / Alg. 1 from the control samples f and the rows b_j of B."""
     H = step_hamiltonians(prob.H0, prob.M, f)
     lam_e, W = eigensystems(H)                       # first loop: store V_j, D_j
     U = propagators(W, lam_e, prob.dt)
@@ -279,13 +300,13 @@ def evaluate(prob, theta, order=2, keep=False):
         return out
     lam = costates(U, a[-1], prob.beta, prob.w_t)   # second loop
     G = frechet1(W, lam_e, prob.M, prob.dt)          # third loop: dexp . M
-    grad, g = gradient(prob.B, f, prob.w_f, G, a, lam)
+    grad, g = gradient(B, f, prob.w_f, G, a, lam)
     out.update(grad=grad, g=g)
     if order >= 2:
         G2 = frechet2(W, lam_e, prob.M, prob.dt)     # third loop: d^2exp . (M x M)
-        S = tangents(U, G, a, prob.B)                # fourth loop
-        mu = second_adjoints(U, G, lam, S[-1], prob.B, prob.w_t)  # fifth loop
-        Hraw, c, V, Uc = hessian(prob.B, prob.w_f, G, G2, a, lam, S, mu)
+        S = tangents(U, G, a, B)                # fourth loop
+        mu = second_adjoints(U, G, lam, S[-1], B, prob.w_t)  # fifth loop
+        Hraw, c, V, Uc = hessian(B, prob.w_f, G, G2, a, lam, S, mu)
         nrm = np.linalg.norm(Hraw)
         out.update(hess=0.5 * (Hraw + Hraw.T), hess_raw=Hraw,
                    asym=float(np.linalg.norm(Hraw - Hraw.T) / max(nrm, 1e-300)),

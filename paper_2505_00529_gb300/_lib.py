@@ -33,7 +33,8 @@ EXPORTS = [
     "qoc_batch_eval_grad_hess_dev", "qoc_batch_destroy", "qoc_assemble_noalloc_scratch_doubles",
     "qoc_assemble_grad_hess_noalloc", "qoc_get_phase_times", "qoc_get_eig_stats",
     "qoc_set_panel_columns", "qoc_get_precision", "qoc_measure_fp64_rate",
-    "qoc_batch_trust_region_solve", "qoc_trust_region_solve_bfgs",
+    "qoc_batch_trust_region_solve", "qoc_trust_region_solve_bfgs", "qoc_tr_subproblem",
+    "qoc_eval_grad_hess_model",
 ]
 
 
@@ -92,7 +93,9 @@ def lib() -> C.CDLL:
                                              C.POINTER(TrReport)]
         L.qoc_trust_region_solve_bfgs.argtypes = [C.c_void_p, _dp, C.POINTER(TrOptions), _dp,
                                                   C.POINTER(TrReport)]
-        L.qoc_get_diagnostics.argtypes = [C.c_void_p, _dp]
+        L.qoc_tr_subproblem.argtypes = [C.c_int, _dp, _dp, C.c_double, C.c_int, _dp, _dp]
+        L.qoc_eval_grad_hess_model.argtypes = [C.c_void_p, _dp, _dp, _dp, _dp, _dp, _dp]
+        L.qoc_get_diagnostics.argtypes = [C.c_void_p, _dp, _dp, _dp]
         L.qoc_get_phase_times.argtypes = [C.c_void_p, _dp, C.c_int]
         L.qoc_get_eig_stats.argtypes = [C.c_void_p, _dp]
         L.qoc_enable_timing.argtypes = [C.c_void_p, C.c_int]
@@ -235,6 +238,20 @@ def qoc_eval_grad_hess(h, theta):
     return float(J[0]), g, H
 
 
+def qoc_eval_grad_hess_model(h, f, jac):
+    """(J, grad, hess without the model term, dJ/df) for samples f and Jacobian jac."""
+    f = _f64(f).ravel()
+    jac = _f64(jac)
+    K = jac.shape[1]
+    J = C.c_double(0.0)
+    g = np.zeros(K)
+    H = np.zeros((K, K))
+    d = np.zeros(f.size)
+    _check(lib().qoc_eval_grad_hess_model(C.c_void_p(h), _ptr(f), _ptr(jac), C.byref(J), _ptr(g), _ptr(H),
+                                          _ptr(d)), "qoc_eval_grad_hess_model")
+    return J.value, g, H, d
+
+
 def qoc_eval_grad_hess_dev(h, theta_dev_ptr: int, out_dev_ptr: int):
     """Device pointers (e.g. torch tensor .data_ptr()); enqueues and returns."""
     _check(lib().qoc_eval_grad_hess_dev(C.c_void_p(h), C.c_void_p(int(theta_dev_ptr)),
@@ -290,11 +307,26 @@ def qoc_batch_trust_region_solve(handles, theta0s, gtol=1e-10, xtol=1e-10, radiu
     return thetas, infos, s
 
 
+def qoc_tr_subproblem(g, H, radius, method=0):
+    """(s, info) of one trust-region subproblem; info = [pred, |s|, sigma, |g|]."""
+    g = _f64(g).ravel()
+    H = _f64(H)
+    K = g.size
+    s = np.zeros(K)
+    info = np.zeros(4)
+    _check(lib().qoc_tr_subproblem(K, _ptr(g), _ptr(H), float(radius), int(method), _ptr(s), _ptr(info)),
+           "qoc_tr_subproblem")
+    return s, info
+
+
 def qoc_get_diagnostics(h):
-    out = np.zeros(8)
-    _check(lib().qoc_get_diagnostics(C.c_void_p(h), _ptr(out)), "qoc_get_diagnostics")
-    return {"norm_drift": out[0], "hess_asym": out[1],
-            "phase_ms": dict(zip(["eig", "prep", "chains", "pointwise", "panels", "assembly"], out[2:]))}
+    drift = C.c_double(0.0)
+    asym = C.c_double(0.0)
+    ph = np.zeros(6)
+    _check(lib().qoc_get_diagnostics(C.c_void_p(h), C.byref(drift), C.byref(asym), _ptr(ph)),
+           "qoc_get_diagnostics")
+    return {"norm_drift": drift.value, "hess_asym": asym.value,
+            "phase_ms": dict(zip(["eig", "prep", "chains", "pointwise", "panels", "assembly"], ph))}
 
 
 PHASES = ["control", "eig_jacobi", "eig_refine", "prep_D", "deriv_prep", "chains", "pointwise",
@@ -503,6 +535,9 @@ class Problem:
 
     def eval_grad_hess(self, theta):
         return qoc_eval_grad_hess(self.handle, theta)
+
+    def eval_grad_hess_model(self, f, jac):
+        return qoc_eval_grad_hess_model(self.handle, f, jac)
 
     def trust_region_solve(self, theta0, **kw):
         return qoc_trust_region_solve(self.handle, theta0, **kw)

@@ -330,7 +330,8 @@ qoc_status enqueue_eval(qoc_problem* p, const double* theta_dev, int order, doub
   const int mixed = p->precision == QOC_MIXED_FP32 ? 1 : 0;
   const int d_fp64 = mixed ? 0 : 1;
   if (p->timing) cudaEventRecord(p->ev[0], st);
-  QOC_TRY(launch_control(p->B, p->Kp, theta_dev, J, K, p->f, st));
+  // theta_dev == nullptr: the samples f are already in p->f (a model evaluation)
+  if (theta_dev) QOC_TRY(launch_control(p->B, p->Kp, theta_dev, J, K, p->f, st));
   if (p->timing) {
     cudaEventRecord(p->ev[7], st);
     QOC_TRY(cudaMemsetAsync(p->eigstats, 0, 4 * sizeof(unsigned int), st));
@@ -456,7 +457,7 @@ void qoc::note_error(const char* msg) { std::snprintf(g_last_error, sizeof(g_las
 
 extern "C" {
 
-int qoc_version(void) { return 100; }
+int qoc_version(void) { return 200; }
 
 const char* qoc_last_error(void) { return g_last_error; }
 int qoc_max_basis_size(void) { return kMaxN; }
@@ -754,6 +755,48 @@ qoc_status qoc_eval_grad_hess(qoc_problem* p, const double* theta, double* J, do
   return eval_host(p, theta, 2, J, grad, hess);
 }
 
+qoc_status qoc_eval_grad_hess_model(qoc_problem* p, const double* f, const double* jac, double* J,
+                                    double* grad, double* hess, double* dJdf) {
+  if (!p || !f || !jac || !J || !grad || !hess || !dJdf) return QOC_EINVAL;
+  const int K = p->K, Jn = p->J, Kp = p->Kp;
+  if (!finite_all(f, Jn) || !finite_all(jac, (size_t)Jn * K)) return QOC_EINVAL;
+  // the Jacobian becomes the problem's basis (padded to Kp columns, with its binary32 copy)
+  std::vector<double> Bp((size_t)Jn * Kp, 0.0);
+  std::vector<float> Bfp((size_t)Jn * Kp, 0.0f);
+  bool id = K == Jn;
+  for (int j = 0; j < Jn; ++j)
+    for (int l = 0; l < K; ++l) {
+      const double v = jac[(size_t)j * K + l];
+      Bp[(size_t)j * Kp + l] = v;
+      Bfp[(size_t)j * Kp + l] = (float)v;
+      if (v != (j == l ? 1.0 : 0.0)) id = false;
+    }
+  QOC_TRY(cudaStreamSynchronize(p->stream));
+  QOC_TRY(cudaMemcpy(p->B, Bp.data(), 8 * Bp.size(), cudaMemcpyHostToDevice));
+  QOC_TRY(cudaMemcpy(p->Bf, Bfp.data(), 4 * Bfp.size(), cudaMemcpyHostToDevice));
+  QOC_TRY(cudaMemcpy(p->f, f, 8 * (size_t)Jn, cudaMemcpyHostToDevice));
+  p->identity_basis = id ? 1 : 0;
+  const size_t nout = 1 + (size_t)K + (size_t)K * K;
+  qoc_status s = enqueue_eval(p, nullptr, 2, p->out);
+  if (s != QOC_OK) return s;
+  std::vector<double> o(nout), g(Jn);
+  QOC_TRY(cudaMemcpyAsync(o.data(), p->out, 8 * nout, cudaMemcpyDeviceToHost, p->stream));
+  QOC_TRY(cudaMemcpyAsync(g.data(), p->g, 8 * (size_t)Jn, cudaMemcpyDeviceToHost, p->stream));
+  QOC_TRY(cudaMemcpyAsync(p->hstatus, p->status, sizeof(int), cudaMemcpyDeviceToHost, p->stream));
+  QOC_TRY(cudaMemsetAsync(p->status, 0, sizeof(int), p->stream));
+  QOC_TRY(cudaStreamSynchronize(p->stream));
+  collect_timing(p);
+  p->last_order = 2;
+  s = device_status(p);
+  if (s != QOC_OK) return s;
+  *J = o[0];
+  std::memcpy(grad, o.data() + 1, 8 * (size_t)K);
+  std::memcpy(hess, o.data() + 1 + K, 8 * (size_t)K * K);
+  for (int j = 0; j < Jn; ++j) dJdf[j] = 2.0 * p->w_f * f[j] + g[j];
+  if (!finite_all(o.data(), nout)) return QOC_ENUMERIC;
+  return QOC_OK;
+}
+
 qoc_status qoc_eval_grad_hess_dev(qoc_problem* p, const double* theta_dev, double* out_dev) {
   if (!p || !theta_dev || !out_dev) return QOC_EINVAL;
   p->last_order = 2;
@@ -769,11 +812,13 @@ qoc_status qoc_sync_status(qoc_problem* p) {
   return device_status(p);
 }
 
-qoc_status qoc_get_diagnostics(const qoc_problem* p, double* out) {
-  if (!p || !out) return QOC_EINVAL;
-  out[0] = p->diag[0];
-  out[1] = p->diag[1];
-  for (int k = 0; k < 6; ++k) out[2 + k] = p->timing ? p->phase_ms[k] : 0.0;
+qoc_status qoc_get_diagnostics(const qoc_problem* p, double* norm_drift, double* hess_asym,
+                               double* phase_ms) {
+  if (!p) return QOC_EINVAL;
+  if (norm_drift) *norm_drift = p->diag[0];
+  if (hess_asym) *hess_asym = p->diag[1];
+  if (phase_ms)
+    for (int k = 0; k < 6; ++k) phase_ms[k] = p->timing ? p->phase_ms[k] : 0.0;
   return QOC_OK;
 }
 
@@ -902,8 +947,9 @@ qoc_status qoc_trust_region_solve(qoc_problem* p, const double* theta0, const qo
   auto eval_gh = [&]() -> qoc_status {
     qoc_status s = enqueue_eval(p, p->theta, 2, p->out);
     if (s != QOC_OK) return s;
-    QOC_TRY(launch_eig(p->out + 1 + K, p->trzero, p->trzero, K, 1, p->trwork + 3 * K,
-                       p->trwork + 2 * K, p->status, EIG_JACOBI_FP64, 0, 0.0, st, p->ws[0]));
+    if (tr_needs_eig(K))
+      QOC_TRY(launch_eig(p->out + 1 + K, p->trzero, p->trzero, K, 1, p->trwork + 3 * K,
+                         p->trwork + 2 * K, p->status, EIG_JACOBI_FP64, 0, 0.0, st, p->ws[0]));
     QOC_TRY(cudaMemcpyAsync(p->hstatus, p->status, sizeof(int), cudaMemcpyDeviceToHost, st));
     QOC_TRY(cudaMemsetAsync(p->status, 0, sizeof(int), st));
     QOC_TRY(cudaStreamSynchronize(st));
@@ -990,8 +1036,9 @@ qoc_status qoc_trust_region_solve_bfgs(qoc_problem* p, const double* theta0, con
   double* hs = p->hbuf + K;
   int it = 0, stop = 2;
   for (it = 1; it <= opt->max_iter; ++it) {
-    QOC_TRY(launch_eig(Bm, p->trzero, p->trzero, K, 1, p->trwork + 3 * K, p->trwork + 2 * K, p->status,
-                       EIG_JACOBI_FP64, 0, 0.0, st, p->ws[0]));
+    if (tr_needs_eig(K))
+      QOC_TRY(launch_eig(Bm, p->trzero, p->trzero, K, 1, p->trwork + 3 * K, p->trwork + 2 * K, p->status,
+                         EIG_JACOBI_FP64, 0, 0.0, st, p->ws[0]));
     QOC_TRY(launch_tr_subproblem(p->out, K, radius, p->trwork, p->trstep, p->trinfo, p->status, st));
     QOC_TRY(launch_axpy(p->theta, p->trstep, K, p->theta_trial, st));
     s = enqueue_eval(p, p->theta_trial, 1, p->out_trial);
@@ -1397,6 +1444,7 @@ qoc_status tr_eval_trials(TrBatchRun& run) {
   for (size_t k = 0; k < run.act.size(); ++k) {
     qoc_problem* p = run.P[run.act[k]];
     const int K = p->K;
+    if (!tr_needs_eig(K)) continue;   // the subproblem reduces the Hessian itself
     double* e = run.etrial + run.eoff[run.act[k]];
     QOC_TRY(launch_eig(run.b->out + run.b->ooff[k] + 1 + K, p->trzero, p->trzero, K, 1, e + K, e,
                        p->status, EIG_JACOBI_FP64, 0, 0.0, run.st, p->ws[0]));

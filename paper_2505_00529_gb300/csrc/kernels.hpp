@@ -220,12 +220,19 @@ cudaError_t launch_assemble(const double* B, int Kp, const double* f, const doub
                             double* hess_raw, double* asym, cudaStream_t st, int identity = 0);
 size_t assemble_work_doubles(int J, int K);
 
-// trust-region subproblem on the device (K x K, binary64); work holds
-// [gt (K) | st (K) | eigenvalues d (K) | eigenvectors Q (K*K)]
+// trust-region subproblem on the device (K x K, binary64).  K < kTriMin: from
+// the Hessian's eigendecomposition, expected in work as [gt (K) | st (K) |
+// eigenvalues d (K) | eigenvectors Q (K*K)]; K >= kTriMin: from the Hessian in
+// out_gh itself by tridiagonal reduction (no eigendecomposition needed;
+// work then holds that method's 8K + K*K scratch)
+constexpr int kTriMin = 48;
+__host__ __device__ inline bool tr_needs_eig(int K) { return K < kTriMin; }
 size_t tr_work_doubles(int K);
 cudaError_t launch_axpy(const double* x, const double* s, int K, double* y, cudaStream_t st);
+// method: 0 by K, 1 eigendecomposition (expected in work), 2 tridiagonal reduction
 cudaError_t launch_tr_subproblem(const double* out_gh, int K, double radius, double* work,
-                                 double* step, double* info, int* status, cudaStream_t st);
+                                 double* step, double* info, int* status, cudaStream_t st,
+                                 int method = 0);
 
 // BFGS update of the K x K model Hessian B from the step s and the gradients
 // (state[0]: 0 until the first update with positive curvature scales B, then 1);

@@ -15,9 +15,11 @@
 // X' is formed from the commutator identity
 //   sum_r M~_pr M~_rq phi[l_p, l_r, l_q] = ((P~ M~)_pq - (P~ M~)_qp) / (l_p - l_q)
 // (the recurrence phi[p,r,q] = (phi[p,r] - phi[r,q]) / (l_p - l_q) summed over
-// r), which costs one complex-by-real N^3 product, and from the direct
-// N-term sum with a stable second divided difference for the pairs with
-// dt |l_p - l_q| <= TAU_DD2 (always including p == q).
+// r), which costs one complex-by-real N^3 product, for the pairs with
+// dt |l_p - l_q| > TAU_DD2; on the diagonal from the same recurrence term by
+// term (phi[p,r,p] = (Gamma1_pp - Gamma1_pr) / (l_p - l_r) for far r, the stable
+// series for near r); and for the remaining near pairs from the direct N-term
+// sum with a stable second divided difference.
 #include <type_traits>
 
 #include "common.cuh"
@@ -100,23 +102,6 @@ __device__ __forceinline__ void tri_index(int t, int N, int& i, int& k) {
   k = t - (r * N - r * (r - 1) / 2) + r;
 }
 
-// Near pairs (dt |l_p - l_q| <= TAU_DD2, always p == q) take the direct sum
-// sum_r M~_pr M~_rq phi[l_p, l_r, l_q], one warp per pair with the lanes over
-// r, so that the binary64 pipe is never held by a single active lane.
-__device__ __forceinline__ double2 dd2_table(int a, int b, int c, const double* lam,
-                                             const double2* G, int ldg, const double2* eh,
-                                             double dt) {
-  int lo = a, mid = b, hi = c;
-  if (lam[lo] > lam[mid]) { int t = lo; lo = mid; mid = t; }
-  if (lam[mid] > lam[hi]) { int t = mid; mid = hi; hi = t; }
-  if (lam[lo] > lam[mid]) { int t = lo; lo = mid; mid = t; }
-  if (dt * (lam[hi] - lam[lo]) > TAU_DD2) {
-    const double2 g1 = G[lo * ldg + mid], g2 = G[mid * ldg + hi];
-    return cscale(csub(g1, g2), 1.0 / (lam[lo] - lam[hi]));
-  }
-  return dd2_dev(a, b, c, lam, eh, dt);
-}
-
 __device__ __forceinline__ void prep_step(const double* __restrict__ Wg,
                                           const double* __restrict__ eig,
                                           const double* __restrict__ Mg, int N, int j, double dt,
@@ -192,11 +177,6 @@ __device__ __forceinline__ void prep_step(const double* __restrict__ Wg,
   }
   }
   if (!doX) return;
-  // list the near pairs (p <= q)
-  for (int e = tid; e < N * N; e += nt) {
-    const int p = e / N, q = e % N;
-    if (q >= p && !(dt * fabs(lam[p] - lam[q]) > TAU_DD2)) near[atomicAdd(&n_near, 1)] = p * N + q;
-  }
   __syncthreads();
   // Y = P~ M~  (W, T are dead: Y overlays them)
   for (int e = tid; e < N * N; e += nt) {
@@ -210,31 +190,70 @@ __device__ __forceinline__ void prep_step(const double* __restrict__ Wg,
     Y[p * ld + q] = make_double2(re, im);
   }
   __syncthreads();
-  // P~ is dead: Gamma1 table in its place
-  for (int e = tid; e < N * N; e += nt) {
-    const int p = e / N, q = e % N;
-    P[p * ld + q] = gamma1(p, q, lam, eh, dt);
-  }
-  __syncthreads();
   double2* Xg = Xp + (size_t)j * N * N;
   bool bad = false;
-  // far pairs: commutator form
-  for (int e = tid; e < N * N; e += nt) {
-    const int p = e / N, q = e % N;
-    if (!(dt * fabs(lam[p] - lam[q]) > TAU_DD2)) continue;
-    const double2 d = csub(Y[p * ld + q], Y[q * ld + p]);
-    const double2 x = cscale(d, 2.0 / (lam[p] - lam[q]));
+  // Pairs p < q.  Far (dt |l_p - l_q| > TAU_DD2): X' is symmetric, so one
+  // thread forms X'_pq = X'_qp = 2 (Y_pq - Y_qp) / (l_p - l_q) and leaves the
+  // reciprocal of l_p - l_q (and of l_q - l_p) in the real part of its two
+  // (now dead) Y entries for the diagonal sums below.  Near: listed for the
+  // direct sum, their Y entries zeroed as the mark.
+  for (int t = tid; t < NT; t += nt) {
+    int p, q;
+    tri_index(t, N, p, q);
+    if (p == q) continue;
+    const double dl = lam[p] - lam[q];
+    if (!(dt * fabs(dl) > TAU_DD2)) {
+      near[atomicAdd(&n_near, 1)] = p * N + q;
+      Y[p * ld + q].x = 0.0;
+      Y[q * ld + p].x = 0.0;
+      continue;
+    }
+    const double rec = 1.0 / dl;
+    const double2 x = cscale(csub(Y[p * ld + q], Y[q * ld + p]), 2.0 * rec);
     bad |= !(isfinite(x.x) && isfinite(x.y));
-    Xg[e] = x;
+    Xg[(size_t)p * N + q] = x;
+    Xg[(size_t)q * N + p] = x;
+    Y[p * ld + q].x = rec;
+    Y[q * ld + p].x = -rec;
   }
-  // near pairs: one warp per pair, lanes over r
+  __syncthreads();
   const int warp = tid >> 5, lane = tid & 31, nwarp = (nt + 31) >> 5;
+  // Diagonal: X'_pp = 2 sum_r M~_pr^2 phi[l_p, l_r, l_p], one warp per p, lanes
+  // over r.  For far r the recurrence on the extremes gives
+  // phi[l_p, l_r, l_p] = (Gamma1_pp - Gamma1_pr) / (l_p - l_r), so the term is
+  // M~_pr (Gamma1_pp M~_pr - P~_pr) / (l_p - l_r) (P~ = Gamma1 o M~); near r
+  // (r = p included) takes the stable series.
+  for (int p = warp; p < N; p += nwarp) {
+    const double2 gpp = gamma1(p, p, lam, eh, dt);
+    double re = 0, im = 0;
+    for (int r = lane; r < N; r += 32) {
+      const double m = Mt[p * ld + r];
+      const double rec = r == p ? 0.0 : Y[p * ld + r].x;
+      double2 term;
+      if ((__double_as_longlong(rec) << 1) != 0) {    // rec != 0: a far pair
+        const double2 tr = csub(cscale(gpp, m), P[p * ld + r]);
+        term = cscale(tr, m * rec);
+      } else {
+        term = cscale(dd2_dev(p, r, p, lam, eh, dt), m * m);
+      }
+      re += term.x;
+      im += term.y;
+    }
+    re = warp_sum(re);
+    im = warp_sum(im);
+    if (lane == 0) {
+      const double2 x = make_double2(2.0 * re, 2.0 * im);
+      bad |= !(isfinite(x.x) && isfinite(x.y));
+      Xg[(size_t)p * N + p] = x;
+    }
+  }
+  // near pairs p < q: the direct N-term sum, one warp per pair, lanes over r
   for (int k = warp; k < n_near; k += nwarp) {
     const int p = near[k] / N, q = near[k] % N;
     double re = 0, im = 0;
     for (int r = lane; r < N; r += 32) {
       const double m2 = Mt[p * ld + r] * Mt[r * ld + q];
-      const double2 g2 = dd2_table(p, r, q, lam, P, ld, eh, dt);
+      const double2 g2 = dd2_dev(p, r, q, lam, eh, dt);
       re = fma(m2, g2.x, re);
       im = fma(m2, g2.y, im);
     }

@@ -13,6 +13,7 @@
 // with a multiple of the lowest eigenvector.  One CTA, binary64.
 #include "common.cuh"
 #include "kernels.hpp"
+#include "qoc.h"
 
 namespace qoc {
 
@@ -145,12 +146,271 @@ __device__ void tr_subproblem_body(const double* __restrict__ gh, const double* 
   __syncthreads();
 }
 
+// ---------------------------------------------------------------------------
+// The same subproblem without the eigendecomposition (K >= kTriMin): the
+// Hessian is reduced to tridiagonal form T = Q^T Hess Q by Householder
+// reflections (Golub & Van Loan, Sec. 8.3.1), the secular equation is solved
+// on T with tridiagonal LDL^T solves of (T + sigma I) x = -Q^T g, and the step
+// is mapped back with Q.  The lowest eigenvalue of T (the bracket of sigma)
+// comes from bisection on Sturm sequence counts; in the hard case its
+// eigenvector comes from inverse iteration.  The reduction costs 4K^3/3
+// flops where the binary64 Jacobi costs about ten sweeps of 3K^3.
+// work: [gt K | st K | a K | b K | beta K | u K | w K | z K | A K*K] (8K + K*K)
+// ---------------------------------------------------------------------------
+
+// (T + sigma I) x = r by LDL^T without pivoting (T + sigma I positive
+// definite); l, dd: K scratch each.  One thread.
+__device__ void tri_solve(const double* a, const double* b, int K, double sigma, const double* r,
+                          double* x, double* l, double* dd) {
+  dd[0] = a[0] + sigma;
+  x[0] = r[0];
+  for (int i = 1; i < K; ++i) {
+    l[i] = b[i - 1] / dd[i - 1];
+    dd[i] = (a[i] + sigma) - l[i] * b[i - 1];
+    x[i] = r[i] - l[i] * x[i - 1];
+  }
+  x[K - 1] = x[K - 1] / dd[K - 1];
+  for (int i = K - 2; i >= 0; --i) x[i] = x[i] / dd[i] - l[i + 1] * x[i + 1];
+}
+
+// number of eigenvalues of T below x (Sturm sequence of the LDL^T pivots)
+__device__ int sturm_count(const double* a, const double* b, int K, double x) {
+  int cnt = 0;
+  double q = a[0] - x;
+  if (q < 0) ++cnt;
+  for (int i = 1; i < K; ++i) {
+    if (q == 0) q = 1e-300;
+    q = (a[i] - x) - b[i - 1] * b[i - 1] / q;
+    if (q < 0) ++cnt;
+  }
+  return cnt;
+}
+
+__device__ double dot_norm(const double* x, int K) {
+  double s = 0;
+  for (int i = 0; i < K; ++i) s = fma(x[i], x[i], s);
+  return sqrt(s);
+}
+
+__device__ void tr_subproblem_tri_body(const double* __restrict__ gh, int K, double radius,
+                                       double* __restrict__ work, double* __restrict__ step,
+                                       double* __restrict__ info, int* status, double* red) {
+  double* gt = work;
+  double* st = gt + K;
+  double* a = st + K;
+  double* b = a + K;
+  double* bet = b + K;
+  double* u = bet + K;
+  double* w = u + K;
+  double* z = w + K;
+  double* A = z + K;
+  const double* H = gh + 1 + K;
+  const double* g = gh + 1;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  for (int e = tid; e < K * K; e += nt) A[e] = H[e];
+  for (int l = tid; l < K; l += nt) gt[l] = g[l];
+  __syncthreads();
+  // ---- Householder reduction: column k below the diagonal -> b_k e_1 ----
+  for (int k = 0; k + 2 < K; ++k) {
+    const int n = K - k - 1;
+    double xs = 0;
+    for (int i = tid; i < n; i += nt) {
+      const double x = A[(size_t)(k + 1 + i) * K + k];
+      xs = fma(x, x, xs);
+    }
+    xs = block_sum(xs, red);
+    const double x0 = A[(size_t)(k + 1) * K + k];
+    const double nrm = sqrt(xs);
+    const double alpha = x0 >= 0 ? -nrm : nrm;
+    const double vtv = xs - 2.0 * alpha * x0 + alpha * alpha;
+    const double beta = (nrm > 0 && vtv > 0) ? 2.0 / vtv : 0.0;
+    for (int i = tid; i < n; i += nt) u[i] = i == 0 ? x0 - alpha : A[(size_t)(k + 1 + i) * K + k];
+    if (tid == 0) {
+      a[k] = A[(size_t)k * K + k];
+      b[k] = beta != 0.0 ? alpha : x0;
+      bet[k] = beta;
+    }
+    __syncthreads();
+    if (beta != 0.0) {
+      // p = beta A22 u, then w = p - (beta/2)(p^T u) u, A22 -= u w^T + w u^T
+      double pu = 0;
+      for (int i = tid; i < n; i += nt) {
+        const double* row = A + (size_t)(k + 1 + i) * K + (k + 1);
+        double acc = 0;
+        for (int j = 0; j < n; ++j) acc = fma(row[j], u[j], acc);
+        w[i] = beta * acc;
+        pu = fma(w[i], u[i], pu);
+      }
+      pu = block_sum(pu, red);
+      const double c = 0.5 * beta * pu;
+      for (int i = tid; i < n; i += nt) w[i] -= c * u[i];
+      __syncthreads();
+      for (int e = tid; e < n * n; e += nt) {
+        const int i = e / n, j = e % n;
+        A[(size_t)(k + 1 + i) * K + (k + 1 + j)] -= u[i] * w[j] + w[i] * u[j];
+      }
+    }
+    // the reflector's vector replaces column k below the diagonal
+    for (int i = tid; i < n; i += nt) A[(size_t)(k + 1 + i) * K + k] = u[i];
+    __syncthreads();
+  }
+  if (tid == 0) {
+    if (K >= 2) {
+      a[K - 2] = A[(size_t)(K - 2) * K + (K - 2)];
+      b[K - 2] = A[(size_t)(K - 1) * K + (K - 2)];
+    }
+    a[K - 1] = A[(size_t)(K - 1) * K + (K - 1)];
+  }
+  __syncthreads();
+  // ---- gt = Q^T g: reflectors 0 .. K-3 in order ----
+  for (int k = 0; k + 2 < K; ++k) {
+    const int n = K - k - 1;
+    const double beta = bet[k];
+    if (beta == 0.0) continue;   // uniform
+    double vg = 0;
+    for (int i = tid; i < n; i += nt) vg = fma(A[(size_t)(k + 1 + i) * K + k], gt[k + 1 + i], vg);
+    vg = block_sum(vg, red);
+    for (int i = tid; i < n; i += nt) gt[k + 1 + i] -= beta * vg * A[(size_t)(k + 1 + i) * K + k];
+    __syncthreads();
+  }
+  // ---- lowest eigenvalue of T: multisection of the Gershgorin bracket, each
+  // thread taking one Sturm count per round (the interval shrinks nt + 1 fold) ----
+  __shared__ double ms_lo, ms_hi;
+  __shared__ int ms_first;
+  if (tid == 0) {
+    double glo = a[0], ghi = a[0];
+    for (int i = 0; i < K; ++i) {
+      const double r = (i > 0 ? fabs(b[i - 1]) : 0.0) + (i + 1 < K ? fabs(b[i]) : 0.0);
+      glo = fmin(glo, a[i] - r);
+      ghi = fmax(ghi, a[i] + r);
+    }
+    ms_lo = glo;
+    ms_hi = ghi;
+  }
+  __syncthreads();
+  for (int round = 0; round < 64; ++round) {
+    const double lo = ms_lo, hi = ms_hi;
+    if (!(hi - lo > 1e-15 * fmax(fabs(lo), fabs(hi)) + 1e-300)) break;   // uniform
+    if (tid == 0) ms_first = nt;
+    __syncthreads();
+    const double x = lo + (hi - lo) * ((double)(tid + 1) / (double)(nt + 1));
+    if (x > lo && x < hi && sturm_count(a, b, K, x) >= 1) atomicMin(&ms_first, tid);
+    __syncthreads();
+    if (tid == 0) {
+      const int t = ms_first;   // smallest point with an eigenvalue below it
+      const double nlo = t == 0 ? lo : lo + (hi - lo) * ((double)t / (double)(nt + 1));
+      const double nhi = t == nt ? hi : lo + (hi - lo) * ((double)(t + 1) / (double)(nt + 1));
+      ms_lo = nlo;
+      ms_hi = nhi;
+    }
+    __syncthreads();
+  }
+  const double dmin = 0.5 * (ms_lo + ms_hi);
+  // ---- secular equation on T (one thread) ----
+  if (tid == 0) {
+    const double gn = dot_norm(gt, K);
+    double sigma = 0.0;
+    bool done = false;
+    for (int i = 0; i < K; ++i) z[i] = -gt[i];
+    if (dmin > 0) {
+      tri_solve(a, b, K, 0.0, z, st, u, w);
+      if (dot_norm(st, K) <= radius) done = true;
+    }
+    const double slo0 = fmax(0.0, -dmin);
+    if (!done) {
+      // hard case: g (nearly) orthogonal to the lowest eigenvector, so that the
+      // step stays inside the region as sigma approaches its lower limit
+      const double sh = slo0 + 1e-12 * fmax(1.0, fabs(dmin));
+      tri_solve(a, b, K, sh, z, st, u, w);
+      const double nh = dot_norm(st, K);
+      if (nh <= radius) {
+        // eigenvector of the lowest eigenvalue by inverse iteration on T + sh I
+        // (tri_solve may run in place: x[i] reads r[i] before writing it)
+        double* v = z;
+        for (int i = 0; i < K; ++i) v[i] = 1.0 / sqrt((double)K);
+        for (int itr = 0; itr < 3; ++itr) {
+          tri_solve(a, b, K, sh, v, v, u, w);
+          const double nv = dot_norm(v, K);
+          for (int i = 0; i < K; ++i) v[i] /= nv;
+        }
+        double xz = 0;
+        for (int i = 0; i < K; ++i) xz = fma(st[i], v[i], xz);
+        const double tau = -xz + sqrt(fmax(xz * xz + radius * radius - nh * nh, 0.0));
+        for (int i = 0; i < K; ++i) st[i] = fma(tau, v[i], st[i]);
+        sigma = slo0;
+        done = true;
+      }
+    }
+    if (!done) {
+      for (int i = 0; i < K; ++i) z[i] = -gt[i];
+      double shi = slo0 + gn / radius + 1.0;
+      for (int k = 0; k < 200; ++k) {
+        tri_solve(a, b, K, shi, z, st, u, w);
+        if (dot_norm(st, K) <= radius) break;
+        shi *= 2.0;
+      }
+      double sig = shi, slo = slo0;
+      for (int itn = 0; itn < 200; ++itn) {
+        tri_solve(a, b, K, sig, z, st, u, w);
+        const double ns = dot_norm(st, K);
+        if (fabs(ns - radius) <= 1e-13 * radius) break;
+        const double phi = 1.0 / ns - 1.0 / radius;
+        if (phi < 0) slo = sig; else shi = sig;
+        // d|s|/dsigma = -s^T (T + sigma I)^-1 s / |s| (the step buffer as scratch)
+        tri_solve(a, b, K, sig, st, step, u, w);
+        double dd = 0;
+        for (int i = 0; i < K; ++i) dd = fma(st[i], step[i], dd);
+        const double dns = -dd / ns;
+        const double dphi = -dns / (ns * ns);
+        double nw = sig - phi / dphi;
+        if (!(nw > slo && nw < shi)) nw = 0.5 * (slo + shi);
+        sig = nw;
+      }
+      tri_solve(a, b, K, sig, z, st, u, w);
+      sigma = sig;
+    }
+    // predicted decrease from T directly, |s|
+    double pr = 0, ns2 = 0;
+    for (int i = 0; i < K; ++i) {
+      double ts = a[i] * st[i];
+      if (i > 0) ts = fma(b[i - 1], st[i - 1], ts);
+      if (i + 1 < K) ts = fma(b[i], st[i + 1], ts);
+      pr += gt[i] * st[i] + 0.5 * st[i] * ts;
+      ns2 = fma(st[i], st[i], ns2);
+    }
+    info[0] = -pr;
+    info[1] = sqrt(ns2);
+    info[2] = sigma;
+    info[3] = gn;
+  }
+  __syncthreads();
+  // ---- s = Q st: reflectors K-3 .. 0 ----
+  for (int l = tid; l < K; l += nt) step[l] = st[l];
+  __syncthreads();
+  for (int k = K - 3; k >= 0; --k) {
+    const int n = K - k - 1;
+    const double beta = bet[k];
+    if (beta == 0.0) continue;
+    double vs = 0;
+    for (int i = tid; i < n; i += nt) vs = fma(A[(size_t)(k + 1 + i) * K + k], step[k + 1 + i], vs);
+    vs = block_sum(vs, red);
+    for (int i = tid; i < n; i += nt) step[k + 1 + i] -= beta * vs * A[(size_t)(k + 1 + i) * K + k];
+    __syncthreads();
+  }
+  for (int l = tid; l < K; l += nt)
+    if (!isfinite(step[l])) raise_status(status, DEV_NONFINITE);
+  __syncthreads();
+}
+
+// method: 0 by K (eigendecomposition below kTriMin), 1 eigendecomposition, 2 tridiagonal
 __global__ void k_tr_subproblem(const double* __restrict__ gh, const double* __restrict__ Q,
                                 const double* __restrict__ d, int K, double radius,
                                 double* __restrict__ work, double* __restrict__ step,
-                                double* __restrict__ info, int* status) {
+                                double* __restrict__ info, int* status, int method) {
   __shared__ double red[32];
-  tr_subproblem_body(gh, Q, d, K, radius, work, step, info, status, red);
+  const bool tri = method == 2 || (method == 0 && !tr_needs_eig(K));
+  if (tri) tr_subproblem_tri_body(gh, K, radius, work, step, info, status, red);
+  else tr_subproblem_body(gh, Q, d, K, radius, work, step, info, status, red);
 }
 
 // ---------------------------------------------------------------------------
@@ -182,8 +442,11 @@ __global__ void k_tr_batch_propose(TrSlot* slots, int n, int it, double gtol) {
     return;
   }
   __syncthreads();
-  tr_subproblem_body(t.gh, t.work + 3 * K, t.work + 2 * K, K, t.radius, t.work, t.step, t.info,
-                     t.status, red);
+  if (tr_needs_eig(K))
+    tr_subproblem_body(t.gh, t.work + 3 * K, t.work + 2 * K, K, t.radius, t.work, t.step, t.info,
+                       t.status, red);
+  else
+    tr_subproblem_tri_body(t.gh, K, t.radius, t.work, t.step, t.info, t.status, red);
   const double pred = t.info[0];
   if (!(pred > 0) || !isfinite(pred)) {
     if (threadIdx.x == 0) { t.stop = 3; t.iters = it; t.active = 0; }
@@ -237,8 +500,10 @@ __global__ void k_tr_batch_update(TrSlot* slots, int n, int it, int max_iter, do
     for (int l = threadIdx.x; l < K; l += blockDim.x) t.theta[l] = t.theta_trial[l];
     const size_t ngh = 1 + (size_t)K + (size_t)K * K;
     for (size_t e = threadIdx.x; e < ngh; e += blockDim.x) t.gh[e] = t.gh_trial[e];
-    const size_t neig = (size_t)K + (size_t)K * K;   // eigenvalues d, eigenvectors Q
-    for (size_t e = threadIdx.x; e < neig; e += blockDim.x) t.work[2 * K + e] = t.eig_trial[e];
+    if (tr_needs_eig(K)) {
+      const size_t neig = (size_t)K + (size_t)K * K;   // eigenvalues d, eigenvectors Q
+      for (size_t e = threadIdx.x; e < neig; e += blockDim.x) t.work[2 * K + e] = t.eig_trial[e];
+    }
   }
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -255,8 +520,10 @@ __global__ void k_tr_batch_init(TrSlot* slots, int n, double radius0) {
   const int K = t.K;
   const size_t ngh = 1 + (size_t)K + (size_t)K * K;
   for (size_t e = threadIdx.x; e < ngh; e += blockDim.x) t.gh[e] = t.gh_trial[e];
-  const size_t neig = (size_t)K + (size_t)K * K;
-  for (size_t e = threadIdx.x; e < neig; e += blockDim.x) t.work[2 * K + e] = t.eig_trial[e];
+  if (tr_needs_eig(K)) {
+    const size_t neig = (size_t)K + (size_t)K * K;
+    for (size_t e = threadIdx.x; e < neig; e += blockDim.x) t.work[2 * K + e] = t.eig_trial[e];
+  }
   for (int l = threadIdx.x; l < K; l += blockDim.x) t.theta[l] = t.theta_trial[l];
   if (threadIdx.x == 0) {
     const int st = *t.status;
@@ -353,14 +620,16 @@ __global__ void k_axpy(const double* __restrict__ x, const double* __restrict__ 
   if (i < K) y[i] = x[i] + s[i];
 }
 
-size_t tr_work_doubles(int K) { return 3 * (size_t)K + (size_t)K * K; }
+size_t tr_work_doubles(int K) { return 8 * (size_t)K + (size_t)K * K; }
 
 cudaError_t launch_tr_subproblem(const double* out_gh, int K, double radius, double* work,
-                                 double* step, double* info, int* status, cudaStream_t st) {
-  // eigendecomposition of the Hessian is expected in work + 2K (d) and work + 3K (Q)
+                                 double* step, double* info, int* status, cudaStream_t st, int method) {
+  // eigendecomposition of the Hessian (eigendecomposition method) expected in
+  // work + 2K (d) and work + 3K (Q)
   const double* d = work + 2 * K;
   const double* Q = work + 3 * K;
-  k_tr_subproblem<<<1, 128, 0, st>>>(out_gh, Q, d, K, radius, work, step, info, status);
+  k_tr_subproblem<<<1, K >= kTriMin ? 256 : 128, 0, st>>>(out_gh, Q, d, K, radius, work, step, info,
+                                                           status, method);
   return cudaGetLastError();
 }
 
@@ -370,3 +639,55 @@ cudaError_t launch_axpy(const double* x, const double* s, int K, double* y, cuda
 }
 
 }  // namespace qoc
+
+// ---------------------------------------------------------------------------
+// C ABI: one subproblem from host data (see include/qoc.h)
+// ---------------------------------------------------------------------------
+extern "C" qoc_status qoc_tr_subproblem(int K, const double* g, const double* H, double radius,
+                                        int method, double* s, double* info) {
+  using namespace qoc;
+  if (K < 1 || K > 4096 || !g || !H || !s || !info || !(radius > 0) || method < 0 || method > 2)
+    return QOC_EINVAL;
+  const bool eig = method == 1 || (method == 0 && tr_needs_eig(K));
+  const size_t ngh = 1 + (size_t)K + (size_t)K * K;
+  double *dgh = nullptr, *work = nullptr, *step = nullptr, *dinfo = nullptr, *zero = nullptr;
+  int* status = nullptr;
+  StepSpace ws;
+  cudaStream_t st = nullptr;
+  cudaError_t e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaMalloc(&dgh, 8 * ngh);
+  if (e == cudaSuccess) e = cudaMalloc(&work, 8 * tr_work_doubles(K));
+  if (e == cudaSuccess) e = cudaMalloc(&step, 8 * (size_t)K);
+  if (e == cudaSuccess) e = cudaMalloc(&dinfo, 8 * 8);
+  if (e == cudaSuccess) e = cudaMalloc(&zero, 8 * ((size_t)K * K + 1));
+  if (e == cudaSuccess) e = cudaMalloc(&status, sizeof(int));
+  if (e == cudaSuccess && eig) {
+    ws.bytes = (eig_step_bytes(K) + 255) & ~size_t(255);
+    e = cudaMalloc(&ws.base, ws.bytes);
+  }
+  if (e == cudaSuccess) e = cudaMemsetAsync(zero, 0, 8 * ((size_t)K * K + 1), st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(status, 0, sizeof(int), st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(dgh, 0, 8, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(dgh + 1, g, 8 * (size_t)K, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(dgh + 1 + K, H, 8 * (size_t)K * K, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess && eig)
+    e = launch_eig(dgh + 1 + K, zero, zero, K, 1, work + 3 * K, work + 2 * K, status, EIG_JACOBI_FP64, 0,
+                   0.0, st, ws);
+  if (e == cudaSuccess) e = launch_tr_subproblem(dgh, K, radius, work, step, dinfo, status, st, eig ? 1 : 2);
+  int hst = 0;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(s, step, 8 * (size_t)K, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(info, dinfo, 4 * sizeof(double), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&hst, status, sizeof(int), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  cudaFree(dgh); cudaFree(work); cudaFree(step); cudaFree(dinfo); cudaFree(zero); cudaFree(status);
+  cudaFree(ws.base);
+  if (st) cudaStreamDestroy(st);
+  if (e != cudaSuccess) {
+    note_error(cudaGetErrorString(e));
+    return e == cudaErrorMemoryAllocation ? QOC_ENOMEM : QOC_ECUDA;
+  }
+  if (hst & DEV_TIMEOUT) return QOC_ETIMEOUT;
+  if (hst) return QOC_ENUMERIC;
+  return QOC_OK;
+}

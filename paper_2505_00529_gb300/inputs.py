@@ -202,6 +202,33 @@ def scaling_problem(N: int, J: int, seed: int, dt: float = 0.1) -> Problem:
     return Problem(H0, M, alpha, beta, maximal_basis(J), dt, 0.5, 0.5, name=f"scaling_N{N}_J{J}")
 
 
+def tanh_network_control(t, theta):
+    """A control model that is not linear in its parameters (the neural
+    network f(t; theta) the paper proposes for future work, Sec. III-D):
+    f(t) = sum_h v_h tanh(w_h t + c_h), theta = [v (H), w (H), c (H)].
+    Returns f (J), its Jacobian df/dtheta (J x 3H) and its second
+    derivatives d^2 f / dtheta^2 (J x 3H x 3H), all analytic."""
+    t = np.asarray(t, float)
+    theta = np.asarray(theta, float)
+    H = theta.size // 3
+    v, w, c = theta[:H], theta[H:2 * H], theta[2 * H:]
+    z = np.tanh(np.outer(t, w) + c)                 # J x H
+    s = 1.0 - z ** 2                                 # tanh'
+    s2 = -2.0 * z * s                                # tanh''
+    J = t.size
+    f = z @ v
+    jac = np.concatenate([z, s * v * t[:, None], s * v], axis=1)
+    hess = np.zeros((J, 3 * H, 3 * H))
+    for h in range(H):
+        iv, iw, ic = h, H + h, 2 * H + h
+        hess[:, iv, iw] = hess[:, iw, iv] = s[:, h] * t
+        hess[:, iv, ic] = hess[:, ic, iv] = s[:, h]
+        hess[:, iw, iw] = v[h] * s2[:, h] * t ** 2
+        hess[:, iw, ic] = hess[:, ic, iw] = v[h] * s2[:, h] * t
+        hess[:, ic, ic] = v[h] * s2[:, h]
+    return f, jac, hess
+
+
 def batched_shape(index: int):
     """(N, K, J) of problem `index` of the batched workload (config 3), drawn
     exactly as config_problem(3, index) draws them, without the matrices."""

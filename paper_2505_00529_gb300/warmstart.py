@@ -70,6 +70,28 @@ def solve_many(prob, betas, theta0s, precision=_lib.QOC_MIXED_FP32, batch=32, **
     return thetas, infos, secs
 
 
+def solve_sequential(prob, betas, theta0s, precision=_lib.QOC_FP64, **tr):
+    """The plain method: one problem object, its exact trust region
+    (qoc_trust_region_solve) run target after target.  Returns (thetas,
+    infos, seconds)."""
+    n = len(betas)
+    K = prob.B.shape[1]
+    thetas = np.zeros((n, K))
+    infos = [None] * n
+    t0 = time.perf_counter()
+    with _lib.Problem(prob, precision=precision) as P:
+        for i in range(n):
+            P.set_target(betas[i])
+            try:
+                th, info = P.trust_region_solve(theta0s[i], **tr)
+            except _lib.QocError as e:
+                th, info = np.full(K, np.nan), {"iters": tr.get("max_iter", 0), "J": np.nan,
+                                                 "stop": f"error {e.status}"}
+            thetas[i] = th
+            infos[i] = info
+    return thetas, infos, time.perf_counter() - t0
+
+
 GUARD_STEPS = (0.0, 0.25, 0.5, 0.75, 1.0)
 
 
@@ -158,6 +180,9 @@ def compare(prob, train_betas, test_betas, precision=_lib.QOC_MIXED_FP32, worker
     theta_g, tstar, t_guard_eval = guarded_starts(prob, test_betas, theta0, precision, workers)
     _, info_g, t_g = solve_many(prob, test_betas, theta_g, precision, tr_batch, **tr)
     ws.close()
+    # the plain method on the same targets: binary64, one problem at a time, from theta = 0
+    _, info_plain, t_plain = solve_sequential(prob, test_betas, np.zeros((len(test_betas), K)),
+                                              _lib.QOC_FP64, **tr)
     conv = lambda i: i["stop"] in ("gtol", "xtol")
     good = np.array([conv(a) and conv(b) and conv(c) for a, b, c in zip(info_zero, info_mlp, info_g)])
     gh0 = np.array([i.get("n_eval_gh", 0) for i in info_zero])[good]
@@ -183,6 +208,17 @@ def compare(prob, train_betas, test_betas, precision=_lib.QOC_MIXED_FP32, worker
         "frac_mlp_not_worse_J": float(np.mean(J1 <= J0 * (1 + 1e-6))),
         "converged_zero": float(np.mean([i["stop"] in ("gtol", "xtol") for i in info_zero])),
         "converged_mlp": float(np.mean([i["stop"] in ("gtol", "xtol") for i in info_mlp])),
+        "combined_vs_plain_fp64": {
+            "form": "batched trust region (batches of %d), %s, theta0 from the network" % (
+                tr_batch, "mixed precision" if precision == _lib.QOC_MIXED_FP32 else "binary64"),
+            "plain": "binary64, one problem at a time, theta0 = 0",
+            "wall_combined_s": t_mlp, "wall_plain_s": t_plain, "speedup": t_plain / t_mlp,
+            "iters_plain_mean": float(np.mean([i["iters"] for i in info_plain])),
+            "converged_plain": float(np.mean([conv(i) for i in info_plain])),
+            "frac_combined_not_worse_J": float(np.mean([
+                a["J"] <= b["J"] * (1 + 1e-6) for a, b in zip(info_mlp, info_plain)
+                if conv(a) and conv(b)])),
+        },
         "guarded": {
             "rule": "theta0 = t* MLP(beta), t* = argmin J(t MLP(beta)) over t in "
                     + ", ".join(f"{t:g}" for t in GUARD_STEPS),

@@ -471,3 +471,48 @@ def test_bfgs_trust_region_reaches_the_exact_minimiser():
     assert np.linalg.norm(th1 - th2) <= 1e-6 * max(1.0, np.linalg.norm(th2))
     assert abs(info1["J"] - info2["J"]) <= 1e-12 * abs(info2["J"])
     assert info1["iters"] >= info2["iters"]
+
+
+# --------------------------------------------------------------------------
+# control models that are not linear in theta (Eq. d2Ldf2 with d^2 f != 0)
+# --------------------------------------------------------------------------
+
+def test_model_evaluation_reduces_to_the_linear_one():
+    """Samples and Jacobian of a linear model (f = B theta, jac = B) give
+    exactly the linear evaluation."""
+    prob = inputs.small_problem(N=4, K=3, J=40, seed=71, dt=0.05, basis="random")
+    theta = inputs.eval_theta(3, 72)
+    a = orc.evaluate(prob, theta, order=2)
+    b = orc.evaluate_model(prob, prob.B @ theta, prob.B, order=2)
+    assert a["J"] == b["J"]
+    np.testing.assert_array_equal(a["grad"], b["grad"])
+    np.testing.assert_array_equal(a["hess"], b["hess"])
+    np.testing.assert_array_equal(b["d"], 2 * prob.w_f * (prob.B @ theta) + a["g"])
+
+
+def test_nonlinear_model_gradient_and_hessian_by_finite_differences():
+    """f(t) = sum_h v_h tanh(w_h t + c_h): jac^T d is the gradient of
+    J(theta) and hess + sum_j d_j d^2 f_j / dtheta^2 its Hessian (central
+    differences with Richardson extrapolation)."""
+    prob = inputs.small_problem(N=4, K=6, J=60, seed=73, dt=0.05)
+    t = np.arange(prob.J) * prob.dt
+    theta = np.array([0.7, -0.4, 1.1, 0.3, 0.5, -0.2])
+
+    def full(th):
+        f, jac, hf = inputs.tanh_network_control(t, th)
+        r = orc.evaluate_model(prob, f, jac, order=2)
+        return r["J"], r["grad"], r["hess"] + np.einsum("j,jlm->lm", r["d"], hf)
+
+    def J_of(th):
+        f, _, _ = inputs.tanh_network_control(t, th)
+        return orc.evaluate_samples(prob, f, np.zeros((prob.J, 1)), order=0)["J"]
+
+    J0, g, H = full(theta)
+    g_fd = _richardson(J_of, theta, 1e-3)
+    assert np.linalg.norm(g - g_fd) <= 1e-8 * np.linalg.norm(g)
+    H_fd = np.stack([_richardson(lambda th, l=l: full(th)[1][l], theta, 1e-3) for l in range(6)])
+    assert np.linalg.norm(H - H_fd) <= 1e-6 * np.linalg.norm(H), np.linalg.norm(H - H_fd) / np.linalg.norm(H)
+    # the model's own second-derivative term matters here
+    f, jac, hf = inputs.tanh_network_control(t, theta)
+    r = orc.evaluate_model(prob, f, jac, order=2)
+    assert np.linalg.norm(np.einsum("j,jlm->lm", r["d"], hf)) > 1e-3 * np.linalg.norm(H)
