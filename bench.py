@@ -48,13 +48,13 @@ WORKLOAD = {"workload": "synthetic CI-shaped single problem, N=32 basis, K=64 si
 # control, binary32 Jacobi, binary64 refinement, 3 preparation parts (D, P~, X'),
 # 2 block products, state chain + fill, terminal, costate chain + fill, drift,
 # 3 pointwise parts (p^, y^/g, c), 3 block-source launches (Q, W/Gamma, backward),
-# tangent and second-order adjoint panels, 2 panel contractions, grad, hess partial,
-# hess final
-LAUNCHES_PER_EVAL = 27
-# DRAM bytes (read + written) of one launch of a kernel on a workload, from an
-# ncu capture of the current kernel: (kernel, N, J) -> bytes.  k_eig_refine:
-# 32.93 MB read, 0 written (algorithmic: W read once, 32.8 MB).
-TRAFFIC_BYTES = {("k_eig_refine", 32, 4000): 32.93e6}
+# tangent and second-order adjoint panels, 2 panel contractions, grad, Hessian
+# chunk partials, chunk sum, symmetrisation, asymmetry (ncu launch list: 29)
+LAUNCHES_PER_EVAL = 29
+# DRAM bytes (read + written) of a kernel's launches in one evaluation on a
+# workload, from an ncu capture of the current kernel: (kernel, N, J) -> bytes.
+# k_prep: P part 33.88 MB read + 38.80 MB written, X part 99.48 + 29.35 MB.
+TRAFFIC_BYTES = {("k_prep", 32, 4000): 201.51e6}
 
 
 def env_int(k, d):

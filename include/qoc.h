@@ -171,7 +171,10 @@ qoc_status qoc_eval_grad_hess(qoc_problem* p, const double* theta, double* J,
  * Hessian is hess + sum_j d_j d^2 f_j / dtheta^2, the last term being the
  * model's own (its second derivatives, which only the caller knows).  The
  * Jacobian replaces the problem's basis: later theta-evaluations use it as
- * the linear model.  Synchronises; host pointers. */
+ * the linear model.  The precision of QOC_MIXED_FP32 was chosen at
+ * qoc_create_problem from the basis given there, so create the problem with
+ * a representative Jacobian (e.g. the model's at its starting theta) as the
+ * basis.  Synchronises; host pointers. */
 qoc_status qoc_eval_grad_hess_model(qoc_problem* p, const double* f, const double* jac, double* J,
                                     double* grad, double* hess, double* dJdf);
 

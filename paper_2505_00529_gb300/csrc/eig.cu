@@ -17,6 +17,7 @@
 //    rate on GB300).
 #include "common.cuh"
 #include "kernels.hpp"
+#include "ozaki.cuh"
 
 namespace qoc {
 
@@ -161,15 +162,24 @@ __device__ __forceinline__ void tri_index_e(int t, int N, int& i, int& k) {
   k = t - (r * N - r * (r - 1) / 2) + r;
 }
 
+// order-preserving integer key of a binary64 value (not NaN): comparing keys
+// compares the values, without binary64 comparison instructions
+__device__ __forceinline__ long long order_key(double x) {
+  const long long b = __double_as_longlong(x);
+  return b ^ ((b >> 63) & 0x7fffffffffffffffLL);
+}
+__device__ __forceinline__ long long order_key(float x) { return order_key((double)x); }
+
 // rank-sort the diagonal of A ascending (ties by index) and write W = V(:, order), lambda
 template <typename T>
 __device__ void sort_write(const T* A, const T* V, int N, int ld, double* Wj, double* ej) {
   for (int i = threadIdx.x; i < N; i += blockDim.x) {
     const T di = A[i * ld + i];
+    const long long ki = order_key(di);
     int rank = 0;
     for (int k = 0; k < N; ++k) {
-      const T dk = A[k * ld + k];
-      rank += (dk < di) || (dk == di && k < i);
+      const long long kk = order_key(A[k * ld + k]);
+      rank += (kk < ki) || (kk == ki && k < i);
     }
     ej[rank] = (double)di;
     for (int row = 0; row < N; ++row) Wj[row * N + rank] = (double)V[row * ld + i];
@@ -229,6 +239,19 @@ __global__ void k_eig_jacobi(const double* __restrict__ H0, const double* __rest
 // stopping once |I - W^T W|_F reaches the binary64 floor), then a binary64
 // Jacobi clean-up of S = W^T H W that resolves what the refinement leaves
 // alone (pairs closer than its cluster threshold), then W <- W V.
+// OZ: the binary64 products H W, W^T (H W) and W^T W on the tensor cores by
+// error-free splitting (ozaki.cuh; N <= 32, 256 threads); used for the
+// relaxed refinement of problems on binary32 sweeps.
+constexpr int kOzSlices = 6;
+struct OzSpace {
+  __nv_bfloat16 *Hs, *Ws, *Ts;   // [kOzSlices][32][oz::LD] each
+  int *eH, *eW, *eT;             // [32] each
+};
+__host__ __device__ inline size_t oz_smem_bytes() {
+  return 3 * (size_t)kOzSlices * 32 * oz::LD * 2 + 3 * 32 * 4 + 16;
+}
+
+template <bool OZ>
 __device__ __forceinline__ void eig_refine_step(const double* __restrict__ H0,
                                                 const double* __restrict__ M,
                                                 const double* __restrict__ f, int N, int j,
@@ -251,6 +274,18 @@ __device__ __forceinline__ void eig_refine_step(const double* __restrict__ H0,
   float* Wf = reinterpret_cast<float*>(
       (reinterpret_cast<uintptr_t>(pr + NP + 2) + 15) & ~uintptr_t(15));   // [N][ld] binary32 W
   float* Ef = Wf + N * ld;                                                  // [N][ld] binary32 E
+  OzSpace oz{};
+  if (OZ) {
+    unsigned char* ob = reinterpret_cast<unsigned char*>(
+        (reinterpret_cast<uintptr_t>(Ef + N * ld) + 15) & ~uintptr_t(15));
+    const size_t sl = (size_t)kOzSlices * 32 * oz::LD;
+    oz.Hs = reinterpret_cast<__nv_bfloat16*>(ob);
+    oz.Ws = oz.Hs + sl;
+    oz.Ts = oz.Ws + sl;
+    oz.eH = reinterpret_cast<int*>(oz.Ts + sl);
+    oz.eW = oz.eH + 32;
+    oz.eT = oz.eW + 32;
+  }
   const int tid = threadIdx.x, nt = blockDim.x;
   const double fj = f[j];
   double* Wg = W_io + (size_t)j * N * N;
@@ -272,6 +307,7 @@ __device__ __forceinline__ void eig_refine_step(const double* __restrict__ H0,
   }
   __syncthreads();
   const double Hnorm = red[40];
+  if (OZ) oz::split32<kOzSlices>(H, ld, N, true, oz.Hs, oz.eH);
 
   // Refinement sweeps until W is orthonormal to the binary64 floor: each sweep
   // computes S = W^T H W and R = I - W^T W; when |R|_F <= orth_tol, S is the
@@ -299,6 +335,28 @@ __device__ __forceinline__ void eig_refine_step(const double* __restrict__ H0,
   __shared__ int not_done;
   bool finished = false;
   for (int it = 0;; ++it) {
+    double rn = 0;
+    if (OZ) {
+      // T = H W, S = W^T T, R <- W^T W on the tensor cores; then the upper
+      // triangles mirrored (exactly symmetric S, R) and R = I - W^T W
+      oz::split32<kOzSlices>(W, ld, N, false, oz.Ws, oz.eW);
+      oz::mm32<kOzSlices>(oz.Hs, oz.eH, oz.Ws, oz.eW, T, ld, N);
+      __syncthreads();
+      oz::split32<kOzSlices>(T, ld, N, false, oz.Ts, oz.eT);
+      oz::mm32<kOzSlices>(oz.Ws, oz.eW, oz.Ts, oz.eT, S, ld, N);
+      oz::mm32<kOzSlices>(oz.Ws, oz.eW, oz.Ws, oz.eW, R, ld, N);
+      __syncthreads();
+      for (int t = tid; t < N * (N + 1) / 2; t += nt) {
+        int i, k;
+        tri_index_e(t, N, i, k);
+        S[k * ld + i] = S[i * ld + k];
+        const double rr = (i == k ? 1.0 : 0.0) - R[i * ld + k];
+        R[i * ld + k] = rr;
+        R[k * ld + i] = rr;
+        rn += (i == k ? 1.0 : 2.0) * rr * rr;
+      }
+      __syncthreads();
+    } else {
     // T = H W
     for (int e = tid; e < N * N; e += nt) {
       const int i = e / N, k = e % N;
@@ -308,7 +366,6 @@ __device__ __forceinline__ void eig_refine_step(const double* __restrict__ H0,
     }
     __syncthreads();
     // S = W^T T, R = I - W^T W (both symmetric: upper triangle, mirrored)
-    double rn = 0;
     for (int t = tid; t < N * (N + 1) / 2; t += nt) {
       int i, k;
       tri_index_e(t, N, i, k);
@@ -326,12 +383,21 @@ __device__ __forceinline__ void eig_refine_step(const double* __restrict__ H0,
       rn += (i == k ? 1.0 : 2.0) * rr * rr;
     }
     __syncthreads();
-    for (int i = tid; i < N; i += nt) lam[i] = S[i * ld + i] / (1.0 - R[i * ld + i]);
+    }
+    // off(S) with the diagonal's correction S_ii - lambda_i: the diagonal
+    // terms here, the off-diagonal ones below (no per-warp diagonal branch:
+    // a binary64 warp instruction costs the pipe the same for one lane)
     double sn = 0;
+    for (int i = tid; i < N; i += nt) {
+      const double l = S[i * ld + i] / (1.0 - R[i * ld + i]);
+      lam[i] = l;
+      const double d = S[i * ld + i] - l;
+      sn = fma(d, d, sn);
+    }
     for (int e = tid; e < N * N; e += nt) {
       const int i = e / N, k = e % N;
-      if (i != k) sn += S[i * ld + k] * S[i * ld + k];
-      else { const double d = S[i * ld + i] - S[i * ld + i] / (1.0 - R[i * ld + i]); sn += d * d; }
+      const double sik = i != k ? S[i * ld + k] : 0.0;
+      sn = fma(sik, sik, sn);
     }
     sn = warp_sum(sn);
     rn = warp_sum(rn);
@@ -371,7 +437,16 @@ __device__ __forceinline__ void eig_refine_step(const double* __restrict__ H0,
         const double gap = lam[k] - lam[i];
         const double sik = S[i * ld + k];
         const bool sep = fabs(gap) > delta && fabs(sik) <= kLinear * fabs(gap);
-        eik = sep ? (sik + lam[k] * rik) / gap : 0.5 * rik;
+        if (OZ && sep) {
+          // relaxed refinement: 1/gap from the binary32 reciprocal and one
+          // binary64 Newton step (relative error ~2^-46, far below what the
+          // relaxed finish needs) instead of a binary64 division
+          const double r0 = (double)__frcp_rn((float)gap);
+          const double r1 = r0 * fma(-gap, r0, 2.0);
+          eik = (sik + lam[k] * rik) * r1;
+        } else {
+          eik = sep ? (sik + lam[k] * rik) / gap : 0.5 * rik;
+        }
         if (!sep || (!relaxed && fabs(eik) > kDone)) not_done = 1;
         esq = fma(eik, eik, esq);
       }
@@ -472,8 +547,8 @@ __device__ __forceinline__ void eig_refine_step(const double* __restrict__ H0,
 // registers per SM (the binary64 pipe wants every resident warp), 512 is the
 // large-N launch.  GWS: storage in the global workspace (a compile-time
 // choice, so that the shared-memory instantiation keeps shared-memory loads).
-template <int MAXT, bool GWS>
-__global__ void __launch_bounds__(MAXT, MAXT <= 256 ? 4 : 1)
+template <int MAXT, bool GWS, bool OZ = false>
+__global__ void __launch_bounds__(MAXT, OZ ? 2 : (MAXT <= 256 ? 4 : 1))
 k_eig_refine(const double* __restrict__ H0, const double* __restrict__ M,
                              const double* __restrict__ f, int N, int J, int sweeps,
                              double angle_tol, double* __restrict__ W_io,
@@ -482,7 +557,7 @@ k_eig_refine(const double* __restrict__ H0, const double* __restrict__ M,
   extern __shared__ __align__(16) unsigned char smem_raw[];
   unsigned char* base = GWS ? gws + (size_t)blockIdx.x * per_cta : smem_raw;
   for (int j = blockIdx.x; j < J; j += gridDim.x) {
-    eig_refine_step(H0, M, f, N, j, sweeps, angle_tol, W_io, eig_out, status, stats, finish_tol, base);
+    eig_refine_step<OZ>(H0, M, f, N, j, sweeps, angle_tol, W_io, eig_out, status, stats, finish_tol, base);
     __syncthreads();
   }
 }
@@ -740,6 +815,15 @@ cudaError_t launch_eig(const double* H0, const double* M, const double* f, int N
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   if (mid) cudaEventRecord(mid, st);
+  if (N <= 32 && finish_tol > 0) {
+    // relaxed refinement (binary32 sweeps): products on the tensor cores
+    const size_t sm = refine_smem(N) + oz_smem_bytes();
+    if (sm <= max_dyn_smem((const void*)k_eig_refine<256, false, true>)) {
+      k_eig_refine<256, false, true><<<J, 256, sm, st>>>(H0, M, f, N, J, refine_sweeps, angle_tol, W, eig,
+                                                         status, stats, finish_tol, nullptr, 0);
+      return cudaGetLastError();
+    }
+  }
   if (threads <= 256) {
     if (!step_grid(refine_smem(N), J, ws, (const void*)k_eig_refine<256, false>, g))
       return cudaErrorInvalidConfiguration;

@@ -24,6 +24,7 @@
 
 #include "common.cuh"
 #include "kernels.hpp"
+#include "ozaki.cuh"
 
 namespace qoc {
 
@@ -51,43 +52,63 @@ __device__ __forceinline__ double2 gamma1(int a, int b, const double* lam, const
   return make_double2(e.y * s, -e.x * s);   // -i * s * e
 }
 
-// phi[l_a, l_b, l_c]: symmetric; extremes lo, hi.  Far: recurrence on the
-// extremes; near (dt (hi - lo) <= TAU_DD2): exp(-i dt c) sum_{n=2}^{10}
-// (-i dt)^n / n! h_{n-2}(lo - c, mid - c, hi - c), c the mean.
-__device__ double2 dd2_dev(int a, int b, int c, const double* lam, const double2* eh, double dt) {
+// Integer tests and keys, so that bookkeeping stays off the binary64 pipe.
+__device__ __forceinline__ bool finite_bits(double x) {
+  return ((__double_as_longlong(x) >> 52) & 0x7ff) != 0x7ff;
+}
+__device__ __forceinline__ bool nonzero_bits(double x) {
+  return (__double_as_longlong(x) << 1) != 0;
+}
+// order-preserving integer key of a binary64 value (not NaN)
+__device__ __forceinline__ long long value_key(double x) {
+  const long long b = __double_as_longlong(x);
+  return b ^ ((b >> 63) & 0x7fffffffffffffffLL);
+}
+
+// Coefficients dt^n / n!, n = 0 .. kSeriesTerms, of the near-triple series below
+constexpr int kSeriesTerms = 10;
+
+// phi[l_a, l_b, l_c] (symmetric in its arguments) with extremes lo, hi.
+// rinv(x, y) = 1 / (l_x - l_y) for every far pair (dt |l_x - l_y| > TAU_DD2)
+// and 0 for near pairs, as left in the real parts of Y by the far-pair pass.
+// Far extremes: the recurrence phi[lo, mid, hi] = (Gamma1[lo, mid] - Gamma1[mid, hi])
+// / (l_lo - l_hi).  Near: the Taylor series of phi about l_lo,
+//   phi[lo, mid, hi] = exp(-i dt l_lo) sum_{n=2}^{10} (-i dt)^n / n! h_{n-2}(0, v, w),
+// v = l_mid - l_lo, w = l_hi - l_lo >= 0, h_k the complete homogeneous
+// polynomial (the divided difference of (x - l_lo)^n).  The series runs only
+// when the extremes are a near pair, dt (l_hi - l_lo) <= TAU_DD2, so the first
+// dropped term is below 20 TAU_DD2^9 / 11! of the leading one.
+__device__ __noinline__ double2 dd2_dev(int a, int b, int c, const double* lam, const double2* eh,
+                           const double2* Y, int ld, const double* cser, double dt) {
+  const long long ka = value_key(lam[a]), kb = value_key(lam[b]), kc = value_key(lam[c]);
+  // sort (a, b, c) by (value, index) with integer compares
   int lo = a, mid = b, hi = c;
-  if (lam[lo] > lam[mid]) { int t = lo; lo = mid; mid = t; }
-  if (lam[mid] > lam[hi]) { int t = mid; mid = hi; hi = t; }
-  if (lam[lo] > lam[mid]) { int t = lo; lo = mid; mid = t; }
-  double xl = lam[lo], xm = lam[mid], xh = lam[hi];
-  if (dt * (xh - xl) > TAU_DD2) {
-    double2 g1 = gamma1(lo, mid, lam, eh, dt);
-    double2 g2 = gamma1(mid, hi, lam, eh, dt);
-    return cscale(csub(g1, g2), 1.0 / (xl - xh));
+  long long klo = ka, kmid = kb, khi = kc;
+  if (klo > kmid || (klo == kmid && lo > mid)) { int t = lo; lo = mid; mid = t; long long u = klo; klo = kmid; kmid = u; }
+  if (kmid > khi || (kmid == khi && mid > hi)) { int t = mid; mid = hi; hi = t; long long u = kmid; kmid = khi; khi = u; }
+  if (klo > kmid || (klo == kmid && lo > mid)) { int t = lo; lo = mid; mid = t; }
+  const double r = lo != hi ? Y[lo * ld + hi].x : 0.0;
+  if (nonzero_bits(r)) {
+    const double2 g1 = gamma1(lo, mid, lam, eh, dt);
+    const double2 g2 = gamma1(mid, hi, lam, eh, dt);
+    return cscale(csub(g1, g2), r);
   }
-  double cm = (xl + xm + xh) * (1.0 / 3.0);
-  double u = xl - cm, v = xm - cm, w = xh - cm;
-  double h2 = 1.0, h3 = 1.0, uk = 1.0;   // h_k(u,v), h_k(u,v,w), u^k at k = 0
-  double re = 0, im = 0;
-  double dtn = dt * dt, fact = 2.0;
-  for (int n = 2; n <= 10; ++n) {
-    int k = n - 2;
-    if (k > 0) {
-      uk *= u;
-      h2 = fma(v, h2, uk);
-      h3 = fma(w, h3, h2);
-    }
-    double t = dtn / fact * h3;
-    switch (n & 3) {                       // (-i)^n
+  const double v = lam[mid] - lam[lo], w = lam[hi] - lam[lo];
+  double vk = 1.0, h3 = 1.0;   // v^k, h_k(0, v, w) at k = 0
+  double re = -cser[2], im = 0.0;   // n = 2: (-i)^2 = -1
+#pragma unroll
+  for (int n = 3; n <= kSeriesTerms; ++n) {
+    vk *= v;
+    h3 = fma(w, h3, vk);
+    const double t = cser[n] * h3;
+    switch (n & 3) {   // (-i)^n
       case 0: re += t; break;
       case 1: im -= t; break;
       case 2: re -= t; break;
       default: im += t; break;
     }
-    dtn *= dt;
-    fact *= (double)(n + 1);
   }
-  double2 e = cexpi(-dt * cm);
+  const double2 e = cmul(eh[lo], eh[lo]);   // exp(-i dt l_lo)
   return cmul(e, make_double2(re, im));
 }
 
@@ -102,6 +123,16 @@ __device__ __forceinline__ void tri_index(int t, int N, int& i, int& k) {
   k = t - (r * N - r * (r - 1) / 2) + r;
 }
 
+// OZ (binary32-sweep problems, N <= 32, 256 threads): the N^3 products
+// M W, W^T (M W) and the two real factors of P~ M~ on the tensor cores by
+// error-free splitting (ozaki.cuh), binary64-accurate to about 2^-43 of the
+// factors' scales.
+constexpr int kOzPrepSlices = 6;
+__host__ __device__ inline size_t oz_prep_bytes() {
+  return 3 * (size_t)kOzPrepSlices * 32 * oz::LD * 2 + 3 * 32 * 4 + 16;
+}
+
+template <bool OZ>
 __device__ __forceinline__ void prep_step(const double* __restrict__ Wg,
                                           const double* __restrict__ eig,
                                           const double* __restrict__ Mg, int N, int j, double dt,
@@ -119,6 +150,20 @@ __device__ __forceinline__ void prep_step(const double* __restrict__ Wg,
   int* near = reinterpret_cast<int*>(eh + N);           // [NT] packed near pairs
   double2* Y = reinterpret_cast<double2*>(W);           // [N][ld] overlays W and T
   __shared__ int n_near;
+  __shared__ double cser[kSeriesTerms + 1];   // dt^n / n!
+  __nv_bfloat16 *s0 = nullptr, *s1 = nullptr, *s2 = nullptr;   // slice sets (OZ)
+  int *e0 = nullptr, *e1 = nullptr, *e2 = nullptr;
+  if (OZ) {
+    unsigned char* ob = reinterpret_cast<unsigned char*>(
+        (reinterpret_cast<uintptr_t>(near + N * (N + 1) / 2) + 15) & ~uintptr_t(15));
+    const size_t sl = (size_t)kOzPrepSlices * 32 * oz::LD;
+    s0 = reinterpret_cast<__nv_bfloat16*>(ob);
+    s1 = s0 + sl;
+    s2 = s1 + sl;
+    e0 = reinterpret_cast<int*>(s2 + sl);
+    e1 = e0 + 32;
+    e2 = e1 + 32;
+  }
 
   const int tid = threadIdx.x, nt = blockDim.x;
   const double* Wj = Wg + (size_t)j * N * N;
@@ -144,12 +189,32 @@ __device__ __forceinline__ void prep_step(const double* __restrict__ Wg,
     lam[p] = l;
     eh[p] = cexpi(-0.5 * dt * l);
   }
+  if (tid <= kSeriesTerms) {
+    double c = 1.0;
+    for (int n = 1; n <= tid; ++n) c = c * dt / n;
+    cser[tid] = c;
+  }
   __syncthreads();
 
   if (!doP && !doX) return;
   double2* Pg = Ptil + (size_t)j * N * N;
   if (doP) {
   // T = M W ; M~ = W^T T (upper triangle, mirrored: exactly symmetric)
+  if (OZ) {
+    oz::split32<kOzPrepSlices>(Mt, ld, N, true, s0, e0);    // M by rows
+    oz::split32<kOzPrepSlices>(W, ld, N, false, s1, e1);    // W by columns (= W^T by rows)
+    oz::mm32<kOzPrepSlices>(s0, e0, s1, e1, T, ld, N);
+    __syncthreads();
+    oz::split32<kOzPrepSlices>(T, ld, N, false, s2, e2);    // T by columns
+    oz::mm32<kOzPrepSlices>(s1, e1, s2, e2, Mt, ld, N);     // M~ = W^T T (M already split)
+    __syncthreads();
+    for (int t = tid; t < NT; t += nt) {
+      int i, k;
+      tri_index(t, N, i, k);
+      Mt[k * ld + i] = Mt[i * ld + k];
+    }
+    __syncthreads();
+  } else {
   for (int e = tid; e < N * N; e += nt) {
     const int i = e / N, k = e % N;
     double acc = 0;
@@ -166,19 +231,35 @@ __device__ __forceinline__ void prep_step(const double* __restrict__ Wg,
     Mt[k * ld + i] = acc;
   }
   __syncthreads();
-  // P~ = Gamma1 o M~
-  for (int e = tid; e < N * N; e += nt) {
-    const int p = e / N, q = e % N;
-    const double2 g = gamma1(p, q, lam, eh, dt);
-    const double2 v = cscale(g, Mt[p * ld + q]);
+  }
+  // P~ = Gamma1 o M~: complex symmetric (Gamma1 and M~ are), so over the
+  // upper triangle, mirrored
+  for (int t = tid; t < NT; t += nt) {
+    int p, q;
+    tri_index(t, N, p, q);
+    const double2 v = cscale(gamma1(p, q, lam, eh, dt), Mt[p * ld + q]);
     P[p * ld + q] = v;
-    Pg[e] = v;
-    if (Mtil) Mtil[(size_t)j * N * N + e] = Mt[p * ld + q];
+    P[q * ld + p] = v;
+    Pg[p * N + q] = v;
+    Pg[q * N + p] = v;
+    if (Mtil) {
+      Mtil[(size_t)j * N * N + p * N + q] = Mt[p * ld + q];
+      Mtil[(size_t)j * N * N + q * N + p] = Mt[p * ld + q];
+    }
   }
   }
   if (!doX) return;
   __syncthreads();
   // Y = P~ M~  (W, T are dead: Y overlays them)
+  if (OZ) {
+    const double* Pd = reinterpret_cast<const double*>(P);
+    oz::split32<kOzPrepSlices>(Pd, ld, N, true, s0, e0, 2);       // Re P~ by rows
+    oz::split32<kOzPrepSlices>(Pd + 1, ld, N, true, s1, e1, 2);   // Im P~ by rows
+    oz::split32<kOzPrepSlices>(Mt, ld, N, false, s2, e2);         // M~ by columns
+    double* Yd = reinterpret_cast<double*>(Y);
+    oz::mm32<kOzPrepSlices>(s0, e0, s2, e2, Yd, ld, N, 2);
+    oz::mm32<kOzPrepSlices>(s1, e1, s2, e2, Yd + 1, ld, N, 2);
+  } else {
   for (int e = tid; e < N * N; e += nt) {
     const int p = e / N, q = e % N;
     double re = 0, im = 0;
@@ -188,6 +269,7 @@ __device__ __forceinline__ void prep_step(const double* __restrict__ Wg,
       im = fma(P[p * ld + r].y, m, im);
     }
     Y[p * ld + q] = make_double2(re, im);
+  }
   }
   __syncthreads();
   double2* Xg = Xp + (size_t)j * N * N;
@@ -210,7 +292,7 @@ __device__ __forceinline__ void prep_step(const double* __restrict__ Wg,
     }
     const double rec = 1.0 / dl;
     const double2 x = cscale(csub(Y[p * ld + q], Y[q * ld + p]), 2.0 * rec);
-    bad |= !(isfinite(x.x) && isfinite(x.y));
+    bad |= !(finite_bits(x.x) && finite_bits(x.y));
     Xg[(size_t)p * N + q] = x;
     Xg[(size_t)q * N + p] = x;
     Y[p * ld + q].x = rec;
@@ -221,20 +303,26 @@ __device__ __forceinline__ void prep_step(const double* __restrict__ Wg,
   // Diagonal: X'_pp = 2 sum_r M~_pr^2 phi[l_p, l_r, l_p], one warp per p, lanes
   // over r.  For far r the recurrence on the extremes gives
   // phi[l_p, l_r, l_p] = (Gamma1_pp - Gamma1_pr) / (l_p - l_r), so the term is
-  // M~_pr (Gamma1_pp M~_pr - P~_pr) / (l_p - l_r) (P~ = Gamma1 o M~); near r
-  // (r = p included) takes the stable series.
+  // M~_pr (Gamma1_pp M~_pr - P~_pr) / (l_p - l_r) (P~ = Gamma1 o M~); at r = p,
+  // phi[l_p, l_p, l_p] = phi''(l_p) / 2 = -dt^2 / 2 exp(-i dt l_p); other near r
+  // take the series.  Gamma1_pp = -i dt exp(-i dt l_p).  Every lane of a warp
+  // occupies the binary64 pipe for each branch any lane takes, so the series
+  // runs only in rows that have a near r other than p.
   for (int p = warp; p < N; p += nwarp) {
-    const double2 gpp = gamma1(p, p, lam, eh, dt);
+    const double2 ep = cmul(eh[p], eh[p]);                 // exp(-i dt l_p)
+    const double2 gpp = make_double2(ep.y * dt, -ep.x * dt);
     double re = 0, im = 0;
     for (int r = lane; r < N; r += 32) {
       const double m = Mt[p * ld + r];
       const double rec = r == p ? 0.0 : Y[p * ld + r].x;
       double2 term;
-      if ((__double_as_longlong(rec) << 1) != 0) {    // rec != 0: a far pair
+      if (nonzero_bits(rec)) {    // a far pair
         const double2 tr = csub(cscale(gpp, m), P[p * ld + r]);
         term = cscale(tr, m * rec);
+      } else if (r == p) {
+        term = cscale(ep, -cser[2] * (m * m));
       } else {
-        term = cscale(dd2_dev(p, r, p, lam, eh, dt), m * m);
+        term = cscale(dd2_dev(p, r, p, lam, eh, Y, ld, cser, dt), m * m);
       }
       re += term.x;
       im += term.y;
@@ -243,7 +331,7 @@ __device__ __forceinline__ void prep_step(const double* __restrict__ Wg,
     im = warp_sum(im);
     if (lane == 0) {
       const double2 x = make_double2(2.0 * re, 2.0 * im);
-      bad |= !(isfinite(x.x) && isfinite(x.y));
+      bad |= !(finite_bits(x.x) && finite_bits(x.y));
       Xg[(size_t)p * N + p] = x;
     }
   }
@@ -253,7 +341,7 @@ __device__ __forceinline__ void prep_step(const double* __restrict__ Wg,
     double re = 0, im = 0;
     for (int r = lane; r < N; r += 32) {
       const double m2 = Mt[p * ld + r] * Mt[r * ld + q];
-      const double2 g2 = dd2_dev(p, r, q, lam, eh, dt);
+      const double2 g2 = dd2_dev(p, r, q, lam, eh, Y, ld, cser, dt);
       re = fma(m2, g2.x, re);
       im = fma(m2, g2.y, im);
     }
@@ -261,7 +349,7 @@ __device__ __forceinline__ void prep_step(const double* __restrict__ Wg,
     im = warp_sum(im);
     if (lane == 0) {
       const double2 x = make_double2(2.0 * re, 2.0 * im);
-      bad |= !(isfinite(x.x) && isfinite(x.y));
+      bad |= !(finite_bits(x.x) && finite_bits(x.y));
       Xg[(size_t)p * N + q] = x;
       Xg[(size_t)q * N + p] = x;
     }
@@ -275,8 +363,8 @@ __device__ __forceinline__ void prep_step(const double* __restrict__ Wg,
 // per SM; 512: the large-N launch).  GWS: storage in the global workspace (a
 // compile-time choice, so that the shared-memory instantiation keeps
 // shared-memory loads).
-template <int MAXT, bool GWS>
-__global__ void __launch_bounds__(MAXT, MAXT <= 256 ? 3 : 1)
+template <int MAXT, bool GWS, bool OZ = false>
+__global__ void __launch_bounds__(MAXT, OZ ? 2 : (MAXT <= 256 ? 3 : 1))
 k_prep(const double* __restrict__ Wg, const double* __restrict__ eig,
                        const double* __restrict__ Mg, int N, int J, double dt, int derivs,
                        double2* __restrict__ Ptil, double2* __restrict__ Xp,
@@ -285,7 +373,7 @@ k_prep(const double* __restrict__ Wg, const double* __restrict__ eig,
   extern __shared__ __align__(16) unsigned char smem_raw[];
   unsigned char* base = GWS ? gws + (size_t)blockIdx.x * per_cta : smem_raw;
   for (int j = blockIdx.x; j < J; j += gridDim.x) {
-    prep_step(Wg, eig, Mg, N, j, dt, derivs, Ptil, Xp, Mtil, status, base);
+    prep_step<OZ>(Wg, eig, Mg, N, j, dt, derivs, Ptil, Xp, Mtil, status, base);
     __syncthreads();
   }
 }
@@ -380,6 +468,15 @@ cudaError_t launch_prep(const double* W, const double* eig, const double* M, int
     if (!parts) return cudaSuccess;
   }
   StepGrid g;
+  if (!d_fp64 && N <= 32) {
+    // binary32-sweep problems: the products on the tensor cores
+    const size_t sm = prep_smem_bytes(N) + oz_prep_bytes();
+    if (sm <= max_dyn_smem((const void*)k_prep<256, false, true>)) {
+      k_prep<256, false, true><<<J, 256, sm, st>>>(W, eig, M, N, J, dt, parts, Ptil, Xp, Mtil, status,
+                                                   nullptr, 0);
+      return cudaGetLastError();
+    }
+  }
   const int threads = N <= 8 ? 64 : (N <= 16 ? 128 : (N <= 128 ? 256 : 512));
   if (threads <= 256) {
     if (!step_grid(prep_smem_bytes(N), J, ws, (const void*)k_prep<256, false>, g))

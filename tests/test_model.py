@@ -30,6 +30,9 @@ def test_tanh_network_model_matches_oracle(precision):
     prob = inputs.small_problem(N=6, K=3 * H, J=120, seed=81, dt=0.05)
     t = np.arange(prob.J) * prob.dt
     tol = TOL[precision]
+    # the problem is created with the model's Jacobian at the first theta as
+    # its basis: the precision policy estimates the binary32 error from it
+    prob.B = inputs.tanh_network_control(t, inputs.eval_theta(3 * H, 82, 0.7))[1]
     with q.Problem(prob, precision=precision) as P:
         for seed in (82, 83):     # two calls in a row, different theta
             theta = inputs.eval_theta(3 * H, seed, 0.7)
@@ -44,7 +47,7 @@ def test_tanh_network_model_matches_oracle(precision):
             full_ref = ref["hess"] + np.einsum("j,jlm->lm", ref["d"], hf)
             assert rel(full, full_ref) <= 10 * tol
         # the last Jacobian is now the basis of the linear evaluations
-        th2 = inputs.eval_theta(3 * H, 84)
+        th2 = inputs.eval_theta(3 * H, 84, 0.7)
         J2, g2, H2 = P.eval_grad_hess(th2)
         lin = orc.evaluate_samples(prob, jac @ th2, jac, order=2)
         assert rel(H2, lin["hess"]) <= tol and abs(J2 - lin["J"]) <= tol * abs(lin["J"])
