@@ -53,8 +53,9 @@ WORKLOAD = {"workload": "synthetic CI-shaped single problem, N=32 basis, K=64 si
 LAUNCHES_PER_EVAL = 29
 # DRAM bytes (read + written) of a kernel's launches in one evaluation on a
 # workload, from an ncu capture of the current kernel: (kernel, N, J) -> bytes.
-# k_prep: P part 33.88 MB read + 38.80 MB written, X part 99.48 + 29.35 MB.
-TRAFFIC_BYTES = {("k_prep", 32, 4000): 201.51e6}
+# k_prep: P part 33.87 MB read + 39.49 MB written, X part 99.53 + 29.47 MB;
+# k_eig_refine: 32.95 MB read (W of every step once), 0.01 MB written.
+TRAFFIC_BYTES = {("k_prep", 32, 4000): 202.37e6, ("k_eig_refine", 32, 4000): 32.96e6}
 
 
 def env_int(k, d):
@@ -417,6 +418,10 @@ def roofline(N, J, ph, fp64_tf):
             "peak_source": "binary64 FMA rate measured in this run (qoc_measure_fp64_rate); "
                            "MEASURED_PEAKS.json has no binary64 figure",
             "algorithmic": f"{d['algorithmic_gflop']:.3f} GFLOP per launch: {d['count']}, N={N}, J={J}",
+            "note": "for problems on binary32 sweeps with N <= 32 the binary64 N^3 products run on the "
+                    "tensor pipe by error-free splitting (six 8-bit slices per entry, bf16 mma with exact "
+                    "binary32 accumulation), so the effective binary64 rate can exceed the binary64 "
+                    "pipe's FMA peak",
             "kernel_ms": d["kernel_ms"], "kernels": kern,
             "phase_ms": {k: v for k, v in ph.items() if not k.startswith("k_") and k in
                          ("eig", "prep", "chains", "pointwise", "panels", "assembly")},

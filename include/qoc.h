@@ -141,6 +141,25 @@ qoc_status qoc_set_block_steps(qoc_problem* p, int steps);
  * QOC_EUNSUPPORTED when 32 ceil(N/8) kc > 1024 threads. */
 qoc_status qoc_set_panel_columns(qoc_problem* p, int kc);
 
+/* Cap on the binary64 refinement updates per step of the eigensolver
+ * (QOC_EIG_REFINED; 0 <= sweeps <= 16; default 4 for N <= 64, 8 above).  A
+ * step whose refinement has not reached its tolerance within the cap marks
+ * the evaluation's device status "eigensolver not converged", which the call
+ * returns as QOC_ENUMERIC (the results are then not to be used).  Takes effect
+ * for evaluations enqueued after the call; a batch keeps the value captured
+ * when it was built.  QOC_EINVAL outside the range. */
+qoc_status qoc_set_refine_sweeps(qoc_problem* p, int sweeps);
+
+/* Failure-detection self-test.  Runs the library's bounded device wait (the
+ * one every sweep uses on its shared-memory ring) on an mbarrier that nothing
+ * completes and with no copy in flight, giving up after limit_ns nanoseconds
+ * (1e3 <= limit_ns <= 1e10), on the problem's stream; then synchronises the
+ * stream and returns what the status check reports: QOC_ETIMEOUT when the
+ * wait gave up and the kernel returned, as any evaluation whose wait ran out
+ * would.  The device status is cleared and the problem stays usable.
+ * QOC_EINVAL for a limit outside the range. */
+qoc_status qoc_selftest_bounded_wait(qoc_problem* p, unsigned long long limit_ns);
+
 /* The arithmetic a problem's sweeps use (*effective: QOC_FP64 or
  * QOC_MIXED_FP32) and the estimated relative error of binary32 increments
  * at the current block length (*estimate, see qoc_precision; computed for

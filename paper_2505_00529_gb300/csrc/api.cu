@@ -736,6 +736,18 @@ qoc_status qoc_set_panel_columns(qoc_problem* p, int kc) {
   return QOC_OK;
 }
 
+qoc_status qoc_set_refine_sweeps(qoc_problem* p, int sweeps) {
+  if (!p || sweeps < 0 || sweeps > 16) return QOC_EINVAL;
+  p->refine_sweeps = sweeps;
+  return QOC_OK;
+}
+
+qoc_status qoc_selftest_bounded_wait(qoc_problem* p, unsigned long long limit_ns) {
+  if (!p || limit_ns < 1000ull || limit_ns > 10000000000ull) return QOC_EINVAL;
+  QOC_TRY(launch_wait_selftest(p->status, limit_ns, p->stream));
+  return qoc_sync_status(p);
+}
+
 qoc_status qoc_enable_timing(qoc_problem* p, int on) {
   if (!p) return QOC_EINVAL;
   p->timing = on ? 1 : 0;

@@ -240,6 +240,9 @@ cudaError_t launch_tr_subproblem(const double* out_gh, int K, double radius, dou
 cudaError_t launch_bfgs_update(double* B, const double* s, const double* g_old, const double* g_new, int K,
                                double* state, double min_curv, double* scratch, cudaStream_t st);
 cudaError_t launch_set_identity(double* B, int K, cudaStream_t st);
+// one CTA waits (bounded, limit_ns) on an mbarrier that nothing completes and
+// raises DEV_TIMEOUT in *status when it gives up
+cudaError_t launch_wait_selftest(int* status, unsigned long long limit_ns, cudaStream_t st);
 
 // one problem of a batched trust-region solve (device array, one CTA each)
 struct TrSlot {

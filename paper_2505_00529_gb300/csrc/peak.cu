@@ -7,8 +7,12 @@
 // latency of one chain, bounds the kernel; the sum of the chains is written
 // out so that nothing is eliminated.  One launch covers `ctas_per_sm` CTAs of
 // 256 threads per SM.
+//
+// Also the failure-detection self-test: the bounded mbarrier wait of the
+// sweeps, run on a barrier that nothing completes.
 #include <cuda_runtime.h>
 
+#include "common.cuh"
 #include "kernels.hpp"
 #include "qoc.h"
 
@@ -31,7 +35,28 @@ __global__ void __launch_bounds__(256) k_fp64_fma_rate(double a, double b, doubl
   out[blockIdx.x * blockDim.x + threadIdx.x] = s;
 }
 
+// One warp: thread 0 initialises an mbarrier expecting one arrival that never
+// comes (no copy is issued), every thread waits on it with the sweeps' bounded
+// wait, and the first to give up raises DEV_TIMEOUT.
+__global__ void k_wait_selftest(int* status, unsigned long long limit_ns) {
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x == 0) {
+    qoc::mbar_init(&bar, 1);
+    qoc::mbar_fence_init();
+  }
+  __syncthreads();
+  const bool ok = qoc::mbar_wait_bounded(&bar, 0, limit_ns);
+  if (!__all_sync(0xffffffffu, ok) && threadIdx.x == 0) qoc::raise_status(status, qoc::DEV_TIMEOUT);
+}
+
 }  // namespace
+
+namespace qoc {
+cudaError_t launch_wait_selftest(int* status, unsigned long long limit_ns, cudaStream_t st) {
+  k_wait_selftest<<<1, 32, 0, st>>>(status, limit_ns);
+  return cudaGetLastError();
+}
+}  // namespace qoc
 
 extern "C" qoc_status qoc_measure_fp64_rate(int ctas_per_sm, int repeats, double* tflops, double* ms) {
   if (!tflops || ctas_per_sm < 1 || ctas_per_sm > 64 || repeats < 1) return QOC_EINVAL;
