@@ -685,13 +685,15 @@ def run_profile(args):
 
 
 def run_warm_start(args):
-    """Learned warm start on the N=32 system (H0, M of the bench workload),
-    horizon shortened to T=5 (J=1000, dt=0.005) with a K=64 Fourier basis:
-    theta* from the library's trust region on random unit targets, MLP
-    2N -> 256^3 -> K trained by the library's kernels, then held-out targets
-    solved from theta=0, from the MLP's theta0, and from the guarded start
-    t* MLP(beta) (t* minimising J over t in {0, 1/4, 1/2, 3/4, 1}) to the
-    same tolerance."""
+    """Learned warm start on the N=32 system (H0, M of the bench workload,
+    dt=0.005) with a K=64 Fourier basis over J = --ws-steps steps (4000:
+    T=20, the bench workload itself): theta* from the library's trust region
+    on random unit targets, MLP 2N -> 256^3 -> K trained by the library's
+    kernels, then held-out targets solved from theta=0, from the MLP's
+    theta0, from the guarded start t* MLP(beta) (t* minimising J over t in
+    {0, 1/4, 1/2, 3/4, 1}) and from the decrement-chosen start (0 or
+    MLP(beta), the smaller Newton decrement) to the same tolerance; the plain
+    binary64 method on the first --ws-plain held-out targets."""
     import numpy as np
     import torch
     import paper_2505_00529_gb300 as q
@@ -699,22 +701,25 @@ def run_warm_start(args):
     torch.cuda.set_device(env_int("LOCAL_RANK", 0))
     build.build()
     base = inputs.config_problem(4)
-    J = 1000
-    prob = inputs.Problem(base.H0, base.M, base.alpha, base.beta,
-                          inputs.sine_cosine_basis(J, base.dt, 64), base.dt, base.dt, 1.0, "warm-start")
+    J = args.ws_steps
+    prob = base if J == base.J else inputs.Problem(base.H0, base.M, base.alpha, base.beta,
+                                                   inputs.sine_cosine_basis(J, base.dt, 64), base.dt,
+                                                   base.dt, 1.0, "warm-start")
     train = inputs.random_targets(4000, prob.N, args.ws_train)
     test = inputs.random_targets(4001, prob.N, args.ws_test)
     prec = q.QOC_MIXED_FP32 if args.precision == "mixed" else q.QOC_FP64
     t0 = time.perf_counter()
     r = warmstart.compare(prob, train, test, precision=prec, workers=args.ws_workers, epochs=args.ws_epochs,
-                          batch=128, lr=1e-3, seed=0, gtol=args.ws_gtol, xtol=1e-12, max_iter=500)
+                          batch=128, lr=1e-3, seed=0, n_plain=args.ws_plain, train_cache=args.ws_cache,
+                          gtol=args.ws_gtol, xtol=1e-12, max_iter=500)
     r["total_seconds"] = time.perf_counter() - t0
     line = {"metric": "trust-region iterations and wall time on held-out targets: learned warm start vs theta=0",
             "value": r["wall_ratio_zero_over_mlp"],
             "unit": "wall-time ratio of the held-out solves, theta=0 / MLP start (same final tolerance)",
             "higher_is_better": True, "n_gpus": 1, "dtype": "f32 panels + f64" if prec else "f64",
             "data": "synthetic",
-            "config": {"workload": f"N=32 system, K=64 Fourier basis, T=5, J={J}; {args.ws_train} training / "
+            "config": {"workload": f"N=32 system, K=64 Fourier basis, T={J * base.dt:g}, J={J}; "
+                                   f"{args.ws_train} training / "
                                    f"{args.ws_test} held-out random unit targets; MLP 64-256-256-256-64 GELU, "
                                    f"{args.ws_epochs} epochs Adam, bfloat16 inference", "gtol": args.ws_gtol},
             "warm_start": r}
@@ -871,6 +876,10 @@ def main():
     ap.add_argument("--batch-size", type=int, default=256)
     ap.add_argument("--batch-mem-gb", type=float, default=160.0,
                     help="device memory per batch chunk (problems are created chunk by chunk)")
+    ap.add_argument("--ws-steps", type=int, default=4000, help="time steps J of the warm-start system")
+    ap.add_argument("--ws-plain", type=int, default=200,
+                    help="held-out targets also solved by the plain binary64 method")
+    ap.add_argument("--ws-cache", default=None, help=".npz file caching the training optima")
     ap.add_argument("--ws-train", type=int, default=2000)
     ap.add_argument("--ws-test", type=int, default=200)
     ap.add_argument("--ws-epochs", type=int, default=300)

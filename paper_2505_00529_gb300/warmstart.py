@@ -130,6 +130,52 @@ def guarded_starts(prob, betas, theta_mlp, precision=_lib.QOC_MIXED_FP32, worker
     return out, tstar, secs
 
 
+def newton_decrement(grad, hess):
+    """g^T H^-1 g when H is positive definite (Cholesky), else +inf: the
+    quadratic model's predicted decrease of J (times two) to its minimiser,
+    a measure of how far a start is from a local minimum in the Newton
+    metric."""
+    try:
+        L = np.linalg.cholesky(np.asarray(hess))
+    except np.linalg.LinAlgError:
+        return np.inf
+    y = np.linalg.solve(L, np.asarray(grad))
+    return float(y @ y)
+
+
+def decrement_starts(prob, betas, theta_mlp, precision=_lib.QOC_MIXED_FP32, workers=4):
+    """theta0 = the one of (0, MLP(beta)) with the smaller Newton decrement
+    (gradient and Hessian from the library at both), ties and two indefinite
+    Hessians decided by the lower J.  Returns (theta0s, chose_mlp, seconds)."""
+    n, K = len(betas), prob.B.shape[1]
+    out = np.zeros((n, K))
+    chose = np.zeros(n, dtype=bool)
+    problems = [_lib.Problem(prob, precision=precision) for _ in range(workers)]
+
+    def run(w):
+        P = problems[w]
+        for i in range(w, n, workers):
+            P.set_target(betas[i])
+            cand = []
+            for th in (np.zeros(K), theta_mlp[i]):
+                try:
+                    J, g, H = P.eval_grad_hess(th)
+                    cand.append((newton_decrement(g, H), J))
+                except _lib.QocError:
+                    cand.append((np.inf, np.inf))
+            pick = 1 if (cand[1][0], cand[1][1]) <= (cand[0][0], cand[0][1]) else 0
+            chose[i] = pick == 1
+            out[i] = theta_mlp[i] if pick else 0.0
+
+    t0 = time.perf_counter()
+    with cf.ThreadPoolExecutor(workers) as ex:
+        list(ex.map(run, range(workers)))
+    secs = time.perf_counter() - t0
+    for P in problems:
+        P.close()
+    return out, chose, secs
+
+
 class WarmStart:
     """theta0 = scale * MLP([Re beta, Im beta]) + shift (outputs standardised
     on the training set)."""
@@ -161,15 +207,31 @@ class WarmStart:
 
 
 def compare(prob, train_betas, test_betas, precision=_lib.QOC_MIXED_FP32, workers=4, epochs=200,
-            batch=128, lr=1e-3, seed=0, tr_batch=32, **tr):
+            batch=128, lr=1e-3, seed=0, tr_batch=32, n_plain=None, train_cache=None, **tr):
     """Full warm-start experiment: theta* for the training targets (from 0),
-    train, then solve the held-out targets from 0 and from the MLP."""
+    train, then solve the held-out targets from 0, from the MLP, from the
+    guarded start and from the decrement-chosen start; the plain binary64
+    method on the first `n_plain` held-out targets (all when None).
+    `train_cache`: an .npz path holding the training optima (theta*, their
+    convergence flags, the seconds they took) for these targets, written
+    after they are computed and read instead of recomputing them."""
+    import os
     K = prob.B.shape[1]
     N = prob.H0.shape[0]
-    th_train, info_train, t_data = solve_many(prob, train_betas, np.zeros((len(train_betas), K)),
-                                              precision, tr_batch, **tr)
-    ok = np.array([i["stop"] in ("gtol", "xtol") and np.all(np.isfinite(t))
-                   for i, t in zip(info_train, th_train)])
+    cached = None
+    if train_cache and os.path.exists(train_cache):
+        z = np.load(train_cache)
+        if z["betas"].shape == train_betas.shape and np.array_equal(z["betas"], train_betas):
+            cached = z
+    if cached is not None:
+        th_train, ok, t_data = cached["theta"], cached["ok"], float(cached["seconds"])
+    else:
+        th_train, info_train, t_data = solve_many(prob, train_betas, np.zeros((len(train_betas), K)),
+                                                  precision, tr_batch, **tr)
+        ok = np.array([i["stop"] in ("gtol", "xtol") and np.all(np.isfinite(t))
+                       for i, t in zip(info_train, th_train)])
+        if train_cache:
+            np.savez(train_cache, betas=train_betas, theta=th_train, ok=ok, seconds=t_data)
     ws = WarmStart(N, K, seed=seed)
     t0 = time.perf_counter()
     losses = ws.fit(train_betas[ok], th_train[ok], epochs=epochs, batch=batch, lr=lr, seed=seed)
@@ -179,12 +241,21 @@ def compare(prob, train_betas, test_betas, precision=_lib.QOC_MIXED_FP32, worker
     _, info_mlp, t_mlp = solve_many(prob, test_betas, theta0, precision, tr_batch, **tr)
     theta_g, tstar, t_guard_eval = guarded_starts(prob, test_betas, theta0, precision, workers)
     _, info_g, t_g = solve_many(prob, test_betas, theta_g, precision, tr_batch, **tr)
+    theta_d, chose, t_dec_eval = decrement_starts(prob, test_betas, theta0, precision, workers)
+    _, info_d, t_d = solve_many(prob, test_betas, theta_d, precision, tr_batch, **tr)
     ws.close()
-    # the plain method on the same targets: binary64, one problem at a time, from theta = 0
-    _, info_plain, t_plain = solve_sequential(prob, test_betas, np.zeros((len(test_betas), K)),
+    # the plain method on (a prefix of) the same targets: binary64, one problem
+    # at a time, from theta = 0; the combined form timed on the same prefix
+    npl = len(test_betas) if n_plain is None else min(n_plain, len(test_betas))
+    _, info_plain, t_plain = solve_sequential(prob, test_betas[:npl], np.zeros((npl, K)),
                                               _lib.QOC_FP64, **tr)
+    _, info_comb, t_comb = solve_many(prob, test_betas[:npl], theta0[:npl], precision, tr_batch, **tr)
     conv = lambda i: i["stop"] in ("gtol", "xtol")
-    good = np.array([conv(a) and conv(b) and conv(c) for a, b, c in zip(info_zero, info_mlp, info_g)])
+    good = np.array([conv(a) and conv(b) and conv(c) and conv(d)
+                     for a, b, c, d in zip(info_zero, info_mlp, info_g, info_d)])
+    itd = np.array([i["iters"] for i in info_d])[good]
+    Jd = np.array([i["J"] for i in info_d])[good]
+    ghd = np.array([i.get("n_eval_gh", 0) for i in info_d])[good]
     gh0 = np.array([i.get("n_eval_gh", 0) for i in info_zero])[good]
     gh1 = np.array([i.get("n_eval_gh", 0) for i in info_mlp])[good]
     it0 = np.array([i["iters"] for i in info_zero])[good]
@@ -212,12 +283,26 @@ def compare(prob, train_betas, test_betas, precision=_lib.QOC_MIXED_FP32, worker
             "form": "batched trust region (batches of %d), %s, theta0 from the network" % (
                 tr_batch, "mixed precision" if precision == _lib.QOC_MIXED_FP32 else "binary64"),
             "plain": "binary64, one problem at a time, theta0 = 0",
-            "wall_combined_s": t_mlp, "wall_plain_s": t_plain, "speedup": t_plain / t_mlp,
+            "targets": npl,
+            "wall_combined_s": t_comb, "wall_plain_s": t_plain, "speedup": t_plain / t_comb,
+            "iters_combined_mean": float(np.mean([i["iters"] for i in info_comb])),
             "iters_plain_mean": float(np.mean([i["iters"] for i in info_plain])),
+            "converged_combined": float(np.mean([conv(i) for i in info_comb])),
             "converged_plain": float(np.mean([conv(i) for i in info_plain])),
             "frac_combined_not_worse_J": float(np.mean([
-                a["J"] <= b["J"] * (1 + 1e-6) for a, b in zip(info_mlp, info_plain)
+                a["J"] <= b["J"] * (1 + 1e-6) for a, b in zip(info_comb, info_plain)
                 if conv(a) and conv(b)])),
+        },
+        "decrement": {
+            "rule": "theta0 = the one of 0 and MLP(beta) with the smaller Newton decrement g^T H^-1 g "
+                    "(H positive definite; else +inf), ties by J",
+            "chose_mlp_fraction": float(chose.mean()),
+            "iters_mean": float(itd.mean()), "iters_median": float(np.median(itd)),
+            "frac_fewer_iters": float(np.mean(itd < it0)), "frac_more_iters": float(np.mean(itd > it0)),
+            "hess_evals_mean": float(ghd.mean()),
+            "wall_s": t_d + t_dec_eval, "choice_eval_s": t_dec_eval,
+            "J_mean": float(Jd.mean()), "frac_not_worse_J": float(np.mean(Jd <= J0 * (1 + 1e-6))),
+            "converged": float(np.mean([conv(i) for i in info_d])),
         },
         "guarded": {
             "rule": "theta0 = t* MLP(beta), t* = argmin J(t MLP(beta)) over t in "

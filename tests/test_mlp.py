@@ -94,3 +94,17 @@ def test_gpu_warm_start_reduces_trust_region_iterations():
                           lr=2e-3, gtol=1e-7, xtol=1e-12, max_iter=200)
     assert r["converged_mlp"] >= r["converged_zero"] - 1e-9
     assert r["iters_mlp_mean"] < r["iters_zero_mean"], r
+
+
+def test_newton_decrement():
+    """g^T H^-1 g for a positive definite H (against a direct solve), +inf
+    for an indefinite or singular one."""
+    from paper_2505_00529_gb300 import warmstart
+    rng = np.random.default_rng(3)
+    A = rng.normal(size=(6, 6))
+    H = A @ A.T + 0.5 * np.eye(6)
+    g = rng.normal(size=6)
+    assert np.isclose(warmstart.newton_decrement(g, H), g @ np.linalg.solve(H, g), rtol=1e-12)
+    Hi = H - 10.0 * np.eye(6) * np.abs(np.linalg.eigvalsh(H)).max()
+    assert warmstart.newton_decrement(g, Hi) == np.inf
+    assert warmstart.newton_decrement(g, np.zeros((6, 6))) == np.inf
