@@ -371,6 +371,8 @@ def run_ours(args):
                 "fp64_plain": fp64, "tr_solve": tr, "tr_solve_batched": trb,
                 "fp64_fma_peak": {"tflops": fp64_tf, "ms": fp64_ms, "how": "qoc_measure_fp64_rate: "
                                   "independent binary64 FMA chains, 4 CTAs x 256 threads per SM, best of 5"},
+                "eig_stats": {k: ph_mean[k] for k in ("refine_updates_per_step", "cleanup_rotated_fraction",
+                                                      "final_pass_fraction") if k in ph_mean},
                 "other_workloads": extra}
         print(json.dumps(line), flush=True)
     if dist:

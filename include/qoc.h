@@ -357,7 +357,11 @@ qoc_status qoc_mlp_train(qoc_mlp* m, const int* perm, int epochs, int batch, flo
 qoc_status qoc_mlp_gradient(qoc_mlp* m, const float* X, const float* T, int batch, float* loss,
                             float* grad);
 
-/* Inference on n rows of X into Y (n x n_out); bf16 != 0 uses bfloat16 weights. */
+/* Inference on n rows of X into Y (n x n_out).  bf16 != 0: every layer on
+ * the tensor cores with bfloat16 weights and bfloat16 activations (rounded
+ * from binary32 as each layer reads them), binary32 accumulation, bias and
+ * GELU in binary32 (relative error against a binary64 evaluation of the same
+ * network of order 1e-2 of the output scale); bf16 == 0: binary32 throughout. */
 qoc_status qoc_mlp_predict(qoc_mlp* m, const float* X, int n, float* Y, int bf16);
 
 /* Copy the current parameters to the host. */

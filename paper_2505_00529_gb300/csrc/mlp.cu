@@ -6,7 +6,9 @@
 //   forward   h_{k+1} = gelu(W_k h_k + b_k) (last layer linear), binary32
 //   backward  standard reverse mode through the same layers, binary32
 //   Adam      m <- b1 m + (1-b1) g, v <- b2 v + (1-b2) g^2, w -= lr mhat / (sqrt(vhat) + eps)
-//   inference bfloat16 weights, binary32 arithmetic
+//   inference bfloat16 weights and activations on the tensor cores
+//             (mma.sync m16n8k16, binary32 accumulation, bias and GELU in
+//             the epilogue), or binary32 throughout
 // GELU is the exact form x Phi(x) = x (1 + erf(x / sqrt 2)) / 2.
 #include <cuda_bf16.h>
 
@@ -75,6 +77,72 @@ __global__ void k_gemm(const float* __restrict__ A, long sam, long sak, const TW
   }
 }
 
+// Inference GEMM on the tensor cores: C = A B with A (binary32 activations,
+// rounded to bfloat16 as they are staged) and B (bfloat16 weights), binary32
+// accumulation; epilogue mode 1 (bias + GELU) or 2 (bias).  32 x 32 output
+// tile per CTA of 4 warps, warp w the 16 x 16 block (w / 2, w % 2) as two
+// m16n8 tiles; K in chunks of 32 (two k16 steps).  Shared tiles hold A as
+// [m][k] and B transposed as [n][k] (k contiguous, as the .col operand
+// wants), 40 bfloat16 per row so the fragment loads are free of bank
+// conflicts.  Entries outside M, N, K are zero.
+__device__ __forceinline__ uint32_t ld_b32(const __nv_bfloat16* p) {
+  return *reinterpret_cast<const uint32_t*>(p);
+}
+
+__global__ void __launch_bounds__(128) k_gemm_bf16_tc(const float* __restrict__ A, long sam, long sak,
+                                                      const __nv_bfloat16* __restrict__ B, long sbk,
+                                                      long sbn, float* __restrict__ C, long scm, int M,
+                                                      int N, int K, int mode,
+                                                      const float* __restrict__ bias) {
+  constexpr int LDT = 40;
+  __shared__ __align__(16) __nv_bfloat16 As[32 * LDT];
+  __shared__ __align__(16) __nv_bfloat16 Bs[32 * LDT];
+  const int m0 = blockIdx.y * 32, n0 = blockIdx.x * 32;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int g = lane >> 2, t = lane & 3;
+  const int rm = (warp >> 1) * 16, cw = (warp & 1) * 16;
+  float acc[2][4] = {{0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}};
+  for (int k0 = 0; k0 < K; k0 += 32) {
+    for (int idx = tid; idx < 32 * 32; idx += 128) {
+      const int r = idx >> 5, c = idx & 31;
+      const int m = m0 + r, ka = k0 + c;
+      As[r * LDT + c] = __float2bfloat16_rn((m < M && ka < K) ? A[m * sam + ka * sak] : 0.f);
+      const int kb = k0 + r, n = n0 + c;   // B(kb, n) -> Bs[n][kb]
+      Bs[c * LDT + r] = (kb < K && n < N) ? B[kb * sbk + n * sbn] : __float2bfloat16_rn(0.f);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < 32; kk += 16) {
+      const uint32_t a0 = ld_b32(As + (rm + g) * LDT + kk + 2 * t);
+      const uint32_t a1 = ld_b32(As + (rm + g + 8) * LDT + kk + 2 * t);
+      const uint32_t a2 = ld_b32(As + (rm + g) * LDT + kk + 2 * t + 8);
+      const uint32_t a3 = ld_b32(As + (rm + g + 8) * LDT + kk + 2 * t + 8);
+#pragma unroll
+      for (int nt = 0; nt < 2; ++nt) {
+        const int cn = cw + nt * 8;
+        const uint32_t b0 = ld_b32(Bs + (cn + g) * LDT + kk + 2 * t);
+        const uint32_t b1 = ld_b32(Bs + (cn + g) * LDT + kk + 2 * t + 8);
+        asm volatile(
+            "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
+            "{%8,%9}, {%0,%1,%2,%3};\n"
+            : "+f"(acc[nt][0]), "+f"(acc[nt][1]), "+f"(acc[nt][2]), "+f"(acc[nt][3])
+            : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+      }
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int nt = 0; nt < 2; ++nt) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int m = m0 + rm + g + (q >= 2 ? 8 : 0), n = n0 + cw + nt * 8 + 2 * t + (q & 1);
+      if (m >= M || n >= N) continue;
+      const float v = acc[nt][q] + bias[n];
+      C[m * scm + n] = mode == 1 ? gelu_f(v) : v;
+    }
+  }
+}
+
 // bias gradient: db[n] = sum_b dY[b][n]
 __global__ void k_colsum(const float* __restrict__ dY, int Bn, int N, float* __restrict__ db) {
   const int n = blockIdx.x * blockDim.x + threadIdx.x;
@@ -137,6 +205,14 @@ cudaError_t mlp_gemm(const float* A, long sam, long sak, const void* B, int b_bf
   else
     k_gemm<float><<<gemm_grid(M, N), 256, 0, st>>>(A, sam, sak, (const float*)B, sbk, sbn, C, scm, M,
                                                    N, K, mode, bias, pre, pre_in, accumulate);
+  return cudaGetLastError();
+}
+
+cudaError_t mlp_gemm_bf16_tc(const float* A, long sam, long sak, const void* B, long sbk, long sbn,
+                             float* C, long scm, int M, int N, int K, int mode, const float* bias,
+                             cudaStream_t st) {
+  k_gemm_bf16_tc<<<gemm_grid(M, N), 128, 0, st>>>(A, sam, sak, (const __nv_bfloat16*)B, sbk, sbn, C, scm,
+                                                  M, N, K, mode, bias);
   return cudaGetLastError();
 }
 

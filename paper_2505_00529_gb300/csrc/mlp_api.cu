@@ -22,6 +22,9 @@ cudaError_t mlp_mse(const float* Y, const float* T, int n, float inv_b, float* d
 cudaError_t mlp_adam(float* w, const float* g, float* m, float* v, int n, float lr, float b1,
                      float b2, float eps, float c1, float c2, cudaStream_t st);
 cudaError_t mlp_to_bf16(const float* x, void* y, int n, cudaStream_t st);
+cudaError_t mlp_gemm_bf16_tc(const float* A, long sam, long sak, const void* B, long sbk, long sbn,
+                             float* C, long scm, int M, int N, int K, int mode, const float* bias,
+                             cudaStream_t st);
 cudaError_t mlp_gather(const float* src, const int* idx, int rows, int cols, float* dst,
                        cudaStream_t st);
 }  // namespace qoc
@@ -73,9 +76,14 @@ qoc_status forward(qoc_mlp* p, const float* X, int B, int bf16) {
   for (int k = 0; k < p->L; ++k) {
     const int a = p->d[k], b = p->d[k + 1];
     const bool last = k == p->L - 1;
-    const void* W = bf16 ? (const void*)((const unsigned short*)p->wbf + p->woff[k]) : (const void*)(p->w + p->woff[k]);
-    MTRY(mlp_gemm(in, a, 1, W, bf16, b, 1, p->h[k + 1], b, B, b, a, last ? 2 : 1, p->w + p->boff[k],
-                  p->pre[k], nullptr, 0, p->stream));
+    if (bf16) {   // inference on the tensor cores: bfloat16 weights and activations
+      const void* W = (const void*)((const unsigned short*)p->wbf + p->woff[k]);
+      MTRY(mlp_gemm_bf16_tc(in, a, 1, W, b, 1, p->h[k + 1], b, B, b, a, last ? 2 : 1, p->w + p->boff[k],
+                            p->stream));
+    } else {
+      MTRY(mlp_gemm(in, a, 1, p->w + p->woff[k], 0, b, 1, p->h[k + 1], b, B, b, a, last ? 2 : 1,
+                    p->w + p->boff[k], p->pre[k], nullptr, 0, p->stream));
+    }
     in = p->h[k + 1];
   }
   return QOC_OK;

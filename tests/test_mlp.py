@@ -58,9 +58,58 @@ def test_gpu_mlp_gradient_matches_oracle():
     y32 = m.predict(X, bf16=False)
     y_o, _ = mo.forward(p.astype(float), d, X.astype(float))
     assert np.linalg.norm(y32 - y_o) <= 1e-5 * np.linalg.norm(y_o)
-    y16 = m.predict(X, bf16=True)                           # bfloat16 weights: ~3 significant digits
+    y16 = m.predict(X, bf16=True)           # bfloat16 weights and activations: ~2-3 significant digits
     assert np.linalg.norm(y16 - y_o) <= 2e-2 * np.linalg.norm(y_o)
     m.close()
+
+
+def _bf16(x):
+    """Round binary32 values to bfloat16 (nearest, ties to even), kept as binary32."""
+    a = np.ascontiguousarray(x, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    r = (a + 0x7FFF + ((a >> 16) & 1)) & 0xFFFF0000
+    return r.astype(np.uint32).view(np.float32)
+
+
+def _bf16_forward(params, d, X):
+    """The network with every layer's weights and input activations rounded
+    to bfloat16, products and sums in binary64, bias and GELU in binary64."""
+    layers = mo.unpack(params, d)
+    h = X.astype(np.float32)
+    for k, (W, b) in enumerate(layers):
+        z = _bf16(h).astype(float) @ _bf16(W.astype(np.float32)).astype(float) + b.astype(np.float32)
+        h = (mo.gelu(z) if k < len(layers) - 1 else z).astype(np.float32)
+    return h.astype(float)
+
+
+def test_bf16_rounding_helper():
+    x = np.array([1.0, 1.00390625, 1.001953125, 1.005859375, -3.0e-3, 0.0], dtype=np.float32)
+    # 1 + 2^-8 is halfway between 1 and 1 + 2^-7: ties to even (1); 1 + 3 * 2^-9 rounds up
+    np.testing.assert_array_equal(_bf16(x)[:4], np.array([1.0, 1.0, 1.0, 1.0078125], dtype=np.float32))
+    assert abs(_bf16(x)[4] + 3.0e-3) <= 3.0e-3 * 2.0 ** -8 and _bf16(x)[5] == 0.0
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("shape,batch", [((64, 256, 3, 64), 37), ((64, 256, 3, 64), 200), ((8, 64, 2, 4), 45)])
+def test_gpu_mlp_bf16_tensor_core_inference(shape, batch):
+    """bfloat16 inference on the tensor cores against the same rounding done
+    on the host with binary64 sums (only the binary32 accumulation order
+    differs), and against the unrounded binary64 network (the bfloat16
+    error itself)."""
+    import paper_2505_00529_gb300 as q
+    from paper_2505_00529_gb300 import build
+    build.build()
+    n_in, hid, nh, n_out = shape
+    d = mo.widths(n_in, hid, nh, n_out)
+    p = _params(d, 7).astype(np.float32)
+    X = np.random.default_rng(8).normal(size=(batch, n_in)).astype(np.float32)
+    m = q.MLP(n_in, hid, nh, n_out, p, max_batch=256)
+    y16 = m.predict(X, bf16=True).astype(float)
+    m.close()
+    y_r = _bf16_forward(p, d, X)
+    y_o, _ = mo.forward(p.astype(float), d, X.astype(float))
+    assert np.linalg.norm(y16 - y_r) <= 2e-4 * np.linalg.norm(y_r)
+    assert np.abs(y16 - y_r).max() <= 2e-3 * np.abs(y_r).max()
+    assert np.linalg.norm(y16 - y_o) <= 2e-2 * np.linalg.norm(y_o)
 
 
 @pytest.mark.gpu
