@@ -131,6 +131,18 @@ qoc_status qoc_set_eig_method(qoc_problem* p, int method);
  * would raise the error estimate above 1e-6. */
 qoc_status qoc_set_block_steps(qoc_problem* p, int steps);
 
+/* Forward pipeline of a time-blocked gradient or Hessian evaluation (no
+ * counterpart in the paper; a reordering of Alg. 2's first loops that
+ * changes no result): after the binary32 eigensolver start over all steps,
+ * the binary64 refinement and the increments D_j run in `chunks` chunks of
+ * whole time blocks, and the forward state sweep follows chunk by chunk on
+ * its own stream, resuming each chunk from the block-start state the
+ * previous one stored, so that its dependent steps overlap the refinement of
+ * the later chunks.  Results are bit-identical to the unchunked schedule.
+ * chunks: 0 or 1 off, 2..8 the chunk count (at most one block each), -1 the
+ * built-in choice (4 when steps >= 1024, else off).  QOC_EINVAL otherwise. */
+qoc_status qoc_set_pipeline(qoc_problem* p, int chunks);
+
 /* Panel columns per CTA of the tangent and second-order adjoint sweeps
  * (1, 2 or 4; 0 restores the built-in choice, 1).  A launch-shape knob; the
  * autotuner in the Python package picks it together with the block steps.

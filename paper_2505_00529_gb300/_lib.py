@@ -34,7 +34,7 @@ EXPORTS = [
     "qoc_assemble_grad_hess_noalloc", "qoc_get_phase_times", "qoc_get_eig_stats",
     "qoc_set_panel_columns", "qoc_get_precision", "qoc_measure_fp64_rate",
     "qoc_batch_trust_region_solve", "qoc_trust_region_solve_bfgs", "qoc_tr_subproblem",
-    "qoc_eval_grad_hess_model", "qoc_set_refine_sweeps", "qoc_selftest_bounded_wait",
+    "qoc_eval_grad_hess_model", "qoc_set_refine_sweeps", "qoc_selftest_bounded_wait", "qoc_set_pipeline",
 ]
 
 
@@ -83,6 +83,7 @@ def lib() -> C.CDLL:
         L.qoc_set_block_steps.argtypes = [C.c_void_p, C.c_int]
         L.qoc_set_panel_columns.argtypes = [C.c_void_p, C.c_int]
         L.qoc_set_refine_sweeps.argtypes = [C.c_void_p, C.c_int]
+        L.qoc_set_pipeline.argtypes = [C.c_void_p, C.c_int]
         L.qoc_selftest_bounded_wait.argtypes = [C.c_void_p, C.c_ulonglong]
         L.qoc_get_precision.argtypes = [C.c_void_p, C.POINTER(C.c_int), _dp]
         L.qoc_measure_fp64_rate.argtypes = [C.c_int, C.c_int, _dp, _dp]
@@ -200,6 +201,10 @@ def qoc_set_block_steps(h, steps):
 
 def qoc_set_panel_columns(h, kc):
     _check(lib().qoc_set_panel_columns(C.c_void_p(h), int(kc)), "qoc_set_panel_columns")
+
+
+def qoc_set_pipeline(h, chunks):
+    _check(lib().qoc_set_pipeline(C.c_void_p(h), int(chunks)), "qoc_set_pipeline")
 
 
 def qoc_set_refine_sweeps(h, sweeps):

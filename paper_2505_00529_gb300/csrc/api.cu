@@ -50,6 +50,13 @@ struct qoc_problem {
   cudaEvent_t ev_state = nullptr, ev_ptil = nullptr, ev_panels = nullptr;
   int timing = 0;
   int sched = 0;                        // 0 sequential, 1 three-stream (time-blocked, order >= 1)
+  // forward pipeline: the refinement and increments in chunks of steps, the
+  // state chain following chunk by chunk on the chain stream
+  static constexpr int kMaxChunks = 8;
+  int pipeline = -1;                    // chunks (qoc_set_pipeline); -1 the built-in choice
+  int piped = 0;                        // chunks of the last evaluation (0: not pipelined)
+  cudaEvent_t ev_chunk[kMaxChunks] = {};
+  cudaEvent_t evp[2 * kMaxChunks] = {}; // timing mode: after each chunk's refinement / increments
   cudaEvent_t ev[14] = {};
   double phase_ms[6] = {0, 0, 0, 0, 0, 0};
   double kphase_ms[QOC_N_PHASES] = {};
@@ -249,8 +256,10 @@ qoc_status enqueue_blocked(qoc_problem* p, int order, double* out_dev) {
   // ---- chains ----
   QOC_TRY(cudaStreamWaitEvent(cs, p->fork, 0));
   if (p->timing) cudaEventRecord(p->ev[10], cs);
-  QOC_TRY(launch_block_delta(p->D, p->dstride, N, J, bs, 0, mixed, p->Mf, p->mstride, cs, p->ws[1]));
-  QOC_TRY(launch_bsweep(chain_sweep_args(p, 0), mixed, cs));
+  if (!p->piped) {   // else already enqueued chunk by chunk behind the refinement
+    QOC_TRY(launch_block_delta(p->D, p->dstride, N, J, bs, 0, mixed, p->Mf, p->mstride, cs, p->ws[1]));
+    QOC_TRY(launch_bsweep(chain_sweep_args(p, 0), mixed, cs));
+  }
   QOC_TRY(launch_block_fill(p->D, p->dstride, N, J, bs, 0, mixed, p->Xa, p->a_hat, cs));
   QOC_TRY(launch_terminal(p->f, J, p->a_hat, mixed, p->beta, N, cexpi_h(thetaJ), p->w_f, p->w_t,
                           p->lamJ, p->scal + 0, nullptr, cs));
@@ -322,6 +331,63 @@ qoc_status enqueue_blocked(qoc_problem* p, int order, double* out_dev) {
   return QOC_OK;
 }
 
+// Chunks of the forward pipeline for an evaluation of this order (0: none).
+// Time-blocked evaluations with gradients and the refined eigensolver only;
+// the built-in choice pipelines horizons of 1024 steps or more in 4 chunks.
+int pipeline_chunks(const qoc_problem* p, int order) {
+  if (order < 1 || p->bs <= 1 || p->eig_method != QOC_EIG_REFINED) return 0;
+  const int nblk = (p->J + p->bs - 1) / p->bs;
+  int c = p->pipeline;
+  if (c < 0) c = p->J >= 1024 ? 4 : 0;
+  if (c > qoc_problem::kMaxChunks) c = qoc_problem::kMaxChunks;
+  if (c > nblk) c = nblk;
+  return c >= 2 ? c : 0;
+}
+
+// The eigendecompositions, increments D_j and the forward state chain of a
+// pipelined evaluation.  The binary32 start runs over all steps at once (it
+// needs every step to fill the GPU); the refinement and the increments then
+// run in chunks of whole blocks on the main stream, and the chain stream
+// takes each chunk's forward block products and state-chain blocks as soon
+// as that chunk's increments exist, resuming from the block-start state the
+// previous chunk left: bit for bit the unchunked evaluation, with the chain's
+// latency hidden behind the refinement of the later chunks.
+qoc_status enqueue_pipelined_start(qoc_problem* p) {
+  cudaStream_t st = p->stream, cs = p->side;
+  const int N = p->N, J = p->J, bs = p->bs, C = p->piped;
+  const int nblk = (J + bs - 1) / bs;
+  const int mixed = p->precision == QOC_MIXED_FP32 ? 1 : 0;
+  const size_t NN = (size_t)N * N;
+  unsigned int* stats = p->timing ? p->eigstats : nullptr;
+  QOC_TRY(launch_eig(p->H0, p->M, p->f, N, J, p->W, p->eig, p->status, EIG_REFINED, p->refine_sweeps,
+                     p->angle_tol, st, p->ws[0], p->timing ? p->ev[8] : nullptr, stats, eig_finish_tol(p),
+                     EIG_PHASE_START));
+  for (int c = 0; c < C; ++c) {
+    const int b0 = (int)((long long)c * nblk / C), b1 = (int)((long long)(c + 1) * nblk / C);
+    const int j0 = b0 * bs, j1 = b1 * bs < J ? b1 * bs : J, jn = j1 - j0;
+    QOC_TRY(launch_eig(p->H0, p->M, p->f + j0, N, jn, p->W + j0 * NN, p->eig + (size_t)j0 * N, p->status,
+                       EIG_REFINED, p->refine_sweeps, p->angle_tol, st, p->ws[0], nullptr, stats,
+                       eig_finish_tol(p), EIG_PHASE_REFINE));
+    if (p->timing) cudaEventRecord(p->evp[2 * c], st);
+    unsigned char* Dc = static_cast<unsigned char*>(p->D) + (size_t)j0 * p->dstride;
+    QOC_TRY(launch_prep(p->W + j0 * NN, p->eig + (size_t)j0 * N, p->M, N, jn, p->dt, p->mshift, Dc,
+                        p->dstride, mixed ? 0 : 1, PREP_D, p->Ptil, p->Xp, nullptr, p->status, st, p->ws[0]));
+    if (p->timing) cudaEventRecord(p->evp[2 * c + 1], st);
+    QOC_TRY(cudaEventRecord(p->ev_chunk[c], st));
+    QOC_TRY(cudaStreamWaitEvent(cs, p->ev_chunk[c], 0));
+    QOC_TRY(launch_block_delta(Dc, p->dstride, N, jn, bs, 0, mixed,
+                               static_cast<unsigned char*>(p->Mf) + (size_t)b0 * p->mstride, p->mstride,
+                               cs, p->ws[1]));
+    BSweepArgs a = chain_sweep_args(p, 0);
+    a.blk0 = b0;
+    a.blk1 = b1;
+    a.resume = c > 0;
+    QOC_TRY(launch_bsweep(a, mixed, cs));
+  }
+  if (p->timing) cudaEventRecord(p->ev[1], st);
+  return QOC_OK;
+}
+
 // Enqueue one evaluation.  order 0: J; 1: J + grad; 2: J + grad + Hess.
 // theta_dev: K doubles on the device.  out_dev: 1 + K (+ K*K) doubles.
 qoc_status enqueue_eval(qoc_problem* p, const double* theta_dev, int order, double* out_dev) {
@@ -336,13 +402,19 @@ qoc_status enqueue_eval(qoc_problem* p, const double* theta_dev, int order, doub
     cudaEventRecord(p->ev[7], st);
     QOC_TRY(cudaMemsetAsync(p->eigstats, 0, 4 * sizeof(unsigned int), st));
   }
-  QOC_TRY(launch_eig(p->H0, p->M, p->f, N, J, p->W, p->eig, p->status,
-                     p->eig_method == QOC_EIG_JACOBI_FP64 ? EIG_JACOBI_FP64 : EIG_REFINED,
-                     p->refine_sweeps, p->angle_tol, st, p->ws[0], p->timing ? p->ev[8] : nullptr,
-                     p->timing ? p->eigstats : nullptr, eig_finish_tol(p)));
-  if (p->timing) cudaEventRecord(p->ev[1], st);
-  QOC_TRY(launch_prep(p->W, p->eig, p->M, N, J, p->dt, p->mshift, p->D, p->dstride, d_fp64, PREP_D,
-                      p->Ptil, p->Xp, nullptr, p->status, st, p->ws[0]));
+  p->piped = pipeline_chunks(p, order);
+  if (p->piped) {
+    const qoc_status ps = enqueue_pipelined_start(p);
+    if (ps != QOC_OK) return ps;
+  } else {
+    QOC_TRY(launch_eig(p->H0, p->M, p->f, N, J, p->W, p->eig, p->status,
+                       p->eig_method == QOC_EIG_JACOBI_FP64 ? EIG_JACOBI_FP64 : EIG_REFINED,
+                       p->refine_sweeps, p->angle_tol, st, p->ws[0], p->timing ? p->ev[8] : nullptr,
+                       p->timing ? p->eigstats : nullptr, eig_finish_tol(p)));
+    if (p->timing) cudaEventRecord(p->ev[1], st);
+    QOC_TRY(launch_prep(p->W, p->eig, p->M, N, J, p->dt, p->mshift, p->D, p->dstride, d_fp64, PREP_D,
+                        p->Ptil, p->Xp, nullptr, p->status, st, p->ws[0]));
+  }
   if (p->timing) cudaEventRecord(p->ev[2], st);
   if (p->bs > 1) return enqueue_blocked(p, order, out_dev);
   p->sched = 0;
@@ -407,6 +479,17 @@ void collect_timing(qoc_problem* p) {
   double* k = p->kphase_ms;
   k[9] = el(0, 6);
   k[0] = el(0, 7); k[1] = el(7, 8); k[2] = el(8, 1); k[3] = el(1, 2); k[8] = el(5, 6);
+  if (p->piped) {   // refinement and increments interleaved by chunk on the main stream
+    auto elp = [&](cudaEvent_t a, cudaEvent_t b) {
+      float ms = 0;
+      return cudaEventElapsedTime(&ms, a, b) == cudaSuccess ? (double)ms : 0.0;
+    };
+    k[2] = k[3] = 0;
+    for (int c = 0; c < p->piped; ++c) {
+      k[2] += elp(c ? p->evp[2 * c - 1] : p->ev[8], p->evp[2 * c]);
+      k[3] += elp(p->evp[2 * c], p->evp[2 * c + 1]);
+    }
+  }
   if (p->sched == 1) {
     k[4] = el(2, 3); k[5] = el(10, 11); k[6] = el(3, 4); k[7] = el(12, 13);
     const double ph[6] = {el(0, 1), el(1, 3), el(10, 11), el(3, 4), el(12, 13), el(5, 6)};
@@ -483,6 +566,10 @@ void qoc_destroy_problem(qoc_problem* p) {
   if (p->hbuf) cudaFreeHost(p->hbuf);
   if (p->hstatus) cudaFreeHost(p->hstatus);
   for (auto& e : p->ev)
+    if (e) cudaEventDestroy(e);
+  for (auto& e : p->ev_chunk)
+    if (e) cudaEventDestroy(e);
+  for (auto& e : p->evp)
     if (e) cudaEventDestroy(e);
   for (cudaStream_t* sp : {&p->side, &p->pstream})
     if (*sp) {
@@ -563,6 +650,10 @@ qoc_status qoc_create_problem(int N, const double* H0, const double* M, const do
   }
   for (auto& ev : p->ev)
     if ((e = cudaEventCreate(&ev)) != cudaSuccess) return fail(e);
+  for (auto& ev : p->evp)
+    if ((e = cudaEventCreate(&ev)) != cudaSuccess) return fail(e);
+  for (auto& ev : p->ev_chunk)
+    if ((e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming)) != cudaSuccess) return fail(e);
   {
     int lo = 0, hi = 0;
     cudaDeviceGetStreamPriorityRange(&lo, &hi);
@@ -733,6 +824,12 @@ qoc_status qoc_set_panel_columns(qoc_problem* p, int kc) {
   if (!p || kc < 0 || kc > 4) return QOC_EINVAL;
   if (kc > 0 && 32 * ((p->N + 7) / 8) * kc > 1024) return QOC_EUNSUPPORTED;
   p->kc = kc;
+  return QOC_OK;
+}
+
+qoc_status qoc_set_pipeline(qoc_problem* p, int chunks) {
+  if (!p || chunks < -1 || chunks > qoc_problem::kMaxChunks) return QOC_EINVAL;
+  p->pipeline = chunks;
   return QOC_OK;
 }
 

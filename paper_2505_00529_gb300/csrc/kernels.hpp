@@ -105,11 +105,16 @@ constexpr double TAU_DD2 = 1e-3;
 // finish_tol > 0: the refinement ends after the first update with no cluster
 // pairs whose |I - W^T W|_F and largest correction are <= finish_tol (W then
 // accurate to about finish_tol^2); 0: refinement to the binary64 floor.
+// the parts of a refined eigendecomposition a launch_eig call enqueues: the
+// binary32 start, the binary64 refinement (which reads the start from W), or
+// both; the refinement of steps [j0, j1) alone takes f + j0, W + j0 N^2,
+// eig + j0 N and J = j1 - j0
+enum { EIG_PHASE_START = 1, EIG_PHASE_REFINE = 2, EIG_PHASE_ALL = 3 };
 cudaError_t launch_eig(const double* H0, const double* M, const double* f, int N, int J,
                        double* W, double* eig, int* status, int method, int refine_sweeps,
                        double angle_tol, cudaStream_t st, const StepSpace& ws,
                        cudaEvent_t mid = nullptr, unsigned int* stats = nullptr,
-                       double finish_tol = 0.0);
+                       double finish_tol = 0.0, int phases = EIG_PHASE_ALL);
 size_t eig_step_bytes(int N);   // largest per-matrix storage of the eigensolver kernels
 
 size_t prep_smem_bytes(int N);
@@ -162,6 +167,14 @@ struct BSweepArgs {
   int xblk_pairs;
   void* states;          // vector chains: final state row (J forward, 0 backward), or null
   int* status;
+  // Block range [blk0, blk1) of this launch (blk1 = 0: to the last block);
+  // final_out and states are written only by the launch that ends at the last
+  // block.  resume != 0: start from the block-start state Xblk[blk0] (exact:
+  // binary64 states, or binary32 pairs with xblk_pairs) instead of init; a
+  // launch that stops before the last block leaves its end state in
+  // Xblk[blk1] for the next one.
+  int blk0, blk1;
+  int resume;
 };
 cudaError_t launch_bsweep(const BSweepArgs& a, int mixed, cudaStream_t st);
 // which sweep kernel launch_bsweep takes for `a`: 0 the general one, 1 or 2

@@ -318,6 +318,7 @@ __device__ __forceinline__ void bsweep_body(const BSweepArgs& a, const int cta, 
   using R = typename SweepT<MIX>::R;
   const int N = a.N, kc = a.kc, J = a.J, bs = a.bs;
   const int nblk = (J + bs - 1) / bs;
+  const int b0 = a.blk0, b1 = a.blk1 > 0 ? a.blk1 : nblk;   // this launch's blocks
   constexpr int RPW = 32 / RS;
   const int WPC = (N + RPW - 1) / RPW;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -341,7 +342,7 @@ __device__ __forceinline__ void bsweep_body(const BSweepArgs& a, const int cta, 
 
   const unsigned char* gB = reinterpret_cast<const unsigned char*>(a.Brow);
   auto issue = [&](int it) {
-    const int s = it % nstage;
+    const int s = (it - b0) % nstage;
     const int t0 = it * bs, bl = min(bs, J - t0);
     const int row0 = a.backward ? J - t0 - bl : t0;     // rows of this block, ascending in memory
     const uint32_t bb = a.Brow ? browb * bl : 0u;
@@ -361,7 +362,7 @@ __device__ __forceinline__ void bsweep_body(const BSweepArgs& a, const int cta, 
     mbar_fence_init();
   }
   double2 x0 = make_double2(0.0, 0.0);
-  if (active && a.init) {
+  if (active && a.init && !a.resume) {
     x0 = a.init[(size_t)(col0 + l) * N + i];
     x0.x *= a.init_scale;
     x0.y *= a.init_scale;
@@ -372,6 +373,16 @@ __device__ __forceinline__ void bsweep_body(const BSweepArgs& a, const int cta, 
     lx = (float)(x0.x - (double)hx);
     ly = (float)(x0.y - (double)hy);
   }
+  if (active && a.resume) {   // the state a previous launch left at block b0
+    const size_t e = ((size_t)b0 * a.K + col0 + l) * N + i;
+    if (a.xblk_pairs) {
+      const float4 v = reinterpret_cast<const float4*>(a.Xblk)[e];
+      hx = (R)v.x; hy = (R)v.y; lx = v.z; ly = v.w;
+    } else {
+      const TD v = reinterpret_cast<const TD*>(a.Xblk)[e];
+      hx = v.x; hy = v.y;
+    }
+  }
   if (owner) {
     TD v;
     v.x = hx; v.y = hy;
@@ -379,14 +390,14 @@ __device__ __forceinline__ void bsweep_body(const BSweepArgs& a, const int cta, 
   }
   __syncthreads();
   if (threadIdx.x == 0 && ring_mode) {
-    const int pre = min(nstage - 1, nblk);
-    for (int it = 0; it < pre; ++it) issue(it);
+    const int pre = min(nstage - 1, b1 - b0);
+    for (int it = b0; it < b0 + pre; ++it) issue(it);
   }
-  int cur = 0, it = 0, s = 0;
+  int cur = 0, it = b0, s = 0;
   uint32_t par = 0;
-  for (; it < nblk; ++it) {
+  for (; it < b1; ++it) {
     const int t0 = it * bs, bl = min(bs, J - t0);
-    if (threadIdx.x == 0 && ring_mode && it + nstage - 1 < nblk) {
+    if (threadIdx.x == 0 && ring_mode && it + nstage - 1 < b1) {
       fence_proxy_async_smem();
       issue(it + nstage - 1);
     }
@@ -479,8 +490,21 @@ __device__ __forceinline__ void bsweep_body(const BSweepArgs& a, const int cta, 
   if (abort_flag) {
     if (threadIdx.x == 0) {
       raise_status(a.status, DEV_TIMEOUT);
-      for (int k = it; k < min(nblk, it + nstage - 1); ++k)
-        mbar_wait_bounded(&bar[k % nstage], (uint32_t)((k / nstage) & 1), 100000000ull);
+      for (int k = it; k < min(b1, it + nstage - 1); ++k)
+        mbar_wait_bounded(&bar[(k - b0) % nstage], (uint32_t)(((k - b0) / nstage) & 1), 100000000ull);
+    }
+    return;
+  }
+  if (b1 < nblk) {   // a chunk: hand the end state to the launch that resumes at b1
+    if (owner) {
+      const size_t e = ((size_t)b1 * a.K + col0 + l) * N + i;
+      if (a.xblk_pairs) {
+        reinterpret_cast<float4*>(a.Xblk)[e] = make_float4((float)hx, (float)hy, lx, ly);
+      } else {
+        TD v;
+        v.x = hx; v.y = hy;
+        reinterpret_cast<TD*>(a.Xblk)[e] = v;
+      }
     }
     return;
   }
@@ -564,6 +588,8 @@ __device__ __forceinline__ void bsweep_fast_body(const BSweepArgs& a, const int 
   const bool bwd = a.backward != 0, has_q = a.Q != nullptr, has_b = a.Brow != nullptr;
   const bool pairs = a.xblk_pairs != 0;
   const int nblk = (J + bs - 1) / bs;
+  const int b0 = a.blk0, nloc = (a.blk1 > 0 ? a.blk1 : nblk) - b0;   // blocks b0 .. b0 + nloc - 1
+  const bool last = b0 + nloc == nblk;
   const int WPC = (N + RPW - 1) / RPW;
   const int ncw = WPC * kc;                       // consumer warps
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -597,9 +623,10 @@ __device__ __forceinline__ void bsweep_fast_body(const BSweepArgs& a, const int 
     const unsigned char* gB = reinterpret_cast<const unsigned char*>(a.Brow);
     const size_t ms = a.mstride, qs = a.qstride;
     int s = 0, round = 0, issued = 0;
-    for (int it = 0; it < nblk; ++it) {
+    for (int li = 0; li < nloc; ++li) {
+      const int it = b0 + li;
       if (*abort_flag) break;
-      if (it >= nstage && !mbar_wait_or_flag(&empty[s], (uint32_t)((round - 1) & 1), abort_flag)) {
+      if (li >= nstage && !mbar_wait_or_flag(&empty[s], (uint32_t)((round - 1) & 1), abort_flag)) {
         *abort_flag = 1;
         break;
       }
@@ -613,7 +640,7 @@ __device__ __forceinline__ void bsweep_fast_body(const BSweepArgs& a, const int 
       bulk_g2s(dst, gM + (size_t)it * ms, mbytes, &full[s]);
       if (qb) bulk_g2s(dst + mbytes, gQ + (size_t)it * qs, qb, &full[s]);
       if (bb) bulk_g2s(dst + mbytes + qbytes, gB + (size_t)row0 * browb, bb, &full[s]);
-      issued = it + 1;
+      issued = li + 1;
       if (++s == nstage) { s = 0; ++round; }
     }
     // the copies issued last (each the latest phase of its slot) have landed
@@ -637,7 +664,7 @@ __device__ __forceinline__ void bsweep_fast_body(const BSweepArgs& a, const int 
   const float4* Xr = reinterpret_cast<const float4*>(Xl + rsub * XS);
 
   double2 x0 = make_double2(0.0, 0.0);
-  if (active && a.init) {
+  if (active && a.init && !a.resume) {
     x0 = a.init[(size_t)col * N + i];
     x0.x *= a.init_scale;
     x0.y *= a.init_scale;
@@ -645,8 +672,12 @@ __device__ __forceinline__ void bsweep_fast_body(const BSweepArgs& a, const int 
   float hx = (float)x0.x, hy = (float)x0.y;
   float lx = (float)(x0.x - (double)hx), ly = (float)(x0.y - (double)hy);
   const size_t xb_stride = (size_t)K * N;
-  float4* xb4 = reinterpret_cast<float4*>(a.Xblk) + (size_t)col * N + i;
-  float2* xb2 = reinterpret_cast<float2*>(a.Xblk) + (size_t)col * N + i;
+  float4* xb4 = reinterpret_cast<float4*>(a.Xblk) + ((size_t)b0 * K + col) * N + i;
+  float2* xb2 = reinterpret_cast<float2*>(a.Xblk) + ((size_t)b0 * K + col) * N + i;
+  if (active && a.resume && pairs) {   // the state a previous launch left at block b0
+    const float4 v = *xb4;
+    hx = v.x; hy = v.y; lx = v.z; ly = v.w;
+  }
   if (owner) {
     Xl[xw] = make_float2(hx, hy);
     if (pairs) *xb4 = make_float4(hx, hy, lx, ly);
@@ -667,9 +698,9 @@ __device__ __forceinline__ void bsweep_fast_body(const BSweepArgs& a, const int 
     bad = true;
     *abort_flag = 1;
   }
-  fast_load<RS, NQ, NF>(ra, ring, N, mbytes, qbytes, has_q, min(bs, J), bwd, Kp, rsub, i, col, kq,
-                        active);
-  if (nblk > 1 &&
+  fast_load<RS, NQ, NF>(ra, ring, N, mbytes, qbytes, has_q, min(bs, J - b0 * bs), bwd, Kp, rsub, i, col,
+                        kq, active);
+  if (nloc > 1 &&
       !mbar_wait_or_flag(&full[1 % nstage], (uint32_t)((1 / nstage) & 1), abort_flag)) {
     bad = true;
     *abort_flag = 1;
@@ -684,18 +715,19 @@ __device__ __forceinline__ void bsweep_fast_body(const BSweepArgs& a, const int 
     int s1 = s + 1;
     uint32_t par1 = par;
     if (s1 == nstage) { s1 = 0; par1 ^= 1u; }
-    const bool more = it + 1 < nblk;
+    const bool more = it + 1 < nloc;            // it: the block's index within this launch
+    const bool next_start = b0 + it + 1 < nblk;  // a block follows (here or in a later launch)
     // release this block's slot: its entries were loaded before the last barrier
     if (lane == 0) mbar_arrive(&empty[s]);
     const float4* xp = Xr + cur * (xbuf / 2);
     float4 xv[NQ / 2];
 #pragma unroll
     for (int k = 0; k < NQ / 2; ++k) xv[k] = xp[k];
-    const bool look = it + 2 < nblk;
+    const bool look = it + 2 < nloc;
     const uint32_t rdy = look ? mbar_try_wait(&full[s2], par2) : 1u;
     // the next block (independent of X, landed as tested one step earlier)
     if (more) {
-      const int t1 = (it + 1) * bs;
+      const int t1 = (b0 + it + 1) * bs;
       fast_load<RS, NQ, NF>(nx, ring + (size_t)s1 * stage, N, mbytes, qbytes, has_q, min(bs, J - t1),
                             bwd, Kp, rsub, i, col, kq, active);
     }
@@ -727,7 +759,7 @@ __device__ __forceinline__ void bsweep_fast_body(const BSweepArgs& a, const int 
       two_sum(hx, __fadd_rn(sx, lx), hx, lx);
       two_sum(hy, __fadd_rn(sy, ly), hy, ly);
       Xl[(cur ^ 1) * xbuf + xw] = make_float2(hx, hy);
-      if (more) {
+      if (next_start) {
         xb4 += xb_stride;
         xb2 += xb_stride;
         if (pairs) *xb4 = make_float4(hx, hy, lx, ly);
@@ -746,16 +778,17 @@ __device__ __forceinline__ void bsweep_fast_body(const BSweepArgs& a, const int 
     return !stop;
   };
   int it = 0;
-  for (; ok && it + 1 < nblk; it += 2) {
+  for (; ok && it + 1 < nloc; it += 2) {
     ok = step(it, ra, rb2);
     if (ok) ok = step(it + 1, rb2, ra);
   }
-  if (ok && it < nblk) ok = step(it, ra, rb2);
+  if (ok && it < nloc) ok = step(it, ra, rb2);
   if (!ok) {
     if (threadIdx.x == 0) raise_status(a.status, DEV_TIMEOUT);
     *abort_flag = 1;   // stops the producer
     return;
   }
+  if (!last) return;   // a chunk: its end state is in Xblk[b0 + nloc]
   const double fx = (double)hx + (double)lx, fy = (double)hy + (double)ly;
   if (owner) {
     if (a.final_out) a.final_out[(size_t)col * N + i] = make_double2(fx, fy);

@@ -1,0 +1,58 @@
+"""The forward pipeline (refinement and increments in chunks, the state chain
+following chunk by chunk from the stored block-start states) reorders work
+only: every result must equal the unchunked schedule's bit for bit, for each
+sweep variant (binary32 warp-specialised at N <= 32 and N <= 64, the general
+sweep above, binary64), ragged horizons and every chunk count."""
+import numpy as np
+import pytest
+
+from paper_2505_00529_gb300 import _lib, inputs
+
+pytestmark = pytest.mark.gpu
+
+CASES = [  # (N, K, J), block steps, chunks
+    ((5, 4, 203), 4, 3),
+    ((32, 9, 400), 4, 8),
+    ((40, 6, 333), 3, 2),
+    ((72, 5, 130), 2, 4),
+    ((16, 7, 64), 8, 8),      # one block per chunk
+]
+
+
+def _run(P, theta, chunks):
+    _lib.qoc_set_pipeline(P.handle, chunks)
+    J, g, H = P.eval_grad_hess(theta)
+    states = P.buffer(_lib.QOC_BUF_STATE)
+    costates = P.buffer(_lib.QOC_BUF_COSTATE)
+    J1, g1 = P.eval_grad(theta)
+    return J, g, H, states, costates, J1, g1
+
+
+@pytest.mark.parametrize("case", CASES, ids=lambda c: "N%d_K%d_J%d_b%d_c%d" % (*c[0], c[1], c[2]))
+@pytest.mark.parametrize("precision", [_lib.QOC_FP64, _lib.QOC_MIXED_FP32], ids=["fp64", "mixed"])
+def test_pipelined_forward_chain_is_bit_identical(case, precision):
+    (N, K, J), bs, chunks = case
+    prob = inputs.small_problem(N=N, K=K, J=J, seed=300 + N + J, dt=0.05, basis="random")
+    theta = inputs.eval_theta(K, 11, 0.7)
+    with _lib.Problem(prob, precision=precision, block_steps=bs) as P:
+        ref = _run(P, theta, 0)
+        got = _run(P, theta, chunks)
+        again = _run(P, theta, 0)
+    for a, b, c in zip(ref, got, again):
+        np.testing.assert_array_equal(np.asarray(b), np.asarray(a))
+        np.testing.assert_array_equal(np.asarray(c), np.asarray(a))
+
+
+def test_pipeline_timing_and_range():
+    prob = inputs.small_problem(N=8, K=4, J=256, seed=9, dt=0.05, basis="random")
+    theta = inputs.eval_theta(4, 2, 0.5)
+    with _lib.Problem(prob, precision=_lib.QOC_MIXED_FP32, block_steps=4) as P:
+        _lib.qoc_enable_timing(P.handle, 1)
+        _lib.qoc_set_pipeline(P.handle, 4)
+        P.eval_grad_hess(theta)
+        ph = _lib.qoc_get_phase_times(P.handle)
+        assert ph["eig_refine"] > 0 and ph["prep_D"] > 0 and ph["total"] > 0
+        for bad in (-2, 9):
+            with pytest.raises(_lib.QocError) as e:
+                _lib.qoc_set_pipeline(P.handle, bad)
+            assert e.value.status == _lib.QOC_EINVAL
