@@ -131,7 +131,7 @@ qoc_status qoc_set_eig_method(qoc_problem* p, int method);
  * would raise the error estimate above 1e-6. */
 qoc_status qoc_set_block_steps(qoc_problem* p, int steps);
 
-/* Forward pipeline of a time-blocked gradient or Hessian evaluation (no
+/* Forward pipeline of a time-blocked evaluation (no
  * counterpart in the paper; a reordering of Alg. 2's first loops that
  * changes no result): after the binary32 eigensolver start over all steps,
  * the binary64 refinement and the increments D_j run in `chunks` chunks of

@@ -240,8 +240,13 @@ qoc_status enqueue_blocked(qoc_problem* p, int order, double* out_dev) {
   const void* Bsrc = mixed ? static_cast<const void*>(p->Bf) : static_cast<const void*>(p->B);
   if (order == 0) {
     p->sched = 0;
-    QOC_TRY(launch_block_delta(p->D, p->dstride, N, J, bs, 0, mixed, p->Mf, p->mstride, st, p->ws[0]));
-    QOC_TRY(launch_bsweep(chain_sweep_args(p, 0), mixed, st));
+    if (p->piped) {   // the chain ran chunk by chunk on the chain stream
+      QOC_TRY(cudaEventRecord(p->join, p->side));
+      QOC_TRY(cudaStreamWaitEvent(st, p->join, 0));
+    } else {
+      QOC_TRY(launch_block_delta(p->D, p->dstride, N, J, bs, 0, mixed, p->Mf, p->mstride, st, p->ws[0]));
+      QOC_TRY(launch_bsweep(chain_sweep_args(p, 0), mixed, st));
+    }
     QOC_TRY(launch_block_fill(p->D, p->dstride, N, J, bs, 0, mixed, p->Xa, p->a_hat, st));
     QOC_TRY(launch_terminal(p->f, J, p->a_hat, mixed, p->beta, N, cexpi_h(thetaJ), p->w_f, p->w_t,
                             p->lamJ, p->scal + 0, nullptr, st));
@@ -331,11 +336,11 @@ qoc_status enqueue_blocked(qoc_problem* p, int order, double* out_dev) {
   return QOC_OK;
 }
 
-// Chunks of the forward pipeline for an evaluation of this order (0: none).
-// Time-blocked evaluations with gradients and the refined eigensolver only;
-// the built-in choice pipelines horizons of 1024 steps or more in 4 chunks.
-int pipeline_chunks(const qoc_problem* p, int order) {
-  if (order < 1 || p->bs <= 1 || p->eig_method != QOC_EIG_REFINED) return 0;
+// Chunks of the forward pipeline for an evaluation (0: none).  Time-blocked
+// evaluations with the refined eigensolver only; the built-in choice
+// pipelines horizons of 1024 steps or more in 4 chunks.
+int pipeline_chunks(const qoc_problem* p, int /*order*/) {
+  if (p->bs <= 1 || p->eig_method != QOC_EIG_REFINED) return 0;
   const int nblk = (p->J + p->bs - 1) / p->bs;
   int c = p->pipeline;
   if (c < 0) c = p->J >= 1024 ? 4 : 0;

@@ -1,6 +1,7 @@
 """The forward pipeline (refinement and increments in chunks, the state chain
 following chunk by chunk from the stored block-start states) reorders work
-only: every result must equal the unchunked schedule's bit for bit, for each
+only: every result (J alone, J and the gradient, J, gradient and Hessian,
+the stored states) must equal the unchunked schedule's bit for bit, for each
 sweep variant (binary32 warp-specialised at N <= 32 and N <= 64, the general
 sweep above, binary64), ragged horizons and every chunk count."""
 import numpy as np
@@ -25,7 +26,8 @@ def _run(P, theta, chunks):
     states = P.buffer(_lib.QOC_BUF_STATE)
     costates = P.buffer(_lib.QOC_BUF_COSTATE)
     J1, g1 = P.eval_grad(theta)
-    return J, g, H, states, costates, J1, g1
+    J0 = P.eval_J(theta)
+    return J, g, H, states, costates, J1, g1, J0
 
 
 @pytest.mark.parametrize("case", CASES, ids=lambda c: "N%d_K%d_J%d_b%d_c%d" % (*c[0], c[1], c[2]))
