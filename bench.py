@@ -233,6 +233,7 @@ def run_ours(args):
         P = q.Problem(prob, precision=precision, cuda_stream=stream.cuda_stream)
         if precision in tuned:
             autotune.apply(P, tuned[precision])
+        q.qoc_set_pipeline(P.handle, args.pipeline)
         if timing:
             q.qoc_enable_timing(P.handle, True)
         th = torch.tensor(theta, dtype=torch.float64, device=dev)
@@ -360,6 +361,7 @@ def run_ours(args):
                 "data": "synthetic",
                 "config": dict(WORKLOAD, precision=args.precision, l2="flushed between timed steps",
                                parallelism=f"replicas x{world}" if world > 1 else "single problem",
+                               pipeline_chunks=args.pipeline if args.pipeline >= 0 else "library choice (4)",
                                launch=({"block_steps": tuned[prec]["block_steps"],
                                         "panel_columns": tuned[prec]["panel_columns"],
                                         "autotune_table_ms": tuned[prec]["table"]}
@@ -865,6 +867,8 @@ def main():
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-tr", action="store_true")
     ap.add_argument("--no-autotune", action="store_true", help="library default launch shapes")
+    ap.add_argument("--pipeline", type=int, default=-1,
+                    help="forward-pipeline chunks of the timed problem (0 off, -1 library choice)")
     ap.add_argument("--no-extra", action="store_true", help="skip the other workloads")
     ap.add_argument("--fp64-peak", action="store_true", help="measure the binary64 peak and exit")
     ap.add_argument("--profile", action="store_true", help="evaluations of the bench workload only (for ncu)")
