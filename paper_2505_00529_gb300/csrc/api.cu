@@ -55,6 +55,12 @@ struct qoc_problem {
   static constexpr int kMaxChunks = 8;
   int pipeline = -1;                    // chunks (qoc_set_pipeline); -1 the built-in choice
   int piped = 0;                        // chunks of the last evaluation (0: not pipelined)
+  // the next time-blocked evaluation with gradients is at the theta of the
+  // evaluation just enqueued, whose samples f, eigendecompositions,
+  // increments, forward block products and state chain it reuses (set by the
+  // trust region after an accepted step; consumed by that evaluation)
+  int reuse_fwd = 0;
+  int fwd_reused = 0;                   // the last evaluation did
   cudaEvent_t ev_chunk[kMaxChunks] = {};
   cudaEvent_t evp[2 * kMaxChunks] = {}; // timing mode: after each chunk's refinement / increments
   cudaEvent_t ev[14] = {};
@@ -261,7 +267,7 @@ qoc_status enqueue_blocked(qoc_problem* p, int order, double* out_dev) {
   // ---- chains ----
   QOC_TRY(cudaStreamWaitEvent(cs, p->fork, 0));
   if (p->timing) cudaEventRecord(p->ev[10], cs);
-  if (!p->piped) {   // else already enqueued chunk by chunk behind the refinement
+  if (!p->piped && !p->fwd_reused) {   // else enqueued chunk by chunk behind the refinement, or reused
     QOC_TRY(launch_block_delta(p->D, p->dstride, N, J, bs, 0, mixed, p->Mf, p->mstride, cs, p->ws[1]));
     QOC_TRY(launch_bsweep(chain_sweep_args(p, 0), mixed, cs));
   }
@@ -401,6 +407,14 @@ qoc_status enqueue_eval(qoc_problem* p, const double* theta_dev, int order, doub
   const int mixed = p->precision == QOC_MIXED_FP32 ? 1 : 0;
   const int d_fp64 = mixed ? 0 : 1;
   if (p->timing) cudaEventRecord(p->ev[0], st);
+  p->fwd_reused = p->reuse_fwd && p->bs > 1 && order >= 1;
+  p->reuse_fwd = 0;
+  if (p->fwd_reused) {   // f, W, lambda, D, the forward products and chain are current
+    p->piped = 0;
+    if (p->timing)
+      for (int k : {7, 8, 1, 2}) cudaEventRecord(p->ev[k], st);
+    return enqueue_blocked(p, order, out_dev);
+  }
   // theta_dev == nullptr: the samples f are already in p->f (a model evaluation)
   if (theta_dev) QOC_TRY(launch_control(p->B, p->Kp, theta_dev, J, K, p->f, st));
   if (p->timing) {
@@ -1102,6 +1116,7 @@ qoc_status qoc_trust_region_solve(qoc_problem* p, const double* theta0, const qo
       radius = std::fmin(2.0 * radius, opt->radius_max);
     if (rho > opt->eta) {
       QOC_TRY(cudaMemcpyAsync(p->theta, p->theta_trial, 8 * (size_t)K, cudaMemcpyDeviceToDevice, st));
+      p->reuse_fwd = trial_ok;   // the trial's cost evaluation left its forward part in place
       s = eval_gh();
       if (s != QOC_OK) return s;
       report->n_eval_gh++;

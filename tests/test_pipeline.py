@@ -58,3 +58,23 @@ def test_pipeline_timing_and_range():
             with pytest.raises(_lib.QocError) as e:
                 _lib.qoc_set_pipeline(P.handle, bad)
             assert e.value.status == _lib.QOC_EINVAL
+
+
+@pytest.mark.parametrize("precision", [_lib.QOC_FP64, _lib.QOC_MIXED_FP32], ids=["fp64", "mixed"])
+def test_trust_region_reuses_the_trial_forward_part_exactly(precision):
+    """After an accepted step the trust region evaluates the gradient and
+    Hessian at the trial point reusing the trial's control samples,
+    eigendecompositions, increments and forward chain: the J it reports must
+    be a fresh evaluation's at the returned point bit for bit (the gradient
+    norm to its summation order)."""
+    prob = inputs.small_problem(N=12, K=6, J=240, seed=41, dt=0.05, basis="sine_cosine")
+    with _lib.Problem(prob, precision=precision) as P:
+        accepted = 0
+        for iters in (1, 2, 4, 8):
+            th, info = P.trust_region_solve(np.zeros(6), gtol=0.0, xtol=0.0, max_iter=iters)
+            J, g, H = P.eval_grad_hess(th)
+            assert info["J"] == J
+            gn = float(np.linalg.norm(np.asarray(g)))
+            assert abs(info["grad_norm"] - gn) <= 1e-14 * max(gn, 1e-300)
+            accepted = max(accepted, info["n_eval_gh"] - 1)
+        assert accepted >= 2   # the reused evaluations were exercised
