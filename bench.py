@@ -361,7 +361,7 @@ def run_ours(args):
                 "data": "synthetic",
                 "config": dict(WORKLOAD, precision=args.precision, l2="flushed between timed steps",
                                parallelism=f"replicas x{world}" if world > 1 else "single problem",
-                               pipeline_chunks=args.pipeline if args.pipeline >= 0 else "library choice (4)",
+                               pipeline_chunks=args.pipeline if args.pipeline >= 0 else "library choice (off)",
                                launch=({"block_steps": tuned[prec]["block_steps"],
                                         "panel_columns": tuned[prec]["panel_columns"],
                                         "autotune_table_ms": tuned[prec]["table"]}

@@ -140,7 +140,10 @@ qoc_status qoc_set_block_steps(qoc_problem* p, int steps);
  * previous one stored, so that its dependent steps overlap the refinement of
  * the later chunks.  Results are bit-identical to the unchunked schedule.
  * chunks: 0 or 1 off, 2..8 the chunk count (at most one block each), -1 the
- * built-in choice (4 when steps >= 1024, else off).  QOC_EINVAL otherwise. */
+ * built-in choice, off: at N = 32, J = 4000 four chunks measured 4.20 ms per
+ * gradient + Hessian evaluation against 3.94 ms unchunked (the chunked
+ * refinement's part-empty waves and the SMs the chain shares cost more than
+ * the chain's overlap gains).  QOC_EINVAL otherwise. */
 qoc_status qoc_set_pipeline(qoc_problem* p, int chunks);
 
 /* Panel columns per CTA of the tangent and second-order adjoint sweeps

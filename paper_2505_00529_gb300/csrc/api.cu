@@ -343,13 +343,14 @@ qoc_status enqueue_blocked(qoc_problem* p, int order, double* out_dev) {
 }
 
 // Chunks of the forward pipeline for an evaluation (0: none).  Time-blocked
-// evaluations with the refined eigensolver only; the built-in choice
-// pipelines horizons of 1024 steps or more in 4 chunks.
+// evaluations with the refined eigensolver only, on request: measured at
+// N = 32, J = 4000, the refinement in four chunks of 1000 steps loses more
+// to its part-empty last waves and to the chain sharing the SMs (0.68 ->
+// 1.00 ms) than the chain gains, so the built-in choice is off.
 int pipeline_chunks(const qoc_problem* p, int /*order*/) {
   if (p->bs <= 1 || p->eig_method != QOC_EIG_REFINED) return 0;
   const int nblk = (p->J + p->bs - 1) / p->bs;
-  int c = p->pipeline;
-  if (c < 0) c = p->J >= 1024 ? 4 : 0;
+  int c = p->pipeline < 0 ? 0 : p->pipeline;
   if (c > qoc_problem::kMaxChunks) c = qoc_problem::kMaxChunks;
   if (c > nblk) c = nblk;
   return c >= 2 ? c : 0;
