@@ -174,10 +174,12 @@ double mixed_error_estimate(const qoc_problem* p, int bs) {
 // from the binary32 Jacobi start reaches on most steps (orthogonality defect
 // <= 3e-5, whose square is what the update leaves); binary64 sweeps refine
 // to the binary64 floor.
-// relaxed refinement finish for problems on binary32 sweeps: |I - W^T W|_F
-// at most 1e-4 before the update leaves O(|R|^2 + |E| |R|) ~ 1e-8 after it
-// (the binary32 Jacobi start is at a few 1e-5)
-double eig_finish_tol(const qoc_problem* p) { return p->precision == QOC_MIXED_FP32 ? 1e-4 : 0.0; }
+// relaxed refinement finish for problems on binary32 sweeps: |I - W^T W|_F at
+// most 3e-5 before the finishing update.  A looser 1e-4, which would end
+// most steps after one update, measured a 1.6e-6 mixed Hessian error on an
+// avoided crossing (N = 48, J = 4000): the orthogonality left behind
+// accumulates over the steps.
+double eig_finish_tol(const qoc_problem* p) { return p->precision == QOC_MIXED_FP32 ? 3e-5 : 0.0; }
 
 // panel columns per CTA: one by default, which spreads a panel over K SMs
 // (binary64 is throughput-limited per SM; the binary32 sweep is latency-bound
