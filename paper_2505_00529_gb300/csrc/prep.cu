@@ -277,12 +277,26 @@ __device__ __forceinline__ void prep_step(const double* __restrict__ Wg,
   // Pairs p < q.  Far (dt |l_p - l_q| > TAU_DD2): X' is symmetric, so one
   // thread forms X'_pq = X'_qp = 2 (Y_pq - Y_qp) / (l_p - l_q) and leaves the
   // reciprocal of l_p - l_q (and of l_q - l_p) in the real part of its two
-  // (now dead) Y entries for the diagonal sums below.  Near: listed for the
-  // direct sum, their Y entries zeroed as the mark.
+  // (now dead) Y entries for the near-triple recurrences below.  Near: listed
+  // for the direct sum, their Y entries zeroed as the mark.
+  //
+  // The same thread also forms the pair's two terms of the diagonal sums
+  // X'_pp = 2 sum_r M~_pr^2 phi[l_p, l_r, l_p] and leaves them in P (whose
+  // P~ it reads once, and which nothing reads afterwards): for far r the
+  // recurrence on the extremes gives phi[l_p, l_r, l_p] = (Gamma1_pp -
+  // Gamma1_pr) / (l_p - l_r), so the term of row p is
+  // M~_pr (Gamma1_pp M~_pr - P~_pr) / (l_p - l_r) (P~ = Gamma1 o M~, symmetric).
+  // At r = p, phi[l_p, l_p, l_p] = phi''(l_p) / 2 = -dt^2 / 2 exp(-i dt l_p);
+  // the near r != p terms follow (series), then each row is summed in order.
   for (int t = tid; t < NT; t += nt) {
     int p, q;
     tri_index(t, N, p, q);
-    if (p == q) continue;
+    const double m = Mt[p * ld + q];
+    if (p == q) {
+      const double2 ep = cmul(eh[p], eh[p]);                 // exp(-i dt l_p)
+      P[p * ld + p] = cscale(ep, -cser[2] * (m * m));
+      continue;
+    }
     const double dl = lam[p] - lam[q];
     if (!(dt * fabs(dl) > TAU_DD2)) {
       near[atomicAdd(&n_near, 1)] = p * N + q;
@@ -297,43 +311,34 @@ __device__ __forceinline__ void prep_step(const double* __restrict__ Wg,
     Xg[(size_t)q * N + p] = x;
     Y[p * ld + q].x = rec;
     Y[q * ld + p].x = -rec;
+    const double2 pv = P[p * ld + q];
+    const double2 ep = cmul(eh[p], eh[p]), eq = cmul(eh[q], eh[q]);
+    const double2 gp = make_double2(ep.y * dt, -ep.x * dt);   // Gamma1_pp = -i dt exp(-i dt l_p)
+    const double2 gq = make_double2(eq.y * dt, -eq.x * dt);
+    const double mr = m * rec;
+    P[p * ld + q] = cscale(csub(cscale(gp, m), pv), mr);
+    P[q * ld + p] = cscale(csub(cscale(gq, m), pv), -mr);
   }
   __syncthreads();
   const int warp = tid >> 5, lane = tid & 31, nwarp = (nt + 31) >> 5;
-  // Diagonal: X'_pp = 2 sum_r M~_pr^2 phi[l_p, l_r, l_p], one warp per p, lanes
-  // over r.  For far r the recurrence on the extremes gives
-  // phi[l_p, l_r, l_p] = (Gamma1_pp - Gamma1_pr) / (l_p - l_r), so the term is
-  // M~_pr (Gamma1_pp M~_pr - P~_pr) / (l_p - l_r) (P~ = Gamma1 o M~); at r = p,
-  // phi[l_p, l_p, l_p] = phi''(l_p) / 2 = -dt^2 / 2 exp(-i dt l_p); other near r
-  // take the series.  Gamma1_pp = -i dt exp(-i dt l_p).  Every lane of a warp
-  // occupies the binary64 pipe for each branch any lane takes, so the series
-  // runs only in rows that have a near r other than p.
-  for (int p = warp; p < N; p += nwarp) {
-    const double2 ep = cmul(eh[p], eh[p]);                 // exp(-i dt l_p)
-    const double2 gpp = make_double2(ep.y * dt, -ep.x * dt);
+  // near r != p terms of the diagonal sums, one series per thread: entry
+  // 2k + s is pair k's term in row p (s = 0) or q (s = 1)
+  for (int e = tid; e < 2 * n_near; e += nt) {
+    const int pq = near[e >> 1];
+    const int a = (e & 1) ? pq % N : pq / N, b = (e & 1) ? pq / N : pq % N;
+    const double m = Mt[a * ld + b];
+    P[a * ld + b] = cscale(dd2_dev(a, b, a, lam, eh, Y, ld, cser, dt), m * m);
+  }
+  __syncthreads();
+  for (int p = tid; p < N; p += nt) {   // X'_pp, each row summed in order
     double re = 0, im = 0;
-    for (int r = lane; r < N; r += 32) {
-      const double m = Mt[p * ld + r];
-      const double rec = r == p ? 0.0 : Y[p * ld + r].x;
-      double2 term;
-      if (nonzero_bits(rec)) {    // a far pair
-        const double2 tr = csub(cscale(gpp, m), P[p * ld + r]);
-        term = cscale(tr, m * rec);
-      } else if (r == p) {
-        term = cscale(ep, -cser[2] * (m * m));
-      } else {
-        term = cscale(dd2_dev(p, r, p, lam, eh, Y, ld, cser, dt), m * m);
-      }
-      re += term.x;
-      im += term.y;
+    for (int r = 0; r < N; ++r) {
+      re += P[p * ld + r].x;
+      im += P[p * ld + r].y;
     }
-    re = warp_sum(re);
-    im = warp_sum(im);
-    if (lane == 0) {
-      const double2 x = make_double2(2.0 * re, 2.0 * im);
-      bad |= !(finite_bits(x.x) && finite_bits(x.y));
-      Xg[(size_t)p * N + p] = x;
-    }
+    const double2 x = make_double2(2.0 * re, 2.0 * im);
+    bad |= !(finite_bits(x.x) && finite_bits(x.y));
+    Xg[(size_t)p * N + p] = x;
   }
   // near pairs p < q: the direct N-term sum, one warp per pair, lanes over r
   for (int k = warp; k < n_near; k += nwarp) {
