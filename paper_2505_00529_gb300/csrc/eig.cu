@@ -668,9 +668,9 @@ __global__ void __launch_bounds__(128, 6) k_eig_jacobi32(const double* __restric
         const float ck = cs[2 * k], sk = cs[2 * k + 1];
         const int p0 = pr[2 * k], p1 = pr[2 * k + 1];
         const bool pr1 = p1 < N;
-        constexpr int BT = 4;                      // blocks per batch (<= NH^2 / 32 = 8)
-#pragma unroll
-        for (int t0 = 0; t0 < 8; t0 += BT) {
+        constexpr int BT = 4;                      // blocks per batch
+        // NH^2 / 32 blocks per lane: 8 at N = 32, 32 at N = 64 (NH = 32)
+        for (int t0 = 0; lane / NH + t0 * lstep < NH; t0 += BT) {
           float x00[BT], x01[BT], x10[BT], x11[BT], clv[BT], slv[BT];
           int q0v[BT], q1v[BT];
           bool go[BT];
@@ -734,8 +734,7 @@ __global__ void __launch_bounds__(128, 6) k_eig_jacobi32(const double* __restric
         // eight rows loaded before they are stored
         if (sk != 0.f && pr1) {
           constexpr int VT = 8;
-#pragma unroll
-          for (int t0 = 0; t0 < 16; t0 += VT) {
+          for (int t0 = 0; lane / NH + t0 * lstep < N; t0 += VT) {   // N NH / 32 rows per lane
             float v0[VT], v1[VT];
 #pragma unroll
             for (int u = 0; u < VT; ++u) {
