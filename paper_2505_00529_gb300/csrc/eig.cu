@@ -602,7 +602,7 @@ __device__ __forceinline__ float warp_sum_f(float v) {
   return v;
 }
 
-__global__ void __launch_bounds__(128, 6) k_eig_jacobi32(const double* __restrict__ H0,
+__global__ void __launch_bounds__(128) k_eig_jacobi32(const double* __restrict__ H0,
                                                       const double* __restrict__ M,
                                                       const double* __restrict__ f, int N, int J,
                                                       int mpb, double* __restrict__ W_out,
@@ -658,101 +658,47 @@ __global__ void __launch_bounds__(128, 6) k_eig_jacobi32(const double* __restric
       if (++qa == NR) qa = 0;
       __syncwarp();
       if (kstep == 0) {
-        // NH divides 32: every lane keeps one row pair k (blocks) and one column
-        // pair (V).  The blocks of a round are disjoint, so a batch of them is
-        // loaded before any is stored: the loads overlap instead of each
-        // waiting for the previous block's stores (which the compiler cannot
-        // tell apart from them).  Rows or columns of the dummy index of odd N
-        // enter as zeros and are not stored (their rotation is the identity).
+        // NH divides 32: every lane keeps one row pair k (blocks) and one column pair l (V)
         const int k = lane % NH;
         const float ck = cs[2 * k], sk = cs[2 * k + 1];
         const int p0 = pr[2 * k], p1 = pr[2 * k + 1];
-        const bool pr1 = p1 < N;
-        constexpr int BT = 4;                      // blocks per batch
-        // NH^2 / 32 blocks per lane: 8 at N = 32, 32 at N = 64 (NH = 32)
-        for (int t0 = 0; lane / NH + t0 * lstep < NH; t0 += BT) {
-          float x00[BT], x01[BT], x10[BT], x11[BT], clv[BT], slv[BT];
-          int q0v[BT], q1v[BT];
-          bool go[BT];
-#pragma unroll
-          for (int u = 0; u < BT; ++u) {
-            const int l = lane / NH + (t0 + u) * lstep;
-            go[u] = false;
-            x00[u] = x01[u] = x10[u] = x11[u] = 0.f;
-            clv[u] = 1.f;
-            slv[u] = 0.f;
-            q0v[u] = q1v[u] = 0;
-            if (l < NH) {
-              slv[u] = cs[2 * l + 1];
-              clv[u] = cs[2 * l];
-              q0v[u] = pr[2 * l];
-              q1v[u] = pr[2 * l + 1];
-              go[u] = !(sk == 0.f && slv[u] == 0.f);
-              if (go[u]) {
-                const bool qc1 = q1v[u] < N;
-                x00[u] = A[p0 * ld + q0v[u]];
-                if (qc1) x01[u] = A[p0 * ld + q1v[u]];
-                if (pr1) x10[u] = A[p1 * ld + q0v[u]];
-                if (pr1 && qc1) x11[u] = A[p1 * ld + q1v[u]];
-              }
+        for (int l = lane / NH; l < NH; l += lstep) {
+          const float sl = cs[2 * l + 1];
+          if (sk == 0.f && sl == 0.f) continue;
+          const float cl = cs[2 * l];
+          const int q0 = pr[2 * l], q1 = pr[2 * l + 1];
+          if (p1 >= N) {
+            if (q1 < N) {
+              const float x0 = A[p0 * ld + q0], x1 = A[p0 * ld + q1];
+              A[p0 * ld + q0] = cl * x0 - sl * x1;
+              A[p0 * ld + q1] = sl * x0 + cl * x1;
             }
-          }
-#pragma unroll
-          for (int u = 0; u < BT; ++u) {
-            if (!go[u]) continue;
-            const int l = lane / NH + (t0 + u) * lstep;
-            const float cl = clv[u], sl = slv[u];
-            const int q0 = q0v[u], q1 = q1v[u];
-            const bool qc1 = q1 < N;
-            if (!pr1) {
-              if (qc1) {
-                const float y0 = x00[u], y1 = x01[u];
-                A[p0 * ld + q0] = cl * y0 - sl * y1;
-                A[p0 * ld + q1] = sl * y0 + cl * y1;
-              }
-            } else if (!qc1) {
-              const float y0 = x00[u], y1 = x10[u];
-              A[p0 * ld + q0] = ck * y0 - sk * y1;
-              A[p1 * ld + q0] = sk * y0 + ck * y1;
+          } else if (q1 >= N) {
+            const float x0 = A[p0 * ld + q0], x1 = A[p1 * ld + q0];
+            A[p0 * ld + q0] = ck * x0 - sk * x1;
+            A[p1 * ld + q0] = sk * x0 + ck * x1;
+          } else {
+            const float a00 = A[p0 * ld + q0], a01 = A[p0 * ld + q1];
+            const float a10 = A[p1 * ld + q0], a11 = A[p1 * ld + q1];
+            const float b00 = ck * a00 - sk * a10, b01 = ck * a01 - sk * a11;
+            const float b10 = sk * a00 + ck * a10, b11 = sk * a01 + ck * a11;
+            A[p0 * ld + q0] = cl * b00 - sl * b01;
+            A[p1 * ld + q1] = sl * b10 + cl * b11;
+            if (k == l) {
+              A[p0 * ld + q1] = 0.f;
+              A[p1 * ld + q0] = 0.f;
             } else {
-              const float a00 = x00[u], a01 = x01[u], a10 = x10[u], a11 = x11[u];
-              const float b00 = ck * a00 - sk * a10, b01 = ck * a01 - sk * a11;
-              const float b10 = sk * a00 + ck * a10, b11 = sk * a01 + ck * a11;
-              A[p0 * ld + q0] = cl * b00 - sl * b01;
-              A[p1 * ld + q1] = sl * b10 + cl * b11;
-              if (k == l) {
-                A[p0 * ld + q1] = 0.f;
-                A[p1 * ld + q0] = 0.f;
-              } else {
-                A[p0 * ld + q1] = sl * b00 + cl * b01;
-                A[p1 * ld + q0] = cl * b10 - sl * b11;
-              }
+              A[p0 * ld + q1] = sl * b00 + cl * b01;
+              A[p1 * ld + q0] = cl * b10 - sl * b11;
             }
           }
         }
-        // V <- V R: this lane's column pair is k, rows i = lane / NH + lstep t,
-        // eight rows loaded before they are stored
-        if (sk != 0.f && pr1) {
-          constexpr int VT = 8;
-          for (int t0 = 0; lane / NH + t0 * lstep < N; t0 += VT) {   // N NH / 32 rows per lane
-            float v0[VT], v1[VT];
-#pragma unroll
-            for (int u = 0; u < VT; ++u) {
-              const int i = lane / NH + (t0 + u) * lstep;
-              v0[u] = v1[u] = 0.f;
-              if (i < N) {
-                v0[u] = V[i * ld + p0];
-                v1[u] = V[i * ld + p1];
-              }
-            }
-#pragma unroll
-            for (int u = 0; u < VT; ++u) {
-              const int i = lane / NH + (t0 + u) * lstep;
-              if (i < N) {
-                V[i * ld + p0] = ck * v0[u] - sk * v1[u];
-                V[i * ld + p1] = sk * v0[u] + ck * v1[u];
-              }
-            }
+        // V <- V R: this lane's column pair is k, rows i = lane / NH + lstep t
+        if (sk != 0.f && p1 < N) {
+          for (int i = lane / NH; i < N; i += lstep) {
+            const float v0 = V[i * ld + p0], v1 = V[i * ld + p1];
+            V[i * ld + p0] = ck * v0 - sk * v1;
+            V[i * ld + p1] = sk * v0 + ck * v1;
           }
         }
         __syncwarp();
