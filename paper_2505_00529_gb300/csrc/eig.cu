@@ -657,6 +657,73 @@ __global__ void __launch_bounds__(128) k_eig_jacobi32(const double* __restrict__
       if (++pa == NR) pa = 0;
       if (++qa == NR) qa = 0;
       __syncwarp();
+      if (N == 32) {
+        // N = 32 exactly: every lane owns 8 blocks (k, l = lane / 16 + 2 t) and
+        // 16 rows of its V column pair, all valid (no dummy index), so a batch
+        // of four blocks (eight rows) is loaded before any is stored with no
+        // guards; the blocks of a round are disjoint.  (c, s) and the index
+        // pair of a rotation are one 8-byte load each.  Same arithmetic as the
+        // general path below.
+        const int k = lane & 15, lb = lane >> 4;
+        const float2 csk = reinterpret_cast<const float2*>(cs)[k];
+        const int2 prk = reinterpret_cast<const int2*>(pr)[k];
+        const float ck = csk.x, sk = csk.y;
+        const int p0 = prk.x, p1 = prk.y;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          float a00[4], a01[4], a10[4], a11[4];
+          float2 csl[4];
+          int2 prl[4];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const int l = lb + 2 * (4 * h + u);
+            csl[u] = reinterpret_cast<const float2*>(cs)[l];
+            prl[u] = reinterpret_cast<const int2*>(pr)[l];
+            a00[u] = A[p0 * ld + prl[u].x];
+            a01[u] = A[p0 * ld + prl[u].y];
+            a10[u] = A[p1 * ld + prl[u].x];
+            a11[u] = A[p1 * ld + prl[u].y];
+          }
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const int l = lb + 2 * (4 * h + u);
+            const float cl = csl[u].x, sl = csl[u].y;
+            if (sk == 0.f && sl == 0.f) continue;   // both identity: block unchanged
+            const int q0 = prl[u].x, q1 = prl[u].y;
+            const float b00 = ck * a00[u] - sk * a10[u], b01 = ck * a01[u] - sk * a11[u];
+            const float b10 = sk * a00[u] + ck * a10[u], b11 = sk * a01[u] + ck * a11[u];
+            A[p0 * ld + q0] = cl * b00 - sl * b01;
+            A[p1 * ld + q1] = sl * b10 + cl * b11;
+            if (k == l) {
+              A[p0 * ld + q1] = 0.f;
+              A[p1 * ld + q0] = 0.f;
+            } else {
+              A[p0 * ld + q1] = sl * b00 + cl * b01;
+              A[p1 * ld + q0] = cl * b10 - sl * b11;
+            }
+          }
+        }
+        if (sk != 0.f) {   // V <- V R on column pair k, rows lane / 16 + 2 t
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            float v0[8], v1[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+              const int i = lb + 2 * (8 * h + u);
+              v0[u] = V[i * ld + p0];
+              v1[u] = V[i * ld + p1];
+            }
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+              const int i = lb + 2 * (8 * h + u);
+              V[i * ld + p0] = ck * v0[u] - sk * v1[u];
+              V[i * ld + p1] = sk * v0[u] + ck * v1[u];
+            }
+          }
+        }
+        __syncwarp();
+        continue;
+      }
       if (kstep == 0) {
         // NH divides 32: every lane keeps one row pair k (blocks) and one column pair l (V)
         const int k = lane % NH;
