@@ -262,22 +262,28 @@ __device__ __forceinline__ void eig_refine_step(const double* __restrict__ H0,
                                                 unsigned char* smem_raw) {
   const int ld = N + 1;
   const int NP = N + (N & 1);
-  double* H = reinterpret_cast<double*>(smem_raw);
-  double* W = H + N * ld;
-  double* T = W + N * ld;
-  double* S = T + N * ld;
-  double* R = S + N * ld;
-  double* lam = R + N * ld;          // [N + 1]
-  double* red = lam + N + 1;         // [64]
-  double* cs = red + 64;             // [NP]
-  int* pr = reinterpret_cast<int*>(cs + NP);  // [NP + 2]
-  float* Wf = reinterpret_cast<float*>(
-      (reinterpret_cast<uintptr_t>(pr + NP + 2) + 15) & ~uintptr_t(15));   // [N][ld] binary32 W
-  float* Ef = Wf + N * ld;                                                  // [N][ld] binary32 E
+  double *H, *W, *T, *S, *R, *lam, *red, *cs;
+  int* pr;
+  float *Wf, *Ef;
+  double* Tc;                        // scratch of the clean-up's W V product
   OzSpace oz{};
   if (OZ) {
+    // Three binary64 matrices instead of five, so that three CTAs fit an SM:
+    // H lives in T until it is split (its slices are all the products use),
+    // S overwrites T once T is split, and the binary32 W and E of the update
+    // (and the clean-up's scratch) use the slice buffers of W and T, which
+    // are dead from the S and R products to the next update's split of W.
+    W = reinterpret_cast<double*>(smem_raw);
+    T = W + N * ld;
+    R = T + N * ld;
+    H = T;
+    S = T;
+    lam = R + N * ld;
+    red = lam + N + 1;
+    cs = red + 64;
+    pr = reinterpret_cast<int*>(cs + NP);
     unsigned char* ob = reinterpret_cast<unsigned char*>(
-        (reinterpret_cast<uintptr_t>(Ef + N * ld) + 15) & ~uintptr_t(15));
+        (reinterpret_cast<uintptr_t>(pr + NP + 2) + 15) & ~uintptr_t(15));
     const size_t sl = (size_t)kOzSlices * 32 * oz::LD;
     oz.Hs = reinterpret_cast<__nv_bfloat16*>(ob);
     oz.Ws = oz.Hs + sl;
@@ -285,6 +291,23 @@ __device__ __forceinline__ void eig_refine_step(const double* __restrict__ H0,
     oz.eH = reinterpret_cast<int*>(oz.Ts + sl);
     oz.eW = oz.eH + 32;
     oz.eT = oz.eW + 32;
+    Wf = reinterpret_cast<float*>(oz.Ws);
+    Ef = reinterpret_cast<float*>(oz.Ts);
+    Tc = reinterpret_cast<double*>(oz.Ws);
+  } else {
+    H = reinterpret_cast<double*>(smem_raw);
+    W = H + N * ld;
+    T = W + N * ld;
+    S = T + N * ld;
+    R = S + N * ld;
+    lam = R + N * ld;                // [N + 1]
+    red = lam + N + 1;               // [64]
+    cs = red + 64;                   // [NP]
+    pr = reinterpret_cast<int*>(cs + NP);  // [NP + 2]
+    Wf = reinterpret_cast<float*>(
+        (reinterpret_cast<uintptr_t>(pr + NP + 2) + 15) & ~uintptr_t(15));   // [N][ld] binary32 W
+    Ef = Wf + N * ld;                                                        // [N][ld] binary32 E
+    Tc = T;
   }
   const int tid = threadIdx.x, nt = blockDim.x;
   const double fj = f[j];
@@ -545,15 +568,15 @@ __device__ __forceinline__ void eig_refine_step(const double* __restrict__ H0,
   }
   __syncthreads();
   if (stats && tid == 0 && any_rot) atomicAdd(&stats[1], 1u);
-  if (any_rot) {   // W <- W V (T as scratch)
+  if (any_rot) {   // W <- W V (Tc as scratch)
     for (int e = tid; e < N * N; e += nt) {
       const int i = e / N, k = e % N;
       double acc = 0;
       for (int r = 0; r < N; ++r) acc = fma(W[i * ld + r], R[r * ld + k], acc);
-      T[i * ld + k] = acc;
+      Tc[i * ld + k] = acc;
     }
     __syncthreads();
-    for (int e = tid; e < N * N; e += nt) W[(e / N) * ld + (e % N)] = T[(e / N) * ld + (e % N)];
+    for (int e = tid; e < N * N; e += nt) W[(e / N) * ld + (e % N)] = Tc[(e / N) * ld + (e % N)];
     __syncthreads();
   }
   }
@@ -568,7 +591,7 @@ __device__ __forceinline__ void eig_refine_step(const double* __restrict__ H0,
 // large-N launch.  GWS: storage in the global workspace (a compile-time
 // choice, so that the shared-memory instantiation keeps shared-memory loads).
 template <int MAXT, bool GWS, bool OZ = false>
-__global__ void __launch_bounds__(MAXT, OZ ? 2 : (MAXT <= 256 ? 4 : 1))
+__global__ void __launch_bounds__(MAXT, OZ ? 3 : (MAXT <= 256 ? 4 : 1))
 k_eig_refine(const double* __restrict__ H0, const double* __restrict__ M,
                              const double* __restrict__ f, int N, int J, int sweeps,
                              double angle_tol, double* __restrict__ W_io,
@@ -858,6 +881,13 @@ static size_t jacobi_smem(int N, size_t tsize) {
   s = (s + 15) & ~size_t(15);
   return s + 64 * sizeof(double) + 16;
 }
+// the tensor-core refinement's layout: W, T (H, then S), R, then the slices
+static size_t refine_oz_smem(int N) {
+  const int NP = N + (N & 1);
+  return (3 * (size_t)N * (N + 1) + N + 1 + 64 + NP) * sizeof(double) + (NP + 2) * sizeof(int) + 16 +
+         oz_smem_bytes();
+}
+
 static size_t refine_smem(int N) {
   const int NP = N + (N & 1);
   return (5 * (size_t)N * (N + 1) + N + 1 + 64 + NP) * sizeof(double) + (NP + 2) * sizeof(int) + 16 +
@@ -906,7 +936,7 @@ cudaError_t launch_eig(const double* H0, const double* M, const double* f, int N
   if (!(phases & EIG_PHASE_REFINE)) return cudaSuccess;
   if (N <= 32 && finish_tol > 0) {
     // relaxed refinement (binary32 sweeps): products on the tensor cores
-    const size_t sm = refine_smem(N) + oz_smem_bytes();
+    const size_t sm = refine_oz_smem(N);
     if (sm <= max_dyn_smem((const void*)k_eig_refine<256, false, true>)) {
       k_eig_refine<256, false, true><<<J, 256, sm, st>>>(H0, M, f, N, J, refine_sweeps, angle_tol, W, eig,
                                                          status, stats, finish_tol, nullptr, 0);
