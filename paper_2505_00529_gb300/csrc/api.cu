@@ -49,6 +49,7 @@ struct qoc_problem {
   cudaEvent_t fork = nullptr, join = nullptr;
   cudaEvent_t ev_state = nullptr, ev_ptil = nullptr, ev_panels = nullptr;
   cudaEvent_t ev_bprod = nullptr;       // backward block products done (panel stream)
+  cudaEvent_t ev_fprod = nullptr;       // forward block products done (panel stream)
   int timing = 0;
   int sched = 0;                        // 0 sequential, 1 three-stream (time-blocked, order >= 1)
   // forward pipeline: the refinement and increments in chunks of steps, the
@@ -232,11 +233,12 @@ BSweepArgs panel_sweep_args(qoc_problem* p, int bwd) {
 
 
 // Time-blocked evaluation on three streams (order >= 1):
-//   main: forward block products (before the fork), derivative preparation
-//       P~ (then X' for the Hessian), pointwise c_j, assembly
-//   chains (high priority): state chain + fill, terminal; costate chain
-//       (after the backward block products) + fill
-//   panels (high priority): backward block products at the fork; order 2,
+//   main: derivative preparation P~ (then X' for the Hessian), pointwise c_j,
+//       assembly
+//   chains (high priority): state chain (after the forward block products)
+//       + fill, terminal; costate chain (after the backward ones) + fill
+//   panels (high priority): forward, then backward block products at the
+//       fork; order 2,
 //       as soon as the state and P~ exist: p^ -> propagated sources ->
 //       tangent panel sweep; after the costate: y^, g -> contraction U ->
 //       second-order adjoint sources and sweep -> contraction V
@@ -269,21 +271,27 @@ qoc_status enqueue_blocked(qoc_problem* p, int order, double* out_dev) {
   }
   p->sched = 1;
   cudaStream_t cs = p->side, ps = p->pstream;
-  // The block products depend on the increments only: the forward ones run
-  // on the main stream before the fork (the derivative preparation they
-  // delay is off the critical path), the backward ones on the panel stream
-  // beside the forward chain, so that neither sits on the chain stream in
-  // front of its chain.
-  if (!p->piped && !p->fwd_reused)   // else enqueued chunk by chunk behind the refinement, or reused
-    QOC_TRY(launch_block_delta(p->D, p->dstride, N, J, bs, 0, mixed, p->Mf, p->mstride, st, p->ws[0]));
+  // The block products depend on the increments only: both run on the panel
+  // stream at the fork, the forward ones first, so that the state chain
+  // waits for them alone and the costate chain finds its products done;
+  // neither sits on the chain stream, and the derivative preparation on the
+  // main stream starts at the fork.
+  const bool fwd_here = !p->piped && !p->fwd_reused;   // else chunked behind the refinement, or reused
   QOC_TRY(cudaEventRecord(p->fork, st));
   QOC_TRY(cudaStreamWaitEvent(ps, p->fork, 0));
+  if (fwd_here) {
+    QOC_TRY(launch_block_delta(p->D, p->dstride, N, J, bs, 0, mixed, p->Mf, p->mstride, ps, p->ws[2]));
+    QOC_TRY(cudaEventRecord(p->ev_fprod, ps));
+  }
   QOC_TRY(launch_block_delta(p->D, p->dstride, N, J, bs, 1, mixed, p->Mb, p->mstride, ps, p->ws[2]));
   QOC_TRY(cudaEventRecord(p->ev_bprod, ps));
   // ---- chains ----
   QOC_TRY(cudaStreamWaitEvent(cs, p->fork, 0));
   if (p->timing) cudaEventRecord(p->ev[10], cs);
-  if (!p->piped && !p->fwd_reused) QOC_TRY(launch_bsweep(chain_sweep_args(p, 0), mixed, cs));
+  if (fwd_here) {
+    QOC_TRY(cudaStreamWaitEvent(cs, p->ev_fprod, 0));
+    QOC_TRY(launch_bsweep(chain_sweep_args(p, 0), mixed, cs));
+  }
   QOC_TRY(launch_block_fill(p->D, p->dstride, N, J, bs, 0, mixed, p->Xa, p->a_hat, cs));
   QOC_TRY(launch_terminal(p->f, J, p->a_hat, mixed, p->beta, N, cexpi_h(thetaJ), p->w_f, p->w_t,
                           p->lamJ, p->scal + 0, nullptr, cs));
@@ -608,7 +616,7 @@ void qoc_destroy_problem(qoc_problem* p) {
       cudaStreamSynchronize(*sp);
       cudaStreamDestroy(*sp);
     }
-  for (cudaEvent_t e : {p->fork, p->join, p->ev_state, p->ev_ptil, p->ev_panels, p->ev_bprod})
+  for (cudaEvent_t e : {p->fork, p->join, p->ev_state, p->ev_ptil, p->ev_panels, p->ev_bprod, p->ev_fprod})
     if (e) cudaEventDestroy(e);
   if (p->own_stream && p->stream) cudaStreamDestroy(p->stream);
   delete p;
@@ -693,7 +701,7 @@ qoc_status qoc_create_problem(int N, const double* H0, const double* M, const do
     if ((e = cudaStreamCreateWithPriority(&p->pstream, cudaStreamNonBlocking, hi)) != cudaSuccess)
       return fail(e);
   }
-  for (cudaEvent_t* ep : {&p->fork, &p->join, &p->ev_state, &p->ev_ptil, &p->ev_panels, &p->ev_bprod})
+  for (cudaEvent_t* ep : {&p->fork, &p->join, &p->ev_state, &p->ev_ptil, &p->ev_panels, &p->ev_bprod, &p->ev_fprod})
     if ((e = cudaEventCreateWithFlags(ep, cudaEventDisableTiming)) != cudaSuccess) return fail(e);
 #define ALLOC(ptr, bytes) \
   if ((e = dalloc(p, &(ptr), (bytes))) != cudaSuccess) return fail(e)
