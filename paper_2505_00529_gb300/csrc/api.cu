@@ -50,6 +50,7 @@ struct qoc_problem {
   cudaEvent_t ev_state = nullptr, ev_ptil = nullptr, ev_panels = nullptr;
   cudaEvent_t ev_bprod = nullptr;       // backward block products done (panel stream)
   cudaEvent_t ev_fprod = nullptr;       // forward block products done (panel stream)
+  cudaEvent_t ev_yhat = nullptr;        // y^ and g done, tangent panel swept (panel stream)
   int timing = 0;
   int sched = 0;                        // 0 sequential, 1 three-stream (time-blocked, order >= 1)
   // forward pipeline: the refinement and increments in chunks of steps, the
@@ -233,17 +234,18 @@ BSweepArgs panel_sweep_args(qoc_problem* p, int bwd) {
 
 
 // Time-blocked evaluation on three streams (order >= 1):
-//   main: derivative preparation P~ (then X' for the Hessian), pointwise c_j,
-//       assembly
+//   main: derivative preparation P~ (then X' for the Hessian); after the
+//       costate: pointwise c_j, drift, the forward contraction (W, Gamma,
+//       U); assembly
 //   chains (high priority): state chain (after the forward block products)
 //       + fill, terminal; costate chain (after the backward ones) + fill
 //   panels (high priority): forward, then backward block products at the
-//       fork; order 2,
-//       as soon as the state and P~ exist: p^ -> propagated sources ->
-//       tangent panel sweep; after the costate: y^, g -> contraction U ->
+//       fork; order 2, as soon as the state and P~ exist: p^ -> propagated
+//       sources -> tangent panel sweep; after the costate: y^, g ->
 //       second-order adjoint sources and sweep -> contraction V
-// so that the two latency-bound panel sweeps overlap the costate chain and
-// the binary64 X' preparation instead of following them.
+// so that the latency-bound sweeps overlap the binary64 X' preparation and
+// each other instead of following them, and the chain state -> costate ->
+// second-order adjoint carries nothing it does not need.
 qoc_status enqueue_blocked(qoc_problem* p, int order, double* out_dev) {
   cudaStream_t st = p->stream;
   const int N = p->N, K = p->K, J = p->J, bs = p->bs;
@@ -311,7 +313,6 @@ qoc_status enqueue_blocked(qoc_problem* p, int order, double* out_dev) {
     QOC_TRY(cudaStreamWaitEvent(ps, p->ev_ptil, 0));
     QOC_TRY(cudaStreamWaitEvent(ps, p->ev_state, 0));
     if (p->timing) cudaEventRecord(p->ev[12], ps);
-    QOC_TRY(launch_drift(p->a_hat, mixed, N, J, p->scal + 1, ps));
     QOC_TRY(launch_pointwise(p->W, p->Ptil, p->Xp, p->a_hat, p->l_hat, mixed, N, J, kappa, p->p_hat,
                              p->y_hat, p->g, p->c, PW_P, ps, p->ws[2]));
     QOC_TRY(launch_block_src(p->D, p->dstride, N, J, bs, 0, mixed, p->p_hat, p->y_hat, p->vstride,
@@ -320,10 +321,9 @@ qoc_status enqueue_blocked(qoc_problem* p, int order, double* out_dev) {
     QOC_TRY(cudaStreamWaitEvent(ps, p->join, 0));
     QOC_TRY(launch_pointwise(p->W, p->Ptil, p->Xp, p->a_hat, p->l_hat, mixed, N, J, kappa, p->p_hat,
                              p->y_hat, p->g, p->c, PW_Y, ps, p->ws[2]));
-    QOC_TRY(launch_block_src(p->D, p->dstride, N, J, bs, 0, mixed, p->p_hat, p->y_hat, p->vstride,
-                             p->Qf, p->Wf, p->Gf, p->qstride, p->gstride, BS_WG, ps, p->ws[2]));
-    QOC_TRY(launch_block_contract(p->XS, p->Wf, p->Gf, p->qstride, p->gstride, Bsrc, p->Kp, N, K, J,
-                                  bs, 0, mixed, p->U, ps));
+    // the forward contraction (W, Gamma and U) is not on the way to the
+    // second-order adjoint sweep: the main stream takes it, beside that sweep
+    QOC_TRY(cudaEventRecord(p->ev_yhat, ps));
     if (soa) {
       QOC_TRY(launch_block_src(p->D, p->dstride, N, J, bs, 1, mixed, p->y_hat, p->p_hat, p->vstride,
                                p->Qb, p->Wb, p->Gb, p->qstride, p->gstride, BS_Q | BS_WG, ps, p->ws[2]));
@@ -340,7 +340,13 @@ qoc_status enqueue_blocked(qoc_problem* p, int order, double* out_dev) {
     QOC_TRY(cudaStreamWaitEvent(st, p->join, 0));
     QOC_TRY(launch_pointwise(p->W, p->Ptil, p->Xp, p->a_hat, p->l_hat, mixed, N, J, kappa, p->p_hat,
                              p->y_hat, p->g, p->c, PW_C, st, p->ws[0]));
+    QOC_TRY(launch_drift(p->a_hat, mixed, N, J, p->scal + 1, st));
     if (p->timing) cudaEventRecord(p->ev[4], st);
+    QOC_TRY(cudaStreamWaitEvent(st, p->ev_yhat, 0));
+    QOC_TRY(launch_block_src(p->D, p->dstride, N, J, bs, 0, mixed, p->p_hat, p->y_hat, p->vstride,
+                             p->Qf, p->Wf, p->Gf, p->qstride, p->gstride, BS_WG, st, p->ws[0]));
+    QOC_TRY(launch_block_contract(p->XS, p->Wf, p->Gf, p->qstride, p->gstride, Bsrc, p->Kp, N, K, J,
+                                  bs, 0, mixed, p->U, st));
     QOC_TRY(cudaStreamWaitEvent(st, p->ev_panels, 0));
   } else {
     if (p->timing) {
@@ -616,7 +622,7 @@ void qoc_destroy_problem(qoc_problem* p) {
       cudaStreamSynchronize(*sp);
       cudaStreamDestroy(*sp);
     }
-  for (cudaEvent_t e : {p->fork, p->join, p->ev_state, p->ev_ptil, p->ev_panels, p->ev_bprod, p->ev_fprod})
+  for (cudaEvent_t e : {p->fork, p->join, p->ev_state, p->ev_ptil, p->ev_panels, p->ev_bprod, p->ev_fprod, p->ev_yhat})
     if (e) cudaEventDestroy(e);
   if (p->own_stream && p->stream) cudaStreamDestroy(p->stream);
   delete p;
@@ -701,7 +707,7 @@ qoc_status qoc_create_problem(int N, const double* H0, const double* M, const do
     if ((e = cudaStreamCreateWithPriority(&p->pstream, cudaStreamNonBlocking, hi)) != cudaSuccess)
       return fail(e);
   }
-  for (cudaEvent_t* ep : {&p->fork, &p->join, &p->ev_state, &p->ev_ptil, &p->ev_panels, &p->ev_bprod, &p->ev_fprod})
+  for (cudaEvent_t* ep : {&p->fork, &p->join, &p->ev_state, &p->ev_ptil, &p->ev_panels, &p->ev_bprod, &p->ev_fprod, &p->ev_yhat})
     if ((e = cudaEventCreateWithFlags(ep, cudaEventDisableTiming)) != cudaSuccess) return fail(e);
 #define ALLOC(ptr, bytes) \
   if ((e = dalloc(p, &(ptr), (bytes))) != cudaSuccess) return fail(e)
