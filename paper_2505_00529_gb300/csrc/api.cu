@@ -86,6 +86,7 @@ struct qoc_problem {
   StepSpace ws[3];                      // per-step storage beyond shared memory, one region per
                                         // stream (main, chains, panels); empty for N <= 64
   void *D = nullptr, *a_hat = nullptr, *l_hat = nullptr, *p_hat = nullptr, *y_hat = nullptr;
+  double2* rvec = nullptr;              // r_j = P~ a~_j (J x N), from p^ for g
   int* status = nullptr;
   double *trwork = nullptr, *trstep = nullptr, *trinfo = nullptr, *trzero = nullptr;
   // time blocking (bs steps per block; bs == 1: per-step sweeps)
@@ -314,13 +315,13 @@ qoc_status enqueue_blocked(qoc_problem* p, int order, double* out_dev) {
     QOC_TRY(cudaStreamWaitEvent(ps, p->ev_state, 0));
     if (p->timing) cudaEventRecord(p->ev[12], ps);
     QOC_TRY(launch_pointwise(p->W, p->Ptil, p->Xp, p->a_hat, p->l_hat, mixed, N, J, kappa, p->p_hat,
-                             p->y_hat, p->g, p->c, PW_P, ps, p->ws[2]));
+                             p->y_hat, p->g, p->c, PW_P, ps, p->ws[2], p->rvec));
     QOC_TRY(launch_block_src(p->D, p->dstride, N, J, bs, 0, mixed, p->p_hat, p->y_hat, p->vstride,
                              p->Qf, p->Wf, p->Gf, p->qstride, p->gstride, BS_Q, ps, p->ws[2]));
     QOC_TRY(launch_bsweep(panel_sweep_args(p, 0), mixed, ps));
     QOC_TRY(cudaStreamWaitEvent(ps, p->join, 0));
     QOC_TRY(launch_pointwise(p->W, p->Ptil, p->Xp, p->a_hat, p->l_hat, mixed, N, J, kappa, p->p_hat,
-                             p->y_hat, p->g, p->c, PW_Y, ps, p->ws[2]));
+                             p->y_hat, p->g, p->c, PW_Y | PW_RUSE, ps, p->ws[2], p->rvec));
     // the forward contraction (W, Gamma and U) is not on the way to the
     // second-order adjoint sweep: the main stream takes it, beside that sweep
     QOC_TRY(cudaEventRecord(p->ev_yhat, ps));
@@ -741,6 +742,7 @@ qoc_status qoc_create_problem(int N, const double* H0, const double* M, const do
   ALLOC(p->a_hat, 16 * (size_t)(J + 1) * N);
   ALLOC(p->l_hat, 16 * (size_t)(J + 1) * N);
   ALLOC(p->p_hat, (size_t)J * p->vstride);
+  ALLOC(p->rvec, 16 * (size_t)J * N);
   ALLOC(p->y_hat, (size_t)J * p->vstride);
   ALLOC(p->status, sizeof(int));
   // block size: binary32 rounding of the block increment grows ~ sqrt(bs), so

@@ -206,12 +206,14 @@ cudaError_t launch_block_fill(const void* D, size_t dstride, int N, int J, int b
 // p^_j, y^_j, g_j, c_j for all steps from the stored states/costates
 // states / costates as written by the vector chains (double2, or float4 pairs
 // when mixed); p^, y^ written as double2 (binary64 sweeps) or float2 (mixed)
-// what: PW_P (p^ from a^), PW_Y (y^ and g from lambda^ and a^), PW_C (c from X', a^, lambda^)
-enum { PW_P = 1, PW_Y = 2, PW_C = 4 };
+// what: PW_P (p^ from a^), PW_Y (y^ and g from lambda^ and a^), PW_C (c from X', a^, lambda^);
+// with r (J x N): PW_P also stores r_j = P~ a~_j there, and PW_Y | PW_RUSE
+// takes g's r_j from it instead of forming a~_j and r_j again (same values)
+enum { PW_P = 1, PW_Y = 2, PW_C = 4, PW_RUSE = 8 };
 cudaError_t launch_pointwise(const double* W, const double2* Ptil, const double2* Xp,
                              const void* a_hat, const void* l_hat, int mixed, int N, int J,
                              double2 kappa, void* p_hat, void* y_hat, double* g, double* c,
-                             int what, cudaStream_t st, const StepSpace& ws);
+                             int what, cudaStream_t st, const StepSpace& ws, double2* r = nullptr);
 size_t pointwise_step_bytes(int N);
 // max_j | |a_j| - 1 | over the stored states j = 0..J into *drift (zeroed here)
 cudaError_t launch_drift(const void* a_hat, int mixed, int N, int J, double* drift, cudaStream_t st);

@@ -33,9 +33,12 @@ __device__ __forceinline__ void pointwise_step(const double* __restrict__ Wg,
                                                double2 kappa, void* p_hat, void* y_hat,
                                                size_t vstride, double* __restrict__ g,
                                                double* __restrict__ c, int what,
+                                               double2* __restrict__ rbuf,
                                                unsigned char* smem_raw) {
   const bool wp = what & PW_P, wy = what & PW_Y, wc = what & PW_C;
+  const bool reuse = (what & PW_RUSE) && rbuf && wy && !wp;   // r_j stored by an earlier PW_P
   const bool need_l = wy || wc;
+  const bool need_a = wp || wc || (wy && !reuse);
   const int ld = N + 1;
   double* W = reinterpret_cast<double*>(smem_raw);                     // [N][ld]
   // N (N + 1) is even, so the double2 arrays after W stay 16-byte aligned
@@ -48,7 +51,7 @@ __device__ __forceinline__ void pointwise_step(const double* __restrict__ Wg,
   const double* Wj = Wg + (size_t)j * N * N;
   for (int e = tid; e < N * N; e += nt) W[(e / N) * ld + (e % N)] = Wj[e];
   for (int p = tid; p < N; p += nt) {
-    at[p] = load_state(a_hat, mixed, (size_t)j * N + p);
+    if (need_a) at[p] = load_state(a_hat, mixed, (size_t)j * N + p);
     if (need_l) lt[p] = load_state(l_hat, mixed, (size_t)(j + 1) * N + p);
   }
   __syncthreads();
@@ -57,7 +60,7 @@ __device__ __forceinline__ void pointwise_step(const double* __restrict__ Wg,
     double2 sa = make_double2(0, 0), sl = make_double2(0, 0);
     for (int r = 0; r < N; ++r) {
       double w = W[r * ld + p];
-      sa.x = fma(w, at[r].x, sa.x); sa.y = fma(w, at[r].y, sa.y);
+      if (need_a) { sa.x = fma(w, at[r].x, sa.x); sa.y = fma(w, at[r].y, sa.y); }
       if (need_l) { sl.x = fma(w, lt[r].x, sl.x); sl.y = fma(w, lt[r].y, sl.y); }
     }
     av[p] = sa;
@@ -72,11 +75,13 @@ __device__ __forceinline__ void pointwise_step(const double* __restrict__ Wg,
     for (int q = 0; q < N; ++q) {
       if (wp || wy) {
         const double2 P = Pj[(size_t)q * N + p];          // symmetric: P[p][q] = P[q][p]
-        cfma(r, P, av[q]);
+        if (!reuse) cfma(r, P, av[q]);
         if (wy) cfma_conj(s, P, lv[q]);
       }
       if (wc) cfma(x, Xj[(size_t)q * N + p], av[q]);
     }
+    if (reuse) r = rbuf[(size_t)j * N + p];
+    else if (wp && rbuf) rbuf[(size_t)j * N + p] = r;
     // Re(kappa conj(l~_p) r_p), Re(kappa conj(l~_p) x_p)
     if (wy) gpart += cmul(kappa, cconjmul(lv[p], r)).x;
     if (wc) cpart += cmul(kappa, cconjmul(lv[p], x)).x;
@@ -126,12 +131,12 @@ __global__ void k_pointwise(const double* __restrict__ Wg, const double2* __rest
                             const double2* __restrict__ Xp, const void* a_hat, const void* l_hat,
                             int mixed, int N, int J, double2 kappa, void* p_hat, void* y_hat,
                             size_t vstride, double* __restrict__ g, double* __restrict__ c,
-                            int what, unsigned char* gws, size_t per_cta) {
+                            int what, double2* __restrict__ rbuf, unsigned char* gws, size_t per_cta) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   unsigned char* base = GWS ? gws + (size_t)blockIdx.x * per_cta : smem_raw;
   for (int j = blockIdx.x; j < J; j += gridDim.x) {
     pointwise_step(Wg, Ptil, Xp, a_hat, l_hat, mixed, N, j, kappa, p_hat, y_hat, vstride, g, c,
-                   what, base);
+                   what, rbuf, base);
     __syncthreads();
   }
 }
@@ -169,7 +174,7 @@ size_t pointwise_step_bytes(int N) { return (size_t)N * (N + 1) * 8 + 4 * (size_
 cudaError_t launch_pointwise(const double* W, const double2* Ptil, const double2* Xp,
                              const void* a_hat, const void* l_hat, int mixed, int N, int J,
                              double2 kappa, void* p_hat, void* y_hat, double* g, double* c,
-                             int what, cudaStream_t st, const StepSpace& ws) {
+                             int what, cudaStream_t st, const StepSpace& ws, double2* rbuf) {
   const int threads = N <= 32 ? 32 : (N <= 64 ? 64 : (N <= 128 ? 128 : 256));
   const size_t vstride = ((mixed ? 8 : 16) * (size_t)N + 15) / 16 * 16;
   StepGrid sg;
@@ -177,12 +182,12 @@ cudaError_t launch_pointwise(const double* W, const double2* Ptil, const double2
     return cudaErrorInvalidConfiguration;
   if (sg.gws)
     k_pointwise<true><<<sg.grid, threads, sg.smem, st>>>(W, Ptil, Xp, a_hat, l_hat, mixed, N, J, kappa,
-                                                         p_hat, y_hat, vstride, g, c, what, sg.gws,
-                                                         sg.per_cta);
+                                                         p_hat, y_hat, vstride, g, c, what, rbuf,
+                                                         sg.gws, sg.per_cta);
   else
     k_pointwise<false><<<sg.grid, threads, sg.smem, st>>>(W, Ptil, Xp, a_hat, l_hat, mixed, N, J, kappa,
-                                                          p_hat, y_hat, vstride, g, c, what, sg.gws,
-                                                          sg.per_cta);
+                                                          p_hat, y_hat, vstride, g, c, what, rbuf,
+                                                          sg.gws, sg.per_cta);
   return cudaGetLastError();
 }
 
