@@ -313,6 +313,16 @@ qoc_status qoc_get_phase_times(const qoc_problem* p, double* out, int n);
  *            clean-up (the others finish early after their last update)
  * Synchronises the problem's stream. */
 qoc_status qoc_get_eig_stats(qoc_problem* p, double* out /* [3] */);
+
+/* Device time of the phases of the last qoc_trust_region_solve, in
+ * milliseconds, taken with CUDA events when timing is enabled
+ * (qoc_enable_timing; zeros otherwise):
+ *   out[0] = subproblems and trial points, summed over the iterations
+ *   out[1] = cost-only evaluations at the trial points
+ *   out[2] = gradient + Hessian evaluations (and their eigendecompositions
+ *            for the subproblem when K < 48)
+ * The rest of the solve's wall time is host work and synchronisation. */
+qoc_status qoc_get_tr_phase_times(const qoc_problem* p, double* out /* [3] */);
 qoc_status qoc_enable_timing(qoc_problem* p, int on);
 
 /* Copy an intermediate of the last evaluation to the host, for parity

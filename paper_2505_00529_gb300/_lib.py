@@ -35,6 +35,7 @@ EXPORTS = [
     "qoc_set_panel_columns", "qoc_get_precision", "qoc_measure_fp64_rate",
     "qoc_batch_trust_region_solve", "qoc_trust_region_solve_bfgs", "qoc_tr_subproblem",
     "qoc_eval_grad_hess_model", "qoc_set_refine_sweeps", "qoc_selftest_bounded_wait", "qoc_set_pipeline",
+    "qoc_get_tr_phase_times",
 ]
 
 
@@ -84,6 +85,7 @@ def lib() -> C.CDLL:
         L.qoc_set_panel_columns.argtypes = [C.c_void_p, C.c_int]
         L.qoc_set_refine_sweeps.argtypes = [C.c_void_p, C.c_int]
         L.qoc_set_pipeline.argtypes = [C.c_void_p, C.c_int]
+        L.qoc_get_tr_phase_times.argtypes = [C.c_void_p, _dp]
         L.qoc_selftest_bounded_wait.argtypes = [C.c_void_p, C.c_ulonglong]
         L.qoc_get_precision.argtypes = [C.c_void_p, C.POINTER(C.c_int), _dp]
         L.qoc_measure_fp64_rate.argtypes = [C.c_int, C.c_int, _dp, _dp]
@@ -201,6 +203,13 @@ def qoc_set_block_steps(h, steps):
 
 def qoc_set_panel_columns(h, kc):
     _check(lib().qoc_set_panel_columns(C.c_void_p(h), int(kc)), "qoc_set_panel_columns")
+
+
+def qoc_get_tr_phase_times(h):
+    """Device milliseconds of the last trust-region solve's phases (timing mode)."""
+    out = np.zeros(3)
+    _check(lib().qoc_get_tr_phase_times(C.c_void_p(h), _ptr(out)), "qoc_get_tr_phase_times")
+    return {"subproblem": out[0], "eval_J": out[1], "eval_grad_hess": out[2]}
 
 
 def qoc_set_pipeline(h, chunks):

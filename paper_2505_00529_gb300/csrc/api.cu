@@ -66,6 +66,8 @@ struct qoc_problem {
   int fwd_reused = 0;                   // the last evaluation did
   cudaEvent_t ev_chunk[kMaxChunks] = {};
   cudaEvent_t evp[2 * kMaxChunks] = {}; // timing mode: after each chunk's refinement / increments
+  cudaEvent_t trev[4] = {};             // timing mode: around a trust-region iteration's phases
+  double trphase_ms[3] = {0, 0, 0};     // last solve: subproblem, cost evaluations, grad + Hess evaluations
   cudaEvent_t ev[14] = {};
   double phase_ms[6] = {0, 0, 0, 0, 0, 0};
   double kphase_ms[QOC_N_PHASES] = {};
@@ -618,6 +620,8 @@ void qoc_destroy_problem(qoc_problem* p) {
     if (e) cudaEventDestroy(e);
   for (auto& e : p->evp)
     if (e) cudaEventDestroy(e);
+  for (auto& e : p->trev)
+    if (e) cudaEventDestroy(e);
   for (cudaStream_t* sp : {&p->side, &p->pstream})
     if (*sp) {
       cudaStreamSynchronize(*sp);
@@ -698,6 +702,8 @@ qoc_status qoc_create_problem(int N, const double* H0, const double* M, const do
   for (auto& ev : p->ev)
     if ((e = cudaEventCreate(&ev)) != cudaSuccess) return fail(e);
   for (auto& ev : p->evp)
+    if ((e = cudaEventCreate(&ev)) != cudaSuccess) return fail(e);
+  for (auto& ev : p->trev)
     if ((e = cudaEventCreate(&ev)) != cudaSuccess) return fail(e);
   for (auto& ev : p->ev_chunk)
     if ((e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming)) != cudaSuccess) return fail(e);
@@ -872,6 +878,12 @@ qoc_status qoc_set_panel_columns(qoc_problem* p, int kc) {
   if (!p || kc < 0 || kc > 4) return QOC_EINVAL;
   if (kc > 0 && 32 * ((p->N + 7) / 8) * kc > 1024) return QOC_EUNSUPPORTED;
   p->kc = kc;
+  return QOC_OK;
+}
+
+qoc_status qoc_get_tr_phase_times(const qoc_problem* p, double* out) {
+  if (!p || !out) return QOC_EINVAL;
+  for (int k = 0; k < 3; ++k) out[k] = p->trphase_ms[k];
   return QOC_OK;
 }
 
@@ -1100,16 +1112,24 @@ qoc_status qoc_trust_region_solve(qoc_problem* p, const double* theta0, const qo
   std::memcpy(p->hbuf, theta0, 8 * (size_t)K);
   QOC_TRY(cudaMemcpyAsync(p->theta, p->hbuf, 8 * (size_t)K, cudaMemcpyHostToDevice, st));
   double* hs = p->hbuf + K;   // [J, |g|] and [pred, |s|, sigma, |g|, J_trial]
+  for (double& t : p->trphase_ms) t = 0.0;
+  auto elapsed = [](cudaEvent_t a, cudaEvent_t b) {
+    float ms = 0;
+    return cudaEventElapsedTime(&ms, a, b) == cudaSuccess ? (double)ms : 0.0;
+  };
   // evaluate grad/Hess at theta and factor the Hessian; device status checked here
   auto eval_gh = [&]() -> qoc_status {
+    if (p->timing) cudaEventRecord(p->trev[0], st);
     qoc_status s = enqueue_eval(p, p->theta, 2, p->out);
     if (s != QOC_OK) return s;
     if (tr_needs_eig(K))
       QOC_TRY(launch_eig(p->out + 1 + K, p->trzero, p->trzero, K, 1, p->trwork + 3 * K,
                          p->trwork + 2 * K, p->status, EIG_JACOBI_FP64, 0, 0.0, st, p->ws[0]));
+    if (p->timing) cudaEventRecord(p->trev[1], st);
     QOC_TRY(cudaMemcpyAsync(p->hstatus, p->status, sizeof(int), cudaMemcpyDeviceToHost, st));
     QOC_TRY(cudaMemsetAsync(p->status, 0, sizeof(int), st));
     QOC_TRY(cudaStreamSynchronize(st));
+    if (p->timing) p->trphase_ms[2] += elapsed(p->trev[0], p->trev[1]);
     return device_status(p);
   };
   qoc_status s = eval_gh();
@@ -1119,10 +1139,13 @@ qoc_status qoc_trust_region_solve(qoc_problem* p, const double* theta0, const qo
   int it = 0;
   int stop = 2;
   for (it = 1; it <= opt->max_iter; ++it) {
+    if (p->timing) cudaEventRecord(p->trev[0], st);
     QOC_TRY(launch_tr_subproblem(p->out, K, radius, p->trwork, p->trstep, p->trinfo, p->status, st));
     QOC_TRY(launch_axpy(p->theta, p->trstep, K, p->theta_trial, st));
+    if (p->timing) cudaEventRecord(p->trev[2], st);
     s = enqueue_eval(p, p->theta_trial, 0, p->out_trial);
     if (s != QOC_OK) return s;
+    if (p->timing) cudaEventRecord(p->trev[3], st);
     QOC_TRY(cudaMemcpyAsync(hs, p->trinfo, 4 * sizeof(double), cudaMemcpyDeviceToHost, st));
     QOC_TRY(cudaMemcpyAsync(hs + 4, p->out_trial, sizeof(double), cudaMemcpyDeviceToHost, st));
     QOC_TRY(cudaMemcpyAsync(hs + 5, p->out, sizeof(double), cudaMemcpyDeviceToHost, st));
@@ -1131,6 +1154,10 @@ qoc_status qoc_trust_region_solve(qoc_problem* p, const double* theta0, const qo
     QOC_TRY(cudaStreamSynchronize(st));
     s = device_status(p);
     if (s == QOC_ETIMEOUT || s == QOC_EUNSUPPORTED) return s;
+    if (p->timing) {
+      p->trphase_ms[0] += elapsed(p->trev[0], p->trev[2]);
+      p->trphase_ms[1] += elapsed(p->trev[2], p->trev[3]);
+    }
     const double pred = hs[0], snorm = hs[1], gnorm = hs[3], Jt = hs[4];
     // a trial point whose evaluation failed numerically is a rejected step
     const bool trial_ok = s == QOC_OK && std::isfinite(Jt);

@@ -78,3 +78,19 @@ def test_trust_region_reuses_the_trial_forward_part_exactly(precision):
             assert abs(info["grad_norm"] - gn) <= 1e-14 * max(gn, 1e-300)
             accepted = max(accepted, info["n_eval_gh"] - 1)
         assert accepted >= 2   # the reused evaluations were exercised
+
+
+def test_trust_region_phase_times():
+    """With timing enabled the solve's device phases are measured: each
+    positive, together within the solve's wall time."""
+    import time
+    prob = inputs.small_problem(N=12, K=6, J=240, seed=41, dt=0.05, basis="sine_cosine")
+    with _lib.Problem(prob, precision=_lib.QOC_MIXED_FP32) as P:
+        _lib.qoc_enable_timing(P.handle, 1)
+        t0 = time.perf_counter()
+        _, info = P.trust_region_solve(np.zeros(6), gtol=0.0, xtol=0.0, max_iter=6)
+        wall_ms = 1e3 * (time.perf_counter() - t0)
+        ph = _lib.qoc_get_tr_phase_times(P.handle)
+    assert info["iters"] == 6
+    assert all(v > 0 for v in ph.values()), ph
+    assert sum(ph.values()) <= wall_ms
