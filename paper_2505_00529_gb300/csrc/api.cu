@@ -1695,7 +1695,8 @@ extern "C" qoc_status qoc_batch_trust_region_solve(qoc_problem* const* problems,
     run.slot[i].eig_trial = run.etrial + run.eoff[i];
     run.slot[i].theta = run.thcur + run.toff[i];
   }
-  const TrBatchOptions o{opt->gtol, opt->xtol, opt->radius0, opt->radius_max, opt->eta, opt->max_iter};
+  TrBatchOptions o{opt->gtol, opt->xtol, opt->radius0, opt->radius_max, opt->eta, opt->max_iter};
+  for (int i = 0; i < n; ++i) o.kmax = run.P[i]->K > o.kmax ? run.P[i]->K : o.kmax;
   qoc_status s = tr_rebuild(run);
   if (s != QOC_OK) return s;
   // initial point: theta0 into the trial slots, evaluated and taken as current

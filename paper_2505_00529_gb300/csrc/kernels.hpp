@@ -277,6 +277,7 @@ struct TrSlot {
 struct TrBatchOptions {
   double gtol, xtol, radius0, radius_max, eta;
   int max_iter;
+  int kmax = 0;          // largest K among the problems (sizes the subproblem's shared memory)
 };
 // phase 0: take the evaluated initial point; 1: propose (gtol test,
 // subproblem, trial point); 2: update (ratio test, radius, acceptance, xtol

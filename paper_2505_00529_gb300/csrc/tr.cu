@@ -192,9 +192,15 @@ __device__ double dot_norm(const double* x, int K) {
   return sqrt(s);
 }
 
+// sw: the same work area in this CTA's shared memory (rows of A padded to
+// K + 1 doubles, so that the threads' row-wise matrix-vector reads fall in
+// different banks) when it fits, else nullptr and `work` is used
 __device__ void tr_subproblem_tri_body(const double* __restrict__ gh, int K, double radius,
                                        double* __restrict__ work, double* __restrict__ step,
-                                       double* __restrict__ info, int* status, double* red) {
+                                       double* __restrict__ info, int* status, double* red,
+                                       double* sw = nullptr) {
+  if (sw) work = sw;
+  const int lda = sw ? K + 1 : K;
   double* gt = work;
   double* st = gt + K;
   double* a = st + K;
@@ -207,7 +213,7 @@ __device__ void tr_subproblem_tri_body(const double* __restrict__ gh, int K, dou
   const double* H = gh + 1 + K;
   const double* g = gh + 1;
   const int tid = threadIdx.x, nt = blockDim.x;
-  for (int e = tid; e < K * K; e += nt) A[e] = H[e];
+  for (int e = tid; e < K * K; e += nt) A[(size_t)(e / K) * lda + e % K] = H[e];
   for (int l = tid; l < K; l += nt) gt[l] = g[l];
   __syncthreads();
   // ---- Householder reduction: column k below the diagonal -> b_k e_1 ----
@@ -215,18 +221,18 @@ __device__ void tr_subproblem_tri_body(const double* __restrict__ gh, int K, dou
     const int n = K - k - 1;
     double xs = 0;
     for (int i = tid; i < n; i += nt) {
-      const double x = A[(size_t)(k + 1 + i) * K + k];
+      const double x = A[(size_t)(k + 1 + i) * lda + k];
       xs = fma(x, x, xs);
     }
     xs = block_sum(xs, red);
-    const double x0 = A[(size_t)(k + 1) * K + k];
+    const double x0 = A[(size_t)(k + 1) * lda + k];
     const double nrm = sqrt(xs);
     const double alpha = x0 >= 0 ? -nrm : nrm;
     const double vtv = xs - 2.0 * alpha * x0 + alpha * alpha;
     const double beta = (nrm > 0 && vtv > 0) ? 2.0 / vtv : 0.0;
-    for (int i = tid; i < n; i += nt) u[i] = i == 0 ? x0 - alpha : A[(size_t)(k + 1 + i) * K + k];
+    for (int i = tid; i < n; i += nt) u[i] = i == 0 ? x0 - alpha : A[(size_t)(k + 1 + i) * lda + k];
     if (tid == 0) {
-      a[k] = A[(size_t)k * K + k];
+      a[k] = A[(size_t)k * lda + k];
       b[k] = beta != 0.0 ? alpha : x0;
       bet[k] = beta;
     }
@@ -235,7 +241,7 @@ __device__ void tr_subproblem_tri_body(const double* __restrict__ gh, int K, dou
       // p = beta A22 u, then w = p - (beta/2)(p^T u) u, A22 -= u w^T + w u^T
       double pu = 0;
       for (int i = tid; i < n; i += nt) {
-        const double* row = A + (size_t)(k + 1 + i) * K + (k + 1);
+        const double* row = A + (size_t)(k + 1 + i) * lda + (k + 1);
         double acc = 0;
         for (int j = 0; j < n; ++j) acc = fma(row[j], u[j], acc);
         w[i] = beta * acc;
@@ -247,19 +253,19 @@ __device__ void tr_subproblem_tri_body(const double* __restrict__ gh, int K, dou
       __syncthreads();
       for (int e = tid; e < n * n; e += nt) {
         const int i = e / n, j = e % n;
-        A[(size_t)(k + 1 + i) * K + (k + 1 + j)] -= u[i] * w[j] + w[i] * u[j];
+        A[(size_t)(k + 1 + i) * lda + (k + 1 + j)] -= u[i] * w[j] + w[i] * u[j];
       }
     }
     // the reflector's vector replaces column k below the diagonal
-    for (int i = tid; i < n; i += nt) A[(size_t)(k + 1 + i) * K + k] = u[i];
+    for (int i = tid; i < n; i += nt) A[(size_t)(k + 1 + i) * lda + k] = u[i];
     __syncthreads();
   }
   if (tid == 0) {
     if (K >= 2) {
-      a[K - 2] = A[(size_t)(K - 2) * K + (K - 2)];
-      b[K - 2] = A[(size_t)(K - 1) * K + (K - 2)];
+      a[K - 2] = A[(size_t)(K - 2) * lda + (K - 2)];
+      b[K - 2] = A[(size_t)(K - 1) * lda + (K - 2)];
     }
-    a[K - 1] = A[(size_t)(K - 1) * K + (K - 1)];
+    a[K - 1] = A[(size_t)(K - 1) * lda + (K - 1)];
   }
   __syncthreads();
   // ---- gt = Q^T g: reflectors 0 .. K-3 in order ----
@@ -268,9 +274,9 @@ __device__ void tr_subproblem_tri_body(const double* __restrict__ gh, int K, dou
     const double beta = bet[k];
     if (beta == 0.0) continue;   // uniform
     double vg = 0;
-    for (int i = tid; i < n; i += nt) vg = fma(A[(size_t)(k + 1 + i) * K + k], gt[k + 1 + i], vg);
+    for (int i = tid; i < n; i += nt) vg = fma(A[(size_t)(k + 1 + i) * lda + k], gt[k + 1 + i], vg);
     vg = block_sum(vg, red);
-    for (int i = tid; i < n; i += nt) gt[k + 1 + i] -= beta * vg * A[(size_t)(k + 1 + i) * K + k];
+    for (int i = tid; i < n; i += nt) gt[k + 1 + i] -= beta * vg * A[(size_t)(k + 1 + i) * lda + k];
     __syncthreads();
   }
   // ---- lowest eigenvalue of T: multisection of the Gershgorin bracket, each
@@ -392,9 +398,9 @@ __device__ void tr_subproblem_tri_body(const double* __restrict__ gh, int K, dou
     const double beta = bet[k];
     if (beta == 0.0) continue;
     double vs = 0;
-    for (int i = tid; i < n; i += nt) vs = fma(A[(size_t)(k + 1 + i) * K + k], step[k + 1 + i], vs);
+    for (int i = tid; i < n; i += nt) vs = fma(A[(size_t)(k + 1 + i) * lda + k], step[k + 1 + i], vs);
     vs = block_sum(vs, red);
-    for (int i = tid; i < n; i += nt) step[k + 1 + i] -= beta * vs * A[(size_t)(k + 1 + i) * K + k];
+    for (int i = tid; i < n; i += nt) step[k + 1 + i] -= beta * vs * A[(size_t)(k + 1 + i) * lda + k];
     __syncthreads();
   }
   for (int l = tid; l < K; l += nt)
@@ -402,14 +408,21 @@ __device__ void tr_subproblem_tri_body(const double* __restrict__ gh, int K, dou
   __syncthreads();
 }
 
+// shared memory of the tridiagonal subproblem's work area (A padded to K + 1)
+constexpr size_t kTriSmemMax = 200 * 1024;
+static inline size_t tri_smem_bytes(int K) {
+  return (8 * (size_t)K + (size_t)K * (K + 1)) * sizeof(double);
+}
+
 // method: 0 by K (eigendecomposition below kTriMin), 1 eigendecomposition, 2 tridiagonal
 __global__ void k_tr_subproblem(const double* __restrict__ gh, const double* __restrict__ Q,
                                 const double* __restrict__ d, int K, double radius,
                                 double* __restrict__ work, double* __restrict__ step,
-                                double* __restrict__ info, int* status, int method) {
+                                double* __restrict__ info, int* status, int method, int use_sw) {
   __shared__ double red[32];
+  extern __shared__ __align__(16) double dsm[];
   const bool tri = method == 2 || (method == 0 && !tr_needs_eig(K));
-  if (tri) tr_subproblem_tri_body(gh, K, radius, work, step, info, status, red);
+  if (tri) tr_subproblem_tri_body(gh, K, radius, work, step, info, status, red, use_sw ? dsm : nullptr);
   else tr_subproblem_body(gh, Q, d, K, radius, work, step, info, status, red);
 }
 
@@ -423,8 +436,9 @@ __global__ void k_tr_subproblem(const double* __restrict__ gh, const double* __r
 // ---------------------------------------------------------------------------
 
 // first half of iteration `it`: gtol test, subproblem, trial point
-__global__ void k_tr_batch_propose(TrSlot* slots, int n, int it, double gtol) {
+__global__ void k_tr_batch_propose(TrSlot* slots, int n, int it, double gtol, int use_sw) {
   __shared__ double red[32];
+  extern __shared__ __align__(16) double dsm[];
   const int i = blockIdx.x;
   if (i >= n) return;
   TrSlot& t = slots[i];
@@ -446,7 +460,8 @@ __global__ void k_tr_batch_propose(TrSlot* slots, int n, int it, double gtol) {
     tr_subproblem_body(t.gh, t.work + 3 * K, t.work + 2 * K, K, t.radius, t.work, t.step, t.info,
                        t.status, red);
   else
-    tr_subproblem_tri_body(t.gh, K, t.radius, t.work, t.step, t.info, t.status, red);
+    tr_subproblem_tri_body(t.gh, K, t.radius, t.work, t.step, t.info, t.status, red,
+                           use_sw ? dsm : nullptr);
   const double pred = t.info[0];
   if (!(pred > 0) || !isfinite(pred)) {
     if (threadIdx.x == 0) { t.stop = 3; t.iters = it; t.active = 0; }
@@ -609,7 +624,12 @@ cudaError_t launch_tr_batch(int phase, TrSlot* slots, int n, int it, const TrBat
                             cudaStream_t st) {
   if (n < 1) return cudaSuccess;
   if (phase == 0) k_tr_batch_init<<<n, 128, 0, st>>>(slots, n, o.radius0);
-  else if (phase == 1) k_tr_batch_propose<<<n, 128, 0, st>>>(slots, n, it, o.gtol);
+  else if (phase == 1) {
+    const size_t sw = tri_smem_bytes(o.kmax);
+    set_max_smem((const void*)k_tr_batch_propose);
+    const bool fits = o.kmax >= kTriMin && sw <= kTriSmemMax;
+    k_tr_batch_propose<<<n, 128, fits ? sw : 0, st>>>(slots, n, it, o.gtol, fits ? 1 : 0);
+  }
   else k_tr_batch_update<<<n, 128, 0, st>>>(slots, n, it, o.max_iter, o.xtol, o.radius_max, o.eta);
   return cudaGetLastError();
 }
@@ -628,8 +648,12 @@ cudaError_t launch_tr_subproblem(const double* out_gh, int K, double radius, dou
   // work + 2K (d) and work + 3K (Q)
   const double* d = work + 2 * K;
   const double* Q = work + 3 * K;
-  k_tr_subproblem<<<1, K >= kTriMin ? 256 : 128, 0, st>>>(out_gh, Q, d, K, radius, work, step, info,
-                                                           status, method);
+  const bool tri = method == 2 || (method == 0 && !tr_needs_eig(K));
+  const size_t sw = tri_smem_bytes(K);
+  const bool fits = tri && sw <= kTriSmemMax;
+  if (fits) set_max_smem((const void*)k_tr_subproblem);
+  k_tr_subproblem<<<1, K >= kTriMin ? 256 : 128, fits ? sw : 0, st>>>(out_gh, Q, d, K, radius, work, step,
+                                                                     info, status, method, fits ? 1 : 0);
   return cudaGetLastError();
 }
 
