@@ -173,6 +173,21 @@ __device__ void tri_solve(const double* a, const double* b, int K, double sigma,
   for (int i = K - 2; i >= 0; --i) x[i] = x[i] / dd[i] - l[i + 1] * x[i + 1];
 }
 
+// Binary32 version of tri_solve for the secular equation's starting point;
+// l is recomputed from dd in the backward pass, so only dd is stored.
+__device__ void tri_solve_f(const float* a, const float* b, int K, float sigma, const float* r, float* x,
+                            float* dd) {
+  dd[0] = a[0] + sigma;
+  x[0] = r[0];
+  for (int i = 1; i < K; ++i) {
+    const float l = __fdividef(b[i - 1], dd[i - 1]);
+    dd[i] = (a[i] + sigma) - l * b[i - 1];
+    x[i] = r[i] - l * x[i - 1];
+  }
+  x[K - 1] = __fdividef(x[K - 1], dd[K - 1]);
+  for (int i = K - 2; i >= 0; --i) x[i] = __fdividef(x[i], dd[i]) - __fdividef(b[i], dd[i]) * x[i + 1];
+}
+
 // number of eigenvalues of T below x (Sturm sequence of the LDL^T pivots)
 __device__ int sturm_count(const double* a, const double* b, int K, double x) {
   int cnt = 0;
@@ -268,17 +283,21 @@ __device__ void tr_subproblem_tri_body(const double* __restrict__ gh, int K, dou
     a[K - 1] = A[(size_t)(K - 1) * lda + (K - 1)];
   }
   __syncthreads();
-  // ---- gt = Q^T g: reflectors 0 .. K-3 in order ----
-  for (int k = 0; k + 2 < K; ++k) {
-    const int n = K - k - 1;
-    const double beta = bet[k];
-    if (beta == 0.0) continue;   // uniform
-    double vg = 0;
-    for (int i = tid; i < n; i += nt) vg = fma(A[(size_t)(k + 1 + i) * lda + k], gt[k + 1 + i], vg);
-    vg = block_sum(vg, red);
-    for (int i = tid; i < n; i += nt) gt[k + 1 + i] -= beta * vg * A[(size_t)(k + 1 + i) * lda + k];
-    __syncthreads();
+  // ---- gt = Q^T g: reflectors 0 .. K-3 in order, by one warp (a chain of
+  // short dot products: warp shuffles instead of a block barrier each) ----
+  if (tid < 32) {
+    for (int k = 0; k + 2 < K; ++k) {
+      const int n = K - k - 1;
+      const double beta = bet[k];
+      if (beta == 0.0) continue;   // uniform
+      double vg = 0;
+      for (int i = tid; i < n; i += 32) vg = fma(A[(size_t)(k + 1 + i) * lda + k], gt[k + 1 + i], vg);
+      vg = warp_sum(vg);
+      for (int i = tid; i < n; i += 32) gt[k + 1 + i] -= beta * vg * A[(size_t)(k + 1 + i) * lda + k];
+      __syncwarp();
+    }
   }
+  __syncthreads();
   // ---- lowest eigenvalue of T: multisection of the Gershgorin bracket, each
   // thread taking one Sturm count per round (the interval shrinks nt + 1 fold) ----
   __shared__ double ms_lo, ms_hi;
@@ -356,6 +375,44 @@ __device__ void tr_subproblem_tri_body(const double* __restrict__ gh, int K, dou
         shi *= 2.0;
       }
       double sig = shi, slo = slo0;
+      {
+        // Starting point: the same safeguarded Newton iteration in binary32
+        // (a binary64 instruction occupies its pipe for every lane, and this
+        // runs on one thread), to about 1e-5; the binary64 iteration below
+        // then converges from it in two or three steps.  u and w hold the
+        // binary32 T, right-hand side, solution and pivots, step the
+        // derivative solve.
+        float* af = reinterpret_cast<float*>(u);
+        float* bf = af + K;
+        float* zf = reinterpret_cast<float*>(w);
+        float* xf = zf + K;
+        float* df = reinterpret_cast<float*>(step);
+        float* yf = df + K;
+        for (int i = 0; i < K; ++i) {
+          af[i] = (float)a[i];
+          bf[i] = (float)b[i];
+          zf[i] = (float)z[i];
+        }
+        float fs = (float)shi, flo = (float)slo, fhi = (float)shi;
+        const float fr = (float)radius;
+        for (int itn = 0; itn < 60; ++itn) {
+          tri_solve_f(af, bf, K, fs, zf, xf, df);
+          float n2 = 0.f;
+          for (int i = 0; i < K; ++i) n2 = fmaf(xf[i], xf[i], n2);
+          const float ns = sqrtf(n2);
+          if (!(ns > 0.f) || fabsf(ns - fr) <= 1e-5f * fr) break;
+          const float phi = 1.f / ns - 1.f / fr;
+          if (phi < 0.f) flo = fs; else fhi = fs;
+          tri_solve_f(af, bf, K, fs, xf, yf, df);
+          float d2 = 0.f;
+          for (int i = 0; i < K; ++i) d2 = fmaf(xf[i], yf[i], d2);
+          const float dphi = d2 / (ns * ns * ns);
+          float nw = fs - phi / dphi;
+          if (!(nw > flo && nw < fhi)) nw = 0.5f * (flo + fhi);
+          fs = nw;
+        }
+        if (isfinite(fs) && (double)fs > slo && (double)fs < shi) sig = (double)fs;
+      }
       for (int itn = 0; itn < 200; ++itn) {
         tri_solve(a, b, K, sig, z, st, u, w);
         const double ns = dot_norm(st, K);
@@ -393,16 +450,19 @@ __device__ void tr_subproblem_tri_body(const double* __restrict__ gh, int K, dou
   // ---- s = Q st: reflectors K-3 .. 0 ----
   for (int l = tid; l < K; l += nt) step[l] = st[l];
   __syncthreads();
-  for (int k = K - 3; k >= 0; --k) {
-    const int n = K - k - 1;
-    const double beta = bet[k];
-    if (beta == 0.0) continue;
-    double vs = 0;
-    for (int i = tid; i < n; i += nt) vs = fma(A[(size_t)(k + 1 + i) * lda + k], step[k + 1 + i], vs);
-    vs = block_sum(vs, red);
-    for (int i = tid; i < n; i += nt) step[k + 1 + i] -= beta * vs * A[(size_t)(k + 1 + i) * lda + k];
-    __syncthreads();
+  if (tid < 32) {   // one warp, as for Q^T g
+    for (int k = K - 3; k >= 0; --k) {
+      const int n = K - k - 1;
+      const double beta = bet[k];
+      if (beta == 0.0) continue;
+      double vs = 0;
+      for (int i = tid; i < n; i += 32) vs = fma(A[(size_t)(k + 1 + i) * lda + k], step[k + 1 + i], vs);
+      vs = warp_sum(vs);
+      for (int i = tid; i < n; i += 32) step[k + 1 + i] -= beta * vs * A[(size_t)(k + 1 + i) * lda + k];
+      __syncwarp();
+    }
   }
+  __syncthreads();
   for (int l = tid; l < K; l += nt)
     if (!isfinite(step[l])) raise_status(status, DEV_NONFINITE);
   __syncthreads();
