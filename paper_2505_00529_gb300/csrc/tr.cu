@@ -188,14 +188,15 @@ __device__ void tri_solve_f(const float* a, const float* b, int K, float sigma, 
   for (int i = K - 2; i >= 0; --i) x[i] = __fdividef(x[i], dd[i]) - __fdividef(b[i], dd[i]) * x[i + 1];
 }
 
-// number of eigenvalues of T below x (Sturm sequence of the LDL^T pivots)
-__device__ int sturm_count(const double* a, const double* b, int K, double x) {
+// number of eigenvalues of T below x (Sturm sequence of the LDL^T pivots);
+// b2[i] = b[i]^2
+__device__ int sturm_count(const double* a, const double* b2, int K, double x) {
   int cnt = 0;
   double q = a[0] - x;
   if (q < 0) ++cnt;
   for (int i = 1; i < K; ++i) {
     if (q == 0) q = 1e-300;
-    q = (a[i] - x) - b[i - 1] * b[i - 1] / q;
+    q = (a[i] - x) - b2[i - 1] / q;
     if (q < 0) ++cnt;
   }
   return cnt;
@@ -298,10 +299,17 @@ __device__ void tr_subproblem_tri_body(const double* __restrict__ gh, int K, dou
     }
   }
   __syncthreads();
-  // ---- lowest eigenvalue of T: multisection of the Gershgorin bracket, each
-  // thread taking one Sturm count per round (the interval shrinks nt + 1 fold) ----
+  // ---- lowest eigenvalue of T: multisection of the Gershgorin bracket, mp
+  // threads taking one Sturm count each per round (the interval shrinks
+  // mp + 1 fold).  At most 128 points: every warp issuing a binary64 Sturm
+  // chain occupies its sub-partition's pipe, so a second warp per
+  // sub-partition costs as much as it gains.  Down to 1e-13 of the values
+  // (the hard case shifts by 1e-12 of |lambda_min|).  b^2 in w (free until
+  // the secular equation). ----
   __shared__ double ms_lo, ms_hi;
   __shared__ int ms_first;
+  const int mp = nt < 128 ? nt : 128;
+  for (int i = tid; i + 1 < K; i += nt) w[i] = b[i] * b[i];
   if (tid == 0) {
     double glo = a[0], ghi = a[0];
     for (int i = 0; i < K; ++i) {
@@ -315,16 +323,18 @@ __device__ void tr_subproblem_tri_body(const double* __restrict__ gh, int K, dou
   __syncthreads();
   for (int round = 0; round < 64; ++round) {
     const double lo = ms_lo, hi = ms_hi;
-    if (!(hi - lo > 1e-15 * fmax(fabs(lo), fabs(hi)) + 1e-300)) break;   // uniform
-    if (tid == 0) ms_first = nt;
+    if (!(hi - lo > 1e-13 * fmax(fabs(lo), fabs(hi)) + 1e-300)) break;   // uniform
+    if (tid == 0) ms_first = mp;
     __syncthreads();
-    const double x = lo + (hi - lo) * ((double)(tid + 1) / (double)(nt + 1));
-    if (x > lo && x < hi && sturm_count(a, b, K, x) >= 1) atomicMin(&ms_first, tid);
+    if (tid < mp) {
+      const double x = lo + (hi - lo) * ((double)(tid + 1) / (double)(mp + 1));
+      if (x > lo && x < hi && sturm_count(a, w, K, x) >= 1) atomicMin(&ms_first, tid);
+    }
     __syncthreads();
     if (tid == 0) {
       const int t = ms_first;   // smallest point with an eigenvalue below it
-      const double nlo = t == 0 ? lo : lo + (hi - lo) * ((double)t / (double)(nt + 1));
-      const double nhi = t == nt ? hi : lo + (hi - lo) * ((double)(t + 1) / (double)(nt + 1));
+      const double nlo = t == 0 ? lo : lo + (hi - lo) * ((double)t / (double)(mp + 1));
+      const double nhi = t == mp ? hi : lo + (hi - lo) * ((double)(t + 1) / (double)(mp + 1));
       ms_lo = nlo;
       ms_hi = nhi;
     }
