@@ -21,7 +21,7 @@ BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libqoc.so")
 
 SOURCES = ["api.cu", "eig.cu", "prep.cu", "sweep.cu", "block.cu", "pointwise.cu", "assemble.cu", "tr.cu",
-           "mlp.cu", "mlp_api.cu", "noalloc.cu", "peak.cu"]
+           "mlp.cu", "mlp_api.cu", "noalloc.cu", "peak.cu", "jacobi32.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE,
          "--expt-relaxed-constexpr"]

@@ -82,6 +82,7 @@ struct qoc_problem {
   double *V = nullptr, *U = nullptr, *work = nullptr, *out = nullptr, *out_trial = nullptr;
   double *hess_raw = nullptr, *scal = nullptr;
   unsigned int* eigstats = nullptr;     // refinement counters (timing mode)
+  int* eigorder = nullptr;              // J + 2 ints: the refinement's step order and its counters
   double2 *alpha = nullptr, *beta = nullptr, *Ptil = nullptr, *Xp = nullptr, *SJ = nullptr,
           *lamJ = nullptr;
   double* Mtil = nullptr;               // M~_j = W_j^T M W_j (three-stream schedule)
@@ -459,7 +460,7 @@ qoc_status enqueue_eval(qoc_problem* p, const double* theta_dev, int order, doub
     QOC_TRY(launch_eig(p->H0, p->M, p->f, N, J, p->W, p->eig, p->status,
                        p->eig_method == QOC_EIG_JACOBI_FP64 ? EIG_JACOBI_FP64 : EIG_REFINED,
                        p->refine_sweeps, p->angle_tol, st, p->ws[0], p->timing ? p->ev[8] : nullptr,
-                       p->timing ? p->eigstats : nullptr, eig_finish_tol(p)));
+                       p->timing ? p->eigstats : nullptr, eig_finish_tol(p), EIG_PHASE_ALL, p->eigorder));
     if (p->timing) cudaEventRecord(p->ev[1], st);
     QOC_TRY(launch_prep(p->W, p->eig, p->M, N, J, p->dt, p->mshift, p->D, p->dstride, d_fp64, PREP_D,
                         p->Ptil, p->Xp, nullptr, p->status, st, p->ws[0]));
@@ -737,6 +738,7 @@ qoc_status qoc_create_problem(int N, const double* H0, const double* M, const do
   ALLOC(p->hess_raw, 8 * (size_t)K * K);
   ALLOC(p->scal, 8 * 8);
   ALLOC(p->eigstats, 4 * sizeof(unsigned int));
+  ALLOC(p->eigorder, sizeof(int) * ((size_t)J + 2));
   ALLOC(p->alpha, 16 * (size_t)N);
   ALLOC(p->beta, 16 * (size_t)N);
   ALLOC(p->lamJ, 16 * (size_t)N);
@@ -1323,7 +1325,8 @@ qoc_status batch_phase(qoc_batch* b, int i, int phase, cudaStream_t s) {
       QOC_TRY(launch_control(p->B, p->Kp, p->theta, J, K, p->f, s));
       QOC_TRY(launch_eig(p->H0, p->M, p->f, N, J, p->W, p->eig, p->status,
                          p->eig_method == QOC_EIG_JACOBI_FP64 ? EIG_JACOBI_FP64 : EIG_REFINED,
-                         p->refine_sweeps, p->angle_tol, s, p->ws[0], nullptr, nullptr, eig_finish_tol(p)));
+                         p->refine_sweeps, p->angle_tol, s, p->ws[0], nullptr, nullptr, eig_finish_tol(p),
+                         EIG_PHASE_ALL, p->eigorder));
       QOC_TRY(launch_prep(p->W, p->eig, p->M, N, J, p->dt, p->mshift, p->D, p->dstride, mixed ? 0 : 1,
                           PREP_D | PREP_P | PREP_X, p->Ptil, p->Xp, nullptr, p->status, s, p->ws[0]));
       QOC_TRY(launch_block_delta(p->D, p->dstride, N, J, bs, 0, mixed, p->Mf, p->mstride, s, p->ws[0]));

@@ -596,10 +596,13 @@ k_eig_refine(const double* __restrict__ H0, const double* __restrict__ M,
                              const double* __restrict__ f, int N, int J, int sweeps,
                              double angle_tol, double* __restrict__ W_io,
                              double* __restrict__ eig_out, int* status, unsigned int* stats,
-                             double finish_tol, unsigned char* gws, size_t per_cta) {
+                             double finish_tol, unsigned char* gws, size_t per_cta,
+                             const int* __restrict__ order) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   unsigned char* base = GWS ? gws + (size_t)blockIdx.x * per_cta : smem_raw;
-  for (int j = blockIdx.x; j < J; j += gridDim.x) {
+  for (int b = blockIdx.x; b < J; b += gridDim.x) {
+    int j = order ? order[b] : b;   // a permutation of the steps
+    if ((unsigned)j >= (unsigned)J) j = b;
     eig_refine_step<OZ>(H0, M, f, N, j, sweeps, angle_tol, W_io, eig_out, status, stats, finish_tol, base);
     __syncthreads();
   }
@@ -873,6 +876,12 @@ __global__ void __launch_bounds__(128) k_eig_jacobi32(const double* __restrict__
   }
 }
 
+// rounds per loop body of the register-resident N = 32 start (0: the
+// shared-memory kernel below for N = 32 too)
+#ifndef QOC_JACOBI32_ROUNDS
+#define QOC_JACOBI32_ROUNDS 4
+#endif
+
 static int jacobi32_mpb(int N) { return N <= 16 ? 4 : (N <= 40 ? 2 : 1); }
 
 static size_t jacobi_smem(int N, size_t tsize) {
@@ -897,7 +906,7 @@ static size_t refine_smem(int N) {
 cudaError_t launch_eig(const double* H0, const double* M, const double* f, int N, int J,
                        double* W, double* eig, int* status, int method, int refine_sweeps,
                        double angle_tol, cudaStream_t st, const StepSpace& ws, cudaEvent_t mid,
-                       unsigned int* stats, double finish_tol, int phases) {
+                       unsigned int* stats, double finish_tol, int phases, int* order) {
   // Jacobi rounds are barrier-bound: few warps per (small) matrix, many CTAs per SM
   const int jthreads = N <= 32 ? 64 : (N <= 64 ? 128 : (N <= 128 ? 256 : 512));
   const int threads = N <= 16 ? 128 : (N <= 128 ? 256 : 512);   // refinement: binary64-bound
@@ -914,7 +923,12 @@ cudaError_t launch_eig(const double* H0, const double* M, const double* f, int N
     if (mid) cudaEventRecord(mid, st);
     return cudaGetLastError();
   }
+  if (!(phases & EIG_PHASE_START) || !(N == 32 && QOC_JACOBI32_ROUNDS > 0)) order = nullptr;
   if (!(phases & EIG_PHASE_START)) {
+  } else if (N == 32 && QOC_JACOBI32_ROUNDS > 0) {
+    if (phases != EIG_PHASE_ALL) order = nullptr;
+    const cudaError_t e = launch_eig_jacobi32_reg(H0, M, f, J, W, eig, status, QOC_JACOBI32_ROUNDS, order, st);
+    if (e != cudaSuccess) return e;
   } else if (N <= 64) {
     const int mpb = jacobi32_mpb(N);
     const size_t sm = (size_t)mpb * jacobi32_slot_floats(N) * sizeof(float);
@@ -939,7 +953,7 @@ cudaError_t launch_eig(const double* H0, const double* M, const double* f, int N
     const size_t sm = refine_oz_smem(N);
     if (sm <= max_dyn_smem((const void*)k_eig_refine<256, false, true>)) {
       k_eig_refine<256, false, true><<<J, 256, sm, st>>>(H0, M, f, N, J, refine_sweeps, angle_tol, W, eig,
-                                                         status, stats, finish_tol, nullptr, 0);
+                                                         status, stats, finish_tol, nullptr, 0, order);
       return cudaGetLastError();
     }
   }
@@ -948,19 +962,19 @@ cudaError_t launch_eig(const double* H0, const double* M, const double* f, int N
       return cudaErrorInvalidConfiguration;
     if (g.gws)
       k_eig_refine<256, true><<<g.grid, threads, g.smem, st>>>(H0, M, f, N, J, refine_sweeps, angle_tol,
-                                                               W, eig, status, stats, finish_tol, g.gws, g.per_cta);
+                                                               W, eig, status, stats, finish_tol, g.gws, g.per_cta, order);
     else
       k_eig_refine<256, false><<<g.grid, threads, g.smem, st>>>(H0, M, f, N, J, refine_sweeps, angle_tol,
-                                                                W, eig, status, stats, finish_tol, g.gws, g.per_cta);
+                                                                W, eig, status, stats, finish_tol, g.gws, g.per_cta, order);
   } else {
     if (!step_grid(refine_smem(N), J, ws, (const void*)k_eig_refine<512, false>, g))
       return cudaErrorInvalidConfiguration;
     if (g.gws)
       k_eig_refine<512, true><<<g.grid, threads, g.smem, st>>>(H0, M, f, N, J, refine_sweeps, angle_tol,
-                                                               W, eig, status, stats, finish_tol, g.gws, g.per_cta);
+                                                               W, eig, status, stats, finish_tol, g.gws, g.per_cta, order);
     else
       k_eig_refine<512, false><<<g.grid, threads, g.smem, st>>>(H0, M, f, N, J, refine_sweeps, angle_tol,
-                                                                W, eig, status, stats, finish_tol, g.gws, g.per_cta);
+                                                                W, eig, status, stats, finish_tol, g.gws, g.per_cta, order);
   }
   return cudaGetLastError();
 }

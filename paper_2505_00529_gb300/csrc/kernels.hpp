@@ -108,14 +108,23 @@ constexpr double TAU_DD2 = 1e-3;
 // the parts of a refined eigendecomposition a launch_eig call enqueues: the
 // binary32 start, the binary64 refinement (which reads the start from W), or
 // both; the refinement of steps [j0, j1) alone takes f + j0, W + j0 N^2,
-// eig + j0 N and J = j1 - j0
+// eig + j0 N and J = j1 - j0.  order (optional, device, J + 2 ints): with
+// both phases in one call, the binary32 start may write a step order for the
+// refinement into it (near-degenerate steps first)
 enum { EIG_PHASE_START = 1, EIG_PHASE_REFINE = 2, EIG_PHASE_ALL = 3 };
 cudaError_t launch_eig(const double* H0, const double* M, const double* f, int N, int J,
                        double* W, double* eig, int* status, int method, int refine_sweeps,
                        double angle_tol, cudaStream_t st, const StepSpace& ws,
                        cudaEvent_t mid = nullptr, unsigned int* stats = nullptr,
-                       double finish_tol = 0.0, int phases = EIG_PHASE_ALL);
+                       double finish_tol = 0.0, int phases = EIG_PHASE_ALL, int* order = nullptr);
 size_t eig_step_bytes(int N);   // largest per-matrix storage of the eigensolver kernels
+// binary32 Jacobi start for N = 32 exactly, the matrix in registers (one warp
+// per step); rounds_per_body 4, 8 or 31 (the unrolled loop body).  order
+// (optional, device, J + 2 ints): receives a permutation of the steps with the
+// near-degenerate ones first ([J], [J + 1] are its counters, zeroed here)
+cudaError_t launch_eig_jacobi32_reg(const double* H0, const double* M, const double* f, int J,
+                                    double* W, double* eig, int* status, int rounds_per_body,
+                                    int* order, cudaStream_t st);
 
 size_t prep_smem_bytes(int N);
 // parts (bit mask): 1 -> D_j = W diag(exp(-i dt (lambda - m)) - 1) W^T
