@@ -368,6 +368,8 @@ def run_ours(args):
                 "config": dict(WORKLOAD, precision=args.precision, l2="flushed between timed steps",
                                parallelism=f"replicas x{world}" if world > 1 else "single problem",
                                pipeline_chunks=args.pipeline if args.pipeline >= 0 else "library choice (off)",
+                               hessian="second-order adjoint, terminal part in closed form "
+                                       "(qoc_set_mu_split default: mu and tangent panels side by side)",
                                launch=({"block_steps": tuned[prec]["block_steps"],
                                         "panel_columns": tuned[prec]["panel_columns"],
                                         "autotune_table_ms": tuned[prec]["table"]}

@@ -146,6 +146,33 @@ qoc_status qoc_set_block_steps(qoc_problem* p, int steps);
  * the chain's overlap gains).  QOC_EINVAL otherwise. */
 qoc_status qoc_set_pipeline(qoc_problem* p, int chunks);
 
+/* Terminal part of the second-order adjoint in closed form (Sec. III-B,
+ * Eq. musys with its terminal condition mu_J = 2 w_t S_J; a regrouping of
+ * Alg. 2's Hessian sum that changes no result beyond rounding).  The mu
+ * recursion is linear, so mu = mu0 + mu_T: mu0 from the sources y_j with
+ * mu0_J = 0, mu_T the terminal value carried back by the adjoint propagators
+ * alone.  The contraction of mu_T with the tangent sources telescopes to
+ * Re(S_J^H mu_J), so the Hessian is
+ *   B^T diag(2 w_f + c) B + B^T V0 + 2 w_t Re(S_J^H S_J) + B^T U
+ * with V0 from mu0, and the mu sweep no longer waits for the tangent sweep:
+ * on the three-stream schedule (time blocking, Hessian requested) the two
+ * panels run side by side.
+ *   split  1 on: QOC_BUF_V then holds the contraction of mu0;
+ *          0 off: mu starts from mu_J = 2 w_t S_J and QOC_BUF_V holds the full
+ *          contraction;
+ *          -1 (default) the built-in choice: on for binary64 sweeps, off for
+ *          binary32 ones.  Binary32 sweeps round in proportion to the swept
+ *          values, and mu0 can exceed mu where the Hessian is a small
+ *          difference of large terms: on the batched workload's avoided
+ *          crossing (N = 48, K = 32, J = 4000) the split measured a Hessian
+ *          error of 1.22e-6 against 7.6e-7 unsplit, while saving 0.18 ms of
+ *          2.91 at N = 32, K = 64, J = 4000.
+ *          Other values: QOC_EINVAL.
+ * Takes effect at the next evaluation; a batch takes each problem's setting
+ * when it is created (qoc_batch_create).  The per-step (block steps 1)
+ * schedule and the tangent form are unaffected. */
+qoc_status qoc_set_mu_split(qoc_problem* p, int split);
+
 /* Panel columns per CTA of the tangent and second-order adjoint sweeps
  * (1, 2 or 4; 0 restores the built-in choice, 1).  A launch-shape knob; the
  * autotuner in the Python package picks it together with the block steps.
@@ -335,7 +362,8 @@ qoc_status qoc_enable_timing(qoc_problem* p, int on);
  *   QOC_BUF_COSTATE (J+1)*2N: lambda_1..lambda_J in rows 1..J (row 0 = lambda_0)
  *   QOC_BUF_G       J: g_j = Re(lambda_{j+1}^H G_j a_j)
  *   QOC_BUF_C       J: c_j = Re(lambda_{j+1}^H G2_j a_j)
- *   QOC_BUF_V       J*K: Re(mu_{j+1,l}^H G_j a_j)   (second-order-adjoint form only)
+ *   QOC_BUF_V       J*K: Re(mu_{j+1,l}^H G_j a_j)   (second-order-adjoint form only; mu0
+ *                   in place of mu when the terminal part is split, qoc_set_mu_split)
  *   QOC_BUF_U       J*K: Re(lambda_{j+1}^H G_j S_{j,l})
  *   QOC_BUF_SJ      N*K*2: S_J = da_J/dtheta (interleaved complex, row-major N x K)
  *   QOC_BUF_HESS_RAW K*K: Hessian before symmetrisation

@@ -14,7 +14,7 @@ from ._lib import (  # noqa: F401
     qoc_batch_eval_grad_hess, qoc_batch_eval_grad_hess_dev, qoc_batch_set_graph,
     qoc_assemble_grad_hess_noalloc, qoc_assemble_noalloc_scratch_doubles, qoc_get_phase_times, qoc_get_eig_stats, qoc_set_panel_columns,
     qoc_get_precision, QOC_MIXED_FP32_ALWAYS, qoc_measure_fp64_rate, qoc_batch_trust_region_solve, qoc_tr_subproblem,
-    qoc_eval_grad_hess_model, qoc_set_refine_sweeps, qoc_selftest_bounded_wait, qoc_set_pipeline, qoc_get_tr_phase_times,
+    qoc_eval_grad_hess_model, qoc_set_refine_sweeps, qoc_selftest_bounded_wait, qoc_set_pipeline, qoc_get_tr_phase_times, qoc_set_mu_split,
     QOC_FP64, QOC_MIXED_FP32, QOC_HESS_SECOND_ORDER_ADJOINT, QOC_HESS_TANGENT, QOC_EIG_REFINED,
     QOC_EIG_JACOBI_FP64,
 )

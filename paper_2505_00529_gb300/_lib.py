@@ -34,7 +34,7 @@ EXPORTS = [
     "qoc_assemble_grad_hess_noalloc", "qoc_get_phase_times", "qoc_get_eig_stats",
     "qoc_set_panel_columns", "qoc_get_precision", "qoc_measure_fp64_rate",
     "qoc_batch_trust_region_solve", "qoc_trust_region_solve_bfgs", "qoc_tr_subproblem",
-    "qoc_eval_grad_hess_model", "qoc_set_refine_sweeps", "qoc_selftest_bounded_wait", "qoc_set_pipeline",
+    "qoc_eval_grad_hess_model", "qoc_set_refine_sweeps", "qoc_selftest_bounded_wait", "qoc_set_pipeline", "qoc_set_mu_split",
     "qoc_get_tr_phase_times",
 ]
 
@@ -85,6 +85,7 @@ def lib() -> C.CDLL:
         L.qoc_set_panel_columns.argtypes = [C.c_void_p, C.c_int]
         L.qoc_set_refine_sweeps.argtypes = [C.c_void_p, C.c_int]
         L.qoc_set_pipeline.argtypes = [C.c_void_p, C.c_int]
+        L.qoc_set_mu_split.argtypes = [C.c_void_p, C.c_int]
         L.qoc_get_tr_phase_times.argtypes = [C.c_void_p, _dp]
         L.qoc_selftest_bounded_wait.argtypes = [C.c_void_p, C.c_ulonglong]
         L.qoc_get_precision.argtypes = [C.c_void_p, C.POINTER(C.c_int), _dp]
@@ -214,6 +215,10 @@ def qoc_get_tr_phase_times(h):
 
 def qoc_set_pipeline(h, chunks):
     _check(lib().qoc_set_pipeline(C.c_void_p(h), int(chunks)), "qoc_set_pipeline")
+
+
+def qoc_set_mu_split(h, split):
+    _check(lib().qoc_set_mu_split(C.c_void_p(h), int(split)), "qoc_set_mu_split")
 
 
 def qoc_set_refine_sweeps(h, sweeps):
@@ -540,7 +545,7 @@ class Problem:
     H0, M, alpha, beta, B, dt, w_f, w_t (e.g. ``inputs.Problem``)."""
 
     def __init__(self, prob, precision=QOC_FP64, cuda_stream=None, hess_method=None, eig_method=None,
-                 block_steps=None, panel_columns=None):
+                 block_steps=None, panel_columns=None, mu_split=None):
         self.N, self.K, self.J = prob.H0.shape[0], prob.B.shape[1], prob.B.shape[0]
         self.handle = qoc_create_problem(self.N, prob.H0, prob.M, prob.alpha, prob.beta, self.K,
                                          prob.B, prob.dt, self.J, prob.w_f, prob.w_t, precision,
@@ -553,6 +558,8 @@ class Problem:
             qoc_set_block_steps(self.handle, block_steps)
         if panel_columns is not None:
             qoc_set_panel_columns(self.handle, panel_columns)
+        if mu_split is not None:
+            qoc_set_mu_split(self.handle, mu_split)
 
     def eval_J(self, theta):
         return qoc_eval_J(self.handle, theta)

@@ -51,6 +51,8 @@ struct qoc_problem {
   cudaEvent_t ev_bprod = nullptr;       // backward block products done (panel stream)
   cudaEvent_t ev_fprod = nullptr;       // forward block products done (panel stream)
   cudaEvent_t ev_yhat = nullptr;        // y^ and g done, tangent panel swept (panel stream)
+  cudaEvent_t ev_phat = nullptr;        // p^ (and r_j) done (split second-order adjoint)
+  cudaEvent_t ev_tangent = nullptr;     // tangent panel swept (split second-order adjoint)
   int timing = 0;
   int sched = 0;                        // 0 sequential, 1 three-stream (time-blocked, order >= 1)
   // forward pipeline: the refinement and increments in chunks of steps, the
@@ -83,6 +85,11 @@ struct qoc_problem {
   double *hess_raw = nullptr, *scal = nullptr;
   unsigned int* eigstats = nullptr;     // refinement counters (timing mode)
   int* eigorder = nullptr;              // J + 2 ints: the refinement's step order and its counters
+  // second-order adjoint on the three-stream schedule: the mu sweep starts
+  // from zero and the terminal part of its contraction, 2 w_t Re(S_J^H S_J),
+  // is added in the assembly (1), or the sweep starts from mu_J = 2 w_t S_J
+  // (0); -1: 1 for binary64 sweeps, 0 for binary32 ones
+  int mu_split = -1;
   double2 *alpha = nullptr, *beta = nullptr, *Ptil = nullptr, *Xp = nullptr, *SJ = nullptr,
           *lamJ = nullptr;
   double* Mtil = nullptr;               // M~_j = W_j^T M W_j (three-stream schedule)
@@ -220,7 +227,20 @@ BSweepArgs chain_sweep_args(qoc_problem* p, int bwd) {
   return a;
 }
 
-BSweepArgs panel_sweep_args(qoc_problem* p, int bwd) {
+// Whether the second-order adjoint's terminal part is split off (qoc_set_mu_split).
+// Built-in choice: binary64 sweeps only.  With binary32 sweeps the split costs
+// accuracy where the Hessian is a small difference of large terms: mu0 can be
+// larger than mu (the source and terminal parts partly cancel), and the
+// binary32 sweep's rounding scales with it.  Measured on the avoided crossing
+// of the batched workload (N = 48, K = 32, J = 4000, |B^T V| ~ 600 against
+// |H| ~ 50): Hessian error 7.6e-7 unsplit, 1.22e-6 split (target 1e-6); the
+// bench problem (N = 32, K = 64, J = 4000) went 2.91 -> 2.73 ms.
+bool mu_split_on(const qoc_problem* p) {
+  if (p->hess_method != QOC_HESS_SECOND_ORDER_ADJOINT) return false;
+  return p->mu_split < 0 ? p->precision != QOC_MIXED_FP32 : p->mu_split != 0;
+}
+
+BSweepArgs panel_sweep_args(qoc_problem* p, int bwd, bool mu_split = false) {
   BSweepArgs s{};
   const int mixed = p->precision == QOC_MIXED_FP32;
   s.N = p->N; s.K = p->K; s.Kp = p->Kp; s.J = p->J; s.bs = p->bs; s.kc = sweep_kc(p); s.backward = bwd;
@@ -229,7 +249,7 @@ BSweepArgs panel_sweep_args(qoc_problem* p, int bwd) {
   s.Brow = mixed ? static_cast<const void*>(p->Bf) : static_cast<const void*>(p->B);
   s.status = p->status;
   if (bwd) {
-    s.init = p->SJ; s.init_scale = 2.0 * p->w_t; s.Xblk = p->Xmu;
+    s.init = mu_split ? nullptr : p->SJ; s.init_scale = 2.0 * p->w_t; s.Xblk = p->Xmu;
   } else {
     s.final_out = p->SJ; s.Xblk = p->XS;
   }
@@ -312,7 +332,51 @@ qoc_status enqueue_blocked(qoc_problem* p, int order, double* out_dev) {
   QOC_TRY(launch_prep(p->W, p->eig, p->M, N, J, p->dt, p->mshift, p->D, p->dstride, mixed ? 0 : 1,
                       PREP_P, p->Ptil, p->Xp, p->Mtil, p->status, st, p->ws[0]));
   QOC_TRY(cudaEventRecord(p->ev_ptil, st));
-  if (order >= 2) {
+  const bool split = order >= 2 && soa && mu_split_on(p);
+  if (order >= 2 && split) {
+    // ---- panels, split second-order adjoint ----
+    // The mu sweep starts from zero, so it needs the costate and y^ but not
+    // the tangent panel: the tangent sweep runs on the panel stream while the
+    // chain stream, after the costate, goes on to y^ and the mu sweep.
+    QOC_TRY(cudaStreamWaitEvent(ps, p->ev_ptil, 0));
+    QOC_TRY(cudaStreamWaitEvent(ps, p->ev_state, 0));
+    if (p->timing) cudaEventRecord(p->ev[12], ps);
+    QOC_TRY(launch_pointwise(p->W, p->Ptil, p->Xp, p->a_hat, p->l_hat, mixed, N, J, kappa, p->p_hat,
+                             p->y_hat, p->g, p->c, PW_P, ps, p->ws[2], p->rvec));
+    QOC_TRY(cudaEventRecord(p->ev_phat, ps));
+    QOC_TRY(launch_block_src(p->D, p->dstride, N, J, bs, 0, mixed, p->p_hat, p->y_hat, p->vstride,
+                             p->Qf, p->Wf, p->Gf, p->qstride, p->gstride, BS_Q, ps, p->ws[2]));
+    QOC_TRY(launch_bsweep(panel_sweep_args(p, 0), mixed, ps));
+    QOC_TRY(cudaEventRecord(p->ev_tangent, ps));
+    // chain stream: y^ (r_j from the p^ pass), the mu sources, sweep and V
+    QOC_TRY(cudaStreamWaitEvent(cs, p->ev_phat, 0));
+    QOC_TRY(launch_pointwise(p->W, p->Ptil, p->Xp, p->a_hat, p->l_hat, mixed, N, J, kappa, p->p_hat,
+                             p->y_hat, p->g, p->c, PW_Y | PW_RUSE, cs, p->ws[1], p->rvec));
+    QOC_TRY(cudaEventRecord(p->ev_yhat, cs));
+    QOC_TRY(launch_block_src(p->D, p->dstride, N, J, bs, 1, mixed, p->y_hat, p->p_hat, p->vstride,
+                             p->Qb, p->Wb, p->Gb, p->qstride, p->gstride, BS_Q | BS_WG, cs, p->ws[1]));
+    QOC_TRY(launch_bsweep(panel_sweep_args(p, 1, true), mixed, cs));
+    QOC_TRY(launch_block_contract(p->Xmu, p->Wb, p->Gb, p->qstride, p->gstride, Bsrc, p->Kp, N, K,
+                                  J, bs, 1, mixed, p->V, cs));
+    if (p->timing) cudaEventRecord(p->ev[13], cs);
+    QOC_TRY(cudaEventRecord(p->ev_panels, cs));
+    // ---- main: X', c_j, the forward contraction ----
+    QOC_TRY(launch_prep(p->W, p->eig, p->M, N, J, p->dt, p->mshift, p->D, p->dstride, mixed ? 0 : 1,
+                        PREP_X, p->Ptil, p->Xp, p->Mtil, p->status, st, p->ws[0]));
+    if (p->timing) cudaEventRecord(p->ev[3], st);
+    QOC_TRY(cudaStreamWaitEvent(st, p->join, 0));
+    QOC_TRY(launch_pointwise(p->W, p->Ptil, p->Xp, p->a_hat, p->l_hat, mixed, N, J, kappa, p->p_hat,
+                             p->y_hat, p->g, p->c, PW_C, st, p->ws[0]));
+    QOC_TRY(launch_drift(p->a_hat, mixed, N, J, p->scal + 1, st));
+    if (p->timing) cudaEventRecord(p->ev[4], st);
+    QOC_TRY(cudaStreamWaitEvent(st, p->ev_yhat, 0));
+    QOC_TRY(launch_block_src(p->D, p->dstride, N, J, bs, 0, mixed, p->p_hat, p->y_hat, p->vstride,
+                             p->Qf, p->Wf, p->Gf, p->qstride, p->gstride, BS_WG, st, p->ws[0]));
+    QOC_TRY(cudaStreamWaitEvent(st, p->ev_tangent, 0));
+    QOC_TRY(launch_block_contract(p->XS, p->Wf, p->Gf, p->qstride, p->gstride, Bsrc, p->Kp, N, K, J,
+                                  bs, 0, mixed, p->U, st));
+    QOC_TRY(cudaStreamWaitEvent(st, p->ev_panels, 0));
+  } else if (order >= 2) {
     // ---- panels ----
     QOC_TRY(cudaStreamWaitEvent(ps, p->ev_ptil, 0));
     QOC_TRY(cudaStreamWaitEvent(ps, p->ev_state, 0));
@@ -366,7 +430,7 @@ qoc_status enqueue_blocked(qoc_problem* p, int order, double* out_dev) {
   }
   if (p->timing) cudaEventRecord(p->ev[5], st);
   QOC_TRY(launch_assemble(p->B, p->Kp, p->f, p->g, p->c, p->V, p->U, mixed, p->SJ, N, J, K,
-                          p->w_f, p->w_t, soa ? 0 : 1, order >= 2, p->work, out_dev, p->hess_raw,
+                          p->w_f, p->w_t, soa ? (split ? 2 : 0) : 1, order >= 2, p->work, out_dev, p->hess_raw,
                           p->scal + 2, st, p->identity_basis));
   if (p->timing) cudaEventRecord(p->ev[6], st);
   return QOC_OK;
@@ -628,7 +692,7 @@ void qoc_destroy_problem(qoc_problem* p) {
       cudaStreamSynchronize(*sp);
       cudaStreamDestroy(*sp);
     }
-  for (cudaEvent_t e : {p->fork, p->join, p->ev_state, p->ev_ptil, p->ev_panels, p->ev_bprod, p->ev_fprod, p->ev_yhat})
+  for (cudaEvent_t e : {p->fork, p->join, p->ev_state, p->ev_ptil, p->ev_panels, p->ev_bprod, p->ev_fprod, p->ev_yhat, p->ev_phat, p->ev_tangent})
     if (e) cudaEventDestroy(e);
   if (p->own_stream && p->stream) cudaStreamDestroy(p->stream);
   delete p;
@@ -715,7 +779,7 @@ qoc_status qoc_create_problem(int N, const double* H0, const double* M, const do
     if ((e = cudaStreamCreateWithPriority(&p->pstream, cudaStreamNonBlocking, hi)) != cudaSuccess)
       return fail(e);
   }
-  for (cudaEvent_t* ep : {&p->fork, &p->join, &p->ev_state, &p->ev_ptil, &p->ev_panels, &p->ev_bprod, &p->ev_fprod, &p->ev_yhat})
+  for (cudaEvent_t* ep : {&p->fork, &p->join, &p->ev_state, &p->ev_ptil, &p->ev_panels, &p->ev_bprod, &p->ev_fprod, &p->ev_yhat, &p->ev_phat, &p->ev_tangent})
     if ((e = cudaEventCreateWithFlags(ep, cudaEventDisableTiming)) != cudaSuccess) return fail(e);
 #define ALLOC(ptr, bytes) \
   if ((e = dalloc(p, &(ptr), (bytes))) != cudaSuccess) return fail(e)
@@ -892,6 +956,12 @@ qoc_status qoc_get_tr_phase_times(const qoc_problem* p, double* out) {
 qoc_status qoc_set_pipeline(qoc_problem* p, int chunks) {
   if (!p || chunks < -1 || chunks > qoc_problem::kMaxChunks) return QOC_EINVAL;
   p->pipeline = chunks;
+  return QOC_OK;
+}
+
+qoc_status qoc_set_mu_split(qoc_problem* p, int split) {
+  if (!p || split < -1 || split > 1) return QOC_EINVAL;
+  p->mu_split = split;
   return QOC_OK;
 }
 
@@ -1303,6 +1373,7 @@ struct qoc_batch {
   cudaEvent_t fork[4] = {};                // per sweep: fork of the groups
   cudaEvent_t gjoin[NG] = {};              // per group: its join
   std::vector<size_t> toff, ooff;
+  std::vector<char> split;             // per problem: split second-order adjoint (at creation)
   size_t ntheta = 0, nout = 0;
   double *theta = nullptr, *out = nullptr, *hbuf = nullptr;
   int* hstat = nullptr;
@@ -1359,7 +1430,8 @@ qoc_status batch_phase(qoc_batch* b, int i, int phase, cudaStream_t s) {
         QOC_TRY(launch_block_contract(p->Xmu, p->Wb, p->Gb, p->qstride, p->gstride, Bsrc, p->Kp, N, K,
                                       J, bs, 1, mixed, p->V, s));
       QOC_TRY(launch_assemble(p->B, p->Kp, p->f, p->g, p->c, p->V, p->U, mixed, p->SJ, N, J, K,
-                              p->w_f, p->w_t, p->hess_method == QOC_HESS_SECOND_ORDER_ADJOINT ? 0 : 1,
+                              p->w_f, p->w_t,
+                              p->hess_method == QOC_HESS_SECOND_ORDER_ADJOINT ? (b->split[i] ? 2 : 0) : 1,
                               1, p->work, out, p->hess_raw, p->scal + 2, s, p->identity_basis));
       return QOC_OK;
   }
@@ -1475,8 +1547,10 @@ qoc_status qoc_batch_create(qoc_problem* const* problems, int n, void* cuda_stre
     b->ntheta += p->K;
     b->nout += 1 + (size_t)p->K + (size_t)p->K * p->K;
     // descriptor lists of the four batched sweeps
+    const bool split = mu_split_on(p);
+    b->split.push_back(split ? 1 : 0);
     BSweepArgs args[4] = {chain_sweep_args(p, 0), chain_sweep_args(p, 1), panel_sweep_args(p, 0),
-                           panel_sweep_args(p, 1)};
+                           panel_sweep_args(p, 1, split)};
     for (int k = 0; k < 4; ++k) {
       if (k == 3 && p->hess_method != QOC_HESS_SECOND_ORDER_ADJOINT) continue;
       const int mx = p->precision == QOC_MIXED_FP32 ? 1 : 0;

@@ -7,6 +7,15 @@
 //   grad = B^T (2 w_f f + g)                       (Eq. dLdf)
 //   Hess = B^T diag(2 w_f + c) B + B^T V + B^T U   (Eq. d2Ldf2, second-order adjoint)
 //   Hess = B^T diag(2 w_f + c) B + 2 w_t Re(S_J^H S_J) + B^T U + U^T B   (tangent form)
+//   Hess = B^T diag(2 w_f + c) B + B^T V0 + 2 w_t Re(S_J^H S_J) + B^T U  (split adjoint)
+// Split adjoint: the sweep of mu is linear, mu = mu0 + mu_T with mu0 from the
+// sources and a zero terminal value and mu_T the terminal value 2 w_t S_J
+// carried back by the adjoint propagators alone.  The contraction of mu_T
+// with the tangent sources telescopes: sum_j b_jl Re(p_j^H Phi(j+1, J)^H
+// mu_J,m) = Re(S_J,l^H mu_J,m), since S_J,l = sum_j Phi(j+1, J) p_j b_jl.  So
+// B^T V = B^T V0 + 2 w_t Re(S_J^H S_J), and the mu sweep no longer waits for
+// the tangent sweep's S_J.
+// method: 0 second-order adjoint, 1 tangent form, 2 split adjoint.
 // The reported Hessian is (H + H^T)/2; |H - H^T|_F / |H|_F is kept.
 // An identity basis (the maximal model, B = I) skips the contractions over j.
 #include "common.cuh"
@@ -89,9 +98,9 @@ cudaError_t launch_terminal(const double* f, int J, const void* a_hat, int mixed
 // ---------------------------------------------------------------------------
 // Hessian: partial sums over chunks of steps.  Tile of 16 x 16 (l, m) per
 // CTA, one output per thread; blockIdx.z = chunk of JC steps.
-//   acc1[l][m] = sum_j b_jl ( (2 w_f + c_j) b_jm + U_jm + (SOA ? V_jm : 0) )
+//   acc1[l][m] = sum_j b_jl ( (2 w_f + c_j) b_jm + U_jm + (method != 1 ? V_jm : 0) )
 //   acc2[l][m] = sum_j U_jl b_jm                      (tangent form only)
-// The extra chunk z == nchunk adds 2 w_t Re(S_J^H S_J) (tangent form).
+// The extra chunk z == nchunk adds 2 w_t Re(S_J^H S_J) (tangent form and split adjoint).
 // ---------------------------------------------------------------------------
 constexpr int HT = 16;
 constexpr int JC = 64;
@@ -120,7 +129,7 @@ __global__ void k_hess_partial(const double* __restrict__ B, int Kp, const doubl
       double zv = cj * bmv;
       if (ok && mm < K) {
         zv += (double)U[(size_t)j * K + mm];
-        if (method == 0) zv += (double)V[(size_t)j * K + mm];
+        if (method != 1) zv += (double)V[(size_t)j * K + mm];
       }
       zm[jj][t] = zv;
       ul[jj][t] = (ok && ll < K && method == 1) ? (double)U[(size_t)j * K + ll] : 0.0;
@@ -130,7 +139,7 @@ __global__ void k_hess_partial(const double* __restrict__ B, int Kp, const doubl
       acc1 = fma(bl[jj][tl], zm[jj][tm], acc1);
       if (method == 1) acc2 = fma(ul[jj][tl], bm[jj][tm], acc2);
     }
-  } else if (method == 1 && l < K && m < K) {
+  } else if (method != 0 && l < K && m < K) {
     double s = 0;
     for (int i = 0; i < N; ++i) {
       double2 a = SJ[(size_t)l * N + i], b = SJ[(size_t)m * N + i];
@@ -183,7 +192,15 @@ __global__ void k_hess_identity(const double* __restrict__ c, const TU* __restri
   // every other term it adds is an exact zero
   double h = (2.0 * w_f + c[l]) * (l == m ? 1.0 : 0.0);
   h += (double)U[(size_t)l * K + m];
-  if (method == 0) h += (double)V[(size_t)l * K + m];
+  if (method != 1) h += (double)V[(size_t)l * K + m];
+  if (method == 2) {   // + the S_J^H S_J chunk last
+    double sjs = 0;
+    for (int i = 0; i < N; ++i) {
+      const double2 a = SJ[(size_t)l * N + i], b = SJ[(size_t)m * N + i];
+      sjs = fma(a.x, b.x, fma(a.y, b.y, sjs));
+    }
+    h = h + 2.0 * w_t * sjs;
+  }
   if (method == 1) {
     // tangent form: + U_ml (the chunk holding step m; the chunk sums add the
     // two in either order, which rounds the same) + the S_J^H S_J chunk last
@@ -273,7 +290,7 @@ cudaError_t launch_assemble(const double* B, int Kp, const double* f, const doub
                                                   method, hess_raw);
   } else {
     const int nchunk = (J + JC - 1) / JC;
-    const int nz = nchunk + (method == 1 ? 1 : 0);
+    const int nz = nchunk + (method != 0 ? 1 : 0);
     dim3 grid((K + HT - 1) / HT, (K + HT - 1) / HT, nz);
     if (uv_f32)
       k_hess_partial<float><<<grid, HT * HT, 0, st>>>(B, Kp, c, static_cast<const float*>(V),

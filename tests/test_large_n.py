@@ -101,7 +101,9 @@ def test_largest_system_200_steps(largest_200, precision, block_steps):
     tol = TOL[precision]
     tin = {q.QOC_FP64: 1e-10, q.QOC_MIXED_FP32: 1e-5}[precision]
     trow = {q.QOC_FP64: 1e-9, q.QOC_MIXED_FP32: 1e-4}[precision]
-    with q.Problem(prob, precision=precision, block_steps=block_steps) as P:
+    # the unsplit second-order adjoint, so that V is the full contraction the
+    # stored reference holds
+    with q.Problem(prob, precision=precision, block_steps=block_steps, mu_split=False) as P:
         assert P.precision()[0] == precision
         J, g, H = P.eval_grad_hess(theta)
         assert abs(J - ref["J"]) <= tol * abs(ref["J"]), (J, ref["J"])

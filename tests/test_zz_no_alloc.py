@@ -49,7 +49,8 @@ def test_noalloc_assembly_matches_eval_grad_hess(precision):
     for (N, K, J), seed in cases:
         prob = inputs.small_problem(N, K, J, seed=seed)
         theta = inputs.eval_theta(K, seed + 100, 0.5)
-        with q.Problem(prob, precision=precision) as P:
+        # the no-alloc assembly takes the full contraction V (unsplit adjoint)
+        with q.Problem(prob, precision=precision, mu_split=False) as P:
             Jv, g_ref, H_ref = P.eval_grad_hess(theta)
             f = P.buffer(_lib.QOC_BUF_F)
             g = P.buffer(_lib.QOC_BUF_G)
