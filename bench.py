@@ -413,7 +413,7 @@ def roofline(N, J, ph, fp64_tf):
                    "M~ = W^T M W (4 N^3) and X' (8 N^3) per step"),
         "k_eig_refine": (eig_flops_per_step(N) * J, ph["k_eig_refine"],
                          "the whole eigendecomposition's 9 N^3 per step, credited to the refinement kernel"),
-        "eig (k_eig_jacobi32 + k_eig_refine)": (eig_flops_per_step(N) * J, ph["k_eig_jacobi"] + ph["k_eig_refine"],
+        "eig (binary32 Jacobi start + k_eig_refine)": (eig_flops_per_step(N) * J, ph["k_eig_jacobi"] + ph["k_eig_refine"],
                                                 "9 N^3 per step over both eigensolver kernels"),
     }
     kern = {}
