@@ -184,14 +184,47 @@ def test_zero_control_and_degenerate_spectrum():
         check_eval(prob, theta, q.QOC_MIXED_FP32)
 
 
+def test_doubly_degenerate_spectrum_n32():
+    """N = 32 made of two identical decoupled 16 x 16 systems (H0 + f M =
+    Q (A ⊕ A) Q^T with a random orthogonal Q): every eigenvalue is exactly
+    doubly degenerate at every step and every control value, and every
+    entry is dense.  The binary32 start ranks the ties by index, each pair
+    is a cluster for the refinement (the binary64 clean-up on every step),
+    and the propagator derivatives stay well defined (Daleckii-Krein with
+    divided differences at equal points)."""
+    rng = np.random.default_rng(3232)
+    n, K, J, dt = 16, 4, 48, 0.05
+    A0 = np.diag(np.sort(rng.uniform(-2.0, 0.0, n)))
+    Bx = rng.normal(0.0, 0.05, (n, n))
+    A0 = A0 + (Bx + Bx.T) / 2
+    Mx = rng.normal(0.0, 0.3, (n, n))
+    M1 = (Mx + Mx.T) / 2
+    Q, _ = np.linalg.qr(rng.normal(size=(2 * n, 2 * n)))
+    H0 = Q @ np.kron(np.eye(2), A0) @ Q.T
+    M = Q @ np.kron(np.eye(2), M1) @ Q.T
+    H0 = (H0 + H0.T) / 2
+    M = (M + M.T) / 2
+    prob = inputs.small_problem(N=2 * n, K=K, J=J, seed=33, dt=dt, basis="random")
+    prob.H0, prob.M = H0, M
+    lam = np.linalg.eigvalsh(H0)
+    assert np.abs(lam[1::2] - lam[0::2]).max() <= 1e-12 * np.abs(lam).max()
+    theta = inputs.eval_theta(K, 34)
+    ref = orc.evaluate(prob, theta, order=2, keep=True)
+    check_eval(prob, theta, q.QOC_FP64, ref=ref)
+    check_eval(prob, theta, q.QOC_MIXED_FP32, ref=ref)
+
+
 @pytest.mark.parametrize("precision", [q.QOC_FP64, q.QOC_MIXED_FP32], ids=["fp64", "mixed"])
-def test_avoided_crossing(precision):
+@pytest.mark.parametrize("N", [8, 32])
+def test_avoided_crossing(precision, N):
     """A step lands exactly on an avoided crossing (gap 2e-6 against |H| ~ 5):
     levels 0 and 1 of H0 + f M cross at f = 1 with coupling 1e-6, the whole
     system rotated by a random orthogonal Q so every entry is dense.  The
-    binary32 eigenvector start mixes the close pair by a large angle there."""
+    binary32 eigenvector start mixes the close pair by a large angle there.
+    N = 32 takes the register-resident start and the refinement's step order
+    (near-degenerate steps first)."""
     rng = np.random.default_rng(77)
-    N, K, J, dt, c = 8, 3, 120, 0.02, 1e-6
+    K, J, dt, c = 3, 120, 0.02, 1e-6
     A = rng.normal(0.0, 0.05, (N - 2, N - 2))
     H0 = np.zeros((N, N)); M = np.zeros((N, N))
     H0[:2, :2] = [[0.0, c], [c, 1.0]]
