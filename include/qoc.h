@@ -319,7 +319,7 @@ qoc_status qoc_get_diagnostics(const qoc_problem* p, double* norm_drift, double*
 
 /* Per-kernel timing of the last evaluation (timing enabled), milliseconds
  * between events, in this order:
- *   0 control (f = B theta)         1 binary32 Jacobi (k_eig_jacobi32)
+ *   0 control (f = B theta)         1 binary32 Jacobi (k_eig_jacobi32_reg at N = 32, else k_eig_jacobi32)
  *   2 binary64 refinement or the binary64 Jacobi (k_eig_refine / k_eig_jacobi)
  *   3 propagator increments D_j     4 derivative preparation (M~, P~, X')
  *   5 state and costate chains      6 pointwise contractions
