@@ -50,9 +50,10 @@ struct qoc_problem {
   cudaEvent_t ev_state = nullptr, ev_ptil = nullptr, ev_panels = nullptr;
   cudaEvent_t ev_bprod = nullptr;       // backward block products done (panel stream)
   cudaEvent_t ev_fprod = nullptr;       // forward block products done (panel stream)
-  cudaEvent_t ev_yhat = nullptr;        // y^ and g done, tangent panel swept (panel stream)
-  cudaEvent_t ev_phat = nullptr;        // p^ (and r_j) done (split second-order adjoint)
-  cudaEvent_t ev_tangent = nullptr;     // tangent panel swept (split second-order adjoint)
+  cudaEvent_t ev_yhat = nullptr;        // y^ and g done (chain stream)
+  cudaEvent_t ev_phat = nullptr;        // p^ (and r_j) done (panel stream)
+  cudaEvent_t ev_tangent = nullptr;     // tangent panel swept (panel stream)
+  cudaEvent_t ev_musrc = nullptr;       // second-order sources done (chain stream, unsplit adjoint)
   int timing = 0;
   int sched = 0;                        // 0 sequential, 1 three-stream (time-blocked, order >= 1)
   // forward pipeline: the refinement and increments in chunks of steps, the
@@ -262,11 +263,14 @@ BSweepArgs panel_sweep_args(qoc_problem* p, int bwd, bool mu_split = false) {
 //       costate: pointwise c_j, drift, the forward contraction (W, Gamma,
 //       U); assembly
 //   chains (high priority): state chain (after the forward block products)
-//       + fill, terminal; costate chain (after the backward ones) + fill
+//       + fill, terminal; costate chain (after the backward ones) + fill;
+//       order 2, after the costate and p^: y^, g -> second-order adjoint
+//       sources (and, split, its sweep and contraction V)
 //   panels (high priority): forward, then backward block products at the
 //       fork; order 2, as soon as the state and P~ exist: p^ -> propagated
-//       sources -> tangent panel sweep; after the costate: y^, g ->
-//       second-order adjoint sources and sweep -> contraction V
+//       sources -> tangent panel sweep; unsplit, then the second-order
+//       adjoint sweep (its sources ready beside the tangent sweep) ->
+//       contraction V
 // so that the latency-bound sweeps overlap the binary64 X' preparation and
 // each other instead of following them, and the chain state -> costate ->
 // second-order adjoint carries nothing it does not need.
@@ -385,16 +389,23 @@ qoc_status enqueue_blocked(qoc_problem* p, int order, double* out_dev) {
                              p->y_hat, p->g, p->c, PW_P, ps, p->ws[2], p->rvec));
     QOC_TRY(launch_block_src(p->D, p->dstride, N, J, bs, 0, mixed, p->p_hat, p->y_hat, p->vstride,
                              p->Qf, p->Wf, p->Gf, p->qstride, p->gstride, BS_Q, ps, p->ws[2]));
+    QOC_TRY(cudaEventRecord(p->ev_phat, ps));
     QOC_TRY(launch_bsweep(panel_sweep_args(p, 0), mixed, ps));
-    QOC_TRY(cudaStreamWaitEvent(ps, p->join, 0));
+    QOC_TRY(cudaEventRecord(p->ev_tangent, ps));
+    // y^, g and the second-order sources need the costate and p^ but not the
+    // tangent panel: the chain stream takes them after the costate, beside
+    // the tangent sweep, and the mu sweep follows the tangent sweep directly
+    QOC_TRY(cudaStreamWaitEvent(cs, p->ev_phat, 0));
     QOC_TRY(launch_pointwise(p->W, p->Ptil, p->Xp, p->a_hat, p->l_hat, mixed, N, J, kappa, p->p_hat,
-                             p->y_hat, p->g, p->c, PW_Y | PW_RUSE, ps, p->ws[2], p->rvec));
+                             p->y_hat, p->g, p->c, PW_Y | PW_RUSE, cs, p->ws[1], p->rvec));
     // the forward contraction (W, Gamma and U) is not on the way to the
     // second-order adjoint sweep: the main stream takes it, beside that sweep
-    QOC_TRY(cudaEventRecord(p->ev_yhat, ps));
+    QOC_TRY(cudaEventRecord(p->ev_yhat, cs));
     if (soa) {
       QOC_TRY(launch_block_src(p->D, p->dstride, N, J, bs, 1, mixed, p->y_hat, p->p_hat, p->vstride,
-                               p->Qb, p->Wb, p->Gb, p->qstride, p->gstride, BS_Q | BS_WG, ps, p->ws[2]));
+                               p->Qb, p->Wb, p->Gb, p->qstride, p->gstride, BS_Q | BS_WG, cs, p->ws[1]));
+      QOC_TRY(cudaEventRecord(p->ev_musrc, cs));
+      QOC_TRY(cudaStreamWaitEvent(ps, p->ev_musrc, 0));
       QOC_TRY(launch_bsweep(panel_sweep_args(p, 1), mixed, ps));
       QOC_TRY(launch_block_contract(p->Xmu, p->Wb, p->Gb, p->qstride, p->gstride, Bsrc, p->Kp, N, K,
                                     J, bs, 1, mixed, p->V, ps));
@@ -413,6 +424,7 @@ qoc_status enqueue_blocked(qoc_problem* p, int order, double* out_dev) {
     QOC_TRY(cudaStreamWaitEvent(st, p->ev_yhat, 0));
     QOC_TRY(launch_block_src(p->D, p->dstride, N, J, bs, 0, mixed, p->p_hat, p->y_hat, p->vstride,
                              p->Qf, p->Wf, p->Gf, p->qstride, p->gstride, BS_WG, st, p->ws[0]));
+    QOC_TRY(cudaStreamWaitEvent(st, p->ev_tangent, 0));
     QOC_TRY(launch_block_contract(p->XS, p->Wf, p->Gf, p->qstride, p->gstride, Bsrc, p->Kp, N, K, J,
                                   bs, 0, mixed, p->U, st));
     QOC_TRY(cudaStreamWaitEvent(st, p->ev_panels, 0));
@@ -692,7 +704,7 @@ void qoc_destroy_problem(qoc_problem* p) {
       cudaStreamSynchronize(*sp);
       cudaStreamDestroy(*sp);
     }
-  for (cudaEvent_t e : {p->fork, p->join, p->ev_state, p->ev_ptil, p->ev_panels, p->ev_bprod, p->ev_fprod, p->ev_yhat, p->ev_phat, p->ev_tangent})
+  for (cudaEvent_t e : {p->fork, p->join, p->ev_state, p->ev_ptil, p->ev_panels, p->ev_bprod, p->ev_fprod, p->ev_yhat, p->ev_phat, p->ev_tangent, p->ev_musrc})
     if (e) cudaEventDestroy(e);
   if (p->own_stream && p->stream) cudaStreamDestroy(p->stream);
   delete p;
@@ -779,7 +791,7 @@ qoc_status qoc_create_problem(int N, const double* H0, const double* M, const do
     if ((e = cudaStreamCreateWithPriority(&p->pstream, cudaStreamNonBlocking, hi)) != cudaSuccess)
       return fail(e);
   }
-  for (cudaEvent_t* ep : {&p->fork, &p->join, &p->ev_state, &p->ev_ptil, &p->ev_panels, &p->ev_bprod, &p->ev_fprod, &p->ev_yhat, &p->ev_phat, &p->ev_tangent})
+  for (cudaEvent_t* ep : {&p->fork, &p->join, &p->ev_state, &p->ev_ptil, &p->ev_panels, &p->ev_bprod, &p->ev_fprod, &p->ev_yhat, &p->ev_phat, &p->ev_tangent, &p->ev_musrc})
     if ((e = cudaEventCreateWithFlags(ep, cudaEventDisableTiming)) != cudaSuccess) return fail(e);
 #define ALLOC(ptr, bytes) \
   if ((e = dalloc(p, &(ptr), (bytes))) != cudaSuccess) return fail(e)
