@@ -1,7 +1,7 @@
 // Binary32 two-sided Jacobi start of the eigendecomposition H_j = W_j Lambda_j W_j^T
-// (Sec. III-B: every step's Hamiltonian H0 + f_j M is diagonalised before the
-// first- and second-order adjoint sweeps) for exactly 32 x 32 matrices, with
-// the matrix held in registers.
+// (Sec. III-A: exp of each step's Hamiltonian H0 + f_j M and its derivatives
+// come from that eigendecomposition, stored in the first loop of Alg. 1 and
+// Alg. 2) for exactly 32 x 32 matrices, with the matrix held in registers.
 //
 // One warp per step j.  Lane i holds row i of A and row i of V.  In round r
 // (r = 1..31) every index i is paired with i ^ r, so the 16 pairs of a round
