@@ -44,6 +44,9 @@ UNIT = "evals/s"
 WORKLOAD = {"workload": "synthetic CI-shaped single problem, N=32 basis, K=64 sine/cosine "
                         "coefficients, J=4000 steps, T=20 (dt=0.005)",
             "N": 32, "K": 64, "J": 4000}
+# the `config` both arms print (the workload, and how the timed steps treat
+# the cache); what differs between the arms goes under `run`
+CONFIG = dict(WORKLOAD, l2="GPU arm: L2 flushed between timed steps (reference arm: host CPU)")
 # library kernel launches per gradient + Hessian evaluation on the time-blocked path:
 # control, binary32 Jacobi, binary64 refinement, 3 preparation parts (D, P~, X'),
 # 2 block products, state chain + fill, terminal, costate chain + fill, drift,
@@ -131,7 +134,7 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": dict(WORKLOAD, precision="fp64 (CPU oracle)"),
+            "data": "synthetic", "config": CONFIG, "run": {"precision": "fp64 (CPU oracle)"},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
                              "sample": f"each step: one whole oracle evaluation of the {WORKLOAD['J']}-step "
                                        f"workload (J, gradient, Hessian), timed whole; warm-up steps "
@@ -366,11 +369,14 @@ def run_ours(args):
                 "scaling": "weak", "vs_baseline": None,
                 "dtype": "f32 panels + f64" if prec == q.QOC_MIXED_FP32 else "f64",
                 "data": "synthetic",
-                "config": dict(WORKLOAD, precision=args.precision, l2="flushed between timed steps",
+                "config": CONFIG,
+                "run": dict(precision=args.precision,
                                parallelism=f"replicas x{world}" if world > 1 else "single problem",
                                pipeline_chunks=args.pipeline if args.pipeline >= 0 else "library choice (off)",
-                               hessian="second-order adjoint, terminal part in closed form "
-                                       "(qoc_set_mu_split default: mu and tangent panels side by side)",
+                               hessian=("second-order adjoint, unsplit (the qoc_set_mu_split built-in "
+                                        "choice for binary32 sweeps)" if prec == q.QOC_MIXED_FP32 else
+                                        "second-order adjoint, terminal part in closed form (the "
+                                        "qoc_set_mu_split built-in choice for binary64 sweeps)"),
                                launch=({"block_steps": tuned[prec]["block_steps"],
                                         "panel_columns": tuned[prec]["panel_columns"],
                                         "autotune_table_ms": tuned[prec]["table"]}
